@@ -1,0 +1,286 @@
+"""FP64 CPU oracle of the GS3LAM semantic-splatting rasterizer (test infrastructure).
+
+Only the tests, the smoke check and the benchmark's CPU-baseline leg may import
+this package.  The product path (the CUDA library and its binding) never calls
+it; there is no CPU fallback.  The C source `gs_oracle.c` is compiled with gcc
+into `oracle/_build/libgs_oracle.so` on first use (or by `build()`).
+
+Every function takes float64 numpy arrays (float32 inputs are widened exactly)
+and returns float64 results.  Images are planar [C, H, W].
+
+Parity status per function (pins live in tests/test_oracle_pins.py):
+  project       pinned: closed forms, Monte-Carlo EWA, rotation invariance
+  rects         pinned: brute-force tile/square intersection
+  bin_sort      pinned: brute-force per-tile lists
+  render_fwd    pinned: closed forms, brute force without tiles, Eq. 4 literal sum
+  render_bwd    pinned: central finite differences
+  project_bwd   pinned: central finite differences, translation invariance
+  loss          pinned: textbook softmax-CE, hand-computed L1, median by sorting
+  dsr           pinned: hand-sized arrays
+  pose_step     pinned: matrix exponential, first Adam step
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gs_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_build", "libgs_oracle.so")
+_lib = None
+
+# Raster parameter order of the C source.
+PARAM_NAMES = ("tile", "alpha_min", "alpha_max", "T_min", "z_near", "lowpass", "radius_sigma",
+               "bg_r", "bg_g", "bg_b")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (IEEE double, no contraction, no fast-math)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _L():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        _lib.or_count_instances.restype = ctypes.c_int64
+        _lib.or_bin_sort.restype = ctypes.c_int64
+        _lib.or_loss.restype = ctypes.c_double
+        _lib.or_dsr.restype = ctypes.c_double
+        _lib.or_lower_median.restype = ctypes.c_double
+    return _lib
+
+
+def _d(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+I64 = ctypes.c_int64
+
+
+@dataclasses.dataclass
+class Params:
+    tile: int = 16
+    alpha_min: float = 1.0 / 255.0
+    alpha_max: float = 0.99
+    T_min: float = 1e-4
+    z_near: float = 0.2
+    lowpass: float = 0.3
+    radius_sigma: float = 3.0
+    bg: tuple = (0.0, 0.0, 0.0)
+
+    def array(self):
+        return np.array([self.tile, self.alpha_min, self.alpha_max, self.T_min, self.z_near,
+                         self.lowpass, self.radius_sigma, *self.bg], dtype=np.float64)
+
+
+def _cam(cam):
+    return (np.array([cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy], np.float64),
+            _d(np.asarray(cam.T_cw, np.float64).reshape(16)))
+
+
+def _tiles(cam, tile):
+    tx = (cam.width + tile - 1) // tile
+    ty = (cam.height + tile - 1) // tile
+    return tx, ty
+
+
+# ------------------------------------------------------------------ projection
+def project(gs, cam, prm: Params):
+    n = gs.n
+    c, T = _cam(cam)
+    out = dict(uv=np.zeros((n, 2)), depth=np.zeros(n), depth_key=np.zeros(n, np.float32),
+               conic=np.zeros((n, 3)), opacity=np.zeros(n), radius=np.zeros(n, np.int32),
+               rect=np.zeros((n, 4), np.int32), touched=np.zeros(n, np.int32),
+               radius_real=np.zeros(n), cov2d=np.zeros((n, 3)))
+    a = [_d(gs.means), _d(gs.quats), _d(gs.log_scales), _d(gs.opacity_logits)]
+    _L().or_project(I64(n), *map(_p, a), _p(c), _p(T), _p(prm.array()),
+                    *(_p(out[k]) for k in ("uv", "depth", "depth_key", "conic", "opacity", "radius",
+                                           "rect", "touched", "radius_real", "cov2d")))
+    return out
+
+
+def rects(uv, radius, width, height, tile=16):
+    uv = _d(uv)
+    radius = np.ascontiguousarray(radius, np.int32)
+    n = radius.shape[0]
+    rect = np.zeros((n, 4), np.int32)
+    touched = np.zeros(n, np.int32)
+    _L().or_rects(I64(n), _p(uv), _p(radius), ctypes.c_int(width), ctypes.c_int(height),
+                  ctypes.c_int(tile), _p(rect), _p(touched))
+    return rect, touched
+
+
+def bin_sort(rect, depth_key, cams, tile=16, n_per_view=None):
+    """Keys, values and per-tile ranges of the (tile | depth) order over all views."""
+    rect = np.ascontiguousarray(rect, np.int32)
+    depth_key = np.ascontiguousarray(depth_key, np.float32)
+    nv = len(cams)
+    n_per_view = rect.shape[0] // nv if n_per_view is None else n_per_view
+    txs = np.array([_tiles(c, tile)[0] for c in cams], np.int32)
+    tpv = np.array([np.prod(_tiles(c, tile)) for c in cams], np.int32)
+    m = int(((rect[:, 2] - rect[:, 0]).astype(np.int64) * (rect[:, 3] - rect[:, 1])).sum())
+    keys = np.zeros(max(m, 1), np.uint64)
+    vals = np.zeros(max(m, 1), np.uint32)
+    ranges = np.zeros((int(tpv.sum()), 2), np.uint32)
+    got = _L().or_bin_sort(ctypes.c_int(nv), I64(n_per_view), _p(rect), _p(depth_key), _p(txs),
+                           _p(tpv), _p(keys), _p(vals), _p(ranges))
+    assert got == m
+    return keys[:m], vals[:m], ranges
+
+
+# ---------------------------------------------------------------------- render
+def render_fwd(cam, proj, rgb, feat, vals, ranges, prm: Params, view_offset=0, tile_offset=0):
+    W, H = cam.width, cam.height
+    D = feat.shape[1]
+    P = W * H
+    out = dict(rgb=np.zeros((3, H, W)), depth=np.zeros((H, W)), sil=np.zeros((H, W)),
+               feat=np.zeros((D, H, W)), T=np.zeros((H, W)), n_contrib=np.zeros((H, W), np.int32),
+               margin=np.zeros((H, W)))
+    args = [_d(proj["uv"]), _d(proj["conic"]), _d(proj["opacity"]), _d(proj["depth"]), _d(rgb), _d(feat)]
+    _L().or_render_fwd(ctypes.c_int(W), ctypes.c_int(H), ctypes.c_int(prm.tile), ctypes.c_int(D),
+                       I64(view_offset), I64(tile_offset), *map(_p, args),
+                       _p(np.ascontiguousarray(vals, np.uint32)), _p(np.ascontiguousarray(ranges, np.uint32)),
+                       _p(prm.array()), *(_p(out[k]) for k in ("rgb", "depth", "sil", "feat", "T",
+                                                               "n_contrib", "margin")))
+    return out
+
+
+def render_bwd(cam, proj, rgb, feat, vals, ranges, prm: Params, g_rgb, g_depth, g_sil, g_feat,
+               view_offset=0, tile_offset=0):
+    W, H = cam.width, cam.height
+    n = proj["uv"].shape[0]
+    D = feat.shape[1]
+    out = dict(uv=np.zeros((n, 2)), conic=np.zeros((n, 3)), opacity=np.zeros(n), depth=np.zeros(n),
+               rgb=np.zeros((n, 3)), feat=np.zeros((n, D)))
+    args = [_d(proj["uv"]), _d(proj["conic"]), _d(proj["opacity"]), _d(proj["depth"]), _d(rgb), _d(feat)]
+    g = [_d(g_rgb), _d(g_depth), _d(g_sil), _d(g_feat)]
+    _L().or_render_bwd(ctypes.c_int(W), ctypes.c_int(H), ctypes.c_int(prm.tile), ctypes.c_int(D),
+                       I64(view_offset), I64(tile_offset), *map(_p, args),
+                       _p(np.ascontiguousarray(vals, np.uint32)), _p(np.ascontiguousarray(ranges, np.uint32)),
+                       _p(prm.array()), *map(_p, g),
+                       *(_p(out[k]) for k in ("uv", "conic", "opacity", "depth", "rgb", "feat")))
+    return out
+
+
+def project_bwd(gs, cam, prm: Params, d_uv, d_conic, d_opacity, d_depth):
+    n = gs.n
+    c, T = _cam(cam)
+    out = dict(means=np.zeros((n, 3)), quats=np.zeros((n, 4)), log_scales=np.zeros((n, 3)),
+               opacity_logits=np.zeros(n), twist=np.zeros(6))
+    a = [_d(gs.means), _d(gs.quats), _d(gs.log_scales), _d(gs.opacity_logits)]
+    g = [_d(d_uv), _d(d_conic), _d(d_opacity), _d(d_depth)]
+    _L().or_project_bwd(I64(n), *map(_p, a), _p(c), _p(T), _p(prm.array()), *map(_p, g),
+                        *(_p(out[k]) for k in ("means", "quats", "log_scales", "opacity_logits", "twist")))
+    return out
+
+
+# ------------------------------------------------------------------------ loss
+@dataclasses.dataclass
+class LossWeights:
+    color: float = 0.5
+    depth: float = 1.0
+    sem: float = 0.01
+    big: float = 0.01
+    small: float = 0.001
+    mask_mode: int = 0      # 0 mapping (no mask), 1 tracking (Eq. 21 mask)
+    tau_obs: float = 0.99
+
+
+MAPPING = LossWeights()
+TRACKING = LossWeights(color=0.5, depth=1.0, sem=0.001, big=0.0, small=0.0, mask_mode=1)
+
+
+def loss(images, target, dec, w: LossWeights):
+    rgb, depth, sil, feat = images["rgb"], images["depth"], images["sil"], images["feat"]
+    D = feat.shape[0]
+    H, W = depth.shape
+    P = H * W
+    K = dec.W.shape[0]
+    out = dict(rgb=np.zeros((3, H, W)), depth=np.zeros((H, W)), sil=np.zeros((H, W)),
+               feat=np.zeros((D, H, W)), W=np.zeros((K, D)), b=np.zeros(K), mask=np.zeros((H, W)),
+               terms=np.zeros(3), median=np.zeros(1))
+    med = ctypes.c_double(0)
+    a = [_d(rgb), _d(depth), _d(sil), _d(feat), _d(target.rgb), _d(target.depth)]
+    total = _L().or_loss(I64(P), ctypes.c_int(D), ctypes.c_int(K), *map(_p, a),
+                         _p(np.ascontiguousarray(target.label, np.uint8)), _p(_d(dec.W)), _p(_d(dec.b)),
+                         ctypes.c_double(w.color), ctypes.c_double(w.depth), ctypes.c_double(w.sem),
+                         ctypes.c_int(w.mask_mode), ctypes.c_double(w.tau_obs),
+                         *(_p(out[k]) for k in ("rgb", "depth", "sil", "feat", "W", "b", "mask", "terms")),
+                         ctypes.byref(med))
+    out["median"] = med.value
+    out["total"] = total
+    return out
+
+
+def lower_median(values):
+    v = _d(values).ravel()
+    return _L().or_lower_median(I64(v.shape[0]), _p(v))
+
+
+def dsr(log_scales, lam_big, lam_small):
+    ls = _d(log_scales)
+    grad = np.zeros_like(ls)
+    stats = np.zeros(6)
+    n = ls.size // 3
+    val = _L().or_dsr(I64(n), _p(ls), ctypes.c_double(lam_big), ctypes.c_double(lam_small), _p(grad),
+                      _p(stats))
+    return val, grad, dict(mu=stats[0], sigma=stats[1], n_big=int(stats[2]), n_small=int(stats[3]),
+                           L_big=stats[4], L_small=stats[5])
+
+
+def pose_step(T, grad, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-15):
+    T = _d(np.asarray(T).reshape(16)).copy()
+    m = _d(m).copy()
+    v = _d(v).copy()
+    _L().or_pose_step(_p(T), _p(_d(grad)), _p(m), _p(v), ctypes.c_int(step), _p(_d(lr)),
+                      ctypes.c_double(b1), ctypes.c_double(b2), ctypes.c_double(eps))
+    return T.reshape(4, 4), m, v
+
+
+# ------------------------------------------------------------- full pipelines
+def forward(gs, cam, prm: Params):
+    """Projection, binning, sort and blend of one view; returns (proj, bins, images)."""
+    proj = project(gs, cam, prm)
+    keys, vals, ranges = bin_sort(proj["rect"], proj["depth_key"], [cam], prm.tile)
+    img = render_fwd(cam, proj, gs.rgb, gs.feat, vals, ranges, prm)
+    return proj, (keys, vals, ranges), img
+
+
+def backward_from_image_grads(gs, cam, prm: Params, proj, bins, g):
+    """All parameter gradients and the pose twist from image gradients g."""
+    _, vals, ranges = bins
+    r = render_bwd(cam, proj, gs.rgb, gs.feat, vals, ranges, prm, g["rgb"], g["depth"], g["sil"], g["feat"])
+    p = project_bwd(gs, cam, prm, r["uv"], r["conic"], r["opacity"], r["depth"])
+    return dict(means=p["means"], quats=p["quats"], log_scales=p["log_scales"],
+                opacity_logits=p["opacity_logits"], rgb=r["rgb"], feat=r["feat"], twist=p["twist"],
+                d2=r)
+
+
+def step(gs, cam, prm: Params, target, dec, w: LossWeights, with_dsr=True):
+    """One fwd+bwd iteration: render, loss (+ DSR), all gradients, pose twist."""
+    proj, bins, img = forward(gs, cam, prm)
+    L = loss(img, target, dec, w)
+    grads = backward_from_image_grads(gs, cam, prm, proj, bins, L)
+    total = L["total"]
+    if with_dsr and (w.big or w.small):
+        v, gls, stats = dsr(gs.log_scales, w.big, w.small)
+        total += v
+        grads["log_scales"] = grads["log_scales"] + gls
+        grads["dsr"] = stats
+    grads["W"], grads["b"] = L["W"], L["b"]
+    return dict(total=total, proj=proj, bins=bins, img=img, loss=L, grads=grads)
