@@ -1,0 +1,368 @@
+#!/usr/bin/env python
+"""Throughput of the GS3LAM semantic-splatting rasterizer on GB300.
+
+Metric: fwd+bwd iterations/s at 1200x680 with 1M Gaussians and 16-dim
+semantic features (synthetic room scene standing in for Replica-shaped
+RGB-D-semantic frames).  One step is the whole hot path once: projection,
+tile binning and depth sort, forward blend, decoder + losses, blend and
+projection backward to every parameter, the SE(3) pose-twist gradient,
+the depth-adaptive scale regularisation and the pose step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank renders its own frame: independent problems,
+weak scaling, no collective in the data path.  `--impl reference` times the
+FP64 CPU oracle on the host cores on the same workload (a bounded sample per
+step).  Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "fwd+bwd iters/s at 1200x680, 1M Gaussians, D=16; batched/BF16 vs plain FP32"
+WORKLOAD = dict(workload="room 1M Gaussians, D=16, K=8 classes, 1200x680 fx=600, single frame, FP32",
+                n=1_000_000, d=16, k=8, width=1200, height=680, fx=600.0)
+GRAD_MODE_NAME = "map+pose"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def make_workload():
+    from paper_2603_27781_gb300 import synth
+    room = synth.make_room(synth.SEED_SCENE)
+    gs = synth.room_field(WORKLOAD["n"], WORKLOAD["d"], seed=synth.SEED_SCENE, room=room)
+    cam = synth.room_camera(WORKLOAD["width"], WORKLOAD["height"], WORKLOAD["fx"], room=room)
+    tgt = synth.raycast_room(room, cam)
+    dec = synth.decoder(WORKLOAD["k"], WORKLOAD["d"])
+    start = synth.perturb_pose(cam.T_cw, 2.0, 0.05)
+    return gs, cam, tgt, dec, start
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------ CPU oracle
+def oracle_iteration(gs, cam, tgt, dec, crop_rows=None):
+    """One full oracle fwd+bwd iteration (optionally on a horizontal strip of the view)."""
+    import oracle
+    from paper_2603_27781_gb300 import synth
+    prm = oracle.Params()
+    if crop_rows is not None:
+        r0, r1 = crop_rows
+        cam = synth.camera(cam.width, r1 - r0, cam.fx, cam.fy, cam.cx, cam.cy - r0, T_cw=cam.T_cw)
+        tgt = synth.Frame(np.ascontiguousarray(tgt.rgb[:, r0:r1]), np.ascontiguousarray(tgt.depth[r0:r1]),
+                          np.ascontiguousarray(tgt.label[r0:r1]))
+    out = oracle.step(gs, cam, prm, tgt, dec, oracle.MAPPING)
+    return out["total"]
+
+
+def cpu_baseline(gs, cam, tgt, dec):
+    t0 = time.perf_counter()
+    oracle_iteration(gs, cam, tgt, dec)
+    dt = time.perf_counter() - t0
+    return {"value": 1.0 / dt, "unit": "iters/s", "cores": 1, "kind": "oracle",
+            "sample": f"one full FP64 oracle iteration of the same workload (single thread, {dt:.1f} s)"}
+
+
+def run_reference(args, rank, world):
+    import oracle
+    oracle.build()
+    if rank != 0:
+        return
+    gs, cam, tgt, dec, _ = make_workload()
+    strip = (0, 85)          # 1/8 of the rows per step, scaled by the pixel fraction
+    frac = (strip[1] - strip[0]) / cam.height
+    for _ in range(args.warmup):
+        oracle_iteration(gs, cam, tgt, dec, strip)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_iteration(gs, cam, tgt, dec, strip)
+        times.append(time.perf_counter() - t0)
+    t = float(np.mean(times))
+    value = frac / t
+    sample = (f"FP64 oracle, full iteration restricted to rows {strip[0]}-{strip[1]} of 680 per step "
+              f"(all 1M Gaussians projected), scaled by the pixel fraction {frac:.4f}")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(WORKLOAD, l2="inputs larger than L2"),
+            "cpu_baseline": {"value": value, "unit": "iters/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------- GPU arm
+def kernels_per_step(n_tiles):
+    tile_passes = max(1, math.ceil(math.ceil(math.log2(max(n_tiles, 2))) / 8))
+    project = 1
+    bin_sort = 3 + 1 + 4 + 3 + 1 + tile_passes + 1
+    fwd, loss, bwd, proj_bwd, pose, dsr, step = 1, 1, 1, 1, 1, 3, 1
+    return project + bin_sort + fwd + loss + bwd + proj_bwd + pose + dsr + step
+
+
+def fwd_bwd_flops(evaluated, blended, D):
+    """Algorithmic FP32 work of the two blend kernels (an FMA counts as 2, ex2 and min as 1)."""
+    eval_pair = 12                       # 2 sub, fmul+ffma, 2 fmul + ffma, ex2, fmul, min
+    fwd_blend = 12 + 2 * D               # T update, weight, 3 rgb + depth FMAs, silhouette add, D feature FMAs
+    bwd_blend = 54 + 6 * D               # T recovery, 5+D channels x (sub + 2 FMA), opacity/conic/centre terms
+    return evaluated * eval_pair + blended * fwd_blend, evaluated * eval_pair + blended * bwd_blend
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_2603_27781_gb300 import build as gbuild
+    from paper_2603_27781_gb300 import _lib as L
+    from paper_2603_27781_gb300 import raster
+
+    gbuild.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    gs, cam, tgt, dec, start_pose = make_workload()
+    field = raster.Field.from_numpy(gs, dev)
+    r = raster.fit_capacity(field, [cam], WORKLOAD["d"], margin=1.3, n_classes=WORKLOAD["k"], device=dev)
+    targets = dict(rgb=torch.as_tensor(tgt.rgb.reshape(3, -1)).to(dev),
+                   depth=torch.as_tensor(tgt.depth.ravel()).to(dev),
+                   label=torch.as_tensor(tgt.label.ravel()).to(dev))
+    W = torch.as_tensor(dec.W).to(dev)
+    b = torch.as_tensor(dec.b).to(dev)
+    w = raster.MAPPING
+    mode = L.GS_GRAD_MAP | L.GS_GRAD_POSE
+    T_state = torch.as_tensor(start_pose.reshape(1, 16), dtype=torch.float64).to(dev)
+    adam = torch.zeros(1, 12, dtype=torch.float64, device=dev)
+    pose_f32 = torch.zeros(1, 16, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    step_no = [0]
+
+    def step(ev=None):
+        rec = (lambda i: ev[i].record(stream)) if ev is not None else (lambda i: None)
+        rec(0)
+        r.project(field)
+        rec(1)
+        r.bin_sort()
+        rec(2)
+        r.render_fwd(field)
+        rec(3)
+        r.loss(targets, W, b, w)
+        rec(4)
+        r.render_bwd(field, mode)
+        rec(5)
+        r.project_bwd(field, mode)
+        rec(6)
+        r.pose_grad()
+        r.dsr(field, w.big, w.small)
+        step_no[0] += 1
+        r.pose_step(T_state, adam, step_no[0], pose_f32=pose_f32)
+        rec(7)
+
+    stages = ["project", "bin_sort", "render_fwd", "loss", "render_bwd", "project_bwd", "pose+dsr+step"]
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if r.status() != 0:
+        raise RuntimeError(f"binning status {r.status()} ({L.gs_strerror(r.status())})")
+    # pair counts of this frame (for the algorithmic work of the blend kernels)
+    r.count_blended = True
+    r.forward(field)
+    torch.cuda.synchronize()
+    evaluated = int(r.img_nc.sum(dtype=torch.int64).item())
+    blended = int(r.img_nb.sum(dtype=torch.int64).item())
+    r.count_blended = False
+    m_inst = r.instances()
+
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    events = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clocks:
+        t_wall = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(float(k))            # evict L2 between timed steps (outside the events)
+            step(events[k])
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    if world > 1:
+        dist.barrier()
+    per_stage = np.zeros(len(stages))
+    total = 0.0
+    for ev in events:
+        for s in range(len(stages)):
+            per_stage[s] += ev[s].elapsed_time(ev[s + 1])
+        total += ev[0].elapsed_time(ev[7])
+    per_stage /= args.steps
+    ms = total / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * 1000.0 / ms
+
+    # ---- end to end: host (pinned) inputs -> device -> step -> results back to host, every step
+    host = {k: getattr(field, k).cpu().pin_memory() for k in
+            ("means", "quats", "log_scales", "opacity_logits", "rgb", "feat")}
+    host_t = {k: v.cpu().pin_memory() for k, v in targets.items()}
+    outs = [r.d_means, r.d_quats, r.d_log_scales, r.d_logits, r.d_rgb, r.d_feat, r.loss_out, r.dsr_out,
+            r.d_twist]
+    host_out = [o.cpu().pin_memory() for o in outs]
+    h2d = sum(v.numel() * v.element_size() for v in list(host.values()) + list(host_t.values()))
+    d2h = sum(o.numel() * o.element_size() for o in outs)
+    e2e_ms = []
+    for k in range(args.e2e_steps):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for name, hv in host.items():
+            getattr(field, name).copy_(hv, non_blocking=True)
+        for name, hv in host_t.items():
+            targets[name].copy_(hv, non_blocking=True)
+        step()
+        for o, ho in zip(outs, host_out):
+            ho.copy_(o, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    e2e_value = world * 1000.0 / float(np.mean(e2e_ms))
+
+    # ---- roofline of the dominant kernel (from the per-stage events of the timed steps)
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        with open(pk_path) as fh:
+            peaks = json.load(fh)
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    props = torch.cuda.get_device_properties(dev)
+    fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s, FMA = 2
+    fwd_fl, bwd_fl = fwd_bwd_flops(evaluated, blended, WORKLOAD["d"])
+    dom = int(np.argmax(per_stage))
+    if stages[dom] in ("render_bwd", "render_fwd"):
+        fl = bwd_fl if stages[dom] == "render_bwd" else fwd_fl
+        achieved = fl / (per_stage[dom] * 1e-3) / 1e12
+        roof = {"kernel": "raster_bwd_kernel" if stages[dom] == "render_bwd" else "raster_fwd_kernel",
+                "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": None,
+                "peak_source": f"FP32 FMA issue: {props.multi_processor_count} SMs x 128 lanes x 2 x {sm_max:.0f} MHz",
+                "work": f"{evaluated} evaluated pairs, {blended} blended pairs per launch"}
+    else:
+        roof = {"kernel": stages[dom], "bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"),
+                "unit": "GB/s", "frac": None, "traffic": None}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(gs, cam, tgt, dec)
+
+    clk = clocks.summary()
+    line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded room scene; Replica-shaped)",
+            "config": dict(WORKLOAD, grad_mode=GRAD_MODE_NAME, l2="flushed between timed steps (512 MB write)",
+                           instances=m_inst, parallelism=f"replicas x{world}"),
+            "stages_ms": {s: float(t) for s, t in zip(stages, per_stage)},
+            "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "iters/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": kernels_per_step(r.n_tiles) * args.steps,
+            "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+            "wall_s": t_wall}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "gloo" if args.impl == "reference" else "nccl"
+        if backend == "nccl":
+            import torch
+            torch.cuda.set_device(local_rank)
+        dist.init_process_group(backend)
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank, world)
+        else:
+            run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,318 @@
+/*
+ * libgs — C ABI of the GB300 (sm_103a) semantic-splatting rasterizer.
+ *
+ * The library computes the differentiable splatting renderer of a Semantic
+ * Gaussian Field (GS3LAM, Sec. 3.2): projection of 3D Gaussians through a
+ * pinhole camera with EWA 2D covariances, binning into 16x16 tiles with a
+ * (tile | depth) sort, front-to-back alpha blending of colour, depth,
+ * D-dimensional semantic feature and silhouette, the tracking and mapping
+ * losses, and the backward pass to every Gaussian parameter and to the camera
+ * pose as an SE(3) twist (supplementary B.1).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every data pointer is DEVICE memory owned by the caller unless the
+ *    argument says "host".  The library never allocates device memory; the
+ *    scratch it needs is a caller-provided workspace sized by
+ *    gs_workspace_size().
+ *  - Calls are asynchronous on `stream` (a cudaStream_t; NULL = the legacy
+ *    default stream) and never synchronise the device, so they can be
+ *    captured in a CUDA graph.  Host-side argument errors return before any
+ *    launch; launch failures return GS_ERR_CUDA.  Conditions only the device
+ *    can see (instance overflow, a bounded wait that gave up) set a device
+ *    status word (gs_binning.status) that the caller reads after the stream
+ *    completes.  Nothing crosses the ABI as an exception, and the library
+ *    never exits, aborts or traps.
+ *  - Cameras and parameters are host structs copied into kernel arguments at
+ *    call time.
+ *  - Items: with V views and N Gaussians the projected records are indexed by
+ *    item = view * N + gaussian.  Tiles of view v are numbered after all tiles
+ *    of views 0..v-1; images of view v occupy pixels [pix_off(v), pix_off(v) +
+ *    W_v H_v) of every planar channel, pix_off(v) = sum of earlier W H.
+ *  - Gradient outputs are overwritten by each call unless documented "+=".
+ *    With several views, per-Gaussian gradients are summed over the views.
+ */
+#ifndef GS_H
+#define GS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef void *gs_stream; /* cudaStream_t */
+
+typedef enum {
+    GS_OK = 0,
+    GS_ERR_ARG = -1,         /* invalid argument (null pointer, bad size, bad enum) */
+    GS_ERR_CAPACITY = -2,    /* more tile instances than gs_binning.capacity */
+    GS_ERR_CUDA = -3,        /* a CUDA runtime call or launch failed */
+    GS_ERR_TIMEOUT = -4,     /* a bounded device-side wait gave up */
+    GS_ERR_UNSUPPORTED = -5  /* valid but not built (feature dim, tile size, dtype) */
+} gs_status;
+
+typedef enum { GS_F32 = 0, GS_BF16 = 1, GS_F16 = 2 } gs_dtype;
+
+/* gs_render_bwd modes (bit set).  GS3LAM optimises poses and the field
+ * separately (Sec. 3.2.3): tracking needs only the pose twist, mapping only
+ * the Gaussian parameters. */
+enum { GS_GRAD_MAP = 1, GS_GRAD_POSE = 2 };
+
+/* Pinhole camera.  T_cw is the row-major 4x4 world-to-camera transform
+ * (Sec. 3.2.1), OpenCV axes: x right, y down, z forward.  Pixel (x, y) samples
+ * the point (x + 0.5, y + 0.5). */
+typedef struct {
+    int32_t width, height;
+    float fx, fy, cx, cy;
+    float T_cw[16];
+} gs_camera;
+
+/* Raster parameters the paper leaves open (defaults in parentheses).
+ * tile: tile edge in pixels (16; the only size built).  A splat is skipped at a
+ * pixel where alpha < alpha_min (1/255), alpha is clamped to alpha_max (0.99),
+ * and a pixel stops blending before the splat that would take its
+ * transmittance below T_min (1e-4).  Gaussians with camera z <= z_near (0.2)
+ * are culled; lowpass (0.3 px^2) is added to the diagonal of Sigma2D; the
+ * splat radius is ceil(radius_sigma (3) * sqrt(lambda_max(Sigma2D))).
+ * bg_rgb is the colour behind the last splat (0,0,0). */
+typedef struct {
+    int32_t tile;
+    float alpha_min, alpha_max, T_min, z_near, lowpass, radius_sigma;
+    float bg_rgb[3];
+} gs_raster_params;
+
+/* The Semantic Gaussian Field of Eq. 1, structure of arrays.
+ *   means [n,3], quats [n,4] (w,x,y,z; normalised inside), log_scales [n,3]
+ *   (Eq. 2: S = diag(exp(log_s))), opacity_logits [n] (o = sigmoid), all f32;
+ *   rgb [n,3] in rgb_dtype (F32 or F16), feat [n,feat_dim] in feat_dtype (F32
+ *   or BF16).  feat_dim is one of 0, 4, 8, 16, 32; feat may be NULL when 0. */
+typedef struct {
+    int64_t n;
+    int32_t feat_dim;
+    const float *means;
+    const float *quats;
+    const float *log_scales;
+    const float *opacity_logits;
+    const void *rgb;
+    int32_t rgb_dtype;
+    const void *feat;
+    int32_t feat_dtype;
+} gs_gaussians;
+
+/* Projected splats, one record per item (float4-aligned, 16-byte aligned):
+ *   uvdo[4*item]  = (u, v, depth, opacity): centre g_i (supp. B.1), camera-frame
+ *                   depth d_i (Eq. 6) and the activated opacity o_i (Eq. 5);
+ *   conic[4*item] = (A, B, C, radius): Sigma2D^-1 = [[A, B], [B, C]] (Eq. 3, 5)
+ *                   and the integer pixel radius stored as a float;
+ *   tiles_touched[item] = tiles covered (0 = culled). */
+typedef struct {
+    float *uvdo;
+    float *conic;
+    int32_t *tiles_touched;
+} gs_projected;
+
+/* Tile binning.  keys[j] = (tile << 32) | bits(depth as float32) of sorted
+ * instance j (may be NULL if not wanted), vals[j] = its item; ranges[2t],
+ * ranges[2t+1] = [start, end) of tile t; n_inst = instance count (device
+ * int64); status = device word, 0 or a negative gs_status.  capacity bounds
+ * keys/vals. */
+typedef struct {
+    int64_t capacity;
+    uint64_t *keys;
+    uint32_t *vals;
+    uint32_t *ranges;
+    int64_t *n_inst;
+    int32_t *status;
+} gs_binning;
+
+/* Rendered images, planar f32 over all views' pixels (P = sum W H):
+ * rgb [3,P], depth [P], sil [P] (cumulative opacity, Eq. 10), feat [D,P],
+ * T_final [P] (transmittance after the last blended splat), n_contrib [P]
+ * (1-based position in the tile list of the last blended splat) and, if not
+ * NULL, n_blended [P] (number of splats blended into the pixel). */
+typedef struct {
+    float *rgb;
+    float *depth;
+    float *sil;
+    float *feat;
+    float *T_final;
+    int32_t *n_contrib;
+    int32_t *n_blended;
+} gs_images;
+
+/* Gradients of the loss w.r.t. the rendered images, same layout as gs_images.
+ * sil may be NULL (treated as zero). */
+typedef struct {
+    const float *rgb;
+    const float *depth;
+    const float *sil;
+    const float *feat;
+} gs_image_grads;
+
+/* Writable image gradients produced by gs_loss_fwd_bwd. */
+typedef struct {
+    float *rgb;
+    float *depth;
+    float *sil;
+    float *feat;
+} gs_image_grads_out;
+
+/* Gradients w.r.t. the gs_gaussians parameters, all f32, same shapes. */
+typedef struct {
+    float *means;
+    float *quats;
+    float *log_scales;
+    float *opacity_logits;
+    float *rgb;
+    float *feat;
+} gs_gaussian_grads;
+
+/* Targets of the losses, planar over all views' pixels: rgb [3,P] f32,
+ * depth [P] f32 (<= 0: no measurement), label [P] u8 (255: unlabelled). */
+typedef struct {
+    const float *rgb;
+    const float *depth;
+    const uint8_t *label;
+} gs_targets;
+
+/* Loss weights and mode.  mask_mode 0 = mapping (Eq. 18 without the SSIM and
+ * DSR terms), 1 = tracking (Eq. 21 with the M_obs mask, tau_obs threshold on
+ * the silhouette).  n_classes = K of the linear decoder (<= 32). */
+typedef struct {
+    float color, depth, sem;
+    int32_t mask_mode;
+    float tau_obs;
+    int32_t n_classes;
+} gs_loss_params;
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int gs_version(void);
+
+/* Human-readable text of a status code (static storage). */
+const char *gs_strerror(int status);
+
+/* Bytes of workspace needed by gs_bin_sort, gs_loss_fwd_bwd and gs_dsr for n
+ * Gaussians, n_views host cameras, an instance capacity and a
+ * feature dimension.  One buffer of this size serves all of them in stream
+ * order.  Must be 256-byte aligned.  Returns 0 on invalid arguments. */
+size_t gs_workspace_size(int64_t n, int n_views, const gs_camera *cams, int64_t inst_capacity,
+                         int feat_dim);
+
+/* Projection (Eq. 2, 3; supp. B.1).  For every view and Gaussian: quaternion
+ * and scale to Sigma, camera-frame centre p = R_cw mu + t_cw, pinhole centre
+ * (u, v) = (fx x/z + cx, fy y/z + cy), Sigma2D = J R_cw Sigma R_cw^T J^T +
+ * lowpass I, its inverse (in f64 when near singular), the radius and the number
+ * of tiles it covers.  The depth is computed as the f32 fused chain
+ * fma(r20, x, fma(r21, y, fma(r22, z, t_z))).  pose_dev, if not NULL, is a
+ * device f32 [n_views,16] array of world-to-camera transforms that replaces
+ * cams[v].T_cw (for device-resident poses); intrinsics always come from cams.
+ * out arrays hold n_views * n items. */
+gs_status gs_project(const gs_gaussians *g, const gs_camera *cams, int n_views,
+                     const float *pose_dev, const gs_raster_params *p, gs_projected *out,
+                     gs_stream stream);
+
+/* Binning and depth sort (Sec. 3.2.1: "sorting the Gaussians in depth order";
+ * tile-based rasterisation).  Emits one instance per (item, covered tile) and
+ * orders instances by (tile, f32 depth bits, item), i.e. a stable sort by the
+ * 64-bit key (tile << 32 | depth bits) of items listed in index order.  Writes
+ * ranges for every tile (empty tiles get [0,0)), n_inst, and keys if non-NULL.
+ * If the count exceeds out->capacity, *out->status = GS_ERR_CAPACITY and the
+ * binning is incomplete (its required size is still written to n_inst).
+ * ws: workspace of ws_bytes >= gs_workspace_size(...). */
+gs_status gs_bin_sort(int64_t n, const gs_projected *proj, const gs_camera *cams, int n_views,
+                      const gs_raster_params *p, void *ws, size_t ws_bytes, gs_binning *out,
+                      gs_stream stream);
+
+/* Forward blend (Eq. 4-7, 10).  One thread per pixel walks its tile's
+ * instances front to back: alpha = min(alpha_max, o exp(-1/2 s^T Sigma2D^-1 s))
+ * (Eq. 5), skip below alpha_min, stop before T drops below T_min, accumulate
+ * w = alpha T times colour, depth, feature and 1.  rgb gets + T_final * bg. */
+gs_status gs_render_fwd(const gs_gaussians *g, const gs_projected *proj, const gs_binning *bins,
+                        const gs_camera *cams, int n_views, const gs_raster_params *p,
+                        gs_images *out, gs_stream stream);
+
+/* Per-splat gradients of the blend, written by gs_render_bwd and consumed by
+ * gs_project_bwd (device f32, 16-byte aligned):
+ *   uvod[4*item]  = dL/du, dL/dv, dL/do (activated opacity), dL/ddepth;
+ *   conic[4*item] = dL/dA, dL/dB, dL/dC, 0;
+ *   rgb[4*g]      = dL/dc of Gaussian g summed over views, 0 (GS_GRAD_MAP only). */
+typedef struct {
+    float *uvod;
+    float *conic;
+    float *rgb;
+} gs_splat_grads;
+
+/* Backward of the blend (Eq. 4-7, 10).  Per pixel the blend is walked back to
+ * front from n_contrib, recomputing each alpha exactly as the forward did and
+ * the transmittance in front of it as T / (1 - alpha) from T_final; with S the
+ * blended value behind a splat, d out / d alpha = T (x - S).  Per-splat
+ * gradients are reduced across the warp and the CTA before one atomic add per
+ * (tile, splat).  Overwrites sg (rgb only with GS_GRAD_MAP) and, with
+ * GS_GRAD_MAP, d_feat (f32 [n, feat_dim], summed over views).  fwd must be the
+ * gs_render_fwd output of the same inputs (T_final, n_contrib are read). */
+gs_status gs_render_bwd(const gs_gaussians *g, const gs_projected *proj, const gs_binning *bins,
+                        const gs_camera *cams, int n_views, const gs_raster_params *p, int grad_mode,
+                        const gs_images *fwd, const gs_image_grads *dL, gs_splat_grads *sg, float *d_feat,
+                        gs_stream stream);
+
+/* Backward of the projection (chain rule of supp. B.1, per factor): from the
+ * per-splat gradients to the 3D parameters, summed over views.  GS_GRAD_MAP
+ * writes out->means, quats, log_scales, opacity_logits and rgb (out->feat is
+ * not touched: gs_render_bwd wrote it).  GS_GRAD_POSE writes pose_part, a
+ * device f32 [n_views, 6, n] array of per-Gaussian contributions to the
+ * gradient of the left twist (rho, phi): rho gets g_p, phi gets
+ * p x g_p + 2 (A12, A20, A01) with A = Sc Gc - Gc Sc, g_p and Gc being the
+ * gradients w.r.t. the camera-frame centre and covariance Sc.  pose_dev as for
+ * gs_project. */
+gs_status gs_project_bwd(const gs_gaussians *g, const gs_camera *cams, int n_views, const float *pose_dev,
+                         const gs_raster_params *p, int grad_mode, const gs_splat_grads *sg,
+                         gs_gaussian_grads *out, float *pose_part, gs_stream stream);
+
+/* Pose twist gradient (supp. B.1), reduced in double precision:
+ * d_twist[6 v + k] = sum over Gaussians of pose_part[v, k, :], k = rho_x,
+ * rho_y, rho_z, phi_x, phi_y, phi_z, for the left perturbation
+ * T(xi) = Exp(xi) T_cw at xi = 0.  d_twist: device f64 [6 n_views]. */
+gs_status gs_pose_grad(int64_t n, int n_views, const float *pose_part, double *d_twist,
+                       gs_stream stream);
+
+/* Decoder and losses (Eq. 8, 15-17, 21) with their gradients.  Per view v
+ * with P_v pixels: logits z = W f + b (W: dec_W [K,D] f32, b: dec_b [K]);
+ * L_v = (color sum |c - c_gt|_1 + depth sum_{d_gt>0} |d - d_gt| +
+ * sem sum_{label != 255} (logsumexp z - z_label)) / P_v, times M_obs in
+ * tracking mode (sil > tau_obs, d_gt > 0, |d - d_gt| < 10 x the lower median
+ * of |d - d_gt| over the view's pixels with d_gt > 0).  Writes grad (all four
+ * images; sil gradient is zero), d_dec_W, d_dec_b (overwritten), loss_out
+ * (device f64 [4]: total, colour, depth, semantic summed over views),
+ * mask_out (optional device f32 [P]) and median_out (optional device f32
+ * [n_views]). */
+gs_status gs_loss_fwd_bwd(const gs_camera *cams, int n_views, int feat_dim, const gs_images *img,
+                          const gs_targets *tgt, const float *dec_W, const float *dec_b,
+                          const gs_loss_params *lp, void *ws, size_t ws_bytes,
+                          gs_image_grads_out *grad, float *d_dec_W, float *d_dec_b,
+                          double *loss_out, float *mask_out, float *median_out, gs_stream stream);
+
+/* Depth-adaptive scale regularisation (Eq. 12) over the 3n axis scales
+ * s = exp(log_scales): mu, sigma = population mean and deviation (constants
+ * for differentiation), L_big = mean of s > mu + 2 sigma, L_small = mean of
+ * -log s < mu - 2 sigma.  Adds lam_big * dL_big + lam_small * dL_small to
+ * d_log_scales (+=).  out: device f64 [8] = (lam_big L_big + lam_small
+ * L_small, mu, sigma, n_big, n_small, L_big, L_small, 0). */
+gs_status gs_dsr(int64_t n, const float *log_scales, float lam_big, float lam_small, void *ws,
+                 size_t ws_bytes, float *d_log_scales, double *out, gs_stream stream);
+
+/* Pose step for tracking (Sec. 3.4; learning rates of supp. C.1): Adam on
+ * the left twist of each view, then T <- Exp(delta) T.  T_state: device f64
+ * [n_views,16] (updated); adam: device f64 [n_views,12] (m, v; zero before
+ * step 1); lr: host [6] (rho, phi); step: 1-based.  If pose_f32 is not NULL
+ * it receives the f32 copy of the new poses (for gs_project's pose_dev). */
+gs_status gs_pose_step(int n_views, const double *d_twist, double *T_state, double *adam,
+                       int step, const double *lr, double beta1, double beta2, double eps,
+                       float *pose_f32, gs_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GS_H */

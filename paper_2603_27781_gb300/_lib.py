@@ -1,0 +1,154 @@
+"""ctypes binding of libgs (include/gs.h): the same names, argument marshalling only.
+
+Every computation happens in the CUDA library.  If the library has not been
+built this module raises on first use; there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, Structure, c_char_p, c_double, c_float, c_int, c_int32, c_int64, c_size_t, c_void_p
+
+from . import build as _build
+
+LIB_PATH = _build.LIB_PATH
+
+GS_OK, GS_ERR_ARG, GS_ERR_CAPACITY, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
+GS_F32, GS_BF16, GS_F16 = 0, 1, 2
+GS_GRAD_MAP, GS_GRAD_POSE = 1, 2
+
+
+class gs_camera(Structure):
+    _fields_ = [("width", c_int32), ("height", c_int32), ("fx", c_float), ("fy", c_float), ("cx", c_float),
+                ("cy", c_float), ("T_cw", c_float * 16)]
+
+
+class gs_raster_params(Structure):
+    _fields_ = [("tile", c_int32), ("alpha_min", c_float), ("alpha_max", c_float), ("T_min", c_float),
+                ("z_near", c_float), ("lowpass", c_float), ("radius_sigma", c_float), ("bg_rgb", c_float * 3)]
+
+
+class gs_gaussians(Structure):
+    _fields_ = [("n", c_int64), ("feat_dim", c_int32), ("means", c_void_p), ("quats", c_void_p),
+                ("log_scales", c_void_p), ("opacity_logits", c_void_p), ("rgb", c_void_p), ("rgb_dtype", c_int32),
+                ("feat", c_void_p), ("feat_dtype", c_int32)]
+
+
+class gs_projected(Structure):
+    _fields_ = [("uvdo", c_void_p), ("conic", c_void_p), ("tiles_touched", c_void_p)]
+
+
+class gs_binning(Structure):
+    _fields_ = [("capacity", c_int64), ("keys", c_void_p), ("vals", c_void_p), ("ranges", c_void_p),
+                ("n_inst", c_void_p), ("status", c_void_p)]
+
+
+class gs_images(Structure):
+    _fields_ = [("rgb", c_void_p), ("depth", c_void_p), ("sil", c_void_p), ("feat", c_void_p),
+                ("T_final", c_void_p), ("n_contrib", c_void_p), ("n_blended", c_void_p)]
+
+
+class gs_splat_grads(Structure):
+    _fields_ = [("uvod", c_void_p), ("conic", c_void_p), ("rgb", c_void_p)]
+
+
+class gs_image_grads(Structure):
+    _fields_ = [("rgb", c_void_p), ("depth", c_void_p), ("sil", c_void_p), ("feat", c_void_p)]
+
+
+gs_image_grads_out = gs_image_grads
+
+
+class gs_gaussian_grads(Structure):
+    _fields_ = [("means", c_void_p), ("quats", c_void_p), ("log_scales", c_void_p), ("opacity_logits", c_void_p),
+                ("rgb", c_void_p), ("feat", c_void_p)]
+
+
+class gs_targets(Structure):
+    _fields_ = [("rgb", c_void_p), ("depth", c_void_p), ("label", c_void_p)]
+
+
+class gs_loss_params(Structure):
+    _fields_ = [("color", c_float), ("depth", c_float), ("sem", c_float), ("mask_mode", c_int32),
+                ("tau_obs", c_float), ("n_classes", c_int32)]
+
+
+_P = POINTER
+_SIGNATURES = {
+    "gs_version": (c_int, []),
+    "gs_strerror": (c_char_p, [c_int]),
+    "gs_workspace_size": (c_size_t, [c_int64, c_int, _P(gs_camera), c_int64, c_int]),
+    "gs_project": (c_int, [_P(gs_gaussians), _P(gs_camera), c_int, c_void_p, _P(gs_raster_params),
+                           _P(gs_projected), c_void_p]),
+    "gs_bin_sort": (c_int, [c_int64, _P(gs_projected), _P(gs_camera), c_int, _P(gs_raster_params), c_void_p,
+                            c_size_t, _P(gs_binning), c_void_p]),
+    "gs_render_fwd": (c_int, [_P(gs_gaussians), _P(gs_projected), _P(gs_binning), _P(gs_camera), c_int,
+                              _P(gs_raster_params), _P(gs_images), c_void_p]),
+    "gs_render_bwd": (c_int, [_P(gs_gaussians), _P(gs_projected), _P(gs_binning), _P(gs_camera), c_int,
+                              _P(gs_raster_params), c_int, _P(gs_images), _P(gs_image_grads), _P(gs_splat_grads),
+                              c_void_p, c_void_p]),
+    "gs_project_bwd": (c_int, [_P(gs_gaussians), _P(gs_camera), c_int, c_void_p, _P(gs_raster_params), c_int,
+                               _P(gs_splat_grads), _P(gs_gaussian_grads), c_void_p, c_void_p]),
+    "gs_pose_grad": (c_int, [c_int64, c_int, c_void_p, c_void_p, c_void_p]),
+    "gs_loss_fwd_bwd": (c_int, [_P(gs_camera), c_int, c_int, _P(gs_images), _P(gs_targets), c_void_p, c_void_p,
+                                _P(gs_loss_params), c_void_p, c_size_t, _P(gs_image_grads_out), c_void_p, c_void_p,
+                                c_void_p, c_void_p, c_void_p, c_void_p]),
+    "gs_dsr": (c_int, [c_int64, c_void_p, c_float, c_float, c_void_p, c_size_t, c_void_p, c_void_p, c_void_p]),
+    "gs_pose_step": (c_int, [c_int, c_void_p, c_void_p, c_void_p, c_int, _P(c_double), c_double, c_double,
+                             c_double, c_void_p, c_void_p]),
+}
+
+_lib = None
+
+
+def library():
+    """Loads libgs.so (raising if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libgs is not built ({LIB_PATH} missing): call paper_2603_27781_gb300.build.build()")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGNATURES)
+
+
+class GsError(RuntimeError):
+    def __init__(self, name, status):
+        msg = library().gs_strerror(status).decode()
+        super().__init__(f"{name} failed: {msg} ({status})")
+        self.status = status
+
+
+def check(name, status):
+    if status != GS_OK:
+        raise GsError(name, status)
+    return status
+
+
+def _wrap(name):
+    def call(*args):
+        return getattr(library(), name)(*args)
+    call.__name__ = name
+    return call
+
+
+gs_version = _wrap("gs_version")
+gs_strerror = _wrap("gs_strerror")
+gs_workspace_size = _wrap("gs_workspace_size")
+gs_project = _wrap("gs_project")
+gs_bin_sort = _wrap("gs_bin_sort")
+gs_render_fwd = _wrap("gs_render_fwd")
+gs_render_bwd = _wrap("gs_render_bwd")
+gs_project_bwd = _wrap("gs_project_bwd")
+gs_pose_grad = _wrap("gs_pose_grad")
+gs_loss_fwd_bwd = _wrap("gs_loss_fwd_bwd")
+gs_dsr = _wrap("gs_dsr")
+gs_pose_step = _wrap("gs_pose_step")

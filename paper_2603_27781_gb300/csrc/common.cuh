@@ -1,0 +1,186 @@
+// Shared device/host helpers of libgs (sm_103a).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gs.h"
+
+namespace gs {
+
+constexpr int kMaxViews = 64;
+constexpr int kTile = 16;
+constexpr int kTilePix = kTile * kTile;  // one thread per pixel, 8 warps per tile
+constexpr float kLog2e = 1.4426950408889634f;
+
+// Per-call camera table, passed by value as a kernel argument.
+struct ViewTable {
+    int n_views;
+    int64_t n;                       // Gaussians per view
+    int tile_off[kMaxViews + 1];     // first global tile of each view
+    int64_t pix_off[kMaxViews + 1];  // first pixel of each view
+    int W[kMaxViews], H[kMaxViews], TX[kMaxViews], TY[kMaxViews];
+    float fx[kMaxViews], fy[kMaxViews], cx[kMaxViews], cy[kMaxViews];
+    float T[kMaxViews][12];          // rows 0..2 of world->camera
+};
+
+struct Params {
+    float alpha_min, alpha_max, T_min, z_near, lowpass, radius_sigma;
+    float bg[3];
+};
+
+// Builds the table from host cameras; returns false on invalid input.
+bool make_view_table(const gs_camera *cams, int n_views, int64_t n, ViewTable *vt);
+bool make_params(const gs_raster_params *p, Params *out);
+
+__device__ __forceinline__ int view_of_tile(const ViewTable &vt, int gt) {
+    int v = 0;
+    while (v + 1 < vt.n_views && gt >= vt.tile_off[v + 1]) ++v;
+    return v;
+}
+
+__device__ __forceinline__ int view_of_pixel(const ViewTable &vt, int64_t pix) {
+    int v = 0;
+    while (v + 1 < vt.n_views && pix >= vt.pix_off[v + 1]) ++v;
+    return v;
+}
+
+// Loads row-major world->camera rows 0..2, from device poses when given.
+__device__ __forceinline__ void load_pose(const ViewTable &vt, const float *pose_dev, int v,
+                                          float R[9], float t[3]) {
+    if (pose_dev) {
+        const float *P = pose_dev + 16 * v;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            R[3 * r] = P[4 * r]; R[3 * r + 1] = P[4 * r + 1]; R[3 * r + 2] = P[4 * r + 2];
+            t[r] = P[4 * r + 3];
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            R[3 * r] = vt.T[v][4 * r]; R[3 * r + 1] = vt.T[v][4 * r + 1];
+            R[3 * r + 2] = vt.T[v][4 * r + 2]; t[r] = vt.T[v][4 * r + 3];
+        }
+    }
+}
+
+// 2^x on the special-function unit (PTX ex2.approx.ftz.f32; relative error
+// about 2^-22).  e^p is evaluated as 2^(p log2 e) with the log2 e factor
+// folded into the stored conic.
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Splat record staged in shared memory for the blend loops.  The conic is kept
+// pre-scaled: (qa, qb, qc) = (-A/2, -B, -C/2) * log2 e, so that
+// power2 = qa dx^2 + qb dx dy + qc dy^2 = power * log2 e and G = 2^power2.
+struct SplatGeo {
+    float u, v, o, depth;
+    float qa, qb, qc, pad;
+};
+
+// Evaluates one (pixel, splat) pair.  Both blend kernels call this one
+// function, written with explicitly rounded operations so that forward and
+// backward take bit-identical skip / clamp decisions.
+struct PairEval {
+    float dx, dy, G, oG, alpha;
+    bool skip;
+};
+
+__device__ __forceinline__ PairEval eval_pair(const SplatGeo &s, float pxc, float pyc,
+                                              float alpha_min, float alpha_max) {
+    PairEval e;
+    e.dx = __fsub_rn(pxc, s.u);
+    e.dy = __fsub_rn(pyc, s.v);
+    float t = __fmaf_rn(s.qa, e.dx, __fmul_rn(s.qb, e.dy));
+    float p2 = __fmaf_rn(t, e.dx, __fmul_rn(__fmul_rn(s.qc, e.dy), e.dy));
+    e.G = ex2_approx(p2);
+    e.oG = __fmul_rn(s.o, e.G);
+    e.alpha = fminf(alpha_max, e.oG);
+    e.skip = (p2 > 0.f) || (e.alpha < alpha_min);
+    return e;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Relaxed device-scope load / store (flags of the chained scans).
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void set_status(int32_t *status, int32_t code) {
+    if (status) atomicCAS(status, 0, code);
+}
+
+template <typename T> __device__ __forceinline__ float to_f32(T x);
+template <> __device__ __forceinline__ float to_f32<float>(float x) { return x; }
+template <> __device__ __forceinline__ float to_f32<__half>(__half x) { return __half2float(x); }
+template <> __device__ __forceinline__ float to_f32<__nv_bfloat16>(__nv_bfloat16 x) {
+    return __bfloat162float(x);
+}
+
+// Exact tile rectangle of a splat (half-open, in tiles): floor((u - r)/16) is
+// floordiv(floor(u) - r, 16) because r is an integer.
+__device__ __forceinline__ void tile_rect(float u, float v, int r, int TX, int TY, int &x0, int &y0,
+                                          int &x1, int &y1) {
+    const float lim = 1099511627776.0f;  // 2^40
+    float fu = fminf(fmaxf(floorf(u), -lim), lim), fv = fminf(fmaxf(floorf(v), -lim), lim);
+    long long iu = (long long)fu, iv = (long long)fv;
+    auto fdiv = [](long long a) -> long long { return a >= 0 ? a / kTile : -((-a + kTile - 1) / kTile); };
+    auto cl = [](long long a, long long hi) -> int { return (int)(a < 0 ? 0 : (a > hi ? hi : a)); };
+    x0 = cl(fdiv(iu - r), TX);
+    y0 = cl(fdiv(iv - r), TY);
+    x1 = cl(fdiv(iu + r) + 1, TX);
+    y1 = cl(fdiv(iv + r) + 1, TY);
+}
+
+// Host helpers.
+inline gs_status cuda_status(cudaError_t e) { return e == cudaSuccess ? GS_OK : GS_ERR_CUDA; }
+inline gs_status last_launch() {
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+inline bool feat_dim_ok(int d) { return d == 0 || d == 4 || d == 8 || d == 16 || d == 32; }
+
+// Workspace layout shared by the entry points (offsets in bytes, 256-aligned).
+struct WsLayout {
+    // bin_sort
+    size_t scan_blocks;   // u32 [scan block sums], two levels
+    size_t counters;      // u32 [16]: n_vis, M (clamped), tile counters ...
+    size_t dkeys_a, dvals_a, dkeys_b, dvals_b;  // u32 [VN]
+    size_t tkeys_a, tkeys_b, tvals_b;           // u32 [capacity]
+    size_t hist;          // u32 [8 passes][256]
+    size_t lookback;      // u32 [8 passes][max tiles][256]
+    size_t bin_end;
+    // loss / dsr
+    size_t med_hist;      // u32 [4][V][256]
+    size_t dsr_acc;       // f64 [8]
+    size_t misc_end;
+    size_t total;
+    int64_t vn, capacity;
+    int lb_tiles_depth, lb_tiles_inst;
+};
+
+constexpr int kSortThreads = 256;
+constexpr int kSortIPT = 8;
+constexpr int kSortTile = kSortThreads * kSortIPT;
+constexpr int kScanIPT = 8;
+constexpr int kScanBlock = 256 * kScanIPT;
+
+WsLayout ws_layout(int64_t n, int n_views, int64_t capacity);
+
+}  // namespace gs

@@ -1,0 +1,451 @@
+// Tile binning and depth sort (GS3LAM Sec. 3.2.1: Gaussians are blended in
+// depth order; rasterisation is tile based).
+//
+// The result is the order of the 64-bit keys (tile << 32 | depth bits) with
+// ties broken by item index.  Instead of radix-sorting 64-bit keys over all
+// M instances (six 8-bit passes over M), the sort runs in two stages:
+//   1. the visible items (tiles_touched > 0) are compacted in index order and
+//      sorted by their 32-bit depth bits (four passes over the visible items);
+//   2. instances are emitted in that depth order and stably sorted by their
+//      tile id (one pass per 8 bits of tile id, two for up to 65536 tiles).
+// A stable sort by tile of a depth-ordered, index-tie-broken stream is exactly
+// the (tile, depth, index) order.
+//
+// Each radix pass is one kernel: a block ranks its 2048 keys stably within the
+// block (warp match + per-warp digit counters), publishes its per-digit
+// counts, finds its global offsets by a chained look-back over earlier blocks,
+// and scatters through shared memory.  Blocks take tile numbers from an atomic
+// counter so a block only waits on blocks that are already running; every wait
+// is bounded and reports GS_ERR_TIMEOUT in the status word if it gives up.
+#include "common.cuh"
+
+namespace gs {
+
+// Counter slots in the workspace.
+enum { CTR_NVIS = 0, CTR_M = 1, CTR_MRAW = 2, CTR_TILE = 8 };
+
+namespace {
+
+constexpr uint32_t kFlagAgg = 1u << 30;
+constexpr uint32_t kFlagPre = 2u << 30;
+constexpr uint32_t kValMask = (1u << 30) - 1;
+constexpr int kSpinLimit = 1 << 22;
+
+// ----------------------------------------------------------- block scan helper
+// Exclusive scan of one value per thread over a 256-thread block; returns the
+// prefix and writes the block total to *total.
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t *total, uint32_t *s_warp) {
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_warp[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t t = lane < 8 ? s_warp[lane] : 0, ti = t;
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, ti, o);
+            if (lane >= o) ti += y;
+        }
+        if (lane < 8) s_warp[lane] = ti - t;
+        if (lane == 7) s_warp[8] = ti;
+    }
+    __syncthreads();
+    uint32_t r = s_warp[w] + inc - x;
+    *total = s_warp[8];
+    __syncthreads();
+    return r;
+}
+
+// ------------------------------------------------ compaction of visible items
+__global__ void __launch_bounds__(256) vis_reduce_kernel(const int32_t *touched, int64_t count, uint32_t *block_sums) {
+    __shared__ uint32_t s_warp[9];
+    int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanIPT;
+    uint32_t c = 0;
+#pragma unroll
+    for (int k = 0; k < kScanIPT; ++k) c += (base + k < count && touched[base + k] > 0) ? 1u : 0u;
+    uint32_t tot;
+    block_exclusive_scan(c, &tot, s_warp);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+}
+
+// Single-block exclusive scan of nb block sums; total -> counters[slot].
+// If cap_slot >= 0 the total is also clamped to capacity into counters[cap_slot],
+// the raw count goes to *n_inst and overflow sets the status word.
+__global__ void __launch_bounds__(1024) blocksum_scan_kernel(uint32_t *block_sums, const uint32_t *nb_from,
+                                                             int64_t nb_fixed, int items_per_block,
+                                                             uint32_t *counters, int slot, int cap_slot,
+                                                             int64_t capacity, int64_t *n_inst, int32_t *status) {
+    __shared__ uint32_t s_part[1024];
+    int64_t nb = nb_from ? ((int64_t)*nb_from + items_per_block - 1) / items_per_block : nb_fixed;
+    int64_t per = (nb + 1023) / 1024;
+    int64_t b0 = (int64_t)threadIdx.x * per;
+    uint32_t s = 0;
+    for (int64_t i = b0; i < b0 + per && i < nb; ++i) s += block_sums[i];
+    s_part[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        uint32_t y = threadIdx.x >= o ? s_part[threadIdx.x - o] : 0;
+        __syncthreads();
+        s_part[threadIdx.x] += y;
+        __syncthreads();
+    }
+    uint32_t run = s_part[threadIdx.x] - s;
+    for (int64_t i = b0; i < b0 + per && i < nb; ++i) {
+        uint32_t x = block_sums[i];
+        block_sums[i] = run;
+        run += x;
+    }
+    if (threadIdx.x == 1023) {
+        uint32_t total = s_part[1023];
+        counters[slot] = total;
+        if (cap_slot >= 0) {
+            counters[cap_slot] = (int64_t)total > capacity ? (uint32_t)capacity : total;
+            if (n_inst) *n_inst = total;
+            if ((int64_t)total > capacity) set_status(status, GS_ERR_CAPACITY);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) vis_compact_kernel(const int32_t *touched, const float4 *uvdo, int64_t count,
+                                                          const uint32_t *block_sums, uint32_t *keys, uint32_t *vals) {
+    __shared__ uint32_t s_warp[9];
+    int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanIPT;
+    bool f[kScanIPT];
+    uint32_t c = 0;
+#pragma unroll
+    for (int k = 0; k < kScanIPT; ++k) {
+        f[k] = base + k < count && touched[base + k] > 0;
+        c += f[k];
+    }
+    uint32_t tot;
+    uint32_t off = block_sums[blockIdx.x] + block_exclusive_scan(c, &tot, s_warp);
+#pragma unroll
+    for (int k = 0; k < kScanIPT; ++k)
+        if (f[k]) {
+            keys[off] = __float_as_uint(uvdo[base + k].z);
+            vals[off] = (uint32_t)(base + k);
+            ++off;
+        }
+}
+
+// ------------------------------------------------------------ instance emission
+__global__ void __launch_bounds__(256) emit_reduce_kernel(const uint32_t *sorted_items, const int32_t *touched,
+                                                          const uint32_t *counters, uint32_t *block_sums) {
+    __shared__ uint32_t s_warp[9];
+    int64_t count = counters[CTR_NVIS];
+    int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanIPT;
+    if ((int64_t)blockIdx.x * kScanBlock >= count) return;
+    uint32_t c = 0;
+#pragma unroll
+    for (int k = 0; k < kScanIPT; ++k)
+        if (base + k < count) c += (uint32_t)touched[sorted_items[base + k]];
+    uint32_t tot;
+    block_exclusive_scan(c, &tot, s_warp);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(256) emit_kernel(ViewTable vt, const uint32_t *sorted_items, const int32_t *touched,
+                                                   const float4 *uvdo, const float4 *conic, const uint32_t *counters,
+                                                   const uint32_t *block_sums, int64_t capacity, uint32_t *tile_keys,
+                                                   uint32_t *inst_vals) {
+    __shared__ uint32_t s_warp[9];
+    int64_t count = counters[CTR_NVIS];
+    if ((int64_t)blockIdx.x * kScanBlock >= count) return;
+    int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanIPT;
+    uint32_t item[kScanIPT];
+    uint32_t c = 0;
+#pragma unroll
+    for (int k = 0; k < kScanIPT; ++k) {
+        item[k] = base + k < count ? sorted_items[base + k] : 0xffffffffu;
+        c += item[k] != 0xffffffffu ? (uint32_t)touched[item[k]] : 0u;
+    }
+    uint32_t tot;
+    int64_t off = (int64_t)block_sums[blockIdx.x] + block_exclusive_scan(c, &tot, s_warp);
+#pragma unroll 1
+    for (int k = 0; k < kScanIPT; ++k) {
+        if (item[k] == 0xffffffffu) continue;
+        int v = (int)(item[k] / (uint32_t)vt.n);
+        float4 rec = uvdo[item[k]];
+        int r = (int)conic[item[k]].w;
+        int x0, y0, x1, y1;
+        tile_rect(rec.x, rec.y, r, vt.TX[v], vt.TY[v], x0, y0, x1, y1);
+        uint32_t tb = (uint32_t)vt.tile_off[v];
+        for (int y = y0; y < y1; ++y)
+            for (int x = x0; x < x1; ++x) {
+                if (off < capacity) {
+                    tile_keys[off] = tb + (uint32_t)(y * vt.TX[v] + x);
+                    inst_vals[off] = item[k];
+                }
+                ++off;
+            }
+    }
+}
+
+// ------------------------------------------------------------------ radix sort
+// Digit histograms of every pass in one read of the keys.
+__global__ void __launch_bounds__(256) radix_hist_kernel(const uint32_t *keys, const uint32_t *count_ptr,
+                                                         int n_passes, uint32_t *hist) {
+    __shared__ uint32_t sh[4][256];
+    for (int i = threadIdx.x; i < 4 * 256; i += 256) (&sh[0][0])[i] = 0;
+    __syncthreads();
+    int64_t n = *count_ptr;
+    int lane = threadIdx.x & 31;
+    int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t wb = warp * 32; wb < n; wb += nwarps * 32) {
+        int64_t i = wb + lane;
+        bool valid = i < n;
+        uint32_t mask = __ballot_sync(0xffffffffu, valid);
+        if (valid) {
+            uint32_t k = keys[i];
+            for (int p = 0; p < n_passes; ++p) {
+                uint32_t d = (k >> (8 * p)) & 255u;
+                uint32_t peers = __match_any_sync(mask, d);
+                if (lane == __ffs(peers) - 1) atomicAdd(&sh[p][d], __popc(peers));
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n_passes * 256; i += 256) {
+        uint32_t c = (&sh[0][0])[i];
+        if (c) atomicAdd(&hist[i], c);
+    }
+}
+
+__global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint32_t *keys_in, const uint32_t *vals_in,
+                                                                uint32_t *keys_out, uint32_t *vals_out,
+                                                                const uint32_t *count_ptr, int shift,
+                                                                const uint32_t *pass_hist, uint32_t *tile_ctr,
+                                                                uint32_t *lookback, int32_t *status) {
+    constexpr int W = kSortThreads / 32;
+    __shared__ uint32_t s_keys[kSortTile];
+    __shared__ uint32_t s_vals[kSortTile];
+    __shared__ uint32_t s_whist[W][256];
+    __shared__ uint32_t s_excl[256];   // block-local exclusive digit offsets
+    __shared__ uint32_t s_glob[256];   // global destination of the digit's first key in this block
+    __shared__ uint32_t s_dbase[256];  // global exclusive digit base of the pass
+    __shared__ uint32_t s_warp[9];
+    __shared__ uint32_t s_tile;
+
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
+    for (int i = tid; i < W * 256; i += kSortThreads) (&s_whist[0][0])[i] = 0;
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const int64_t n = *count_ptr;
+    const int64_t base = (int64_t)tile * kSortTile;
+    if (base >= n) return;
+
+    uint32_t key[kSortIPT], val[kSortIPT], rank[kSortIPT];
+#pragma unroll
+    for (int r = 0; r < kSortIPT; ++r) {
+        int64_t i = base + (int64_t)w * (kSortIPT * 32) + r * 32 + lane;
+        bool valid = i < n;
+        key[r] = valid ? keys_in[i] : 0u;
+        val[r] = valid ? vals_in[i] : 0u;
+        uint32_t d = valid ? (key[r] >> shift) & 255u : 256u + lane;  // invalid lanes never match
+        uint32_t peers = __match_any_sync(0xffffffffu, d);
+        int leader = __ffs(peers) - 1;
+        uint32_t b = 0;
+        if (valid && lane == leader) {
+            b = s_whist[w][d];
+            s_whist[w][d] = b + __popc(peers);
+        }
+        b = __shfl_sync(0xffffffffu, b, leader);
+        rank[r] = b + __popc(peers & lanemask_lt());
+        __syncwarp();
+    }
+    __syncthreads();
+
+    // per-digit: warp-exclusive offsets, block count, block-exclusive offsets
+    const int d = tid;  // kSortThreads == 256 == radix
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int ww = 0; ww < W; ++ww) {
+        uint32_t c = s_whist[ww][d];
+        s_whist[ww][d] = cnt;
+        cnt += c;
+    }
+    uint32_t lb_tot;
+    uint32_t hist_d = pass_hist[d];
+    uint32_t excl_local = block_exclusive_scan(cnt, &lb_tot, s_warp);
+    s_excl[d] = excl_local;
+    uint32_t hist_tot;
+    s_dbase[d] = block_exclusive_scan(hist_d, &hist_tot, s_warp);
+
+    // chained look-back over earlier tiles for digit d
+    uint32_t *my = lookback + (size_t)tile * 256 + d;
+    uint32_t prefix = 0;
+    if (tile == 0) {
+        st_relaxed(my, kFlagPre | cnt);
+    } else {
+        st_relaxed(my, kFlagAgg | cnt);
+        int64_t t = (int64_t)tile - 1;
+        while (t >= 0) {
+            const uint32_t *p = lookback + (size_t)t * 256 + d;
+            uint32_t vv = ld_relaxed(p);
+            int spin = 0;
+            while ((vv & ~kValMask) == 0u) {
+                if (++spin > kSpinLimit) break;
+                if (spin > 64) __nanosleep(64);
+                vv = ld_relaxed(p);
+            }
+            if ((vv & ~kValMask) == 0u) {
+                set_status(status, GS_ERR_TIMEOUT);
+                break;
+            }
+            prefix += vv & kValMask;
+            if ((vv & ~kValMask) == kFlagPre) break;
+            --t;
+        }
+        st_relaxed(my, kFlagPre | (prefix + cnt));
+    }
+    s_glob[d] = s_dbase[d] + prefix;
+    __syncthreads();
+
+    // local scatter by digit, then coalesced-by-run global writes
+#pragma unroll
+    for (int r = 0; r < kSortIPT; ++r) {
+        int64_t i = base + (int64_t)w * (kSortIPT * 32) + r * 32 + lane;
+        if (i < n) {
+            uint32_t dd = (key[r] >> shift) & 255u;
+            uint32_t pos = s_excl[dd] + s_whist[w][dd] + rank[r];
+            s_keys[pos] = key[r];
+            s_vals[pos] = val[r];
+        }
+    }
+    __syncthreads();
+    int tile_n = (int)min((int64_t)kSortTile, n - base);
+    for (int i = tid; i < tile_n; i += kSortThreads) {
+        uint32_t k = s_keys[i];
+        uint32_t dd = (k >> shift) & 255u;
+        uint32_t dst = s_glob[dd] + (uint32_t)i - s_excl[dd];
+        keys_out[dst] = k;
+        vals_out[dst] = s_vals[i];
+    }
+}
+
+__global__ void __launch_bounds__(256) ranges_kernel(const uint32_t *tile_keys, const uint32_t *vals,
+                                                     const uint32_t *counters, const float4 *uvdo, uint32_t *ranges,
+                                                     uint64_t *keys64) {
+    int64_t m = counters[CTR_M];
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    uint32_t t = tile_keys[j];
+    if (j == 0 || tile_keys[j - 1] != t) ranges[2 * (size_t)t] = (uint32_t)j;
+    if (j == m - 1 || tile_keys[j + 1] != t) ranges[2 * (size_t)t + 1] = (uint32_t)(j + 1);
+    if (keys64) keys64[j] = ((uint64_t)t << 32) | __float_as_uint(uvdo[vals[j]].z);
+}
+
+struct SortBufs {
+    uint32_t *k0, *v0, *k1, *v1;
+};
+
+// Stable LSD sort of (key, val) pairs by `n_passes` 8-bit digits from bit 0.
+// Input in (k0, v0); output lands in (k0, v0) if n_passes is even, else (k1, v1).
+gs_status radix_sort(SortBufs b, const uint32_t *count_ptr, int64_t max_count, int n_passes, uint32_t *hist,
+                     uint32_t *lookback, int lb_tiles, uint32_t *tile_ctrs, int32_t *status, cudaStream_t st) {
+    if (max_count <= 0 || n_passes <= 0) return GS_OK;
+    int grid_h = ceil_div(max_count, 256 * 8);
+    if (grid_h > 152 * 8) grid_h = 152 * 8;
+    radix_hist_kernel<<<grid_h, 256, 0, st>>>(b.k0, count_ptr, n_passes, hist);
+    int grid = ceil_div(max_count, kSortTile);
+    uint32_t *ki = b.k0, *vi = b.v0, *ko = b.k1, *vo = b.v1;
+    for (int p = 0; p < n_passes; ++p) {
+        onesweep_kernel<<<grid, kSortThreads, 0, st>>>(ki, vi, ko, vo, count_ptr, 8 * p, hist + 256 * p,
+                                                         tile_ctrs + p, lookback + (size_t)p * lb_tiles * 256,
+                                                         status);
+        uint32_t *tk = ki, *tv = vi;
+        ki = ko; vi = vo; ko = tk; vo = tv;
+    }
+    return last_launch();
+}
+
+}  // namespace
+}  // namespace gs
+
+extern "C" gs_status gs_bin_sort(int64_t n, const gs_projected *proj, const gs_camera *cams, int n_views,
+                                 const gs_raster_params *p, void *ws, size_t ws_bytes, gs_binning *out,
+                                 gs_stream stream) {
+    using namespace gs;
+    cudaStream_t st = (cudaStream_t)stream;
+    ViewTable vt;
+    Params prm;
+    if (!proj || !out || n < 0) return GS_ERR_ARG;
+    if (!make_view_table(cams, n_views, n, &vt) || !make_params(p, &prm)) return GS_ERR_ARG;
+    if (out->capacity < 0 || out->capacity >= ((int64_t)1 << 30) || n * n_views >= ((int64_t)1 << 30)) return GS_ERR_ARG;
+    if (!out->vals || !out->ranges || !out->n_inst || !out->status || !ws) return GS_ERR_ARG;
+    WsLayout L = ws_layout(n, n_views, out->capacity);
+    if (ws_bytes < L.bin_end || (reinterpret_cast<uintptr_t>(ws) & 255)) return GS_ERR_ARG;
+    char *w = static_cast<char *>(ws);
+    uint32_t *counters = reinterpret_cast<uint32_t *>(w + L.counters);
+    uint32_t *block_sums = reinterpret_cast<uint32_t *>(w + L.scan_blocks);
+    uint32_t *hist = reinterpret_cast<uint32_t *>(w + L.hist);
+    uint32_t *lookback = reinterpret_cast<uint32_t *>(w + L.lookback);
+    int64_t total_tiles = vt.tile_off[n_views];
+    int64_t vn = n * n_views;
+
+    gs_status s;
+    if ((s = cuda_status(cudaMemsetAsync(out->ranges, 0, sizeof(uint32_t) * 2 * total_tiles, st)))) return s;
+    if ((s = cuda_status(cudaMemsetAsync(counters, 0, sizeof(uint32_t) * 64, st)))) return s;
+    if ((s = cuda_status(cudaMemsetAsync(out->n_inst, 0, sizeof(int64_t), st)))) return s;
+    if ((s = cuda_status(cudaMemsetAsync(out->status, 0, sizeof(int32_t), st)))) return s;
+    if (vn == 0) return GS_OK;
+    if (!proj->uvdo || !proj->conic || !proj->tiles_touched) return GS_ERR_ARG;
+    if ((s = cuda_status(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * 8 * 256, st)))) return s;
+    size_t lb_bytes = sizeof(uint32_t) * 256 * ((size_t)4 * L.lb_tiles_depth + (size_t)3 * L.lb_tiles_inst);
+    if ((s = cuda_status(cudaMemsetAsync(lookback, 0, lb_bytes, st)))) return s;
+
+    const float4 *uvdo = reinterpret_cast<const float4 *>(proj->uvdo);
+    const float4 *conic = reinterpret_cast<const float4 *>(proj->conic);
+    uint32_t *dk_a = reinterpret_cast<uint32_t *>(w + L.dkeys_a), *dv_a = reinterpret_cast<uint32_t *>(w + L.dvals_a);
+    uint32_t *dk_b = reinterpret_cast<uint32_t *>(w + L.dkeys_b), *dv_b = reinterpret_cast<uint32_t *>(w + L.dvals_b);
+
+    // 1. compact visible items in index order, keyed by depth bits
+    int nb = ceil_div(vn, kScanBlock);
+    vis_reduce_kernel<<<nb, 256, 0, st>>>(proj->tiles_touched, vn, block_sums);
+    blocksum_scan_kernel<<<1, 1024, 0, st>>>(block_sums, nullptr, nb, kScanBlock, counters, CTR_NVIS, -1, 0, nullptr,
+                                             nullptr);
+    vis_compact_kernel<<<nb, 256, 0, st>>>(proj->tiles_touched, uvdo, vn, block_sums, dk_a, dv_a);
+    if ((s = last_launch())) return s;
+
+    // 2. stable sort of the visible items by depth (4 passes: result in dk_a/dv_a)
+    if ((s = radix_sort({dk_a, dv_a, dk_b, dv_b}, counters + CTR_NVIS, vn, 4, hist, lookback, L.lb_tiles_depth,
+                        counters + CTR_TILE, out->status, st)))
+        return s;
+    const uint32_t *sorted_items = dv_a;
+
+    // 3. emit instances in depth order; instance count -> n_inst (clamped copy for the sort)
+    int tile_bits = 1;
+    while (((int64_t)1 << tile_bits) < total_tiles) ++tile_bits;
+    int tile_passes = (tile_bits + 7) / 8;
+    uint32_t *tk_a = reinterpret_cast<uint32_t *>(w + L.tkeys_a), *tk_b = reinterpret_cast<uint32_t *>(w + L.tkeys_b);
+    uint32_t *tv_b = reinterpret_cast<uint32_t *>(w + L.tvals_b);
+    // the emitted values go where the final pass must not land: out->vals ends the sort
+    uint32_t *emit_vals = (tile_passes % 2 == 0) ? out->vals : tv_b;
+    uint32_t *other_vals = (tile_passes % 2 == 0) ? tv_b : out->vals;
+    emit_reduce_kernel<<<nb, 256, 0, st>>>(sorted_items, proj->tiles_touched, counters, block_sums);
+    blocksum_scan_kernel<<<1, 1024, 0, st>>>(block_sums, counters + CTR_NVIS, 0, kScanBlock, counters, CTR_MRAW, CTR_M,
+                                             out->capacity, out->n_inst, out->status);
+    emit_kernel<<<nb, 256, 0, st>>>(vt, sorted_items, proj->tiles_touched, uvdo, conic, counters, block_sums,
+                                    out->capacity, tk_a, emit_vals);
+    if ((s = last_launch())) return s;
+    if (out->capacity == 0) return GS_OK;
+
+    // 4. stable sort of the instances by tile id
+    if ((s = radix_sort({tk_a, emit_vals, tk_b, other_vals}, counters + CTR_M, out->capacity, tile_passes,
+                        hist + 4 * 256, lookback + (size_t)4 * L.lb_tiles_depth * 256, L.lb_tiles_inst,
+                        counters + CTR_TILE + 4, out->status, st)))
+        return s;
+    const uint32_t *sorted_tiles = (tile_passes % 2 == 0) ? tk_a : tk_b;
+
+    // 5. per-tile ranges (and the 64-bit keys if requested)
+    ranges_kernel<<<ceil_div(out->capacity, 256), 256, 0, st>>>(sorted_tiles, out->vals, counters, uvdo, out->ranges,
+                                                                out->keys);
+    return last_launch();
+}

@@ -1,0 +1,347 @@
+"""Torch-side driver of libgs: device buffers, one fwd+bwd iteration, autograd.
+
+PyTorch provides device memory and the stream; every step of the rasterizer
+runs in the CUDA library through the C ABI (`_lib`).  Nothing here computes
+any part of the method.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+from typing import Optional, Sequence
+
+import torch
+
+from . import _lib as L
+
+
+@dataclasses.dataclass
+class RasterParams:
+    """Raster parameters the paper leaves open (see include/gs.h)."""
+    tile: int = 16
+    alpha_min: float = 1.0 / 255.0
+    alpha_max: float = 0.99
+    T_min: float = 1e-4
+    z_near: float = 0.2
+    lowpass: float = 0.3
+    radius_sigma: float = 3.0
+    bg: tuple = (0.0, 0.0, 0.0)
+
+    def c(self) -> L.gs_raster_params:
+        return L.gs_raster_params(self.tile, self.alpha_min, self.alpha_max, self.T_min, self.z_near, self.lowpass,
+                                  self.radius_sigma, (ctypes.c_float * 3)(*self.bg))
+
+
+@dataclasses.dataclass
+class LossWeights:
+    """Loss weights of supplementary C.1 (mapping defaults) and the tracking mask switch."""
+    color: float = 0.5
+    depth: float = 1.0
+    sem: float = 0.01
+    big: float = 0.01
+    small: float = 0.001
+    mask_mode: int = 0
+    tau_obs: float = 0.99
+
+
+MAPPING = LossWeights()
+TRACKING = LossWeights(color=0.5, depth=1.0, sem=0.001, big=0.0, small=0.0, mask_mode=1)
+# supplementary C.1: pose learning rates, translation (rho) then rotation (phi)
+TRACKING_LR = (2e-3, 2e-3, 2e-3, 4e-4, 4e-4, 4e-4)
+
+
+def camera_c(cam) -> L.gs_camera:
+    T = [float(x) for x in torch.as_tensor(cam.T_cw, dtype=torch.float64).reshape(16).tolist()]
+    return L.gs_camera(int(cam.width), int(cam.height), float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy),
+                       (ctypes.c_float * 16)(*T))
+
+
+def cameras_c(cams) -> ctypes.Array:
+    arr = (L.gs_camera * len(cams))()
+    for i, c in enumerate(cams):
+        arr[i] = camera_c(c)
+    return arr
+
+
+def _p(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+_DTYPE = {torch.float32: L.GS_F32, torch.float16: L.GS_F16, torch.bfloat16: L.GS_BF16}
+
+
+@dataclasses.dataclass
+class Field:
+    """Semantic Gaussian field on the device (Eq. 1), structure of arrays."""
+    means: torch.Tensor
+    quats: torch.Tensor
+    log_scales: torch.Tensor
+    opacity_logits: torch.Tensor
+    rgb: torch.Tensor
+    feat: torch.Tensor
+
+    @property
+    def n(self) -> int:
+        return int(self.means.shape[0])
+
+    @property
+    def feat_dim(self) -> int:
+        return int(self.feat.shape[1])
+
+    @staticmethod
+    def from_numpy(gs, device="cuda", rgb_dtype=torch.float32, feat_dtype=torch.float32) -> "Field":
+        t = lambda a, dt=torch.float32: torch.as_tensor(a).to(device=device, dtype=dt).contiguous()
+        return Field(t(gs.means), t(gs.quats), t(gs.log_scales), t(gs.opacity_logits), t(gs.rgb, rgb_dtype),
+                     t(gs.feat, feat_dtype))
+
+    def c(self) -> L.gs_gaussians:
+        return L.gs_gaussians(self.n, self.feat_dim, _p(self.means), _p(self.quats), _p(self.log_scales),
+                              _p(self.opacity_logits), _p(self.rgb), _DTYPE[self.rgb.dtype],
+                              _p(self.feat) if self.feat_dim else None, _DTYPE[self.feat.dtype])
+
+
+class Renderer:
+    """Device buffers for rendering a field of n Gaussians into a fixed set of views.
+
+    One instance serves repeated iterations (and CUDA-graph capture): every
+    buffer is allocated here, once.  `capacity` bounds the (tile, splat)
+    instances; `status()` reports an overflow after the stream has run.
+    """
+
+    def __init__(self, n: int, cams: Sequence, feat_dim: int, capacity: int, device="cuda",
+                 params: RasterParams = RasterParams(), n_classes: int = 0):
+        self.n, self.feat_dim, self.capacity = int(n), int(feat_dim), int(capacity)
+        self.params = params
+        self.device = torch.device(device)
+        self.set_cameras(cams)
+        V, dev = self.n_views, self.device
+        f32, i32 = torch.float32, torch.int32
+        self.uvdo = torch.zeros(V * n, 4, dtype=f32, device=dev)
+        self.conic = torch.zeros(V * n, 4, dtype=f32, device=dev)
+        self.touched = torch.zeros(V * n, dtype=i32, device=dev)
+        self.keys = torch.zeros(max(capacity, 1), dtype=torch.int64, device=dev)
+        self.vals = torch.zeros(max(capacity, 1), dtype=i32, device=dev)
+        self.ranges = torch.zeros(2 * self.n_tiles, dtype=i32, device=dev)
+        self.n_inst = torch.zeros(1, dtype=torch.int64, device=dev)
+        self.status_word = torch.zeros(1, dtype=i32, device=dev)
+        ws_bytes = L.library().gs_workspace_size(n, V, self.cams_c, capacity, feat_dim)
+        if ws_bytes == 0:
+            raise ValueError("invalid renderer configuration (workspace size 0)")
+        self.ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+        P, D = self.P, feat_dim
+        self.img_rgb = torch.zeros(3, P, dtype=f32, device=dev)
+        self.img_depth = torch.zeros(P, dtype=f32, device=dev)
+        self.img_sil = torch.zeros(P, dtype=f32, device=dev)
+        self.img_feat = torch.zeros(max(D, 1), P, dtype=f32, device=dev)
+        self.img_T = torch.zeros(P, dtype=f32, device=dev)
+        self.img_nc = torch.zeros(P, dtype=i32, device=dev)
+        self.img_nb = torch.zeros(P, dtype=i32, device=dev)
+        self.count_blended = False
+        self.sg_uvod = torch.zeros(V * n, 4, dtype=f32, device=dev)
+        self.sg_conic = torch.zeros(V * n, 4, dtype=f32, device=dev)
+        self.sg_rgb = torch.zeros(n, 4, dtype=f32, device=dev)
+        self.g_rgb = torch.zeros(3, P, dtype=f32, device=dev)
+        self.g_depth = torch.zeros(P, dtype=f32, device=dev)
+        self.g_sil = torch.zeros(P, dtype=f32, device=dev)
+        self.g_feat = torch.zeros(max(D, 1), P, dtype=f32, device=dev)
+        self.d_means = torch.zeros(n, 3, dtype=f32, device=dev)
+        self.d_quats = torch.zeros(n, 4, dtype=f32, device=dev)
+        self.d_log_scales = torch.zeros(n, 3, dtype=f32, device=dev)
+        self.d_logits = torch.zeros(n, dtype=f32, device=dev)
+        self.d_rgb = torch.zeros(n, 3, dtype=f32, device=dev)
+        self.d_feat = torch.zeros(n, max(D, 1), dtype=f32, device=dev)
+        self.pose_part = torch.zeros(V, 6, n, dtype=f32, device=dev)
+        self.d_twist = torch.zeros(V, 6, dtype=torch.float64, device=dev)
+        self.loss_out = torch.zeros(4, dtype=torch.float64, device=dev)
+        self.dsr_out = torch.zeros(8, dtype=torch.float64, device=dev)
+        self.mask = torch.zeros(P, dtype=f32, device=dev)
+        self.median = torch.zeros(V, dtype=f32, device=dev)
+        K = max(int(n_classes), 1)
+        self.d_dec_W = torch.zeros(K, max(D, 1), dtype=f32, device=dev)
+        self.d_dec_b = torch.zeros(K, dtype=f32, device=dev)
+        self.prm_c = params.c()
+
+    # ------------------------------------------------------------ geometry
+    def set_cameras(self, cams):
+        self.cams = list(cams)
+        self.n_views = len(self.cams)
+        self.cams_c = cameras_c(self.cams)
+        self.sizes = [(int(c.height), int(c.width)) for c in self.cams]
+        self.P = sum(h * w for h, w in self.sizes)
+        self.pix_off = [0]
+        for h, w in self.sizes:
+            self.pix_off.append(self.pix_off[-1] + h * w)
+        t = 16
+        self.n_tiles = sum(((h + t - 1) // t) * ((w + t - 1) // t) for h, w in self.sizes)
+
+    # -------------------------------------------------------------- C ABI
+    def projected_c(self):
+        return L.gs_projected(_p(self.uvdo), _p(self.conic), _p(self.touched))
+
+    def binning_c(self, want_keys=False):
+        return L.gs_binning(self.capacity, _p(self.keys) if want_keys else None, _p(self.vals), _p(self.ranges),
+                            _p(self.n_inst), _p(self.status_word))
+
+    def images_c(self):
+        return L.gs_images(_p(self.img_rgb), _p(self.img_depth), _p(self.img_sil),
+                           _p(self.img_feat) if self.feat_dim else None, _p(self.img_T), _p(self.img_nc),
+                           _p(self.img_nb) if self.count_blended else None)
+
+    def splat_grads_c(self):
+        return L.gs_splat_grads(_p(self.sg_uvod), _p(self.sg_conic), _p(self.sg_rgb))
+
+    def image_grads_c(self):
+        return L.gs_image_grads(_p(self.g_rgb), _p(self.g_depth), _p(self.g_sil),
+                                _p(self.g_feat) if self.feat_dim else None)
+
+    def gaussian_grads_c(self):
+        return L.gs_gaussian_grads(_p(self.d_means), _p(self.d_quats), _p(self.d_log_scales), _p(self.d_logits),
+                                   _p(self.d_rgb), _p(self.d_feat) if self.feat_dim else None)
+
+    def project(self, field: Field, pose_dev: Optional[torch.Tensor] = None, stream=None):
+        pc = self.projected_c()
+        L.check("gs_project", L.gs_project(ctypes.byref(field.c()), self.cams_c, self.n_views, _p(pose_dev),
+                                           ctypes.byref(self.prm_c), ctypes.byref(pc), _stream(stream)))
+
+    def bin_sort(self, want_keys=False, stream=None):
+        pc, bc = self.projected_c(), self.binning_c(want_keys)
+        L.check("gs_bin_sort", L.gs_bin_sort(self.n, ctypes.byref(pc), self.cams_c, self.n_views,
+                                             ctypes.byref(self.prm_c), _p(self.ws), self.ws.numel(),
+                                             ctypes.byref(bc), _stream(stream)))
+
+    def render_fwd(self, field: Field, stream=None):
+        pc, bc, ic = self.projected_c(), self.binning_c(), self.images_c()
+        L.check("gs_render_fwd", L.gs_render_fwd(ctypes.byref(field.c()), ctypes.byref(pc), ctypes.byref(bc),
+                                                 self.cams_c, self.n_views, ctypes.byref(self.prm_c),
+                                                 ctypes.byref(ic), _stream(stream)))
+
+    def loss(self, targets, decoder_W: torch.Tensor, decoder_b: torch.Tensor, w: LossWeights, stream=None):
+        K = int(decoder_W.shape[0]) if decoder_W is not None else 0
+        lp = L.gs_loss_params(w.color, w.depth, w.sem, w.mask_mode, w.tau_obs, K)
+        tc = L.gs_targets(_p(targets["rgb"]), _p(targets["depth"]), _p(targets["label"]))
+        ic, gc = self.images_c(), self.image_grads_c()
+        L.check("gs_loss_fwd_bwd", L.gs_loss_fwd_bwd(self.cams_c, self.n_views, self.feat_dim, ctypes.byref(ic),
+                                                     ctypes.byref(tc), _p(decoder_W), _p(decoder_b),
+                                                     ctypes.byref(lp), _p(self.ws), self.ws.numel(),
+                                                     ctypes.byref(gc), _p(self.d_dec_W), _p(self.d_dec_b),
+                                                     _p(self.loss_out), _p(self.mask), _p(self.median),
+                                                     _stream(stream)))
+
+    def render_bwd(self, field: Field, grad_mode: int = L.GS_GRAD_MAP, stream=None):
+        pc, bc, ic, gc, sg = (self.projected_c(), self.binning_c(), self.images_c(), self.image_grads_c(),
+                              self.splat_grads_c())
+        L.check("gs_render_bwd", L.gs_render_bwd(ctypes.byref(field.c()), ctypes.byref(pc), ctypes.byref(bc),
+                                                 self.cams_c, self.n_views, ctypes.byref(self.prm_c), grad_mode,
+                                                 ctypes.byref(ic), ctypes.byref(gc), ctypes.byref(sg),
+                                                 _p(self.d_feat) if self.feat_dim else None, _stream(stream)))
+
+    def project_bwd(self, field: Field, grad_mode: int = L.GS_GRAD_MAP, pose_dev=None, stream=None):
+        sg, oc = self.splat_grads_c(), self.gaussian_grads_c()
+        L.check("gs_project_bwd", L.gs_project_bwd(ctypes.byref(field.c()), self.cams_c, self.n_views,
+                                                   _p(pose_dev), ctypes.byref(self.prm_c), grad_mode,
+                                                   ctypes.byref(sg), ctypes.byref(oc), _p(self.pose_part),
+                                                   _stream(stream)))
+
+    def backward(self, field: Field, grad_mode: int = L.GS_GRAD_MAP, pose_dev=None, stream=None):
+        """Blend backward then projection backward (and the twist reduction in pose mode)."""
+        self.render_bwd(field, grad_mode, stream)
+        self.project_bwd(field, grad_mode, pose_dev, stream)
+        if grad_mode & L.GS_GRAD_POSE:
+            self.pose_grad(stream)
+
+    def pose_grad(self, stream=None):
+        L.check("gs_pose_grad", L.gs_pose_grad(self.n, self.n_views, _p(self.pose_part), _p(self.d_twist),
+                                               _stream(stream)))
+
+    def dsr(self, field: Field, lam_big: float, lam_small: float, stream=None):
+        L.check("gs_dsr", L.gs_dsr(self.n, _p(field.log_scales), lam_big, lam_small, _p(self.ws), self.ws.numel(),
+                                   _p(self.d_log_scales), _p(self.dsr_out), _stream(stream)))
+
+    def pose_step(self, T_state, adam, step, lr=TRACKING_LR, b1=0.9, b2=0.999, eps=1e-15, pose_f32=None,
+                  stream=None):
+        lr_c = (ctypes.c_double * 6)(*lr)
+        L.check("gs_pose_step", L.gs_pose_step(self.n_views, _p(self.d_twist), _p(T_state), _p(adam), step, lr_c,
+                                               b1, b2, eps, _p(pose_f32), _stream(stream)))
+
+    # --------------------------------------------------------- iteration
+    def forward(self, field: Field, pose_dev=None, stream=None, want_keys=False):
+        self.project(field, pose_dev, stream)
+        self.bin_sort(want_keys, stream)
+        self.render_fwd(field, stream)
+
+    def iteration(self, field: Field, targets, decoder_W, decoder_b, w: LossWeights, grad_mode=L.GS_GRAD_MAP,
+                  pose_dev=None, stream=None):
+        """One fwd+bwd pass of the whole path: project, bin/sort, blend, loss, blend and
+        projection backward, pose-twist reduction, DSR.  Asynchronous."""
+        self.forward(field, pose_dev, stream)
+        self.loss(targets, decoder_W, decoder_b, w, stream)
+        self.backward(field, grad_mode, pose_dev, stream)
+        if (grad_mode & L.GS_GRAD_MAP) and (w.big or w.small):
+            self.dsr(field, w.big, w.small, stream)
+
+    def status(self) -> int:
+        """Device status word of the last binning (0 = ok); synchronises."""
+        return int(self.status_word.item())
+
+    def instances(self) -> int:
+        return int(self.n_inst.item())
+
+    def images(self, view: int = 0):
+        """Views of the rendered images of one view as [C,H,W] tensors (renderer-owned)."""
+        h, w = self.sizes[view]
+        a, b = self.pix_off[view], self.pix_off[view + 1]
+        return dict(rgb=self.img_rgb[:, a:b].view(3, h, w), depth=self.img_depth[a:b].view(h, w),
+                    sil=self.img_sil[a:b].view(h, w), feat=self.img_feat[: self.feat_dim, a:b].view(-1, h, w),
+                    T=self.img_T[a:b].view(h, w), n_contrib=self.img_nc[a:b].view(h, w))
+
+
+def fit_capacity(field: Field, cams, feat_dim: int, margin: float = 1.25, params: RasterParams = RasterParams(),
+                 n_classes: int = 0, device="cuda") -> Renderer:
+    """Builds a Renderer whose instance capacity fits this field and these views."""
+    probe = Renderer(field.n, cams, feat_dim, 0, device, params, n_classes)
+    probe.project(field)
+    need = int(probe.touched.sum(dtype=torch.int64).item())
+    cap = max(1024, int(need * margin))
+    return Renderer(field.n, cams, feat_dim, cap, device, params, n_classes)
+
+
+class RasterizeSG(torch.autograd.Function):
+    """Differentiable render of a Semantic Gaussian Field through libgs.
+
+    forward(renderer, means, quats, log_scales, opacity_logits, rgb, feat) returns
+    (rgb [3,P], depth [P], sil [P], feat [D,P]) over the renderer's views;
+    backward runs gs_render_bwd and returns the parameter gradients.
+    """
+
+    @staticmethod
+    def forward(ctx, renderer: Renderer, means, quats, log_scales, opacity_logits, rgb, feat):
+        field = Field(means.detach().contiguous(), quats.detach().contiguous(), log_scales.detach().contiguous(),
+                      opacity_logits.detach().contiguous(), rgb.detach().contiguous(), feat.detach().contiguous())
+        renderer.forward(field)
+        ctx.renderer, ctx.field = renderer, field
+        D = renderer.feat_dim
+        return (renderer.img_rgb.clone(), renderer.img_depth.clone(), renderer.img_sil.clone(),
+                renderer.img_feat[:D].clone())
+
+    @staticmethod
+    def backward(ctx, g_rgb, g_depth, g_sil, g_feat):
+        r = ctx.renderer
+        z = lambda g, like: like.zero_() if g is None else like.copy_(g)
+        z(g_rgb, r.g_rgb)
+        z(g_depth, r.g_depth)
+        z(g_sil, r.g_sil)
+        if r.feat_dim:
+            z(g_feat, r.g_feat[: r.feat_dim])
+        r.backward(ctx.field, L.GS_GRAD_MAP)
+        D = r.feat_dim
+        return (None, r.d_means.clone(), r.d_quats.clone(), r.d_log_scales.clone(), r.d_logits.clone(),
+                r.d_rgb.clone(), r.d_feat[:, :D].clone() if D else torch.zeros_like(ctx.field.feat))
+
+
+def rasterize(renderer: Renderer, means, quats, log_scales, opacity_logits, rgb, feat):
+    return RasterizeSG.apply(renderer, means, quats, log_scales, opacity_logits, rgb, feat)

@@ -1,0 +1,78 @@
+"""The C-ABI library builds, loads and exports every symbol include/gs.h declares (no GPU needed).
+
+Only host-side argument checks are exercised here: they return before any CUDA call.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2603_27781_gb300 import _lib as L
+from paper_2603_27781_gb300 import build, raster, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "gs.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(gs_\w+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return L.library()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 11
+    for name in names:
+        assert hasattr(lib, name), name
+        assert name in L.exported_symbols(), name
+
+
+def test_version_and_status_text(lib):
+    assert lib.gs_version() >= 10000
+    assert lib.gs_strerror(L.GS_ERR_CAPACITY).decode().startswith("tile instance")
+    assert lib.gs_strerror(12345).decode() == "unknown status"
+
+
+def test_workspace_size(lib):
+    cams = raster.cameras_c([synth.camera(1200, 680, 600.0)])
+    small = lib.gs_workspace_size(1000, 1, cams, 10000, 16)
+    big = lib.gs_workspace_size(1_000_000, 1, cams, 4_000_000, 16)
+    assert 0 < small < big
+    assert lib.gs_workspace_size(1000, 1, cams, 10000, 5) == 0          # unsupported feature dim
+    assert lib.gs_workspace_size(1000, 1, cams, 1 << 30, 16) == 0       # capacity too large
+    assert lib.gs_workspace_size(1000, 0, cams, 100, 16) == 0           # no views
+
+
+def test_argument_errors_before_any_launch(lib):
+    cam = raster.cameras_c([synth.camera(64, 48, 60.0)])
+    prm = raster.RasterParams().c()
+    g = L.gs_gaussians(10, 16, None, None, None, None, None, 0, None, 0)
+    pj = L.gs_projected(None, None, None)
+    assert lib.gs_project(ctypes.byref(g), cam, 0, None, ctypes.byref(prm), ctypes.byref(pj), None) == L.GS_ERR_ARG
+    bad = raster.RasterParams(tile=8).c()
+    assert lib.gs_project(ctypes.byref(g), cam, 1, None, ctypes.byref(bad), ctypes.byref(pj), None) == L.GS_ERR_ARG
+    assert lib.gs_project(ctypes.byref(g), cam, 1, None, ctypes.byref(prm), ctypes.byref(pj), None) == L.GS_ERR_ARG
+    b = L.gs_binning(-1, None, None, None, None, None)
+    assert lib.gs_bin_sort(10, ctypes.byref(pj), cam, 1, ctypes.byref(prm), None, 0, ctypes.byref(b),
+                           None) == L.GS_ERR_ARG
+    assert lib.gs_pose_grad(10, 0, None, None, None) == L.GS_ERR_ARG
+    assert lib.gs_dsr(-1, None, 0.0, 0.0, None, 0, None, None, None) == L.GS_ERR_ARG
+    lr = (ctypes.c_double * 6)(*([1e-3] * 6))
+    assert lib.gs_pose_step(1, None, None, None, 1, lr, 0.9, 0.999, 1e-15, None, None) == L.GS_ERR_ARG
+    zero_w = synth.camera(64, 48, 60.0)
+    zero_w.width = 0
+    assert lib.gs_workspace_size(10, 1, raster.cameras_c([zero_w]), 10, 16) == 0
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    monkeypatch.setattr(L, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(L, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        L.library()

@@ -1,0 +1,385 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, element by element.
+
+Sizes run from the tiny box scene to room scenes spanning hundreds of tiles with
+ragged image edges, multi-view batches and the reduced-precision storage form.
+Binning and sort are compared bit for bit; floating-point outputs within the
+stated tolerances, excluding (and counting) pixels where a threshold decision is
+within rounding distance in the oracle.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2603_27781_gb300 import raster, synth
+from paper_2603_27781_gb300 import _lib as L
+
+import gpu_cases as C
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib_built():
+    from paper_2603_27781_gb300 import build
+    build.build()
+    L.library()
+
+
+def _cases():
+    T = synth.look_pose((0.15, -0.1, -0.3), (0.05, 0.04, 1.0), up=(0, -1, 0))
+    return {
+        "box_64x48": lambda: C.box_case(2000, 16, 64, 48, 60.0),
+        "box_ragged_pose_70x50": lambda: C.box_case(3000, 8, 70, 50, 55.0, seed=3, T=T),
+        "room_20k_330x190": lambda: C.room_case(20000, 16, 330, 190, 165.0)[:2],
+    }
+
+
+CASES = _cases()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_projection_matches_oracle(name):
+    gs, cam = CASES[name]()
+    prm_g, prm_o = C.params_pair()
+    _, r = C.gpu_forward(gs, cam, prm_g)
+    gp = C.gpu_projection(r)
+    op = oracle.project(gs, cam, prm_o)
+    # the sort key is the same f32 fused chain on both sides: bit-exact
+    np.testing.assert_array_equal(gp["depth"].view(np.uint32), op["depth_key"].view(np.uint32))
+    np.testing.assert_allclose(gp["opacity"], op["opacity"], rtol=0, atol=1e-6)
+    vis = (gp["radius"] > 0) & (op["radius"] > 0)
+    # culling agrees except within rounding of z_near
+    assert ((gp["radius"] > 0) != (op["radius"] > 0)).sum() == 0
+    np.testing.assert_allclose(gp["uv"][vis], op["uv"][vis], rtol=2e-6, atol=2e-4)
+    scale = np.maximum(np.abs(op["conic"][vis, 0]), np.abs(op["conic"][vis, 2]))[:, None]
+    assert (np.abs(gp["conic"][vis] - op["conic"][vis]) <= 2e-4 * scale).all()
+    near_int = np.abs(op["radius_real"] - np.round(op["radius_real"])) < 1e-4
+    rad_diff = (gp["radius"] != op["radius"]) & ~near_int
+    assert rad_diff.sum() == 0
+    # tiles touched follow the exact integer rectangle rule from the GPU's own centre and radius
+    _, touched = oracle.rects(gp["uv"], gp["radius"], cam.width, cam.height)
+    np.testing.assert_array_equal(gp["touched"], touched)
+
+
+def _check_sort(gs, cams, prm_g):
+    _, r = C.gpu_forward(gs, cams, prm_g)
+    assert r.status() == 0
+    gp = C.gpu_projection(r)
+    n = gs.n
+    rects = []
+    for v, cam in enumerate(cams):
+        sl = slice(v * n, (v + 1) * n)
+        rects.append(oracle.rects(gp["uv"][sl], gp["radius"][sl], cam.width, cam.height)[0])
+    keys, vals, ranges = oracle.bin_sort(np.concatenate(rects), gp["depth"].astype(np.float32), cams,
+                                         n_per_view=n)
+    gk, gv, gr = C.gpu_binning(r)
+    assert r.instances() == len(keys)
+    np.testing.assert_array_equal(gk, keys)
+    np.testing.assert_array_equal(gv, vals)
+    np.testing.assert_array_equal(gr, ranges)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_bin_sort_bit_exact(name):
+    gs, cam = CASES[name]()
+    _check_sort(gs, [cam], C.params_pair()[0])
+
+
+def test_bin_sort_bit_exact_multiview_and_ties():
+    gs, cam, room = C.room_case(30000, 8, 200, 120, 100.0)
+    poses = synth.keyframe_loop(12, room=room)
+    cams = [synth.camera(200, 120, 100.0, T_cw=poses[0]), synth.camera(97, 61, 50.0, T_cw=poses[5]),
+            synth.camera(160, 90, 80.0, T_cw=poses[9])]
+    gs.means[1::2] = gs.means[0::2][: gs.means[1::2].shape[0]]  # duplicated centres: equal depth keys
+    _check_sort(gs, cams, C.params_pair()[0])
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_render_fwd_matches_oracle(name):
+    gs, cam = CASES[name]()
+    prm_g, prm_o = C.params_pair()
+    _, r = C.gpu_forward(gs, cam, prm_g)
+    gimg = C.np_images(r)
+    op, _, oimg = oracle.forward(gs, cam, prm_o)
+    excl, ndiff = C.excluded_pixels(cam, op, C.gpu_projection(r), oimg)
+    assert excl.mean() < 5e-3, (excl.sum(), ndiff)
+    C.assert_forward_close(gimg, oimg, excl, gs.feat_dim)
+    np.testing.assert_allclose(gimg["sil"] + gimg["T"], 1.0, atol=1e-5)
+
+
+def _bwd_compare(gs, cams, prm_g, prm_o, seed=7, rgb_dtype=torch.float32, feat_dtype=torch.float32,
+                 gs_oracle=None):
+    field, r = C.gpu_forward(gs, cams, prm_g, rgb_dtype=rgb_dtype, feat_dtype=feat_dtype)
+    gso = gs if gs_oracle is None else gs_oracle
+    projs, bins, oimgs = C.oracle_multiview(gso, cams, prm_o)
+    gp = C.gpu_projection(r)
+    grads_v, P_off = [], 0
+    for v, cam in enumerate(cams):
+        sl = slice(v * gs.n, (v + 1) * gs.n)
+        gpv = {k: a[sl] for k, a in gp.items()}
+        excl, _ = C.excluded_pixels(cam, projs[v], gpv, oimgs[v])
+        C.assert_forward_close(C.np_images(r, v), oimgs[v], excl, gs.feat_dim)
+        P = cam.width * cam.height
+        g = C.random_image_grads(P, gs.feat_dim, seed + v)
+        keep = ~excl.ravel()
+        for k in g:
+            g[k] = g[k] * keep
+        grads_v.append({k: a.reshape((-1, cam.height, cam.width) if a.ndim == 2 else (cam.height, cam.width))
+                        for k, a in g.items()})
+        # upload into the renderer's image-gradient buffers
+        a, b = r.pix_off[v], r.pix_off[v + 1]
+        r.g_rgb[:, a:b] = torch.as_tensor(g["rgb"], dtype=torch.float32)
+        r.g_depth[a:b] = torch.as_tensor(g["depth"], dtype=torch.float32)
+        r.g_sil[a:b] = torch.as_tensor(g["sil"], dtype=torch.float32)
+        if gs.feat_dim:
+            r.g_feat[:, a:b] = torch.as_tensor(g["feat"], dtype=torch.float32)
+    r.backward(field, L.GS_GRAD_MAP | L.GS_GRAD_POSE)
+    torch.cuda.synchronize()
+    ob = C.oracle_multiview_backward(gso, cams, prm_o, projs, bins, grads_v)
+    D = gs.feat_dim
+    got = dict(means=r.d_means, quats=r.d_quats, log_scales=r.d_log_scales, opacity_logits=r.d_logits, rgb=r.d_rgb,
+               feat=r.d_feat[:, :D], twist=r.d_twist)
+    for k, t in got.items():
+        if k == "feat" and D == 0:
+            continue
+        C.assert_grad_close(k, t.cpu().numpy(), ob[k])
+    return r, ob
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_render_bwd_matches_oracle(name):
+    gs, cam = CASES[name]()
+    prm_g, prm_o = C.params_pair()
+    _bwd_compare(gs, [cam], prm_g, prm_o)
+
+
+def test_render_bwd_multiview_sums_views():
+    gs, cam, room = C.room_case(20000, 16, 160, 96, 80.0)
+    poses = synth.keyframe_loop(8, room=room)
+    cams = [synth.camera(160, 96, 80.0, T_cw=poses[1]), synth.camera(100, 70, 60.0, T_cw=poses[4])]
+    prm_g, prm_o = C.params_pair()
+    _bwd_compare(gs, cams, prm_g, prm_o)
+
+
+def test_half_storage_matches_oracle_on_rounded_values():
+    """F16 colour and BF16 features, blended in f32: against the oracle fed the same rounded values."""
+    gs, cam = C.box_case(2000, 16, 64, 48, 60.0)
+    rounded = gs.copy()
+    rounded.rgb = torch.as_tensor(gs.rgb).to(torch.float16).float().numpy()
+    rounded.feat = torch.as_tensor(gs.feat).to(torch.bfloat16).float().numpy()
+    prm_g, prm_o = C.params_pair()
+    _bwd_compare(gs, [cam], prm_g, prm_o, rgb_dtype=torch.float16, feat_dtype=torch.bfloat16, gs_oracle=rounded)
+
+
+def test_pose_translation_gradient_invariant_on_gpu():
+    """g_rho = R_cw sum_i g_mu,i, checked between two outputs of the CUDA path."""
+    gs, cam, _ = C.room_case(20000, 8, 160, 96, 80.0)
+    field, r = C.gpu_forward(gs, cam, C.params_pair()[0])
+    g = C.random_image_grads(r.P, 8, 3)
+    r.g_rgb.copy_(torch.as_tensor(g["rgb"])); r.g_depth.copy_(torch.as_tensor(g["depth"]))
+    r.g_sil.copy_(torch.as_tensor(g["sil"])); r.g_feat.copy_(torch.as_tensor(g["feat"]))
+    r.backward(field, L.GS_GRAD_MAP | L.GS_GRAD_POSE)
+    R = torch.as_tensor(cam.T_cw[:3, :3])
+    want = R @ r.d_means.double().sum(0).cpu()
+    np.testing.assert_allclose(r.d_twist[0, :3].cpu().numpy(), want.numpy(), rtol=1e-4,
+                               atol=1e-4 * float(want.abs().max()))
+
+
+# --------------------------------------------------------------------- losses
+def _loss_case(P_shape=(48, 64), D=16, K=8, seed=20, views=1):
+    g = synth.rng(seed)
+    H, W = P_shape
+    cams = [synth.camera(W, H, 60.0) for _ in range(views)]
+    imgs = [dict(rgb=g.random((3, H, W)), depth=g.uniform(2, 5, (H, W)), sil=g.uniform(0.9, 1.0, (H, W)),
+                 feat=g.standard_normal((D, H, W))) for _ in range(views)]
+    tgts = [synth.Frame(g.random((3, H, W)).astype(np.float32), (im["depth"] + g.normal(0, 0.05, (H, W))).astype(np.float32),
+                        g.integers(0, K, (H, W)).astype(np.uint8)) for im in imgs]
+    for t in tgts:
+        t.depth[0, :5] = 0.0
+        t.label[1, :7] = 255
+    dec = synth.decoder(K, D, seed=seed + 1)
+    imgs = [{k: v.astype(np.float32).astype(np.float64) for k, v in im.items()} for im in imgs]
+    return cams, imgs, tgts, dec
+
+
+@pytest.mark.parametrize("mode", ["mapping", "tracking"])
+@pytest.mark.parametrize("views", [1, 2])
+def test_loss_matches_oracle(mode, views):
+    cams, imgs, tgts, dec = _loss_case(views=views)
+    w = raster.MAPPING if mode == "mapping" else raster.TRACKING
+    wo = oracle.MAPPING if mode == "mapping" else oracle.TRACKING
+    D, K = 16, dec.W.shape[0]
+    r = raster.Renderer(0, cams, D, 0, n_classes=K)
+    cat = lambda key, f=lambda a: a: torch.as_tensor(np.concatenate([f(im[key]).reshape(im[key].shape[0], -1)
+                                                                     if im[key].ndim == 3 else f(im[key]).reshape(1, -1)
+                                                                     for im in imgs], 1), dtype=torch.float32).cuda()
+    r.img_rgb.copy_(cat("rgb")); r.img_depth.copy_(cat("depth")[0]); r.img_sil.copy_(cat("sil")[0])
+    r.img_feat.copy_(cat("feat"))
+    tg = dict(rgb=torch.as_tensor(np.concatenate([t.rgb.reshape(3, -1) for t in tgts], 1)).cuda(),
+              depth=torch.as_tensor(np.concatenate([t.depth.ravel() for t in tgts])).cuda(),
+              label=torch.as_tensor(np.concatenate([t.label.ravel() for t in tgts])).cuda())
+    Wd, bd = torch.as_tensor(dec.W).cuda(), torch.as_tensor(dec.b).cuda()
+    r.loss(tg, Wd, bd, w)
+    torch.cuda.synchronize()
+    total, dW, db = 0.0, 0.0, 0.0
+    for v, (im, t) in enumerate(zip(imgs, tgts)):
+        o = oracle.loss(im, t, dec, wo)
+        a, b = r.pix_off[v], r.pix_off[v + 1]
+        H, W = r.sizes[v]
+        if mode == "tracking":
+            # the median is an integer decision taken on the f32 depth errors
+            e = np.abs(im["depth"].astype(np.float32) - t.depth)[t.depth > 0]
+            assert r.median[v].item() == np.float32(oracle.lower_median(e.astype(np.float64)))
+            gmask = r.mask[a:b].cpu().numpy().reshape(H, W)
+            near = np.abs(np.abs(im["depth"] - t.depth) - 10 * o["median"]) < 1e-5 * o["median"]
+            assert (gmask != o["mask"])[~near].sum() == 0
+        np.testing.assert_allclose(r.g_rgb[:, a:b].cpu().numpy().reshape(3, H, W), o["rgb"], atol=1e-9)
+        np.testing.assert_allclose(r.g_depth[a:b].cpu().numpy().reshape(H, W), o["depth"], atol=1e-9)
+        np.testing.assert_allclose(r.g_feat[:, a:b].cpu().numpy().reshape(D, H, W), o["feat"], atol=1e-9,
+                                   rtol=1e-5)
+        total += o["total"]
+        dW = dW + o["W"]
+        db = db + o["b"]
+    assert r.loss_out[0].item() == pytest.approx(total, rel=1e-5)
+    C.assert_grad_close("dW", r.d_dec_W.cpu().numpy(), dW, 1e-5)
+    C.assert_grad_close("db", r.d_dec_b.cpu().numpy(), db, 1e-5)
+
+
+def test_median_is_bit_exact_on_large_views():
+    g = synth.rng(33)
+    cams = [synth.camera(1200, 680, 600.0), synth.camera(640, 480, 525.0)]
+    r = raster.Renderer(0, cams, 0, 0, n_classes=1)
+    depth = g.uniform(0.5, 6.0, r.P).astype(np.float32)
+    tdepth = (depth + g.standard_normal(r.P).astype(np.float32) * 0.02).astype(np.float32)
+    tdepth[g.random(r.P) < 0.1] = 0.0
+    r.img_depth.copy_(torch.as_tensor(depth))
+    r.img_sil.fill_(1.0)
+    tg = dict(rgb=torch.zeros(3, r.P, device="cuda"), depth=torch.as_tensor(tdepth).cuda(),
+              label=torch.full((r.P,), 255, dtype=torch.uint8, device="cuda"))
+    r.loss(tg, torch.zeros(1, 0, device="cuda"), torch.zeros(1, device="cuda"), raster.TRACKING)
+    for v in range(2):
+        a, b = r.pix_off[v], r.pix_off[v + 1]
+        e = np.abs(depth[a:b] - tdepth[a:b])[tdepth[a:b] > 0]
+        assert r.median[v].item() == np.float32(oracle.lower_median(e.astype(np.float64)))
+
+
+def test_dsr_matches_oracle():
+    gs, _, _ = C.room_case(200000, 0, 64, 48, 60.0)
+    ls = torch.as_tensor(gs.log_scales).cuda()
+    r = raster.Renderer(gs.n, [synth.camera(64, 48, 60.0)], 0, 0)
+    r.d_log_scales.zero_()
+    field = raster.Field(torch.zeros(gs.n, 3).cuda(), torch.zeros(gs.n, 4).cuda(), ls, torch.zeros(gs.n).cuda(),
+                         torch.zeros(gs.n, 3).cuda(), torch.zeros(gs.n, 0).cuda())
+    r.dsr(field, 0.01, 0.001)
+    torch.cuda.synchronize()
+    val, grad, st = oracle.dsr(gs.log_scales, 0.01, 0.001)
+    s = np.exp(gs.log_scales.astype(np.float64))
+    near = (np.abs(s - (st["mu"] + 2 * st["sigma"])) < 1e-5 * s) | (np.abs(s - (st["mu"] - 2 * st["sigma"])) < 1e-5 * s)
+    assert near.sum() == 0
+    out = r.dsr_out.cpu().numpy()
+    assert out[0] == pytest.approx(val, rel=1e-5)
+    assert (out[3], out[4]) == (st["n_big"], st["n_small"])
+    np.testing.assert_allclose(r.d_log_scales.cpu().numpy(), grad, rtol=1e-5, atol=1e-12)
+
+
+def test_pose_step_matches_oracle():
+    T = synth.look_pose((1.0, 2.0, 1.5), (0.3, 1.0, -0.1))
+    g = synth.rng(40)
+    r = raster.Renderer(0, [synth.camera(64, 48, 60.0)], 0, 0)
+    Ts = torch.as_tensor(T.reshape(1, 16)).cuda()
+    adam = torch.zeros(1, 12, dtype=torch.float64, device="cuda")
+    Tf = torch.zeros(1, 16, device="cuda")
+    Tref, m, v = T.copy(), np.zeros(6), np.zeros(6)
+    for step in range(1, 4):
+        grad = g.standard_normal(6)
+        r.d_twist.copy_(torch.as_tensor(grad.reshape(1, 6)))
+        r.pose_step(Ts, adam, step, pose_f32=Tf)
+        Tref, m, v = oracle.pose_step(Tref, grad, m, v, step, np.array(raster.TRACKING_LR))
+    np.testing.assert_allclose(Ts.cpu().numpy().reshape(4, 4), Tref, atol=1e-12)
+    np.testing.assert_allclose(Tf.cpu().numpy().reshape(4, 4), Tref, atol=1e-6)
+
+
+# ---------------------------------------------------------------- whole step
+def test_full_iteration_tiny_scene():
+    """cfg: 2,000 Gaussians in a box, 64x48, mapping loss + DSR + pose twist vs oracle.step."""
+    gs, cam = C.box_case(2000, 16, 64, 48, 60.0)
+    prm_g, prm_o = C.params_pair()
+    dec = synth.decoder(8, 16)
+    tgt_img = oracle.forward(synth.jitter_means(gs), cam, prm_o)[2]
+    f = tgt_img["feat"].reshape(16, -1).T
+    label = np.argmax(f @ dec.W.T.astype(np.float64) + dec.b, 1).astype(np.uint8).reshape(48, 64)
+    tgt = synth.Frame(tgt_img["rgb"].astype(np.float32), tgt_img["depth"].astype(np.float32), label)
+    ref = oracle.step(gs, cam, prm_o, tgt, dec, oracle.MAPPING)
+    field, r = C.gpu_forward(gs, cam, prm_g)
+    excl, _ = C.excluded_pixels(cam, ref["proj"], C.gpu_projection(r), ref["img"])
+    assert excl.sum() == 0
+    tg = dict(rgb=torch.as_tensor(tgt.rgb.reshape(3, -1)).cuda(), depth=torch.as_tensor(tgt.depth.ravel()).cuda(),
+              label=torch.as_tensor(tgt.label.ravel()).cuda())
+    r.iteration(field, tg, torch.as_tensor(dec.W).cuda(), torch.as_tensor(dec.b).cuda(), raster.MAPPING,
+                L.GS_GRAD_MAP | L.GS_GRAD_POSE)
+    torch.cuda.synchronize()
+    total = r.loss_out[0].item() + r.dsr_out[0].item()
+    assert total == pytest.approx(ref["total"], rel=1e-5)
+    gr = ref["grads"]
+    for k, t in dict(means=r.d_means, quats=r.d_quats, log_scales=r.d_log_scales, opacity_logits=r.d_logits,
+                     rgb=r.d_rgb, feat=r.d_feat, twist=r.d_twist[0], W=r.d_dec_W, b=r.d_dec_b).items():
+        C.assert_grad_close(k, t.cpu().numpy(), gr[k])
+
+
+def test_autograd_function_matches_direct_backward():
+    gs, cam = C.box_case(2000, 8, 64, 48, 60.0)
+    field, r = C.gpu_forward(gs, cam, C.params_pair()[0])
+    params = [torch.as_tensor(a).cuda().requires_grad_(True) for a in gs.arrays()]
+    rgb, depth, sil, feat = raster.rasterize(r, *params)
+    g = C.random_image_grads(r.P, 8, 11)
+    gl = [torch.as_tensor(g[k], dtype=torch.float32).cuda() for k in ("rgb", "depth", "sil", "feat")]
+    loss = (rgb * gl[0]).sum() + (depth * gl[1]).sum() + (sil * gl[2]).sum() + (feat * gl[3]).sum()
+    loss.backward()
+    r.g_rgb.copy_(gl[0]); r.g_depth.copy_(gl[1]); r.g_sil.copy_(gl[2]); r.g_feat.copy_(gl[3])
+    r.backward(field, L.GS_GRAD_MAP)
+    for p, d in zip(params, (r.d_means, r.d_quats, r.d_log_scales, r.d_logits, r.d_rgb, r.d_feat)):
+        torch.testing.assert_close(p.grad, d, rtol=1e-5, atol=1e-9)
+
+
+# ----------------------------------------------------------------- edge cases
+def test_empty_field_renders_background():
+    cam = synth.camera(50, 37, 40.0)
+    prm = raster.RasterParams(bg=(0.2, 0.4, 0.6))
+    gs = synth.box_field(0, 8)
+    field, r = C.gpu_forward(gs, cam, prm, capacity=16)
+    img = C.np_images(r)
+    for c in range(3):
+        np.testing.assert_array_equal(img["rgb"][c], np.float32(prm.bg[c]))
+    assert (img["depth"] == 0).all() and (img["sil"] == 0).all() and (img["T"] == 1).all()
+    assert (img["n_contrib"] == 0).all() and r.instances() == 0 and r.status() == 0
+
+
+def test_all_culled_field():
+    gs, cam = C.box_case(500, 8, 40, 30, 40.0)
+    gs.means[:, 2] *= -1
+    field, r = C.gpu_forward(gs, cam, C.params_pair()[0], capacity=64)
+    assert r.instances() == 0 and r.status() == 0
+    r.g_rgb.fill_(1.0); r.g_depth.fill_(1.0); r.g_feat.fill_(1.0)
+    r.backward(field, L.GS_GRAD_MAP | L.GS_GRAD_POSE)
+    for t in (r.d_means, r.d_quats, r.d_log_scales, r.d_logits, r.d_rgb, r.d_feat, r.d_twist):
+        assert not bool(t.abs().max() > 0)
+
+
+def test_capacity_overflow_is_reported():
+    gs, cam = C.box_case(2000, 8, 64, 48, 60.0)
+    field, r = C.gpu_forward(gs, cam, C.params_pair()[0], capacity=100)
+    assert r.status() == L.GS_ERR_CAPACITY
+    op = oracle.project(gs, cam, oracle.Params())
+    assert r.instances() == int(op["touched"].sum())
+
+
+def test_argument_errors_return_status():
+    gs, cam = C.box_case(10, 8, 32, 32, 30.0)
+    field = raster.Field.from_numpy(gs)
+    r = raster.Renderer(gs.n, [cam], 8, 64)
+    bad = raster.RasterParams(tile=8)
+    with pytest.raises(L.GsError) as e:
+        r.prm_c = bad.c()
+        r.project(field)
+    assert e.value.status == L.GS_ERR_ARG
