@@ -101,14 +101,19 @@ typedef struct {
     int32_t feat_dtype;
 } gs_gaussians;
 
-/* Projected splats, one record per item (float4-aligned, 16-byte aligned):
+/* Projected splats, one record per item (16-byte aligned arrays):
  *   uvdo[4*item]  = (u, v, depth, opacity): centre g_i (supp. B.1), camera-frame
  *                   depth d_i (Eq. 6) and the activated opacity o_i (Eq. 5);
+ *   uv_lo[2*item] = (u - u_f32, v - v_f32): the centre is carried as an
+ *                   unevaluated f32 sum (hi in uvdo, lo here) because a pixel
+ *                   coordinate near 1000 has an f32 spacing of 6e-5 px;
  *   conic[4*item] = (A, B, C, radius): Sigma2D^-1 = [[A, B], [B, C]] (Eq. 3, 5)
  *                   and the integer pixel radius stored as a float;
- *   tiles_touched[item] = tiles covered (0 = culled). */
+ *   tiles_touched[item] = tiles covered (0 = culled).  Binning uses the f32
+ *   centre uvdo.xy. */
 typedef struct {
     float *uvdo;
+    float *uv_lo;
     float *conic;
     int32_t *tiles_touched;
 } gs_projected;
@@ -205,7 +210,8 @@ size_t gs_workspace_size(int64_t n, int n_views, const gs_camera *cams, int64_t 
  * (u, v) = (fx x/z + cx, fy y/z + cy), Sigma2D = J R_cw Sigma R_cw^T J^T +
  * lowpass I, its inverse (in f64 when near singular), the radius and the number
  * of tiles it covers.  The depth is computed as the f32 fused chain
- * fma(r20, x, fma(r21, y, fma(r22, z, t_z))).  pose_dev, if not NULL, is a
+ * fma(r20, x, fma(r21, y, fma(r22, z, t_z))); the centre (u, v) is computed
+ * with compensated (double-f32) arithmetic.  pose_dev, if not NULL, is a
  * device f32 [n_views,16] array of world-to-camera transforms that replaces
  * cams[v].T_cw (for device-resident poses); intrinsics always come from cams.
  * out arrays hold n_views * n items. */

@@ -150,13 +150,13 @@ def render_fwd(cam, proj, rgb, feat, vals, ranges, prm: Params, view_offset=0, t
     P = W * H
     out = dict(rgb=np.zeros((3, H, W)), depth=np.zeros((H, W)), sil=np.zeros((H, W)),
                feat=np.zeros((D, H, W)), T=np.zeros((H, W)), n_contrib=np.zeros((H, W), np.int32),
-               margin=np.zeros((H, W)))
+               margin=np.zeros((H, W)), sens=np.zeros((H, W)))
     args = [_d(proj["uv"]), _d(proj["conic"]), _d(proj["opacity"]), _d(proj["depth"]), _d(rgb), _d(feat)]
     _L().or_render_fwd(ctypes.c_int(W), ctypes.c_int(H), ctypes.c_int(prm.tile), ctypes.c_int(D),
                        I64(view_offset), I64(tile_offset), *map(_p, args),
                        _p(np.ascontiguousarray(vals, np.uint32)), _p(np.ascontiguousarray(ranges, np.uint32)),
                        _p(prm.array()), *(_p(out[k]) for k in ("rgb", "depth", "sil", "feat", "T",
-                                                               "n_contrib", "margin")))
+                                                               "n_contrib", "margin", "sens")))
     return out
 
 

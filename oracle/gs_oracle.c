@@ -104,11 +104,29 @@ static float depth_key(const double T[16], const double mu[3]) {
     return fmaf(r20, x, fmaf(r21, y, fmaf(r22, z, tz)));
 }
 
+/* Point at which the EWA Jacobian J of Eq. 3 is evaluated: (x/z, y/z) of the
+ * camera-frame centre, clamped to the view's extent widened by 15% of the image
+ * size on each side (for a centred principal point: 1.3 x the half field of
+ * view, the convention of the 3DGS rasterizer that GS3LAM renders with).  The
+ * projected centre itself is never clamped.  in_x / in_y report whether the
+ * coordinate is inside the clamp interval (its derivative is 0 outside). */
+static void jacobian_point(const double p[3], const double *cam, double *tx, double *ty, int *in_x, int *in_y) {
+    double W = cam[C_W], H = cam[C_H], fx = cam[C_FX], fy = cam[C_FY], cx = cam[C_CX], cy = cam[C_CY];
+    double lox = (-cx - 0.15 * W) / fx, hix = (W - cx + 0.15 * W) / fx;
+    double loy = (-cy - 0.15 * H) / fy, hiy = (H - cy + 0.15 * H) / fy;
+    double x = p[0] / p[2], y = p[1] / p[2];
+    *tx = x < lox ? lox : (x > hix ? hix : x);
+    *ty = y < loy ? loy : (y > hiy ? hiy : y);
+    if (in_x) *in_x = (x >= lox && x <= hix);
+    if (in_y) *in_y = (y >= loy && y <= hiy);
+}
+
 /* ------------------------------------------------- A1-A2: projection (Eq. 2, 3) */
 /*
  * For each Gaussian: activate the parameters, build Sigma (Eq. 2), move the
  * mean into the camera frame, project it (supp. B.1: g = K T_cw mu / d), form
- * Sigma2D by the EWA approximation (Eq. 3), add the low-pass term, invert it
+ * Sigma2D by the EWA approximation (Eq. 3) with J evaluated at the clamped
+ * point of jacobian_point(), add the low-pass term, invert it
  * to the conic, and bound the splat by radius_sigma standard deviations of the
  * larger eigenvalue.  Culled Gaussians (z <= z_near, singular or non-finite
  * Sigma2D) get radius 0 and touch no tile.
@@ -166,8 +184,10 @@ void or_project(int64_t n, const double *means, const double *quats, const doubl
         double tmp[9], Sc[9];
         mm3(Rcw, Sig, tmp);
         mm3(tmp, RcwT, Sc);
-        double z = p[2], z2 = z * z;
-        double J[6] = {fx / z, 0, -fx * p[0] / z2, 0, fy / z, -fy * p[1] / z2};
+        double z = p[2];
+        double tx_, ty_;
+        jacobian_point(p, cam, &tx_, &ty_, NULL, NULL);
+        double J[6] = {fx / z, 0, -fx * tx_ / z, 0, fy / z, -fy * ty_ / z};
         double JS[6];
         for (int r = 0; r < 2; r++)
             for (int c = 0; c < 3; c++)
@@ -289,7 +309,12 @@ int64_t or_bin_sort(int n_views, int64_t n_per_view, const int32_t *rect, const 
  * feat = sum w f, T_final, n_contrib = 1-based list position of the last
  * blended splat.  margin = smallest relative distance of any threshold
  * decision taken for that pixel (for excluding pixels where a different
- * rounding could flip a decision).
+ * rounding could flip a decision).  sens = sum over blended splats of
+ * w (|A| dx^2 + 2 |B dx dy| + |C| dy^2) / 2: the absolute change of the
+ * exponents, weighted by the blend, per unit relative change of the conics,
+ * i.e. how strongly the pixel amplifies rounding in the 2D covariances (an
+ * elongated splat evaluated far along its long axis makes the quadratic form
+ * a difference of large terms).
  *
  * Gaussian attributes are indexed by vals[j] (a view-local index after
  * subtracting view_offset); images are planar [C, H, W].
@@ -309,12 +334,12 @@ static double rel_gap(double a, double b) { return fabs(a - b) / fabs(b); }
  * arrays when given; returns the number of blended splats. */
 static int64_t blend_pixel(const raster_ctx *c, int px, int py, double *acc_rgb, double *acc_depth,
                            double *acc_sil, double *acc_feat, double *T_out, int64_t *last_out,
-                           double *margin_out, int64_t *list_pos, double *list_alpha, double *list_T,
-                           double *list_G, int *list_clamped) {
+                           double *margin_out, double *sens_out, int64_t *list_pos, double *list_alpha,
+                           double *list_T, double *list_G, int *list_clamped) {
     const double *prm = c->prm;
     int64_t t = c->tile_offset + (int64_t)(py / c->tile) * c->tx + px / c->tile;
     uint32_t start = c->ranges[2 * t], end = c->ranges[2 * t + 1];
-    double T = 1.0, margin = INFINITY;
+    double T = 1.0, margin = INFINITY, sens = 0.0;
     double pxc = px + 0.5, pyc = py + 0.5;
     int64_t nb = 0, last = 0;
     for (int d = 0; d < 3; d++) acc_rgb[d] = 0;
@@ -344,6 +369,8 @@ static int64_t blend_pixel(const raster_ctx *c, int px, int py, double *acc_rgb,
         }
         if (Tn < prm[P_T_MIN]) break;
         double w = alpha * T;
+        /* conditioning: the exponent's absolute error per unit relative error of (A, B, C) */
+        sens += w * 0.5 * (fabs(cn[0]) * dx * dx + 2.0 * fabs(cn[1] * dx * dy) + fabs(cn[2]) * dy * dy);
         for (int d = 0; d < 3; d++) acc_rgb[d] += w * c->rgb[3 * g + d];
         *acc_depth += w * c->depth[g];
         *acc_sil += w;
@@ -362,6 +389,7 @@ static int64_t blend_pixel(const raster_ctx *c, int px, int py, double *acc_rgb,
     *T_out = T;
     *last_out = last;
     *margin_out = margin;
+    *sens_out = sens;
     return nb;
 }
 
@@ -370,7 +398,8 @@ void or_render_fwd(int W, int H, int tile, int D, int64_t view_offset, int64_t t
                    const double *uv, const double *conic, const double *opacity, const double *depth,
                    const double *rgb, const double *feat, const uint32_t *vals, const uint32_t *ranges,
                    const double *prm, double *out_rgb, double *out_depth, double *out_sil,
-                   double *out_feat, double *out_T, int32_t *out_ncontrib, double *out_margin) {
+                   double *out_feat, double *out_T, int32_t *out_ncontrib, double *out_margin,
+                   double *out_sens) {
     raster_ctx c = {W, H, tile, (W + tile - 1) / tile, D, uv, conic, opacity, depth, rgb, feat,
                     vals, ranges, prm, view_offset, tile_offset};
     int64_t P = (int64_t)W * H;
@@ -378,9 +407,9 @@ void or_render_fwd(int W, int H, int tile, int D, int64_t view_offset, int64_t t
     for (int py = 0; py < H; py++)
         for (int px = 0; px < W; px++) {
             int64_t pix = (int64_t)py * W + px;
-            double acc_rgb[3], acc_depth, acc_sil, T, margin;
+            double acc_rgb[3], acc_depth, acc_sil, T, margin, sens;
             int64_t last;
-            blend_pixel(&c, px, py, acc_rgb, &acc_depth, &acc_sil, acc_feat, &T, &last, &margin,
+            blend_pixel(&c, px, py, acc_rgb, &acc_depth, &acc_sil, acc_feat, &T, &last, &margin, &sens,
                         NULL, NULL, NULL, NULL, NULL);
             for (int d = 0; d < 3; d++) out_rgb[d * P + pix] = acc_rgb[d] + T * prm[P_BG_R + d];
             out_depth[pix] = acc_depth;
@@ -389,6 +418,7 @@ void or_render_fwd(int W, int H, int tile, int D, int64_t view_offset, int64_t t
             out_T[pix] = T;
             out_ncontrib[pix] = (int32_t)last;
             out_margin[pix] = margin;
+            out_sens[pix] = sens;
         }
     free(acc_feat);
 }
@@ -436,10 +466,10 @@ void or_render_bwd(int W, int H, int tile, int D, int64_t view_offset, int64_t t
     for (int py = 0; py < H; py++)
         for (int px = 0; px < W; px++) {
             int64_t pix = (int64_t)py * W + px;
-            double acc_rgb[3], acc_depth, acc_sil, T, margin;
+            double acc_rgb[3], acc_depth, acc_sil, T, margin, sens;
             int64_t last;
             int64_t nb = blend_pixel(&c, px, py, acc_rgb, &acc_depth, &acc_sil, acc_feat, &T, &last,
-                                     &margin, lp, la, lT, lG, lc);
+                                     &margin, &sens, lp, la, lT, lG, lc);
             /* channel order: r, g, b, depth, sil, feat[0..D) */
             for (int d = 0; d < 3; d++) { gx[d] = g_rgb[d * P + pix]; S[d] = prm[P_BG_R + d]; }
             gx[3] = g_depth[pix]; S[3] = 0;
@@ -487,7 +517,8 @@ void or_render_bwd(int W, int H, int tile, int D, int64_t view_offset, int64_t t
  *   conic = Sigma2D^-1:      G2 = -conic Ghat conic, Ghat = [[dA, dB/2], [dB/2, dC]]
  *   Sigma2D = J Sc J^T:      Gc = J^T G2 J,  dJ = 2 G2 J Sc
  *   Sc = R_cw Sigma R_cw^T:  GSigma = R_cw^T Gc R_cw
- *   J(p), u(p), v(p), d = p_z give g_p; g_mu = R_cw^T g_p
+ *   J(p) (through the clamped evaluation point), u(p), v(p), d = p_z give g_p;
+ *   g_mu = R_cw^T g_p
  *   Sigma = M M^T, M = Rq diag(s): dM = 2 GSigma M -> ds, dRq -> dq_hat -> dq
  *   o = sigmoid(logit): dlogit = o (1 - o) do
  *   pose: p' = p + phi x p + rho, Sc' = Sc + [phi]x Sc - Sc [phi]x, so
@@ -532,8 +563,11 @@ void or_project_bwd(int64_t n, const double *means, const double *quats, const d
         mm3(M, MT, Sig);
         mm3(Rcw, Sig, tmp);
         mm3(tmp, RcwT, Sc);
-        double x = p[0], y = p[1], z = p[2], z2 = z * z, z3 = z2 * z;
-        double J[6] = {fx / z, 0, -fx * x / z2, 0, fy / z, -fy * y / z2};
+        double x = p[0], y = p[1], z = p[2], z2 = z * z;
+        double tx_, ty_;
+        int in_x, in_y;
+        jacobian_point(p, cam, &tx_, &ty_, &in_x, &in_y);
+        double J[6] = {fx / z, 0, -fx * tx_ / z, 0, fy / z, -fy * ty_ / z};
         double JS[6];
         for (int r = 0; r < 2; r++)
             for (int c = 0; c < 3; c++)
@@ -579,12 +613,15 @@ void or_project_bwd(int64_t n, const double *means, const double *quats, const d
         gp[1] += dv * fy / z;
         gp[2] += -dv * fy * y / z2;
         gp[2] += d_depth[i];
+        /* J02 = -fx t_x / z, t_x = clamp(x / z): dt_x/dx = 1/z, dt_x/dz = -x/z^2 inside, 0 outside */
+        double dtx_dx = in_x ? 1.0 / z : 0.0, dtx_dz = in_x ? -x / z2 : 0.0;
+        double dty_dy = in_y ? 1.0 / z : 0.0, dty_dz = in_y ? -y / z2 : 0.0;
         gp[2] += dJ[0] * (-fx / z2);
-        gp[0] += dJ[2] * (-fx / z2);
-        gp[2] += dJ[2] * (2.0 * fx * x / z3);
+        gp[0] += dJ[2] * (-fx / z) * dtx_dx;
+        gp[2] += dJ[2] * (-fx * dtx_dz / z + fx * tx_ / z2);
         gp[2] += dJ[4] * (-fy / z2);
-        gp[1] += dJ[5] * (-fy / z2);
-        gp[2] += dJ[5] * (2.0 * fy * y / z3);
+        gp[1] += dJ[5] * (-fy / z) * dty_dy;
+        gp[2] += dJ[5] * (-fy * dty_dz / z + fy * ty_ / z2);
         for (int k = 0; k < 3; k++) gm[k] = RcwT[3 * k] * gp[0] + RcwT[3 * k + 1] * gp[1] + RcwT[3 * k + 2] * gp[2];
 
         /* Sc -> Sigma -> M -> (s, Rq) */

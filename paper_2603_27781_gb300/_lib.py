@@ -35,7 +35,7 @@ class gs_gaussians(Structure):
 
 
 class gs_projected(Structure):
-    _fields_ = [("uvdo", c_void_p), ("conic", c_void_p), ("tiles_touched", c_void_p)]
+    _fields_ = [("uvdo", c_void_p), ("uv_lo", c_void_p), ("conic", c_void_p), ("tiles_touched", c_void_p)]
 
 
 class gs_binning(Structure):

@@ -26,6 +26,10 @@ bool make_view_table(const gs_camera *cams, int n_views, int64_t n, ViewTable *v
         vt->TY[v] = (c.height + kTile - 1) / kTile;
         vt->fx[v] = c.fx; vt->fy[v] = c.fy; vt->cx[v] = c.cx; vt->cy[v] = c.cy;
         for (int k = 0; k < 12; ++k) vt->T[v][k] = c.T_cw[k];
+        vt->jx_lo[v] = (float)((-(double)c.cx - 0.15 * c.width) / c.fx);
+        vt->jx_hi[v] = (float)(((double)c.width - c.cx + 0.15 * c.width) / c.fx);
+        vt->jy_lo[v] = (float)((-(double)c.cy - 0.15 * c.height) / c.fy);
+        vt->jy_hi[v] = (float)(((double)c.height - c.cy + 0.15 * c.height) / c.fy);
         tiles += (int64_t)vt->TX[v] * vt->TY[v];
         pix += (int64_t)c.width * c.height;
     }

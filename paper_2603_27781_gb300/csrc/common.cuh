@@ -24,6 +24,8 @@ struct ViewTable {
     int W[kMaxViews], H[kMaxViews], TX[kMaxViews], TY[kMaxViews];
     float fx[kMaxViews], fy[kMaxViews], cx[kMaxViews], cy[kMaxViews];
     float T[kMaxViews][12];          // rows 0..2 of world->camera
+    // clamp interval of (x/z, y/z) for the EWA Jacobian: the view widened by 15% per side
+    float jx_lo[kMaxViews], jx_hi[kMaxViews], jy_lo[kMaxViews], jy_hi[kMaxViews];
 };
 
 struct Params {
@@ -75,12 +77,58 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
-// Splat record staged in shared memory for the blend loops.  The conic is kept
-// pre-scaled: (qa, qb, qc) = (-A/2, -B, -C/2) * log2 e, so that
+// Error-free transformations (Dekker, Knuth; Ogita-Rump-Oishi compensated dot):
+// a*b = p + e and a+b = s + e exactly, with explicitly rounded operations so
+// the compiler cannot contract or reassociate them.
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// r0 x0 + r1 x1 + r2 x2 + t as an unevaluated sum hi + lo (compensated dot
+// product: as accurate as a twice-precision evaluation rounded at the end).
+__device__ __forceinline__ void dot3_dd(float r0, float r1, float r2, float x0, float x1, float x2, float t,
+                                        float &hi, float &lo) {
+    float p, s, h, e, q;
+    two_prod(r0, x0, p, s);
+    two_prod(r1, x1, h, e);
+    two_sum(p, h, p, q);
+    s = __fadd_rn(s, __fadd_rn(q, e));
+    two_prod(r2, x2, h, e);
+    two_sum(p, h, p, q);
+    s = __fadd_rn(s, __fadd_rn(q, e));
+    two_sum(p, t, p, q);
+    s = __fadd_rn(s, q);
+    two_sum(p, s, hi, lo);
+}
+
+// f (xh + xl) / (zh + zl) + c as an unevaluated sum hi + lo.
+__device__ __forceinline__ void proj_dd(float f, float xh, float xl, float zh, float zl, float c, float &hi,
+                                        float &lo) {
+    float q1 = __fdiv_rn(xh, zh);
+    float ph, pe;
+    two_prod(q1, zh, ph, pe);
+    float r = __fadd_rn(__fsub_rn(__fsub_rn(xh, ph), pe), __fsub_rn(xl, __fmul_rn(q1, zl)));
+    float q2 = __fdiv_rn(r, zh);
+    float h, e, s, e2;
+    two_prod(f, q1, h, e);
+    e = __fmaf_rn(f, q2, e);
+    two_sum(h, c, s, e2);
+    two_sum(s, __fadd_rn(e, e2), hi, lo);
+}
+
+// Splat record staged in shared memory for the blend loops.  The centre is the
+// unevaluated sum (u + ulo, v + vlo); the conic is kept pre-scaled:
+// (qa, qb, qc) = (-A/2, -B, -C/2) * log2 e, so that
 // power2 = qa dx^2 + qb dx dy + qc dy^2 = power * log2 e and G = 2^power2.
 struct SplatGeo {
-    float u, v, o, depth;
-    float qa, qb, qc, pad;
+    float u, v, ulo, vlo;
+    float qa, qb, qc, o;
 };
 
 // Evaluates one (pixel, splat) pair.  Both blend kernels call this one
@@ -94,8 +142,8 @@ struct PairEval {
 __device__ __forceinline__ PairEval eval_pair(const SplatGeo &s, float pxc, float pyc,
                                               float alpha_min, float alpha_max) {
     PairEval e;
-    e.dx = __fsub_rn(pxc, s.u);
-    e.dy = __fsub_rn(pyc, s.v);
+    e.dx = __fsub_rn(__fsub_rn(pxc, s.u), s.ulo);
+    e.dy = __fsub_rn(__fsub_rn(pyc, s.v), s.vlo);
     float t = __fmaf_rn(s.qa, e.dx, __fmul_rn(s.qb, e.dy));
     float p2 = __fmaf_rn(t, e.dx, __fmul_rn(__fmul_rn(s.qc, e.dy), e.dy));
     e.G = ex2_approx(p2);

@@ -58,15 +58,24 @@ __device__ __forceinline__ float sym(const Cov3 &c, int r, int k) {
 struct Geo {
     float p[3];
     Cov3 Sc;                     // R_cw Sigma R_cw^T
-    float j00, j02, j11, j12;    // perspective Jacobian at p
+    float j00, j02, j11, j12;    // perspective Jacobian at the clamped point
+    float tx, ty;                // clamped (x/z, y/z) where J is evaluated
+    bool in_x, in_y;             // whether x/z, y/z lie inside the clamp interval
     float a, b, c;               // Sigma2D + lowpass I
     float A, B, C;               // its inverse
-    float u, v;
+    float u, v;                  // f32 centre (u_lo, v_lo: remainders, forward only)
+    float ulo, vlo;
     bool ok;
 };
 
+// EWA projection of one Gaussian into view v.  J is evaluated at (x/z, y/z)
+// clamped to the view widened by 15% of its size per side (1.3 x the half field
+// of view for a centred principal point), which keeps splats whose centres fall
+// far outside the view from stretching with (x/z)^2; the centre is not clamped.
 __device__ __forceinline__ void project_geo(const float mu[3], const Shape &sh, const float R[9], const float t[3],
-                                            float fx, float fy, float cx, float cy, const Params &prm, Geo &o) {
+                                            const ViewTable &vt, int v, const Params &prm, Geo &o,
+                                            bool precise_centre = false) {
+    const float fx = vt.fx[v], fy = vt.fy[v], cx = vt.cx[v], cy = vt.cy[v];
     // p = R mu + t as an explicit fused chain; p.z is the sort key
 #pragma unroll
     for (int r = 0; r < 3; ++r)
@@ -87,16 +96,32 @@ __device__ __forceinline__ void project_geo(const float mu[3], const Shape &sh, 
         o.Sc.m[e] = RS[3 * r] * R[3 * k] + RS[3 * r + 1] * R[3 * k + 1] + RS[3 * r + 2] * R[3 * k + 2];
     }
     float iz = 1.f / o.p[2];
+    const float xz = o.p[0] * iz, yz = o.p[1] * iz;
+    o.in_x = xz >= vt.jx_lo[v] && xz <= vt.jx_hi[v];
+    o.in_y = yz >= vt.jy_lo[v] && yz <= vt.jy_hi[v];
+    o.tx = fminf(fmaxf(xz, vt.jx_lo[v]), vt.jx_hi[v]);
+    o.ty = fminf(fmaxf(yz, vt.jy_lo[v]), vt.jy_hi[v]);
     o.j00 = fx * iz;
     o.j11 = fy * iz;
-    o.j02 = -fx * o.p[0] * iz * iz;
-    o.j12 = -fy * o.p[1] * iz * iz;
+    o.j02 = -fx * o.tx * iz;
+    o.j12 = -fy * o.ty * iz;
     const float *S = o.Sc.m;
     o.a = o.j00 * o.j00 * S[0] + 2.f * o.j00 * o.j02 * S[2] + o.j02 * o.j02 * S[5] + prm.lowpass;
     o.b = o.j00 * o.j11 * S[1] + o.j00 * o.j12 * S[2] + o.j02 * o.j11 * S[4] + o.j02 * o.j12 * S[5];
     o.c = o.j11 * o.j11 * S[3] + 2.f * o.j11 * o.j12 * S[4] + o.j12 * o.j12 * S[5] + prm.lowpass;
-    o.u = fx * o.p[0] * iz + cx;
-    o.v = fy * o.p[1] * iz + cy;
+    if (precise_centre) {
+        // p and the pinhole division in compensated arithmetic: u, v to ~1e-10 px
+        float xh, xl, yh, yl, zh, zl;
+        dot3_dd(R[0], R[1], R[2], mu[0], mu[1], mu[2], t[0], xh, xl);
+        dot3_dd(R[3], R[4], R[5], mu[0], mu[1], mu[2], t[1], yh, yl);
+        dot3_dd(R[6], R[7], R[8], mu[0], mu[1], mu[2], t[2], zh, zl);
+        proj_dd(fx, xh, xl, zh, zl, cx, o.u, o.ulo);
+        proj_dd(fy, yh, yl, zh, zl, cy, o.v, o.vlo);
+    } else {
+        o.u = fx * o.p[0] * iz + cx;
+        o.v = fy * o.p[1] * iz + cy;
+        o.ulo = o.vlo = 0.f;
+    }
     float det = o.a * o.c - o.b * o.b;
     if (det > 1e-2f * o.a * o.c && isfinite(det)) {
         float id = 1.f / det;
@@ -114,7 +139,7 @@ __device__ __forceinline__ void project_geo(const float mu[3], const Shape &sh, 
 __global__ void __launch_bounds__(256) project_fwd_kernel(ViewTable vt, Params prm, int64_t n, const float *means,
                                                           const float *quats, const float *log_scales,
                                                           const float *logits, const float *pose_dev, float4 *uvdo,
-                                                          float4 *conic, int32_t *touched) {
+                                                          float2 *uv_lo, float4 *conic, int32_t *touched) {
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int v = blockIdx.y;
     if (g >= n) return;
@@ -126,8 +151,9 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(ViewTable vt, Params p
     float R[9], t[3];
     load_pose(vt, pose_dev, v, R, t);
     Geo ge;
-    project_geo(mu, sh, R, t, vt.fx[v], vt.fy[v], vt.cx[v], vt.cy[v], prm, ge);
+    project_geo(mu, sh, R, t, vt, v, prm, ge, true);
     float4 rec = make_float4(0.f, 0.f, ge.p[2], o);
+    float2 lo = make_float2(0.f, 0.f);
     float4 cn = make_float4(0.f, 0.f, 0.f, 0.f);
     int tt = 0;
     if (ge.ok) {
@@ -143,9 +169,11 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(ViewTable vt, Params p
         }
         rec.x = ge.u;
         rec.y = ge.v;
+        lo = make_float2(ge.ulo, ge.vlo);
         cn = make_float4(ge.A, ge.B, ge.C, (float)r);
     }
     uvdo[item] = rec;
+    uv_lo[item] = lo;
     conic[item] = cn;
     touched[item] = tt;
 }
@@ -176,7 +204,7 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(ViewTable vt, Params p
             load_pose(vt, pose_dev, v, R, t);
             float fx = vt.fx[v], fy = vt.fy[v];
             Geo ge;
-            project_geo(mu, sh, R, t, fx, fy, vt.cx[v], vt.cy[v], prm, ge);
+            project_geo(mu, sh, R, t, vt, v, prm, ge);
             if (ge.ok) {
                 dop += a0.z;
                 // conic -> Sigma2D: G2 = -conic Ghat conic, Ghat = [[dA, dB/2], [dB/2, dC]]
@@ -203,11 +231,15 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(ViewTable vt, Params p
                 float dJ12 = 2.f * (g01 * JS0[2] + g11 * JS1[2]);
                 // camera-frame centre
                 float x = ge.p[0], y = ge.p[1], z = ge.p[2];
-                float iz = 1.f / z, iz2 = iz * iz, iz3 = iz2 * iz;
-                float gp0 = a0.x * fx * iz + dJ02 * (-fx * iz2);
-                float gp1 = a0.y * fy * iz + dJ12 * (-fy * iz2);
+                float iz = 1.f / z, iz2 = iz * iz;
+                // J02 = -fx t_x / z with t_x = clamp(x / z): dt_x/dx = 1/z, dt_x/dz = -x/z^2 inside, 0 outside
+                const float dtx_dx = ge.in_x ? iz : 0.f, dtx_dz = ge.in_x ? -x * iz2 : 0.f;
+                const float dty_dy = ge.in_y ? iz : 0.f, dty_dz = ge.in_y ? -y * iz2 : 0.f;
+                float gp0 = a0.x * fx * iz + dJ02 * (-fx * iz) * dtx_dx;
+                float gp1 = a0.y * fy * iz + dJ12 * (-fy * iz) * dty_dy;
                 float gp2 = -a0.x * fx * x * iz2 - a0.y * fy * y * iz2 + a0.w + dJ00 * (-fx * iz2) +
-                            dJ02 * (2.f * fx * x * iz3) + dJ11 * (-fy * iz2) + dJ12 * (2.f * fy * y * iz3);
+                            dJ02 * (-fx * dtx_dz * iz + fx * ge.tx * iz2) + dJ11 * (-fy * iz2) +
+                            dJ12 * (-fy * dty_dz * iz + fy * ge.ty * iz2);
 #pragma unroll
                 for (int k = 0; k < 3; ++k) gmu[k] += R[k] * gp0 + R[3 + k] * gp1 + R[6 + k] * gp2;
                 // Sigma gradient: R^T Gc R
@@ -292,16 +324,17 @@ extern "C" gs_status gs_project(const gs_gaussians *g, const gs_camera *cams, in
     if (!make_view_table(cams, n_views, g->n, &vt) || !make_params(p, &prm)) return GS_ERR_ARG;
     if (g->n * n_views >= ((int64_t)1 << 30)) return GS_ERR_ARG;
     if (g->n == 0) return GS_OK;
-    if (!g->means || !g->quats || !g->log_scales || !g->opacity_logits || !out->uvdo || !out->conic ||
-        !out->tiles_touched)
+    if (!g->means || !g->quats || !g->log_scales || !g->opacity_logits || !out->uvdo || !out->uv_lo ||
+        !out->conic || !out->tiles_touched)
         return GS_ERR_ARG;
     if ((reinterpret_cast<uintptr_t>(g->quats) | reinterpret_cast<uintptr_t>(out->uvdo) |
-         reinterpret_cast<uintptr_t>(out->conic)) & 15)
+         reinterpret_cast<uintptr_t>(out->conic)) & 15 || (reinterpret_cast<uintptr_t>(out->uv_lo) & 7))
         return GS_ERR_ARG;
     dim3 grid(ceil_div(g->n, 256), n_views);
     project_fwd_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(
         vt, prm, g->n, g->means, g->quats, g->log_scales, g->opacity_logits, pose_dev,
-        reinterpret_cast<float4 *>(out->uvdo), reinterpret_cast<float4 *>(out->conic), out->tiles_touched);
+        reinterpret_cast<float4 *>(out->uvdo), reinterpret_cast<float2 *>(out->uv_lo),
+        reinterpret_cast<float4 *>(out->conic), out->tiles_touched);
     return last_launch();
 }
 

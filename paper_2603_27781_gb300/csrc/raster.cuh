@@ -11,9 +11,10 @@ template <> struct Store<float> { static constexpr int code = GS_F32; };
 template <> struct Store<__half> { static constexpr int code = GS_F16; };
 template <> struct Store<__nv_bfloat16> { static constexpr int code = GS_BF16; };
 
+// Colour of Gaussian g with the splat depth in the fourth lane (both are blended values).
 template <typename T>
-__device__ __forceinline__ float4 load_rgb(const T *rgb, int64_t g) {
-    return make_float4(to_f32(rgb[3 * g]), to_f32(rgb[3 * g + 1]), to_f32(rgb[3 * g + 2]), 0.f);
+__device__ __forceinline__ float4 load_rgbd(const T *rgb, int64_t g, float depth) {
+    return make_float4(to_f32(rgb[3 * g]), to_f32(rgb[3 * g + 1]), to_f32(rgb[3 * g + 2]), depth);
 }
 
 // Loads 4 consecutive feature values (16-byte aligned for f32, 8 for bf16).
@@ -28,16 +29,16 @@ template <> __device__ __forceinline__ float4 load_feat4<__nv_bfloat16>(const __
     return make_float4(fa.x, fa.y, fb.x, fb.y);
 }
 
-__device__ __forceinline__ SplatGeo make_geo(float4 a, float4 c) {
+__device__ __forceinline__ SplatGeo make_geo(float4 a, float2 lo, float4 c) {
     SplatGeo s;
     s.u = a.x;
     s.v = a.y;
-    s.depth = a.z;
+    s.ulo = lo.x;
+    s.vlo = lo.y;
     s.o = a.w;
     s.qa = -0.5f * kLog2e * c.x;
     s.qb = -kLog2e * c.y;
     s.qc = -0.5f * kLog2e * c.z;
-    s.pad = 0.f;
     return s;
 }
 

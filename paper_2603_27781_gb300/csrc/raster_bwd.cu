@@ -55,7 +55,8 @@ struct Layout {
 
 template <int D, bool MAP, typename RT, typename FT>
 __global__ void __launch_bounds__(kTilePix) raster_bwd_kernel(
-    ViewTable vt, Params prm, const float4 *__restrict__ uvdo, const float4 *__restrict__ conic,
+    ViewTable vt, Params prm, const float4 *__restrict__ uvdo, const float2 *__restrict__ uv_lo,
+    const float4 *__restrict__ conic,
     const RT *__restrict__ rgb, const FT *__restrict__ feat, const uint32_t *__restrict__ vals,
     const uint32_t *__restrict__ ranges, int64_t P, const float *__restrict__ T_final,
     const int32_t *__restrict__ n_contrib, const float *__restrict__ g_rgb, const float *__restrict__ g_depth,
@@ -120,8 +121,9 @@ __global__ void __launch_bounds__(kTilePix) raster_bwd_kernel(
         if (tid < cnt) {
             uint32_t item = vals[start + b_start + tid];
             int64_t g = (int64_t)item - voff;
-            s_geo[tid] = make_geo(uvdo[item], conic[item]);
-            s_rgb[tid] = load_rgb(rgb, g);
+            const float4 a = uvdo[item];
+            s_geo[tid] = make_geo(a, uv_lo[item], conic[item]);
+            s_rgb[tid] = load_rgbd(rgb, g, a.z);
 #pragma unroll
             for (int q = 0; q < D4; ++q) s_feat[tid * D4 + q] = load_feat4(feat, g * D + 4 * q);
         }
@@ -145,7 +147,7 @@ __global__ void __launch_bounds__(kTilePix) raster_bwd_kernel(
                 const float w = a * Tb;
                 float4 c = s_rgb[k];
                 float x[NCH];
-                x[0] = c.x; x[1] = c.y; x[2] = c.z; x[3] = s.depth; x[4] = 1.f;
+                x[0] = c.x; x[1] = c.y; x[2] = c.z; x[3] = c.w; x[4] = 1.f;
 #pragma unroll
                 for (int q = 0; q < D4; ++q) {
                     float4 f = s_feat[k * D4 + q];
@@ -238,8 +240,9 @@ gs_status launch(const ViewTable &vt, const Params &prm, const gs_gaussians *g, 
     int tiles = vt.tile_off[vt.n_views];
     int64_t P = vt.pix_off[vt.n_views];
     raster_bwd_kernel<D, MAP, RT, FT><<<tiles, kTilePix, 0, st>>>(
-        vt, prm, reinterpret_cast<const float4 *>(proj->uvdo), reinterpret_cast<const float4 *>(proj->conic),
-        static_cast<const RT *>(g->rgb), static_cast<const FT *>(g->feat), bins->vals, bins->ranges, P, fwd->T_final,
+        vt, prm, reinterpret_cast<const float4 *>(proj->uvdo), reinterpret_cast<const float2 *>(proj->uv_lo),
+        reinterpret_cast<const float4 *>(proj->conic), static_cast<const RT *>(g->rgb),
+        static_cast<const FT *>(g->feat), bins->vals, bins->ranges, P, fwd->T_final,
         fwd->n_contrib, dL->rgb, dL->depth, dL->sil, dL->feat, acc_uvod, acc_conic, acc_rgb, d_feat);
     return last_launch();
 }
@@ -283,7 +286,7 @@ extern "C" gs_status gs_render_bwd(const gs_gaussians *g, const gs_projected *pr
     if (g->n == 0) return GS_OK;
     if (!storage_ok(g)) return GS_ERR_UNSUPPORTED;
     if (!sg->uvod || !sg->conic || (map && (!sg->rgb || (g->feat_dim && !d_feat)))) return GS_ERR_ARG;
-    if (!proj->uvdo || !proj->conic || !bins->vals || !bins->ranges || !fwd->T_final || !fwd->n_contrib ||
+    if (!proj->uvdo || !proj->uv_lo || !proj->conic || !bins->vals || !bins->ranges || !fwd->T_final || !fwd->n_contrib ||
         !dL->rgb || !dL->depth || (g->feat_dim && !dL->feat))
         return GS_ERR_ARG;
     if ((reinterpret_cast<uintptr_t>(sg->uvod) | reinterpret_cast<uintptr_t>(sg->conic) |

@@ -12,6 +12,7 @@ constexpr int kBatch = 256;
 
 template <int D, typename RT, typename FT>
 __global__ void __launch_bounds__(kTilePix) raster_fwd_kernel(ViewTable vt, Params prm, const float4 *__restrict__ uvdo,
+                                                              const float2 *__restrict__ uv_lo,
                                                               const float4 *__restrict__ conic,
                                                               const RT *__restrict__ rgb, const FT *__restrict__ feat,
                                                               const uint32_t *__restrict__ vals,
@@ -48,8 +49,9 @@ __global__ void __launch_bounds__(kTilePix) raster_fwd_kernel(ViewTable vt, Para
         if (j < end) {
             uint32_t item = vals[j];
             int64_t g = (int64_t)item - voff;
-            s_geo[tid] = make_geo(uvdo[item], conic[item]);
-            s_rgb[tid] = load_rgb(rgb, g);
+            const float4 a = uvdo[item];
+            s_geo[tid] = make_geo(a, uv_lo[item], conic[item]);
+            s_rgb[tid] = load_rgbd(rgb, g, a.z);
 #pragma unroll
             for (int q = 0; q < D4; ++q) s_feat[tid * D4 + q] = load_feat4(feat, g * D + 4 * q);
         }
@@ -69,7 +71,7 @@ __global__ void __launch_bounds__(kTilePix) raster_fwd_kernel(ViewTable vt, Para
             acc_r = fmaf(w, c.x, acc_r);
             acc_g = fmaf(w, c.y, acc_g);
             acc_b = fmaf(w, c.z, acc_b);
-            acc_d = fmaf(w, s.depth, acc_d);
+            acc_d = fmaf(w, c.w, acc_d);
             acc_s += w;
 #pragma unroll
             for (int q = 0; q < D4; ++q) {
@@ -104,8 +106,9 @@ gs_status launch(const ViewTable &vt, const Params &prm, const gs_gaussians *g, 
     int tiles = vt.tile_off[vt.n_views];
     int64_t P = vt.pix_off[vt.n_views];
     raster_fwd_kernel<D, RT, FT><<<tiles, kTilePix, 0, st>>>(
-        vt, prm, reinterpret_cast<const float4 *>(proj->uvdo), reinterpret_cast<const float4 *>(proj->conic),
-        static_cast<const RT *>(g->rgb), static_cast<const FT *>(g->feat), bins->vals, bins->ranges, P, out->rgb,
+        vt, prm, reinterpret_cast<const float4 *>(proj->uvdo), reinterpret_cast<const float2 *>(proj->uv_lo),
+        reinterpret_cast<const float4 *>(proj->conic), static_cast<const RT *>(g->rgb),
+        static_cast<const FT *>(g->feat), bins->vals, bins->ranges, P, out->rgb,
         out->depth, out->sil, out->feat, out->T_final, out->n_contrib, out->n_blended);
     return last_launch();
 }
@@ -156,7 +159,7 @@ extern "C" gs_status gs_render_fwd(const gs_gaussians *g, const gs_projected *pr
     if (!out->rgb || !out->depth || !out->sil || !out->T_final || !out->n_contrib || (g->feat_dim && !out->feat) ||
         !bins->ranges)
         return GS_ERR_ARG;
-    if (g->n > 0 && (!storage_ok(g) || !bins->vals || !proj->uvdo || !proj->conic)) {
+    if (g->n > 0 && (!storage_ok(g) || !bins->vals || !proj->uvdo || !proj->uv_lo || !proj->conic)) {
         return storage_ok(g) ? GS_ERR_ARG : GS_ERR_UNSUPPORTED;
     }
     if (g->feat_dim && (reinterpret_cast<uintptr_t>(g->feat) & 15)) return GS_ERR_ARG;

@@ -122,6 +122,7 @@ class Renderer:
         V, dev = self.n_views, self.device
         f32, i32 = torch.float32, torch.int32
         self.uvdo = torch.zeros(V * n, 4, dtype=f32, device=dev)
+        self.uv_lo = torch.zeros(V * n, 2, dtype=f32, device=dev)
         self.conic = torch.zeros(V * n, 4, dtype=f32, device=dev)
         self.touched = torch.zeros(V * n, dtype=i32, device=dev)
         self.keys = torch.zeros(max(capacity, 1), dtype=torch.int64, device=dev)
@@ -181,7 +182,7 @@ class Renderer:
 
     # -------------------------------------------------------------- C ABI
     def projected_c(self):
-        return L.gs_projected(_p(self.uvdo), _p(self.conic), _p(self.touched))
+        return L.gs_projected(_p(self.uvdo), _p(self.uv_lo), _p(self.conic), _p(self.touched))
 
     def binning_c(self, want_keys=False):
         return L.gs_binning(self.capacity, _p(self.keys) if want_keys else None, _p(self.vals), _p(self.ranges),

@@ -224,10 +224,15 @@ def perturb_pose(T_cw: np.ndarray, deg: float = 2.0, metres: float = 0.05,
     return D @ T_cw
 
 
-def camera(width, height, fx, fy=None, cx=None, cy=None, T_cw=None) -> Camera:
-    return Camera(int(width), int(height), float(fx), float(fx if fy is None else fy),
-                  float(width / 2 if cx is None else cx), float(height / 2 if cy is None else cy),
-                  np.eye(4) if T_cw is None else np.asarray(T_cw, float))
+def camera(width, height, fx, fy=None, cx=None, cy=None, T_cw=None, round_f32=True) -> Camera:
+    """Pinhole camera.  By default intrinsics and pose are rounded to float32 values (the
+    C ABI's camera is float32), so every consumer sees exactly the same camera."""
+    f = (lambda x: float(np.float32(x))) if round_f32 else float
+    T = np.eye(4) if T_cw is None else np.asarray(T_cw, float)
+    if round_f32:
+        T = T.astype(np.float32).astype(np.float64)
+    return Camera(int(width), int(height), f(fx), f(fx if fy is None else fy),
+                  f(width / 2 if cx is None else cx), f(height / 2 if cy is None else cy), T)
 
 
 def room_camera(width=1200, height=680, fx=600.0, room: Room | None = None,

@@ -16,6 +16,10 @@ TOL_GRAD = 1e-3
 # A pixel whose nearest threshold decision (alpha_min, alpha_max, T_min) is within this
 # relative distance in the oracle is excluded (FP32 rounding may decide it differently).
 MARGIN = 1e-4
+# A pixel whose blend amplifies relative rounding of the 2D covariances by more than this
+# (oracle "sens": blend-weighted |A|dx^2 + 2|B dx dy| + |C|dy^2, halved) is excluded: at
+# f32's ~1e-7 relative rounding of Sigma2D its value is not determined to 1e-5.
+SENS_MAX = 100.0
 
 
 def params_pair(**kw):
@@ -48,10 +52,13 @@ def gpu_forward(gs, cams, prm, capacity=None, want_keys=True, rgb_dtype=torch.fl
 
 
 def gpu_projection(r):
+    """uv: the f32 centre the binning uses; uv_full: f32 centre plus its low part."""
     uvdo = r.uvdo.cpu().numpy()
     conic = r.conic.cpu().numpy()
-    return dict(uv=uvdo[:, :2].astype(np.float64), depth=uvdo[:, 2], opacity=uvdo[:, 3], conic=conic[:, :3],
-                radius=conic[:, 3].astype(np.int32), touched=r.touched.cpu().numpy())
+    lo = r.uv_lo.cpu().numpy().astype(np.float64)
+    return dict(uv=uvdo[:, :2].astype(np.float64), uv_full=uvdo[:, :2].astype(np.float64) + lo, depth=uvdo[:, 2],
+                opacity=uvdo[:, 3], conic=conic[:, :3], radius=conic[:, 3].astype(np.int32),
+                touched=r.touched.cpu().numpy())
 
 
 def gpu_binning(r):
@@ -61,9 +68,9 @@ def gpu_binning(r):
 
 
 def excluded_pixels(cam, orc_proj, gpu_proj, orc_img, tile=16):
-    """Pixels where FP32 and FP64 may legitimately take a different integer decision:
-    tiles covered by a splat whose rectangle differs between the two projections, and
-    pixels whose nearest threshold decision lies within MARGIN (relative) in the oracle."""
+    """Pixels where FP32 and FP64 may legitimately differ: tiles covered by a splat whose
+    rectangle differs between the two projections, pixels whose nearest threshold decision
+    lies within MARGIN (relative) in the oracle, and ill-conditioned pixels (SENS_MAX)."""
     W, H = cam.width, cam.height
     g_rect, _ = oracle.rects(gpu_proj["uv"], gpu_proj["radius"], W, H, tile)
     diff = np.nonzero(np.any(g_rect != orc_proj["rect"], axis=1))[0]
@@ -75,6 +82,7 @@ def excluded_pixels(cam, orc_proj, gpu_proj, orc_img, tile=16):
             bad_tiles[rc[1]:rc[3], rc[0]:rc[2]] = True
     mask = np.repeat(np.repeat(bad_tiles, tile, 0), tile, 1)[:H, :W]
     mask |= orc_img["margin"] < MARGIN
+    mask |= orc_img["sens"] > SENS_MAX
     return mask, len(diff)
 
 
@@ -87,9 +95,16 @@ def assert_forward_close(gimg, oimg, excl, D):
             assert err.max() <= TOL_ABS, (k, float(err.max()))
     err = np.abs(gimg["sil"] - oimg["sil"])[keep]
     assert err.size == 0 or err.max() <= TOL_ABS, ("sil", float(err.max()))
-    d_o = oimg["depth"][keep]
-    err = np.abs(gimg["depth"][keep] - d_o) / np.maximum(np.abs(d_o), 1e-3)
-    assert err.size == 0 or err.max() <= TOL_DEPTH_REL, ("depth", float(err.max()))
+    # depth: relative 1e-5 image-wise (max error over max depth, as for the gradient groups) and
+    # per pixel wherever the pixel is covered (sil >= 0.5); a faint pixel's depth is a small sum
+    # of weights whose f32 rounding is bounded by the silhouette tolerance instead
+    d_o, d_g = oimg["depth"][keep], gimg["depth"][keep]
+    if d_o.size:
+        assert np.abs(d_g - d_o).max() <= TOL_DEPTH_REL * np.abs(oimg["depth"]).max(), ("depth", "image")
+        cov = oimg["sil"][keep] >= 0.5
+        if cov.any():
+            err = np.abs(d_g[cov] - d_o[cov]) / np.abs(d_o[cov])
+            assert err.max() <= TOL_DEPTH_REL, ("depth", float(err.max()))
     np.testing.assert_array_equal(gimg["n_contrib"][keep], oimg["n_contrib"][keep])
 
 

@@ -31,6 +31,11 @@ def field(means, quats, log_scales, logits, rgb, feat):
     return synth.Gaussians(f(means), f(quats), f(log_scales), f(logits), f(rgb), f(feat))
 
 
+def camera(*args, **kw):
+    """Cameras of the pins keep their exact float64 values (finite differences perturb them)."""
+    return synth.camera(*args, round_f32=False, **kw)
+
+
 def sigmoid(x):
     return 1.0 / (1.0 + math.exp(-x))
 
@@ -39,7 +44,7 @@ def sigmoid(x):
 @pytest.mark.parametrize("rot90", [False, True])
 def test_single_gaussian_closed_form(rot90):
     """Eq. 2-7 for one Gaussian on the optical axis: Sigma2D = diag((f s_x / z)^2, (f s_y / z)^2)."""
-    cam = synth.camera(33, 33, 40.0, cx=16.5, cy=16.5)
+    cam = camera(33, 33, 40.0, cx=16.5, cy=16.5)
     q = [math.cos(math.pi / 4), 0, 0, math.sin(math.pi / 4)] if rot90 else [1, 0, 0, 0]
     s = np.array([0.1, 0.05, 0.2])
     logit = 0.3
@@ -75,14 +80,14 @@ def test_pinhole_centre_and_depth():
     """The projected centre is K [R|t] mu (homogeneous pinhole, supp. B.1) and d = camera z."""
     g = synth.rng(11)
     T = synth.look_pose((0.3, -0.2, 0.1), (0.2, 1.0, 0.3))
-    cam = synth.camera(200, 150, 180.0, 170.0, 97.0, 71.0, T_cw=T)
+    cam = camera(200, 150, 180.0, 170.0, 97.0, 71.0, T_cw=T)
     n = 50
     mu = T[:3, :3].T @ (np.stack([g.uniform(-1, 1, n), g.uniform(-1, 1, n), g.uniform(1, 4, n)]) - T[:3, 3:4])
     gs = field(mu.T, np.tile([1.0, 0, 0, 0], (n, 1)), np.full((n, 3), -3.0), np.zeros(n),
                np.zeros((n, 3)), np.zeros((n, 1)))
     proj = oracle.project(gs, cam, Params())
-    K = np.array([[180.0, 0, 97.0], [0, 170.0, 71.0], [0, 0, 1]])
-    h = K @ T[:3, :] @ np.vstack([mu, np.ones(n)])
+    K = np.array([[cam.fx, 0, cam.cx], [0, cam.fy, cam.cy], [0, 0, 1]])
+    h = K @ cam.T_cw[:3, :] @ np.vstack([mu, np.ones(n)])
     np.testing.assert_allclose(proj["uv"], (h[:2] / h[2]).T, rtol=1e-12)
     np.testing.assert_allclose(proj["depth"], h[2], rtol=1e-12)
     np.testing.assert_allclose(proj["depth_key"], h[2].astype(np.float32), rtol=2e-7)
@@ -92,7 +97,7 @@ def test_ewa_covariance_matches_monte_carlo():
     """Eq. 3 is the linearisation of the pinhole map: compare with sampled projections."""
     g = synth.rng(12)
     T = synth.look_pose((0.0, 0.0, 0.0), (0.3, 1.0, -0.2))
-    cam = synth.camera(640, 480, 500.0, 520.0, 320.0, 240.0, T_cw=T)
+    cam = camera(640, 480, 500.0, 520.0, 320.0, 240.0, T_cw=T)
     q_wxyz = g.standard_normal(4)
     q_wxyz /= np.linalg.norm(q_wxyz)
     s = np.array([0.02, 0.008, 0.014])
@@ -118,7 +123,7 @@ def test_ewa_covariance_matches_monte_carlo():
 def test_joint_rigid_motion_leaves_image_unchanged():
     """Moving the world and the camera by the same rigid motion gives the same render."""
     gs = synth.box_field(60, 4, seed=21)
-    cam = synth.camera(48, 40, 50.0, cx=24, cy=20)
+    cam = camera(48, 40, 50.0, cx=24, cy=20)
     base = oracle.forward(gs, cam, EXACT)[2]
     Q = Rotation.from_rotvec([0.3, -0.5, 0.8]).as_matrix()
     shift = np.array([0.4, -1.0, 2.0])
@@ -130,7 +135,7 @@ def test_joint_rigid_motion_leaves_image_unchanged():
     moved.quats = np.c_[prod[:, 3:], prod[:, :3]]
     M = np.eye(4)
     M[:3, :3], M[:3, 3] = Q, shift
-    cam2 = synth.camera(48, 40, 50.0, cx=24, cy=20, T_cw=np.linalg.inv(M))
+    cam2 = camera(48, 40, 50.0, cx=24, cy=20, T_cw=np.linalg.inv(M))
     img2 = oracle.forward(moved, cam2, EXACT)[2]
     for k in ("rgb", "depth", "sil", "feat"):
         np.testing.assert_allclose(img2[k], base[k], atol=1e-9)
@@ -138,7 +143,7 @@ def test_joint_rigid_motion_leaves_image_unchanged():
 
 def test_two_gaussians_front_to_back():
     """Eq. 4: c = a1 c1 + a2 (1 - a1) c2 with the nearer splat first, whatever the input order."""
-    cam = synth.camera(17, 17, 30.0, cx=8.5, cy=8.5)
+    cam = camera(17, 17, 30.0, cx=8.5, cy=8.5)
     c1, c2 = [0.9, 0.1, 0.2], [0.1, 0.8, 0.3]
     l1, l2 = 0.7, -0.2
     a1, a2 = sigmoid(l1), sigmoid(l2)
@@ -164,7 +169,7 @@ def test_two_gaussians_front_to_back():
 def test_early_stop_at_min_transmittance():
     """A splat that would take T below T_min ends the pixel's blend: later splats are not
     blended even when their own alpha would keep T above T_min."""
-    cam = synth.camera(9, 9, 20.0, cx=4.5, cy=4.5)
+    cam = camera(9, 9, 20.0, cx=4.5, cy=4.5)
     alphas = [0.95, 0.95, 0.95, 0.95, 0.1]
     logits = [math.log(a / (1 - a)) for a in alphas]
     cols = synth.rng(70).random((5, 3))
@@ -183,7 +188,7 @@ def test_early_stop_at_min_transmittance():
 
 
 def test_empty_and_fully_culled_maps_render_background():
-    cam = synth.camera(40, 24, 30.0)
+    cam = camera(40, 24, 30.0)
     prm = Params(bg=(0.1, 0.2, 0.3))
     for gs in (field(np.zeros((0, 3)), np.zeros((0, 4)), np.zeros((0, 3)), np.zeros(0), np.zeros((0, 3)),
                      np.zeros((0, 8))),
@@ -205,7 +210,7 @@ def test_empty_and_fully_culled_maps_render_background():
 
 def test_silhouette_plus_transmittance_is_one():
     gs = synth.box_field(500, 8, seed=5)
-    cam = synth.camera(64, 48, 60.0, cx=32, cy=24)
+    cam = camera(64, 48, 60.0, cx=32, cy=24)
     img = oracle.forward(gs, cam, Params())[2]
     np.testing.assert_allclose(img["sil"] + img["T"], 1.0, atol=1e-12)
     assert img["sil"].max() > 0.9
@@ -213,7 +218,7 @@ def test_silhouette_plus_transmittance_is_one():
 
 def test_input_order_invariance():
     gs = synth.box_field(300, 8, seed=6)
-    cam = synth.camera(64, 48, 60.0, cx=32, cy=24)
+    cam = camera(64, 48, 60.0, cx=32, cy=24)
     base = oracle.forward(gs, cam, Params())[2]
     perm = synth.rng(9).permutation(gs.n)
     img = oracle.forward(gs.subset(perm), cam, Params())[2]
@@ -275,7 +280,7 @@ def test_tiled_equals_brute_force(dense):
     gs.log_scales[:] += 0.8 if dense else -0.5
     if dense:
         gs.opacity_logits[:] += 2.0
-    cam = synth.camera(32, 32, 60.0 if dense else 30.0, cx=16, cy=16)
+    cam = camera(32, 32, 60.0 if dense else 30.0, cx=16, cy=16)
     prm = Params()
     img = oracle.forward(gs, cam, prm)[2]
     bf = brute_force_render(gs, cam, prm)
@@ -289,7 +294,7 @@ def test_tiled_equals_brute_force(dense):
 def test_exact_mode_equals_literal_eq4_sum():
     """With no thresholds and a covering radius the tiled blend is the literal sum of Eq. 4."""
     gs = synth.box_field(30, 2, seed=8)
-    cam = synth.camera(32, 24, 30.0, cx=16, cy=12)
+    cam = camera(32, 24, 30.0, cx=16, cy=12)
     img = oracle.forward(gs, cam, EXACT)[2]
     bf = brute_force_render(gs, cam, EXACT, use_tiles=False)
     for k in ("rgb", "depth", "sil", "feat"):
@@ -320,8 +325,8 @@ def test_tile_rect_matches_interval_intersection():
 
 def test_bin_sort_matches_per_tile_brute_force():
     gs = synth.box_field(120, 2, seed=14)
-    cams = [synth.camera(64, 48, 60.0, cx=32, cy=24),
-            synth.camera(40, 40, 50.0, T_cw=synth.look_pose((0.2, 0, 0), (0.05, 0.0, 1.0), up=(0, -1, 0)))]
+    cams = [camera(64, 48, 60.0, cx=32, cy=24),
+            camera(40, 40, 50.0, T_cw=synth.look_pose((0.2, 0, 0), (0.05, 0.0, 1.0), up=(0, -1, 0)))]
     projs = [oracle.project(gs, c, Params()) for c in cams]
     rect = np.concatenate([p["rect"] for p in projs])
     dk = np.concatenate([p["depth_key"] for p in projs])
@@ -354,7 +359,7 @@ def _fd_setup(seed, prm):
     gs = synth.Gaussians(*(a.astype(np.float64) for a in gs.arrays()))
     gs.log_scales += 0.6
     T = synth.look_pose((0.1, -0.05, -0.2), (0.05, 0.03, 1.0), up=(0, -1, 0))
-    cam = synth.camera(24, 20, 22.0, cx=11.7, cy=10.2, T_cw=T)
+    cam = camera(24, 20, 22.0, cx=11.7, cy=10.2, T_cw=T)
     g = synth.rng(seed + 100)
     H, W = cam.height, cam.width
     gimg = dict(rgb=g.standard_normal((3, H, W)), depth=g.standard_normal((H, W)),
@@ -391,7 +396,7 @@ def _check_fd(gs, cam, prm, gimg, h, rtol):
         e[k] = h
         vals = []
         for sgn in (1, -1):
-            c2 = synth.camera(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy,
+            c2 = camera(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy,
                               T_cw=_se3_exp(sgn * e) @ cam.T_cw)
             vals.append(_render_functional(gs, c2, prm, gimg))
         fd = (vals[0] - vals[1]) / (2 * h)
@@ -413,6 +418,32 @@ def test_backward_matches_finite_differences_with_thresholds():
     img = oracle.forward(gs, cam, prm)[2]
     assert img["margin"].min() > 1e-4
     _check_fd(gs, cam, prm, gimg, 1e-7, 1e-5)
+
+
+def test_backward_matches_finite_differences_with_clamped_jacobian():
+    """Gaussians whose centres lie beyond the Jacobian clamp (off to the side of the view)
+    still reach it with their tails: their gradients follow the clamped J."""
+    prm = Params(alpha_min=0.0, alpha_max=1.0, T_min=0.0, lowpass=0.3, radius_sigma=40.0)
+    gs, cam, gimg = _fd_setup(34, prm)
+    gs.means[:4, 0] = gs.means[:4, 2] * np.array([1.1, -1.2, 1.05, -1.3])   # x/z far outside 0.65 W/fx
+    gs.log_scales[:4] += 1.0
+    proj = oracle.project(gs, cam, prm)
+    tx = (gs.means[:4] @ cam.T_cw[:3, :3].T + cam.T_cw[:3, 3])
+    assert (np.abs(tx[:, 0] / tx[:, 2]) > 0.65 * cam.width / cam.fx + 0.1).all()
+    assert (proj["radius"][:4] > 0).all()
+    _check_fd(gs, cam, prm, gimg, 1e-6, 1e-6)
+
+
+def test_jacobian_clamp_bounds_off_view_footprints():
+    """Eq. 3 with J at the clamped point: a Gaussian far to the side keeps a footprint like
+    one at the clamp boundary instead of stretching with (x/z)^2."""
+    cam = camera(64, 48, 40.0, cx=32, cy=24)
+    s = np.log(np.array([0.05, 0.05, 0.05]))
+    at_edge = field([[0.65 * 64 / 40 * 1.0, 0, 1.0]], [[1, 0, 0, 0]], [s], [0.0], [[0, 0, 0]], [[0.0]])
+    far = field([[8.0, 0, 1.0]], [[1, 0, 0, 0]], [s], [0.0], [[0, 0, 0]], [[0.0]])
+    ce = oracle.project(at_edge, cam, Params(lowpass=0.0))["cov2d"][0]
+    cf = oracle.project(far, cam, Params(lowpass=0.0))["cov2d"][0]
+    np.testing.assert_allclose(cf, ce, rtol=1e-12)
 
 
 def test_pose_translation_gradient_is_rotated_mean_gradient_sum():
