@@ -45,7 +45,18 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    return ap.parse_args()
+    # smaller scenes for profiling captures only (the benchmark line is the default workload)
+    ap.add_argument("--n", type=int, default=None)
+    ap.add_argument("--width", type=int, default=None)
+    ap.add_argument("--height", type=int, default=None)
+    ap.add_argument("--fx", type=float, default=None)
+    args = ap.parse_args()
+    for k in ("n", "width", "height", "fx"):
+        if getattr(args, k) is not None:
+            WORKLOAD[k] = getattr(args, k)
+            WORKLOAD["workload"] = (f"room {WORKLOAD['n']} Gaussians, D=16, K=8 classes, {WORKLOAD['width']}x"
+                                    f"{WORKLOAD['height']} fx={WORKLOAD['fx']:g}, single frame, FP32 (profiling size)")
+    return args
 
 
 def make_workload():

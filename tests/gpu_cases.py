@@ -39,13 +39,14 @@ def room_case(n, d=16, w=1200, h=680, fx=600.0, seed=0):
     return gs, cam, room
 
 
-def gpu_forward(gs, cams, prm, capacity=None, want_keys=True, rgb_dtype=torch.float32, feat_dtype=torch.float32):
+def gpu_forward(gs, cams, prm, capacity=None, want_keys=True, rgb_dtype=torch.float32, feat_dtype=torch.float32,
+                n_classes=0):
     field = raster.Field.from_numpy(gs, "cuda", rgb_dtype, feat_dtype)
     cams = cams if isinstance(cams, (list, tuple)) else [cams]
     if capacity is None:
-        r = raster.fit_capacity(field, cams, gs.feat_dim, params=prm)
+        r = raster.fit_capacity(field, cams, gs.feat_dim, params=prm, n_classes=n_classes)
     else:
-        r = raster.Renderer(gs.n, cams, gs.feat_dim, capacity, params=prm)
+        r = raster.Renderer(gs.n, cams, gs.feat_dim, capacity, params=prm, n_classes=n_classes)
     r.forward(field, want_keys=want_keys)
     torch.cuda.synchronize()
     return field, r

@@ -313,11 +313,11 @@ def test_pose_step_matches_oracle():
 # ---------------------------------------------------------------- whole step
 @pytest.mark.parametrize("exact", [True, False])
 def test_full_iteration_tiny_scene(exact):
-    """2,000 Gaussians in a box, 64x48, mapping loss + DSR + pose twist vs oracle.step.  In
-    exact mode (no thresholds) every pixel is comparable; with the default thresholds the
-    scene must have no pixel within rounding distance of a decision."""
+    """Box scene, 64x48, mapping loss + DSR + pose twist vs oracle.step.  In exact mode (no
+    thresholds) every pixel is comparable; the default-threshold scene (seed 11) has no pixel
+    within rounding distance of a decision, so the whole iteration is compared."""
     # exact mode has no T_min stop: keep the field thin enough that T stays far above f32 underflow
-    gs, cam = C.box_case(300 if exact else 2000, 16, 64, 48, 60.0)
+    gs, cam = C.box_case(300 if exact else 2000, 16, 64, 48, 60.0, seed=0 if exact else 11)
     kw = dict(alpha_min=0.0, alpha_max=1.0, T_min=0.0, radius_sigma=8.0) if exact else {}
     prm_g, prm_o = C.params_pair(**kw)
     dec = synth.decoder(8, 16)
@@ -326,10 +326,9 @@ def test_full_iteration_tiny_scene(exact):
     label = np.argmax(f @ dec.W.T.astype(np.float64) + dec.b, 1).astype(np.uint8).reshape(48, 64)
     tgt = synth.Frame(tgt_img["rgb"].astype(np.float32), tgt_img["depth"].astype(np.float32), label)
     ref = oracle.step(gs, cam, prm_o, tgt, dec, oracle.MAPPING)
-    field, r = C.gpu_forward(gs, cam, prm_g)
+    field, r = C.gpu_forward(gs, cam, prm_g, n_classes=8)
     excl, _ = C.excluded_pixels(cam, ref["proj"], C.gpu_projection(r), ref["img"])
-    if excl.sum():
-        pytest.skip(f"{int(excl.sum())} pixels within rounding distance of a threshold decision")
+    assert excl.sum() == 0
     tg = dict(rgb=torch.as_tensor(tgt.rgb.reshape(3, -1)).cuda(), depth=torch.as_tensor(tgt.depth.ravel()).cuda(),
               label=torch.as_tensor(tgt.label.ravel()).cuda())
     r.iteration(field, tg, torch.as_tensor(dec.W).cuda(), torch.as_tensor(dec.b).cuda(), raster.MAPPING,
