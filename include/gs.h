@@ -81,6 +81,10 @@ typedef struct {
     int32_t tile;
     float alpha_min, alpha_max, T_min, z_near, lowpass, radius_sigma;
     float bg_rgb[3];
+    /* Launch shape of the blend kernels (results do not depend on it): pixels
+     * per thread of gs_render_fwd / gs_render_bwd, 1, 2 or 4 (2 and 4 only for
+     * feature dims 16 and 32; 4 only up to 16); 0 = the library's default. */
+    int32_t fwd_px_per_thread, bwd_px_per_thread;
 } gs_raster_params;
 
 /* The Semantic Gaussian Field of Eq. 1, structure of arrays.

@@ -1,0 +1,68 @@
+"""Launch-shape autotuner for the two blend kernels.
+
+The blend kernels take the number of pixels each thread owns (1, 2 or 4) as a
+launch parameter: more pixels per thread share shared-memory reads and warp
+reductions, fewer keep more warps resident.  Which wins depends on the scene
+(splats per tile, pixels each splat reaches, feature width), so the tuner
+times every supported shape on the caller's own frame with CUDA events and
+returns raster parameters with the fastest ones.  The rendered images do not
+depend on the shape; gradients differ only by the order of float atomics.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import torch
+
+from . import _lib as L
+from .raster import RasterParams, Renderer
+
+CANDIDATES = (1, 2, 4)
+
+
+def _time(fn, reps: int, stream) -> float:
+    fn()                                   # warm-up (and module load)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    for _ in range(reps):
+        fn()
+    ev[1].record(stream)
+    ev[1].synchronize()
+    return ev[0].elapsed_time(ev[1]) / reps
+
+
+def tune_blend(r: Renderer, field, grad_mode: int = L.GS_GRAD_MAP, reps: int = 5, verbose: bool = False):
+    """Returns (RasterParams with the fastest fwd/bwd pixels-per-thread, timings in ms).
+
+    The renderer's image gradients (r.g_*) must hold the gradients to time the
+    backward with (e.g. after a loss call); the projection and binning are run here.
+    """
+    stream = torch.cuda.current_stream()
+    base = r.params
+    r.project(field)
+    r.bin_sort()
+    timings = {"fwd": {}, "bwd": {}}
+    for np_ in CANDIDATES:
+        r.prm_c = dataclasses.replace(base, fwd_px_per_thread=np_).c()
+        try:
+            timings["fwd"][np_] = _time(lambda: r.render_fwd(field), reps, stream)
+        except L.GsError as e:
+            if e.status != L.GS_ERR_UNSUPPORTED:
+                raise
+    best_f = min(timings["fwd"], key=timings["fwd"].get)
+    r.prm_c = dataclasses.replace(base, fwd_px_per_thread=best_f).c()
+    r.render_fwd(field)
+    for np_ in CANDIDATES:
+        r.prm_c = dataclasses.replace(base, fwd_px_per_thread=best_f, bwd_px_per_thread=np_).c()
+        try:
+            timings["bwd"][np_] = _time(lambda: r.render_bwd(field, grad_mode), reps, stream)
+        except L.GsError as e:
+            if e.status != L.GS_ERR_UNSUPPORTED:
+                raise
+    best_b = min(timings["bwd"], key=timings["bwd"].get)
+    tuned = dataclasses.replace(base, fwd_px_per_thread=best_f, bwd_px_per_thread=best_b)
+    r.params = tuned
+    r.prm_c = tuned.c()
+    if verbose:
+        print("autotune:", timings, "->", best_f, best_b)
+    return tuned, timings

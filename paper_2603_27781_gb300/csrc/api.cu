@@ -52,6 +52,10 @@ bool make_params(const gs_raster_params *p, Params *out) {
     out->lowpass = p->lowpass;
     out->radius_sigma = p->radius_sigma;
     for (int k = 0; k < 3; ++k) out->bg[k] = p->bg_rgb[k];
+    auto np_ok = [](int np) { return np == 0 || np == 1 || np == 2 || np == 4; };
+    if (!np_ok(p->fwd_px_per_thread) || !np_ok(p->bwd_px_per_thread)) return false;
+    out->fwd_np = p->fwd_px_per_thread;
+    out->bwd_np = p->bwd_px_per_thread;
     return true;
 }
 
@@ -83,7 +87,9 @@ WsLayout ws_layout(int64_t n, int n_views, int64_t capacity) {
     L.bin_end = off;
     off = 0;
     L.med_hist = take(sizeof(uint32_t) * 4 * 256 * (size_t)n_views);
-    L.dsr_acc = take(sizeof(double) * 8);
+    L.loss_part_f = take(sizeof(float) * (size_t)kLossBlocks * (32 * 32 + 32));
+    L.loss_part_d = take(sizeof(double) * (size_t)kLossBlocks * 3);
+    L.dsr_part = take(sizeof(double) * 512 * 6);
     L.misc_end = off;
     L.total = L.bin_end;
     if (L.misc_end > L.total) L.total = L.misc_end;

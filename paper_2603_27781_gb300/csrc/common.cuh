@@ -31,7 +31,12 @@ struct ViewTable {
 struct Params {
     float alpha_min, alpha_max, T_min, z_near, lowpass, radius_sigma;
     float bg[3];
+    int fwd_np, bwd_np;  // pixels per thread of the blend kernels (0 = default for the feature dim)
 };
+
+// Default pixels per thread of the blend kernels for a feature dimension.
+inline int default_fwd_np(int D) { return D >= 16 ? 2 : 1; }
+inline int default_bwd_np(int D) { return D >= 32 ? 2 : (D >= 16 ? 4 : 1); }
 
 // Builds the table from host cameras; returns false on invalid input.
 bool make_view_table(const gs_camera *cams, int n_views, int64_t n, ViewTable *vt);
@@ -216,13 +221,16 @@ struct WsLayout {
     size_t bin_end;
     // loss / dsr
     size_t med_hist;      // u32 [4][V][256]
-    size_t dsr_acc;       // f64 [8]
+    size_t loss_part_f;   // f32 [kLossBlocks][32 * 32 + 32] decoder-gradient partials
+    size_t loss_part_d;   // f64 [kLossBlocks][3] loss-term partials
+    size_t dsr_part;      // f64 [512][6] DSR partials
     size_t misc_end;
     size_t total;
     int64_t vn, capacity;
     int lb_tiles_depth, lb_tiles_inst;
 };
 
+constexpr int kLossBlocks = 1024;
 constexpr int kSortThreads = 256;
 constexpr int kSortIPT = 8;
 constexpr int kSortTile = kSortThreads * kSortIPT;

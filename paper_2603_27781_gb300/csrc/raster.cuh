@@ -1,15 +1,37 @@
-// Shared pieces of the blend kernels: splat staging and storage conversions.
+// Shared pieces of the blend kernels: launch shapes, splat staging and culling,
+// storage conversions.
 #pragma once
 
 #include "common.cuh"
 
 namespace gs {
 
-// Storage forms of colour and feature (F32 plain, F16 colour + BF16 feature).
-template <typename T> struct Store;
-template <> struct Store<float> { static constexpr int code = GS_F32; };
-template <> struct Store<__half> { static constexpr int code = GS_F16; };
-template <> struct Store<__nv_bfloat16> { static constexpr int code = GS_BF16; };
+constexpr int kBatch = 128;  // splats staged in shared memory per round
+
+// Launch shape with NP pixels per thread (1, 2 or 4) for one 16x16 tile.
+//   NP = 1: 8 warps, each an 8x4 block of pixels;
+//   NP = 2: 4 warps, each a 16x4 band, a thread owning 2 horizontal neighbours;
+//   NP = 4: 2 warps, each a 16x8 band, a thread owning a 2x2 block.
+// A thread's pixels share every shared-memory read of a splat and are
+// evaluated together, so their arithmetic chains interleave.
+template <int NP> struct Shape {
+    static constexpr int THREADS = kTilePix / NP;
+    static constexpr int WARPS = THREADS / 32;
+    static constexpr int BW = NP == 1 ? 8 : 16;        // warp box width
+    static constexpr int BH = NP == 1 ? 4 : (NP == 2 ? 4 : 8);
+    __device__ static void warp_origin(int w, int &x0, int &y0) {
+        x0 = NP == 1 ? (w & 1) * 8 : 0;
+        y0 = NP == 1 ? (w >> 1) * 4 : w * BH;
+    }
+    __device__ static void pixel(int tid, int p, int &lx, int &ly) {
+        const int lane = tid & 31, w = tid >> 5;
+        int x0, y0;
+        warp_origin(w, x0, y0);
+        if (NP == 1) { lx = x0 + (lane & 7); ly = y0 + (lane >> 3); }
+        else if (NP == 2) { lx = (lane & 7) * 2 + p; ly = y0 + (lane >> 3); }
+        else { lx = (lane & 7) * 2 + (p & 1); ly = y0 + (lane >> 3) * 2 + (p >> 1); }
+    }
+};
 
 // Colour of Gaussian g with the splat depth in the fourth lane (both are blended values).
 template <typename T>
@@ -42,11 +64,25 @@ __device__ __forceinline__ SplatGeo make_geo(float4 a, float2 lo, float4 c) {
     return s;
 }
 
-// Pixel of thread `tid` in a 16x16 tile: each warp covers an 8x4 block.
-__device__ __forceinline__ void tile_pixel(int tid, int tx, int ty, int &px, int &py) {
-    int lane = tid & 31, w = tid >> 5;
-    px = tx * kTile + (w & 1) * 8 + (lane & 7);
-    py = ty * kTile + (w >> 1) * 4 + (lane >> 3);
+// Half extents (x, y) of the region where the splat can reach alpha >= alpha_min:
+// o exp(-q/2) >= alpha_min  <=>  q <= 2 ln(o / alpha_min), and the ellipse
+// x^T Sigma^-1 x <= qmax spans +-sqrt(qmax Sigma_xx) in x.  Widened by 0.1% and
+// 0.01 px so that f32 rounding never culls a pixel the evaluation would blend;
+// infinite (no culling) when alpha_min is 0.
+__device__ __forceinline__ float2 splat_extent(float4 c, float o, float alpha_min) {
+    if (!(alpha_min > 0.f)) return make_float2(INFINITY, INFINITY);
+    if (!(o > alpha_min)) return make_float2(-1.f, -1.f);
+    const float qmax = 2.f * logf(o / alpha_min);
+    const float det = c.x * c.z - c.y * c.y;
+    if (!(det > 0.f)) return make_float2(INFINITY, INFINITY);
+    const float sxx = c.z / det, syy = c.x / det;
+    return make_float2(sqrtf(qmax * sxx) * 1.001f + 0.01f, sqrtf(qmax * syy) * 1.001f + 0.01f);
+}
+
+// Whether a splat centred at (u, v) with extent e can reach the warp's pixel box
+// (pixel centres from (bx0 + 0.5, by0 + 0.5), bw x bh of them).
+__device__ __forceinline__ bool reaches_box(float u, float v, float2 e, float bcx, float bcy, float hx, float hy) {
+    return fabsf(u - bcx) <= e.x + hx && fabsf(v - bcy) <= e.y + hy;
 }
 
 }  // namespace gs

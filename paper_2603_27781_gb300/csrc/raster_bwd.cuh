@@ -1,0 +1,305 @@
+// Backward of the blend (Eq. 4-7, 10): kernel template shared by the map-mode
+// and pose-mode translation units.
+//
+// Same grid as the forward: one CTA per 16x16 tile, NP pixels per thread.  A
+// pixel walks the splats it blended back to front, starting from its stored
+// final transmittance and last-contributor position; the transmittance in
+// front of each splat is recovered as T / (1 - alpha).  With S the blended
+// value behind a splat, d out / d alpha = T (x - S) per channel; the loss needs
+// only sum_ch g_ch (x_ch - S_ch) = g.x - g.S, and g.S obeys the same recurrence
+// as S, so one scalar per pixel replaces the per-channel S.
+//
+// Per splat a thread first sums its pixels' contributions, the warp sums its
+// lanes with a transpose reduction (each shuffle step halves the values a lane
+// carries, so N values take N - 1 shuffles and lane l ends with the sum of
+// value l), the warps combine through shared-memory atomics, and each
+// (tile, splat) issues one 16-byte vector atomic per 4 values to the
+// per-Gaussian accumulators.  A warp skips splats whose alpha >= alpha_min
+// region misses its pixel box, exactly as the forward did.
+#pragma once
+
+#include "raster.cuh"
+
+namespace gs {
+
+constexpr int pow2_at_least(int x) { return x <= 8 ? 8 : (x <= 16 ? 16 : 32); }
+
+// Sums v[0..N) over the warp; lane l returns the total of value (l mod N).
+template <int N>
+__device__ __forceinline__ float warp_transpose_reduce(float (&v)[N], int lane) {
+#pragma unroll
+    for (int s = N / 2; s >= 1; s >>= 1) {
+        const bool up = lane & s;
+#pragma unroll
+        for (int i = 0; i < s; ++i) {
+            float send = up ? v[i] : v[i + s];
+            float keep = up ? v[i + s] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+        }
+    }
+    float r = v[0];
+#pragma unroll
+    for (int s = N; s < 32; s <<= 1) r += __shfl_xor_sync(0xffffffffu, r, s);
+    return r;
+}
+
+template <int D, bool MAP>
+struct BwdLayout {
+    static constexpr int NV = MAP ? 10 + D : 6;                 // reduced values per splat
+    static constexpr int C0 = NV > 32 ? 32 : pow2_at_least(NV);  // first chunk (power of two)
+    static constexpr int R1 = NV > 32 ? NV - 32 : 0;             // values in the second chunk
+    static constexpr int C1 = R1 > 0 ? pow2_at_least(R1) : 0;
+    static constexpr int ROW = C0 + C1;                          // shared accumulator row
+};
+
+struct BwdArgs {
+    const float4 *uvdo;
+    const float2 *uv_lo;
+    const float4 *conic;
+    const void *rgb;
+    const void *feat;
+    const uint32_t *vals;
+    const uint32_t *ranges;
+    int64_t P;
+    const float *T_final;
+    const int32_t *n_contrib;
+    const float *g_rgb, *g_depth, *g_sil, *g_feat;
+    float4 *acc_uvod, *acc_conic, *acc_rgb;
+    float *d_feat;
+};
+
+template <int D, int NP, bool MAP, typename RT, typename FT>
+__global__ void __launch_bounds__(Shape<NP>::THREADS) raster_bwd_kernel(ViewTable vt, Params prm, BwdArgs A) {
+    using LY = BwdLayout<D, MAP>;
+    using SH = Shape<NP>;
+    constexpr int NT = SH::THREADS;
+    constexpr int D4 = D / 4;
+    constexpr int NCH = 5 + D;  // r, g, b, depth, sil, features
+    __shared__ SplatGeo s_geo[kBatch];
+    __shared__ float2 s_ext[kBatch];
+    __shared__ float4 s_rgbd[kBatch];
+    __shared__ float4 s_feat[kBatch * (D4 > 0 ? D4 : 1)];
+    __shared__ float s_acc[kBatch * LY::ROW];
+    __shared__ int s_max_last;
+    const RT *rgb = static_cast<const RT *>(A.rgb);
+    const FT *feat = static_cast<const FT *>(A.feat);
+
+    const int gt = blockIdx.x;
+    const int v = view_of_tile(vt, gt);
+    const int t = gt - vt.tile_off[v];
+    const int tx = t % vt.TX[v], ty = t / vt.TX[v];
+    const int tid = threadIdx.x, lane = tid & 31;
+    const uint32_t start = A.ranges[2 * gt];
+    const int64_t voff = (int64_t)v * vt.n;
+    const int64_t P = A.P;
+    int bx0, by0;
+    SH::warp_origin(tid >> 5, bx0, by0);
+    const float bcx = (float)(tx * kTile + bx0) + 0.5f * SH::BW, bcy = (float)(ty * kTile + by0) + 0.5f * SH::BH;
+    const float hx = 0.5f * (SH::BW - 1), hy = 0.5f * (SH::BH - 1);
+
+    // per-pixel state: upstream gradient g, transmittance, g.S behind the current splat
+    float gch[NP][NCH], T[NP], gS[NP], pxc[NP], pyc[NP];
+    int last[NP];
+    int my_max = 0;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        int lx, ly;
+        SH::pixel(tid, p, lx, ly);
+        const int px = tx * kTile + lx, py = ty * kTile + ly;
+        pxc[p] = (float)px + 0.5f;
+        pyc[p] = (float)py + 0.5f;
+        T[p] = 1.f;
+        last[p] = 0;
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) gch[p][c] = 0.f;
+        if (px < vt.W[v] && py < vt.H[v]) {
+            const int64_t pix = vt.pix_off[v] + (int64_t)py * vt.W[v] + px;
+            T[p] = A.T_final[pix];
+            last[p] = A.n_contrib[pix];
+            gch[p][0] = A.g_rgb[pix];
+            gch[p][1] = A.g_rgb[P + pix];
+            gch[p][2] = A.g_rgb[2 * P + pix];
+            gch[p][3] = A.g_depth[pix];
+            gch[p][4] = A.g_sil ? A.g_sil[pix] : 0.f;
+#pragma unroll
+            for (int d = 0; d < D; ++d) gch[p][5 + d] = A.g_feat[d * P + pix];
+        }
+        gS[p] = gch[p][0] * prm.bg[0] + gch[p][1] * prm.bg[1] + gch[p][2] * prm.bg[2];
+        my_max = max(my_max, last[p]);
+    }
+
+    if (tid == 0) s_max_last = 0;
+    __syncthreads();
+    if (my_max > 0) atomicMax(&s_max_last, my_max);
+    __syncthreads();
+    const int max_last = s_max_last;
+    const float inv_l2e = 1.f / kLog2e;
+
+    for (int b_end = max_last; b_end > 0; b_end -= kBatch) {
+        const int b_start = max(0, b_end - kBatch);
+        const int cnt = b_end - b_start;
+        __syncthreads();
+        for (int i = tid; i < cnt; i += NT) {
+            const uint32_t item = A.vals[start + b_start + i];
+            const int64_t g = (int64_t)item - voff;
+            const float4 a = A.uvdo[item];
+            const float4 c = A.conic[item];
+            s_geo[i] = make_geo(a, A.uv_lo[item], c);
+            s_ext[i] = splat_extent(c, a.w, prm.alpha_min);
+            s_rgbd[i] = load_rgbd(rgb, g, a.z);
+#pragma unroll
+            for (int q = 0; q < D4; ++q) s_feat[i * D4 + q] = load_feat4(feat, g * D + 4 * q);
+        }
+        for (int i = tid; i < cnt * LY::ROW; i += NT) s_acc[i] = 0.f;
+        __syncthreads();
+
+        for (int k = cnt - 1; k >= 0; --k) {
+            const int pos = b_start + k;
+            if (!__any_sync(0xffffffffu, pos < my_max)) continue;
+            const SplatGeo s = s_geo[k];
+            if (!reaches_box(s.u, s.v, s_ext[k], bcx, bcy, hx, hy)) continue;
+            PairEval e[NP];
+            bool contrib[NP], any = false;
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                e[p] = eval_pair(s, pxc[p], pyc[p], prm.alpha_min, prm.alpha_max);
+                contrib[p] = pos < last[p] && !e[p].skip;
+                any |= contrib[p];
+            }
+            if (!__any_sync(0xffffffffu, any)) continue;
+
+            float val[LY::C0 + LY::C1];
+#pragma unroll
+            for (int i = 0; i < LY::C0 + LY::C1; ++i) val[i] = 0.f;
+            if (any) {
+                const float4 c = s_rgbd[k];
+                float x[NCH];
+                x[0] = c.x; x[1] = c.y; x[2] = c.z; x[3] = c.w; x[4] = 1.f;
+#pragma unroll
+                for (int q = 0; q < D4; ++q) {
+                    const float4 f = s_feat[k * D4 + q];
+                    x[5 + 4 * q] = f.x; x[6 + 4 * q] = f.y; x[7 + 4 * q] = f.z; x[8 + 4 * q] = f.w;
+                }
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    if (!contrib[p]) continue;
+                    const float a = e[p].alpha;
+                    const float Tb = __fdividef(T[p], 1.f - a);
+                    const float w = a * Tb;
+                    float gx = 0.f;
+#pragma unroll
+                    for (int ch = 0; ch < NCH; ++ch) gx = fmaf(gch[p][ch], x[ch], gx);
+                    const float da = Tb * (gx - gS[p]);
+                    gS[p] = fmaf(a, gx - gS[p], gS[p]);
+                    T[p] = Tb;
+                    if (e[p].oG < prm.alpha_max) {
+                        const float dpow = e[p].oG * da;
+                        const float dx = e[p].dx, dy = e[p].dy;
+                        val[0] += (2.f * s.qa * dx + s.qb * dy) * (-dpow * inv_l2e);
+                        val[1] += (s.qb * dx + 2.f * s.qc * dy) * (-dpow * inv_l2e);
+                        val[2] += -0.5f * dx * dx * dpow;
+                        val[3] += -dx * dy * dpow;
+                        val[4] += -0.5f * dy * dy * dpow;
+                        if (MAP) val[5] += e[p].G * da;
+                    }
+                    if (MAP) {
+                        val[6] = fmaf(w, gch[p][3], val[6]);
+                        val[7] = fmaf(w, gch[p][0], val[7]);
+                        val[8] = fmaf(w, gch[p][1], val[8]);
+                        val[9] = fmaf(w, gch[p][2], val[9]);
+#pragma unroll
+                        for (int d = 0; d < D; ++d) val[10 + d] = fmaf(w, gch[p][5 + d], val[10 + d]);
+                    } else {
+                        val[5] = fmaf(w, gch[p][3], val[5]);
+                    }
+                }
+            }
+            // warp reduction, then CTA combine in shared memory
+            {
+                float v0[LY::C0];
+#pragma unroll
+                for (int i = 0; i < LY::C0; ++i) v0[i] = val[i];
+                const float r = warp_transpose_reduce<LY::C0>(v0, lane);
+                const int idx = lane & (LY::C0 - 1);
+                if (lane < LY::C0 && idx < LY::NV && r != 0.f) atomicAdd(&s_acc[k * LY::ROW + idx], r);
+            }
+            if constexpr (LY::C1 > 0) {
+                float v1[LY::C1];
+#pragma unroll
+                for (int i = 0; i < LY::C1; ++i) v1[i] = val[LY::C0 + i];
+                const float r = warp_transpose_reduce<LY::C1>(v1, lane);
+                const int idx = lane & (LY::C1 - 1);
+                if (lane < LY::C1 && idx < LY::R1 && r != 0.f) atomicAdd(&s_acc[k * LY::ROW + LY::C0 + idx], r);
+            }
+        }
+        __syncthreads();
+        // one set of vector atomics per (tile, splat)
+        for (int i = tid; i < cnt; i += NT) {
+            const float *a = s_acc + i * LY::ROW;
+            bool nz = false;
+#pragma unroll
+            for (int j = 0; j < LY::NV; ++j) nz |= a[j] != 0.f;
+            if (!nz) continue;
+            const uint32_t item = A.vals[start + b_start + i];
+            const int64_t g = (int64_t)item - voff;
+            if (MAP) {
+                atomicAdd(&A.acc_uvod[item], make_float4(a[0], a[1], a[5], a[6]));
+                atomicAdd(&A.acc_conic[item], make_float4(a[2], a[3], a[4], 0.f));
+                atomicAdd(&A.acc_rgb[g], make_float4(a[7], a[8], a[9], 0.f));
+#pragma unroll
+                for (int q = 0; q < D4; ++q)
+                    atomicAdd(reinterpret_cast<float4 *>(A.d_feat + g * D) + q,
+                              make_float4(a[10 + 4 * q], a[11 + 4 * q], a[12 + 4 * q], a[13 + 4 * q]));
+            } else {
+                atomicAdd(&A.acc_uvod[item], make_float4(a[0], a[1], 0.f, a[5]));
+                atomicAdd(&A.acc_conic[item], make_float4(a[2], a[3], a[4], 0.f));
+            }
+        }
+    }
+}
+
+template <int D, int NP, bool MAP, typename RT, typename FT>
+gs_status launch_bwd(const ViewTable &vt, const Params &prm, const BwdArgs &A, cudaStream_t st) {
+    raster_bwd_kernel<D, NP, MAP, RT, FT><<<vt.tile_off[vt.n_views], Shape<NP>::THREADS, 0, st>>>(vt, prm, A);
+    return last_launch();
+}
+
+// Dispatch over feature dim, pixels per thread and storage for one mode.
+template <bool MAP>
+gs_status dispatch_bwd(int D, int np, bool half, const ViewTable &vt, const Params &prm, const BwdArgs &A,
+                       cudaStream_t st) {
+    if (half) {
+        if (D == 16) {
+            if (np == 1) return launch_bwd<16, 1, MAP, __half, __nv_bfloat16>(vt, prm, A, st);
+            if (np == 2) return launch_bwd<16, 2, MAP, __half, __nv_bfloat16>(vt, prm, A, st);
+            if (np == 4) return launch_bwd<16, 4, MAP, __half, __nv_bfloat16>(vt, prm, A, st);
+        } else if (D == 32) {
+            if (np == 1) return launch_bwd<32, 1, MAP, __half, __nv_bfloat16>(vt, prm, A, st);
+            if (np == 2) return launch_bwd<32, 2, MAP, __half, __nv_bfloat16>(vt, prm, A, st);
+        }
+        return GS_ERR_UNSUPPORTED;
+    }
+    switch (D) {
+        case 0: if (np == 1) return launch_bwd<0, 1, MAP, float, float>(vt, prm, A, st); break;
+        case 4: if (np == 1) return launch_bwd<4, 1, MAP, float, float>(vt, prm, A, st); break;
+        case 8: if (np == 1) return launch_bwd<8, 1, MAP, float, float>(vt, prm, A, st); break;
+        case 16:
+            if (np == 1) return launch_bwd<16, 1, MAP, float, float>(vt, prm, A, st);
+            if (np == 2) return launch_bwd<16, 2, MAP, float, float>(vt, prm, A, st);
+            if (np == 4) return launch_bwd<16, 4, MAP, float, float>(vt, prm, A, st);
+            break;
+        case 32:
+            if (np == 1) return launch_bwd<32, 1, MAP, float, float>(vt, prm, A, st);
+            if (np == 2) return launch_bwd<32, 2, MAP, float, float>(vt, prm, A, st);
+            break;
+        default: break;
+    }
+    return GS_ERR_UNSUPPORTED;
+}
+
+gs_status dispatch_bwd_map(int D, int np, bool half, const ViewTable &vt, const Params &prm, const BwdArgs &A,
+                           cudaStream_t st);
+gs_status dispatch_bwd_pose(int D, int np, bool half, const ViewTable &vt, const Params &prm, const BwdArgs &A,
+                            cudaStream_t st);
+
+}  // namespace gs

@@ -1,27 +1,26 @@
-// Forward blend (GS3LAM Eq. 4-7 and 10): one CTA per 16x16 tile, one thread per
-// pixel.  Splats of the tile are staged 256 at a time in shared memory (one
-// coalesced-per-thread record each) and read back as broadcasts; every thread
-// walks them front to back and stops at the T_min threshold; the CTA leaves
-// as soon as all of its pixels are done.
+// Forward blend (GS3LAM Eq. 4-7 and 10): one CTA per 16x16 tile, NP pixels per
+// thread.  Splats of the tile are staged 128 at a time in shared memory (one
+// record per thread load) and read back as broadcasts; a warp skips a splat
+// whose alpha >= alpha_min region misses its pixel box; every pixel walks the
+// rest front to back and stops at the T_min threshold; the CTA leaves as soon
+// as all of its pixels are done.
 #include "raster.cuh"
 
 namespace gs {
 namespace {
 
-constexpr int kBatch = 256;
-
-template <int D, typename RT, typename FT>
-__global__ void __launch_bounds__(kTilePix) raster_fwd_kernel(ViewTable vt, Params prm, const float4 *__restrict__ uvdo,
-                                                              const float2 *__restrict__ uv_lo,
-                                                              const float4 *__restrict__ conic,
-                                                              const RT *__restrict__ rgb, const FT *__restrict__ feat,
-                                                              const uint32_t *__restrict__ vals,
-                                                              const uint32_t *__restrict__ ranges, int64_t P,
-                                                              float *o_rgb, float *o_depth, float *o_sil, float *o_feat,
-                                                              float *o_T, int32_t *o_nc, int32_t *o_nb) {
-    constexpr int D4 = D / 4;
+template <int D, int NP, typename RT, typename FT>
+__global__ void __launch_bounds__(Shape<NP>::THREADS) raster_fwd_kernel(
+    ViewTable vt, Params prm, const float4 *__restrict__ uvdo, const float2 *__restrict__ uv_lo,
+    const float4 *__restrict__ conic, const RT *__restrict__ rgb, const FT *__restrict__ feat,
+    const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges, int64_t P, float *o_rgb, float *o_depth,
+    float *o_sil, float *o_feat, float *o_T, int32_t *o_nc, int32_t *o_nb) {
+    using SH = Shape<NP>;
+    constexpr int NT = SH::THREADS;
+    constexpr int D4 = D / 4, DD = D > 0 ? D : 1;
     __shared__ SplatGeo s_geo[kBatch];
-    __shared__ float4 s_rgb[kBatch];
+    __shared__ float2 s_ext[kBatch];
+    __shared__ float4 s_rgbd[kBatch];
     __shared__ float4 s_feat[kBatch * (D4 > 0 ? D4 : 1)];
 
     const int gt = blockIdx.x;
@@ -29,112 +28,148 @@ __global__ void __launch_bounds__(kTilePix) raster_fwd_kernel(ViewTable vt, Para
     const int t = gt - vt.tile_off[v];
     const int tx = t % vt.TX[v], ty = t / vt.TX[v];
     const int tid = threadIdx.x;
-    int px, py;
-    tile_pixel(tid, tx, ty, px, py);
-    const bool inside = px < vt.W[v] && py < vt.H[v];
-    const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
     const uint32_t start = ranges[2 * gt], end = ranges[2 * gt + 1];
     const int64_t voff = (int64_t)v * vt.n;
+    int bx0, by0;
+    SH::warp_origin(tid >> 5, bx0, by0);
+    const float bcx = (float)(tx * kTile + bx0) + 0.5f * SH::BW, bcy = (float)(ty * kTile + by0) + 0.5f * SH::BH;
+    const float hx = 0.5f * (SH::BW - 1), hy = 0.5f * (SH::BH - 1);
 
-    float T = 1.f, acc_r = 0.f, acc_g = 0.f, acc_b = 0.f, acc_d = 0.f, acc_s = 0.f;
-    float acc_f[D > 0 ? D : 1];
+    float pxc[NP], pyc[NP], T[NP], ar[NP], ag[NP], ab[NP], ad[NP], as[NP], af[NP][DD];
+    int last[NP], blended[NP];
+    bool inside[NP], done[NP];
 #pragma unroll
-    for (int d = 0; d < (D > 0 ? D : 1); ++d) acc_f[d] = 0.f;
-    int last = 0, blended = 0;
-    bool done = !inside;
+    for (int p = 0; p < NP; ++p) {
+        int lx, ly;
+        SH::pixel(tid, p, lx, ly);
+        const int px = tx * kTile + lx, py = ty * kTile + ly;
+        inside[p] = px < vt.W[v] && py < vt.H[v];
+        done[p] = !inside[p];
+        pxc[p] = (float)px + 0.5f;
+        pyc[p] = (float)py + 0.5f;
+        T[p] = 1.f;
+        ar[p] = ag[p] = ab[p] = ad[p] = as[p] = 0.f;
+#pragma unroll
+        for (int d = 0; d < DD; ++d) af[p][d] = 0.f;
+        last[p] = blended[p] = 0;
+    }
+    auto all_done = [&]() {
+        bool a = true;
+#pragma unroll
+        for (int p = 0; p < NP; ++p) a = a && done[p];
+        return a;
+    };
 
     for (uint32_t b0 = start; b0 < end; b0 += kBatch) {
-        if (__syncthreads_count(!done) == 0) break;
-        uint32_t j = b0 + tid;
-        if (j < end) {
-            uint32_t item = vals[j];
-            int64_t g = (int64_t)item - voff;
-            const float4 a = uvdo[item];
-            s_geo[tid] = make_geo(a, uv_lo[item], conic[item]);
-            s_rgb[tid] = load_rgbd(rgb, g, a.z);
+        if (__syncthreads_count(!all_done()) == 0) break;
+        for (int i = tid; i < kBatch; i += NT) {
+            const uint32_t j = b0 + i;
+            if (j < end) {
+                const uint32_t item = vals[j];
+                const int64_t g = (int64_t)item - voff;
+                const float4 a = uvdo[item];
+                const float4 c = conic[item];
+                s_geo[i] = make_geo(a, uv_lo[item], c);
+                s_ext[i] = splat_extent(c, a.w, prm.alpha_min);
+                s_rgbd[i] = load_rgbd(rgb, g, a.z);
 #pragma unroll
-            for (int q = 0; q < D4; ++q) s_feat[tid * D4 + q] = load_feat4(feat, g * D + 4 * q);
+                for (int q = 0; q < D4; ++q) s_feat[i * D4 + q] = load_feat4(feat, g * D + 4 * q);
+            }
         }
         __syncthreads();
         const int nb = min((uint32_t)kBatch, end - b0);
-        for (int k = 0; k < nb && !done; ++k) {
+        for (int k = 0; k < nb; ++k) {
+            if (all_done()) break;
             const SplatGeo s = s_geo[k];
-            PairEval e = eval_pair(s, pxc, pyc, prm.alpha_min, prm.alpha_max);
-            if (e.skip) continue;
-            float Tn = T * (1.f - e.alpha);
-            if (Tn < prm.T_min) {
-                done = true;
-                break;
+            if (!reaches_box(s.u, s.v, s_ext[k], bcx, bcy, hx, hy)) continue;
+            // evaluate all of the thread's pixels first (independent chains), then decide
+            float al[NP];
+            bool ok[NP];
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const PairEval e = eval_pair(s, pxc[p], pyc[p], prm.alpha_min, prm.alpha_max);
+                al[p] = e.alpha;
+                ok[p] = !done[p] && !e.skip;
             }
-            float w = e.alpha * T;
-            float4 c = s_rgb[k];
-            acc_r = fmaf(w, c.x, acc_r);
-            acc_g = fmaf(w, c.y, acc_g);
-            acc_b = fmaf(w, c.z, acc_b);
-            acc_d = fmaf(w, c.w, acc_d);
-            acc_s += w;
+            float wgt[NP];
+            bool any = false;
+            const int pos = (int)(b0 - start) + k + 1;
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const float Tn = T[p] * (1.f - al[p]);
+                const bool stop = ok[p] && Tn < prm.T_min;
+                const bool b = ok[p] && !stop;
+                done[p] = done[p] || stop;
+                wgt[p] = b ? al[p] * T[p] : 0.f;
+                T[p] = b ? Tn : T[p];
+                last[p] = b ? pos : last[p];
+                blended[p] += b ? 1 : 0;
+                any = any || b;
+            }
+            if (!any) continue;
+            const float4 c = s_rgbd[k];
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const float w = wgt[p];
+                ar[p] = fmaf(w, c.x, ar[p]);
+                ag[p] = fmaf(w, c.y, ag[p]);
+                ab[p] = fmaf(w, c.z, ab[p]);
+                ad[p] = fmaf(w, c.w, ad[p]);
+                as[p] += w;
+            }
 #pragma unroll
             for (int q = 0; q < D4; ++q) {
-                float4 f = s_feat[k * D4 + q];
-                acc_f[4 * q] = fmaf(w, f.x, acc_f[4 * q]);
-                acc_f[4 * q + 1] = fmaf(w, f.y, acc_f[4 * q + 1]);
-                acc_f[4 * q + 2] = fmaf(w, f.z, acc_f[4 * q + 2]);
-                acc_f[4 * q + 3] = fmaf(w, f.w, acc_f[4 * q + 3]);
+                const float4 f = s_feat[k * D4 + q];
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    af[p][4 * q] = fmaf(wgt[p], f.x, af[p][4 * q]);
+                    af[p][4 * q + 1] = fmaf(wgt[p], f.y, af[p][4 * q + 1]);
+                    af[p][4 * q + 2] = fmaf(wgt[p], f.z, af[p][4 * q + 2]);
+                    af[p][4 * q + 3] = fmaf(wgt[p], f.w, af[p][4 * q + 3]);
+                }
             }
-            T = Tn;
-            last = (int)(b0 - start) + k + 1;
-            ++blended;
         }
     }
-    if (!inside) return;
-    const int64_t pix = vt.pix_off[v] + (int64_t)py * vt.W[v] + px;
-    o_rgb[pix] = acc_r + T * prm.bg[0];
-    o_rgb[P + pix] = acc_g + T * prm.bg[1];
-    o_rgb[2 * P + pix] = acc_b + T * prm.bg[2];
-    o_depth[pix] = acc_d;
-    o_sil[pix] = acc_s;
 #pragma unroll
-    for (int d = 0; d < D; ++d) o_feat[d * P + pix] = acc_f[d];
-    o_T[pix] = T;
-    o_nc[pix] = last;
-    if (o_nb) o_nb[pix] = blended;
+    for (int p = 0; p < NP; ++p) {
+        if (!inside[p]) continue;
+        const int64_t pix = vt.pix_off[v] + (int64_t)((int)pyc[p]) * vt.W[v] + (int)pxc[p];
+        o_rgb[pix] = ar[p] + T[p] * prm.bg[0];
+        o_rgb[P + pix] = ag[p] + T[p] * prm.bg[1];
+        o_rgb[2 * P + pix] = ab[p] + T[p] * prm.bg[2];
+        o_depth[pix] = ad[p];
+        o_sil[pix] = as[p];
+#pragma unroll
+        for (int d = 0; d < D; ++d) o_feat[d * P + pix] = af[p][d];
+        o_T[pix] = T[p];
+        o_nc[pix] = last[p];
+        if (o_nb) o_nb[pix] = blended[p];
+    }
 }
 
-template <int D, typename RT, typename FT>
+template <int D, int NP, typename RT, typename FT>
 gs_status launch(const ViewTable &vt, const Params &prm, const gs_gaussians *g, const gs_projected *proj,
                  const gs_binning *bins, gs_images *out, cudaStream_t st) {
-    int tiles = vt.tile_off[vt.n_views];
-    int64_t P = vt.pix_off[vt.n_views];
-    raster_fwd_kernel<D, RT, FT><<<tiles, kTilePix, 0, st>>>(
+    const int tiles = vt.tile_off[vt.n_views];
+    const int64_t P = vt.pix_off[vt.n_views];
+    raster_fwd_kernel<D, NP, RT, FT><<<tiles, Shape<NP>::THREADS, 0, st>>>(
         vt, prm, reinterpret_cast<const float4 *>(proj->uvdo), reinterpret_cast<const float2 *>(proj->uv_lo),
         reinterpret_cast<const float4 *>(proj->conic), static_cast<const RT *>(g->rgb),
-        static_cast<const FT *>(g->feat), bins->vals, bins->ranges, P, out->rgb,
-        out->depth, out->sil, out->feat, out->T_final, out->n_contrib, out->n_blended);
+        static_cast<const FT *>(g->feat), bins->vals, bins->ranges, P, out->rgb, out->depth, out->sil, out->feat,
+        out->T_final, out->n_contrib, out->n_blended);
     return last_launch();
 }
 
-template <typename RT, typename FT>
-gs_status dispatch_d(int D, const ViewTable &vt, const Params &prm, const gs_gaussians *g, const gs_projected *proj,
-                     const gs_binning *bins, gs_images *out, cudaStream_t st) {
-    switch (D) {
-        case 0: return launch<0, RT, FT>(vt, prm, g, proj, bins, out, st);
-        case 4: return launch<4, RT, FT>(vt, prm, g, proj, bins, out, st);
-        case 8: return launch<8, RT, FT>(vt, prm, g, proj, bins, out, st);
-        case 16: return launch<16, RT, FT>(vt, prm, g, proj, bins, out, st);
-        case 32: return launch<32, RT, FT>(vt, prm, g, proj, bins, out, st);
-        default: return GS_ERR_UNSUPPORTED;
+template <int D, typename RT, typename FT>
+gs_status by_np(int np, const ViewTable &vt, const Params &prm, const gs_gaussians *g, const gs_projected *proj,
+                const gs_binning *bins, gs_images *out, cudaStream_t st) {
+    if (np == 1) return launch<D, 1, RT, FT>(vt, prm, g, proj, bins, out, st);
+    if constexpr (D >= 16) {
+        if (np == 2) return launch<D, 2, RT, FT>(vt, prm, g, proj, bins, out, st);
+        if constexpr (D <= 16)
+            if (np == 4) return launch<D, 4, RT, FT>(vt, prm, g, proj, bins, out, st);
     }
-}
-
-template <>
-gs_status dispatch_d<__half, __nv_bfloat16>(int D, const ViewTable &vt, const Params &prm, const gs_gaussians *g,
-                                            const gs_projected *proj, const gs_binning *bins, gs_images *out,
-                                            cudaStream_t st) {
-    switch (D) {
-        case 16: return launch<16, __half, __nv_bfloat16>(vt, prm, g, proj, bins, out, st);
-        case 32: return launch<32, __half, __nv_bfloat16>(vt, prm, g, proj, bins, out, st);
-        default: return GS_ERR_UNSUPPORTED;
-    }
+    return GS_ERR_UNSUPPORTED;
 }
 
 }  // namespace
@@ -164,6 +199,17 @@ extern "C" gs_status gs_render_fwd(const gs_gaussians *g, const gs_projected *pr
     }
     if (g->feat_dim && (reinterpret_cast<uintptr_t>(g->feat) & 15)) return GS_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    if (g->rgb_dtype == GS_F16) return dispatch_d<__half, __nv_bfloat16>(g->feat_dim, vt, prm, g, proj, bins, out, st);
-    return dispatch_d<float, float>(g->feat_dim, vt, prm, g, proj, bins, out, st);
+    const int np = prm.fwd_np ? prm.fwd_np : default_fwd_np(g->feat_dim);
+    if (g->rgb_dtype == GS_F16) {
+        if (g->feat_dim == 16) return by_np<16, __half, __nv_bfloat16>(np, vt, prm, g, proj, bins, out, st);
+        return by_np<32, __half, __nv_bfloat16>(np, vt, prm, g, proj, bins, out, st);
+    }
+    switch (g->feat_dim) {
+        case 0: return by_np<0, float, float>(np, vt, prm, g, proj, bins, out, st);
+        case 4: return by_np<4, float, float>(np, vt, prm, g, proj, bins, out, st);
+        case 8: return by_np<8, float, float>(np, vt, prm, g, proj, bins, out, st);
+        case 16: return by_np<16, float, float>(np, vt, prm, g, proj, bins, out, st);
+        case 32: return by_np<32, float, float>(np, vt, prm, g, proj, bins, out, st);
+        default: return GS_ERR_UNSUPPORTED;
+    }
 }

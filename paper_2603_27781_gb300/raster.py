@@ -26,10 +26,13 @@ class RasterParams:
     lowpass: float = 0.3
     radius_sigma: float = 3.0
     bg: tuple = (0.0, 0.0, 0.0)
+    fwd_px_per_thread: int = 0     # launch shape only (0 = library default)
+    bwd_px_per_thread: int = 0
 
     def c(self) -> L.gs_raster_params:
         return L.gs_raster_params(self.tile, self.alpha_min, self.alpha_max, self.T_min, self.z_near, self.lowpass,
-                                  self.radius_sigma, (ctypes.c_float * 3)(*self.bg))
+                                  self.radius_sigma, (ctypes.c_float * 3)(*self.bg), self.fwd_px_per_thread,
+                                  self.bwd_px_per_thread)
 
 
 @dataclasses.dataclass

@@ -156,6 +156,42 @@ def test_render_bwd_matches_oracle(name):
     _bwd_compare(gs, [cam], prm_g, prm_o)
 
 
+@pytest.mark.parametrize("np_", [1, 2, 4])
+def test_launch_shapes_agree(np_):
+    """Every pixels-per-thread shape renders bit-identical images and the same gradients."""
+    gs, cam, _ = C.room_case(20000, 16, 330, 190, 165.0)
+    prm0, prm_o = C.params_pair()
+    field, r0 = C.gpu_forward(gs, cam, prm0)
+    ref = {k: v.clone() for k, v in r0.images().items()}
+    g = C.random_image_grads(r0.P, 16, 5)
+    for rr in (r0,):
+        rr.g_rgb.copy_(torch.as_tensor(g["rgb"])); rr.g_depth.copy_(torch.as_tensor(g["depth"]))
+        rr.g_sil.copy_(torch.as_tensor(g["sil"])); rr.g_feat.copy_(torch.as_tensor(g["feat"]))
+    r0.backward(field, L.GS_GRAD_MAP | L.GS_GRAD_POSE)
+    want = [t.clone() for t in (r0.d_means, r0.d_quats, r0.d_log_scales, r0.d_logits, r0.d_rgb, r0.d_feat,
+                                r0.d_twist)]
+    prm = raster.RasterParams(fwd_px_per_thread=np_, bwd_px_per_thread=np_)
+    r0.params, r0.prm_c = prm, prm.c()
+    r0.forward(field)
+    for k, t in r0.images().items():
+        assert torch.equal(t, ref[k]), k
+    r0.backward(field, L.GS_GRAD_MAP | L.GS_GRAD_POSE)
+    for name, a, b in zip(("means", "quats", "log_scales", "logits", "rgb", "feat", "twist"), want,
+                          (r0.d_means, r0.d_quats, r0.d_log_scales, r0.d_logits, r0.d_rgb, r0.d_feat, r0.d_twist)):
+        C.assert_grad_close(name, b.cpu().numpy(), a.cpu().numpy(), 1e-5)
+
+
+def test_autotuner_picks_a_supported_shape():
+    from paper_2603_27781_gb300 import autotune
+    gs, cam, _ = C.room_case(20000, 16, 330, 190, 165.0)
+    field, r = C.gpu_forward(gs, cam, C.params_pair()[0])
+    g = C.random_image_grads(r.P, 16, 6)
+    r.g_rgb.copy_(torch.as_tensor(g["rgb"])); r.g_feat.copy_(torch.as_tensor(g["feat"]))
+    tuned, t = autotune.tune_blend(r, field, L.GS_GRAD_MAP)
+    assert set(t["fwd"]) == {1, 2, 4} and set(t["bwd"]) == {1, 2, 4}
+    assert tuned.fwd_px_per_thread in t["fwd"] and tuned.bwd_px_per_thread in t["bwd"]
+
+
 def test_render_bwd_multiview_sums_views():
     gs, cam, room = C.room_case(20000, 16, 160, 96, 80.0)
     poses = synth.keyframe_loop(8, room=room)
