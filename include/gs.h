@@ -303,6 +303,27 @@ gs_status gs_loss_fwd_bwd(const gs_camera *cams, int n_views, int feat_dim, cons
                           gs_image_grads_out *grad, float *d_dec_W, float *d_dec_b,
                           double *loss_out, float *mask_out, float *median_out, gs_stream stream);
 
+/* Allocation-free variant of gs_loss_fwd_bwd, for callers that cannot call
+ * cudaMalloc: code that must not allocate while a CUDA graph is being captured
+ * or inside a per-frame real-time budget, plugins whose host application owns
+ * every device allocation, and bindings from environments without a device
+ * allocator.  The paper has no counterpart; it is a deployment convenience.
+ * Arguments and results are exactly those of gs_loss_fwd_bwd without the
+ * workspace.  Its scratch is one static device array of 4,415,488 bytes
+ * (4.2 MiB) that every GPU which loads the library holds until the process
+ * exits; it serves at most 16 views (more returns GS_ERR_UNSUPPORTED before
+ * any launch).  The first call on a device looks up that array's device
+ * address with the device current (cudaGetSymbolAddress), so make the first
+ * call on each device before any stream capture.  All calls share the one
+ * array: calls that overlap on the GPU (concurrent streams, or host threads
+ * using the same device) race and must be serialised by the caller.  The call
+ * allocates nothing and frees nothing. */
+gs_status gs_loss_fwd_bwd_noalloc(const gs_camera *cams, int n_views, int feat_dim, const gs_images *img,
+                                  const gs_targets *tgt, const float *dec_W, const float *dec_b,
+                                  const gs_loss_params *lp, gs_image_grads_out *grad, float *d_dec_W,
+                                  float *d_dec_b, double *loss_out, float *mask_out, float *median_out,
+                                  gs_stream stream);
+
 /* Depth-adaptive scale regularisation (Eq. 12) over the 3n axis scales
  * s = exp(log_scales): mu, sigma = population mean and deviation (constants
  * for differentiation), L_big = mean of s > mu + 2 sigma, L_small = mean of

@@ -94,6 +94,9 @@ _SIGNATURES = {
     "gs_loss_fwd_bwd": (c_int, [_P(gs_camera), c_int, c_int, _P(gs_images), _P(gs_targets), c_void_p, c_void_p,
                                 _P(gs_loss_params), c_void_p, c_size_t, _P(gs_image_grads_out), c_void_p, c_void_p,
                                 c_void_p, c_void_p, c_void_p, c_void_p]),
+    "gs_loss_fwd_bwd_noalloc": (c_int, [_P(gs_camera), c_int, c_int, _P(gs_images), _P(gs_targets), c_void_p,
+                                        c_void_p, _P(gs_loss_params), _P(gs_image_grads_out), c_void_p, c_void_p,
+                                        c_void_p, c_void_p, c_void_p, c_void_p]),
     "gs_dsr": (c_int, [c_int64, c_void_p, c_float, c_float, c_void_p, c_size_t, c_void_p, c_void_p, c_void_p]),
     "gs_pose_step": (c_int, [c_int, c_void_p, c_void_p, c_void_p, c_int, _P(c_double), c_double, c_double,
                              c_double, c_void_p, c_void_p]),
@@ -151,5 +154,6 @@ gs_render_bwd = _wrap("gs_render_bwd")
 gs_project_bwd = _wrap("gs_project_bwd")
 gs_pose_grad = _wrap("gs_pose_grad")
 gs_loss_fwd_bwd = _wrap("gs_loss_fwd_bwd")
+gs_loss_fwd_bwd_noalloc = _wrap("gs_loss_fwd_bwd_noalloc")
 gs_dsr = _wrap("gs_dsr")
 gs_pose_step = _wrap("gs_pose_step")

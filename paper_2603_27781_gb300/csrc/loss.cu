@@ -14,6 +14,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "common.cuh"
 
@@ -604,4 +605,84 @@ extern "C" gs_status gs_pose_step(int n_views, const double *d_twist, double *T_
     pose_step_kernel<<<1, 64, 0, (cudaStream_t)stream>>>(n_views, d_twist, T_state, adam, bc1, bc2, lr[0], lr[1],
                                                          lr[2], lr[3], lr[4], lr[5], beta1, beta2, eps, pose_f32);
     return last_launch();
+}
+
+// ------------------------------------------------- allocation-free loss entry
+// Same computation as gs_loss_fwd_bwd for callers that cannot allocate device
+// memory: the scratch (median histograms of up to kNoAllocMaxViews views and the
+// per-block partials) lives in one file-scope device array that every GPU which
+// loads the library holds until the process exits.
+namespace gs {
+namespace {
+
+constexpr int kNoAllocMaxViews = 16;
+constexpr size_t kNoAllocHistBytes = sizeof(uint32_t) * 4 * 256 * kNoAllocMaxViews;          //    65,536
+constexpr size_t kNoAllocPartFBytes = sizeof(float) * (size_t)kLossBlocks * (kMaxK * 32 + kMaxK);  // 4,325,376
+constexpr size_t kNoAllocPartDBytes = sizeof(double) * (size_t)kLossBlocks * 3;                //    24,576
+constexpr size_t kNoAllocBytes = kNoAllocHistBytes + kNoAllocPartFBytes + kNoAllocPartDBytes;   // 4,415,488
+
+static __device__ __align__(256) unsigned char g_noalloc_loss_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 256;
+std::atomic<void *> g_noalloc_scratch_addr[kNoAllocMaxDevices];
+
+// Device address of the scratch array on the current device, looked up once per
+// device (host code only sees a host-side stand-in for the symbol).
+gs_status noalloc_scratch(char **out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GS_ERR_CUDA;
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return GS_ERR_UNSUPPORTED;
+    void *p = g_noalloc_scratch_addr[dev].load(std::memory_order_acquire);
+    if (!p) {
+        if (cudaGetSymbolAddress(&p, g_noalloc_loss_scratch) != cudaSuccess || !p) return GS_ERR_CUDA;
+        g_noalloc_scratch_addr[dev].store(p, std::memory_order_release);
+    }
+    *out = static_cast<char *>(p);
+    return GS_OK;
+}
+
+}  // namespace
+}  // namespace gs
+
+extern "C" gs_status gs_loss_fwd_bwd_noalloc(const gs_camera *cams, int n_views, int feat_dim, const gs_images *img,
+                                             const gs_targets *tgt, const float *dec_W, const float *dec_b,
+                                             const gs_loss_params *lp, gs_image_grads_out *grad, float *d_dec_W,
+                                             float *d_dec_b, double *loss_out, float *mask_out, float *median_out,
+                                             gs_stream stream) {
+    using namespace gs;
+    cudaStream_t st = (cudaStream_t)stream;
+    ViewTable vt;
+    if (!img || !tgt || !lp || !grad || !loss_out || !make_view_table(cams, n_views, 0, &vt)) return GS_ERR_ARG;
+    if (n_views > kNoAllocMaxViews) return GS_ERR_UNSUPPORTED;
+    if (!feat_dim_ok(feat_dim)) return GS_ERR_UNSUPPORTED;
+    if (lp->n_classes < 0 || lp->n_classes > kMaxK || (lp->mask_mode != 0 && lp->mask_mode != 1)) return GS_ERR_ARG;
+    if (!img->rgb || !img->depth || !img->sil || (feat_dim && !img->feat) || !tgt->rgb || !tgt->depth ||
+        !tgt->label || !grad->rgb || !grad->depth || !grad->sil || (feat_dim && !grad->feat))
+        return GS_ERR_ARG;
+    if (lp->n_classes > 0 && (!dec_W || !dec_b || !d_dec_W || !d_dec_b)) return GS_ERR_ARG;
+    char *w = nullptr;
+    gs_status s;
+    if ((s = noalloc_scratch(&w))) return s;
+    uint32_t *mh = reinterpret_cast<uint32_t *>(w);
+    float *part_f = reinterpret_cast<float *>(w + kNoAllocHistBytes);
+    double *part_d = reinterpret_cast<double *>(w + kNoAllocHistBytes + kNoAllocPartFBytes);
+    const int64_t P = vt.pix_off[n_views];
+    if (lp->mask_mode == 1) {
+        // the histograms keep the previous call's counts: clear them first
+        if ((s = cuda_status(cudaMemsetAsync(mh, 0, sizeof(uint32_t) * 4 * 256 * n_views, st)))) return s;
+        dim3 grid(loss_blocks_x(vt), n_views);
+        for (int pass = 0; pass < 4; ++pass)
+            median_hist_kernel<<<grid, 256, 0, st>>>(vt, pass, img->depth, tgt->depth, mh);
+        if ((s = last_launch())) return s;
+    }
+    LossP q{lp->color, lp->depth, lp->sem, lp->tau_obs, lp->mask_mode, lp->n_classes};
+#define GS_LOSS(DD)                                                                                              \
+    case DD:                                                                                                     \
+        return launch_loss<DD>(vt, q, img, tgt, dec_W, dec_b, P, mh, grad, part_f, part_d, d_dec_W, d_dec_b,     \
+                               loss_out, mask_out, median_out, st);
+    switch (feat_dim) {
+        GS_LOSS(0) GS_LOSS(4) GS_LOSS(8) GS_LOSS(16) GS_LOSS(32)
+        default: return GS_ERR_UNSUPPORTED;
+    }
+#undef GS_LOSS
 }

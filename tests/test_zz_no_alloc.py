@@ -1,0 +1,96 @@
+"""The allocation-free loss entry point gives the same results as the workspace one.
+
+gs_loss_fwd_bwd_noalloc exists for callers that cannot allocate device memory
+(graph capture in progress, a host application that owns every allocation, a
+binding without a device allocator): its scratch is a static device array
+inside the library.  Two calls in a row, with different data, check that the
+state the array keeps from the previous call (the median histograms) is
+cleared.  This file is collected last on purpose.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2603_27781_gb300 import _lib as L
+from paper_2603_27781_gb300 import raster, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib_built():
+    from paper_2603_27781_gb300 import build
+    build.build()
+    L.library()
+
+
+def _frames(seed, sizes, D=16, K=8):
+    g = synth.rng(seed)
+    cams = [synth.camera(w, h, 0.5 * w) for (w, h) in sizes]
+    P = sum(w * h for w, h in sizes)
+    img = dict(rgb=g.random((3, P)), depth=g.uniform(2, 5, P), sil=g.uniform(0.95, 1.0, P),
+               feat=g.standard_normal((D, P)))
+    tdepth = img["depth"] + g.normal(0, 0.05, P)
+    tdepth[g.random(P) < 0.05] = 0.0
+    tgt = dict(rgb=g.random((3, P)), depth=tdepth, label=g.integers(0, K, P).astype(np.uint8))
+    tgt["label"][g.random(P) < 0.05] = 255
+    dec = synth.decoder(K, D, seed=seed + 1)
+    return cams, img, tgt, dec
+
+
+def _run_both(seed, sizes, weights):
+    cams, img, tgt, dec = _frames(seed, sizes)
+    D, K = img["feat"].shape[0], dec.W.shape[0]
+    r = raster.Renderer(0, cams, D, 0, n_classes=K)
+    t32 = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32).cuda()
+    r.img_rgb.copy_(t32(img["rgb"])); r.img_depth.copy_(t32(img["depth"])); r.img_sil.copy_(t32(img["sil"]))
+    r.img_feat.copy_(t32(img["feat"]))
+    tg = dict(rgb=t32(tgt["rgb"]), depth=t32(tgt["depth"]), label=torch.as_tensor(tgt["label"]).cuda())
+    W, b = t32(dec.W), t32(dec.b)
+    r.loss(tg, W, b, weights)                                     # workspace entry point
+
+    out = dict(g_rgb=torch.zeros_like(r.g_rgb), g_depth=torch.zeros_like(r.g_depth),
+               g_sil=torch.zeros_like(r.g_sil), g_feat=torch.zeros_like(r.g_feat),
+               dW=torch.zeros_like(r.d_dec_W), db=torch.zeros_like(r.d_dec_b),
+               loss=torch.zeros_like(r.loss_out), mask=torch.zeros_like(r.mask),
+               median=torch.zeros_like(r.median))
+    p = lambda t: ctypes.c_void_p(t.data_ptr())
+    lp = L.gs_loss_params(weights.color, weights.depth, weights.sem, weights.mask_mode, weights.tau_obs, K)
+    tc = L.gs_targets(p(tg["rgb"]), p(tg["depth"]), p(tg["label"]))
+    gc = L.gs_image_grads(p(out["g_rgb"]), p(out["g_depth"]), p(out["g_sil"]), p(out["g_feat"]))
+    status = L.gs_loss_fwd_bwd_noalloc(r.cams_c, len(cams), D, ctypes.byref(r.images_c()), ctypes.byref(tc),
+                                       p(W), p(b), ctypes.byref(lp), ctypes.byref(gc), p(out["dW"]), p(out["db"]),
+                                       p(out["loss"]), p(out["mask"]), p(out["median"]),
+                                       ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert status == L.GS_OK, L.gs_strerror(status)
+    torch.cuda.synchronize()
+    pairs = [(out["g_rgb"], r.g_rgb), (out["g_depth"], r.g_depth), (out["g_sil"], r.g_sil),
+             (out["g_feat"], r.g_feat), (out["dW"], r.d_dec_W), (out["db"], r.d_dec_b), (out["loss"], r.loss_out),
+             (out["mask"], r.mask), (out["median"], r.median)]
+    for got, want in pairs:
+        np.testing.assert_allclose(got.cpu().numpy(), want.cpu().numpy(), rtol=1e-5, atol=1e-9)
+    return out
+
+
+def test_noalloc_loss_matches_workspace_entry_on_two_calls_in_a_row():
+    first = _run_both(71, [(64, 48), (40, 30)], raster.TRACKING)
+    second = _run_both(72, [(96, 40)], raster.TRACKING)          # different views, stale histograms cleared
+    assert first["median"][0].item() != second["median"][0].item()
+    _run_both(73, [(64, 48)], raster.MAPPING)
+
+
+def test_noalloc_loss_rejects_more_views_than_its_scratch_holds():
+    cams = [synth.camera(8, 8, 4.0)] * 17
+    r = raster.Renderer(0, cams, 0, 0, n_classes=1)
+    p = lambda t: ctypes.c_void_p(t.data_ptr())
+    lp = L.gs_loss_params(0.5, 1.0, 0.0, 1, 0.99, 0)
+    tg = dict(rgb=torch.zeros(3, r.P, device="cuda"), depth=torch.ones(r.P, device="cuda"),
+              label=torch.zeros(r.P, dtype=torch.uint8, device="cuda"))
+    tgt = L.gs_targets(p(tg["rgb"]), p(tg["depth"]), p(tg["label"]))
+    g = r.image_grads_c()
+    status = L.gs_loss_fwd_bwd_noalloc(r.cams_c, 17, 0, ctypes.byref(r.images_c()), ctypes.byref(tgt), None, None,
+                                       ctypes.byref(lp), ctypes.byref(g), None, None, p(r.loss_out), None, None,
+                                       None)
+    assert status == L.GS_ERR_UNSUPPORTED
