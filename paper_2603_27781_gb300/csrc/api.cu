@@ -68,7 +68,7 @@ WsLayout ws_layout(int64_t n, int n_views, int64_t capacity) {
     L.vn = vn;
     L.capacity = capacity;
     int64_t scan_n = vn > capacity ? vn : capacity;
-    int64_t nb1 = (scan_n + kScanBlock - 1) / kScanBlock + 1;
+    int64_t nb1 = (scan_n + 255) / 256 + 1;  // block sums of the 256-item emission blocks (the largest use)
     L.lb_tiles_depth = (int)((vn + kSortTile - 1) / kSortTile);
     L.lb_tiles_inst = (int)((capacity + kSortTile - 1) / kSortTile);
     size_t off = 0;

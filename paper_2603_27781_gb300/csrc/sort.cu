@@ -134,55 +134,76 @@ __global__ void __launch_bounds__(256) vis_compact_kernel(const int32_t *touched
 }
 
 // ------------------------------------------------------------ instance emission
-__global__ void __launch_bounds__(256) emit_reduce_kernel(const uint32_t *sorted_items, const int32_t *touched,
-                                                          const uint32_t *counters, uint32_t *block_sums) {
+constexpr int kEmitBlock = 256;  // sorted items per block of the emission kernels
+
+__global__ void __launch_bounds__(kEmitBlock) emit_reduce_kernel(const uint32_t *sorted_items,
+                                                                 const int32_t *touched, const uint32_t *counters,
+                                                                 uint32_t *block_sums) {
     __shared__ uint32_t s_warp[9];
-    int64_t count = counters[CTR_NVIS];
-    int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanIPT;
-    if ((int64_t)blockIdx.x * kScanBlock >= count) return;
-    uint32_t c = 0;
-#pragma unroll
-    for (int k = 0; k < kScanIPT; ++k)
-        if (base + k < count) c += (uint32_t)touched[sorted_items[base + k]];
+    const int64_t count = counters[CTR_NVIS];
+    const int64_t i = (int64_t)blockIdx.x * kEmitBlock + threadIdx.x;
+    if ((int64_t)blockIdx.x * kEmitBlock >= count) return;
+    const uint32_t c = i < count ? (uint32_t)touched[sorted_items[i]] : 0u;
     uint32_t tot;
     block_exclusive_scan(c, &tot, s_warp);
     if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
 }
 
-__global__ void __launch_bounds__(256) emit_kernel(ViewTable vt, const uint32_t *sorted_items, const int32_t *touched,
-                                                   const float4 *uvdo, const float4 *conic, const uint32_t *counters,
-                                                   const uint32_t *block_sums, int64_t capacity, uint32_t *tile_keys,
-                                                   uint32_t *inst_vals) {
+// One thread per sorted item computes its instance offset; each warp then
+// writes the instances of its 32 items cooperatively, 32 consecutive instances
+// per round (the owner of instance q is found by a 5-step binary search over
+// the lanes' offsets), so every store is coalesced and long items are spread
+// over the warp.
+__global__ void __launch_bounds__(kEmitBlock) emit_kernel(ViewTable vt, const uint32_t *sorted_items,
+                                                          const int32_t *touched, const float4 *uvdo,
+                                                          const float4 *conic, const uint32_t *counters,
+                                                          const uint32_t *block_sums, int64_t capacity,
+                                                          uint32_t *tile_keys, uint32_t *inst_vals) {
     __shared__ uint32_t s_warp[9];
-    int64_t count = counters[CTR_NVIS];
-    if ((int64_t)blockIdx.x * kScanBlock >= count) return;
-    int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanIPT;
-    uint32_t item[kScanIPT];
-    uint32_t c = 0;
-#pragma unroll
-    for (int k = 0; k < kScanIPT; ++k) {
-        item[k] = base + k < count ? sorted_items[base + k] : 0xffffffffu;
-        c += item[k] != 0xffffffffu ? (uint32_t)touched[item[k]] : 0u;
+    const int64_t count = counters[CTR_NVIS];
+    if ((int64_t)blockIdx.x * kEmitBlock >= count) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * kEmitBlock + threadIdx.x;
+    uint32_t item = 0, c = 0;
+    int x0 = 0, y0 = 0, w = 1, tx = 1;
+    uint32_t tb = 0;
+    if (i < count) {
+        item = sorted_items[i];
+        c = (uint32_t)touched[item];
+        const int v = (int)(item / (uint32_t)vt.n);
+        const float4 rec = uvdo[item];
+        int x1, y1;
+        tile_rect(rec.x, rec.y, (int)conic[item].w, vt.TX[v], vt.TY[v], x0, y0, x1, y1);
+        w = max(x1 - x0, 1);
+        tx = vt.TX[v];
+        tb = (uint32_t)vt.tile_off[v];
     }
     uint32_t tot;
-    int64_t off = (int64_t)block_sums[blockIdx.x] + block_exclusive_scan(c, &tot, s_warp);
-#pragma unroll 1
-    for (int k = 0; k < kScanIPT; ++k) {
-        if (item[k] == 0xffffffffu) continue;
-        int v = (int)(item[k] / (uint32_t)vt.n);
-        float4 rec = uvdo[item[k]];
-        int r = (int)conic[item[k]].w;
-        int x0, y0, x1, y1;
-        tile_rect(rec.x, rec.y, r, vt.TX[v], vt.TY[v], x0, y0, x1, y1);
-        uint32_t tb = (uint32_t)vt.tile_off[v];
-        for (int y = y0; y < y1; ++y)
-            for (int x = x0; x < x1; ++x) {
-                if (off < capacity) {
-                    tile_keys[off] = tb + (uint32_t)(y * vt.TX[v] + x);
-                    inst_vals[off] = item[k];
-                }
-                ++off;
-            }
+    const uint32_t excl = block_sums[blockIdx.x] + block_exclusive_scan(c, &tot, s_warp);
+    const uint32_t wbase = __shfl_sync(0xffffffffu, excl, 0);
+    const uint32_t wtotal = __shfl_sync(0xffffffffu, excl + c, 31) - wbase;
+    const uint32_t rel = excl - wbase;
+    for (uint32_t q0 = 0; q0 < wtotal; q0 += 32) {
+        const uint32_t q = q0 + lane;
+        int owner = 0;
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+            const int cand = owner + step;
+            const uint32_t rc = __shfl_sync(0xffffffffu, rel, cand & 31);
+            if (cand < 32 && rc <= q) owner = cand;
+        }
+        const uint32_t o_rel = __shfl_sync(0xffffffffu, rel, owner);
+        const uint32_t o_item = __shfl_sync(0xffffffffu, item, owner);
+        const int o_x0 = __shfl_sync(0xffffffffu, x0, owner), o_y0 = __shfl_sync(0xffffffffu, y0, owner);
+        const int o_w = __shfl_sync(0xffffffffu, w, owner), o_tx = __shfl_sync(0xffffffffu, tx, owner);
+        const uint32_t o_tb = __shfl_sync(0xffffffffu, tb, owner);
+        const int64_t off = (int64_t)wbase + q;
+        if (q < wtotal && off < capacity) {
+            const int k = (int)(q - o_rel);
+            const int ky = k / o_w, kx = k - ky * o_w;
+            tile_keys[off] = o_tb + (uint32_t)((o_y0 + ky) * o_tx + o_x0 + kx);
+            inst_vals[off] = o_item;
+        }
     }
 }
 
@@ -285,24 +306,35 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint32_t *
         st_relaxed(my, kFlagPre | cnt);
     } else {
         st_relaxed(my, kFlagAgg | cnt);
+        // walk back over earlier tiles, reading 8 of their flags at a time; spin
+        // (bounded) only on a tile that has not published its count yet
+        constexpr int kWin = 8;
         int64_t t = (int64_t)tile - 1;
-        while (t >= 0) {
-            const uint32_t *p = lookback + (size_t)t * 256 + d;
-            uint32_t vv = ld_relaxed(p);
-            int spin = 0;
-            while ((vv & ~kValMask) == 0u) {
-                if (++spin > kSpinLimit) break;
-                if (spin > 64) __nanosleep(64);
-                vv = ld_relaxed(p);
+        bool done = false, timeout = false;
+        while (!done && t >= 0) {
+            uint32_t w[kWin];
+#pragma unroll
+            for (int i = 0; i < kWin; ++i) w[i] = t - i >= 0 ? ld_relaxed(lookback + (size_t)(t - i) * 256 + d) : 0u;
+#pragma unroll
+            for (int i = 0; i < kWin; ++i) {
+                if (done) break;
+                if (t - i < 0) { done = true; break; }
+                uint32_t vv = w[i];
+                if ((vv & ~kValMask) == 0u) {
+                    const uint32_t *pp = lookback + (size_t)(t - i) * 256 + d;
+                    int spin = 0;
+                    while ((vv & ~kValMask) == 0u && spin < kSpinLimit) {
+                        if (++spin > 64) __nanosleep(64);
+                        vv = ld_relaxed(pp);
+                    }
+                    if ((vv & ~kValMask) == 0u) { timeout = true; done = true; break; }
+                }
+                prefix += vv & kValMask;
+                if ((vv & ~kValMask) == kFlagPre) done = true;
             }
-            if ((vv & ~kValMask) == 0u) {
-                set_status(status, GS_ERR_TIMEOUT);
-                break;
-            }
-            prefix += vv & kValMask;
-            if ((vv & ~kValMask) == kFlagPre) break;
-            --t;
+            t -= kWin;
         }
+        if (timeout) set_status(status, GS_ERR_TIMEOUT);
         st_relaxed(my, kFlagPre | (prefix + cnt));
     }
     s_glob[d] = s_dbase[d] + prefix;
@@ -429,10 +461,11 @@ extern "C" gs_status gs_bin_sort(int64_t n, const gs_projected *proj, const gs_c
     // the emitted values go where the final pass must not land: out->vals ends the sort
     uint32_t *emit_vals = (tile_passes % 2 == 0) ? out->vals : tv_b;
     uint32_t *other_vals = (tile_passes % 2 == 0) ? tv_b : out->vals;
-    emit_reduce_kernel<<<nb, 256, 0, st>>>(sorted_items, proj->tiles_touched, counters, block_sums);
-    blocksum_scan_kernel<<<1, 1024, 0, st>>>(block_sums, counters + CTR_NVIS, 0, kScanBlock, counters, CTR_MRAW, CTR_M,
+    const int nbe = ceil_div(vn, kEmitBlock);
+    emit_reduce_kernel<<<nbe, kEmitBlock, 0, st>>>(sorted_items, proj->tiles_touched, counters, block_sums);
+    blocksum_scan_kernel<<<1, 1024, 0, st>>>(block_sums, counters + CTR_NVIS, 0, kEmitBlock, counters, CTR_MRAW, CTR_M,
                                              out->capacity, out->n_inst, out->status);
-    emit_kernel<<<nb, 256, 0, st>>>(vt, sorted_items, proj->tiles_touched, uvdo, conic, counters, block_sums,
+    emit_kernel<<<nbe, kEmitBlock, 0, st>>>(vt, sorted_items, proj->tiles_touched, uvdo, conic, counters, block_sums,
                                     out->capacity, tk_a, emit_vals);
     if ((s = last_launch())) return s;
     if (out->capacity == 0) return GS_OK;
