@@ -140,7 +140,11 @@ typedef struct {
  * rgb [3,P], depth [P], sil [P] (cumulative opacity, Eq. 10), feat [D,P],
  * T_final [P] (transmittance after the last blended splat), n_contrib [P]
  * (1-based position in the tile list of the last blended splat) and, if not
- * NULL, n_blended [P] (number of splats blended into the pixel). */
+ * NULL, n_blended [P] (number of splats blended into the pixel) and
+ * blend_mask: u32 [8][capacity / 32 + 1] bit planes, one per 8x4 pixel group
+ * g = (y % 16 / 4) * 2 + (x % 16 / 8) of a tile, bit i of plane g set when a
+ * pixel of that group of instance i's tile blended instance i.  gs_render_bwd
+ * uses the mask, when given, to skip instances no pixel of a group blended. */
 typedef struct {
     float *rgb;
     float *depth;
@@ -149,6 +153,7 @@ typedef struct {
     float *T_final;
     int32_t *n_contrib;
     int32_t *n_blended;
+    uint32_t *blend_mask;
 } gs_images;
 
 /* Gradients of the loss w.r.t. the rendered images, same layout as gs_images.

@@ -46,7 +46,8 @@ class gs_binning(Structure):
 
 class gs_images(Structure):
     _fields_ = [("rgb", c_void_p), ("depth", c_void_p), ("sil", c_void_p), ("feat", c_void_p),
-                ("T_final", c_void_p), ("n_contrib", c_void_p), ("n_blended", c_void_p)]
+                ("T_final", c_void_p), ("n_contrib", c_void_p), ("n_blended", c_void_p),
+                ("blend_mask", c_void_p)]
 
 
 class gs_splat_grads(Structure):

@@ -33,6 +33,17 @@ template <int NP> struct Shape {
     }
 };
 
+// Blend-mask groups: fixed 8x4 pixel groups g = (ly / 4) * 2 + lx / 8 of a tile.
+// Warp w of Shape<NP> covers groups [w * NP, (w + 1) * NP); lanes_of_group
+// returns which lanes own pixels of the j-th of them.
+constexpr int kGroups = 8;
+template <int NP> __device__ __forceinline__ uint32_t lanes_of_group(int j) {
+    if (NP == 1) return 0xffffffffu;
+    if (NP == 2) return j == 0 ? 0x0f0f0f0fu : 0xf0f0f0f0u;
+    const uint32_t m[4] = {0x00000f0fu, 0x0000f0f0u, 0x0f0f0000u, 0xf0f00000u};
+    return m[j];
+}
+
 // Colour of Gaussian g with the splat depth in the fourth lane (both are blended values).
 template <typename T>
 __device__ __forceinline__ float4 load_rgbd(const T *rgb, int64_t g, float depth) {

@@ -66,6 +66,8 @@ struct BwdArgs {
     const float *g_rgb, *g_depth, *g_sil, *g_feat;
     float4 *acc_uvod, *acc_conic, *acc_rgb;
     float *d_feat;
+    const uint32_t *bmask;  // blend-mask planes from the forward (NULL: scan every splat)
+    int64_t bm_stride;
 };
 
 template <int D, int NP, bool MAP, typename RT, typename FT>
@@ -153,11 +155,11 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS) raster_bwd_kernel(ViewTabl
         for (int i = tid; i < cnt * LY::ROW; i += NT) s_acc[i] = 0.f;
         __syncthreads();
 
-        for (int k = cnt - 1; k >= 0; --k) {
+        auto process = [&](const int k) {
             const int pos = b_start + k;
-            if (!__any_sync(0xffffffffu, pos < my_max)) continue;
+            if (!__any_sync(0xffffffffu, pos < my_max)) return;
             const SplatGeo s = s_geo[k];
-            if (!reaches_box(s.u, s.v, s_ext[k], bcx, bcy, hx, hy)) continue;
+            if (!reaches_box(s.u, s.v, s_ext[k], bcx, bcy, hx, hy)) return;
             PairEval e[NP];
             bool contrib[NP], any = false;
 #pragma unroll
@@ -166,7 +168,7 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS) raster_bwd_kernel(ViewTabl
                 contrib[p] = pos < last[p] && !e[p].skip;
                 any |= contrib[p];
             }
-            if (!__any_sync(0xffffffffu, any)) continue;
+            if (!__any_sync(0xffffffffu, any)) return;
 
             float val[LY::C0 + LY::C1];
 #pragma unroll
@@ -231,6 +233,25 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS) raster_bwd_kernel(ViewTabl
                 const int idx = lane & (LY::C1 - 1);
                 if (lane < LY::C1 && idx < LY::R1 && r != 0.f) atomicAdd(&s_acc[k * LY::ROW + LY::C0 + idx], r);
             }
+                };
+        if (A.bmask) {
+            // only the instances some pixel of the warp's groups blended, back to front
+            const int64_t lo_i = (int64_t)start + b_start, hi_i = (int64_t)start + b_end;
+            for (int64_t wi = (hi_i - 1) >> 5; wi >= (lo_i >> 5); --wi) {
+                uint32_t m = 0u;
+#pragma unroll
+                for (int j = 0; j < NP; ++j) m |= A.bmask[(int64_t)((tid >> 5) * NP + j) * A.bm_stride + wi];
+                const int64_t base = wi << 5;
+                if (base < lo_i) m &= ~0u << (int)(lo_i - base);
+                if (hi_i - base < 32) m &= (1u << (int)(hi_i - base)) - 1u;
+                while (m) {
+                    const int bit = 31 - __clz(m);
+                    m &= ~(1u << bit);
+                    process((int)(base + bit - lo_i));
+                }
+            }
+        } else {
+            for (int k = cnt - 1; k >= 0; --k) process(k);
         }
         __syncthreads();
         // one set of vector atomics per (tile, splat)

@@ -14,7 +14,7 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS) raster_fwd_kernel(
     ViewTable vt, Params prm, const float4 *__restrict__ uvdo, const float2 *__restrict__ uv_lo,
     const float4 *__restrict__ conic, const RT *__restrict__ rgb, const FT *__restrict__ feat,
     const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges, int64_t P, float *o_rgb, float *o_depth,
-    float *o_sil, float *o_feat, float *o_T, int32_t *o_nc, int32_t *o_nb) {
+    float *o_sil, float *o_feat, float *o_T, int32_t *o_nc, int32_t *o_nb, uint32_t *bmask, int64_t bm_stride) {
     using SH = Shape<NP>;
     constexpr int NT = SH::THREADS;
     constexpr int D4 = D / 4, DD = D > 0 ? D : 1;
@@ -59,6 +59,21 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS) raster_fwd_kernel(
         for (int p = 0; p < NP; ++p) a = a && done[p];
         return a;
     };
+    // blend-mask bits of the warp's NP groups for the current 32-instance word
+    const int warp = tid >> 5, lane = tid & 31;
+    uint32_t macc[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) macc[j] = 0u;
+    int64_t mword = -1;
+    auto flush = [&]() {
+        if (mword >= 0 && lane == 0) {
+#pragma unroll
+            for (int j = 0; j < NP; ++j)
+                if (macc[j]) atomicOr(&bmask[(int64_t)(warp * NP + j) * bm_stride + mword], macc[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < NP; ++j) macc[j] = 0u;
+    };
 
     for (uint32_t b0 = start; b0 < end; b0 += kBatch) {
         if (__syncthreads_count(!all_done()) == 0) break;
@@ -79,7 +94,7 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS) raster_fwd_kernel(
         __syncthreads();
         const int nb = min((uint32_t)kBatch, end - b0);
         for (int k = 0; k < nb; ++k) {
-            if (all_done()) break;
+            if (__all_sync(0xffffffffu, all_done())) break;
             const SplatGeo s = s_geo[k];
             if (!reaches_box(s.u, s.v, s_ext[k], bcx, bcy, hx, hy)) continue;
             // evaluate all of the thread's pixels first (independent chains), then decide
@@ -106,6 +121,19 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS) raster_fwd_kernel(
                 blended[p] += b ? 1 : 0;
                 any = any || b;
             }
+            if (bmask) {
+                const uint32_t bal = __ballot_sync(0xffffffffu, any);
+                if (bal) {
+                    const int64_t inst = (int64_t)b0 + k;
+                    if ((inst >> 5) != mword) {
+                        flush();
+                        mword = inst >> 5;
+                    }
+#pragma unroll
+                    for (int j = 0; j < NP; ++j)
+                        if (bal & lanes_of_group<NP>(j)) macc[j] |= 1u << (inst & 31);
+                }
+            }
             if (!any) continue;
             const float4 c = s_rgbd[k];
 #pragma unroll
@@ -130,6 +158,7 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS) raster_fwd_kernel(
             }
         }
     }
+    if (bmask) flush();
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
         if (!inside[p]) continue;
@@ -156,7 +185,7 @@ gs_status launch(const ViewTable &vt, const Params &prm, const gs_gaussians *g, 
         vt, prm, reinterpret_cast<const float4 *>(proj->uvdo), reinterpret_cast<const float2 *>(proj->uv_lo),
         reinterpret_cast<const float4 *>(proj->conic), static_cast<const RT *>(g->rgb),
         static_cast<const FT *>(g->feat), bins->vals, bins->ranges, P, out->rgb, out->depth, out->sil, out->feat,
-        out->T_final, out->n_contrib, out->n_blended);
+        out->T_final, out->n_contrib, out->n_blended, out->blend_mask, bins->capacity / 32 + 1);
     return last_launch();
 }
 
@@ -199,6 +228,11 @@ extern "C" gs_status gs_render_fwd(const gs_gaussians *g, const gs_projected *pr
     }
     if (g->feat_dim && (reinterpret_cast<uintptr_t>(g->feat) & 15)) return GS_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
+    if (out->blend_mask) {
+        const gs_status s = cuda_status(cudaMemsetAsync(
+            out->blend_mask, 0, sizeof(uint32_t) * kGroups * (size_t)(bins->capacity / 32 + 1), st));
+        if (s) return s;
+    }
     const int np = prm.fwd_np ? prm.fwd_np : default_fwd_np(g->feat_dim);
     if (g->rgb_dtype == GS_F16) {
         if (g->feat_dim == 16) return by_np<16, __half, __nv_bfloat16>(np, vt, prm, g, proj, bins, out, st);

@@ -146,6 +146,8 @@ class Renderer:
         self.img_nc = torch.zeros(P, dtype=i32, device=dev)
         self.img_nb = torch.zeros(P, dtype=i32, device=dev)
         self.count_blended = False
+        self.blend_mask = torch.zeros(8 * (max(capacity, 1) // 32 + 1), dtype=i32, device=dev)
+        self.use_blend_mask = True
         self.sg_uvod = torch.zeros(V * n, 4, dtype=f32, device=dev)
         self.sg_conic = torch.zeros(V * n, 4, dtype=f32, device=dev)
         self.sg_rgb = torch.zeros(n, 4, dtype=f32, device=dev)
@@ -194,7 +196,8 @@ class Renderer:
     def images_c(self):
         return L.gs_images(_p(self.img_rgb), _p(self.img_depth), _p(self.img_sil),
                            _p(self.img_feat) if self.feat_dim else None, _p(self.img_T), _p(self.img_nc),
-                           _p(self.img_nb) if self.count_blended else None)
+                           _p(self.img_nb) if self.count_blended else None,
+                           _p(self.blend_mask) if self.use_blend_mask else None)
 
     def splat_grads_c(self):
         return L.gs_splat_grads(_p(self.sg_uvod), _p(self.sg_conic), _p(self.sg_rgb))

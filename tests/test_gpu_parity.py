@@ -181,6 +181,24 @@ def test_launch_shapes_agree(np_):
         C.assert_grad_close(name, b.cpu().numpy(), a.cpu().numpy(), 1e-5)
 
 
+def test_blend_mask_skips_only_non_contributing_splats():
+    """The backward with the forward's blend mask equals the full scan."""
+    gs, cam, _ = C.room_case(20000, 16, 330, 190, 165.0)
+    field, r = C.gpu_forward(gs, cam, C.params_pair()[0])
+    g = C.random_image_grads(r.P, 16, 8)
+    r.g_rgb.copy_(torch.as_tensor(g["rgb"])); r.g_depth.copy_(torch.as_tensor(g["depth"]))
+    r.g_sil.copy_(torch.as_tensor(g["sil"])); r.g_feat.copy_(torch.as_tensor(g["feat"]))
+    outs = []
+    for use_mask in (True, False):
+        r.use_blend_mask = use_mask
+        r.forward(field)
+        r.backward(field, L.GS_GRAD_MAP | L.GS_GRAD_POSE)
+        outs.append([t.clone() for t in (r.d_means, r.d_quats, r.d_log_scales, r.d_logits, r.d_rgb, r.d_feat,
+                                         r.d_twist)])
+    for a, b in zip(*outs):
+        C.assert_grad_close("masked", a.cpu().numpy(), b.cpu().numpy(), 1e-5)
+
+
 def test_autotuner_picks_a_supported_shape():
     from paper_2603_27781_gb300 import autotune
     gs, cam, _ = C.room_case(20000, 16, 330, 190, 165.0)
