@@ -3,14 +3,22 @@
 // record per thread load) and read back as broadcasts; a warp skips a splat
 // whose alpha >= alpha_min region misses its pixel box; every pixel walks the
 // rest front to back and stops at the T_min threshold; the CTA leaves as soon
-// as all of its pixels are done.
+// as all of its pixels are done.  With a blend mask, each warp also records, per
+// 8x4 pixel group and 32-instance word, which splats any pixel of it blended.
 #include "raster.cuh"
 
 namespace gs {
 namespace {
 
+// Resident CTAs per SM the register allocation must allow, per feature width and
+// pixels per thread: the blend loop is issue-bound, so warps resident matter
+// more than the few values ptxas would otherwise keep live across the mask flush.
+constexpr int fwd_min_blocks(int D, int NP) {
+    return NP == 1 ? (D == 0 ? 8 : D <= 4 ? 6 : D <= 16 ? 5 : 3) : NP == 2 ? (D <= 16 ? 6 : 4) : 6;
+}
+
 template <int D, int NP, typename RT, typename FT>
-__global__ void __launch_bounds__(Shape<NP>::THREADS) raster_fwd_kernel(
+__global__ void __launch_bounds__(Shape<NP>::THREADS, fwd_min_blocks(D, NP)) raster_fwd_kernel(
     ViewTable vt, Params prm, const float4 *__restrict__ uvdo, const float2 *__restrict__ uv_lo,
     const float4 *__restrict__ conic, const RT *__restrict__ rgb, const FT *__restrict__ feat,
     const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges, int64_t P, float *o_rgb, float *o_depth,
@@ -59,27 +67,28 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS) raster_fwd_kernel(
         for (int p = 0; p < NP; ++p) a = a && done[p];
         return a;
     };
-    // blend-mask bits of the warp's NP groups for the current 32-instance word
+    // blend-mask bits: batches start on 32-instance boundaries, so each 32-splat
+    // chunk of a batch is one word of the mask; a lane ORs "one of my pixels
+    // blended splat k" into a register and the warp combines the lanes of each
+    // of its NP groups at the end of the chunk
     const int warp = tid >> 5, lane = tid & 31;
-    uint32_t macc[NP];
+    auto flush = [&](uint32_t lbits, uint32_t word_idx) {
 #pragma unroll
-    for (int j = 0; j < NP; ++j) macc[j] = 0u;
-    int64_t mword = -1;
-    auto flush = [&]() {
-        if (mword >= 0 && lane == 0) {
-#pragma unroll
-            for (int j = 0; j < NP; ++j)
-                if (macc[j]) atomicOr(&bmask[(int64_t)(warp * NP + j) * bm_stride + mword], macc[j]);
+        for (int j = 0; j < NP; ++j) {
+            const uint32_t mine = (lanes_of_group<NP>(j) >> lane) & 1u ? lbits : 0u;
+            const uint32_t word = __reduce_or_sync(0xffffffffu, mine);
+            if (lane == 0 && word) atomicOr(&bmask[(int64_t)(warp * NP + j) * bm_stride + word_idx], word);
         }
-#pragma unroll
-        for (int j = 0; j < NP; ++j) macc[j] = 0u;
     };
 
-    for (uint32_t b0 = start; b0 < end; b0 += kBatch) {
+    bool finished = false;
+    // every warp stays in the batch loop (it stages splats and meets the CTA
+    // barriers); a warp whose pixels are all done only skips the splat loop
+    for (uint32_t b0 = start & ~31u; b0 < end; b0 += kBatch) {
         if (__syncthreads_count(!all_done()) == 0) break;
         for (int i = tid; i < kBatch; i += NT) {
             const uint32_t j = b0 + i;
-            if (j < end) {
+            if (j >= start && j < end) {
                 const uint32_t item = vals[j];
                 const int64_t g = (int64_t)item - voff;
                 const float4 a = uvdo[item];
@@ -92,73 +101,65 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS) raster_fwd_kernel(
             }
         }
         __syncthreads();
+        const int k_lo = b0 < start ? (int)(start - b0) : 0;
         const int nb = min((uint32_t)kBatch, end - b0);
-        for (int k = 0; k < nb; ++k) {
-            if (__all_sync(0xffffffffu, all_done())) break;
-            const SplatGeo s = s_geo[k];
-            if (!reaches_box(s.u, s.v, s_ext[k], bcx, bcy, hx, hy)) continue;
-            // evaluate all of the thread's pixels first (independent chains), then decide
-            float al[NP];
-            bool ok[NP];
-#pragma unroll
-            for (int p = 0; p < NP; ++p) {
-                const PairEval e = eval_pair(s, pxc[p], pyc[p], prm.alpha_min, prm.alpha_max);
-                al[p] = e.alpha;
-                ok[p] = !done[p] && !e.skip;
-            }
-            float wgt[NP];
-            bool any = false;
-            const int pos = (int)(b0 - start) + k + 1;
-#pragma unroll
-            for (int p = 0; p < NP; ++p) {
-                const float Tn = T[p] * (1.f - al[p]);
-                const bool stop = ok[p] && Tn < prm.T_min;
-                const bool b = ok[p] && !stop;
-                done[p] = done[p] || stop;
-                wgt[p] = b ? al[p] * T[p] : 0.f;
-                T[p] = b ? Tn : T[p];
-                last[p] = b ? pos : last[p];
-                blended[p] += b ? 1 : 0;
-                any = any || b;
-            }
-            if (bmask) {
-                const uint32_t bal = __ballot_sync(0xffffffffu, any);
-                if (bal) {
-                    const int64_t inst = (int64_t)b0 + k;
-                    if ((inst >> 5) != mword) {
-                        flush();
-                        mword = inst >> 5;
-                    }
-#pragma unroll
-                    for (int j = 0; j < NP; ++j)
-                        if (bal & lanes_of_group<NP>(j)) macc[j] |= 1u << (inst & 31);
-                }
-            }
-            if (!any) continue;
-            const float4 c = s_rgbd[k];
-#pragma unroll
-            for (int p = 0; p < NP; ++p) {
-                const float w = wgt[p];
-                ar[p] = fmaf(w, c.x, ar[p]);
-                ag[p] = fmaf(w, c.y, ag[p]);
-                ab[p] = fmaf(w, c.z, ab[p]);
-                ad[p] = fmaf(w, c.w, ad[p]);
-                as[p] += w;
-            }
-#pragma unroll
-            for (int q = 0; q < D4; ++q) {
-                const float4 f = s_feat[k * D4 + q];
+        for (int c0 = k_lo & ~31; c0 < nb && !finished; c0 += 32) {
+            uint32_t lbits = 0u;
+            const int k_end = min(c0 + 32, nb);
+            for (int k = max(c0, k_lo); k < k_end; ++k) {
+                if (__all_sync(0xffffffffu, all_done())) { finished = true; break; }
+                const SplatGeo s = s_geo[k];
+                if (!reaches_box(s.u, s.v, s_ext[k], bcx, bcy, hx, hy)) continue;
+                float al[NP];
+                bool ok[NP];
 #pragma unroll
                 for (int p = 0; p < NP; ++p) {
-                    af[p][4 * q] = fmaf(wgt[p], f.x, af[p][4 * q]);
-                    af[p][4 * q + 1] = fmaf(wgt[p], f.y, af[p][4 * q + 1]);
-                    af[p][4 * q + 2] = fmaf(wgt[p], f.z, af[p][4 * q + 2]);
-                    af[p][4 * q + 3] = fmaf(wgt[p], f.w, af[p][4 * q + 3]);
+                    const PairEval e = eval_pair(s, pxc[p], pyc[p], prm.alpha_min, prm.alpha_max);
+                    al[p] = e.alpha;
+                    ok[p] = !done[p] && !e.skip;
+                }
+                float wgt[NP];
+                bool any = false;
+                const int pos = (int)(b0 - start) + k + 1;
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    const float Tn = T[p] * (1.f - al[p]);
+                    const bool stop = ok[p] && Tn < prm.T_min;
+                    const bool b = ok[p] && !stop;
+                    done[p] = done[p] || stop;
+                    wgt[p] = b ? al[p] * T[p] : 0.f;
+                    T[p] = b ? Tn : T[p];
+                    last[p] = b ? pos : last[p];
+                    blended[p] += b ? 1 : 0;
+                    any = any || b;
+                }
+                lbits |= (any ? 1u : 0u) << (k & 31);
+                if (!any) continue;
+                const float4 c = s_rgbd[k];
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    const float w = wgt[p];
+                    ar[p] = fmaf(w, c.x, ar[p]);
+                    ag[p] = fmaf(w, c.y, ag[p]);
+                    ab[p] = fmaf(w, c.z, ab[p]);
+                    ad[p] = fmaf(w, c.w, ad[p]);
+                    as[p] += w;
+                }
+#pragma unroll
+                for (int q = 0; q < D4; ++q) {
+                    const float4 f = s_feat[k * D4 + q];
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) {
+                        af[p][4 * q] = fmaf(wgt[p], f.x, af[p][4 * q]);
+                        af[p][4 * q + 1] = fmaf(wgt[p], f.y, af[p][4 * q + 1]);
+                        af[p][4 * q + 2] = fmaf(wgt[p], f.z, af[p][4 * q + 2]);
+                        af[p][4 * q + 3] = fmaf(wgt[p], f.w, af[p][4 * q + 3]);
+                    }
                 }
             }
+            if (bmask) flush(lbits, (b0 + c0) >> 5);
         }
     }
-    if (bmask) flush();
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
         if (!inside[p]) continue;
