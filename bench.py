@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--form-steps", type=int, default=10)
     # smaller scenes for profiling captures only (the benchmark line is the default workload)
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--width", type=int, default=None)
@@ -192,6 +194,121 @@ def fwd_bwd_flops(evaluated, blended, D):
     return evaluated * eval_pair + blended * fwd_blend, evaluated * eval_pair + blended * bwd_blend
 
 
+class FormJob:
+    """One fwd+bwd step of the whole path over a set of views (the headline step's
+    calls: projection, binning, forward blend, losses, backward, pose twist, DSR and
+    pose step), with its own renderer, targets and pose state."""
+
+    def __init__(self, field, cams, frames, dec, dev, k):
+        import torch
+        from paper_2603_27781_gb300 import _lib as L
+        from paper_2603_27781_gb300 import raster
+        self.L, self.raster, self.field = L, raster, field
+        self.r = raster.fit_capacity(field, cams, field.feat_dim, margin=1.3, n_classes=k, device=dev)
+        cat = lambda xs: torch.as_tensor(np.ascontiguousarray(np.concatenate(xs, axis=-1))).to(dev)
+        self.targets = dict(rgb=cat([f.rgb.reshape(3, -1) for f in frames]),
+                            depth=cat([f.depth.ravel() for f in frames]),
+                            label=cat([f.label.ravel() for f in frames]))
+        self.W, self.b = torch.as_tensor(dec.W).to(dev), torch.as_tensor(dec.b).to(dev)
+        V = len(cams)
+        self.T_state = torch.as_tensor(np.stack([c.T_cw.reshape(16) for c in cams]), dtype=torch.float64).to(dev)
+        self.adam = torch.zeros(V * 12 + 1, dtype=torch.float64, device=dev)
+        self.pose_f32 = torch.zeros(V, 16, dtype=torch.float32, device=dev)
+        self.mode = L.GS_GRAD_MAP | L.GS_GRAD_POSE
+        self.w = raster.MAPPING
+
+    def tune(self):
+        from paper_2603_27781_gb300 import autotune
+        r = self.r
+        r.forward(self.field)
+        r.loss(self.targets, self.W, self.b, self.w)
+        tuned, _ = autotune.tune_blend(r, self.field, self.mode)
+        return tuned
+
+    def step(self):
+        r, f, w = self.r, self.field, self.w
+        r.project(f)
+        r.bin_sort()
+        r.render_fwd(f)
+        r.loss(self.targets, self.W, self.b, w)
+        r.render_bwd(f, self.mode)
+        r.project_bwd(f, self.mode)
+        r.pose_grad()
+        r.dsr(f, w.big, w.small)
+        r.pose_step(self.T_state, self.adam, 0, pose_f32=self.pose_f32)
+
+
+def time_graph(jobs, steps, flush):
+    """Captures one step of every job, in order, in one CUDA graph and times replays
+    (L2 flushed between them, outside the events).  Returns ms per replay."""
+    import torch
+    cur = torch.cuda.current_stream()
+    side = torch.cuda.Stream()
+    side.wait_stream(cur)
+    with torch.cuda.stream(side):
+        for j in jobs:
+            j.step()
+    cur.wait_stream(side)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for j in jobs:
+            j.step()
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    for j in jobs:
+        if j.r.status() != 0:
+            raise RuntimeError(f"binning status {j.r.status()}")
+    ms = []
+    for k in range(steps):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(cur)
+        g.replay()
+        e1.record(cur)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    del g
+    return float(np.mean(ms))
+
+
+def run_forms(args, gs, dec, dev, flush, batch=8):
+    """The batched and reduced-precision forms against the plain one, on the same
+    keyframes: `batch` poses drawn from the loop through the room, 1200x680, each
+    form's step graph-captured and its blend launch shape autotuned.  Frames/s =
+    frames per step / time per step."""
+    import torch
+    from paper_2603_27781_gb300 import raster, synth
+    room = synth.make_room(synth.SEED_SCENE)
+    loop = synth.keyframe_loop(room=room)
+    cams = [synth.camera(WORKLOAD["width"], WORKLOAD["height"], WORKLOAD["fx"], T_cw=loop[i])
+            for i in synth.draw_keyframes(batch)]
+    frames = [synth.raycast_room(room, c) for c in cams]
+    f32 = raster.Field.from_numpy(gs, dev)
+    half = raster.Field.from_numpy(gs, dev, rgb_dtype=torch.float16, feat_dtype=torch.bfloat16)
+    out = {"keyframes": f"{batch} poses drawn from the 200-pose loop (seed {synth.SEED_KEYFRAMES}), "
+                        f"{WORKLOAD['width']}x{WORKLOAD['height']} fx={WORKLOAD['fx']:g}",
+           "timing": "one CUDA graph per form, replays timed with CUDA events, L2 flushed between replays"}
+    k = WORKLOAD["k"]
+    specs = [("single_fp32", lambda: [FormJob(f32, [c], [fr], dec, dev, k) for c, fr in zip(cams, frames)]),
+             ("batched_fp32", lambda: [FormJob(f32, cams, frames, dec, dev, k)]),
+             ("batched_f16rgb_bf16feat", lambda: [FormJob(half, cams, frames, dec, dev, k)])]
+    for name, make in specs:
+        jobs = make()
+        shapes = sorted({(t.fwd_px_per_thread, t.bwd_px_per_thread) for t in (j.tune() for j in jobs)})
+        ms = time_graph(jobs, args.form_steps, flush)
+        out[name] = {"frames_per_step": batch, "steps_per_graph": len(jobs), "ms_per_step": ms,
+                     "frames_per_s": batch * 1000.0 / ms, "ms_per_frame": ms / batch,
+                     "instances": int(sum(j.r.instances() for j in jobs)),
+                     "px_per_thread_fwd_bwd": shapes}
+        del jobs
+        torch.cuda.empty_cache()
+    base = out["single_fp32"]["frames_per_s"]
+    for name in ("batched_fp32", "batched_f16rgb_bf16feat"):
+        out[name]["speedup_vs_single_fp32"] = out[name]["frames_per_s"] / base
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -213,10 +330,9 @@ def run_ours(args, rank, world, local_rank):
     w = raster.MAPPING
     mode = L.GS_GRAD_MAP | L.GS_GRAD_POSE
     T_state = torch.as_tensor(start_pose.reshape(1, 16), dtype=torch.float64).to(dev)
-    adam = torch.zeros(1, 12, dtype=torch.float64, device=dev)
+    adam = torch.zeros(1 * 12 + 1, dtype=torch.float64, device=dev)       # moments + device step counter
     pose_f32 = torch.zeros(1, 16, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    step_no = [0]
 
     def step(ev=None):
         rec = (lambda i: ev[i].record(stream)) if ev is not None else (lambda i: None)
@@ -235,8 +351,7 @@ def run_ours(args, rank, world, local_rank):
         rec(6)
         r.pose_grad()
         r.dsr(field, w.big, w.small)
-        step_no[0] += 1
-        r.pose_step(T_state, adam, step_no[0], pose_f32=pose_f32)
+        r.pose_step(T_state, adam, 0, pose_f32=pose_f32)
         rec(7)
 
     stages = ["project", "bin_sort", "render_fwd", "loss", "render_bwd", "project_bwd", "pose+dsr+step"]
@@ -336,6 +451,8 @@ def run_ours(args, rank, world, local_rank):
         roof = {"kernel": stages[dom], "bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"),
                 "unit": "GB/s", "frac": None, "traffic": None}
 
+    forms = None if args.no_forms else run_forms(args, gs, dec, dev, flush)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(gs, cam, tgt, dec)
@@ -349,6 +466,7 @@ def run_ours(args, rank, world, local_rank):
                            px_per_thread={"fwd": tuned.fwd_px_per_thread, "bwd": tuned.bwd_px_per_thread},
                            autotune_ms={k: {str(n): round(t, 4) for n, t in v.items()} for k, v in tune_ms.items()}),
             "stages_ms": {s: float(t) for s, t in zip(stages, per_stage)},
+            "forms": forms,
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "iters/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},

@@ -341,8 +341,12 @@ gs_status gs_dsr(int64_t n, const float *log_scales, float lam_big, float lam_sm
 /* Pose step for tracking (Sec. 3.4; learning rates of supp. C.1): Adam on
  * the left twist of each view, then T <- Exp(delta) T.  T_state: device f64
  * [n_views,16] (updated); adam: device f64 [n_views,12] (m, v; zero before
- * step 1); lr: host [6] (rho, phi); step: 1-based.  If pose_f32 is not NULL
- * it receives the f32 copy of the new poses (for gs_project's pose_dev). */
+ * step 1); lr: host [6] (rho, phi); step: 1-based.  step = 0 keeps the count
+ * on the device instead: adam then holds n_views*12 + 1 doubles, the last one
+ * the number of steps taken (zero before the first), which the call reads and
+ * increments, so that a captured CUDA graph can replay the step.  If pose_f32
+ * is not NULL it receives the f32 copy of the new poses (for gs_project's
+ * pose_dev).  GS_ERR_ARG for step < 0 or a missing buffer. */
 gs_status gs_pose_step(int n_views, const double *d_twist, double *T_state, double *adam,
                        int step, const double *lr, double beta1, double beta2, double eps,
                        float *pose_f32, gs_stream stream);

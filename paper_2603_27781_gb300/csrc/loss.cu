@@ -446,10 +446,20 @@ __global__ void __launch_bounds__(256) pose_reduce_kernel(int64_t n, const float
 }
 
 // ------------------------------------------------------------------ pose step
+// bc1 < 0 selects the device step counter: adam[12 * n_views] holds the number
+// of steps taken so far (as a double); this step is that number + 1 and the
+// bias corrections 1 - beta^step are formed here.
 __global__ void pose_step_kernel(int n_views, const double *grad, double *Tst, double *adam, double bc1, double bc2,
                                  double lr0, double lr1, double lr2, double lr3, double lr4, double lr5, double b1,
                                  double b2, double eps, float *pose_f32) {
     const int v = threadIdx.x;
+    if (bc1 < 0.0) {
+        const double step = adam[12 * n_views] + 1.0;
+        bc1 = 1.0 - pow(b1, step);
+        bc2 = 1.0 - pow(b2, step);
+        __syncthreads();                       // every thread has read the counter
+        if (v == 0) adam[12 * n_views] = step;
+    }
     if (v >= n_views) return;
     const double lr[6] = {lr0, lr1, lr2, lr3, lr4, lr5};
     double *m = adam + 12 * v, *vv = m + 6, *T = Tst + 16 * v;
@@ -599,9 +609,10 @@ extern "C" gs_status gs_pose_step(int n_views, const double *d_twist, double *T_
                                   const double *lr, double beta1, double beta2, double eps, float *pose_f32,
                                   gs_stream stream) {
     using namespace gs;
-    if (n_views < 1 || n_views > kMaxViews || !d_twist || !T_state || !adam || !lr || step < 1) return GS_ERR_ARG;
-    // Adam bias corrections 1 - beta^step on the host (keeps pow off the device)
-    const double bc1 = 1.0 - pow(beta1, step), bc2 = 1.0 - pow(beta2, step);
+    if (n_views < 1 || n_views > kMaxViews || !d_twist || !T_state || !adam || !lr || step < 0) return GS_ERR_ARG;
+    // Adam bias corrections 1 - beta^step: on the host for a given step, on the
+    // device (from the counter after the moments) for step 0
+    const double bc1 = step ? 1.0 - pow(beta1, step) : -1.0, bc2 = step ? 1.0 - pow(beta2, step) : -1.0;
     pose_step_kernel<<<1, 64, 0, (cudaStream_t)stream>>>(n_views, d_twist, T_state, adam, bc1, bc2, lr[0], lr[1],
                                                          lr[2], lr[3], lr[4], lr[5], beta1, beta2, eps, pose_f32);
     return last_launch();

@@ -271,6 +271,12 @@ class Renderer:
 
     def pose_step(self, T_state, adam, step, lr=TRACKING_LR, b1=0.9, b2=0.999, eps=1e-15, pose_f32=None,
                   stream=None):
+        """Adam step on the view twists.  step >= 1 is the 1-based step number; step 0
+        keeps the count on the device (adam then holds 12 * n_views + 1 doubles, the
+        last one the steps taken so far), which a captured CUDA graph can replay."""
+        need = 12 * self.n_views + (1 if step == 0 else 0)
+        if adam.numel() < need or adam.dtype != torch.float64:
+            raise ValueError(f"adam state needs {need} float64 values")
         lr_c = (ctypes.c_double * 6)(*lr)
         L.check("gs_pose_step", L.gs_pose_step(self.n_views, _p(self.d_twist), _p(T_state), _p(adam), step, lr_c,
                                                b1, b2, eps, _p(pose_f32), _stream(stream)))
