@@ -126,7 +126,10 @@ typedef struct {
  * instance j (may be NULL if not wanted), vals[j] = its item; ranges[2t],
  * ranges[2t+1] = [start, end) of tile t; n_inst = instance count (device
  * int64); status = device word, 0 or a negative gs_status.  capacity bounds
- * keys/vals. */
+ * keys/vals.  tile_order (optional, device u32 [total tiles]): a permutation
+ * of the tiles by decreasing instance count (order within equal counts
+ * unspecified), in which gs_render_fwd / gs_render_bwd launch their tiles
+ * when it is not NULL; gs_bin_sort writes it whenever it is not NULL. */
 typedef struct {
     int64_t capacity;
     uint64_t *keys;
@@ -134,6 +137,7 @@ typedef struct {
     uint32_t *ranges;
     int64_t *n_inst;
     int32_t *status;
+    uint32_t *tile_order;
 } gs_binning;
 
 /* Rendered images, planar f32 over all views' pixels (P = sum W H):

@@ -41,7 +41,7 @@ class gs_projected(Structure):
 
 class gs_binning(Structure):
     _fields_ = [("capacity", c_int64), ("keys", c_void_p), ("vals", c_void_p), ("ranges", c_void_p),
-                ("n_inst", c_void_p), ("status", c_void_p)]
+                ("n_inst", c_void_p), ("status", c_void_p), ("tile_order", c_void_p)]
 
 
 class gs_images(Structure):

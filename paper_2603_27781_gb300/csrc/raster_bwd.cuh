@@ -43,13 +43,45 @@ __device__ __forceinline__ float warp_transpose_reduce(float (&v)[N], int lane) 
     return r;
 }
 
-template <int D, bool MAP>
+constexpr size_t align16(size_t b) { return (b + 15) / 16 * 16; }
+
+// Per splat the kernel accumulates: centre (2), conic (3), opacity, then the
+// alpha-T weighted terms depth, r, g, b and the D features.
+//
+// With D >= 16 in map mode the weighted terms are not reduced by shuffles: a
+// warp records the weight w of each of its pixels for up to SLOTS splats and
+// then contracts them with its pixels' upstream gradients in one pass, a lane
+// owning one splat and half of the terms (sum over the warp's pixels of
+// w * g, exact FP32 FMAs).  The shuffle reduction then carries 6 values, not 26.
+template <int D, int NP, bool MAP>
 struct BwdLayout {
-    static constexpr int NV = MAP ? 10 + D : 6;                 // reduced values per splat
-    static constexpr int C0 = NV > 32 ? 32 : pow2_at_least(NV);  // first chunk (power of two)
-    static constexpr int R1 = NV > 32 ? NV - 32 : 0;             // values in the second chunk
+    static constexpr int NV = MAP ? 10 + D : 6;                  // values accumulated per splat
+    static constexpr bool DEFER = MAP && D >= 16;
+    static constexpr int NW = 4 + D;                             // deferred weighted terms
+    static constexpr int HW = NW / 2;                            // terms per half-warp
+    static constexpr int HWP = (HW + 3) / 4 * 4;                 // padded to 16-byte loads
+    static constexpr int GROW = 2 * HWP;                         // gradient row of one pixel
+    static constexpr int NR = DEFER ? 6 : NV;                    // values reduced by shuffles
+    static constexpr int C0 = NR > 32 ? 32 : pow2_at_least(NR);  // first chunk (power of two)
+    static constexpr int R1 = NR > 32 ? NR - 32 : 0;             // values in the second chunk
     static constexpr int C1 = R1 > 0 ? pow2_at_least(R1) : 0;
-    static constexpr int ROW = C0 + C1;                          // shared accumulator row
+    static constexpr int ROW = DEFER ? NV : C0 + C1;             // shared accumulator row
+    static constexpr int BATCH = kBatch;                         // splats staged per round
+    static constexpr int SLOTS = 16;                             // splats per deferred pass
+    static constexpr int WARPS = Shape<NP>::WARPS;
+    static constexpr int PXW = 32 * NP;                          // pixels of one warp
+    static constexpr int WROW = PXW + 4;                         // 16-byte rows; 8 lanes' float4 reads span 32 banks
+    static constexpr int D4 = D / 4 > 0 ? D / 4 : 1;
+    // dynamic shared memory, in bytes
+    static constexpr size_t OFF_EXT = sizeof(SplatGeo) * BATCH;
+    static constexpr size_t OFF_RGBD = OFF_EXT + sizeof(float2) * BATCH;
+    static constexpr size_t OFF_FEAT = OFF_RGBD + sizeof(float4) * BATCH;
+    static constexpr size_t OFF_ACC = OFF_FEAT + sizeof(float4) * BATCH * D4;
+    static constexpr size_t OFF_W = OFF_ACC + align16(sizeof(float) * BATCH * ROW);
+    static constexpr size_t OFF_G = OFF_W + (DEFER ? align16(sizeof(float) * WARPS * SLOTS * WROW) : 0);
+    static constexpr size_t OFF_SLOT = OFF_G + (DEFER ? align16(sizeof(float) * WARPS * PXW * GROW) : 0);
+    static constexpr size_t BYTES = OFF_SLOT + (DEFER ? sizeof(int) * WARPS * SLOTS : 0);
+    static_assert(PXW % 4 == 0, "weights are read four pixels at a time");
 };
 
 struct BwdArgs {
@@ -68,25 +100,31 @@ struct BwdArgs {
     float *d_feat;
     const uint32_t *bmask;  // blend-mask planes from the forward (NULL: scan every splat)
     int64_t bm_stride;
+    const uint32_t *order;  // tile launch order (NULL: tile = block index)
 };
 
 template <int D, int NP, bool MAP, typename RT, typename FT>
 __global__ void __launch_bounds__(Shape<NP>::THREADS) raster_bwd_kernel(ViewTable vt, Params prm, BwdArgs A) {
-    using LY = BwdLayout<D, MAP>;
+    using LY = BwdLayout<D, NP, MAP>;
     using SH = Shape<NP>;
     constexpr int NT = SH::THREADS;
     constexpr int D4 = D / 4;
     constexpr int NCH = 5 + D;  // r, g, b, depth, sil, features
-    __shared__ SplatGeo s_geo[kBatch];
-    __shared__ float2 s_ext[kBatch];
-    __shared__ float4 s_rgbd[kBatch];
-    __shared__ float4 s_feat[kBatch * (D4 > 0 ? D4 : 1)];
-    __shared__ float s_acc[kBatch * LY::ROW];
+    extern __shared__ __align__(16) unsigned char smem[];
+    SplatGeo *s_geo = reinterpret_cast<SplatGeo *>(smem);
+    float2 *s_ext = reinterpret_cast<float2 *>(smem + LY::OFF_EXT);
+    float4 *s_rgbd = reinterpret_cast<float4 *>(smem + LY::OFF_RGBD);
+    float4 *s_feat = reinterpret_cast<float4 *>(smem + LY::OFF_FEAT);
+    float *s_acc = reinterpret_cast<float *>(smem + LY::OFF_ACC);
+    float *s_w = reinterpret_cast<float *>(smem + LY::OFF_W);        // [warp][slot][pixel] weights
+    float *s_g = reinterpret_cast<float *>(smem + LY::OFF_G);        // [warp][pixel][term] gradients
+    int *s_slot = reinterpret_cast<int *>(smem + LY::OFF_SLOT);      // [warp][slot] batch index
     __shared__ int s_max_last;
     const RT *rgb = static_cast<const RT *>(A.rgb);
     const FT *feat = static_cast<const FT *>(A.feat);
 
-    const int gt = blockIdx.x;
+    const int gt = A.order ? (int)A.order[blockIdx.x] : (int)blockIdx.x;
+    if (gt < 0 || gt >= vt.tile_off[vt.n_views]) return;  // not a permutation of the tiles: leave the tile
     const int v = view_of_tile(vt, gt);
     const int t = gt - vt.tile_off[v];
     const int tx = t % vt.TX[v], ty = t / vt.TX[v];
@@ -129,6 +167,66 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS) raster_bwd_kernel(ViewTabl
         gS[p] = gch[p][0] * prm.bg[0] + gch[p][1] * prm.bg[1] + gch[p][2] * prm.bg[2];
         my_max = max(my_max, last[p]);
     }
+    const int warp = tid >> 5;
+    if constexpr (LY::DEFER) {
+        // the warp's pixel p * 32 + lane: gradients of depth, r, g, b, features
+        // (terms [0, HW) at row[0..], terms [HW, NW) at row[HWP..]; padding is zero)
+        float *gw = s_g + (size_t)warp * LY::PXW * LY::GROW;
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            float term[LY::NW];
+            term[0] = gch[p][3];
+            term[1] = gch[p][0];
+            term[2] = gch[p][1];
+            term[3] = gch[p][2];
+#pragma unroll
+            for (int d = 0; d < D; ++d) term[4 + d] = gch[p][5 + d];
+            float *row = gw + (p * 32 + lane) * LY::GROW;
+#pragma unroll
+            for (int c = 0; c < LY::GROW; ++c) {
+                const int h = c / LY::HWP, i = c % LY::HWP;
+                row[c] = i < LY::HW ? term[h * LY::HW + i] : 0.f;
+            }
+        }
+    }
+    int n_slot = 0;  // splats recorded in the warp's weight slots (warp-uniform)
+    // Deferred weighted terms: lane (j, h) sums w * g over the warp's pixels for
+    // slot j and terms [h * HW, (h + 1) * HW), then adds them to the splat's row.
+    auto flush = [&]() {
+        __syncwarp();
+        const int j = lane & (LY::SLOTS - 1), h = lane >> 4;
+        const float4 *wr = reinterpret_cast<const float4 *>(s_w + ((size_t)warp * LY::SLOTS + j) * LY::WROW);
+        const float4 *gr =
+            reinterpret_cast<const float4 *>(s_g + (size_t)warp * LY::PXW * LY::GROW + h * LY::HWP);
+        float acc[LY::HWP];
+#pragma unroll
+        for (int c = 0; c < LY::HWP; ++c) acc[c] = 0.f;
+#pragma unroll 2
+        for (int q = 0; q < LY::PXW / 4; ++q) {
+            const float4 w4 = wr[q];
+            const float wq[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float4 *g4 = gr + (4 * q + i) * (LY::GROW / 4);
+#pragma unroll
+                for (int c = 0; c < LY::HWP / 4; ++c) {
+                    const float4 gv = g4[c];
+                    acc[4 * c] = fmaf(wq[i], gv.x, acc[4 * c]);
+                    if (4 * c + 1 < LY::HW) acc[4 * c + 1] = fmaf(wq[i], gv.y, acc[4 * c + 1]);
+                    if (4 * c + 2 < LY::HW) acc[4 * c + 2] = fmaf(wq[i], gv.z, acc[4 * c + 2]);
+                    if (4 * c + 3 < LY::HW) acc[4 * c + 3] = fmaf(wq[i], gv.w, acc[4 * c + 3]);
+                }
+            }
+        }
+        if (j < n_slot) {
+            float *a = s_acc + s_slot[warp * LY::SLOTS + j] * LY::ROW + 6 + h * LY::HW;
+#pragma unroll
+            for (int c = 0; c < LY::HW; ++c)
+                if (acc[c] != 0.f) atomicAdd(a + c, acc[c]);
+        }
+        __syncwarp();
+        n_slot = 0;
+    };
 
     if (tid == 0) s_max_last = 0;
     __syncthreads();
@@ -137,8 +235,8 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS) raster_bwd_kernel(ViewTabl
     const int max_last = s_max_last;
     const float inv_l2e = 1.f / kLog2e;
 
-    for (int b_end = max_last; b_end > 0; b_end -= kBatch) {
-        const int b_start = max(0, b_end - kBatch);
+    for (int b_end = max_last; b_end > 0; b_end -= LY::BATCH) {
+        const int b_start = max(0, b_end - LY::BATCH);
         const int cnt = b_end - b_start;
         __syncthreads();
         for (int i = tid; i < cnt; i += NT) {
@@ -170,9 +268,11 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS) raster_bwd_kernel(ViewTabl
             }
             if (!__any_sync(0xffffffffu, any)) return;
 
-            float val[LY::C0 + LY::C1];
+            float val[LY::C0 + LY::C1], wv[NP];
 #pragma unroll
             for (int i = 0; i < LY::C0 + LY::C1; ++i) val[i] = 0.f;
+#pragma unroll
+            for (int p = 0; p < NP; ++p) wv[p] = 0.f;
             if (any) {
                 const float4 c = s_rgbd[k];
                 float x[NCH];
@@ -204,7 +304,9 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS) raster_bwd_kernel(ViewTabl
                         val[4] += -0.5f * dy * dy * dpow;
                         if (MAP) val[5] += e[p].G * da;
                     }
-                    if (MAP) {
+                    if constexpr (LY::DEFER) {
+                        wv[p] = w;
+                    } else if (MAP) {
                         val[6] = fmaf(w, gch[p][3], val[6]);
                         val[7] = fmaf(w, gch[p][0], val[7]);
                         val[8] = fmaf(w, gch[p][1], val[8]);
@@ -216,6 +318,13 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS) raster_bwd_kernel(ViewTabl
                     }
                 }
             }
+            if constexpr (LY::DEFER) {
+                float *wr = s_w + ((size_t)warp * LY::SLOTS + n_slot) * LY::WROW;
+#pragma unroll
+                for (int p = 0; p < NP; ++p) wr[p * 32 + lane] = wv[p];
+                if (lane == 0) s_slot[warp * LY::SLOTS + n_slot] = k;
+                ++n_slot;
+            }
             // warp reduction, then CTA combine in shared memory
             {
                 float v0[LY::C0];
@@ -223,7 +332,7 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS) raster_bwd_kernel(ViewTabl
                 for (int i = 0; i < LY::C0; ++i) v0[i] = val[i];
                 const float r = warp_transpose_reduce<LY::C0>(v0, lane);
                 const int idx = lane & (LY::C0 - 1);
-                if (lane < LY::C0 && idx < LY::NV && r != 0.f) atomicAdd(&s_acc[k * LY::ROW + idx], r);
+                if (lane < LY::C0 && idx < LY::NR && r != 0.f) atomicAdd(&s_acc[k * LY::ROW + idx], r);
             }
             if constexpr (LY::C1 > 0) {
                 float v1[LY::C1];
@@ -233,14 +342,17 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS) raster_bwd_kernel(ViewTabl
                 const int idx = lane & (LY::C1 - 1);
                 if (lane < LY::C1 && idx < LY::R1 && r != 0.f) atomicAdd(&s_acc[k * LY::ROW + LY::C0 + idx], r);
             }
-                };
+            if constexpr (LY::DEFER) {
+                if (n_slot == LY::SLOTS) flush();
+            }
+        };
         if (A.bmask) {
             // only the instances some pixel of the warp's groups blended, back to front
             const int64_t lo_i = (int64_t)start + b_start, hi_i = (int64_t)start + b_end;
             for (int64_t wi = (hi_i - 1) >> 5; wi >= (lo_i >> 5); --wi) {
                 uint32_t m = 0u;
 #pragma unroll
-                for (int j = 0; j < NP; ++j) m |= A.bmask[(int64_t)((tid >> 5) * NP + j) * A.bm_stride + wi];
+                for (int j = 0; j < NP; ++j) m |= A.bmask[(int64_t)(warp * NP + j) * A.bm_stride + wi];
                 const int64_t base = wi << 5;
                 if (base < lo_i) m &= ~0u << (int)(lo_i - base);
                 if (hi_i - base < 32) m &= (1u << (int)(hi_i - base)) - 1u;
@@ -252,6 +364,9 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS) raster_bwd_kernel(ViewTabl
             }
         } else {
             for (int k = cnt - 1; k >= 0; --k) process(k);
+        }
+        if constexpr (LY::DEFER) {
+            if (n_slot > 0) flush();
         }
         __syncthreads();
         // one set of vector atomics per (tile, splat)
@@ -281,7 +396,14 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS) raster_bwd_kernel(ViewTabl
 
 template <int D, int NP, bool MAP, typename RT, typename FT>
 gs_status launch_bwd(const ViewTable &vt, const Params &prm, const BwdArgs &A, cudaStream_t st) {
-    raster_bwd_kernel<D, NP, MAP, RT, FT><<<vt.tile_off[vt.n_views], Shape<NP>::THREADS, 0, st>>>(vt, prm, A);
+    constexpr size_t bytes = BwdLayout<D, NP, MAP>::BYTES;
+    auto kern = raster_bwd_kernel<D, NP, MAP, RT, FT>;
+    if (bytes > 48 * 1024) {
+        const gs_status s = cuda_status(
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+        if (s) return s;
+    }
+    kern<<<vt.tile_off[vt.n_views], Shape<NP>::THREADS, bytes, st>>>(vt, prm, A);
     return last_launch();
 }
 

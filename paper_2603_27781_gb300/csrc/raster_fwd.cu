@@ -22,7 +22,8 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS, fwd_min_blocks(D, NP)) ras
     ViewTable vt, Params prm, const float4 *__restrict__ uvdo, const float2 *__restrict__ uv_lo,
     const float4 *__restrict__ conic, const RT *__restrict__ rgb, const FT *__restrict__ feat,
     const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges, int64_t P, float *o_rgb, float *o_depth,
-    float *o_sil, float *o_feat, float *o_T, int32_t *o_nc, int32_t *o_nb, uint32_t *bmask, int64_t bm_stride) {
+    float *o_sil, float *o_feat, float *o_T, int32_t *o_nc, int32_t *o_nb, uint32_t *bmask, int64_t bm_stride,
+    const uint32_t *__restrict__ order) {
     using SH = Shape<NP>;
     constexpr int NT = SH::THREADS;
     constexpr int D4 = D / 4, DD = D > 0 ? D : 1;
@@ -31,7 +32,8 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS, fwd_min_blocks(D, NP)) ras
     __shared__ float4 s_rgbd[kBatch];
     __shared__ float4 s_feat[kBatch * (D4 > 0 ? D4 : 1)];
 
-    const int gt = blockIdx.x;
+    const int gt = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
+    if (gt < 0 || gt >= vt.tile_off[vt.n_views]) return;  // not a permutation of the tiles: leave the tile
     const int v = view_of_tile(vt, gt);
     const int t = gt - vt.tile_off[v];
     const int tx = t % vt.TX[v], ty = t / vt.TX[v];
@@ -186,7 +188,7 @@ gs_status launch(const ViewTable &vt, const Params &prm, const gs_gaussians *g, 
         vt, prm, reinterpret_cast<const float4 *>(proj->uvdo), reinterpret_cast<const float2 *>(proj->uv_lo),
         reinterpret_cast<const float4 *>(proj->conic), static_cast<const RT *>(g->rgb),
         static_cast<const FT *>(g->feat), bins->vals, bins->ranges, P, out->rgb, out->depth, out->sil, out->feat,
-        out->T_final, out->n_contrib, out->n_blended, out->blend_mask, bins->capacity / 32 + 1);
+        out->T_final, out->n_contrib, out->n_blended, out->blend_mask, bins->capacity / 32 + 1, bins->tile_order);
     return last_launch();
 }
 

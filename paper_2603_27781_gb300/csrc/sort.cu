@@ -401,6 +401,65 @@ gs_status radix_sort(SortBufs b, const uint32_t *count_ptr, int64_t max_count, i
 }  // namespace
 }  // namespace gs
 
+namespace gs {
+namespace {
+
+// Launch order of the blend kernels' tiles: decreasing instance count, so the
+// longest tiles start first and the short ones fill in behind them (longest-
+// processing-time-first; the order within a count bucket is arbitrary).  One
+// CTA: counting sort on a bucket of the count (exact below 1024 instances,
+// 64-instance steps above, saturating at 50,112), buckets taken high to low.
+__device__ __forceinline__ int order_bucket(uint32_t c) {
+    return c < 1024u ? (int)(c >> 2) : (int)min(256u + ((c - 1024u) >> 6), 1023u);
+}
+
+__global__ void __launch_bounds__(1024) tile_order_kernel(const uint32_t *ranges, int n_tiles, uint32_t *order) {
+    __shared__ uint32_t hist[1024];
+    __shared__ uint32_t warp_tot[32];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    hist[tid] = 0u;
+    __syncthreads();
+    for (int t = tid; t < n_tiles; t += 1024) atomicAdd(&hist[order_bucket(ranges[2 * t + 1] - ranges[2 * t])], 1u);
+    __syncthreads();
+    // exclusive scan over buckets from the highest down: thread i takes bucket 1023 - i
+    const uint32_t h = hist[1023 - tid];
+    uint32_t x = h;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t wsum = warp_tot[lane];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, wsum, d);
+            if (lane >= d) wsum += y;
+        }
+        warp_tot[lane] = wsum;  // inclusive over warps
+    }
+    __syncthreads();
+    const uint32_t before = (wid > 0 ? warp_tot[wid - 1] : 0u) + x - h;
+    __syncthreads();
+    hist[1023 - tid] = before;  // first slot of bucket 1023 - tid
+    __syncthreads();
+    for (int t = tid; t < n_tiles; t += 1024) {
+        const uint32_t pos = atomicAdd(&hist[order_bucket(ranges[2 * t + 1] - ranges[2 * t])], 1u);
+        order[pos] = (uint32_t)t;
+    }
+}
+
+gs_status write_tile_order(const gs_binning *out, int64_t total_tiles, cudaStream_t st) {
+    if (!out->tile_order) return GS_OK;
+    tile_order_kernel<<<1, 1024, 0, st>>>(out->ranges, (int)total_tiles, out->tile_order);
+    return last_launch();
+}
+
+}  // namespace
+}  // namespace gs
+
 extern "C" gs_status gs_bin_sort(int64_t n, const gs_projected *proj, const gs_camera *cams, int n_views,
                                  const gs_raster_params *p, void *ws, size_t ws_bytes, gs_binning *out,
                                  gs_stream stream) {
@@ -427,7 +486,7 @@ extern "C" gs_status gs_bin_sort(int64_t n, const gs_projected *proj, const gs_c
     if ((s = cuda_status(cudaMemsetAsync(counters, 0, sizeof(uint32_t) * 64, st)))) return s;
     if ((s = cuda_status(cudaMemsetAsync(out->n_inst, 0, sizeof(int64_t), st)))) return s;
     if ((s = cuda_status(cudaMemsetAsync(out->status, 0, sizeof(int32_t), st)))) return s;
-    if (vn == 0) return GS_OK;
+    if (vn == 0) return write_tile_order(out, total_tiles, st);
     if (!proj->uvdo || !proj->conic || !proj->tiles_touched) return GS_ERR_ARG;
     if ((s = cuda_status(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * 8 * 256, st)))) return s;
     size_t lb_bytes = sizeof(uint32_t) * 256 * ((size_t)4 * L.lb_tiles_depth + (size_t)3 * L.lb_tiles_inst);
@@ -468,7 +527,7 @@ extern "C" gs_status gs_bin_sort(int64_t n, const gs_projected *proj, const gs_c
     emit_kernel<<<nbe, kEmitBlock, 0, st>>>(vt, sorted_items, proj->tiles_touched, uvdo, conic, counters, block_sums,
                                     out->capacity, tk_a, emit_vals);
     if ((s = last_launch())) return s;
-    if (out->capacity == 0) return GS_OK;
+    if (out->capacity == 0) return write_tile_order(out, total_tiles, st);
 
     // 4. stable sort of the instances by tile id
     if ((s = radix_sort({tk_a, emit_vals, tk_b, other_vals}, counters + CTR_M, out->capacity, tile_passes,
@@ -480,5 +539,6 @@ extern "C" gs_status gs_bin_sort(int64_t n, const gs_projected *proj, const gs_c
     // 5. per-tile ranges (and the 64-bit keys if requested)
     ranges_kernel<<<ceil_div(out->capacity, 256), 256, 0, st>>>(sorted_tiles, out->vals, counters, uvdo, out->ranges,
                                                                 out->keys);
-    return last_launch();
+    if ((s = last_launch())) return s;
+    return write_tile_order(out, total_tiles, st);
 }

@@ -131,6 +131,8 @@ class Renderer:
         self.keys = torch.zeros(max(capacity, 1), dtype=torch.int64, device=dev)
         self.vals = torch.zeros(max(capacity, 1), dtype=i32, device=dev)
         self.ranges = torch.zeros(2 * self.n_tiles, dtype=i32, device=dev)
+        self.tile_order = torch.zeros(max(self.n_tiles, 1), dtype=i32, device=dev)
+        self.use_tile_order = True      # blend tiles launched longest first
         self.n_inst = torch.zeros(1, dtype=torch.int64, device=dev)
         self.status_word = torch.zeros(1, dtype=i32, device=dev)
         ws_bytes = L.library().gs_workspace_size(n, V, self.cams_c, capacity, feat_dim)
@@ -191,7 +193,8 @@ class Renderer:
 
     def binning_c(self, want_keys=False):
         return L.gs_binning(self.capacity, _p(self.keys) if want_keys else None, _p(self.vals), _p(self.ranges),
-                            _p(self.n_inst), _p(self.status_word))
+                            _p(self.n_inst), _p(self.status_word),
+                            _p(self.tile_order) if self.use_tile_order else None)
 
     def images_c(self):
         return L.gs_images(_p(self.img_rgb), _p(self.img_depth), _p(self.img_sil),

@@ -199,6 +199,36 @@ def test_blend_mask_skips_only_non_contributing_splats():
         C.assert_grad_close("masked", a.cpu().numpy(), b.cpu().numpy(), 1e-5)
 
 
+def test_tile_order_is_a_longest_first_permutation_and_changes_nothing():
+    """Two views: the launch order lists every tile once, by non-increasing instance count
+    (in the order's count buckets), and rendering in it or in index order gives the same
+    images and gradients."""
+    gs, cam, room = C.room_case(20000, 16, 330, 190, 165.0)
+    cams = [cam, synth.camera(100, 70, 60.0, T_cw=synth.keyframe_loop(8, room=room)[3])]
+    field, r = C.gpu_forward(gs, cams, C.params_pair()[0])
+    order = r.tile_order.cpu().numpy().astype(np.int64)
+    assert np.array_equal(np.sort(order), np.arange(r.n_tiles))
+    rng_ = r.ranges.cpu().numpy().astype(np.int64).reshape(-1, 2)
+    count = rng_[:, 1] - rng_[:, 0]
+    bucket = np.where(count < 1024, count >> 2, np.minimum(256 + ((count - 1024) >> 6), 1023))
+    assert np.all(np.diff(bucket[order]) <= 0)
+    g = C.random_image_grads(r.P, 16, 9)
+    r.g_rgb.copy_(torch.as_tensor(g["rgb"])); r.g_depth.copy_(torch.as_tensor(g["depth"]))
+    r.g_sil.copy_(torch.as_tensor(g["sil"])); r.g_feat.copy_(torch.as_tensor(g["feat"]))
+    imgs, grads = [], []
+    for use_order in (True, False):
+        r.use_tile_order = use_order
+        r.forward(field)
+        r.backward(field, L.GS_GRAD_MAP | L.GS_GRAD_POSE)
+        imgs.append([t.clone() for t in (r.img_rgb, r.img_depth, r.img_sil, r.img_feat, r.img_T, r.img_nc)])
+        grads.append([t.clone() for t in (r.d_means, r.d_quats, r.d_log_scales, r.d_logits, r.d_rgb, r.d_feat,
+                                          r.d_twist)])
+    for a, b in zip(*imgs):
+        assert torch.equal(a, b)
+    for a, b in zip(*grads):
+        C.assert_grad_close("ordered", a.cpu().numpy(), b.cpu().numpy(), 1e-5)
+
+
 def test_autotuner_picks_a_supported_shape():
     from paper_2603_27781_gb300 import autotune
     gs, cam, _ = C.room_case(20000, 16, 330, 190, 165.0)
