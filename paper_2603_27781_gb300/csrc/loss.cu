@@ -159,27 +159,45 @@ __device__ __forceinline__ double block_sum_f64(double x, double *s_red) {
 
 // Per-pixel losses and image gradients; per-block partials of the decoder
 // gradient (f32 [nblk][K*D + K]) and of the three loss sums (f64 [nblk][3]).
-template <int D>
-__global__ void __launch_bounds__(256) loss_kernel(ViewTable vt, LossP lp, const float *rgb, const float *depth,
-                                                   const float *sil, const float *feat, const float *trgb,
-                                                   const float *tdepth, const uint8_t *label, const float *Wd,
-                                                   const float *bd, int64_t P, const uint32_t *med_hist,
-                                                   float *g_rgb, float *g_depth, float *g_sil, float *g_feat,
-                                                   float *part_f, double *part_d, float *mask_out,
-                                                   float *median_out) {
-    constexpr int DD = D > 0 ? D : 1;
-    __shared__ float s_W[kMaxK * DD], s_b[kMaxK];
-    __shared__ float s_dW[kMaxK * DD + kMaxK];
+//
+// KC is a compile-time bound on the class count (K <= KC).  The decoder
+// gradient dW[k][d] = sum_px dz_k f_d, db[k] = sum_px dz_k is a contraction over
+// pixels: each warp stages dz and f of its 32 pixels in shared memory, and every
+// lane keeps EPL consecutive entries of one row of dW (lanes < KC also one
+// entry of db) in registers for the whole grid-stride loop; they reach the
+// block's shared sums once, at the end.
+template <int D, int KC>
+struct LossShape {
+    static constexpr int NT = (KC <= 8 && D <= 16) ? 256 : 128;  // keeps the static shared memory < 48 KB
+    static constexpr int WARPS = NT / 32;
+    static constexpr int DD = D > 0 ? D : 1;
+    static constexpr int EPL = D > 0 ? KC * D / 32 : 1;          // dW entries per lane
+    static constexpr int FROW = D > 0 ? D + 4 : 4;              // staged feature row (16-byte aligned, padded)
+    static_assert(D == 0 || ((KC * D) % 32 == 0 && D % EPL == 0), "lane blocks of dW");
+};
+
+template <int D, int KC>
+__global__ void __launch_bounds__(LossShape<D, KC>::NT) loss_kernel(
+    ViewTable vt, LossP lp, const float *rgb, const float *depth, const float *sil, const float *feat,
+    const float *trgb, const float *tdepth, const uint8_t *label, const float *Wd, const float *bd, int64_t P,
+    const uint32_t *med_hist, float *g_rgb, float *g_depth, float *g_sil, float *g_feat, float *part_f,
+    double *part_d, float *mask_out, float *median_out) {
+    using SH = LossShape<D, KC>;
+    constexpr int NT = SH::NT, DD = SH::DD, EPL = SH::EPL;
+    __shared__ float s_W[KC * DD], s_b[KC];
+    __shared__ float s_dW[KC * DD + KC];
+    __shared__ float s_dz[SH::WARPS][32][KC + 1];
+    __shared__ __align__(16) float s_f[SH::WARPS][32][SH::FROW];
     __shared__ double s_red[8];
     __shared__ float s_med;
     const int v = blockIdx.y;
     const int blk = v * gridDim.x + blockIdx.x;
     const int64_t Pv = (int64_t)vt.W[v] * vt.H[v];
-    const int K = lp.K, tid = threadIdx.x, lane = tid & 31;
+    const int K = lp.K, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int nval = K * D + K;
-    for (int i = tid; i < K * D; i += 256) s_W[i] = Wd[i];
-    for (int i = tid; i < K; i += 256) s_b[i] = bd[i];
-    for (int i = tid; i < nval; i += 256) s_dW[i] = 0.f;
+    for (int i = tid; i < K * D; i += NT) s_W[i] = Wd[i];
+    for (int i = tid; i < K; i += NT) s_b[i] = bd[i];
+    for (int i = tid; i < nval; i += NT) s_dW[i] = 0.f;
     float med = 0.f;
     if (lp.mask_mode == 1) med = __uint_as_float(block_select(med_hist, vt.n_views, v, 4));
     if (tid == 0) {
@@ -189,12 +207,17 @@ __global__ void __launch_bounds__(256) loss_kernel(ViewTable vt, LossP lp, const
     __syncthreads();
     const float invP = 1.f / (float)Pv;
     float lc = 0.f, ld = 0.f, ls = 0.f;  // per-thread partial sums (a thread sees few pixels)
-
-    for (int64_t base = (int64_t)blockIdx.x * 256; base < Pv; base += (int64_t)gridDim.x * 256) {
-        const int64_t i = base + tid;
-        float f[DD], dz[kMaxK];
+    // this lane's decoder-gradient entries: dW[kr][d0, d0 + EPL) and db[lane]
+    const int kr = D > 0 ? (lane * EPL) / D : 0, d0 = D > 0 ? (lane * EPL) % D : 0;
+    float accW[EPL], accb = 0.f;
 #pragma unroll
-        for (int k = 0; k < kMaxK; ++k) dz[k] = 0.f;
+    for (int e = 0; e < EPL; ++e) accW[e] = 0.f;
+
+    for (int64_t base = (int64_t)blockIdx.x * NT; base < Pv; base += (int64_t)gridDim.x * NT) {
+        const int64_t i = base + tid;
+        float f[DD], dz[KC];
+#pragma unroll
+        for (int k = 0; k < KC; ++k) dz[k] = 0.f;
 #pragma unroll
         for (int d = 0; d < DD; ++d) f[d] = 0.f;
         if (i < Pv) {
@@ -225,10 +248,10 @@ __global__ void __launch_bounds__(256) loss_kernel(ViewTable vt, LossP lp, const
 #pragma unroll
             for (int d = 0; d < DD; ++d) gf[d] = 0.f;
             if (lab != 255 && lab < K) {
-                float z[kMaxK];
+                float z[KC];
                 float zmax = -INFINITY;
 #pragma unroll
-                for (int k = 0; k < kMaxK; ++k) {
+                for (int k = 0; k < KC; ++k) {
                     z[k] = 0.f;
                     if (k < K) {
                         float s = s_b[k];
@@ -240,7 +263,7 @@ __global__ void __launch_bounds__(256) loss_kernel(ViewTable vt, LossP lp, const
                 }
                 float se = 0.f, zl = 0.f;
 #pragma unroll
-                for (int k = 0; k < kMaxK; ++k)
+                for (int k = 0; k < KC; ++k)
                     if (k < K) {
                         se += expf(z[k] - zmax);
                         if (k == lab) zl = z[k];
@@ -249,7 +272,7 @@ __global__ void __launch_bounds__(256) loss_kernel(ViewTable vt, LossP lp, const
                 ls += m * (lse - zl);
                 const float scale = m * lp.sem * invP;
 #pragma unroll
-                for (int k = 0; k < kMaxK; ++k) {
+                for (int k = 0; k < KC; ++k) {
                     if (k < K) {
                         dz[k] = scale * (expf(z[k] - lse) - (k == lab ? 1.f : 0.f));
 #pragma unroll
@@ -260,35 +283,56 @@ __global__ void __launch_bounds__(256) loss_kernel(ViewTable vt, LossP lp, const
 #pragma unroll
             for (int d = 0; d < D; ++d) g_feat[d * P + pix] = gf[d];
         }
-        // decoder gradients dW[k][d] += dz_k f_d, db[k] += dz_k: one warp transpose
-        // reduction per class row (k unrolled so dz stays in registers)
+        if (K > 0) {
+            // stage the warp's dz and f, then accumulate this lane's dW / db entries over its 32 pixels
 #pragma unroll
-        for (int k = 0; k < kMaxK; ++k) {
-            if (k < K) {
+            for (int k = 0; k < KC; ++k) s_dz[wid][lane][k] = dz[k];
+            if constexpr (D > 0) {
+                float4 *fr = reinterpret_cast<float4 *>(&s_f[wid][lane][0]);
+#pragma unroll
+                for (int q = 0; q < D / 4; ++q) fr[q] = make_float4(f[4 * q], f[4 * q + 1], f[4 * q + 2], f[4 * q + 3]);
+            }
+            __syncwarp();
+#pragma unroll 4
+            for (int px = 0; px < 32; ++px) {
                 if constexpr (D > 0) {
-                    constexpr int DP = D < 8 ? 8 : D;
-                    float vals[DP];
+                    const float zk = s_dz[wid][px][kr];
+                    if constexpr (EPL % 4 == 0) {
+                        const float4 *fr = reinterpret_cast<const float4 *>(&s_f[wid][px][d0]);
 #pragma unroll
-                    for (int d = 0; d < DP; ++d) vals[d] = d < D ? dz[k] * f[d] : 0.f;
-                    const float r = warp_transpose_reduce<DP>(vals, lane);
-                    if (lane < D && r != 0.f) atomicAdd(&s_dW[k * D + lane], r);
+                        for (int q = 0; q < EPL / 4; ++q) {
+                            const float4 fv = fr[q];
+                            accW[4 * q] = fmaf(zk, fv.x, accW[4 * q]);
+                            accW[4 * q + 1] = fmaf(zk, fv.y, accW[4 * q + 1]);
+                            accW[4 * q + 2] = fmaf(zk, fv.z, accW[4 * q + 2]);
+                            accW[4 * q + 3] = fmaf(zk, fv.w, accW[4 * q + 3]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < EPL; ++e) accW[e] = fmaf(zk, s_f[wid][px][d0 + e], accW[e]);
+                    }
                 }
+                if (lane < KC) accb += s_dz[wid][px][lane];
+            }
+            __syncwarp();
+        }
+    }
+    if (K > 0) {
+        if constexpr (D > 0) {
+            if (kr < K) {
+#pragma unroll
+                for (int e = 0; e < EPL; ++e)
+                    if (accW[e] != 0.f) atomicAdd(&s_dW[kr * D + d0 + e], accW[e]);
             }
         }
-        if (K > 0) {
-            float vals[kMaxK];
-#pragma unroll
-            for (int k = 0; k < kMaxK; ++k) vals[k] = dz[k];
-            const float r = warp_transpose_reduce<kMaxK>(vals, lane);
-            if (lane < K && r != 0.f) atomicAdd(&s_dW[K * D + lane], r);
-        }
+        if (lane < K && accb != 0.f) atomicAdd(&s_dW[K * D + lane], accb);
     }
     // per-block partials, weighted and normalised by the view's pixel count
     const double wc = block_sum_f64((double)lc * lp.color / (double)Pv, s_red);
     const double wd = block_sum_f64((double)ld * lp.depth / (double)Pv, s_red);
     const double wsm = block_sum_f64((double)ls * lp.sem / (double)Pv, s_red);
     __syncthreads();
-    for (int j = tid; j < nval; j += 256) part_f[(size_t)blk * nval + j] = s_dW[j];
+    for (int j = tid; j < nval; j += NT) part_f[(size_t)blk * nval + j] = s_dW[j];
     if (tid == 0) {
         part_d[3 * blk] = wc;
         part_d[3 * blk + 1] = wd;
@@ -518,9 +562,14 @@ gs_status launch_loss(const ViewTable &vt, const LossP &lp, const gs_images *img
                       float *median_out, cudaStream_t st) {
     const int bx = loss_blocks_x(vt);
     dim3 grid(bx, vt.n_views);
-    loss_kernel<D><<<grid, 256, 0, st>>>(vt, lp, img->rgb, img->depth, img->sil, img->feat, tgt->rgb, tgt->depth,
-                                         tgt->label, W, b, P, mh, g->rgb, g->depth, g->sil, g->feat, part_f, part_d,
-                                         mask_out, median_out);
+    if (lp.K <= 8)
+        loss_kernel<D, 8><<<grid, LossShape<D, 8>::NT, 0, st>>>(
+            vt, lp, img->rgb, img->depth, img->sil, img->feat, tgt->rgb, tgt->depth, tgt->label, W, b, P, mh, g->rgb,
+            g->depth, g->sil, g->feat, part_f, part_d, mask_out, median_out);
+    else
+        loss_kernel<D, kMaxK><<<grid, LossShape<D, kMaxK>::NT, 0, st>>>(
+            vt, lp, img->rgb, img->depth, img->sil, img->feat, tgt->rgb, tgt->depth, tgt->label, W, b, P, mh, g->rgb,
+            g->depth, g->sil, g->feat, part_f, part_d, mask_out, median_out);
     loss_finish_kernel<<<lp.K * D + lp.K + 4, 256, 0, st>>>(bx * vt.n_views, lp.K, D, part_f, part_d, dW, db,
                                                              loss_out);
     return last_launch();

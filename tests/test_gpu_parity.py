@@ -292,10 +292,19 @@ def _loss_case(P_shape=(48, 64), D=16, K=8, seed=20, views=1):
 @pytest.mark.parametrize("mode", ["mapping", "tracking"])
 @pytest.mark.parametrize("views", [1, 2])
 def test_loss_matches_oracle(mode, views):
-    cams, imgs, tgts, dec = _loss_case(views=views)
+    _check_loss(mode, views, 16, 8)
+
+
+@pytest.mark.parametrize("D,K", [(32, 13), (8, 32), (4, 3), (32, 8)])
+def test_loss_feature_and_class_widths(D, K):
+    """The compile-time class bounds (8 and 32) and every staged feature width."""
+    _check_loss("mapping", 1, D, K)
+
+
+def _check_loss(mode, views, D, K):
+    cams, imgs, tgts, dec = _loss_case(views=views, D=D, K=K)
     w = raster.MAPPING if mode == "mapping" else raster.TRACKING
     wo = oracle.MAPPING if mode == "mapping" else oracle.TRACKING
-    D, K = 16, dec.W.shape[0]
     r = raster.Renderer(0, cams, D, 0, n_classes=K)
     cat = lambda key, f=lambda a: a: torch.as_tensor(np.concatenate([f(im[key]).reshape(im[key].shape[0], -1)
                                                                      if im[key].ndim == 3 else f(im[key]).reshape(1, -1)
