@@ -165,3 +165,44 @@ def oracle_multiview_backward(gs, cams, prm, projs, bins, grads_per_view):
         toff += ((c.width + 15) // 16) * ((c.height + 15) // 16)
     out["twist"] = np.stack(twists)
     return out
+
+
+def bwd_compare(gs, cams, prm_g, prm_o, seed=7, rgb_dtype=torch.float32, feat_dtype=torch.float32,
+                gs_oracle=None):
+    """Forward images and every gradient of the CUDA path against the oracle, over several views,
+    for random upstream image gradients that are zero at pixels excluded by the comparison rules."""
+    field, r = gpu_forward(gs, cams, prm_g, rgb_dtype=rgb_dtype, feat_dtype=feat_dtype)
+    gso = gs if gs_oracle is None else gs_oracle
+    projs, bins, oimgs = oracle_multiview(gso, cams, prm_o)
+    gp = gpu_projection(r)
+    grads_v, P_off = [], 0
+    for v, cam in enumerate(cams):
+        sl = slice(v * gs.n, (v + 1) * gs.n)
+        gpv = {k: a[sl] for k, a in gp.items()}
+        excl, _ = excluded_pixels(cam, projs[v], gpv, oimgs[v])
+        assert_forward_close(np_images(r, v), oimgs[v], excl, gs.feat_dim)
+        P = cam.width * cam.height
+        g = random_image_grads(P, gs.feat_dim, seed + v)
+        keep = ~excl.ravel()
+        for k in g:
+            g[k] = g[k] * keep
+        grads_v.append({k: a.reshape((-1, cam.height, cam.width) if a.ndim == 2 else (cam.height, cam.width))
+                        for k, a in g.items()})
+        # upload into the renderer's image-gradient buffers
+        a, b = r.pix_off[v], r.pix_off[v + 1]
+        r.g_rgb[:, a:b] = torch.as_tensor(g["rgb"], dtype=torch.float32)
+        r.g_depth[a:b] = torch.as_tensor(g["depth"], dtype=torch.float32)
+        r.g_sil[a:b] = torch.as_tensor(g["sil"], dtype=torch.float32)
+        if gs.feat_dim:
+            r.g_feat[:, a:b] = torch.as_tensor(g["feat"], dtype=torch.float32)
+    r.backward(field, L.GS_GRAD_MAP | L.GS_GRAD_POSE)
+    torch.cuda.synchronize()
+    ob = oracle_multiview_backward(gso, cams, prm_o, projs, bins, grads_v)
+    D = gs.feat_dim
+    got = dict(means=r.d_means, quats=r.d_quats, log_scales=r.d_log_scales, opacity_logits=r.d_logits, rgb=r.d_rgb,
+               feat=r.d_feat[:, :D], twist=r.d_twist)
+    for k, t in got.items():
+        if k == "feat" and D == 0:
+            continue
+        assert_grad_close(k, t.cpu().numpy(), ob[k])
+    return r, ob

@@ -110,50 +110,11 @@ def test_render_fwd_matches_oracle(name):
     np.testing.assert_allclose(gimg["sil"] + gimg["T"], 1.0, atol=1e-5)
 
 
-def _bwd_compare(gs, cams, prm_g, prm_o, seed=7, rgb_dtype=torch.float32, feat_dtype=torch.float32,
-                 gs_oracle=None):
-    field, r = C.gpu_forward(gs, cams, prm_g, rgb_dtype=rgb_dtype, feat_dtype=feat_dtype)
-    gso = gs if gs_oracle is None else gs_oracle
-    projs, bins, oimgs = C.oracle_multiview(gso, cams, prm_o)
-    gp = C.gpu_projection(r)
-    grads_v, P_off = [], 0
-    for v, cam in enumerate(cams):
-        sl = slice(v * gs.n, (v + 1) * gs.n)
-        gpv = {k: a[sl] for k, a in gp.items()}
-        excl, _ = C.excluded_pixels(cam, projs[v], gpv, oimgs[v])
-        C.assert_forward_close(C.np_images(r, v), oimgs[v], excl, gs.feat_dim)
-        P = cam.width * cam.height
-        g = C.random_image_grads(P, gs.feat_dim, seed + v)
-        keep = ~excl.ravel()
-        for k in g:
-            g[k] = g[k] * keep
-        grads_v.append({k: a.reshape((-1, cam.height, cam.width) if a.ndim == 2 else (cam.height, cam.width))
-                        for k, a in g.items()})
-        # upload into the renderer's image-gradient buffers
-        a, b = r.pix_off[v], r.pix_off[v + 1]
-        r.g_rgb[:, a:b] = torch.as_tensor(g["rgb"], dtype=torch.float32)
-        r.g_depth[a:b] = torch.as_tensor(g["depth"], dtype=torch.float32)
-        r.g_sil[a:b] = torch.as_tensor(g["sil"], dtype=torch.float32)
-        if gs.feat_dim:
-            r.g_feat[:, a:b] = torch.as_tensor(g["feat"], dtype=torch.float32)
-    r.backward(field, L.GS_GRAD_MAP | L.GS_GRAD_POSE)
-    torch.cuda.synchronize()
-    ob = C.oracle_multiview_backward(gso, cams, prm_o, projs, bins, grads_v)
-    D = gs.feat_dim
-    got = dict(means=r.d_means, quats=r.d_quats, log_scales=r.d_log_scales, opacity_logits=r.d_logits, rgb=r.d_rgb,
-               feat=r.d_feat[:, :D], twist=r.d_twist)
-    for k, t in got.items():
-        if k == "feat" and D == 0:
-            continue
-        C.assert_grad_close(k, t.cpu().numpy(), ob[k])
-    return r, ob
-
-
 @pytest.mark.parametrize("name", list(CASES))
 def test_render_bwd_matches_oracle(name):
     gs, cam = CASES[name]()
     prm_g, prm_o = C.params_pair()
-    _bwd_compare(gs, [cam], prm_g, prm_o)
+    C.bwd_compare(gs, [cam], prm_g, prm_o)
 
 
 @pytest.mark.parametrize("np_", [1, 2, 4])
@@ -245,7 +206,7 @@ def test_render_bwd_multiview_sums_views():
     poses = synth.keyframe_loop(8, room=room)
     cams = [synth.camera(160, 96, 80.0, T_cw=poses[1]), synth.camera(100, 70, 60.0, T_cw=poses[4])]
     prm_g, prm_o = C.params_pair()
-    _bwd_compare(gs, cams, prm_g, prm_o)
+    C.bwd_compare(gs, cams, prm_g, prm_o)
 
 
 def test_half_storage_matches_oracle_on_rounded_values():
@@ -255,7 +216,7 @@ def test_half_storage_matches_oracle_on_rounded_values():
     rounded.rgb = torch.as_tensor(gs.rgb).to(torch.float16).float().numpy()
     rounded.feat = torch.as_tensor(gs.feat).to(torch.bfloat16).float().numpy()
     prm_g, prm_o = C.params_pair()
-    _bwd_compare(gs, [cam], prm_g, prm_o, rgb_dtype=torch.float16, feat_dtype=torch.bfloat16, gs_oracle=rounded)
+    C.bwd_compare(gs, [cam], prm_g, prm_o, rgb_dtype=torch.float16, feat_dtype=torch.bfloat16, gs_oracle=rounded)
 
 
 def test_pose_translation_gradient_invariant_on_gpu():
