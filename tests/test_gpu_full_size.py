@@ -145,3 +145,95 @@ def test_differentiation_form_gradients_match_central_differences():
     assert len(resolved) >= 56
     assert {x[0] for x in resolved} == {n for n, _ in _GROUPS}
     assert max(err.values()) < 2e-3, err
+
+
+def _precision_form_scene():
+    room = synth.make_room(synth.SEED_SCENE)
+    gs = synth.room_field(2_000_000, 32, seed=synth.SEED_SCENE, room=room)
+    loop = synth.keyframe_loop(room=room)
+    cams = [synth.camera(1200, 680, 600.0, T_cw=loop[i]) for i in synth.draw_keyframes(8)]
+    return gs, cams
+
+
+def test_precision_form_errors_against_oracle():
+    """8 keyframes of a 2M-Gaussian field with BF16 features and FP16 colours, forward and
+    backward in one batch.  Checked on a 24 x 12-tile window of the first keyframe (every
+    Gaussian whose rectangle meets it, so the window is exact): against the oracle fed the
+    same rounded values within the FP32 tolerances, and against the unrounded FP64 field
+    within the storage rounding (per pixel: 2^-11 of the blended |colour| and 2^-8 of the
+    blended |feature|), with the errors per output printed."""
+    gs, cams = _precision_form_scene()
+    D = 32
+    rounded = gs.copy()
+    rounded.rgb = torch.as_tensor(gs.rgb).to(torch.float16).double().numpy()
+    rounded.feat = torch.as_tensor(gs.feat).to(torch.bfloat16).double().numpy()
+    prm_g, prm_o = C.params_pair()
+    field, r = C.gpu_forward(gs, cams, prm_g, rgb_dtype=torch.float16, feat_dtype=torch.bfloat16, want_keys=False)
+    assert r.status() == 0
+    cam = cams[0]
+    H, W = cam.height, cam.width
+    TX, TY = (W + 15) // 16, (H + 15) // 16
+    win = (TX // 2 - 12, TY // 2 - 6, TX // 2 + 12, TY // 2 + 6)
+    rect = oracle.project(gs, cam, prm_o)["rect"]
+    meets = (rect[:, 0] < win[2]) & (rect[:, 2] > win[0]) & (rect[:, 1] < win[3]) & (rect[:, 3] > win[1])
+    idx = np.nonzero(meets)[0]
+    gp = C.gpu_projection(r)
+    gsub = {k: a[:gs.n][idx] for k, a in gp.items()}
+    in_win = np.zeros((H, W), bool)
+    in_win[16 * win[1]:16 * win[3], 16 * win[0]:16 * win[2]] = True
+
+    oracle_runs = {}
+    for label, src in (("rounded", rounded), ("fp64", gs)):
+        sub = src.subset(idx)
+        op, ob, oimg = oracle.forward(sub, cam, prm_o)
+        oracle_runs[label] = (sub, op, ob, oimg)
+    excl, _ = C.excluded_pixels(cam, oracle_runs["rounded"][1], gsub, oracle_runs["rounded"][3])
+    keep = in_win & ~excl
+    assert keep.sum() > 0.95 * in_win.sum()
+    gimg = C.np_images(r, 0)
+
+    # forward: parity with the rounded values; storage error against FP64
+    C.assert_forward_close(gimg, oracle_runs["rounded"][3], ~keep, D)
+    sub_abs = gs.subset(idx)
+    sub_abs.rgb, sub_abs.feat = np.abs(sub_abs.rgb), np.abs(sub_abs.feat)
+    absimg = oracle.forward(sub_abs, cam, prm_o)[2]
+    o64 = oracle_runs["fp64"][3]
+    err_rgb = np.abs(gimg["rgb"] - o64["rgb"])[:, keep]
+    err_feat = np.abs(gimg["feat"] - o64["feat"])[:, keep]
+    bound_rgb = 2.0 ** -11 * (absimg["rgb"] - absimg["T"] * np.asarray(prm_o.bg)[:, None, None])[:, keep] + C.TOL_ABS
+    bound_feat = 2.0 ** -8 * absimg["feat"][:, keep] + C.TOL_ABS
+    print("precision form, forward vs FP64 (window of keyframe 0): rgb max abs %.3e, feat max abs %.3e, "
+          "rgb max/bound %.3f, feat max/bound %.3f" % (err_rgb.max(), err_feat.max(), (err_rgb / bound_rgb).max(),
+                                                       (err_feat / bound_feat).max()))
+    assert (err_rgb <= bound_rgb).all() and (err_feat <= bound_feat).all()
+
+    # backward: upstream gradients on the kept window pixels of keyframe 0 only
+    g = C.random_image_grads(H * W, D, 23)
+    m = keep.ravel()
+    for k in g:
+        g[k] = g[k] * m
+    for t in (r.g_rgb, r.g_depth, r.g_sil, r.g_feat):
+        t.zero_()
+    r.g_rgb[:, :H * W] = torch.as_tensor(g["rgb"], dtype=torch.float32)
+    r.g_depth[:H * W] = torch.as_tensor(g["depth"], dtype=torch.float32)
+    r.g_sil[:H * W] = torch.as_tensor(g["sil"], dtype=torch.float32)
+    r.g_feat[:, :H * W] = torch.as_tensor(g["feat"], dtype=torch.float32)
+    r.backward(field, L.GS_GRAD_MAP)
+    torch.cuda.synchronize()
+    got = {k: t.cpu().numpy().astype(np.float64)[idx] for k, t in
+           dict(means=r.d_means, quats=r.d_quats, log_scales=r.d_log_scales, opacity_logits=r.d_logits,
+                rgb=r.d_rgb, feat=r.d_feat).items()}
+    gimgs = {k: a.reshape((-1, H, W) if a.ndim == 2 else (H, W)) for k, a in g.items()}
+    report = {}
+    for label in ("rounded", "fp64"):
+        sub, op, ob, _ = oracle_runs[label]
+        want = oracle.backward_from_image_grads(sub, cam, prm_o, op, ob, gimgs)
+        errs = {}
+        for k in got:
+            rmax = np.abs(want[k]).max()
+            errs[k] = float(np.abs(got[k] - want[k]).max() / rmax)
+            if label == "rounded":
+                C.assert_grad_close(k, got[k], want[k])
+        report[label] = errs
+    print("precision form, gradient max error / group max:", report)
+    assert max(report["fp64"].values()) < 2e-2
