@@ -382,6 +382,43 @@ struct Kahan {
 
 constexpr int kRedBlocks = 512;
 
+// Calls f(i, x[i]) for the elements of x this thread owns: block b owns a contiguous range
+// (a multiple of 4 long), which its threads read as float4 with four loads in flight per
+// iteration (scalar loads if x is not 16-byte aligned); a fixed assignment, so per-thread
+// sums are reproducible.
+template <typename F>
+__device__ __forceinline__ void for_my_elements(int64_t m, const float *x, F f) {
+    const int64_t per = ((m + gridDim.x - 1) / gridDim.x + 3) / 4 * 4;
+    const int64_t b0 = (int64_t)blockIdx.x * per, b1 = min(m, b0 + per);
+    if (b0 >= b1) return;
+    if (reinterpret_cast<uintptr_t>(x) & 15) {
+        for (int64_t e = b0 + threadIdx.x; e < b1; e += blockDim.x) f(e, x[e]);
+        return;
+    }
+    const int64_t n4 = (b1 - b0) / 4;
+    const float4 *x4 = reinterpret_cast<const float4 *>(x + b0);
+    for (int64_t i = threadIdx.x; i < n4; i += 4 * (int64_t)blockDim.x) {
+        float4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t j = i + u * (int64_t)blockDim.x;
+            v[u] = j < n4 ? x4[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t j = i + u * (int64_t)blockDim.x;
+            if (j < n4) {
+                const int64_t e = b0 + 4 * j;
+                f(e, v[u].x);
+                f(e + 1, v[u].y);
+                f(e + 2, v[u].z);
+                f(e + 3, v[u].w);
+            }
+        }
+    }
+    for (int64_t e = b0 + 4 * n4 + threadIdx.x; e < b1; e += blockDim.x) f(e, x[e]);
+}
+
 // Sum of a strided f64 partial column over nb blocks, by the whole block (fixed order).
 __device__ double sum_partials(const double *part, int stride, int col, int nb, double *s_red) {
     double x = 0;
@@ -392,11 +429,11 @@ __device__ double sum_partials(const double *part, int stride, int col, int nb, 
 __global__ void __launch_bounds__(256) dsr_stats_kernel(int64_t m, const float *ls, double *part) {
     __shared__ double s_red[8];
     Kahan s1, s2;
-    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < m; i += (int64_t)gridDim.x * 256) {
-        const float s = expf(ls[i]);
+    for_my_elements(m, ls, [&](int64_t, float l) {
+        const float s = expf(l);
         s1.add(s);
         s2.add(s * s);
-    }
+    });
     const double t1 = block_sum_f64((double)s1.s - s1.c, s_red);
     const double t2 = block_sum_f64((double)s2.s - s2.c, s_red);
     if (threadIdx.x == 0) {
@@ -405,86 +442,86 @@ __global__ void __launch_bounds__(256) dsr_stats_kernel(int64_t m, const float *
     }
 }
 
-struct DsrBounds {
-    float hi, lo;
-    double mu, sd;
-};
-
-__device__ DsrBounds dsr_bounds(const double *stats_part, int nb, int64_t m) {
+// One block: the population mean and deviation of the 3N scales from the stats partials,
+// written to out[1], out[2] (the constants of Eq. 12, detached).
+__global__ void __launch_bounds__(256) dsr_finish_stats_kernel(int nb, int64_t m, const double *stats_part,
+                                                               double *out) {
     __shared__ double s_red[8];
-    __shared__ double s_mu, s_var;
     const double t1 = sum_partials(stats_part, 2, 0, nb, s_red);
     const double t2 = sum_partials(stats_part, 2, 1, nb, s_red);
     if (threadIdx.x == 0) {
-        s_mu = t1 / (double)m;
-        s_var = t2 / (double)m - s_mu * s_mu;
+        const double mu = t1 / (double)m, var = t2 / (double)m - mu * mu;
+        out[1] = mu;
+        out[2] = sqrt(var > 0 ? var : 0.0);
     }
-    __syncthreads();
-    DsrBounds b;
-    b.mu = s_mu;
-    b.sd = sqrt(s_var > 0 ? s_var : 0.0);
-    b.hi = (float)(b.mu + 2.0 * b.sd);
-    b.lo = (float)(b.mu - 2.0 * b.sd);
-    return b;
 }
 
-__global__ void __launch_bounds__(256) dsr_mask_kernel(int64_t m, const float *ls, const double *stats_part,
+// Thresholds mu +- 2 sigma in f32, formed the same way by both passes that compare against them.
+__device__ __forceinline__ float2 dsr_bounds(const double *out) {
+    return make_float2((float)(out[1] + 2.0 * out[2]), (float)(out[1] - 2.0 * out[2]));
+}
+
+__global__ void __launch_bounds__(256) dsr_mask_kernel(int64_t m, const float *ls, const double *out,
                                                        double *mask_part) {
     __shared__ double s_red[8];
-    const DsrBounds bd = dsr_bounds(stats_part, gridDim.x, m);
+    const float2 bd = dsr_bounds(out);
     Kahan sb, ss;
     int nb = 0, ns = 0;
-    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < m; i += (int64_t)gridDim.x * 256) {
-        const float l = ls[i];
+    for_my_elements(m, ls, [&](int64_t, float l) {
         const float s = expf(l);
-        if (s > bd.hi) { sb.add(s); ++nb; }
-        if (s < bd.lo) { ss.add(-l); ++ns; }
-    }
+        if (s > bd.x) { sb.add(s); ++nb; }
+        if (s < bd.y) { ss.add(-l); ++ns; }
+    });
     const double t[4] = {block_sum_f64((double)sb.s - sb.c, s_red), block_sum_f64((double)nb, s_red),
                          block_sum_f64((double)ss.s - ss.c, s_red), block_sum_f64((double)ns, s_red)};
     if (threadIdx.x == 0)
         for (int k = 0; k < 4; ++k) mask_part[4 * blockIdx.x + k] = t[k];
 }
 
-__global__ void __launch_bounds__(256) dsr_grad_kernel(int64_t m, const float *ls, float lam_big, float lam_small,
-                                                       const double *stats_part, const double *mask_part,
-                                                       float *d_ls, double *out) {
+// One block: the sizes and means of the two sets and the regulariser's value,
+// out = (lam_big L_big + lam_small L_small, mu, sigma, n_big, n_small, L_big, L_small, 0).
+__global__ void __launch_bounds__(256) dsr_finish_mask_kernel(int nb, const double *mask_part, float lam_big,
+                                                              float lam_small, double *out) {
     __shared__ double s_red[8];
-    __shared__ double s_t[4];
-    const DsrBounds bd = dsr_bounds(stats_part, gridDim.x, m);
-    for (int k = 0; k < 4; ++k) {
-        const double t = sum_partials(mask_part, 4, k, gridDim.x, s_red);
-        if (threadIdx.x == 0) s_t[k] = t;
+    double t[4];
+    for (int k = 0; k < 4; ++k) t[k] = sum_partials(mask_part, 4, k, nb, s_red);
+    if (threadIdx.x == 0) {
+        const double Lb = t[1] > 0 ? t[0] / t[1] : 0.0, Ls = t[3] > 0 ? t[2] / t[3] : 0.0;
+        out[0] = (double)lam_big * Lb + (double)lam_small * Ls;
+        out[3] = t[1];
+        out[4] = t[3];
+        out[5] = Lb;
+        out[6] = Ls;
+        out[7] = 0.0;
     }
-    __syncthreads();
-    const double sum_b = s_t[0], nb = s_t[1], sum_s = s_t[2], ns = s_t[3];
+}
+
+__global__ void __launch_bounds__(256) dsr_grad_kernel(int64_t m, const float *ls, float lam_big, float lam_small,
+                                                       const double *out, float *d_ls) {
+    const float2 bd = dsr_bounds(out);
+    const double nb = out[3], ns = out[4];
     const float gb = nb > 0 ? (float)(lam_big / nb) : 0.f;
     const float gsm = ns > 0 ? (float)(lam_small / ns) : 0.f;
-    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < m; i += (int64_t)gridDim.x * 256) {
-        const float s = expf(ls[i]);
+    for_my_elements(m, ls, [&](int64_t i, float l) {
+        const float s = expf(l);
         float g = 0.f;
-        if (s > bd.hi) g += gb * s;
-        if (s < bd.lo) g -= gsm;
+        if (s > bd.x) g += gb * s;
+        if (s < bd.y) g -= gsm;
         if (g != 0.f) d_ls[i] += g;
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        const double Lb = nb > 0 ? sum_b / nb : 0.0, Ls = ns > 0 ? sum_s / ns : 0.0;
-        out[0] = (double)lam_big * Lb + (double)lam_small * Ls;
-        out[1] = bd.mu; out[2] = bd.sd; out[3] = nb; out[4] = ns; out[5] = Lb; out[6] = Ls; out[7] = 0.0;
-    }
+    });
 }
 
 // ------------------------------------------------------------ pose reduction
 // Block (x, vk) sums a contiguous slice of component vk in compensated f32 and
 // adds its f64 total into d_twist[vk] (at most kPoseBlocks adds per value).
-constexpr int kPoseBlocks = 64;
+constexpr int kPoseBlocks = 128;
 
 __global__ void __launch_bounds__(256) pose_reduce_kernel(int64_t n, const float *pose_part, double *d_twist) {
     __shared__ double s_red[8];
     const int vk = blockIdx.y;  // view * 6 + component
     const float *p = pose_part + (int64_t)vk * n;
     Kahan s;
-    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) s.add(p[i]);
+    for_my_elements(n, p, [&](int64_t, float x) { s.add(x); });
     const double t = block_sum_f64((double)s.s - s.c, s_red);
     if (threadIdx.x == 0 && t != 0) atomicAdd(&d_twist[vk], t);
 }
@@ -634,9 +671,10 @@ extern "C" gs_status gs_dsr(int64_t n, const float *log_scales, float lam_big, f
     const int64_t m = 3 * n;
     const int grid = std::min(ceil_div(m, 256), kRedBlocks);
     dsr_stats_kernel<<<grid, 256, 0, st>>>(m, log_scales, part);
-    dsr_mask_kernel<<<grid, 256, 0, st>>>(m, log_scales, part, part + 2 * kRedBlocks);
-    dsr_grad_kernel<<<grid, 256, 0, st>>>(m, log_scales, lam_big, lam_small, part, part + 2 * kRedBlocks,
-                                          d_log_scales, out);
+    dsr_finish_stats_kernel<<<1, 256, 0, st>>>(grid, m, part, out);
+    dsr_mask_kernel<<<grid, 256, 0, st>>>(m, log_scales, out, part + 2 * kRedBlocks);
+    dsr_finish_mask_kernel<<<1, 256, 0, st>>>(grid, part + 2 * kRedBlocks, lam_big, lam_small, out);
+    dsr_grad_kernel<<<grid, 256, 0, st>>>(m, log_scales, lam_big, lam_small, out, d_log_scales);
     (void)s;
     return last_launch();
 }
