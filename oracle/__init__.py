@@ -57,6 +57,7 @@ def _L():
         _lib.or_bin_sort.restype = ctypes.c_int64
         _lib.or_loss.restype = ctypes.c_double
         _lib.or_dsr.restype = ctypes.c_double
+        _lib.or_ssim.restype = ctypes.c_double
         _lib.or_lower_median.restype = ctypes.c_double
     return _lib
 
@@ -199,9 +200,11 @@ class LossWeights:
     small: float = 0.001
     mask_mode: int = 0      # 0 mapping (no mask), 1 tracking (Eq. 21 mask)
     tau_obs: float = 0.99
+    ssim: float = 0.0       # lambda of Eq. 15: colour = (1 - lambda) L1 + lambda (1 - SSIM); mapping only
 
 
 MAPPING = LossWeights()
+MAPPING_SSIM = LossWeights(ssim=0.2)          # Eq. 15 with the paper's lambda = 0.2
 TRACKING = LossWeights(color=0.5, depth=1.0, sem=0.001, big=0.0, small=0.0, mask_mode=1)
 
 
@@ -214,17 +217,37 @@ def loss(images, target, dec, w: LossWeights):
     out = dict(rgb=np.zeros((3, H, W)), depth=np.zeros((H, W)), sil=np.zeros((H, W)),
                feat=np.zeros((D, H, W)), W=np.zeros((K, D)), b=np.zeros(K), mask=np.zeros((H, W)),
                terms=np.zeros(3), median=np.zeros(1))
+    if w.ssim and w.mask_mode != 0:
+        raise ValueError("the SSIM term belongs to the mapping loss (tracking colour is L1 only)")
     med = ctypes.c_double(0)
     a = [_d(rgb), _d(depth), _d(sil), _d(feat), _d(target.rgb), _d(target.depth)]
     total = _L().or_loss(I64(P), ctypes.c_int(D), ctypes.c_int(K), *map(_p, a),
                          _p(np.ascontiguousarray(target.label, np.uint8)), _p(_d(dec.W)), _p(_d(dec.b)),
-                         ctypes.c_double(w.color), ctypes.c_double(w.depth), ctypes.c_double(w.sem),
-                         ctypes.c_int(w.mask_mode), ctypes.c_double(w.tau_obs),
+                         ctypes.c_double(w.color * (1.0 - w.ssim)), ctypes.c_double(w.depth),
+                         ctypes.c_double(w.sem), ctypes.c_int(w.mask_mode), ctypes.c_double(w.tau_obs),
                          *(_p(out[k]) for k in ("rgb", "depth", "sil", "feat", "W", "b", "mask", "terms")),
                          ctypes.byref(med))
+    if w.ssim:
+        # Eq. 15: colour = lambda_c ((1 - lambda) L1 + lambda (1 - SSIM))
+        s, g = ssim(rgb, target.rgb)
+        term = w.color * w.ssim * (1.0 - s)
+        out["terms"][0] += term
+        total += term
+        out["rgb"] -= w.color * w.ssim * g
+        out["ssim"] = s
     out["median"] = med.value
     out["total"] = total
     return out
+
+
+def ssim(x, y):
+    """Mean SSIM of two [3, H, W] images (11x11 Gaussian window, sigma 1.5, zero padding,
+    C1 = 0.01^2, C2 = 0.03^2) and its gradient with respect to x."""
+    x, y = _d(x), _d(y)
+    H, W = x.shape[1], x.shape[2]
+    grad = np.zeros_like(x)
+    val = _L().or_ssim(I64(H), I64(W), _p(x), _p(y), _p(grad))
+    return val, grad
 
 
 def lower_median(values):

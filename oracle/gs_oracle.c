@@ -848,3 +848,85 @@ void or_pose_step(double *T, const double *grad, double *m, double *v, int step,
         }
     memcpy(T, out, sizeof(out));
 }
+
+/* ------------------------------------------------------------------ SSIM
+ * Structural similarity (Wang et al. 2004) of the rendered and observed colour,
+ * the D-SSIM part of the mapping colour loss (Eq. 15, read as 1 - SSIM):
+ * per channel and pixel p, the window moments over an 11x11 Gaussian window
+ * (sigma 1.5, weights summing to one; pixels outside the image count as zero)
+ *   mx = sum w x, my = sum w y, sx = sum w x^2 - mx^2, sy = sum w y^2 - my^2,
+ *   sxy = sum w x y - mx my,
+ *   S(p) = (2 mx my + C1)(2 sxy + C2) / ((mx^2 + my^2 + C1)(sx + sy + C2)),
+ * C1 = 0.01^2, C2 = 0.03^2 (intensities in [0, 1]).  Returns the mean of S over
+ * the 3 H W positions; grad (may be NULL) receives d(mean)/dx.  With the window
+ * symmetric, dS(p)/dx(q) = w(q - p) (A(p) + 2 B(p) x(q) + C(p) y(q)) where
+ * A = dS/dmx - 2 mx dS/dsx - my dS/dsxy, B = dS/dsx, C = dS/dsxy, so the
+ * gradient is one more pass of the window over the maps A, B, C. */
+double or_ssim(int64_t H, int64_t W, const double *x, const double *y, double *grad) {
+    double g[11], gs = 0.0;
+    for (int k = 0; k < 11; k++) {
+        g[k] = exp(-(double)((k - 5) * (k - 5)) / (2.0 * 1.5 * 1.5));
+        gs += g[k];
+    }
+    for (int k = 0; k < 11; k++) g[k] /= gs;
+    const double C1 = 0.01 * 0.01, C2 = 0.03 * 0.03;
+    const int64_t P = H * W;
+    double *A = NULL, *B = NULL, *Cm = NULL;
+    if (grad) {
+        A = (double *)calloc((size_t)P, sizeof(double));
+        B = (double *)calloc((size_t)P, sizeof(double));
+        Cm = (double *)calloc((size_t)P, sizeof(double));
+    }
+    double total = 0.0;
+    for (int ch = 0; ch < 3; ch++) {
+        const double *xc = x + ch * P, *yc = y + ch * P;
+        for (int64_t py = 0; py < H; py++)
+            for (int64_t px = 0; px < W; px++) {
+                double mx = 0, my = 0, mxx = 0, myy = 0, mxy = 0;
+                for (int dy = -5; dy <= 5; dy++)
+                    for (int dx = -5; dx <= 5; dx++) {
+                        const int64_t qy = py + dy, qx = px + dx;
+                        if (qy < 0 || qy >= H || qx < 0 || qx >= W) continue;
+                        const double w = g[dy + 5] * g[dx + 5];
+                        const double a = xc[qy * W + qx], b = yc[qy * W + qx];
+                        mx += w * a;
+                        my += w * b;
+                        mxx += w * a * a;
+                        myy += w * b * b;
+                        mxy += w * a * b;
+                    }
+                const double sx = mxx - mx * mx, sy = myy - my * my, sxy = mxy - mx * my;
+                const double N1 = 2 * mx * my + C1, N2 = 2 * sxy + C2;
+                const double D1 = mx * mx + my * my + C1, D2 = sx + sy + C2;
+                const double S = N1 * N2 / (D1 * D2);
+                total += S;
+                if (grad) {
+                    const double dS_dmx = 2 * my * N2 / (D1 * D2) - S * 2 * mx / D1;
+                    const double dS_dsx = -S / D2;
+                    const double dS_dsxy = 2 * N1 / (D1 * D2);
+                    A[py * W + px] = dS_dmx - 2 * mx * dS_dsx - my * dS_dsxy;
+                    B[py * W + px] = dS_dsx;
+                    Cm[py * W + px] = dS_dsxy;
+                }
+            }
+        if (!grad) continue;
+        for (int64_t qy = 0; qy < H; qy++)
+            for (int64_t qx = 0; qx < W; qx++) {
+                double s = 0.0;
+                const double a = xc[qy * W + qx], b = yc[qy * W + qx];
+                for (int dy = -5; dy <= 5; dy++)
+                    for (int dx = -5; dx <= 5; dx++) {
+                        const int64_t py = qy + dy, px = qx + dx;
+                        if (py < 0 || py >= H || px < 0 || px >= W) continue;
+                        const double w = g[dy + 5] * g[dx + 5];
+                        const int64_t p = py * W + px;
+                        s += w * (A[p] + 2 * B[p] * a + Cm[p] * b);
+                    }
+                grad[ch * P + qy * W + qx] = s / (double)(3 * P);
+            }
+    }
+    free(A);
+    free(B);
+    free(Cm);
+    return total / (double)(3 * P);
+}

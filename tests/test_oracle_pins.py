@@ -572,3 +572,79 @@ def test_paper_hyperparameters_fixture():
         hp["mapping"]["lambda_big"], hp["mapping"]["lambda_small"])
     assert (t.color, t.depth, t.sem) == (hp["tracking"]["lambda_color"], hp["tracking"]["lambda_depth"],
                                          hp["tracking"]["lambda_sem"])
+    assert oracle.MAPPING_SSIM.ssim == hp["ssim_lambda"]
+
+
+# ---------------------------------------------------------------- SSIM (Eq. 15)
+def _gauss11():
+    k = np.arange(11) - 5
+    g = np.exp(-k ** 2 / (2 * 1.5 ** 2))
+    return g / g.sum()
+
+
+def test_ssim_of_identical_images_is_one_with_zero_gradient():
+    x = synth.rng(60).random((3, 14, 19))
+    s, g = oracle.ssim(x, x)
+    assert s == pytest.approx(1.0, abs=1e-15)
+    assert np.abs(g).max() < 1e-13
+
+
+def test_ssim_of_constant_images_closed_form():
+    """Constant images a and b: with zero padding a pixel whose window keeps mass m of the
+    weights sees mx = a m, sx = a^2 m (1 - m), sxy = a b m (1 - m), so every term of the
+    formula (C1, C2, the window, the padding) shows at the borders."""
+    H, W, a, b = 12, 23, 0.7, 0.25
+    g = _gauss11()
+    mass1 = lambda n: np.array([g[max(0, 5 - i):min(11, n + 5 - i)].sum() for i in range(n)])
+    m = np.outer(mass1(H), mass1(W))
+    C1, C2 = 1e-4, 9e-4
+    S = ((2 * a * b * m ** 2 + C1) * (2 * a * b * m * (1 - m) + C2)
+         / (((a * a + b * b) * m ** 2 + C1) * ((a * a + b * b) * m * (1 - m) + C2)))
+    s, _ = oracle.ssim(np.full((3, H, W), a), np.full((3, H, W), b))
+    assert s == pytest.approx(S.mean(), rel=1e-12)
+    assert (m < 0.999).any() and (m > 0.999).any()      # both borders and interior present
+
+
+def test_ssim_gradient_matches_central_differences():
+    r = synth.rng(61)
+    x, y = r.random((3, 13, 17)), r.random((3, 13, 17))
+    _, g = oracle.ssim(x, y)
+    h = 1e-6
+    for c, i, j in [(0, 0, 0), (1, 6, 8), (2, 12, 16), (0, 3, 15), (2, 10, 1)]:
+        xp, xm = x.copy(), x.copy()
+        xp[c, i, j] += h
+        xm[c, i, j] -= h
+        fd = (oracle.ssim(xp, y)[0] - oracle.ssim(xm, y)[0]) / (2 * h)
+        assert g[c, i, j] == pytest.approx(fd, rel=1e-6, abs=1e-12)
+
+
+def test_ssim_is_symmetric():
+    r = synth.rng(62)
+    x, y = r.random((3, 11, 12)), r.random((3, 11, 12))
+    assert oracle.ssim(x, y)[0] == pytest.approx(oracle.ssim(y, x)[0], rel=1e-14)
+
+
+def test_mapping_loss_with_ssim_is_eq15_and_its_gradient():
+    """lambda_c ((1 - lambda) L1 + lambda (1 - SSIM)) with lambda = 0.2, and the colour image
+    gradient of the whole mapping loss against central differences."""
+    r = synth.rng(63)
+    H, W, D, K = 12, 14, 4, 3
+    img = dict(rgb=r.random((3, H, W)), depth=r.uniform(2, 4, (H, W)), sil=r.random((H, W)),
+               feat=r.standard_normal((D, H, W)))
+    tgt = synth.Frame(r.random((3, H, W)), r.uniform(2, 4, (H, W)), r.integers(0, K, (H, W)).astype(np.uint8))
+    dec = synth.Decoder(r.standard_normal((K, D)), r.standard_normal(K))
+    w = oracle.MAPPING_SSIM
+    assert w.ssim == 0.2
+    out = oracle.loss(img, tgt, dec, w)
+    l1 = np.abs(img["rgb"] - tgt.rgb).sum() / (H * W)
+    s, _ = oracle.ssim(img["rgb"], tgt.rgb)
+    assert out["terms"][0] == pytest.approx(w.color * (0.8 * l1 + 0.2 * (1 - s)), rel=1e-12)
+    h = 1e-7
+    for c, i, j in [(0, 0, 0), (1, 5, 7), (2, 11, 13)]:
+        p, m_ = {k: v.copy() for k, v in img.items()}, {k: v.copy() for k, v in img.items()}
+        p["rgb"][c, i, j] += h
+        m_["rgb"][c, i, j] -= h
+        fd = (oracle.loss(p, tgt, dec, w)["total"] - oracle.loss(m_, tgt, dec, w)["total"]) / (2 * h)
+        assert out["rgb"][c, i, j] == pytest.approx(fd, rel=1e-5)
+    with pytest.raises(ValueError):
+        oracle.loss(img, tgt, dec, oracle.LossWeights(mask_mode=1, ssim=0.2))
