@@ -455,6 +455,25 @@ def run_ours(args, rank, world, local_rank):
 
     forms = None if args.no_forms else run_forms(args, gs, dec, dev, flush)
 
+    # the SSIM term of the paper's mapping colour loss (Eq. 15, lambda = 0.2) on the same frame:
+    # the loss step with and without it (events around 20 calls each)
+    def time_calls(fn, reps=20):
+        fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+    loss_ms = time_calls(lambda: r.loss(targets, W, b, raster.MAPPING))
+    loss_ssim_ms = time_calls(lambda: r.loss(targets, W, b, raster.MAPPING_SSIM))
+    ssim_bytes = 144 * r.P        # f32: forward reads 6, writes 9; backward reads 9 + 6, updates 3 (x2) per pixel
+    ssim_ms = loss_ssim_ms - loss_ms
+    extras = {"loss_ms": loss_ms, "loss_with_ssim_ms": loss_ssim_ms,
+              "ssim_term": {"ms": ssim_ms, "bytes": ssim_bytes,
+                            "GBps": ssim_bytes / (ssim_ms * 1e-3) / 1e9 if ssim_ms > 0 else None}}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(gs, cam, tgt, dec)
@@ -469,6 +488,7 @@ def run_ours(args, rank, world, local_rank):
                            autotune_ms={k: {str(n): round(t, 4) for n, t in v.items()} for k, v in tune_ms.items()}),
             "stages_ms": {s: float(t) for s, t in zip(stages, per_stage)},
             "forms": forms,
+            "extras": extras,
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "iters/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},

@@ -195,14 +195,19 @@ typedef struct {
     const uint8_t *label;
 } gs_targets;
 
-/* Loss weights and mode.  mask_mode 0 = mapping (Eq. 18 without the SSIM and
- * DSR terms), 1 = tracking (Eq. 21 with the M_obs mask, tau_obs threshold on
- * the silhouette).  n_classes = K of the linear decoder (<= 32). */
+/* Loss weights and mode.  mask_mode 0 = mapping (Eq. 18 without the DSR
+ * terms), 1 = tracking (Eq. 21 with the M_obs mask, tau_obs threshold on the
+ * silhouette).  n_classes = K of the linear decoder (<= 32).  ssim = lambda
+ * of Eq. 15 in [0, 1] (mapping only; the paper uses 0.2): the colour term
+ * becomes color ((1 - lambda) L1 + lambda (1 - SSIM)), SSIM over an 11x11
+ * Gaussian window (sigma 1.5, zero padding, C1 = 0.01^2, C2 = 0.03^2)
+ * averaged over the view's 3 P_v channel-pixels; 0 leaves the L1 term alone. */
 typedef struct {
     float color, depth, sem;
     int32_t mask_mode;
     float tau_obs;
     int32_t n_classes;
+    float ssim;
 } gs_loss_params;
 
 /* Library version (major * 10000 + minor * 100 + patch). */
@@ -299,7 +304,8 @@ gs_status gs_pose_grad(int64_t n, int n_views, const float *pose_part, double *d
 /* Decoder and losses (Eq. 8, 15-17, 21) with their gradients.  Per view v
  * with P_v pixels: logits z = W f + b (W: dec_W [K,D] f32, b: dec_b [K]);
  * L_v = (color sum |c - c_gt|_1 + depth sum_{d_gt>0} |d - d_gt| +
- * sem sum_{label != 255} (logsumexp z - z_label)) / P_v, times M_obs in
+ * sem sum_{label != 255} (logsumexp z - z_label)) / P_v (with the SSIM term of
+ * gs_loss_params.ssim in the colour part), times M_obs in
  * tracking mode (sil > tau_obs, d_gt > 0, |d - d_gt| < 10 x the lower median
  * of |d - d_gt| over the view's pixels with d_gt > 0).  Writes grad (all four
  * images; sil gradient is zero), d_dec_W, d_dec_b (overwritten), loss_out

@@ -72,7 +72,7 @@ class gs_targets(Structure):
 
 class gs_loss_params(Structure):
     _fields_ = [("color", c_float), ("depth", c_float), ("sem", c_float), ("mask_mode", c_int32),
-                ("tau_obs", c_float), ("n_classes", c_int32)]
+                ("tau_obs", c_float), ("n_classes", c_int32), ("ssim", c_float)]
 
 
 _P = POINTER

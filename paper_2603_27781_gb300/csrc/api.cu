@@ -61,7 +61,7 @@ bool make_params(const gs_raster_params *p, Params *out) {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-WsLayout ws_layout(int64_t n, int n_views, int64_t capacity) {
+WsLayout ws_layout(int64_t n, int n_views, int64_t capacity, const ViewTable *vt) {
     WsLayout L;
     memset(&L, 0, sizeof(L));
     int64_t vn = n * n_views;
@@ -88,8 +88,11 @@ WsLayout ws_layout(int64_t n, int n_views, int64_t capacity) {
     off = 0;
     L.med_hist = take(sizeof(uint32_t) * 4 * 256 * (size_t)n_views);
     L.loss_part_f = take(sizeof(float) * (size_t)kLossBlocks * (32 * 32 + 32));
-    L.loss_part_d = take(sizeof(double) * (size_t)kLossBlocks * 3);
+    const int64_t P = vt ? vt->pix_off[vt->n_views] : 0;
+    const int ssim_rows = vt ? ssim_blocks(*vt) : 0;
+    L.loss_part_d = take(sizeof(double) * ((size_t)kLossBlocks + ssim_rows) * 3);
     L.dsr_part = take(sizeof(double) * 512 * 6);
+    L.ssim_maps = take(sizeof(float) * 9 * (size_t)P);
     L.misc_end = off;
     L.total = L.bin_end;
     if (L.misc_end > L.total) L.total = L.misc_end;
@@ -120,7 +123,7 @@ size_t gs_workspace_size(int64_t n, int n_views, const gs_camera *cams, int64_t 
     if (!gs::make_view_table(cams, n_views, n, &vt)) return 0;
     if (inst_capacity < 0 || inst_capacity >= (int64_t)1 << 30 || !gs::feat_dim_ok(feat_dim)) return 0;
     if (n * n_views >= (int64_t)1 << 30) return 0;
-    return gs::ws_layout(n, n_views, inst_capacity).total;
+    return gs::ws_layout(n, n_views, inst_capacity, &vt).total;
 }
 
 }  // extern "C"

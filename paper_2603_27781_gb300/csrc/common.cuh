@@ -222,7 +222,8 @@ struct WsLayout {
     // loss / dsr
     size_t med_hist;      // u32 [4][V][256]
     size_t loss_part_f;   // f32 [kLossBlocks][32 * 32 + 32] decoder-gradient partials
-    size_t loss_part_d;   // f64 [kLossBlocks][3] loss-term partials
+    size_t loss_part_d;   // f64 [kLossBlocks + SSIM tiles][3] loss-term partials
+    size_t ssim_maps;     // f32 [9 P] SSIM window partials (3 planes per channel)
     size_t dsr_part;      // f64 [512][6] DSR partials
     size_t misc_end;
     size_t total;
@@ -237,6 +238,12 @@ constexpr int kSortTile = kSortThreads * kSortIPT;
 constexpr int kScanIPT = 8;
 constexpr int kScanBlock = 256 * kScanIPT;
 
-WsLayout ws_layout(int64_t n, int n_views, int64_t capacity);
+// Workspace layout; vt (may be NULL) adds the per-pixel space of the SSIM term.
+WsLayout ws_layout(int64_t n, int n_views, int64_t capacity, const ViewTable *vt = nullptr);
+
+// SSIM term of the mapping colour loss (ssim.cu).
+int ssim_blocks(const ViewTable &vt);
+gs_status launch_ssim(const ViewTable &vt, float coef, const float *rgb, const float *trgb, float *maps,
+                      double *part, float *g_rgb, cudaStream_t st);
 
 }  // namespace gs

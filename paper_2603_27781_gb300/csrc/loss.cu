@@ -121,8 +121,10 @@ __global__ void __launch_bounds__(256) median_hist_kernel(ViewTable vt, int pass
 }
 
 struct LossP {
-    float color, depth, sem, tau_obs;
+    float color, depth, sem, tau_obs;  // color: weight of the L1 part
     int mask_mode, K;
+    float ssim_coef;                   // lambda_c lambda of Eq. 15 (0: no SSIM term)
+    float *ssim_maps;
 };
 
 template <int N>
@@ -340,10 +342,11 @@ __global__ void __launch_bounds__(LossShape<D, KC>::NT) loss_kernel(
     }
 }
 
-// Sums the per-block partials in a fixed order.  Block j < K*D+K reduces decoder
+// Sums the per-block partials in a fixed order (nblk rows of decoder partials, nrows_d rows
+// of loss-term partials: the loss blocks, then any SSIM tiles).  Block j < K*D+K reduces decoder
 // gradient column j; blocks nval+t (t < 3) loss term t; block nval+3 the total
 // (recomputing the three terms in the same order, so the total is their exact sum).
-__global__ void __launch_bounds__(256) loss_finish_kernel(int nblk, int K, int D, const float *part_f,
+__global__ void __launch_bounds__(256) loss_finish_kernel(int nblk, int nrows_d, int K, int D, const float *part_f,
                                                           const double *part_d, float *dW, float *db,
                                                           double *loss_out) {
     __shared__ double s_red[8];
@@ -362,7 +365,7 @@ __global__ void __launch_bounds__(256) loss_finish_kernel(int nblk, int K, int D
     double tot[3];
     for (int c = 0; c < 3; ++c) {
         double x = 0;
-        for (int b = threadIdx.x; b < nblk; b += 256) x += part_d[3 * b + c];
+        for (int b = threadIdx.x; b < nrows_d; b += 256) x += part_d[3 * b + c];
         tot[c] = block_sum_f64(x, s_red);
     }
     if (threadIdx.x == 0) loss_out[term < 3 ? 1 + term : 0] = term < 3 ? tot[term] : tot[0] + tot[1] + tot[2];
@@ -607,7 +610,15 @@ gs_status launch_loss(const ViewTable &vt, const LossP &lp, const gs_images *img
         loss_kernel<D, kMaxK><<<grid, LossShape<D, kMaxK>::NT, 0, st>>>(
             vt, lp, img->rgb, img->depth, img->sil, img->feat, tgt->rgb, tgt->depth, tgt->label, W, b, P, mh, g->rgb,
             g->depth, g->sil, g->feat, part_f, part_d, mask_out, median_out);
-    loss_finish_kernel<<<lp.K * D + lp.K + 4, 256, 0, st>>>(bx * vt.n_views, lp.K, D, part_f, part_d, dW, db,
+    int rows = bx * vt.n_views;
+    if (lp.ssim_coef != 0.f) {
+        // the SSIM tiles add their colour-term shares as further partial rows
+        const gs_status s = launch_ssim(vt, lp.ssim_coef, img->rgb, tgt->rgb, lp.ssim_maps, part_d + 3 * (size_t)rows,
+                                        g->rgb, st);
+        if (s) return s;
+        rows += ssim_blocks(vt);
+    }
+    loss_finish_kernel<<<lp.K * D + lp.K + 4, 256, 0, st>>>(bx * vt.n_views, rows, lp.K, D, part_f, part_d, dW, db,
                                                              loss_out);
     return last_launch();
 }
@@ -630,7 +641,8 @@ extern "C" gs_status gs_loss_fwd_bwd(const gs_camera *cams, int n_views, int fea
         !tgt->label || !grad->rgb || !grad->depth || !grad->sil || (feat_dim && !grad->feat))
         return GS_ERR_ARG;
     if (lp->n_classes > 0 && (!dec_W || !dec_b || !d_dec_W || !d_dec_b)) return GS_ERR_ARG;
-    WsLayout L = ws_layout(0, n_views, 0);
+    if (!(lp->ssim >= 0.f && lp->ssim <= 1.f) || (lp->ssim > 0.f && lp->mask_mode != 0)) return GS_ERR_ARG;
+    WsLayout L = ws_layout(0, n_views, 0, &vt);
     if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) || ws_bytes < L.misc_end) return GS_ERR_ARG;
     char *w = static_cast<char *>(ws);
     uint32_t *mh = reinterpret_cast<uint32_t *>(w + L.med_hist);
@@ -645,7 +657,9 @@ extern "C" gs_status gs_loss_fwd_bwd(const gs_camera *cams, int n_views, int fea
             median_hist_kernel<<<grid, 256, 0, st>>>(vt, pass, img->depth, tgt->depth, mh);
         if ((s = last_launch())) return s;
     }
-    LossP q{lp->color, lp->depth, lp->sem, lp->tau_obs, lp->mask_mode, lp->n_classes};
+    // Eq. 15: the L1 part weighted lambda_c (1 - lambda), the SSIM part lambda_c lambda
+    LossP q{lp->color * (1.f - lp->ssim), lp->depth, lp->sem, lp->tau_obs, lp->mask_mode, lp->n_classes,
+            lp->color * lp->ssim, reinterpret_cast<float *>(w + L.ssim_maps)};
 #define GS_LOSS(DD)                                                                                              \
     case DD:                                                                                                     \
         return launch_loss<DD>(vt, q, img, tgt, dec_W, dec_b, P, mh, grad, part_f, part_d, d_dec_W, d_dec_b,     \
@@ -773,6 +787,7 @@ extern "C" gs_status gs_loss_fwd_bwd_noalloc(const gs_camera *cams, int n_views,
             median_hist_kernel<<<grid, 256, 0, st>>>(vt, pass, img->depth, tgt->depth, mh);
         if ((s = last_launch())) return s;
     }
+    if (lp->ssim != 0.f) return GS_ERR_UNSUPPORTED;  // the SSIM maps need per-pixel scratch
     LossP q{lp->color, lp->depth, lp->sem, lp->tau_obs, lp->mask_mode, lp->n_classes};
 #define GS_LOSS(DD)                                                                                              \
     case DD:                                                                                                     \

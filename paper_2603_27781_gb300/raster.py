@@ -45,9 +45,11 @@ class LossWeights:
     small: float = 0.001
     mask_mode: int = 0
     tau_obs: float = 0.99
+    ssim: float = 0.0      # lambda of Eq. 15 (mapping colour: (1 - lambda) L1 + lambda (1 - SSIM))
 
 
 MAPPING = LossWeights()
+MAPPING_SSIM = LossWeights(ssim=0.2)      # Eq. 15 with the paper's lambda = 0.2
 TRACKING = LossWeights(color=0.5, depth=1.0, sem=0.001, big=0.0, small=0.0, mask_mode=1)
 # supplementary C.1: pose learning rates, translation (rho) then rotation (phi)
 TRACKING_LR = (2e-3, 2e-3, 2e-3, 4e-4, 4e-4, 4e-4)
@@ -232,7 +234,7 @@ class Renderer:
 
     def loss(self, targets, decoder_W: torch.Tensor, decoder_b: torch.Tensor, w: LossWeights, stream=None):
         K = int(decoder_W.shape[0]) if decoder_W is not None else 0
-        lp = L.gs_loss_params(w.color, w.depth, w.sem, w.mask_mode, w.tau_obs, K)
+        lp = L.gs_loss_params(w.color, w.depth, w.sem, w.mask_mode, w.tau_obs, K, w.ssim)
         tc = L.gs_targets(_p(targets["rgb"]), _p(targets["depth"]), _p(targets["label"]))
         ic, gc = self.images_c(), self.image_grads_c()
         L.check("gs_loss_fwd_bwd", L.gs_loss_fwd_bwd(self.cams_c, self.n_views, self.feat_dim, ctypes.byref(ic),

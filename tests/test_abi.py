@@ -69,6 +69,18 @@ def test_argument_errors_before_any_launch(lib):
     zero_w = synth.camera(64, 48, 60.0)
     zero_w.width = 0
     assert lib.gs_workspace_size(10, 1, raster.cameras_c([zero_w]), 10, 16) == 0
+    # the SSIM weight of Eq. 15: in [0, 1] and for the mapping loss only (checked before any
+    # launch; the non-null pointers below are never dereferenced on the host)
+    fake = ctypes.c_void_p(1 << 20)
+    img = L.gs_images(fake, fake, fake, fake, fake, fake, None, None)
+    tgt = L.gs_targets(fake, fake, fake)
+    grads = L.gs_image_grads(fake, fake, fake, fake)
+    for weights in ((0.5, 1.0, 0.01, 1, 0.99, 8, 0.2), (0.5, 1.0, 0.01, 0, 0.99, 8, 1.5),
+                    (0.5, 1.0, 0.01, 0, 0.99, 8, -0.1)):
+        lp = L.gs_loss_params(*weights)
+        assert lib.gs_loss_fwd_bwd(cam, 1, 16, ctypes.byref(img), ctypes.byref(tgt), fake, fake, ctypes.byref(lp),
+                                   fake, 1 << 30, ctypes.byref(grads), fake, fake, fake, None, None,
+                                   None) == L.GS_ERR_ARG
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):

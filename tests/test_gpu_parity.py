@@ -262,10 +262,17 @@ def test_loss_feature_and_class_widths(D, K):
     _check_loss("mapping", 1, D, K)
 
 
-def _check_loss(mode, views, D, K):
-    cams, imgs, tgts, dec = _loss_case(views=views, D=D, K=K)
-    w = raster.MAPPING if mode == "mapping" else raster.TRACKING
-    wo = oracle.MAPPING if mode == "mapping" else oracle.TRACKING
+@pytest.mark.parametrize("views,shape", [(1, (48, 64)), (2, (45, 70))])
+def test_loss_with_ssim_matches_oracle(views, shape):
+    """Eq. 15 with lambda = 0.2: the SSIM tiles (32x16 with a 5-pixel halo) over whole and
+    ragged frames, one and two views."""
+    _check_loss("mapping_ssim", views, 16, 8, shape)
+
+
+def _check_loss(mode, views, D, K, shape=(48, 64)):
+    cams, imgs, tgts, dec = _loss_case(P_shape=shape, views=views, D=D, K=K)
+    w = dict(mapping=raster.MAPPING, mapping_ssim=raster.MAPPING_SSIM, tracking=raster.TRACKING)[mode]
+    wo = dict(mapping=oracle.MAPPING, mapping_ssim=oracle.MAPPING_SSIM, tracking=oracle.TRACKING)[mode]
     r = raster.Renderer(0, cams, D, 0, n_classes=K)
     cat = lambda key, f=lambda a: a: torch.as_tensor(np.concatenate([f(im[key]).reshape(im[key].shape[0], -1)
                                                                      if im[key].ndim == 3 else f(im[key]).reshape(1, -1)
@@ -290,7 +297,9 @@ def _check_loss(mode, views, D, K):
             gmask = r.mask[a:b].cpu().numpy().reshape(H, W)
             near = np.abs(np.abs(im["depth"] - t.depth) - 10 * o["median"]) < 1e-5 * o["median"]
             assert (gmask != o["mask"])[~near].sum() == 0
-        np.testing.assert_allclose(r.g_rgb[:, a:b].cpu().numpy().reshape(3, H, W), o["rgb"], atol=1e-9)
+        # the SSIM gradient is a sum of 121 window terms over f32 moments: 1e-4 of the largest
+        atol = 1e-9 if not w.ssim else 1e-4 * np.abs(o["rgb"]).max()
+        np.testing.assert_allclose(r.g_rgb[:, a:b].cpu().numpy().reshape(3, H, W), o["rgb"], atol=atol)
         np.testing.assert_allclose(r.g_depth[a:b].cpu().numpy().reshape(H, W), o["depth"], atol=1e-9)
         np.testing.assert_allclose(r.g_feat[:, a:b].cpu().numpy().reshape(D, H, W), o["feat"], atol=1e-9,
                                    rtol=1e-5)
@@ -365,8 +374,8 @@ def test_pose_step_matches_oracle():
 
 
 # ---------------------------------------------------------------- whole step
-@pytest.mark.parametrize("exact", [True, False])
-def test_full_iteration_tiny_scene(exact):
+@pytest.mark.parametrize("exact,ssim", [(True, False), (False, False), (False, True)])
+def test_full_iteration_tiny_scene(exact, ssim):
     """Box scene, 64x48, mapping loss + DSR + pose twist vs oracle.step.  In exact mode (no
     thresholds) every pixel is comparable; the default-threshold scene (seed 11) has no pixel
     within rounding distance of a decision, so the whole iteration is compared."""
@@ -379,13 +388,14 @@ def test_full_iteration_tiny_scene(exact):
     f = tgt_img["feat"].reshape(16, -1).T
     label = np.argmax(f @ dec.W.T.astype(np.float64) + dec.b, 1).astype(np.uint8).reshape(48, 64)
     tgt = synth.Frame(tgt_img["rgb"].astype(np.float32), tgt_img["depth"].astype(np.float32), label)
-    ref = oracle.step(gs, cam, prm_o, tgt, dec, oracle.MAPPING)
+    wo, wg = (oracle.MAPPING_SSIM, raster.MAPPING_SSIM) if ssim else (oracle.MAPPING, raster.MAPPING)
+    ref = oracle.step(gs, cam, prm_o, tgt, dec, wo)
     field, r = C.gpu_forward(gs, cam, prm_g, n_classes=8)
     excl, _ = C.excluded_pixels(cam, ref["proj"], C.gpu_projection(r), ref["img"])
     assert excl.sum() == 0
     tg = dict(rgb=torch.as_tensor(tgt.rgb.reshape(3, -1)).cuda(), depth=torch.as_tensor(tgt.depth.ravel()).cuda(),
               label=torch.as_tensor(tgt.label.ravel()).cuda())
-    r.iteration(field, tg, torch.as_tensor(dec.W).cuda(), torch.as_tensor(dec.b).cuda(), raster.MAPPING,
+    r.iteration(field, tg, torch.as_tensor(dec.W).cuda(), torch.as_tensor(dec.b).cuda(), wg,
                 L.GS_GRAD_MAP | L.GS_GRAD_POSE)
     torch.cuda.synchronize()
     total = r.loss_out[0].item() + r.dsr_out[0].item()

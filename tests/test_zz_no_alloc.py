@@ -94,3 +94,19 @@ def test_noalloc_loss_rejects_more_views_than_its_scratch_holds():
                                        ctypes.byref(lp), ctypes.byref(g), None, None, p(r.loss_out), None, None,
                                        None)
     assert status == L.GS_ERR_UNSUPPORTED
+
+
+def test_noalloc_loss_rejects_the_ssim_term():
+    """The SSIM maps of Eq. 15 need per-pixel scratch the static array does not hold."""
+    cams = [synth.camera(8, 8, 4.0)]
+    r = raster.Renderer(0, cams, 0, 0, n_classes=1)
+    p = lambda t: ctypes.c_void_p(t.data_ptr())
+    lp = L.gs_loss_params(0.5, 1.0, 0.0, 0, 0.99, 0, 0.2)
+    tg = dict(rgb=torch.zeros(3, r.P, device="cuda"), depth=torch.ones(r.P, device="cuda"),
+              label=torch.zeros(r.P, dtype=torch.uint8, device="cuda"))
+    tgt = L.gs_targets(p(tg["rgb"]), p(tg["depth"]), p(tg["label"]))
+    g = r.image_grads_c()
+    status = L.gs_loss_fwd_bwd_noalloc(r.cams_c, 1, 0, ctypes.byref(r.images_c()), ctypes.byref(tgt), None, None,
+                                       ctypes.byref(lp), ctypes.byref(g), None, None, p(r.loss_out), None, None,
+                                       None)
+    assert status == L.GS_ERR_UNSUPPORTED
