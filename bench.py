@@ -311,6 +311,77 @@ def run_forms(args, gs, dec, dev, flush, batch=8):
     return out
 
 
+def run_tracking(args, dev, flush, n_it=40):
+    """Tracking (Sec. 3.4, Eq. 20-21) at the 300k-Gaussian room frame, 1200x680: 40 pose-only
+    iterations (tracking loss with the M_obs mask, C.1 weights and learning rates) from the
+    true pose perturbed by 2 degrees and 5 cm, captured as one CUDA graph whose pose step feeds
+    the pose of the next projection on the device.  Reports the time per tracked frame and the
+    pose error before and after (the target is the analytic room seen from the true pose)."""
+    import torch
+    from paper_2603_27781_gb300 import _lib as L
+    from paper_2603_27781_gb300 import raster, synth
+    room = synth.make_room(synth.SEED_SCENE)
+    gs = synth.room_field(300_000, WORKLOAD["d"], seed=synth.SEED_SCENE, room=room)
+    cam = synth.room_camera(WORKLOAD["width"], WORKLOAD["height"], WORKLOAD["fx"], room=room)
+    tgt = synth.raycast_room(room, cam)
+    dec = synth.decoder(WORKLOAD["k"], WORKLOAD["d"])
+    start = synth.perturb_pose(cam.T_cw, 2.0, 0.05)
+    field = raster.Field.from_numpy(gs, dev)
+    r = raster.fit_capacity(field, [cam], WORKLOAD["d"], margin=1.6, n_classes=WORKLOAD["k"], device=dev)
+    tg = dict(rgb=torch.as_tensor(tgt.rgb.reshape(3, -1)).to(dev), depth=torch.as_tensor(tgt.depth.ravel()).to(dev),
+              label=torch.as_tensor(tgt.label.ravel()).to(dev))
+    W, b = torch.as_tensor(dec.W).to(dev), torch.as_tensor(dec.b).to(dev)
+    T0 = torch.as_tensor(start.reshape(1, 16), dtype=torch.float64).to(dev)
+    T_state, adam = T0.clone(), torch.zeros(13, dtype=torch.float64, device=dev)
+    pose = T0.float()
+
+    def iteration():
+        r.iteration(field, tg, W, b, raster.TRACKING, L.GS_GRAD_POSE, pose_dev=pose)
+        r.pose_step(T_state, adam, 0, pose_f32=pose)
+
+    def reset():
+        T_state.copy_(T0)
+        adam.zero_()
+        pose.copy_(T0.float())
+
+    iteration()
+    cur = torch.cuda.current_stream()
+    side = torch.cuda.Stream()
+    side.wait_stream(cur)
+    with torch.cuda.stream(side):
+        iteration()
+    cur.wait_stream(side)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for _ in range(n_it):
+            iteration()
+    ms = []
+    for k in range(max(3, args.form_steps)):
+        reset()
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(cur)
+        g.replay()
+        e1.record(cur)
+        e1.synchronize()
+        if k >= 1:
+            ms.append(e0.elapsed_time(e1))
+    if r.status() != 0:
+        raise RuntimeError(f"binning status {r.status()}")
+
+    def err(T):
+        R = T[:3, :3] @ cam.T_cw[:3, :3].T
+        ang = math.degrees(math.acos(max(-1.0, min(1.0, (np.trace(R) - 1) / 2))))
+        centre = lambda M: -M[:3, :3].T @ M[:3, 3]
+        return {"rot_deg": ang, "centre_cm": 100 * float(np.linalg.norm(centre(T) - centre(cam.T_cw)))}
+    t = float(np.mean(ms))
+    del g
+    return {"workload": "room 300k Gaussians, D=16, 1200x680 fx=600, 40 tracking iterations per frame",
+            "ms_per_frame": t, "iters_per_s": n_it * 1000.0 / t, "frames_per_s": 1000.0 / t,
+            "pose_error_start": err(start), "pose_error_end": err(T_state.cpu().numpy().reshape(4, 4)),
+            "timing": "one CUDA graph of 40 iterations, replays timed with CUDA events, L2 flushed between"}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -454,6 +525,7 @@ def run_ours(args, rank, world, local_rank):
                 "unit": "GB/s", "frac": None, "traffic": None}
 
     forms = None if args.no_forms else run_forms(args, gs, dec, dev, flush)
+    tracking = None if args.no_forms else run_tracking(args, dev, flush)
 
     # the SSIM term of the paper's mapping colour loss (Eq. 15, lambda = 0.2) on the same frame:
     # the loss step with and without it (events around 20 calls each)
@@ -489,6 +561,7 @@ def run_ours(args, rank, world, local_rank):
             "stages_ms": {s: float(t) for s, t in zip(stages, per_stage)},
             "forms": forms,
             "extras": extras,
+            "tracking": tracking,
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "iters/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},

@@ -307,3 +307,25 @@ def step(gs, cam, prm: Params, target, dec, w: LossWeights, with_dsr=True):
         grads["dsr"] = stats
     grads["W"], grads["b"] = L["W"], L["b"]
     return dict(total=total, proj=proj, bins=bins, img=img, loss=L, grads=grads)
+
+
+# parameter groups of the field in the order the Adam update walks them, with the mapping
+# learning rates of supplementary C.1 (position, rotation, scaling, opacity, colour, feature)
+ADAM_GROUPS = ("means", "quats", "log_scales", "opacity_logits", "rgb", "feat")
+MAPPING_LR = dict(means=1e-4, quats=1e-3, log_scales=1e-3, opacity_logits=0.05, rgb=2.5e-3, feat=2.5e-3)
+
+
+def adam_step(params, grads, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-15):
+    """One Adam step (Kingma and Ba, bias-corrected) of every parameter group, in FP64.
+    params/grads/m/v: dicts of arrays by group name; step: 1-based; lr: dict by group.
+    Returns new (params, m, v) dicts; the inputs are left unchanged."""
+    out_p, out_m, out_v = {}, {}, {}
+    for k in ADAM_GROUPS:
+        g = np.asarray(grads[k], np.float64)
+        mk = b1 * np.asarray(m[k], np.float64) + (1 - b1) * g
+        vk = b2 * np.asarray(v[k], np.float64) + (1 - b2) * g * g
+        mhat = mk / (1 - b1 ** step)
+        vhat = vk / (1 - b2 ** step)
+        out_p[k] = np.asarray(params[k], np.float64) - lr[k] * mhat / (np.sqrt(vhat) + eps)
+        out_m[k], out_v[k] = mk, vk
+    return out_p, out_m, out_v

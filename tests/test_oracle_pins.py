@@ -648,3 +648,52 @@ def test_mapping_loss_with_ssim_is_eq15_and_its_gradient():
         assert out["rgb"][c, i, j] == pytest.approx(fd, rel=1e-5)
     with pytest.raises(ValueError):
         oracle.loss(img, tgt, dec, oracle.LossWeights(mask_mode=1, ssim=0.2))
+
+
+# ------------------------------------------------------- Adam (mapping update)
+def test_adam_first_steps_are_sign_steps_and_zero_gradients_stay():
+    """With zero moments, the first step moves every parameter by lr against the sign of its
+    gradient; a constant gradient keeps that step size; a zero gradient moves nothing."""
+    r = synth.rng(64)
+    shapes = dict(means=(5, 3), quats=(5, 4), log_scales=(5, 3), opacity_logits=(5,), rgb=(5, 3), feat=(5, 4))
+    p = {k: r.standard_normal(s) for k, s in shapes.items()}
+    g = {k: r.standard_normal(s) for k, s in shapes.items()}
+    g["feat"][0] = 0.0
+    z = {k: np.zeros(s) for k, s in shapes.items()}
+    lr = oracle.MAPPING_LR
+    p1, m1, v1 = oracle.adam_step(p, g, z, z, 1, lr)
+    p2, _, _ = oracle.adam_step(p1, g, m1, v1, 2, lr)
+    for k in shapes:
+        np.testing.assert_allclose(p1[k], p[k] - lr[k] * np.sign(g[k]), rtol=0, atol=1e-12)
+        np.testing.assert_allclose(p2[k], p[k] - 2 * lr[k] * np.sign(g[k]), rtol=0, atol=1e-12)
+        np.testing.assert_allclose(m1[k], 0.1 * g[k], rtol=1e-14)
+        np.testing.assert_allclose(v1[k], 0.001 * g[k] ** 2, rtol=1e-14)
+    assert (p1["feat"][0] == p["feat"][0]).all()
+
+
+def test_adam_learning_rates_are_the_papers():
+    with open(os.path.join(HERE, "golden", "paper_hyperparameters.json")) as fh:
+        hp = json.load(fh)["mapping"]
+    lr = oracle.MAPPING_LR
+    assert (lr["means"], lr["rgb"], lr["quats"], lr["opacity_logits"], lr["log_scales"], lr["feat"]) == (
+        hp["lr_position"], hp["lr_color"], hp["lr_rotation"], hp["lr_opacity"], hp["lr_scaling"], hp["lr_feature"])
+
+
+def test_adam_steps_follow_the_bias_corrected_recursion_on_a_scalar():
+    """A gradient sequence g_t on one scalar: after T steps the update of step T equals
+    lr m_T / (1 - b1^T) / (sqrt(v_T / (1 - b2^T)) + eps) with m, v the exponential sums written
+    out as series."""
+    gs_ = [0.3, -1.2, 0.7, 2.0]
+    b1, b2, lr = 0.9, 0.999, 0.01
+    keys = oracle.ADAM_GROUPS
+    p = {k: np.zeros(1) for k in keys}
+    m = {k: np.zeros(1) for k in keys}
+    v = {k: np.zeros(1) for k in keys}
+    for t, gt in enumerate(gs_, start=1):
+        prev = p["rgb"].copy()
+        p, m, v = oracle.adam_step(p, {k: np.array([gt]) for k in keys}, m, v, t, {k: lr for k in keys})
+    T = len(gs_)
+    mT = sum((1 - b1) * b1 ** (T - 1 - i) * g for i, g in enumerate(gs_))
+    vT = sum((1 - b2) * b2 ** (T - 1 - i) * g * g for i, g in enumerate(gs_))
+    want = lr * (mT / (1 - b1 ** T)) / (math.sqrt(vT / (1 - b2 ** T)) + 1e-15)
+    assert prev[0] - p["rgb"][0] == pytest.approx(want, rel=1e-12)
