@@ -545,6 +545,18 @@ def run_ours(args, rank, world, local_rank):
     extras = {"loss_ms": loss_ms, "loss_with_ssim_ms": loss_ssim_ms,
               "ssim_term": {"ms": ssim_ms, "bytes": ssim_bytes,
                             "GBps": ssim_bytes / (ssim_ms * 1e-3) / 1e9 if ssim_ms > 0 else None}}
+    # the mapping update (Adam over every parameter group, supp. C.1 rates) on a copy of the field,
+    # with the step's gradients: 28 bytes per parameter (read p, g, m, v; write p, m, v)
+    fcopy = raster.Field(*(t.clone() for t in (field.means, field.quats, field.log_scales, field.opacity_logits,
+                                               field.rgb, field.feat)))
+    opt = raster.MappingAdam(fcopy)
+    adam_ms = time_calls(lambda: opt.step(r, 0))
+    adam_bytes = 28 * fcopy.n * (14 + fcopy.feat_dim)
+    adam_gbs = adam_bytes / (adam_ms * 1e-3) / 1e9
+    extras["mapping_update"] = {"ms": adam_ms, "bytes": adam_bytes, "GBps": adam_gbs,
+                                "frac_of_measured_hbm": adam_gbs / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None,
+                                "timing": "20 back-to-back launches (parameters and moments ~1 GB, above L2)"}
+    del opt, fcopy
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -187,6 +187,19 @@ typedef struct {
     float *feat;
 } gs_gaussian_grads;
 
+/* Writable view of the field's FP32 parameter arrays (same shapes as
+ * gs_gaussians), for the mapping update. */
+typedef struct {
+    int64_t n;
+    int32_t feat_dim;
+    float *means;
+    float *quats;
+    float *log_scales;
+    float *opacity_logits;
+    float *rgb;
+    float *feat;
+} gs_field_mut;
+
 /* Targets of the losses, planar over all views' pixels: rgb [3,P] f32,
  * depth [P] f32 (<= 0: no measurement), label [P] u8 (255: unlabelled). */
 typedef struct {
@@ -360,6 +373,24 @@ gs_status gs_dsr(int64_t n, const float *log_scales, float lam_big, float lam_sm
 gs_status gs_pose_step(int n_views, const double *d_twist, double *T_state, double *adam,
                        int step, const double *lr, double beta1, double beta2, double eps,
                        float *pose_f32, gs_stream stream);
+
+/* Mapping update (Sec. 3.3; learning rates of supp. C.1, which names no
+ * optimiser: read as Adam with bias correction, as for the pose): for every
+ * parameter p of the groups means, quats, log_scales, opacity_logits, rgb,
+ * feat (in this order), m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
+ * p -= lr_group (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps), in f32 with
+ * 1 - b1, 1 - b2 and the bias corrections formed in double.  f: the field,
+ * updated in place (f32 storage only); grads: the gradients of the step
+ * (gs_render_bwd / gs_project_bwd / gs_dsr); moments: device f32
+ * [2][n (14 + feat_dim)], m then v, each the six groups back to back (zero
+ * before the first step); lr: host [6] in group order (C.1: 1e-4, 1e-3, 1e-3,
+ * 0.05, 2.5e-3, 2.5e-3).  step >= 1 is the 1-based step t; step 0 keeps t on
+ * the device in *step_ctr (f64, zero before the first step), which the call
+ * increments, so that a captured CUDA graph can replay the update.
+ * GS_ERR_ARG for a missing buffer, step < 0 or betas outside [0, 1). */
+gs_status gs_adam_step(const gs_field_mut *f, const gs_gaussian_grads *grads, float *moments, int step,
+                       double *step_ctr, const float *lr, double beta1, double beta2, double eps,
+                       gs_stream stream);
 
 #ifdef __cplusplus
 }

@@ -61,6 +61,11 @@ class gs_image_grads(Structure):
 gs_image_grads_out = gs_image_grads
 
 
+class gs_field_mut(Structure):
+    _fields_ = [("n", c_int64), ("feat_dim", c_int32), ("means", c_void_p), ("quats", c_void_p),
+                ("log_scales", c_void_p), ("opacity_logits", c_void_p), ("rgb", c_void_p), ("feat", c_void_p)]
+
+
 class gs_gaussian_grads(Structure):
     _fields_ = [("means", c_void_p), ("quats", c_void_p), ("log_scales", c_void_p), ("opacity_logits", c_void_p),
                 ("rgb", c_void_p), ("feat", c_void_p)]
@@ -101,6 +106,8 @@ _SIGNATURES = {
     "gs_dsr": (c_int, [c_int64, c_void_p, c_float, c_float, c_void_p, c_size_t, c_void_p, c_void_p, c_void_p]),
     "gs_pose_step": (c_int, [c_int, c_void_p, c_void_p, c_void_p, c_int, _P(c_double), c_double, c_double,
                              c_double, c_void_p, c_void_p]),
+    "gs_adam_step": (c_int, [_P(gs_field_mut), _P(gs_gaussian_grads), c_void_p, c_int, c_void_p, _P(c_float),
+                             c_double, c_double, c_double, c_void_p]),
 }
 
 _lib = None
@@ -158,3 +165,4 @@ gs_loss_fwd_bwd = _wrap("gs_loss_fwd_bwd")
 gs_loss_fwd_bwd_noalloc = _wrap("gs_loss_fwd_bwd_noalloc")
 gs_dsr = _wrap("gs_dsr")
 gs_pose_step = _wrap("gs_pose_step")
+gs_adam_step = _wrap("gs_adam_step")

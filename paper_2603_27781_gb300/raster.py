@@ -328,6 +328,34 @@ def fit_capacity(field: Field, cams, feat_dim: int, margin: float = 1.25, params
     return Renderer(field.n, cams, feat_dim, cap, device, params, n_classes)
 
 
+# supplementary C.1 mapping learning rates, in the update's group order:
+# position, rotation, scaling, opacity, colour, feature
+MAPPING_LR = (1e-4, 1e-3, 1e-3, 0.05, 2.5e-3, 2.5e-3)
+
+
+class MappingAdam:
+    """Adam state of the field's parameters (gs_adam_step): moments m, v of every group and a
+    device step counter, so the update can be part of a captured mapping iteration."""
+
+    def __init__(self, field: Field, lr=MAPPING_LR, betas=(0.9, 0.999), eps=1e-15):
+        if field.rgb.dtype != torch.float32 or field.feat.dtype != torch.float32:
+            raise ValueError("the mapping update works on f32 parameter storage")
+        self.field, self.lr, self.betas, self.eps = field, tuple(lr), betas, eps
+        n, D = field.n, field.feat_dim
+        self.moments = torch.zeros(2 * n * (14 + D), dtype=torch.float32, device=field.means.device)
+        self.step_ctr = torch.zeros(1, dtype=torch.float64, device=field.means.device)
+
+    def step(self, r: "Renderer", step: int = 0, stream=None):
+        """One update from the renderer's gradients; step 0 counts on the device."""
+        f = self.field
+        fm = L.gs_field_mut(f.n, f.feat_dim, _p(f.means), _p(f.quats), _p(f.log_scales), _p(f.opacity_logits),
+                            _p(f.rgb), _p(f.feat) if f.feat_dim else None)
+        lr = (ctypes.c_float * 6)(*self.lr)
+        L.check("gs_adam_step", L.gs_adam_step(ctypes.byref(fm), ctypes.byref(r.gaussian_grads_c()),
+                                               _p(self.moments), step, _p(self.step_ctr), lr, self.betas[0],
+                                               self.betas[1], self.eps, _stream(stream)))
+
+
 class RasterizeSG(torch.autograd.Function):
     """Differentiable render of a Semantic Gaussian Field through libgs.
 
