@@ -178,6 +178,27 @@ def run_reference(args, rank, world):
 
 
 # ------------------------------------------------------------- GPU arm
+def captured_traffic(kernel, px_per_thread, feat_dim):
+    """DRAM bytes (read + write) per launch of `kernel` from the committed ncu capture in
+    profiles/roofline_traffic.json, if the capture is of this kernel, launch shape and feature
+    width and its sources are unchanged since (same SHA-256); else None."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        cap = json.load(fh)
+    if (cap.get("kernel"), cap.get("px_per_thread"), cap.get("feat_dim")) != (kernel, px_per_thread, feat_dim):
+        return None
+    h = hashlib.sha256()
+    for f in cap["sources"]:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != cap["sources_sha256"]:
+        return None
+    return cap["dram_bytes_read"] + cap["dram_bytes_write"]
+
+
 def kernels_per_step(n_tiles):
     tile_passes = max(1, math.ceil(math.ceil(math.log2(max(n_tiles, 2))) / 8))
     project = 1
@@ -515,9 +536,11 @@ def run_ours(args, rank, world, local_rank):
     if stages[dom] in ("render_bwd", "render_fwd"):
         fl = bwd_fl if stages[dom] == "render_bwd" else fwd_fl
         achieved = fl / (per_stage[dom] * 1e-3) / 1e12
-        roof = {"kernel": "raster_bwd_kernel" if stages[dom] == "render_bwd" else "raster_fwd_kernel",
-                "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": None,
+        is_bwd = stages[dom] == "render_bwd"
+        kname = "raster_bwd_kernel" if is_bwd else "raster_fwd_kernel"
+        shape = tuned.bwd_px_per_thread if is_bwd else tuned.fwd_px_per_thread
+        roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": captured_traffic(kname, shape, WORKLOAD["d"]),
                 "peak_source": f"FP32 FMA issue: {props.multi_processor_count} SMs x 128 lanes x 2 x {sm_max:.0f} MHz",
                 "work": f"{evaluated} evaluated pairs, {blended} blended pairs per launch"}
     else:
