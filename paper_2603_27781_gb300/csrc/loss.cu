@@ -533,58 +533,79 @@ __global__ void __launch_bounds__(256) pose_reduce_kernel(int64_t n, const float
 // bc1 < 0 selects the device step counter: adam[12 * n_views] holds the number
 // of steps taken so far (as a double); this step is that number + 1 and the
 // bias corrections 1 - beta^step are formed here.
+// One block, 16 threads per view: the six Adam components, then the SE(3) exponential
+// (one thread for theta and its sin/cos, nine for the 3x3 products, sixteen for T <- E T).
+constexpr int kPoseLanes = 16;
+
 __global__ void pose_step_kernel(int n_views, const double *grad, double *Tst, double *adam, double bc1, double bc2,
                                  double lr0, double lr1, double lr2, double lr3, double lr4, double lr5, double b1,
                                  double b2, double eps, float *pose_f32) {
-    const int v = threadIdx.x;
-    if (bc1 < 0.0) {
-        const double step = adam[12 * n_views] + 1.0;
-        bc1 = 1.0 - pow(b1, step);
-        bc2 = 1.0 - pow(b2, step);
-        __syncthreads();                       // every thread has read the counter
-        if (v == 0) adam[12 * n_views] = step;
-    }
-    if (v >= n_views) return;
-    const double lr[6] = {lr0, lr1, lr2, lr3, lr4, lr5};
-    double *m = adam + 12 * v, *vv = m + 6, *T = Tst + 16 * v;
-    double dl[6];
-    for (int k = 0; k < 6; ++k) {
-        const double g = grad[6 * v + k];
-        m[k] = b1 * m[k] + (1 - b1) * g;
-        vv[k] = b2 * vv[k] + (1 - b2) * g * g;
-        const double mh = m[k] / bc1, vh = vv[k] / bc2;
-        dl[k] = -lr[k] * mh / (sqrt(vh) + eps);
-    }
-    // SE(3) exponential of (rho, phi) = dl
-    const double ph[3] = {dl[3], dl[4], dl[5]};
-    const double th = sqrt(ph[0] * ph[0] + ph[1] * ph[1] + ph[2] * ph[2]);
-    double a, b, c;
-    if (th < 1e-8) { a = 1 - th * th / 6; b = 0.5 - th * th / 24; c = 1.0 / 6 - th * th / 120; }
-    else { a = sin(th) / th; b = (1 - cos(th)) / (th * th); c = (th - sin(th)) / (th * th * th); }
-    const double K[9] = {0, -ph[2], ph[1], ph[2], 0, -ph[0], -ph[1], ph[0], 0};
-    double K2[9];
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) K2[3 * i + j] = K[3 * i] * K[j] + K[3 * i + 1] * K[3 + j] + K[3 * i + 2] * K[6 + j];
-    double R[9], V[9];
-    for (int k = 0; k < 9; ++k) {
-        const double id = (k % 4 == 0) ? 1.0 : 0.0;
-        R[k] = id + a * K[k] + b * K2[k];
-        V[k] = id + b * K[k] + c * K2[k];
-    }
-    const double E[16] = {R[0], R[1], R[2], V[0] * dl[0] + V[1] * dl[1] + V[2] * dl[2],
-                          R[3], R[4], R[5], V[3] * dl[0] + V[4] * dl[1] + V[5] * dl[2],
-                          R[6], R[7], R[8], V[6] * dl[0] + V[7] * dl[1] + V[8] * dl[2],
-                          0, 0, 0, 1};
-    double out[16];
-    for (int i = 0; i < 4; ++i)
-        for (int j = 0; j < 4; ++j) {
-            double s = 0;
-            for (int k = 0; k < 4; ++k) s += E[4 * i + k] * T[4 * k + j];
-            out[4 * i + j] = s;
+    __shared__ double s_bc[2];
+    __shared__ double s_dl[kMaxViews][6], s_abc[kMaxViews][3], s_R[kMaxViews][9], s_V[kMaxViews][9];
+    __shared__ double s_t[kMaxViews][3];
+    const int v = threadIdx.x / kPoseLanes, j = threadIdx.x % kPoseLanes;
+    const bool active = v < n_views;
+    if (threadIdx.x == 0) {
+        double c1 = bc1, c2 = bc2;
+        if (bc1 < 0.0) {  // device step count: this step is the stored count + 1
+            const double step = adam[12 * n_views] + 1.0;
+            c1 = 1.0 - pow(b1, step);
+            c2 = 1.0 - pow(b2, step);
+            adam[12 * n_views] = step;
         }
-    for (int k = 0; k < 16; ++k) {
-        T[k] = out[k];
-        if (pose_f32) pose_f32[16 * v + k] = (float)out[k];
+        s_bc[0] = c1;
+        s_bc[1] = c2;
+    }
+    __syncthreads();
+    if (active && j < 6) {
+        const double lr[6] = {lr0, lr1, lr2, lr3, lr4, lr5};
+        double *m = adam + 12 * v, *vv = m + 6;
+        const double g = grad[6 * v + j];
+        m[j] = b1 * m[j] + (1 - b1) * g;
+        vv[j] = b2 * vv[j] + (1 - b2) * g * g;
+        const double mh = m[j] / s_bc[0], vh = vv[j] / s_bc[1];
+        s_dl[v][j] = -lr[j] * mh / (sqrt(vh) + eps);
+    }
+    __syncthreads();
+    // SE(3) exponential of (rho, phi) = dl
+    if (active && j == 0) {
+        const double *ph = s_dl[v] + 3;
+        const double th = sqrt(ph[0] * ph[0] + ph[1] * ph[1] + ph[2] * ph[2]);
+        double a, b, c;
+        if (th < 1e-8) { a = 1 - th * th / 6; b = 0.5 - th * th / 24; c = 1.0 / 6 - th * th / 120; }
+        else { a = sin(th) / th; b = (1 - cos(th)) / (th * th); c = (th - sin(th)) / (th * th * th); }
+        s_abc[v][0] = a;
+        s_abc[v][1] = b;
+        s_abc[v][2] = c;
+    }
+    __syncthreads();
+    if (active && j < 9) {
+        const double *ph = s_dl[v] + 3;
+        const double K[9] = {0, -ph[2], ph[1], ph[2], 0, -ph[0], -ph[1], ph[0], 0};
+        const int i = j / 3, jj = j % 3;
+        const double K2 = K[3 * i] * K[jj] + K[3 * i + 1] * K[3 + jj] + K[3 * i + 2] * K[6 + jj];
+        const double id = (j % 4 == 0) ? 1.0 : 0.0;
+        s_R[v][j] = id + s_abc[v][0] * K[j] + s_abc[v][1] * K2;
+        s_V[v][j] = id + s_abc[v][1] * K[j] + s_abc[v][2] * K2;
+    }
+    __syncthreads();
+    if (active && j < 3) {
+        const double *V = s_V[v], *dl = s_dl[v];
+        s_t[v][j] = V[3 * j] * dl[0] + V[3 * j + 1] * dl[1] + V[3 * j + 2] * dl[2];
+    }
+    __syncthreads();
+    double out = 0.0;
+    double *T = Tst + 16 * v;
+    if (active) {
+        const int i = j / 4, c = j % 4;
+        const double E[4] = {i < 3 ? s_R[v][3 * i] : 0.0, i < 3 ? s_R[v][3 * i + 1] : 0.0,
+                             i < 3 ? s_R[v][3 * i + 2] : 0.0, i < 3 ? s_t[v][i] : 1.0};
+        for (int k = 0; k < 4; ++k) out += E[k] * T[4 * k + c];
+    }
+    __syncthreads();  // every thread has read T before any writes it
+    if (active) {
+        T[j] = out;
+        if (pose_f32) pose_f32[16 * v + j] = (float)out;
     }
 }
 
@@ -714,7 +735,7 @@ extern "C" gs_status gs_pose_step(int n_views, const double *d_twist, double *T_
     // Adam bias corrections 1 - beta^step: on the host for a given step, on the
     // device (from the counter after the moments) for step 0
     const double bc1 = step ? 1.0 - pow(beta1, step) : -1.0, bc2 = step ? 1.0 - pow(beta2, step) : -1.0;
-    pose_step_kernel<<<1, 64, 0, (cudaStream_t)stream>>>(n_views, d_twist, T_state, adam, bc1, bc2, lr[0], lr[1],
+    pose_step_kernel<<<1, kPoseLanes * n_views, 0, (cudaStream_t)stream>>>(n_views, d_twist, T_state, adam, bc1, bc2, lr[0], lr[1],
                                                          lr[2], lr[3], lr[4], lr[5], beta1, beta2, eps, pose_f32);
     return last_launch();
 }
