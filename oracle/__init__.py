@@ -329,3 +329,39 @@ def adam_step(params, grads, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-15):
         out_p[k] = np.asarray(params[k], np.float64) - lr[k] * mhat / (np.sqrt(vhat) + eps)
         out_m[k], out_v[k] = mk, vk
     return out_p, out_m, out_v
+
+
+TAU_UNOBS = 0.5     # Eq. 11 threshold on the cumulative opacity (silent in the paper; reading)
+
+
+def expand(images, target, cam, feat_init, tau_unobs=TAU_UNOBS):
+    """Adaptive Gaussian expansion (Eq. 11 and the initialisation after it), one view.
+
+    M_unobs = (o_hat < tau_unobs) or (d_hat > d_gt and |d_gt - d_hat| > 50 median), the median
+    being the lower median of |d_gt - d_hat| over pixels with d_gt > 0; only pixels with
+    d_gt > 0 can be unprojected.  The decisions are taken in f32 on the f32 inputs (they decide
+    integers).  One Gaussian per masked pixel in raster order: mean = the pixel centre
+    unprojected at d_gt (world frame, FP64), identity rotation, log-scale log(d_gt / fx) on
+    every axis, opacity 0.5 (logit 0), the observed colour, features feat_init[k] for the
+    k-th new Gaussian.  Returns a dict of the new parameters and their source pixels."""
+    sil = np.asarray(images["sil"], np.float32)
+    d_hat = np.asarray(images["depth"], np.float32)
+    d_gt = np.asarray(target.depth, np.float32)
+    H, W = d_gt.shape
+    valid = d_gt > np.float32(0)
+    err = np.abs(d_gt - d_hat).astype(np.float32)
+    med = np.float32(lower_median(err[valid].astype(np.float64))) if valid.any() else np.float32(0)
+    mask = (sil < np.float32(tau_unobs)) | ((d_hat > d_gt) & (err > np.float32(50) * med))
+    mask &= valid
+    pix = np.nonzero(mask.ravel())[0]
+    py, px = pix // W, pix % W
+    d = d_gt.ravel()[pix].astype(np.float64)
+    pc = np.stack([(px + 0.5 - cam.cx) / cam.fx * d, (py + 0.5 - cam.cy) / cam.fy * d, d], 1)
+    T = np.asarray(cam.T_cw, np.float64)
+    means = (pc - T[:3, 3]) @ T[:3, :3]          # R^T (p_c - t), row-wise
+    n = len(pix)
+    return dict(src_pix=pix.astype(np.int64), means=means,
+                quats=np.tile(np.array([1.0, 0.0, 0.0, 0.0]), (n, 1)),
+                log_scales=np.repeat(np.log(d / cam.fx)[:, None], 3, 1), opacity_logits=np.zeros(n),
+                rgb=np.asarray(target.rgb, np.float64).reshape(3, -1)[:, pix].T,
+                feat=np.asarray(feat_init, np.float64)[:n], median=float(med), mask=mask)

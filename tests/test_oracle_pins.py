@@ -697,3 +697,61 @@ def test_adam_steps_follow_the_bias_corrected_recursion_on_a_scalar():
     vT = sum((1 - b2) * b2 ** (T - 1 - i) * g * g for i, g in enumerate(gs_))
     want = lr * (mT / (1 - b1 ** T)) / (math.sqrt(vT / (1 - b2 ** T)) + 1e-15)
     assert prev[0] - p["rgb"][0] == pytest.approx(want, rel=1e-12)
+
+
+# -------------------------------------------------- adaptive expansion (Eq. 11)
+def _expand_frame(H=9, W=13, seed=65):
+    r = synth.rng(seed)
+    depth = r.uniform(1.5, 4.0, (H, W)).astype(np.float32)
+    depth[0, :4] = 0.0                                   # invalid depth: never unprojected
+    return synth.Frame(r.random((3, H, W)).astype(np.float32), depth, np.zeros((H, W), np.uint8))
+
+
+def test_expand_adds_nothing_where_the_map_explains_the_frame():
+    tgt = _expand_frame()
+    cam = camera(13, 9, 7.0, T_cw=synth.look_pose((0.3, -0.2, 0.1), (0.2, 0.1, 1.0), up=(0, -1, 0)))
+    out = oracle.expand(dict(sil=np.ones((9, 13)), depth=tgt.depth), tgt, cam, np.zeros((200, 4)))
+    assert len(out["src_pix"]) == 0
+
+
+def test_expand_of_an_empty_render_unprojects_every_valid_pixel():
+    """Every pixel with depth: the new mean reprojects to its pixel centre at d_gt, scale d/fx,
+    opacity 1/2, the observed colour, features in order."""
+    tgt = _expand_frame()
+    cam = camera(13, 9, 7.0, T_cw=synth.look_pose((0.3, -0.2, 0.1), (0.2, 0.1, 1.0), up=(0, -1, 0)))
+    feat = synth.rng(66).standard_normal((200, 4))
+    out = oracle.expand(dict(sil=np.zeros((9, 13)), depth=np.zeros((9, 13))), tgt, cam, feat)
+    want = np.nonzero(tgt.depth.ravel() > 0)[0]
+    np.testing.assert_array_equal(out["src_pix"], want)
+    T = np.asarray(cam.T_cw)
+    pc = out["means"] @ T[:3, :3].T + T[:3, 3]
+    u = cam.fx * pc[:, 0] / pc[:, 2] + cam.cx
+    v = cam.fy * pc[:, 1] / pc[:, 2] + cam.cy
+    np.testing.assert_allclose(u, want % 13 + 0.5, atol=1e-12)
+    np.testing.assert_allclose(v, want // 13 + 0.5, atol=1e-12)
+    np.testing.assert_allclose(pc[:, 2], tgt.depth.ravel()[want], rtol=1e-12)
+    d = tgt.depth.ravel()[want].astype(np.float64)
+    np.testing.assert_allclose(out["log_scales"], np.log(d / 7.0)[:, None] * np.ones(3), rtol=1e-12)
+    assert (out["opacity_logits"] == 0).all() and sigmoid(0.0) == 0.5
+    np.testing.assert_array_equal(out["rgb"], tgt.rgb.reshape(3, -1)[:, want].T)
+    np.testing.assert_array_equal(out["feat"], feat[:len(want)])
+    np.testing.assert_array_equal(out["quats"], np.tile([1.0, 0, 0, 0], (len(want), 1)))
+
+
+def test_expand_depth_rule_is_fifty_times_the_lower_median():
+    """Covered pixels (sil = 1): a pixel expands only if rendered behind the observation by more
+    than 50 x the lower median of |d_gt - d_hat| (errors exact in f32)."""
+    H, W = 4, 8
+    tgt = synth.Frame(np.zeros((3, H, W), np.float32), np.full((H, W), 2.0, np.float32), np.zeros((H, W), np.uint8))
+    e = np.full(H * W, 2.0 ** -12, np.float32)             # the median error: 2^-12
+    e[3] = 50 * 2.0 ** -12 + 2.0 ** -10                     # behind, just over 50 x median: expands
+    e[4] = 50 * 2.0 ** -12 - 2.0 ** -10                     # behind, just under: no
+    e[5] = -(50 * 2.0 ** -12 + 2.0 ** -10)                  # in front by as much: no (d_hat < d_gt)
+    e[6] = 50 * 2.0 ** -12                                  # exactly 50 x median: no (strict)
+    d_hat = (tgt.depth.ravel() + e).reshape(H, W)
+    out = oracle.expand(dict(sil=np.ones((H, W)), depth=d_hat), tgt, camera(W, H, 5.0), np.zeros((50, 2)))
+    assert out["median"] == 2.0 ** -12
+    np.testing.assert_array_equal(out["src_pix"], [3])
+    out2 = oracle.expand(dict(sil=np.full((H, W), 0.49), depth=d_hat), tgt, camera(W, H, 5.0), np.zeros((50, 2)),
+                         tau_unobs=0.5)
+    assert len(out2["src_pix"]) == H * W                    # low opacity alone expands
