@@ -392,6 +392,29 @@ gs_status gs_adam_step(const gs_field_mut *f, const gs_gaussian_grads *grads, fl
                        double *step_ctr, const float *lr, double beta1, double beta2, double eps,
                        gs_stream stream);
 
+/* Adaptive Gaussian expansion (Eq. 11 and the initialisation that follows it
+ * in Sec. 3.3).  Per view, M_unobs = (sil < tau_unobs) or (depth > d_gt and
+ * |d_gt - depth| > 50 x median) on pixels with d_gt > 0, where median is the
+ * lower median of |depth - d_gt| over the view's pixels with d_gt > 0 and
+ * sil, depth are the rendered images (img->sil, img->depth).  One Gaussian is
+ * appended per masked pixel, pixels in raster order and views in order: mean =
+ * the pixel centre unprojected at d_gt into the world frame, rotation identity,
+ * log-scale log(d_gt / fx) on every axis, opacity 0.5 (logit 0), colour =
+ * tgt->rgb at the pixel, features = row k of feat_init (device f32
+ * [field->n - n_existing, feat_dim], values the caller draws) for the k-th new
+ * Gaussian.  field: arrays of field->n rows; rows [0, n_existing) are kept and
+ * the new ones written from row n_existing.  n_new (device int64) receives the
+ * number of masked pixels; if it exceeds field->n - n_existing only that many
+ * are written and *status (device) becomes GS_ERR_CAPACITY (else 0).  src_pix
+ * (optional device int64 [field->n - n_existing]) receives each new Gaussian's
+ * pixel index (pix_off(v) + y W + x).  ws: the workspace of gs_workspace_size
+ * for these cameras.  GS_ERR_ARG for missing buffers or n_existing outside
+ * [0, field->n]. */
+gs_status gs_expand(const gs_camera *cams, int n_views, const gs_images *img, const gs_targets *tgt,
+                    float tau_unobs, const float *feat_init, int64_t n_existing, gs_field_mut *field,
+                    int64_t *n_new, int64_t *src_pix, int32_t *status, void *ws, size_t ws_bytes,
+                    gs_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -108,6 +108,8 @@ _SIGNATURES = {
                              c_double, c_void_p, c_void_p]),
     "gs_adam_step": (c_int, [_P(gs_field_mut), _P(gs_gaussian_grads), c_void_p, c_int, c_void_p, _P(c_float),
                              c_double, c_double, c_double, c_void_p]),
+    "gs_expand": (c_int, [_P(gs_camera), c_int, _P(gs_images), _P(gs_targets), c_float, c_void_p, c_int64,
+                          _P(gs_field_mut), c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
 }
 
 _lib = None
@@ -166,3 +168,4 @@ gs_loss_fwd_bwd_noalloc = _wrap("gs_loss_fwd_bwd_noalloc")
 gs_dsr = _wrap("gs_dsr")
 gs_pose_step = _wrap("gs_pose_step")
 gs_adam_step = _wrap("gs_adam_step")
+gs_expand = _wrap("gs_expand")

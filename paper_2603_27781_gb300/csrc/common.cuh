@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "gs.h"
 
 namespace gs {
@@ -224,6 +226,7 @@ struct WsLayout {
     size_t loss_part_f;   // f32 [kLossBlocks][32 * 32 + 32] decoder-gradient partials
     size_t loss_part_d;   // f64 [kLossBlocks + SSIM tiles][3] loss-term partials
     size_t ssim_maps;     // f32 [9 P] SSIM window partials (3 planes per channel)
+    size_t expand_counts; // u32 [2][views x 256-pixel blocks] expansion counts and offsets
     size_t dsr_part;      // f64 [512][6] DSR partials
     size_t misc_end;
     size_t total;
@@ -240,6 +243,13 @@ constexpr int kScanBlock = 256 * kScanIPT;
 
 // Workspace layout; vt (may be NULL) adds the per-pixel space of the SSIM term.
 WsLayout ws_layout(int64_t n, int n_views, int64_t capacity, const ViewTable *vt = nullptr);
+
+// 256-pixel blocks per view row of the expansion grid (the largest view's count).
+inline int expand_blocks_x(const ViewTable &vt) {
+    int64_t m = 0;
+    for (int v = 0; v < vt.n_views; ++v) m = std::max<int64_t>(m, (int64_t)vt.W[v] * vt.H[v]);
+    return (int)std::max<int64_t>(1, (m + 255) / 256);
+}
 
 // SSIM term of the mapping colour loss (ssim.cu).
 int ssim_blocks(const ViewTable &vt);

@@ -820,3 +820,174 @@ extern "C" gs_status gs_loss_fwd_bwd_noalloc(const gs_camera *cams, int n_views,
     }
 #undef GS_LOSS
 }
+
+// ---------------------------------------------------- adaptive Gaussian expansion
+// Eq. 11: M_unobs = (o_hat < tau) or (d_hat > d_gt and |d_gt - d_hat| > 50 median) on pixels with
+// d_gt > 0, the median being the view's lower median of |d - d_gt| over d_gt > 0 (the same radix
+// selection as the tracking mask).  One new Gaussian per masked pixel, in pixel order per view,
+// views in order: a count per 256-pixel block, an ordered scan of the counts, then an emit pass
+// that ranks the block's masked pixels by warp ballots.
+namespace gs {
+namespace {
+
+__device__ __forceinline__ bool unobserved(float sil, float d, float dgt, float med, float tau) {
+    if (!(dgt > 0.f)) return false;
+    return sil < tau || (d > dgt && depth_error(d, dgt) > 50.f * med);
+}
+
+__global__ void __launch_bounds__(256) expand_count_kernel(ViewTable vt, const float *sil, const float *depth,
+                                                           const float *tdepth, const uint32_t *hist, float tau,
+                                                           uint32_t *counts) {
+    __shared__ uint32_t s_cnt;
+    const int v = blockIdx.y;
+    // every thread of the block takes part in the selection (it synchronises the block)
+    const float med = __uint_as_float(block_select(hist, vt.n_views, v, 4));
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    const int64_t Pv = (int64_t)vt.W[v] * vt.H[v];
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    bool m = false;
+    if (i < Pv) {
+        const int64_t pix = vt.pix_off[v] + i;
+        m = unobserved(sil[pix], depth[pix], tdepth[pix], med, tau);
+    }
+    const uint32_t bal = __ballot_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0 && bal) atomicAdd(&s_cnt, __popc(bal));
+    __syncthreads();
+    if (threadIdx.x == 0) counts[(int64_t)v * gridDim.x + blockIdx.x] = s_cnt;
+}
+
+// One block: exclusive scan of the counts in order (views, then blocks); the total to *n_new.
+__global__ void __launch_bounds__(1024) expand_scan_kernel(const uint32_t *counts, int64_t n, uint32_t *offsets,
+                                                           int64_t *n_new) {
+    __shared__ uint32_t s_warp[32];
+    __shared__ uint64_t s_carry;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < n; base += 1024) {
+        const int64_t i = base + threadIdx.x;
+        const uint32_t c = i < n ? counts[i] : 0u;
+        uint32_t x = c;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+            if (lane >= d) x += y;
+        }
+        if (lane == 31) s_warp[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            uint32_t t = s_warp[lane];
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, t, d);
+                if (lane >= d) t += y;
+            }
+            s_warp[lane] = t;
+        }
+        __syncthreads();
+        const uint64_t before = s_carry + (w > 0 ? s_warp[w - 1] : 0u) + x - c;
+        if (i < n) offsets[i] = (uint32_t)before;
+        __syncthreads();
+        if (threadIdx.x == 0) s_carry += s_warp[31];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *n_new = (int64_t)s_carry;
+}
+
+struct ExpandOut {
+    float *means, *quats, *log_scales, *logits, *rgb, *feat;
+    int64_t *src_pix;
+};
+
+__global__ void __launch_bounds__(256) expand_emit_kernel(ViewTable vt, const float *sil, const float *depth,
+                                                          const float *trgb, const float *tdepth,
+                                                          const uint32_t *hist, float tau, const uint32_t *offsets,
+                                                          int64_t room, int64_t P, int D, const float *feat_init,
+                                                          ExpandOut o, int32_t *status) {
+    __shared__ uint32_t s_warp[8];
+    const int v = blockIdx.y, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    // every thread of the block takes part in the selection (it synchronises the block)
+    const float med = __uint_as_float(block_select(hist, vt.n_views, v, 4));
+    const int64_t Pv = (int64_t)vt.W[v] * vt.H[v];
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    const int64_t pix = vt.pix_off[v] + i;
+    float d = 0.f;
+    bool m = false;
+    if (i < Pv) {
+        d = tdepth[pix];
+        m = unobserved(sil[pix], depth[pix], d, med, tau);
+    }
+    const uint32_t bal = __ballot_sync(0xffffffffu, m);
+    if (lane == 0) s_warp[w] = __popc(bal);
+    __syncthreads();
+    uint32_t before = 0;
+    for (int k = 0; k < w; ++k) before += s_warp[k];
+    if (!m) return;
+    const int64_t rank = (int64_t)offsets[(int64_t)v * gridDim.x + blockIdx.x] + before +
+                         __popc(bal & ((1u << lane) - 1u));
+    if (rank >= room) {
+        set_status(status, GS_ERR_CAPACITY);
+        return;
+    }
+    const int x = (int)(i % vt.W[v]), y = (int)(i / vt.W[v]);
+    // the pixel centre unprojected at d_gt: camera point, then world = R^T (p_c - t)
+    const float pc[3] = {((float)x + 0.5f - vt.cx[v]) / vt.fx[v] * d, ((float)y + 0.5f - vt.cy[v]) / vt.fy[v] * d, d};
+    const float *T = vt.T[v];
+    const float q[3] = {pc[0] - T[3], pc[1] - T[7], pc[2] - T[11]};
+#pragma unroll
+    for (int j = 0; j < 3; ++j) o.means[3 * rank + j] = T[j] * q[0] + T[4 + j] * q[1] + T[8 + j] * q[2];
+    o.quats[4 * rank] = 1.f;
+    o.quats[4 * rank + 1] = o.quats[4 * rank + 2] = o.quats[4 * rank + 3] = 0.f;
+    const float ls = logf(d / vt.fx[v]);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) o.log_scales[3 * rank + j] = ls;
+    o.logits[rank] = 0.f;                       // opacity 0.5
+#pragma unroll
+    for (int c = 0; c < 3; ++c) o.rgb[3 * rank + c] = trgb[c * P + pix];
+    for (int k = 0; k < D; ++k) o.feat[rank * D + k] = feat_init[rank * D + k];
+    if (o.src_pix) o.src_pix[rank] = pix;
+}
+
+}  // namespace
+}  // namespace gs
+
+extern "C" gs_status gs_expand(const gs_camera *cams, int n_views, const gs_images *img, const gs_targets *tgt,
+                               float tau_unobs, const float *feat_init, int64_t n_existing, gs_field_mut *field,
+                               int64_t *n_new, int64_t *src_pix, int32_t *status, void *ws, size_t ws_bytes,
+                               gs_stream stream) {
+    using namespace gs;
+    ViewTable vt;
+    if (!img || !tgt || !field || !n_new || !status || !make_view_table(cams, n_views, 0, &vt)) return GS_ERR_ARG;
+    if (!feat_dim_ok(field->feat_dim)) return GS_ERR_UNSUPPORTED;
+    const int64_t capacity = field->n;  // rows of the field's arrays
+    if (n_existing < 0 || capacity < n_existing || !img->sil || !img->depth || !tgt->rgb || !tgt->depth ||
+        !field->means || !field->quats || !field->log_scales || !field->opacity_logits || !field->rgb ||
+        (field->feat_dim && (!field->feat || !feat_init)) || !(tau_unobs >= 0.f))
+        return GS_ERR_ARG;
+    WsLayout L = ws_layout(0, n_views, 0, &vt);
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) || ws_bytes < L.misc_end) return GS_ERR_ARG;
+    char *w = static_cast<char *>(ws);
+    uint32_t *mh = reinterpret_cast<uint32_t *>(w + L.med_hist);
+    const int bx = expand_blocks_x(vt);
+    uint32_t *counts = reinterpret_cast<uint32_t *>(w + L.expand_counts);
+    uint32_t *offsets = counts + (size_t)n_views * bx;
+    cudaStream_t st = (cudaStream_t)stream;
+    gs_status s;
+    if ((s = cuda_status(cudaMemsetAsync(status, 0, sizeof(int32_t), st)))) return s;
+    if ((s = cuda_status(cudaMemsetAsync(mh, 0, sizeof(uint32_t) * 4 * 256 * n_views, st)))) return s;
+    const dim3 hgrid(loss_blocks_x(vt), n_views);
+    for (int pass = 0; pass < 4; ++pass)
+        median_hist_kernel<<<hgrid, 256, 0, st>>>(vt, pass, img->depth, tgt->depth, mh);
+    const dim3 grid(bx, n_views);
+    expand_count_kernel<<<grid, 256, 0, st>>>(vt, img->sil, img->depth, tgt->depth, mh, tau_unobs, counts);
+    expand_scan_kernel<<<1, 1024, 0, st>>>(counts, (int64_t)n_views * bx, offsets, n_new);
+    const int64_t D = field->feat_dim;
+    ExpandOut o{field->means + 3 * n_existing, field->quats + 4 * n_existing, field->log_scales + 3 * n_existing,
+                field->opacity_logits + n_existing, field->rgb + 3 * n_existing,
+                D ? field->feat + D * n_existing : nullptr, src_pix};
+    expand_emit_kernel<<<grid, 256, 0, st>>>(vt, img->sil, img->depth, tgt->rgb, tgt->depth, mh, tau_unobs, offsets,
+                                             capacity - n_existing, vt.pix_off[n_views], (int)D, feat_init, o,
+                                             status);
+    return last_launch();
+}

@@ -356,6 +356,38 @@ class MappingAdam:
                                                self.betas[1], self.eps, _stream(stream)))
 
 
+def expand(r: "Renderer", field: Field, targets, feat_init: torch.Tensor, tau_unobs: float = 0.5, stream=None):
+    """Adaptive Gaussian expansion (Eq. 11) after the renderer's last forward over its views:
+    returns (the field with one Gaussian appended per unobserved pixel, the new Gaussians'
+    source pixels, the number of unobserved pixels, the status word: GS_ERR_CAPACITY when that
+    number exceeds n_max and only the first n_max were added).  feat_init [n_max, D] holds the
+    new Gaussians' features (the caller draws them).  Reads the count back to the host (the
+    field's size sets every later launch)."""
+    if field.rgb.dtype != torch.float32 or field.feat.dtype != torch.float32:
+        raise ValueError("expansion appends to f32 parameter storage")
+    n, D = field.n, field.feat_dim
+    n_max = int(feat_init.shape[0])
+    grow = lambda t: torch.cat([t, t.new_zeros((n_max,) + tuple(t.shape[1:]))]).contiguous()
+    out = Field(*(grow(t) for t in (field.means, field.quats, field.log_scales, field.opacity_logits, field.rgb,
+                                    field.feat)))
+    fm = L.gs_field_mut(n + n_max, D, _p(out.means), _p(out.quats), _p(out.log_scales), _p(out.opacity_logits),
+                        _p(out.rgb), _p(out.feat) if D else None)
+    dev = field.means.device
+    n_new = torch.zeros(1, dtype=torch.int64, device=dev)
+    src = torch.zeros(max(n_max, 1), dtype=torch.int64, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    tc = L.gs_targets(_p(targets["rgb"]), _p(targets["depth"]), _p(targets["label"]))
+    fi = feat_init.contiguous().to(torch.float32)
+    L.check("gs_expand", L.gs_expand(r.cams_c, r.n_views, ctypes.byref(r.images_c()), ctypes.byref(tc), tau_unobs,
+                                     _p(fi) if D else None, n, ctypes.byref(fm), _p(n_new), _p(src), _p(status),
+                                     _p(r.ws), r.ws.numel(), _stream(stream)))
+    total = int(n_new.item())
+    k = min(total, n_max)
+    keep = lambda t: t[: n + k].contiguous()
+    return Field(*(keep(t) for t in (out.means, out.quats, out.log_scales, out.opacity_logits, out.rgb,
+                                     out.feat))), src[:k], total, int(status.item())
+
+
 class RasterizeSG(torch.autograd.Function):
     """Differentiable render of a Semantic Gaussian Field through libgs.
 
