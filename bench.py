@@ -580,6 +580,28 @@ def run_ours(args, rank, world, local_rank):
                                 "frac_of_measured_hbm": adam_gbs / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None,
                                 "timing": "20 back-to-back launches (parameters and moments ~1 GB, above L2)"}
     del opt, fcopy
+    # adaptive expansion (Eq. 11) after this frame's forward: median, mask, ordered compaction and
+    # initialisation of up to one Gaussian per pixel, into preallocated rows (C ABI, no host reads)
+    import ctypes
+    from paper_2603_27781_gb300 import _lib as L
+    r.forward(field)
+    n0, D, n_max = field.n, field.feat_dim, r.P
+    rows = [torch.empty((n0 + n_max,) + tuple(t.shape[1:]), dtype=torch.float32, device=dev)
+            for t in (field.means, field.quats, field.log_scales, field.opacity_logits, field.rgb, field.feat)]
+    fm = L.gs_field_mut(n0 + n_max, D, *(raster._p(t) for t in rows))
+    feat_init = torch.randn(n_max, D, device=dev)
+    n_new = torch.zeros(1, dtype=torch.int64, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    tc = L.gs_targets(raster._p(targets["rgb"]), raster._p(targets["depth"]), raster._p(targets["label"]))
+    ic = r.images_c()
+    expand = lambda: L.check("gs_expand", L.gs_expand(r.cams_c, r.n_views, ctypes.byref(ic), ctypes.byref(tc), 0.5,
+                                                      raster._p(feat_init), n0, ctypes.byref(fm), raster._p(n_new),
+                                                      None, raster._p(status), raster._p(r.ws), r.ws.numel(),
+                                                      raster._stream(None)))
+    exp_ms = time_calls(expand)
+    extras["expansion"] = {"ms": exp_ms, "new_gaussians": int(n_new.item()), "pixels": r.P,
+                           "status": int(status.item())}
+    del rows, feat_init
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
