@@ -365,3 +365,36 @@ def expand(images, target, cam, feat_init, tau_unobs=TAU_UNOBS):
                 log_scales=np.repeat(np.log(d / cam.fx)[:, None], 3, 1), opacity_logits=np.zeros(n),
                 rgb=np.asarray(target.rgb, np.float64).reshape(3, -1)[:, pix].T,
                 feat=np.asarray(feat_init, np.float64)[:n], median=float(med), mask=mask)
+
+
+def constant_velocity(T_prev, T_prev2):
+    """Eq. 19: the pose of a new frame from the two before it, T_t = T_{t-1} T_{t-2}^-1 T_{t-1}
+    (world-to-camera, FP64)."""
+    T_prev, T_prev2 = np.asarray(T_prev, np.float64), np.asarray(T_prev2, np.float64)
+    return T_prev @ np.linalg.inv(T_prev2) @ T_prev
+
+
+def track_sequence(gs, cam, prm: Params, frames, dec, T_known, n_it=40, lr=None):
+    """Frame-to-model tracking (Sec. 3.4) over a sequence with a fixed map: the first
+    len(T_known) frames keep the given poses; each later frame starts from the constant-velocity
+    prediction of Eq. 19 (from one known pose only: that pose) and takes n_it pose-only steps of
+    the tracking loss (Eq. 20-21) with Adam (moments reset per frame).  cam gives the
+    intrinsics.  Returns the list of poses."""
+    if lr is None:
+        lr = np.array([2e-3, 2e-3, 2e-3, 4e-4, 4e-4, 4e-4])
+    est = [np.asarray(T, np.float64) for T in T_known]
+    for t in range(len(est), len(frames)):
+        T = constant_velocity(est[-1], est[-2] if t >= 2 else est[-1])
+        m, v = np.zeros(6), np.zeros(6)
+        for it in range(1, n_it + 1):
+            c = type(cam)(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy, T)
+            out = step(gs, c, prm, frames[t], dec, TRACKING)
+            T, m, v = pose_step(T, out["grads"]["twist"], m, v, it, lr)
+        est.append(T)
+    return est
+
+
+def ate_rmse(est, gt):
+    """Absolute trajectory error: RMS distance between estimated and true camera centres."""
+    centre = lambda T: -np.asarray(T)[:3, :3].T @ np.asarray(T)[:3, 3]
+    return float(np.sqrt(np.mean([np.sum((centre(a) - centre(b)) ** 2) for a, b in zip(est, gt)])))

@@ -257,6 +257,21 @@ def keyframe_loop(n_poses: int = 200, seed: int = SEED_KEYFRAMES, room: Room | N
     return poses
 
 
+def smooth_path(n: int, step_deg: float = 0.6, room: Room | None = None):
+    """World->camera poses of a camera moving along the loop ellipse without yaw jitter: n
+    consecutive frames, each step_deg of the ellipse apart, looking along the tangent."""
+    room = room or make_room()
+    cx, cy = room.size[0] / 2, room.size[1] / 2
+    rx, ry = 0.35 * room.size[0], 0.35 * room.size[1]
+    poses = []
+    for k in range(n):
+        th = math.radians(step_deg * k)
+        pos = (cx + rx * math.cos(th), cy + ry * math.sin(th), 1.5)
+        tangent = math.atan2(ry * math.cos(th), -rx * math.sin(th))
+        poses.append(look_pose(pos, (math.cos(tangent), math.sin(tangent), -0.05)))
+    return poses
+
+
 def draw_keyframes(n: int, n_poses: int = 200, seed: int = SEED_KEYFRAMES):
     """Indices of n keyframes drawn i.i.d. uniformly from the n_poses loop poses."""
     return rng(seed + 7).integers(0, n_poses, n)

@@ -755,3 +755,45 @@ def test_expand_depth_rule_is_fifty_times_the_lower_median():
     out2 = oracle.expand(dict(sil=np.full((H, W), 0.49), depth=d_hat), tgt, camera(W, H, 5.0), np.zeros((50, 2)),
                          tau_unobs=0.5)
     assert len(out2["src_pix"]) == H * W                    # low opacity alone expands
+
+
+# --------------------------------------------- tracking over a sequence (Eq. 19)
+def test_constant_velocity_is_exact_for_a_constant_screw_motion():
+    """T_k = Exp(k xi) T_0: the prediction from frames t-1, t-2 is frame t."""
+    xi = np.array([0.03, -0.01, 0.02, 0.01, -0.02, 0.015])
+    T0 = synth.look_pose((1.0, 2.0, 1.5), (0.3, 1.0, -0.1))
+    T = [_se3_exp(k * xi) @ T0 for k in range(5)]
+    for t in range(2, 5):
+        np.testing.assert_allclose(oracle.constant_velocity(T[t - 1], T[t - 2]), T[t], atol=1e-12)
+
+
+def test_ate_of_a_shifted_trajectory_is_the_shift():
+    T0 = synth.look_pose((1.0, 2.0, 1.5), (0.3, 1.0, -0.1))
+    gt = [_se3_exp(k * np.array([0.02, 0, 0, 0, 0.01, 0])) @ T0 for k in range(4)]
+    shift = np.array([0.03, -0.04, 0.0])                       # camera centres moved by 5 cm
+    est = []
+    for T in gt:
+        R, t = T[:3, :3], T[:3, 3]
+        S = T.copy()
+        S[:3, 3] = t - R @ shift                               # centre -R^T t moves by +shift
+        est.append(S)
+    assert oracle.ate_rmse(gt, gt) == 0.0
+    assert oracle.ate_rmse(est, gt) == pytest.approx(0.05, rel=1e-12)
+
+
+def test_tracking_a_sequence_rendered_from_the_map_stays_on_it():
+    """A camera in constant screw motion observing the map's own renders (labels ignored), the
+    first two poses given: the prediction of Eq. 19 is exact and the tracking loss is already at
+    its minimum, so every estimate is the true pose."""
+    gs = synth.box_field(400, 4, seed=9)
+    xi = np.array([0.01, -0.005, 0.0, 0.002, -0.004, 0.003])
+    gt = [_se3_exp(k * xi) for k in range(4)]
+    prm = Params()
+    frames = []
+    for T in gt:
+        img = oracle.forward(gs, camera(48, 36, 45.0, T_cw=T), prm)[2]
+        frames.append(synth.Frame(img["rgb"], img["depth"], np.full((36, 48), 255, np.uint8)))
+    dec = synth.Decoder(np.zeros((2, 4)), np.zeros(2))
+    est = oracle.track_sequence(gs, camera(48, 36, 45.0), prm, frames, dec, gt[:2], n_it=3)
+    for a, b in zip(est, gt):
+        np.testing.assert_allclose(a, b, atol=1e-9)
