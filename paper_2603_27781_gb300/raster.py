@@ -10,6 +10,7 @@ import ctypes
 import dataclasses
 from typing import Optional, Sequence
 
+import numpy as np
 import torch
 
 from . import _lib as L
@@ -386,6 +387,76 @@ def expand(r: "Renderer", field: Field, targets, feat_init: torch.Tensor, tau_un
     keep = lambda t: t[: n + k].contiguous()
     return Field(*(keep(t) for t in (out.means, out.quats, out.log_scales, out.opacity_logits, out.rgb,
                                      out.feat))), src[:k], total, int(status.item())
+
+
+class Tracker:
+    """Frame-to-model tracking (Sec. 3.4) against a fixed map on the GPU.  A frame's n_it
+    pose-only iterations (tracking loss of Eq. 20-21 with the M_obs mask; Adam on the twist with
+    the C.1 rates, moments reset per frame) replay from one CUDA graph in which each pose step
+    writes the pose the next projection reads; per frame the observation is copied into the
+    graph's input buffers and the start pose is set before the replay."""
+
+    def __init__(self, field: Field, cam, dec_W: torch.Tensor, dec_b: torch.Tensor, n_it: int = 40,
+                 params: RasterParams = RasterParams(), margin: float = 1.6, lr=TRACKING_LR):
+        dev = field.means.device
+        self.field, self.W, self.b, self.n_it, self.lr = field, dec_W, dec_b, n_it, lr
+        self.r = fit_capacity(field, [cam], field.feat_dim, margin=margin, params=params,
+                              n_classes=int(dec_W.shape[0]), device=dev)
+        P = cam.width * cam.height
+        self.tg = dict(rgb=torch.zeros(3, P, device=dev), depth=torch.zeros(P, device=dev),
+                       label=torch.zeros(P, dtype=torch.uint8, device=dev))
+        self.T = torch.zeros(1, 16, dtype=torch.float64, device=dev)
+        self.adam = torch.zeros(13, dtype=torch.float64, device=dev)
+        self.pose = torch.zeros(1, 16, dtype=torch.float32, device=dev)
+        self.graph = None
+
+    def _iterations(self):
+        for _ in range(self.n_it):
+            self.r.iteration(self.field, self.tg, self.W, self.b, TRACKING, L.GS_GRAD_POSE, pose_dev=self.pose)
+            self.r.pose_step(self.T, self.adam, 0, lr=self.lr, pose_f32=self.pose)
+
+    def _start(self, T_init):
+        self.T.copy_(torch.as_tensor(np.asarray(T_init, np.float64).reshape(1, 16)))
+        self.adam.zero_()
+        self.pose.copy_(self.T.float())
+
+    def track(self, frame, T_init) -> np.ndarray:
+        """Pose (4x4 world-to-camera, f64) of one observed frame (rgb [3,H,W], depth [H,W],
+        label [H,W]) from the start pose T_init."""
+        self.tg["rgb"].copy_(torch.as_tensor(np.ascontiguousarray(frame.rgb, np.float32).reshape(3, -1)))
+        self.tg["depth"].copy_(torch.as_tensor(np.ascontiguousarray(frame.depth, np.float32).ravel()))
+        self.tg["label"].copy_(torch.as_tensor(np.ascontiguousarray(frame.label, np.uint8).ravel()))
+        if self.graph is None:
+            self._start(T_init)
+            cur = torch.cuda.current_stream()
+            side = torch.cuda.Stream()
+            side.wait_stream(cur)
+            with torch.cuda.stream(side):
+                self._iterations()
+            cur.wait_stream(side)
+            self.graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self.graph):
+                self._iterations()
+        self._start(T_init)
+        self.graph.replay()
+        T = self.T.cpu().numpy().reshape(4, 4)
+        if self.r.status() != 0:
+            raise L.GsError("tracking binning", self.r.status())
+        return T
+
+
+def constant_velocity(T_prev, T_prev2):
+    """Eq. 19: T_t = T_{t-1} T_{t-2}^-1 T_{t-1} (world-to-camera, f64)."""
+    return np.asarray(T_prev, np.float64) @ np.linalg.inv(np.asarray(T_prev2, np.float64)) @ T_prev
+
+
+def track_sequence(tracker: Tracker, frames, T_known):
+    """Poses of a frame sequence: the first len(T_known) frames keep the given poses; each later
+    frame is tracked from the constant-velocity prediction (Eq. 19)."""
+    est = [np.asarray(T, np.float64) for T in T_known]
+    for t in range(len(est), len(frames)):
+        est.append(tracker.track(frames[t], constant_velocity(est[-1], est[-2] if len(est) >= 2 else est[-1])))
+    return est
 
 
 class RasterizeSG(torch.autograd.Function):
