@@ -415,6 +415,39 @@ gs_status gs_expand(const gs_camera *cams, int n_views, const gs_images *img, co
                     int64_t *n_new, int64_t *src_pix, int32_t *status, void *ws, size_t ws_bytes,
                     gs_stream stream);
 
+/* Keyframe store of one camera's frames (device memory, caller-owned), slot
+ * s holding: rgb[s] [3,P] f32, depth[s] [P] f32, label[s] [P] u8 (planar, the
+ * layout of gs_targets) and T_cw[s] [16] f64 (the frame's estimated
+ * world-to-camera pose, row-major). */
+typedef struct {
+    int32_t capacity;
+    int64_t P;
+    const float *rgb;
+    const float *depth;
+    const uint8_t *label;
+    const double *T_cw;
+} gs_keyframes;
+
+/* RSKM keyframe draw (Eq. 13, Sec. 3.3) for one mapping iteration.  The
+ * candidates are the keyframe set K = slots [0, n_kf) together with the
+ * current frame f_cur = cur_slot (0 <= cur_slot <= n_kf: either a stored
+ * keyframe or the slot after them), |K u {f_cur}| = max(n_kf, cur_slot + 1)
+ * candidates in slot order.  With k the mapping iteration counter state[0]
+ * (device int32, set to 0 before a frame's first iteration): if k mod t_opt
+ * is 0 the draw is f_cur (Eq. 13 gives it probability 1 there), otherwise
+ * candidate draws[k mod n_draws] mod |K u {f_cur}| (a uniform draw; draws:
+ * device u32 random words the caller supplies, n_draws >= 1).  The call writes
+ * the slot to state[1] and to picked[k] (optional, device int32 [n_draws],
+ * for k < n_draws), increments state[0], copies the slot's observation into
+ * out_rgb [3,P], out_depth [P], out_label [P] (device) and its pose, rounded
+ * to f32, into pose_f32 [16] (optional; gs_project's pose_dev).  The counter
+ * and slot live on the device, so a captured CUDA graph replays the draw.
+ * GS_ERR_ARG for a missing buffer, t_opt < 1 or slots outside the store. */
+gs_status gs_rskm_draw(const gs_keyframes *kf, int32_t n_kf, int32_t cur_slot, int32_t t_opt,
+                       const uint32_t *draws, int64_t n_draws, int32_t *state, int32_t *picked,
+                       float *out_rgb, float *out_depth, uint8_t *out_label, float *pose_f32,
+                       gs_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -398,3 +398,100 @@ def ate_rmse(est, gt):
     """Absolute trajectory error: RMS distance between estimated and true camera centres."""
     centre = lambda T: -np.asarray(T)[:3, :3].T @ np.asarray(T)[:3, 3]
     return float(np.sqrt(np.mean([np.sum((centre(a) - centre(b)) ** 2) for a, b in zip(est, gt)])))
+
+
+# --------------------------------------------------------------- SLAM loop
+def rskm_select(k_m, t_opt, cur, keyframes, draw):
+    """RSKM keyframe draw of Eq. 13 for mapping iteration k_m (0-based) of the current frame
+    cur.  Where k_m mod t_opt = 0 the formula gives the current frame probability 1: it is
+    taken.  Elsewhere every frame of the candidate set (the keyframe set K, in insertion
+    order, together with the current frame when it is not a keyframe) has probability
+    1/|K|: the candidate with index draw mod |candidates| is taken, draw a uniform 32-bit
+    integer supplied by the caller."""
+    if k_m % t_opt == 0:
+        return cur
+    cands = list(keyframes) + ([] if cur in keyframes else [cur])
+    return cands[int(draw) % len(cands)]
+
+
+@dataclasses.dataclass
+class SlamConfig:
+    """Iteration counts and intervals of the SLAM loop.  C.1 gives 40 tracking and 60
+    mapping iterations per frame (Replica); the paper gives no value for t_opt, the first
+    frame's k_init, or the keyframe interval (readings: 2, the mapping count, every 5th)."""
+    n_track: int = 40
+    n_map: int = 60
+    n_init: int = 60
+    t_opt: int = 2
+    kf_every: int = 5
+    tau_unobs: float = TAU_UNOBS
+
+
+@dataclasses.dataclass
+class Field:
+    """A Gaussian field as FP64 arrays (the attributes the functions above read)."""
+    means: np.ndarray
+    quats: np.ndarray
+    log_scales: np.ndarray
+    opacity_logits: np.ndarray
+    rgb: np.ndarray
+    feat: np.ndarray
+
+    @property
+    def n(self) -> int:
+        return int(self.means.shape[0])
+
+
+def _append(gs, new):
+    cat = lambda a, b: np.concatenate([np.asarray(a, np.float64), np.asarray(b, np.float64).reshape(
+        (-1,) + np.asarray(a).shape[1:])])
+    return Field(*(cat(getattr(gs, k), new[k]) for k in ADAM_GROUPS))
+
+
+def slam(frames, cam, prm: Params, dec, T0, draws, feat_bank, cfg: SlamConfig = SlamConfig()):
+    """The GS3LAM loop over a sequence (Sec. 3.3-3.4), FP64.  For frame t: the pose (T0 for
+    the first frame; later frames tracked for n_track steps from the constant-velocity
+    prediction of Eq. 19 against the map so far); adaptive expansion (Eq. 11) of the map
+    rendered at that pose, new features taken in order from feat_bank; every kf_every-th
+    frame joins the keyframe set; then n_map mapping iterations (n_init for the first
+    frame), each on the frame drawn by RSKM (Eq. 13, one word of draws per iteration,
+    consumed in order) at its estimated pose, with the mapping loss (Eq. 14-18 with the
+    D-SSIM term of Eq. 15) and an Adam step of every parameter group (C.1 rates; moments
+    reset per frame, like the pose's).  The decoder stays fixed.  cam gives the
+    intrinsics.  Returns the estimated poses, the final field, the frames drawn and the
+    field size after each frame."""
+    D = dec.W.shape[1]
+    z = lambda *s: np.zeros(s, np.float64)
+    gs = Field(z(0, 3), z(0, 4), z(0, 3), z(0), z(0, 3), z(0, D))
+    at = lambda T: type(cam)(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy, np.asarray(T, np.float64))
+    lr_pose = np.array([2e-3, 2e-3, 2e-3, 4e-4, 4e-4, 4e-4])
+    est, keyframes, picks, sizes = [], [], [], []
+    n_drawn = n_feat = 0
+    for t, frame in enumerate(frames):
+        if t == 0:
+            T = np.asarray(T0, np.float64)
+        else:
+            T = constant_velocity(est[-1], est[-2] if t >= 2 else est[-1])
+            m, v = np.zeros(6), np.zeros(6)
+            for it in range(1, cfg.n_track + 1):
+                out = step(gs, at(T), prm, frame, dec, TRACKING)
+                T, m, v = pose_step(T, out["grads"]["twist"], m, v, it, lr_pose)
+        est.append(T)
+        img = forward(gs, at(T), prm)[2]
+        new = expand(img, frame, at(T), feat_bank[n_feat:], cfg.tau_unobs)
+        n_feat += len(new["src_pix"])
+        gs = _append(gs, new)
+        if t % cfg.kf_every == 0:
+            keyframes.append(t)
+        p = {k: getattr(gs, k) for k in ADAM_GROUPS}
+        m = {k: np.zeros_like(p[k]) for k in ADAM_GROUPS}
+        v = {k: np.zeros_like(p[k]) for k in ADAM_GROUPS}
+        for k_m in range(cfg.n_init if t == 0 else cfg.n_map):
+            f = rskm_select(k_m, cfg.t_opt, t, keyframes, draws[n_drawn])
+            n_drawn += 1
+            picks.append(f)
+            out = step(gs, at(est[f]), prm, frames[f], dec, MAPPING_SSIM)
+            p, m, v = adam_step(p, out["grads"], m, v, k_m + 1, MAPPING_LR)
+            gs = Field(*(p[k] for k in ADAM_GROUPS))
+        sizes.append(gs.n)
+    return dict(poses=est, gs=gs, picks=picks, sizes=sizes)

@@ -75,6 +75,11 @@ class gs_targets(Structure):
     _fields_ = [("rgb", c_void_p), ("depth", c_void_p), ("label", c_void_p)]
 
 
+class gs_keyframes(Structure):
+    _fields_ = [("capacity", c_int32), ("P", c_int64), ("rgb", c_void_p), ("depth", c_void_p), ("label", c_void_p),
+                ("T_cw", c_void_p)]
+
+
 class gs_loss_params(Structure):
     _fields_ = [("color", c_float), ("depth", c_float), ("sem", c_float), ("mask_mode", c_int32),
                 ("tau_obs", c_float), ("n_classes", c_int32), ("ssim", c_float)]
@@ -110,6 +115,8 @@ _SIGNATURES = {
                              c_double, c_double, c_double, c_void_p]),
     "gs_expand": (c_int, [_P(gs_camera), c_int, _P(gs_images), _P(gs_targets), c_float, c_void_p, c_int64,
                           _P(gs_field_mut), c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "gs_rskm_draw": (c_int, [_P(gs_keyframes), c_int32, c_int32, c_int32, c_void_p, c_int64, c_void_p, c_void_p,
+                             c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
 }
 
 _lib = None
@@ -169,3 +176,4 @@ gs_dsr = _wrap("gs_dsr")
 gs_pose_step = _wrap("gs_pose_step")
 gs_adam_step = _wrap("gs_adam_step")
 gs_expand = _wrap("gs_expand")
+gs_rskm_draw = _wrap("gs_rskm_draw")

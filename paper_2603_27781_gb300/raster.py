@@ -397,9 +397,10 @@ class Tracker:
     graph's input buffers and the start pose is set before the replay."""
 
     def __init__(self, field: Field, cam, dec_W: torch.Tensor, dec_b: torch.Tensor, n_it: int = 40,
-                 params: RasterParams = RasterParams(), margin: float = 1.6, lr=TRACKING_LR):
+                 params: RasterParams = RasterParams(), margin: float = 1.6, lr=TRACKING_LR, use_graph: bool = True):
         dev = field.means.device
         self.field, self.W, self.b, self.n_it, self.lr = field, dec_W, dec_b, n_it, lr
+        self.use_graph = use_graph
         self.r = fit_capacity(field, [cam], field.feat_dim, margin=margin, params=params,
                               n_classes=int(dec_W.shape[0]), device=dev)
         P = cam.width * cam.height
@@ -421,12 +422,20 @@ class Tracker:
         self.pose.copy_(self.T.float())
 
     def track(self, frame, T_init) -> np.ndarray:
-        """Pose (4x4 world-to-camera, f64) of one observed frame (rgb [3,H,W], depth [H,W],
-        label [H,W]) from the start pose T_init."""
-        self.tg["rgb"].copy_(torch.as_tensor(np.ascontiguousarray(frame.rgb, np.float32).reshape(3, -1)))
-        self.tg["depth"].copy_(torch.as_tensor(np.ascontiguousarray(frame.depth, np.float32).ravel()))
-        self.tg["label"].copy_(torch.as_tensor(np.ascontiguousarray(frame.label, np.uint8).ravel()))
-        if self.graph is None:
+        """Pose (4x4 world-to-camera, f64) of one observed frame (host arrays rgb [3,H,W],
+        depth [H,W], label [H,W], or a dict of device targets rgb [3,P], depth [P], label [P])
+        from the start pose T_init."""
+        if isinstance(frame, dict):
+            for k in ("rgb", "depth", "label"):
+                self.tg[k].copy_(frame[k].reshape(self.tg[k].shape))
+        else:
+            self.tg["rgb"].copy_(torch.as_tensor(np.ascontiguousarray(frame.rgb, np.float32).reshape(3, -1)))
+            self.tg["depth"].copy_(torch.as_tensor(np.ascontiguousarray(frame.depth, np.float32).ravel()))
+            self.tg["label"].copy_(torch.as_tensor(np.ascontiguousarray(frame.label, np.uint8).ravel()))
+        if not self.use_graph:
+            self._start(T_init)
+            self._iterations()
+        elif self.graph is None:
             self._start(T_init)
             cur = torch.cuda.current_stream()
             side = torch.cuda.Stream()
@@ -437,8 +446,9 @@ class Tracker:
             self.graph = torch.cuda.CUDAGraph()
             with torch.cuda.graph(self.graph):
                 self._iterations()
-        self._start(T_init)
-        self.graph.replay()
+        if self.use_graph:
+            self._start(T_init)
+            self.graph.replay()
         T = self.T.cpu().numpy().reshape(4, 4)
         if self.r.status() != 0:
             raise L.GsError("tracking binning", self.r.status())

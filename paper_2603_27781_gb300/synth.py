@@ -327,3 +327,16 @@ def random_frame(cam: Camera, k: int, seed: int = SEED_TARGET, depth_range=(2.5,
     return Frame(g.random((3, H, W)).astype(np.float32),
                  g.uniform(*depth_range, (H, W)).astype(np.float32),
                  g.integers(0, k, (H, W)).astype(np.uint8))
+
+
+SEED_SLAM = 6
+
+
+def rskm_draws(n: int, seed: int = SEED_SLAM) -> np.ndarray:
+    """n uniform 32-bit random words for keyframe draws (uint32)."""
+    return rng(seed).integers(0, 2 ** 32, n, dtype=np.uint64).astype(np.uint32)
+
+
+def feature_bank(n: int, d: int, seed: int = SEED_SLAM + 1) -> np.ndarray:
+    """n rows of N(0, 1) features [n, d] float32 for Gaussians added by expansion."""
+    return rng(seed).standard_normal((n, d)).astype(np.float32)

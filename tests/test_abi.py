@@ -82,6 +82,15 @@ def test_argument_errors_before_any_launch(lib):
                                    fake, 1 << 30, ctypes.byref(grads), fake, fake, fake, None, None,
                                    None) == L.GS_ERR_ARG
 
+    # the RSKM draw: slots inside the store, the current slot at most one past the keyframes,
+    # t_opt >= 1, random words present
+    kf = L.gs_keyframes(4, 64 * 48, fake, fake, fake, fake)
+    args = lambda n_kf, cur, t_opt, draws, n: (ctypes.byref(kf), n_kf, cur, t_opt, draws, n, fake, None, fake, fake,
+                                               fake, None, None)
+    for bad_args in (args(2, 3, 2, fake, 8), args(5, 4, 2, fake, 8), args(2, 2, 0, fake, 8), args(2, 2, 2, None, 8),
+                     args(2, 2, 2, fake, 0), args(4, 4, 2, fake, 8), args(-1, 0, 2, fake, 8)):
+        assert lib.gs_rskm_draw(*bad_args) == L.GS_ERR_ARG
+
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(L, "LIB_PATH", str(tmp_path / "missing.so"))

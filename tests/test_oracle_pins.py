@@ -795,3 +795,81 @@ def test_sequence_without_tracking_steps_follows_the_constant_velocity_predictio
     assert len(est) == 5
     for a, b in zip(est, gt):
         np.testing.assert_allclose(a, b, atol=1e-9)
+
+
+# ------------------------------------------------- RSKM keyframe draw (Eq. 13)
+def test_rskm_takes_the_current_frame_every_t_opt_iterations():
+    """Eq. 13 with mod(k_m, t_opt) = 0: p(f_cur) = 1/|K| + (1 - 1/|K|) = 1, whatever the draw."""
+    for draw in (0, 1, 7, 2 ** 32 - 1):
+        for k_m in (0, 3, 6, 9):
+            assert oracle.rskm_select(k_m, 3, 4, [0, 2, 4], draw) == 4
+    assert all(oracle.rskm_select(k, 1, 9, [0, 5], d) == 9 for k in range(5) for d in range(5))
+
+
+def test_rskm_draws_uniformly_between_the_current_frame_iterations():
+    """mod(k_m, t_opt) != 0: p(f) = 1/|K| for every keyframe; a full cycle of draws hits each
+    candidate once, and a current frame that is not a keyframe is a candidate too."""
+    K = [0, 5, 10]
+    got = [oracle.rskm_select(1, 2, 10, K, d) for d in range(3)]
+    assert sorted(got) == K
+    got = [oracle.rskm_select(1, 2, 12, K, d) for d in range(4)]
+    assert sorted(got) == [0, 5, 10, 12]
+    assert oracle.rskm_select(5, 2, 12, K, 0) == 0          # word 0: the oldest keyframe
+
+
+def test_rskm_long_run_share_of_the_current_frame():
+    """Over t_opt |K| m iterations with every draw residue equally often, the current frame's
+    share is 1/t_opt + (1 - 1/t_opt) / |K| (the two cases of Eq. 13 mixed)."""
+    K, t_opt, m = [0, 3, 6, 9], 3, 5
+    n = t_opt * len(K) * m
+    draws = np.arange(n)                                     # residues mod |K| equally often
+    picks = [oracle.rskm_select(k, t_opt, 9, K, draws[k]) for k in range(n)]
+    share = Fraction(sum(p == 9 for p in picks), n)
+    assert share >= Fraction(1, t_opt)
+    # every non-multiple iteration draws one of |K| frames; with k running over whole cycles
+    # of lcm(t_opt, |K|) the residues are equally frequent among them
+    assert share == Fraction(1, t_opt) + (1 - Fraction(1, t_opt)) * Fraction(1, len(K))
+
+
+# ------------------------------------------------------ the SLAM loop (Sec. 3.3-3.4)
+def _slam_case(n_frames=3, W=32, H=24):
+    room = synth.make_room()
+    path = synth.smooth_path(n_frames, step_deg=0.8, room=room)
+    frames = [synth.raycast_room(room, synth.camera(W, H, 30.0, T_cw=T)) for T in path]
+    return path, frames, synth.camera(W, H, 30.0, T_cw=path[0]), synth.decoder(4, 4)
+
+
+def test_slam_first_frame_unprojects_every_pixel_and_draws_only_it():
+    """An empty map renders nothing (silhouette 0), so the first frame's expansion adds one
+    Gaussian per pixel with depth; its mapping iterations can only draw the first frame."""
+    path, frames, cam, dec = _slam_case(1)
+    cfg = oracle.SlamConfig(n_track=0, n_map=0, n_init=3)
+    out = oracle.slam(frames, cam, Params(), dec, path[0], synth.rskm_draws(10), synth.feature_bank(2000, 4), cfg)
+    assert out["sizes"] == [int((frames[0].depth > 0).sum())] == [32 * 24]
+    assert out["picks"] == [0, 0, 0]
+
+
+def test_slam_mapping_lowers_the_mapping_loss():
+    """The loop's mapping iterations descend the mapping loss of the frame they map (a sign or
+    wiring error in the update would raise it)."""
+    path, frames, cam, dec = _slam_case(1)
+    bank = synth.feature_bank(2000, 4)
+    loss_after = []
+    for n_init in (0, 8):
+        cfg = oracle.SlamConfig(n_track=0, n_map=0, n_init=n_init)
+        out = oracle.slam(frames, cam, Params(), dec, path[0], synth.rskm_draws(10), bank, cfg)
+        loss_after.append(oracle.step(out["gs"], cam, Params(), frames[0], dec, oracle.MAPPING_SSIM)["total"])
+    assert loss_after[1] < 0.9 * loss_after[0]
+
+
+def test_slam_keyframes_and_draws_with_one_word():
+    """Every draw word 0 (the first candidate) and t_opt = 2: even iterations take the current
+    frame, odd ones the first keyframe, frame 0; with every frame a keyframe that holds for
+    each frame of the sequence; frames without tracking steps keep Eq. 19's prediction."""
+    path, frames, cam, dec = _slam_case(3)
+    cfg = oracle.SlamConfig(n_track=0, n_map=4, n_init=2, t_opt=2, kf_every=1)
+    out = oracle.slam(frames, cam, Params(), dec, path[0], np.zeros(20, np.uint32), synth.feature_bank(3000, 4), cfg)
+    assert out["picks"] == [0, 0] + [1, 0, 1, 0] + [2, 0, 2, 0]
+    np.testing.assert_allclose(out["poses"][1], path[0], atol=1e-12)   # from one pose: that pose
+    np.testing.assert_allclose(out["poses"][2], path[0], atol=1e-12)
+    assert out["sizes"][0] == 32 * 24 and out["sizes"][2] >= out["sizes"][1] >= out["sizes"][0]
