@@ -18,6 +18,14 @@ Parity status per function (pins live in tests/test_oracle_pins.py):
   loss          pinned: textbook softmax-CE, hand-computed L1, median by sorting
   dsr           pinned: hand-sized arrays
   pose_step     pinned: matrix exponential, first Adam step
+  ssim          pinned: identical and constant images (closed form), central differences
+  adam_step     pinned: sign steps from zero moments, written-out moment series
+  expand        pinned: empty render (reprojection), explained frame, 50 x median rule
+  constant_velocity, track_sequence, ate_rmse
+                pinned: constant screw motion, shifted trajectory, wiring without steps
+  rskm_select   pinned: Eq. 13 cases, full cycles of words, long-run share (fractions)
+  slam          pinned: first frame expands every pixel, mapping lowers the loss,
+                draws and poses with constant words and no tracking steps
 """
 from __future__ import annotations
 

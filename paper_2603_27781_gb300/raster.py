@@ -392,9 +392,10 @@ def expand(r: "Renderer", field: Field, targets, feat_init: torch.Tensor, tau_un
 class Tracker:
     """Frame-to-model tracking (Sec. 3.4) against a fixed map on the GPU.  A frame's n_it
     pose-only iterations (tracking loss of Eq. 20-21 with the M_obs mask; Adam on the twist with
-    the C.1 rates, moments reset per frame) replay from one CUDA graph in which each pose step
-    writes the pose the next projection reads; per frame the observation is copied into the
-    graph's input buffers and the start pose is set before the replay."""
+    the C.1 rates, moments reset per frame) are n_it replays of one captured iteration, whose
+    pose step writes the pose the next projection reads and counts Adam's steps on the device;
+    per frame the observation is copied into the graph's input buffers and the start pose is
+    set before the replays."""
 
     def __init__(self, field: Field, cam, dec_W: torch.Tensor, dec_b: torch.Tensor, n_it: int = 40,
                  params: RasterParams = RasterParams(), margin: float = 1.6, lr=TRACKING_LR, use_graph: bool = True):
@@ -411,10 +412,9 @@ class Tracker:
         self.pose = torch.zeros(1, 16, dtype=torch.float32, device=dev)
         self.graph = None
 
-    def _iterations(self):
-        for _ in range(self.n_it):
-            self.r.iteration(self.field, self.tg, self.W, self.b, TRACKING, L.GS_GRAD_POSE, pose_dev=self.pose)
-            self.r.pose_step(self.T, self.adam, 0, lr=self.lr, pose_f32=self.pose)
+    def _iteration(self):
+        self.r.iteration(self.field, self.tg, self.W, self.b, TRACKING, L.GS_GRAD_POSE, pose_dev=self.pose)
+        self.r.pose_step(self.T, self.adam, 0, lr=self.lr, pose_f32=self.pose)
 
     def _start(self, T_init):
         self.T.copy_(torch.as_tensor(np.asarray(T_init, np.float64).reshape(1, 16)))
@@ -432,23 +432,23 @@ class Tracker:
             self.tg["rgb"].copy_(torch.as_tensor(np.ascontiguousarray(frame.rgb, np.float32).reshape(3, -1)))
             self.tg["depth"].copy_(torch.as_tensor(np.ascontiguousarray(frame.depth, np.float32).ravel()))
             self.tg["label"].copy_(torch.as_tensor(np.ascontiguousarray(frame.label, np.uint8).ravel()))
-        if not self.use_graph:
-            self._start(T_init)
-            self._iterations()
-        elif self.graph is None:
+        if self.use_graph and self.graph is None:
             self._start(T_init)
             cur = torch.cuda.current_stream()
             side = torch.cuda.Stream()
             side.wait_stream(cur)
             with torch.cuda.stream(side):
-                self._iterations()
+                self._iteration()                    # module loads before the capture
             cur.wait_stream(side)
             self.graph = torch.cuda.CUDAGraph()
             with torch.cuda.graph(self.graph):
-                self._iterations()
-        if self.use_graph:
-            self._start(T_init)
-            self.graph.replay()
+                self._iteration()
+        self._start(T_init)
+        for _ in range(self.n_it):
+            if self.use_graph:
+                self.graph.replay()
+            else:
+                self._iteration()
         T = self.T.cpu().numpy().reshape(4, 4)
         if self.r.status() != 0:
             raise L.GsError("tracking binning", self.r.status())

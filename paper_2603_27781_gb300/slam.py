@@ -112,10 +112,10 @@ class Slam:
 
     def __init__(self, cam, dec_W: torch.Tensor, dec_b: torch.Tensor, n_frames: int, draws: np.ndarray,
                  feat_bank: torch.Tensor, cfg: SlamConfig = SlamConfig(), params: RasterParams = RasterParams(),
-                 gaussian_capacity: Optional[int] = None, track_graph: bool = False, device="cuda"):
+                 gaussian_capacity: Optional[int] = None, graphs: bool = True, device="cuda"):
         dev = torch.device(device)
         self.cam, self.W, self.b, self.cfg, self.params = cam, dec_W, dec_b, cfg, params
-        self.track_graph = track_graph
+        self.graphs = graphs
         self.D, self.K = int(dec_W.shape[1]), int(dec_W.shape[0])
         P = cam.width * cam.height
         cap = int(gaussian_capacity or P * n_frames)
@@ -189,7 +189,7 @@ class Slam:
         else:
             T_pred = constant_velocity(self.est[-1], self.est[-2] if t >= 2 else self.est[-1])
             tracker = Tracker(self.field(), self._at(T_pred), self.W, self.b, n_it=cfg.n_track, params=self.params,
-                              margin=2.0, use_graph=self.track_graph)
+                              margin=2.0, use_graph=self.graphs)
             T = tracker.track(self.kf.targets(slot), T_pred) if cfg.n_track > 0 else T_pred
         self.est.append(T)
         t1 = time.perf_counter()
@@ -205,11 +205,24 @@ class Slam:
             r = self._mapping_renderer(field, max(self.n_kf, slot + 1))
             opt = MappingAdam(field)
             self.sampler.begin(self.n_drawn, n_it, self.n_kf, slot, cfg.t_opt)
-            for _ in range(n_it):
+
+            def iteration():
                 self.sampler.draw()
                 r.iteration(field, self.sampler.targets, self.W, self.b, MAPPING_SSIM, L.GS_GRAD_MAP,
                             pose_dev=self.sampler.pose)
                 opt.step(r, 0)
+            if self.graphs and t > 0:
+                # every iteration is the same launches (the draw counter and Adam's step count
+                # live on the device): capture one, replay it; the first frame ran eagerly, so
+                # every kernel is loaded before any capture
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g):
+                    iteration()
+                for _ in range(n_it):
+                    g.replay()
+            else:
+                for _ in range(n_it):
+                    iteration()
             self.n_drawn += n_it
             if r.status() != 0:
                 raise L.GsError("mapping binning", r.status())
