@@ -63,7 +63,7 @@ extern "C" gs_status gs_render_bwd(const gs_gaussians *g, const gs_projected *pr
     A.bmask = fwd->blend_mask;
     A.bm_stride = bins->capacity / 32 + 1;
     A.order = bins->tile_order;
-    const int np = prm.bwd_np ? prm.bwd_np : default_bwd_np(g->feat_dim);
+    const int np = prm.bwd_np ? prm.bwd_np : (map && prm.bwd_warp ? 1 : default_bwd_np(g->feat_dim));
     const bool half = g->rgb_dtype == GS_F16;
     return map ? dispatch_bwd_map(g->feat_dim, np, half, vt, prm, A, st)
                : dispatch_bwd_pose(g->feat_dim, np, half, vt, prm, A, st);

@@ -142,6 +142,47 @@ def test_launch_shapes_agree(np_):
         C.assert_grad_close(name, b.cpu().numpy(), a.cpu().numpy(), 1e-5)
 
 
+@pytest.mark.parametrize("D,np_", [(16, 1), (16, 2), (32, 1), (32, 2)])
+def test_warp_block_backward_matches_oracle(D, np_):
+    """The map-mode backward as one 32-thread block per pixel group, over a frame and a
+    ragged second view, against the oracle."""
+    gs, cam, room = C.room_case(6000, D, 96, 64, 48.0)
+    cams = [cam, synth.camera(70, 45, 40.0, T_cw=synth.keyframe_loop(8, room=room)[2])]
+    prm_g, prm_o = C.params_pair(bwd_warp_blocks=1, bwd_px_per_thread=np_)
+    C.bwd_compare(gs, cams, prm_g, prm_o)
+
+
+@pytest.mark.parametrize("np_", [1, 2])
+def test_warp_block_backward_agrees_with_the_tile_kernel(np_):
+    """Same frame, same upstream gradients: the per-group blocks give the tile kernel's
+    gradients (f32 and half storage); unsupported shapes are refused."""
+    gs, cam, _ = C.room_case(20000, 16, 330, 190, 165.0)
+    for rgb_dt, feat_dt in ((torch.float32, torch.float32), (torch.float16, torch.bfloat16)):
+        field, r = C.gpu_forward(gs, cam, C.params_pair()[0], rgb_dtype=rgb_dt, feat_dtype=feat_dt)
+        g = C.random_image_grads(r.P, 16, 11)
+        r.g_rgb.copy_(torch.as_tensor(g["rgb"])); r.g_depth.copy_(torch.as_tensor(g["depth"]))
+        r.g_sil.copy_(torch.as_tensor(g["sil"])); r.g_feat.copy_(torch.as_tensor(g["feat"]))
+        outs = []
+        for warp in (0, 1):
+            prm = raster.RasterParams(bwd_px_per_thread=np_, bwd_warp_blocks=warp)
+            r.params, r.prm_c = prm, prm.c()
+            r.backward(field, L.GS_GRAD_MAP | L.GS_GRAD_POSE)
+            outs.append([t.clone() for t in (r.d_means, r.d_quats, r.d_log_scales, r.d_logits, r.d_rgb,
+                                             r.d_feat, r.d_twist)])
+        for name, a, b in zip(("means", "quats", "log_scales", "logits", "rgb", "feat", "twist"), *outs):
+            C.assert_grad_close(name, b.cpu().numpy(), a.cpu().numpy(), 1e-5)
+    for bad in (raster.RasterParams(bwd_px_per_thread=4, bwd_warp_blocks=1),):
+        r.params, r.prm_c = bad, bad.c()
+        with pytest.raises(L.GsError):
+            r.backward(field, L.GS_GRAD_MAP)
+    r.use_blend_mask = False
+    r.params = raster.RasterParams(bwd_warp_blocks=1)
+    r.prm_c = r.params.c()
+    r.forward(field)
+    with pytest.raises(L.GsError):
+        r.backward(field, L.GS_GRAD_MAP)
+
+
 def test_blend_mask_skips_only_non_contributing_splats():
     """The backward with the forward's blend mask equals the full scan."""
     gs, cam, _ = C.room_case(20000, 16, 330, 190, 165.0)
@@ -197,8 +238,9 @@ def test_autotuner_picks_a_supported_shape():
     g = C.random_image_grads(r.P, 16, 6)
     r.g_rgb.copy_(torch.as_tensor(g["rgb"])); r.g_feat.copy_(torch.as_tensor(g["feat"]))
     tuned, t = autotune.tune_blend(r, field, L.GS_GRAD_MAP)
-    assert set(t["fwd"]) == {1, 2, 4} and set(t["bwd"]) == {1, 2, 4}
-    assert tuned.fwd_px_per_thread in t["fwd"] and tuned.bwd_px_per_thread in t["bwd"]
+    assert set(t["fwd"]) == {1, 2, 4} and set(t["bwd"]) == {1, 2, 4, "w1", "w2"}
+    assert tuned.fwd_px_per_thread in t["fwd"]
+    assert (f"w{tuned.bwd_px_per_thread}" if tuned.bwd_warp_blocks else tuned.bwd_px_per_thread) in t["bwd"]
 
 
 def test_render_bwd_multiview_sums_views():
