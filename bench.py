@@ -18,6 +18,7 @@ step).  Prints one JSON line on rank 0.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -47,6 +48,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--form-steps", type=int, default=10)
+    # fixed blend launch shapes "fwd,bwd" (e.g. "2,w2") instead of the autotuner's, for profiling
+    ap.add_argument("--shapes", default=None)
     # smaller scenes for profiling captures only (the benchmark line is the default workload)
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--width", type=int, default=None)
@@ -541,7 +544,13 @@ def run_ours(args, rank, world, local_rank):
     from paper_2603_27781_gb300 import autotune
     r.forward(field)
     r.loss(targets, W, b, w)
-    tuned, tune_ms = autotune.tune_blend(r, field, mode)
+    if args.shapes:
+        f_s, b_s = args.shapes.split(",")
+        tuned = dataclasses.replace(r.params, fwd_px_per_thread=int(f_s), bwd_px_per_thread=int(b_s.lstrip("w")),
+                                    bwd_warp_blocks=int(b_s.startswith("w")))
+        r.params, r.prm_c, tune_ms = tuned, tuned.c(), {}
+    else:
+        tuned, tune_ms = autotune.tune_blend(r, field, mode)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()

@@ -288,9 +288,11 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS) raster_bwd_kernel(ViewTabl
                     const float a = e[p].alpha;
                     const float Tb = __fdividef(T[p], 1.f - a);
                     const float w = a * Tb;
-                    float gx = 0.f;
+                    // g.x as three interleaved partial sums (shorter dependent chain)
+                    float gx3[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-                    for (int ch = 0; ch < NCH; ++ch) gx = fmaf(gch[p][ch], x[ch], gx);
+                    for (int ch = 0; ch < NCH; ++ch) gx3[ch % 3] = fmaf(gch[p][ch], x[ch], gx3[ch % 3]);
+                    const float gx = gx3[0] + gx3[1] + gx3[2];
                     const float da = Tb * (gx - gS[p]);
                     gS[p] = fmaf(a, gx - gS[p], gS[p]);
                     T[p] = Tb;

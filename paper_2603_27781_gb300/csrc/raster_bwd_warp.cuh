@@ -6,7 +6,7 @@
 // longest masked list, and the CTA holds its registers and shared memory until
 // its slowest warp ends.  Here each pixel group (the same 8x4 groups, NP of them
 // per warp) is its own 32-thread block: it builds its own list of the instances
-// its pixels blended (back to front, from the mask words), stages 32 splat
+// its pixels blended (back to front, from the mask words), stages 16 splat
 // records at a time in its own shared memory, runs the same per-pixel recurrence
 // and the same deferred contraction of the alpha-T weighted terms, and adds its
 // sums to the per-Gaussian accumulators with vector atomics.  Nothing waits on
@@ -50,7 +50,10 @@ __device__ __forceinline__ void add_deferred(const float (&a)[HW], int64_t item,
     }
 }
 
-template <int D, int NP> constexpr int warp_bwd_min_blocks() { return NP == 1 ? 20 : 14; }
+// Register cap: with one pixel per thread 24 blocks per SM (80 registers at D = 16; shared
+// memory would allow 26); with two, shared memory bounds the blocks at 16, which 127
+// registers still allow.
+template <int D, int NP> constexpr int warp_bwd_min_blocks() { return NP == 1 ? 24 : 16; }
 
 template <int D, int NP, typename RT, typename FT>
 __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP>())
@@ -61,12 +64,12 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP>())
     constexpr int D4 = D / 4;
     constexpr int NCH = 5 + D;
     constexpr int GW = SH::WARPS;  // pixel-group blocks per tile
-    __shared__ SplatGeo s_geo[32];
-    __shared__ float2 s_ext[32];
-    __shared__ float4 s_rgbd[32];
-    __shared__ float4 s_feat[32 * D4];
-    __shared__ uint32_t s_item[32];
-    __shared__ int s_pos[32];
+    constexpr int STAGE = 16;      // splat records staged at a time
+    __shared__ SplatGeo s_geo[STAGE];
+    __shared__ float4 s_rgbd[STAGE];
+    __shared__ float4 s_feat[STAGE * D4];
+    __shared__ uint32_t s_item[STAGE];
+    __shared__ int s_pos[STAGE];
     __shared__ uint32_t s_list[64];
     __shared__ __align__(16) float s_w[LY::SLOTS * LY::WROW];
     __shared__ __align__(16) float s_g[LY::PXW * LY::GROW];
@@ -85,10 +88,6 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP>())
     const uint32_t start = A.ranges[2 * gt];
     const int64_t voff = (int64_t)v * vt.n;
     const int64_t P = A.P;
-    int bx0, by0;
-    SH::warp_origin(grp, bx0, by0);
-    const float bcx = (float)(tx * kTile + bx0) + 0.5f * SH::BW, bcy = (float)(ty * kTile + by0) + 0.5f * SH::BH;
-    const float hx = 0.5f * (SH::BW - 1), hy = 0.5f * (SH::BH - 1);
 
     float gch[NP][NCH], T[NP], gS[NP], pxc[NP], pyc[NP];
     int last[NP];
@@ -182,10 +181,10 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP>())
     };
 
     const float inv_l2e = 1.f / kLog2e;
+    // Every listed splat was blended by a pixel of the group, so no box culling is needed.
     auto process = [&](const int k) {
         const int pos = s_pos[k];
         const SplatGeo s = s_geo[k];
-        if (!reaches_box(s.u, s.v, s_ext[k], bcx, bcy, hx, hy)) return;
         PairEval e[NP];
         bool contrib[NP], any = false;
 #pragma unroll
@@ -214,9 +213,11 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP>())
                 if (!contrib[p]) continue;
                 const float a = e[p].alpha;
                 const float Tb = __fdividef(T[p], 1.f - a);
-                float gx = 0.f;
+                // g.x as three interleaved partial sums (shorter dependent chain)
+                float gx3[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-                for (int ch = 0; ch < NCH; ++ch) gx = fmaf(gch[p][ch], x[ch], gx);
+                for (int ch = 0; ch < NCH; ++ch) gx3[ch % 3] = fmaf(gch[p][ch], x[ch], gx3[ch % 3]);
+                const float gx = gx3[0] + gx3[1] + gx3[2];
                 const float da = Tb * (gx - gS[p]);
                 gS[p] = fmaf(a, gx - gS[p], gS[p]);
                 T[p] = Tb;
@@ -250,16 +251,16 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP>())
         if (n_slot == LY::SLOTS) flush();
     };
 
-    // stages list entries [0, cnt) (instance indices, back to front) and walks them
-    auto stage_and_process = [&](const int cnt) {
+    // stages list entries [off, off + cnt) (instance indices, back to front; cnt <= STAGE)
+    // and walks them
+    auto stage_and_process = [&](const int off, const int cnt) {
         if (lane < cnt) {
-            const uint32_t ii = s_list[lane];
+            const uint32_t ii = s_list[off + lane];
             const uint32_t item = A.vals[ii];
             const int64_t g = (int64_t)item - voff;
             const float4 a = A.uvdo[item];
             const float4 c = A.conic[item];
             s_geo[lane] = make_geo(a, A.uv_lo[item], c);
-            s_ext[lane] = splat_extent(c, a.w, prm.alpha_min);
             s_rgbd[lane] = load_rgbd(rgb, g, a.z);
 #pragma unroll
             for (int q = 0; q < D4; ++q) s_feat[lane * D4 + q] = load_feat4(feat, g * D + 4 * q);
@@ -289,13 +290,14 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP>())
         n += __popc(m);
         __syncwarp();
         if (n >= 32) {
-            stage_and_process(32);
+#pragma unroll
+            for (int off = 0; off < 32; off += STAGE) stage_and_process(off, STAGE);
             if (lane < n - 32) s_list[lane] = s_list[32 + lane];
             __syncwarp();
             n -= 32;
         }
     }
-    if (n > 0) stage_and_process(n);
+    for (int off = 0; off < n; off += STAGE) stage_and_process(off, min(STAGE, n - off));
     if (n_slot > 0) flush();
 }
 

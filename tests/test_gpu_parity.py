@@ -148,8 +148,8 @@ def test_warp_block_backward_matches_oracle(D, np_):
     ragged second view, against the oracle."""
     gs, cam, room = C.room_case(6000, D, 96, 64, 48.0)
     cams = [cam, synth.camera(70, 45, 40.0, T_cw=synth.keyframe_loop(8, room=room)[2])]
-    prm_g, prm_o = C.params_pair(bwd_warp_blocks=1, bwd_px_per_thread=np_)
-    C.bwd_compare(gs, cams, prm_g, prm_o)
+    prm_g = raster.RasterParams(bwd_warp_blocks=1, bwd_px_per_thread=np_)
+    C.bwd_compare(gs, cams, prm_g, C.params_pair()[1])
 
 
 @pytest.mark.parametrize("np_", [1, 2])
