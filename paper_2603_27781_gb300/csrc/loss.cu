@@ -186,7 +186,8 @@ __global__ void __launch_bounds__(LossShape<D, KC>::NT) loss_kernel(
     double *part_d, float *mask_out, float *median_out) {
     using SH = LossShape<D, KC>;
     constexpr int NT = SH::NT, DD = SH::DD, EPL = SH::EPL;
-    __shared__ float s_W[KC * DD], s_b[KC];
+    __shared__ __align__(16) float s_W[KC * DD];
+    __shared__ float s_b[KC];
     __shared__ float s_dW[KC * DD + KC];
     __shared__ float s_dz[SH::WARPS][32][KC + 1];
     __shared__ __align__(16) float s_f[SH::WARPS][32][SH::FROW];
@@ -250,35 +251,66 @@ __global__ void __launch_bounds__(LossShape<D, KC>::NT) loss_kernel(
 #pragma unroll
             for (int d = 0; d < DD; ++d) gf[d] = 0.f;
             if (lab != 255 && lab < K) {
+                // z = W f + b, each row read as float4 and summed in four partial sums
                 float z[KC];
                 float zmax = -INFINITY;
 #pragma unroll
                 for (int k = 0; k < KC; ++k) {
                     z[k] = 0.f;
                     if (k < K) {
-                        float s = s_b[k];
+                        float a[4] = {0.f, 0.f, 0.f, 0.f};
+                        if constexpr (D % 4 == 0) {
+                            const float4 *wr = reinterpret_cast<const float4 *>(s_W + k * D);
 #pragma unroll
-                        for (int d = 0; d < D; ++d) s = fmaf(s_W[k * D + d], f[d], s);
+                            for (int q = 0; q < D / 4; ++q) {
+                                const float4 w4 = wr[q];
+                                a[0] = fmaf(w4.x, f[4 * q], a[0]);
+                                a[1] = fmaf(w4.y, f[4 * q + 1], a[1]);
+                                a[2] = fmaf(w4.z, f[4 * q + 2], a[2]);
+                                a[3] = fmaf(w4.w, f[4 * q + 3], a[3]);
+                            }
+                        } else {
+#pragma unroll
+                            for (int d = 0; d < D; ++d) a[d & 3] = fmaf(s_W[k * D + d], f[d], a[d & 3]);
+                        }
+                        const float s = s_b[k] + ((a[0] + a[1]) + (a[2] + a[3]));
                         z[k] = s;
                         zmax = fmaxf(zmax, s);
                     }
                 }
-                float se = 0.f, zl = 0.f;
+                // softmax from one exponential per class: p_k = e_k / sum_j e_j, e_k = exp(z_k - zmax)
+                float e[KC], se = 0.f, zl = 0.f;
 #pragma unroll
-                for (int k = 0; k < KC; ++k)
+                for (int k = 0; k < KC; ++k) {
+                    e[k] = 0.f;
                     if (k < K) {
-                        se += expf(z[k] - zmax);
+                        e[k] = expf(z[k] - zmax);
+                        se += e[k];
                         if (k == lab) zl = z[k];
                     }
+                }
                 const float lse = zmax + logf(se);
                 ls += m * (lse - zl);
                 const float scale = m * lp.sem * invP;
+                const float inv_se = 1.f / se;
 #pragma unroll
                 for (int k = 0; k < KC; ++k) {
                     if (k < K) {
-                        dz[k] = scale * (expf(z[k] - lse) - (k == lab ? 1.f : 0.f));
+                        dz[k] = scale * (e[k] * inv_se - (k == lab ? 1.f : 0.f));
+                        if constexpr (D % 4 == 0) {
+                            const float4 *wr = reinterpret_cast<const float4 *>(s_W + k * D);
 #pragma unroll
-                        for (int d = 0; d < D; ++d) gf[d] = fmaf(s_W[k * D + d], dz[k], gf[d]);
+                            for (int q = 0; q < D / 4; ++q) {
+                                const float4 w4 = wr[q];
+                                gf[4 * q] = fmaf(w4.x, dz[k], gf[4 * q]);
+                                gf[4 * q + 1] = fmaf(w4.y, dz[k], gf[4 * q + 1]);
+                                gf[4 * q + 2] = fmaf(w4.z, dz[k], gf[4 * q + 2]);
+                                gf[4 * q + 3] = fmaf(w4.w, dz[k], gf[4 * q + 3]);
+                            }
+                        } else {
+#pragma unroll
+                            for (int d = 0; d < D; ++d) gf[d] = fmaf(s_W[k * D + d], dz[k], gf[d]);
+                        }
                     }
                 }
             }
@@ -609,11 +641,23 @@ __global__ void pose_step_kernel(int n_views, const double *grad, double *Tst, d
     }
 }
 
-int loss_blocks_x(const ViewTable &vt) {
+// Blocks per view: at most one resident wave of the loss kernel over all views (resident
+// = blocks per SM x SMs of the current device; 0 = unknown), and at most kLossBlocks in all.
+int loss_blocks_x(const ViewTable &vt, int resident = 0) {
     int64_t maxPv = 0;
     for (int v = 0; v < vt.n_views; ++v) maxPv = std::max<int64_t>(maxPv, (int64_t)vt.W[v] * vt.H[v]);
-    const int per_view = std::max(1, kLossBlocks / vt.n_views);
+    const int total = resident > 0 ? std::min(resident, kLossBlocks) : kLossBlocks;
+    const int per_view = std::max(1, total / vt.n_views);
     return (int)std::max<int64_t>(1, std::min<int64_t>((maxPv + 255) / 256, per_view));
+}
+
+template <typename K>
+int resident_blocks(K kernel, int threads) {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess) return 0;
+    return per_sm * sms;
 }
 
 template <int D>
@@ -621,7 +665,8 @@ gs_status launch_loss(const ViewTable &vt, const LossP &lp, const gs_images *img
                       const float *W, const float *b, int64_t P, const uint32_t *mh, gs_image_grads_out *g,
                       float *part_f, double *part_d, float *dW, float *db, double *loss_out, float *mask_out,
                       float *median_out, cudaStream_t st) {
-    const int bx = loss_blocks_x(vt);
+    const int bx = loss_blocks_x(vt, lp.K <= 8 ? resident_blocks(loss_kernel<D, 8>, LossShape<D, 8>::NT)
+                                              : resident_blocks(loss_kernel<D, kMaxK>, LossShape<D, kMaxK>::NT));
     dim3 grid(bx, vt.n_views);
     if (lp.K <= 8)
         loss_kernel<D, 8><<<grid, LossShape<D, 8>::NT, 0, st>>>(

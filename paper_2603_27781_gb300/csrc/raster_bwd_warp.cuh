@@ -240,14 +240,16 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP>())
         const uint32_t item = s_item[k];
         if (lane == 0) s_slot_item[n_slot] = item;
         ++n_slot;
-        // lane i ends with the warp's sum of value (i mod 8): centre (0, 1), conic (2-4), opacity (5)
+        // lane i ends with the warp's sum of value (i mod 8): centre (0, 1), conic (2-4),
+        // opacity (5); lanes 0-5 add them in one warp-wide reduction instruction (two
+        // 16-byte targets: acc_uvod (u, v, opacity) and acc_conic (A, B, C))
         const float r = warp_transpose_reduce<8>(val, lane);
-        const float r1 = __shfl_sync(0xffffffffu, r, 1), r3 = __shfl_sync(0xffffffffu, r, 3);
-        const float r4 = __shfl_sync(0xffffffffu, r, 4), r5 = __shfl_sync(0xffffffffu, r, 5);
-        if (lane == 0 && (r != 0.f || r1 != 0.f || r5 != 0.f))
-            atomicAdd(A.acc_uvod + item, make_float4(r, r1, r5, 0.f));
-        if (lane == 2 && (r != 0.f || r3 != 0.f || r4 != 0.f))
-            atomicAdd(A.acc_conic + item, make_float4(r, r3, r4, 0.f));
+        if (lane < 6 && r != 0.f) {
+            float *dst = lane == 5 ? reinterpret_cast<float *>(A.acc_uvod + item) + 2
+                         : lane < 2 ? reinterpret_cast<float *>(A.acc_uvod + item) + lane
+                                    : reinterpret_cast<float *>(A.acc_conic + item) + (lane - 2);
+            atomicAdd(dst, r);
+        }
         if (n_slot == LY::SLOTS) flush();
     };
 
