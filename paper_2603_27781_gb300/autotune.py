@@ -18,7 +18,7 @@ from . import _lib as L
 from .raster import RasterParams, Renderer
 
 CANDIDATES = (1, 2, 4)
-WARP_CANDIDATES = (1, 2)   # map-mode backward as one block per pixel group (bwd_warp_blocks = 1)
+WARP_CANDIDATES = (1, 2)   # map-mode backward as one block per pixel group (bwd_blocks = 1)
 
 
 def _time(fn, reps: int, stream) -> float:
@@ -55,9 +55,10 @@ def tune_blend(r: Renderer, field, grad_mode: int = L.GS_GRAD_MAP, reps: int = 5
     best_f = min(timings["fwd"], key=timings["fwd"].get)
     r.prm_c = dataclasses.replace(base, fwd_px_per_thread=best_f).c()
     r.render_fwd(field)
-    shapes = {np_: dict(bwd_px_per_thread=np_, bwd_warp_blocks=0) for np_ in CANDIDATES}
+    shapes = {np_: dict(bwd_px_per_thread=np_, bwd_blocks=L.GS_BWD_BLOCKS_TILE) for np_ in CANDIDATES}
     if grad_mode & L.GS_GRAD_MAP:
-        shapes.update({f"w{np_}": dict(bwd_px_per_thread=np_, bwd_warp_blocks=1) for np_ in WARP_CANDIDATES})
+        shapes.update({f"w{np_}": dict(bwd_px_per_thread=np_, bwd_blocks=L.GS_BWD_BLOCKS_GROUP)
+                       for np_ in WARP_CANDIDATES})
     for key, shape in shapes.items():
         r.prm_c = dataclasses.replace(base, fwd_px_per_thread=best_f, **shape).c()
         try:

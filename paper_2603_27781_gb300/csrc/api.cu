@@ -56,8 +56,9 @@ bool make_params(const gs_raster_params *p, Params *out) {
     if (!np_ok(p->fwd_px_per_thread) || !np_ok(p->bwd_px_per_thread)) return false;
     out->fwd_np = p->fwd_px_per_thread;
     out->bwd_np = p->bwd_px_per_thread;
-    if (p->bwd_warp_blocks != 0 && p->bwd_warp_blocks != 1) return false;
-    out->bwd_warp = p->bwd_warp_blocks;
+    if (p->bwd_blocks < GS_BWD_BLOCKS_DEFAULT || p->bwd_blocks > GS_BWD_BLOCKS_TILE) return false;
+    out->bwd_blocks = p->bwd_blocks;
+    out->bwd_warp = false;
     return true;
 }
 

@@ -34,7 +34,8 @@ struct Params {
     float alpha_min, alpha_max, T_min, z_near, lowpass, radius_sigma;
     float bg[3];
     int fwd_np, bwd_np;  // pixels per thread of the blend kernels (0 = default for the feature dim)
-    int bwd_warp;        // map-mode backward as one 32-thread block per pixel group
+    int bwd_blocks;      // map-mode backward block shape (GS_BWD_BLOCKS_*)
+    bool bwd_warp;       // resolved: map-mode backward as one 32-thread block per pixel group
 };
 
 // Default pixels per thread of the blend kernels for a feature dimension.

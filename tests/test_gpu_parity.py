@@ -148,7 +148,7 @@ def test_warp_block_backward_matches_oracle(D, np_):
     ragged second view, against the oracle."""
     gs, cam, room = C.room_case(6000, D, 96, 64, 48.0)
     cams = [cam, synth.camera(70, 45, 40.0, T_cw=synth.keyframe_loop(8, room=room)[2])]
-    prm_g = raster.RasterParams(bwd_warp_blocks=1, bwd_px_per_thread=np_)
+    prm_g = raster.RasterParams(bwd_blocks=L.GS_BWD_BLOCKS_GROUP, bwd_px_per_thread=np_)
     C.bwd_compare(gs, cams, prm_g, C.params_pair()[1])
 
 
@@ -163,20 +163,22 @@ def test_warp_block_backward_agrees_with_the_tile_kernel(np_):
         r.g_rgb.copy_(torch.as_tensor(g["rgb"])); r.g_depth.copy_(torch.as_tensor(g["depth"]))
         r.g_sil.copy_(torch.as_tensor(g["sil"])); r.g_feat.copy_(torch.as_tensor(g["feat"]))
         outs = []
-        for warp in (0, 1):
-            prm = raster.RasterParams(bwd_px_per_thread=np_, bwd_warp_blocks=warp)
+        for blocks in (L.GS_BWD_BLOCKS_TILE, L.GS_BWD_BLOCKS_GROUP, L.GS_BWD_BLOCKS_DEFAULT):
+            prm = raster.RasterParams(bwd_px_per_thread=np_, bwd_blocks=blocks)
             r.params, r.prm_c = prm, prm.c()
             r.backward(field, L.GS_GRAD_MAP | L.GS_GRAD_POSE)
             outs.append([t.clone() for t in (r.d_means, r.d_quats, r.d_log_scales, r.d_logits, r.d_rgb,
                                              r.d_feat, r.d_twist)])
-        for name, a, b in zip(("means", "quats", "log_scales", "logits", "rgb", "feat", "twist"), *outs):
-            C.assert_grad_close(name, b.cpu().numpy(), a.cpu().numpy(), 1e-5)
-    for bad in (raster.RasterParams(bwd_px_per_thread=4, bwd_warp_blocks=1),):
+        for other in outs[1:]:
+            for name, a, b in zip(("means", "quats", "log_scales", "logits", "rgb", "feat", "twist"), outs[0],
+                                  other):
+                C.assert_grad_close(name, b.cpu().numpy(), a.cpu().numpy(), 1e-5)
+    for bad in (raster.RasterParams(bwd_px_per_thread=4, bwd_blocks=L.GS_BWD_BLOCKS_GROUP),):
         r.params, r.prm_c = bad, bad.c()
         with pytest.raises(L.GsError):
             r.backward(field, L.GS_GRAD_MAP)
     r.use_blend_mask = False
-    r.params = raster.RasterParams(bwd_warp_blocks=1)
+    r.params = raster.RasterParams(bwd_blocks=L.GS_BWD_BLOCKS_GROUP)
     r.prm_c = r.params.c()
     r.forward(field)
     with pytest.raises(L.GsError):
@@ -240,7 +242,8 @@ def test_autotuner_picks_a_supported_shape():
     tuned, t = autotune.tune_blend(r, field, L.GS_GRAD_MAP)
     assert set(t["fwd"]) == {1, 2, 4} and set(t["bwd"]) == {1, 2, 4, "w1", "w2"}
     assert tuned.fwd_px_per_thread in t["fwd"]
-    assert (f"w{tuned.bwd_px_per_thread}" if tuned.bwd_warp_blocks else tuned.bwd_px_per_thread) in t["bwd"]
+    assert (f"w{tuned.bwd_px_per_thread}" if tuned.bwd_blocks == L.GS_BWD_BLOCKS_GROUP
+            else tuned.bwd_px_per_thread) in t["bwd"]
 
 
 def test_render_bwd_multiview_sums_views():
