@@ -85,14 +85,14 @@ typedef struct {
      * per thread of gs_render_fwd / gs_render_bwd, 1, 2 or 4 (2 and 4 only for
      * feature dims 16 and 32; 4 only up to 16); 0 = the library's default. */
     int32_t fwd_px_per_thread, bwd_px_per_thread;
-    /* Block shape of gs_render_bwd in map mode (results do not depend on it
-     * beyond the order of float atomics): GS_BWD_BLOCKS_GROUP = one 32-thread
-     * block per 8x4 pixel group (bwd_px_per_thread 1, or 2 for 16x4 bands; 0
-     * means 1), each adding its own sums with atomics, for feature dims 16 and
-     * 32 with the forward's blend mask (else GS_ERR_UNSUPPORTED);
-     * GS_BWD_BLOCKS_TILE = one block per 16x16 tile whose warps combine each
-     * splat's sums in shared memory; GS_BWD_BLOCKS_DEFAULT (0) = per pixel group
-     * where that form applies, else per tile.  Pose-only mode is per tile. */
+    /* Block shape of gs_render_bwd (results do not depend on it beyond the
+     * order of float atomics): GS_BWD_BLOCKS_GROUP = one 32-thread block per
+     * 8x4 pixel group (bwd_px_per_thread 1, or 2 for 16x4 bands; 0 means 1),
+     * each adding its own sums with atomics, for feature dims 16 and 32 with
+     * the forward's blend mask (else GS_ERR_UNSUPPORTED); GS_BWD_BLOCKS_TILE =
+     * one block per 16x16 tile whose warps combine each splat's sums in shared
+     * memory; GS_BWD_BLOCKS_DEFAULT (0) = per pixel group where that form
+     * applies, else per tile. */
     int32_t bwd_blocks;
 } gs_raster_params;
 

@@ -63,12 +63,12 @@ extern "C" gs_status gs_render_bwd(const gs_gaussians *g, const gs_projected *pr
     A.bmask = fwd->blend_mask;
     A.bm_stride = bins->capacity / 32 + 1;
     A.order = bins->tile_order;
-    // block shape: per pixel group where that form applies (map mode, D 16 or 32, the
-    // blend mask, 1 or 2 pixels per thread), unless the caller asks for one
+    // block shape: per pixel group where that form applies (D 16 or 32, the blend mask,
+    // 1 or 2 pixels per thread), unless the caller asks for one
     const int D = g->feat_dim;
-    const bool group_ok = map && (D == 16 || D == 32) && A.bmask && prm.bwd_np <= 2;
+    const bool group_ok = (D == 16 || D == 32) && A.bmask && prm.bwd_np <= 2;
     Params pr = prm;
-    pr.bwd_warp = map && (prm.bwd_blocks == GS_BWD_BLOCKS_GROUP || (prm.bwd_blocks == GS_BWD_BLOCKS_DEFAULT && group_ok));
+    pr.bwd_warp = prm.bwd_blocks == GS_BWD_BLOCKS_GROUP || (prm.bwd_blocks == GS_BWD_BLOCKS_DEFAULT && group_ok);
     const int np = prm.bwd_np ? prm.bwd_np : (pr.bwd_warp ? 1 : default_bwd_np(D));
     const bool half = g->rgb_dtype == GS_F16;
     return map ? dispatch_bwd_map(D, np, half, vt, pr, A, st) : dispatch_bwd_pose(D, np, half, vt, pr, A, st);

@@ -1,5 +1,7 @@
 // Blend backward (Eq. 4-7 differentiated) with one single-warp block per pixel
-// group: map mode, D >= 16, with the forward's blend mask.
+// group, D 16 or 32, with the forward's blend mask: map mode (every parameter's
+// sums, the weighted terms deferred) and pose-only mode (the six sums the
+// projection backward needs for the twist).
 //
 // The tile kernel's eight warps share one staged splat batch and meet at a CTA
 // barrier per batch, so a tile's warps all wait for whichever of them has the
@@ -55,12 +57,12 @@ __device__ __forceinline__ void add_deferred(const float (&a)[HW], int64_t item,
 // registers still allow.
 template <int D, int NP> constexpr int warp_bwd_min_blocks() { return NP == 1 ? 24 : 16; }
 
-template <int D, int NP, typename RT, typename FT>
+template <int D, int NP, bool MAP, typename RT, typename FT>
 __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP>())
     raster_bwd_warp_kernel(ViewTable vt, Params prm, BwdArgs A) {
-    using LY = BwdLayout<D, NP, true>;
+    using LY = BwdLayout<D, NP, MAP>;
     using SH = Shape<NP>;
-    static_assert(LY::DEFER, "the warp-block backward is the deferred map-mode form");
+    static_assert(!MAP || LY::DEFER, "the map-mode warp-block backward is the deferred form");
     constexpr int D4 = D / 4;
     constexpr int NCH = 5 + D;
     constexpr int GW = SH::WARPS;  // pixel-group blocks per tile
@@ -71,9 +73,9 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP>())
     __shared__ uint32_t s_item[STAGE];
     __shared__ int s_pos[STAGE];
     __shared__ uint32_t s_list[64];
-    __shared__ __align__(16) float s_w[LY::SLOTS * LY::WROW];
-    __shared__ __align__(16) float s_g[LY::PXW * LY::GROW];
-    __shared__ uint32_t s_slot_item[LY::SLOTS];
+    __shared__ __align__(16) float s_w[MAP ? LY::SLOTS * LY::WROW : 4];
+    __shared__ __align__(16) float s_g[MAP ? LY::PXW * LY::GROW : 4];
+    __shared__ uint32_t s_slot_item[MAP ? LY::SLOTS : 1];
     const RT *rgb = static_cast<const RT *>(A.rgb);
     const FT *feat = static_cast<const FT *>(A.feat);
 
@@ -122,7 +124,7 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP>())
     if (wmax == 0) return;  // no pixel of the group blended anything (warp-uniform)
     // the group's pixel p * 32 + lane: gradients of depth, r, g, b, features
 #pragma unroll
-    for (int p = 0; p < NP; ++p) {
+    for (int p = 0; p < (MAP ? NP : 0); ++p) {
         float term[LY::NW];
         term[0] = gch[p][3];
         term[1] = gch[p][0];
@@ -141,6 +143,7 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP>())
     // lane (j, h) contracts slot j's weights with terms [h HW, (h + 1) HW) of the
     // group's gradients and adds the sums to splat j's accumulators
     auto flush = [&]() {
+        if constexpr (!MAP) return;
         __syncwarp();
         const int j = lane & (LY::SLOTS - 1), h = lane >> 4;
         const float4 *wr = reinterpret_cast<const float4 *>(s_w + j * LY::WROW);
@@ -229,28 +232,34 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP>())
                     val[2] += -0.5f * dx * dx * dpow;
                     val[3] += -dx * dy * dpow;
                     val[4] += -0.5f * dy * dy * dpow;
-                    val[5] += e[p].G * da;
+                    if (MAP) val[5] += e[p].G * da;
                 }
-                wv[p] = a * Tb;
+                if (MAP) wv[p] = a * Tb;
+                else val[5] = fmaf(a * Tb, gch[p][3], val[5]);  // pose mode: the depth term
             }
         }
-        float *wr = s_w + n_slot * LY::WROW;
-#pragma unroll
-        for (int p = 0; p < NP; ++p) wr[p * 32 + lane] = wv[p];
         const uint32_t item = s_item[k];
-        if (lane == 0) s_slot_item[n_slot] = item;
-        ++n_slot;
-        // lane i ends with the warp's sum of value (i mod 8): centre (0, 1), conic (2-4),
-        // opacity (5); lanes 0-5 add them in one warp-wide reduction instruction (two
-        // 16-byte targets: acc_uvod (u, v, opacity) and acc_conic (A, B, C))
+        if constexpr (MAP) {
+            float *wr = s_w + n_slot * LY::WROW;
+#pragma unroll
+            for (int p = 0; p < NP; ++p) wr[p * 32 + lane] = wv[p];
+            if (lane == 0) s_slot_item[n_slot] = item;
+            ++n_slot;
+        }
+        // lane i ends with the warp's sum of value (i mod 8): centre (0, 1), conic (2-4), and
+        // opacity (map mode) or depth (pose mode) (5); lanes 0-5 add them in one warp-wide
+        // reduction instruction (two 16-byte targets: acc_uvod (u, v, opacity, depth) and
+        // acc_conic (A, B, C))
         const float r = warp_transpose_reduce<8>(val, lane);
         if (lane < 6 && r != 0.f) {
-            float *dst = lane == 5 ? reinterpret_cast<float *>(A.acc_uvod + item) + 2
+            float *dst = lane == 5 ? reinterpret_cast<float *>(A.acc_uvod + item) + (MAP ? 2 : 3)
                          : lane < 2 ? reinterpret_cast<float *>(A.acc_uvod + item) + lane
                                     : reinterpret_cast<float *>(A.acc_conic + item) + (lane - 2);
             atomicAdd(dst, r);
         }
-        if (n_slot == LY::SLOTS) flush();
+        if constexpr (MAP) {
+            if (n_slot == LY::SLOTS) flush();
+        }
     };
 
     // stages list entries [off, off + cnt) (instance indices, back to front; cnt <= STAGE)
@@ -300,31 +309,34 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP>())
         }
     }
     for (int off = 0; off < n; off += STAGE) stage_and_process(off, min(STAGE, n - off));
-    if (n_slot > 0) flush();
+    if constexpr (MAP) {
+        if (n_slot > 0) flush();
+    }
 }
 
-template <int D, int NP, typename RT, typename FT>
+template <int D, int NP, bool MAP, typename RT, typename FT>
 gs_status launch_bwd_warp(const ViewTable &vt, const Params &prm, const BwdArgs &A, cudaStream_t st) {
     const int n_tiles = vt.tile_off[vt.n_views];
-    raster_bwd_warp_kernel<D, NP, RT, FT><<<n_tiles * Shape<NP>::WARPS, 32, 0, st>>>(vt, prm, A);
+    raster_bwd_warp_kernel<D, NP, MAP, RT, FT><<<n_tiles * Shape<NP>::WARPS, 32, 0, st>>>(vt, prm, A);
     return last_launch();
 }
 
-// The warp-block form: map mode, D 16 or 32, 1 or 2 pixels per thread, blend mask present.
-inline gs_status dispatch_bwd_warp(int D, int np, bool half, const ViewTable &vt, const Params &prm,
-                                   const BwdArgs &A, cudaStream_t st) {
+// The warp-block form: D 16 or 32, 1 or 2 pixels per thread, blend mask present.
+template <bool MAP>
+gs_status dispatch_bwd_warp(int D, int np, bool half, const ViewTable &vt, const Params &prm, const BwdArgs &A,
+                            cudaStream_t st) {
     if (!A.bmask) return GS_ERR_UNSUPPORTED;
     if (half) {
-        if (D == 16 && np == 1) return launch_bwd_warp<16, 1, __half, __nv_bfloat16>(vt, prm, A, st);
-        if (D == 16 && np == 2) return launch_bwd_warp<16, 2, __half, __nv_bfloat16>(vt, prm, A, st);
-        if (D == 32 && np == 1) return launch_bwd_warp<32, 1, __half, __nv_bfloat16>(vt, prm, A, st);
-        if (D == 32 && np == 2) return launch_bwd_warp<32, 2, __half, __nv_bfloat16>(vt, prm, A, st);
+        if (D == 16 && np == 1) return launch_bwd_warp<16, 1, MAP, __half, __nv_bfloat16>(vt, prm, A, st);
+        if (D == 16 && np == 2) return launch_bwd_warp<16, 2, MAP, __half, __nv_bfloat16>(vt, prm, A, st);
+        if (D == 32 && np == 1) return launch_bwd_warp<32, 1, MAP, __half, __nv_bfloat16>(vt, prm, A, st);
+        if (D == 32 && np == 2) return launch_bwd_warp<32, 2, MAP, __half, __nv_bfloat16>(vt, prm, A, st);
         return GS_ERR_UNSUPPORTED;
     }
-    if (D == 16 && np == 1) return launch_bwd_warp<16, 1, float, float>(vt, prm, A, st);
-    if (D == 16 && np == 2) return launch_bwd_warp<16, 2, float, float>(vt, prm, A, st);
-    if (D == 32 && np == 1) return launch_bwd_warp<32, 1, float, float>(vt, prm, A, st);
-    if (D == 32 && np == 2) return launch_bwd_warp<32, 2, float, float>(vt, prm, A, st);
+    if (D == 16 && np == 1) return launch_bwd_warp<16, 1, MAP, float, float>(vt, prm, A, st);
+    if (D == 16 && np == 2) return launch_bwd_warp<16, 2, MAP, float, float>(vt, prm, A, st);
+    if (D == 32 && np == 1) return launch_bwd_warp<32, 1, MAP, float, float>(vt, prm, A, st);
+    if (D == 32 && np == 2) return launch_bwd_warp<32, 2, MAP, float, float>(vt, prm, A, st);
     return GS_ERR_UNSUPPORTED;
 }
 

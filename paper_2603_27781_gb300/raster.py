@@ -123,6 +123,7 @@ class Renderer:
     def __init__(self, n: int, cams: Sequence, feat_dim: int, capacity: int, device="cuda",
                  params: RasterParams = RasterParams(), n_classes: int = 0):
         self.n, self.feat_dim, self.capacity = int(n), int(feat_dim), int(capacity)
+        self.n_cap = self.n            # Gaussians the per-Gaussian buffers hold (set_n picks n <= n_cap)
         self.params = params
         self.device = torch.device(device)
         self.set_cameras(cams)
@@ -177,6 +178,34 @@ class Renderer:
         self.d_dec_W = torch.zeros(K, max(D, 1), dtype=f32, device=dev)
         self.d_dec_b = torch.zeros(K, dtype=f32, device=dev)
         self.prm_c = params.c()
+
+    def set_n(self, n: int):
+        """Serves a field of n <= n_cap Gaussians with the buffers already allocated (every
+        per-Gaussian buffer keeps its n_cap rows; the calls use the first n)."""
+        if not 0 <= n <= self.n_cap:
+            raise ValueError(f"field of {n} Gaussians exceeds the renderer's {self.n_cap}")
+        self.n = int(n)
+
+    def ensure_capacity(self, need: int, growth: float = 1.5):
+        """Grows the instance capacity (keys, values, blend mask, workspace) to hold `need`
+        (tile, splat) instances; a no-op when it already does."""
+        if need <= self.capacity:
+            return
+        cap = int(max(need, self.capacity * growth))
+        dev = self.device
+        self.capacity = cap
+        self.keys = torch.zeros(cap, dtype=torch.int64, device=dev)
+        self.vals = torch.zeros(cap, dtype=torch.int32, device=dev)
+        self.blend_mask = torch.zeros(8 * (cap // 32 + 1), dtype=torch.int32, device=dev)
+        ws_bytes = L.library().gs_workspace_size(self.n_cap, self.n_views, self.cams_c, cap, self.feat_dim)
+        if ws_bytes == 0:
+            raise ValueError("invalid renderer configuration (workspace size 0)")
+        self.ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+
+    def instances_needed(self, field: Field, pose_dev: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Projects the field and returns the (tile, splat) instance count on the device."""
+        self.project(field, pose_dev)
+        return self.touched[: self.n_views * field.n].sum(dtype=torch.int64)
 
     # ------------------------------------------------------------ geometry
     def set_cameras(self, cams):
@@ -339,12 +368,20 @@ class MappingAdam:
     """Adam state of the field's parameters (gs_adam_step): moments m, v of every group and a
     device step counter, so the update can be part of a captured mapping iteration."""
 
-    def __init__(self, field: Field, lr=MAPPING_LR, betas=(0.9, 0.999), eps=1e-15):
+    def __init__(self, field: Field, lr=MAPPING_LR, betas=(0.9, 0.999), eps=1e-15,
+                 moments: Optional[torch.Tensor] = None):
         if field.rgb.dtype != torch.float32 or field.feat.dtype != torch.float32:
             raise ValueError("the mapping update works on f32 parameter storage")
         self.field, self.lr, self.betas, self.eps = field, tuple(lr), betas, eps
         n, D = field.n, field.feat_dim
-        self.moments = torch.zeros(2 * n * (14 + D), dtype=torch.float32, device=field.means.device)
+        size = 2 * n * (14 + D)
+        if moments is None:
+            self.moments = torch.zeros(size, dtype=torch.float32, device=field.means.device)
+        else:                          # a caller's f32 buffer of at least that many values, zeroed here
+            if moments.dtype != torch.float32 or moments.numel() < size:
+                raise ValueError(f"the moments need {size} float32 values")
+            self.moments = moments[:size]
+            self.moments.zero_()
         self.step_ctr = torch.zeros(1, dtype=torch.float64, device=field.means.device)
 
     def step(self, r: "Renderer", step: int = 0, stream=None):
@@ -399,12 +436,14 @@ class Tracker:
     set before the replays."""
 
     def __init__(self, field: Field, cam, dec_W: torch.Tensor, dec_b: torch.Tensor, n_it: int = 40,
-                 params: RasterParams = RasterParams(), margin: float = 1.6, lr=TRACKING_LR, use_graph: bool = True):
+                 params: RasterParams = RasterParams(), margin: float = 1.6, lr=TRACKING_LR, use_graph: bool = True,
+                 renderer: Optional[Renderer] = None):
         dev = field.means.device
         self.field, self.W, self.b, self.n_it, self.lr = field, dec_W, dec_b, n_it, lr
         self.use_graph = use_graph
-        self.r = fit_capacity(field, [cam], field.feat_dim, margin=margin, params=params,
-                              n_classes=int(dec_W.shape[0]), device=dev)
+        # a caller's renderer (one view of cam's size, sized for this field) or a fitted one
+        self.r = renderer if renderer is not None else fit_capacity(
+            field, [cam], field.feat_dim, margin=margin, params=params, n_classes=int(dec_W.shape[0]), device=dev)
         P = cam.width * cam.height
         self.tg = dict(rgb=torch.zeros(3, P, device=dev), depth=torch.zeros(P, device=dev),
                        label=torch.zeros(P, dtype=torch.uint8, device=dev))

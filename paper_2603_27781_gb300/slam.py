@@ -22,8 +22,7 @@ import numpy as np
 import torch
 
 from . import _lib as L
-from .raster import (MAPPING_SSIM, Field, MappingAdam, RasterParams, Renderer, Tracker, _p, _stream, constant_velocity,
-                     fit_capacity)
+from .raster import MAPPING_SSIM, Field, MappingAdam, RasterParams, Renderer, Tracker, _p, _stream, constant_velocity
 
 
 _GROUPS = ("means", "quats", "log_scales", "opacity_logits", "rgb", "feat")
@@ -128,6 +127,10 @@ class Slam:
         self.n = 0
         self.kf = KeyframeStore(n_frames // cfg.kf_every + 2, cam.width, cam.height, dev)
         self.sampler = RskmSampler(self.kf, draws, dev)
+        # one renderer serves tracking, expansion and mapping of every frame: its per-Gaussian
+        # buffers hold the field's capacity, its instance capacity grows when a probe asks
+        self.r = Renderer(cap, [cam], self.D, 4 * P, dev, params, self.K)
+        self.moments = torch.zeros(2 * cap * (14 + self.D), dtype=torch.float32, device=dev)
         self.n_kf = 0
         self.n_drawn = 0
         self.est = []
@@ -141,11 +144,23 @@ class Slam:
     def _at(self, T):
         return dataclasses.replace(self.cam, T_cw=np.asarray(T, np.float64))
 
+    def _fit(self, field: Field, poses=(None,), margin: float = 1.25):
+        """Sets the renderer to the field and grows its instance capacity to the most any of
+        the poses (device f32 [1,16]; None = the renderer's camera) needs, with a margin."""
+        r = self.r
+        r.set_n(field.n)
+        need = None
+        for pose in poses:
+            k = r.instances_needed(field, pose)
+            need = k if need is None else torch.maximum(need, k)
+        r.ensure_capacity(int(int(need.item()) * margin) + 1024)
+
     def _expand(self, T, slot: int):
         """Eq. 11 at pose T: render the field, append one Gaussian per unobserved pixel."""
         field = self.field()
-        r = fit_capacity(field, [self._at(T)], self.D, params=self.params, n_classes=self.K,
-                         device=field.means.device)
+        r = self.r
+        r.set_cameras([self._at(T)])
+        self._fit(field)
         r.forward(field)
         s = self._store
         fm = L.gs_field_mut(self.cap, self.D, _p(s.means), _p(s.quats), _p(s.log_scales), _p(s.opacity_logits),
@@ -164,16 +179,6 @@ class Slam:
         if r.status() != 0:
             raise L.GsError("expansion binning", r.status())
 
-    def _mapping_renderer(self, field: Field, n_cand: int) -> Renderer:
-        """A renderer whose instance capacity fits the field seen from every candidate pose."""
-        probe = Renderer(field.n, [self.cam], self.D, 0, field.means.device, self.params, self.K)
-        need = torch.zeros(1, dtype=torch.int64, device=field.means.device)
-        for slot in range(n_cand):
-            probe.project(field, pose_dev=self.kf.T[slot: slot + 1].float())
-            need = torch.maximum(need, probe.touched.sum(dtype=torch.int64).view(1))
-        cap = max(1024, int(int(need.item()) * 1.25))
-        return Renderer(field.n, [self.cam], self.D, cap, field.means.device, self.params, self.K)
-
     def process(self, frame, T0=None) -> np.ndarray:
         """One frame (host rgb [3,H,W], depth [H,W], label [H,W]); returns its estimated pose.
         T0: the first frame's pose."""
@@ -188,8 +193,10 @@ class Slam:
             T = np.asarray(T0, np.float64)
         else:
             T_pred = constant_velocity(self.est[-1], self.est[-2] if t >= 2 else self.est[-1])
+            self.r.set_cameras([self._at(T_pred)])
+            self._fit(self.field(), margin=1.6)
             tracker = Tracker(self.field(), self._at(T_pred), self.W, self.b, n_it=cfg.n_track, params=self.params,
-                              margin=2.0, use_graph=self.graphs)
+                              use_graph=self.graphs, renderer=self.r)
             T = tracker.track(self.kf.targets(slot), T_pred) if cfg.n_track > 0 else T_pred
         self.est.append(T)
         t1 = time.perf_counter()
@@ -202,8 +209,9 @@ class Slam:
         n_it = cfg.n_init if t == 0 else cfg.n_map
         if n_it > 0:
             field = self.field()
-            r = self._mapping_renderer(field, max(self.n_kf, slot + 1))
-            opt = MappingAdam(field)
+            r = self.r
+            self._fit(field, [self.kf.T[c: c + 1].float() for c in range(max(self.n_kf, slot + 1))])
+            opt = MappingAdam(field, moments=self.moments)
             self.sampler.begin(self.n_drawn, n_it, self.n_kf, slot, cfg.t_opt)
 
             def iteration():

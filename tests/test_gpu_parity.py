@@ -173,6 +173,15 @@ def test_warp_block_backward_agrees_with_the_tile_kernel(np_):
             for name, a, b in zip(("means", "quats", "log_scales", "logits", "rgb", "feat", "twist"), outs[0],
                                   other):
                 C.assert_grad_close(name, b.cpu().numpy(), a.cpu().numpy(), 1e-5)
+        # pose-only mode (tracking): the twist and the splat sums it is reduced from
+        twists = []
+        for blocks in (L.GS_BWD_BLOCKS_TILE, L.GS_BWD_BLOCKS_GROUP):
+            prm = raster.RasterParams(bwd_px_per_thread=np_, bwd_blocks=blocks)
+            r.params, r.prm_c = prm, prm.c()
+            r.backward(field, L.GS_GRAD_POSE)
+            twists.append((r.d_twist.clone(), r.sg_uvod.clone(), r.sg_conic.clone()))
+        for name, a, b in zip(("twist", "uvod", "conic"), *twists):
+            C.assert_grad_close("pose " + name, b.cpu().numpy(), a.cpu().numpy(), 1e-5)
     for bad in (raster.RasterParams(bwd_px_per_thread=4, bwd_blocks=L.GS_BWD_BLOCKS_GROUP),):
         r.params, r.prm_c = bad, bad.c()
         with pytest.raises(L.GsError):
