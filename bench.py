@@ -321,8 +321,9 @@ def run_forms(args, gs, dec, dev, flush, batch=8):
              ("batched_f16rgb_bf16feat", lambda: [FormJob(half, cams, frames, dec, dev, k)])]
     for name, make in specs:
         jobs = make()
-        shapes = sorted({(t.fwd_px_per_thread, f"w{t.bwd_px_per_thread}" if t.bwd_blocks == 1 else
-                          str(t.bwd_px_per_thread)) for t in (j.tune() for j in jobs)})
+        shapes = sorted({(f"w{t.fwd_px_per_thread}" if t.fwd_blocks == 1 else str(t.fwd_px_per_thread),
+                          f"w{t.bwd_px_per_thread}" if t.bwd_blocks == 1 else str(t.bwd_px_per_thread))
+                         for t in (j.tune() for j in jobs)})
         ms = time_graph(jobs, args.form_steps, flush)
         out[name] = {"frames_per_step": batch, "steps_per_graph": len(jobs), "ms_per_step": ms,
                      "frames_per_s": batch * 1000.0 / ms, "ms_per_frame": ms / batch,
@@ -546,8 +547,9 @@ def run_ours(args, rank, world, local_rank):
     r.loss(targets, W, b, w)
     if args.shapes:
         f_s, b_s = args.shapes.split(",")
-        tuned = dataclasses.replace(r.params, fwd_px_per_thread=int(f_s), bwd_px_per_thread=int(b_s.lstrip("w")),
-                                    bwd_blocks=1 if b_s.startswith("w") else 2)
+        tuned = dataclasses.replace(r.params, fwd_px_per_thread=int(f_s.lstrip("w")),
+                                    fwd_blocks=1 if f_s.startswith("w") else 2,
+                                    bwd_px_per_thread=int(b_s.lstrip("w")), bwd_blocks=1 if b_s.startswith("w") else 2)
         r.params, r.prm_c, tune_ms = tuned, tuned.c(), {}
     else:
         tuned, tune_ms = autotune.tune_blend(r, field, mode)
@@ -635,7 +637,7 @@ def run_ours(args, rank, world, local_rank):
         achieved = fl / (per_stage[dom] * 1e-3) / 1e12
         is_bwd = stages[dom] == "render_bwd"
         kname = ("raster_bwd_warp_kernel" if tuned.bwd_blocks == 1 else "raster_bwd_kernel") if is_bwd \
-            else "raster_fwd_kernel"
+            else ("raster_fwd_group_kernel" if tuned.fwd_blocks == 1 else "raster_fwd_kernel")
         shape = tuned.bwd_px_per_thread if is_bwd else tuned.fwd_px_per_thread
         roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak, "traffic": captured_traffic(kname, shape, WORKLOAD["d"]),
@@ -713,7 +715,8 @@ def run_ours(args, rank, world, local_rank):
             "config": dict(WORKLOAD, grad_mode=GRAD_MODE_NAME, l2="flushed between timed steps (512 MB write)",
                            instances=m_inst, parallelism=f"replicas x{world}",
                            px_per_thread={"fwd": tuned.fwd_px_per_thread, "bwd": tuned.bwd_px_per_thread},
-                           bwd_blocks="one per 8x4 pixel group" if tuned.bwd_blocks == 1 else "one per 16x16 tile",
+                           bwd_blocks="one per pixel group" if tuned.bwd_blocks == 1 else "one per 16x16 tile",
+                           fwd_blocks="one per pixel group" if tuned.fwd_blocks == 1 else "one per 16x16 tile",
                            autotune_ms={k: {str(n): round(t, 4) for n, t in v.items()} for k, v in tune_ms.items()}),
             "stages_ms": {s: float(t) for s, t in zip(stages, per_stage)},
             "forms": forms,

@@ -94,6 +94,12 @@ typedef struct {
      * memory; GS_BWD_BLOCKS_DEFAULT (0) = per pixel group where that form
      * applies, else per tile. */
     int32_t bwd_blocks;
+    /* Block shape of gs_render_fwd (images identical either way; the blend mask
+     * too): GS_BWD_BLOCKS_GROUP = one 32-thread block per pixel group
+     * (fwd_px_per_thread 1 or 2), which leaves as soon as its pixels are done;
+     * GS_BWD_BLOCKS_TILE = one block per tile; GS_BWD_BLOCKS_DEFAULT (0) = the
+     * library's choice for the launch shape. */
+    int32_t fwd_blocks;
 } gs_raster_params;
 
 enum { GS_BWD_BLOCKS_DEFAULT = 0, GS_BWD_BLOCKS_GROUP = 1, GS_BWD_BLOCKS_TILE = 2 };

@@ -28,7 +28,7 @@ class gs_raster_params(Structure):
     _fields_ = [("tile", c_int32), ("alpha_min", c_float), ("alpha_max", c_float), ("T_min", c_float),
                 ("z_near", c_float), ("lowpass", c_float), ("radius_sigma", c_float), ("bg_rgb", c_float * 3),
                 ("fwd_px_per_thread", c_int32), ("bwd_px_per_thread", c_int32),
-                ("bwd_blocks", c_int32)]
+                ("bwd_blocks", c_int32), ("fwd_blocks", c_int32)]
 
 
 class gs_gaussians(Structure):

@@ -18,7 +18,7 @@ from . import _lib as L
 from .raster import RasterParams, Renderer
 
 CANDIDATES = (1, 2, 4)
-WARP_CANDIDATES = (1, 2)   # map-mode backward as one block per pixel group (bwd_blocks = 1)
+WARP_CANDIDATES = (1, 2)   # one 32-thread block per pixel group (fwd_blocks / bwd_blocks = 1)
 
 
 def _time(fn, reps: int, stream) -> float:
@@ -33,9 +33,9 @@ def _time(fn, reps: int, stream) -> float:
 
 
 def tune_blend(r: Renderer, field, grad_mode: int = L.GS_GRAD_MAP, reps: int = 5, verbose: bool = False):
-    """Returns (RasterParams with the fastest fwd/bwd launch shapes, timings in ms).  Backward
-    shapes are keyed by pixels per thread (one block per tile) and "w1", "w2" (one block per
-    pixel group, map mode only).
+    """Returns (RasterParams with the fastest fwd/bwd launch shapes, timings in ms).  Shapes
+    are keyed by pixels per thread (one block per tile) and "w1", "w2" (one 32-thread block
+    per pixel group).
 
     The renderer's image gradients (r.g_*) must hold the gradients to time the
     backward with (e.g. after a loss call); the projection and binning are run here.
@@ -45,29 +45,32 @@ def tune_blend(r: Renderer, field, grad_mode: int = L.GS_GRAD_MAP, reps: int = 5
     r.project(field)
     r.bin_sort()
     timings = {"fwd": {}, "bwd": {}}
-    for np_ in CANDIDATES:
-        r.prm_c = dataclasses.replace(base, fwd_px_per_thread=np_).c()
+    fshapes = {np_: dict(fwd_px_per_thread=np_, fwd_blocks=L.GS_BWD_BLOCKS_TILE) for np_ in CANDIDATES}
+    fshapes.update({f"w{np_}": dict(fwd_px_per_thread=np_, fwd_blocks=L.GS_BWD_BLOCKS_GROUP)
+                    for np_ in WARP_CANDIDATES})
+    for key, shape in fshapes.items():
+        r.prm_c = dataclasses.replace(base, **shape).c()
         try:
-            timings["fwd"][np_] = _time(lambda: r.render_fwd(field), reps, stream)
+            timings["fwd"][key] = _time(lambda: r.render_fwd(field), reps, stream)
         except L.GsError as e:
             if e.status != L.GS_ERR_UNSUPPORTED:
                 raise
     best_f = min(timings["fwd"], key=timings["fwd"].get)
-    r.prm_c = dataclasses.replace(base, fwd_px_per_thread=best_f).c()
+    fwd = fshapes[best_f]
+    r.prm_c = dataclasses.replace(base, **fwd).c()
     r.render_fwd(field)
     shapes = {np_: dict(bwd_px_per_thread=np_, bwd_blocks=L.GS_BWD_BLOCKS_TILE) for np_ in CANDIDATES}
-    if grad_mode & L.GS_GRAD_MAP:
-        shapes.update({f"w{np_}": dict(bwd_px_per_thread=np_, bwd_blocks=L.GS_BWD_BLOCKS_GROUP)
-                       for np_ in WARP_CANDIDATES})
+    shapes.update({f"w{np_}": dict(bwd_px_per_thread=np_, bwd_blocks=L.GS_BWD_BLOCKS_GROUP)
+                   for np_ in WARP_CANDIDATES})
     for key, shape in shapes.items():
-        r.prm_c = dataclasses.replace(base, fwd_px_per_thread=best_f, **shape).c()
+        r.prm_c = dataclasses.replace(base, **fwd, **shape).c()
         try:
             timings["bwd"][key] = _time(lambda: r.render_bwd(field, grad_mode), reps, stream)
         except L.GsError as e:
             if e.status != L.GS_ERR_UNSUPPORTED:
                 raise
     best_b = min(timings["bwd"], key=timings["bwd"].get)
-    tuned = dataclasses.replace(base, fwd_px_per_thread=best_f, **shapes[best_b])
+    tuned = dataclasses.replace(base, **fwd, **shapes[best_b])
     r.params = tuned
     r.prm_c = tuned.c()
     if verbose:

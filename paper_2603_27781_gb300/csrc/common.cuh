@@ -36,6 +36,8 @@ struct Params {
     int fwd_np, bwd_np;  // pixels per thread of the blend kernels (0 = default for the feature dim)
     int bwd_blocks;      // map-mode backward block shape (GS_BWD_BLOCKS_*)
     bool bwd_warp;       // resolved: map-mode backward as one 32-thread block per pixel group
+    int fwd_blocks;      // forward block shape (GS_BWD_BLOCKS_*)
+    bool fwd_group;      // resolved: forward as one 32-thread block per pixel group
 };
 
 // Default pixels per thread of the blend kernels for a feature dimension.

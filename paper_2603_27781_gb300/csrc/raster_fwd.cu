@@ -179,16 +179,189 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS, fwd_min_blocks(D, NP)) ras
     }
 }
 
+// The same blend with one 32-thread block per pixel group (an 8x4 group with one pixel
+// per thread, a 16x4 band with two): the group stages the tile's splats 32 at a time in
+// its own shared memory, so it never waits at a barrier for the tile's other groups, and
+// it leaves as soon as its own pixels are done, freeing its registers and shared memory.
+// Arithmetic, order and outputs are those of raster_fwd_kernel.
+// Register caps that keep the blocks spill-free: 80 registers up to D = 16, 128 at D = 32 with two
+// pixels per thread.
+constexpr int fwd_group_min_blocks(int D, int NP) { return NP == 1 ? 24 : (D <= 16 ? 22 : 16); }
+
+template <int D, int NP, typename RT, typename FT>
+__global__ void __launch_bounds__(32, fwd_group_min_blocks(D, NP)) raster_fwd_group_kernel(
+    ViewTable vt, Params prm, const float4 *__restrict__ uvdo, const float2 *__restrict__ uv_lo,
+    const float4 *__restrict__ conic, const RT *__restrict__ rgb, const FT *__restrict__ feat,
+    const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges, int64_t P, float *o_rgb, float *o_depth,
+    float *o_sil, float *o_feat, float *o_T, int32_t *o_nc, int32_t *o_nb, uint32_t *bmask, int64_t bm_stride,
+    const uint32_t *__restrict__ order) {
+    using SH = Shape<NP>;
+    constexpr int D4 = D / 4, DD = D > 0 ? D : 1;
+    constexpr int GW = SH::WARPS;  // pixel-group blocks per tile
+    __shared__ SplatGeo s_geo[32];
+    __shared__ float2 s_ext[32];
+    __shared__ float4 s_rgbd[32];
+    __shared__ float4 s_feat[32 * (D4 > 0 ? D4 : 1)];
+
+    const int rank = blockIdx.x / GW, grp = blockIdx.x % GW;
+    const int gt = order ? (int)order[rank] : rank;
+    if (gt < 0 || gt >= vt.tile_off[vt.n_views]) return;  // not a permutation of the tiles: leave the tile
+    const int v = view_of_tile(vt, gt);
+    const int t = gt - vt.tile_off[v];
+    const int tx = t % vt.TX[v], ty = t / vt.TX[v];
+    const int lane = threadIdx.x;
+    const int tid = grp * 32 + lane;  // the thread's index in the tile kernel's numbering
+    const uint32_t start = ranges[2 * gt], end = ranges[2 * gt + 1];
+    const int64_t voff = (int64_t)v * vt.n;
+    int bx0, by0;
+    SH::warp_origin(grp, bx0, by0);
+    const float bcx = (float)(tx * kTile + bx0) + 0.5f * SH::BW, bcy = (float)(ty * kTile + by0) + 0.5f * SH::BH;
+    const float hx = 0.5f * (SH::BW - 1), hy = 0.5f * (SH::BH - 1);
+
+    float pxc[NP], pyc[NP], T[NP], ar[NP], ag[NP], ab[NP], ad[NP], as[NP], af[NP][DD];
+    int last[NP], blended[NP];
+    bool inside[NP], done[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        int lx, ly;
+        SH::pixel(tid, p, lx, ly);
+        const int px = tx * kTile + lx, py = ty * kTile + ly;
+        inside[p] = px < vt.W[v] && py < vt.H[v];
+        done[p] = !inside[p];
+        pxc[p] = (float)px + 0.5f;
+        pyc[p] = (float)py + 0.5f;
+        T[p] = 1.f;
+        ar[p] = ag[p] = ab[p] = ad[p] = as[p] = 0.f;
+#pragma unroll
+        for (int d = 0; d < DD; ++d) af[p][d] = 0.f;
+        last[p] = blended[p] = 0;
+    }
+    auto all_done = [&]() {
+        bool a = true;
+#pragma unroll
+        for (int p = 0; p < NP; ++p) a = a && done[p];
+        return a;
+    };
+    for (uint32_t b0 = start & ~31u; b0 < end; b0 += 32) {
+        if (__all_sync(0xffffffffu, all_done())) break;
+        {
+            const uint32_t j = b0 + lane;
+            if (j >= start && j < end) {
+                const uint32_t item = vals[j];
+                const int64_t g = (int64_t)item - voff;
+                const float4 a = uvdo[item];
+                const float4 c = conic[item];
+                s_geo[lane] = make_geo(a, uv_lo[item], c);
+                s_ext[lane] = splat_extent(c, a.w, prm.alpha_min);
+                s_rgbd[lane] = load_rgbd(rgb, g, a.z);
+#pragma unroll
+                for (int q = 0; q < D4; ++q) s_feat[lane * D4 + q] = load_feat4(feat, g * D + 4 * q);
+            }
+        }
+        __syncwarp();
+        const int k_lo = b0 < start ? (int)(start - b0) : 0;
+        const int nb = (int)min(32u, end - b0);
+        uint32_t lbits = 0u;
+        for (int k = k_lo; k < nb; ++k) {
+            if (__all_sync(0xffffffffu, all_done())) break;
+            const SplatGeo sg = s_geo[k];
+            if (!reaches_box(sg.u, sg.v, s_ext[k], bcx, bcy, hx, hy)) continue;
+            float al[NP];
+            bool ok[NP];
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const PairEval e = eval_pair(sg, pxc[p], pyc[p], prm.alpha_min, prm.alpha_max);
+                al[p] = e.alpha;
+                ok[p] = !done[p] && !e.skip;
+            }
+            float wgt[NP];
+            bool any = false;
+            const int pos = (int)(b0 - start) + k + 1;
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const float Tn = T[p] * (1.f - al[p]);
+                const bool stop = ok[p] && Tn < prm.T_min;
+                const bool b = ok[p] && !stop;
+                done[p] = done[p] || stop;
+                wgt[p] = b ? al[p] * T[p] : 0.f;
+                T[p] = b ? Tn : T[p];
+                last[p] = b ? pos : last[p];
+                blended[p] += b ? 1 : 0;
+                any = any || b;
+            }
+            lbits |= (any ? 1u : 0u) << k;
+            if (!any) continue;
+            const float4 c = s_rgbd[k];
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const float w = wgt[p];
+                ar[p] = fmaf(w, c.x, ar[p]);
+                ag[p] = fmaf(w, c.y, ag[p]);
+                ab[p] = fmaf(w, c.z, ab[p]);
+                ad[p] = fmaf(w, c.w, ad[p]);
+                as[p] += w;
+            }
+#pragma unroll
+            for (int q = 0; q < D4; ++q) {
+                const float4 f = s_feat[k * D4 + q];
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    af[p][4 * q] = fmaf(wgt[p], f.x, af[p][4 * q]);
+                    af[p][4 * q + 1] = fmaf(wgt[p], f.y, af[p][4 * q + 1]);
+                    af[p][4 * q + 2] = fmaf(wgt[p], f.z, af[p][4 * q + 2]);
+                    af[p][4 * q + 3] = fmaf(wgt[p], f.w, af[p][4 * q + 3]);
+                }
+            }
+        }
+        if (bmask) {
+            // the chunk is one mask word; words at a tile's ends are shared with the
+            // neighbouring tile's blocks, hence the atomic OR
+#pragma unroll
+            for (int j = 0; j < NP; ++j) {
+                const uint32_t mine = (lanes_of_group<NP>(j) >> lane) & 1u ? lbits : 0u;
+                const uint32_t word = __reduce_or_sync(0xffffffffu, mine);
+                if (lane == 0 && word) atomicOr(&bmask[(int64_t)(grp * NP + j) * bm_stride + (b0 >> 5)], word);
+            }
+        }
+        __syncwarp();  // every lane is done with the staged chunk before the next one
+    }
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        if (!inside[p]) continue;
+        const int64_t pix = vt.pix_off[v] + (int64_t)((int)pyc[p]) * vt.W[v] + (int)pxc[p];
+        o_rgb[pix] = ar[p] + T[p] * prm.bg[0];
+        o_rgb[P + pix] = ag[p] + T[p] * prm.bg[1];
+        o_rgb[2 * P + pix] = ab[p] + T[p] * prm.bg[2];
+        o_depth[pix] = ad[p];
+        o_sil[pix] = as[p];
+#pragma unroll
+        for (int d = 0; d < D; ++d) o_feat[d * P + pix] = af[p][d];
+        o_T[pix] = T[p];
+        o_nc[pix] = last[p];
+        if (o_nb) o_nb[pix] = blended[p];
+    }
+}
+
 template <int D, int NP, typename RT, typename FT>
 gs_status launch(const ViewTable &vt, const Params &prm, const gs_gaussians *g, const gs_projected *proj,
                  const gs_binning *bins, gs_images *out, cudaStream_t st) {
     const int tiles = vt.tile_off[vt.n_views];
     const int64_t P = vt.pix_off[vt.n_views];
-    raster_fwd_kernel<D, NP, RT, FT><<<tiles, Shape<NP>::THREADS, 0, st>>>(
-        vt, prm, reinterpret_cast<const float4 *>(proj->uvdo), reinterpret_cast<const float2 *>(proj->uv_lo),
-        reinterpret_cast<const float4 *>(proj->conic), static_cast<const RT *>(g->rgb),
-        static_cast<const FT *>(g->feat), bins->vals, bins->ranges, P, out->rgb, out->depth, out->sil, out->feat,
-        out->T_final, out->n_contrib, out->n_blended, out->blend_mask, bins->capacity / 32 + 1, bins->tile_order);
+    auto args = [&](auto kern, int blocks, int threads) {
+        kern<<<blocks, threads, 0, st>>>(
+            vt, prm, reinterpret_cast<const float4 *>(proj->uvdo), reinterpret_cast<const float2 *>(proj->uv_lo),
+            reinterpret_cast<const float4 *>(proj->conic), static_cast<const RT *>(g->rgb),
+            static_cast<const FT *>(g->feat), bins->vals, bins->ranges, P, out->rgb, out->depth, out->sil,
+            out->feat, out->T_final, out->n_contrib, out->n_blended, out->blend_mask, bins->capacity / 32 + 1,
+            bins->tile_order);
+    };
+    if constexpr (NP <= 2) {
+        if (prm.fwd_group) {
+            args(raster_fwd_group_kernel<D, NP, RT, FT>, tiles * Shape<NP>::WARPS, 32);
+            return last_launch();
+        }
+    }
+    args(raster_fwd_kernel<D, NP, RT, FT>, tiles, Shape<NP>::THREADS);
     return last_launch();
 }
 
@@ -237,6 +410,8 @@ extern "C" gs_status gs_render_fwd(const gs_gaussians *g, const gs_projected *pr
         if (s) return s;
     }
     const int np = prm.fwd_np ? prm.fwd_np : default_fwd_np(g->feat_dim);
+    prm.fwd_group = prm.fwd_blocks == GS_BWD_BLOCKS_GROUP;
+    if (prm.fwd_group && np > 2) return GS_ERR_UNSUPPORTED;
     if (g->rgb_dtype == GS_F16) {
         if (g->feat_dim == 16) return by_np<16, __half, __nv_bfloat16>(np, vt, prm, g, proj, bins, out, st);
         return by_np<32, __half, __nv_bfloat16>(np, vt, prm, g, proj, bins, out, st);

@@ -29,12 +29,13 @@ class RasterParams:
     bg: tuple = (0.0, 0.0, 0.0)
     fwd_px_per_thread: int = 0     # launch shape only (0 = library default)
     bwd_px_per_thread: int = 0
-    bwd_blocks: int = 0            # map-mode backward block shape (0 default, 1 per pixel group, 2 per tile)
+    bwd_blocks: int = 0            # backward block shape (0 default, 1 per pixel group, 2 per tile)
+    fwd_blocks: int = 0            # forward block shape (same values)
 
     def c(self) -> L.gs_raster_params:
         return L.gs_raster_params(self.tile, self.alpha_min, self.alpha_max, self.T_min, self.z_near, self.lowpass,
                                   self.radius_sigma, (ctypes.c_float * 3)(*self.bg), self.fwd_px_per_thread,
-                                  self.bwd_px_per_thread, self.bwd_blocks)
+                                  self.bwd_px_per_thread, self.bwd_blocks, self.fwd_blocks)
 
 
 @dataclasses.dataclass

@@ -117,9 +117,10 @@ def test_render_bwd_matches_oracle(name):
     C.bwd_compare(gs, [cam], prm_g, prm_o)
 
 
-@pytest.mark.parametrize("np_", [1, 2, 4])
-def test_launch_shapes_agree(np_):
-    """Every pixels-per-thread shape renders bit-identical images and the same gradients."""
+@pytest.mark.parametrize("np_,fwd_blocks", [(1, 2), (2, 2), (4, 2), (1, 1), (2, 1)])
+def test_launch_shapes_agree(np_, fwd_blocks):
+    """Every launch shape (pixels per thread; forward blocks per tile or per pixel group)
+    renders bit-identical images and blend masks and the same gradients."""
     gs, cam, _ = C.room_case(20000, 16, 330, 190, 165.0)
     prm0, prm_o = C.params_pair()
     field, r0 = C.gpu_forward(gs, cam, prm0)
@@ -131,11 +132,13 @@ def test_launch_shapes_agree(np_):
     r0.backward(field, L.GS_GRAD_MAP | L.GS_GRAD_POSE)
     want = [t.clone() for t in (r0.d_means, r0.d_quats, r0.d_log_scales, r0.d_logits, r0.d_rgb, r0.d_feat,
                                 r0.d_twist)]
-    prm = raster.RasterParams(fwd_px_per_thread=np_, bwd_px_per_thread=np_)
+    mask_ref = r0.blend_mask.clone()
+    prm = raster.RasterParams(fwd_px_per_thread=np_, bwd_px_per_thread=np_, fwd_blocks=fwd_blocks)
     r0.params, r0.prm_c = prm, prm.c()
     r0.forward(field)
     for k, t in r0.images().items():
         assert torch.equal(t, ref[k]), k
+    assert torch.equal(r0.blend_mask, mask_ref)
     r0.backward(field, L.GS_GRAD_MAP | L.GS_GRAD_POSE)
     for name, a, b in zip(("means", "quats", "log_scales", "logits", "rgb", "feat", "twist"), want,
                           (r0.d_means, r0.d_quats, r0.d_log_scales, r0.d_logits, r0.d_rgb, r0.d_feat, r0.d_twist)):
@@ -249,8 +252,9 @@ def test_autotuner_picks_a_supported_shape():
     g = C.random_image_grads(r.P, 16, 6)
     r.g_rgb.copy_(torch.as_tensor(g["rgb"])); r.g_feat.copy_(torch.as_tensor(g["feat"]))
     tuned, t = autotune.tune_blend(r, field, L.GS_GRAD_MAP)
-    assert set(t["fwd"]) == {1, 2, 4} and set(t["bwd"]) == {1, 2, 4, "w1", "w2"}
-    assert tuned.fwd_px_per_thread in t["fwd"]
+    assert set(t["fwd"]) == {1, 2, 4, "w1", "w2"} and set(t["bwd"]) == {1, 2, 4, "w1", "w2"}
+    assert (f"w{tuned.fwd_px_per_thread}" if tuned.fwd_blocks == L.GS_BWD_BLOCKS_GROUP
+            else tuned.fwd_px_per_thread) in t["fwd"]
     assert (f"w{tuned.bwd_px_per_thread}" if tuned.bwd_blocks == L.GS_BWD_BLOCKS_GROUP
             else tuned.bwd_px_per_thread) in t["bwd"]
 
