@@ -520,23 +520,25 @@ def run_ours(args, rank, world, local_rank):
     pose_f32 = torch.zeros(1, 16, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def step(ev=None):
+    def step(ev=None, f=None, tg=None):
+        f = field if f is None else f
+        tg = targets if tg is None else tg
         rec = (lambda i: ev[i].record(stream)) if ev is not None else (lambda i: None)
         rec(0)
-        r.project(field)
+        r.project(f)
         rec(1)
         r.bin_sort()
         rec(2)
-        r.render_fwd(field)
+        r.render_fwd(f)
         rec(3)
-        r.loss(targets, W, b, w)
+        r.loss(tg, W, b, w)
         rec(4)
-        r.render_bwd(field, mode)
+        r.render_bwd(f, mode)
         rec(5)
-        r.project_bwd(field, mode)
+        r.project_bwd(f, mode)
         rec(6)
         r.pose_grad()
-        r.dsr(field, w.big, w.small)
+        r.dsr(f, w.big, w.small)
         r.pose_step(T_state, adam, 0, pose_f32=pose_f32)
         rec(7)
 
@@ -595,30 +597,29 @@ def run_ours(args, rank, world, local_rank):
         ms = float(t.item())
     value = world * 1000.0 / ms
 
-    # ---- end to end: host (pinned) inputs -> device -> step -> results back to host, every step
+    # ---- end to end through the API: every step uploads its inputs (the field's parameters and
+    # the targets) from pinned host memory and brings its results (every gradient, the loss, the
+    # DSR terms, the twist) back to pinned host memory; HostStepper overlaps each step's
+    # transfers with the neighbouring steps' compute (two input and two result sets)
     host = {k: getattr(field, k).cpu().pin_memory() for k in
             ("means", "quats", "log_scales", "opacity_logits", "rgb", "feat")}
     host_t = {k: v.cpu().pin_memory() for k, v in targets.items()}
     outs = [r.d_means, r.d_quats, r.d_log_scales, r.d_logits, r.d_rgb, r.d_feat, r.loss_out, r.dsr_out,
             r.d_twist]
-    host_out = [o.cpu().pin_memory() for o in outs]
-    h2d = sum(v.numel() * v.element_size() for v in list(host.values()) + list(host_t.values()))
-    d2h = sum(o.numel() * o.element_size() for o in outs)
+    stepper = raster.HostStepper(field, targets, outs)
+    h2d, d2h = stepper.bytes_in, stepper.bytes_out
     e2e_ms = []
-    for k in range(args.e2e_steps):
-        flush.fill_(float(k))
+    if args.e2e_steps > 0:
+        stepper.run(lambda f, tg: step(None, f, tg), [(host, host_t)] * 2)      # untimed warm-up
+        torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(0.0)
         e0.record(stream)
-        for name, hv in host.items():
-            getattr(field, name).copy_(hv, non_blocking=True)
-        for name, hv in host_t.items():
-            targets[name].copy_(hv, non_blocking=True)
-        step()
-        for o, ho in zip(outs, host_out):
-            ho.copy_(o, non_blocking=True)
-        e1.record(stream)
+        stepper.h2d.wait_stream(stream)
+        n_e2e = stepper.run(lambda f, tg: step(None, f, tg), [(host, host_t)] * args.e2e_steps)
+        e1.record(stepper.d2h)
         e1.synchronize()
-        e2e_ms.append(e0.elapsed_time(e1))
+        e2e_ms = [e0.elapsed_time(e1) / n_e2e]
     e2e_value = world * 1000.0 / float(np.mean(e2e_ms)) if e2e_ms else None
 
     # ---- roofline of the dominant kernel (from the per-stage events of the timed steps)

@@ -545,3 +545,78 @@ class RasterizeSG(torch.autograd.Function):
 
 def rasterize(renderer: Renderer, means, quats, log_scales, opacity_logits, rgb, feat):
     return RasterizeSG.apply(renderer, means, quats, log_scales, opacity_logits, rgb, feat)
+
+
+_FIELD_ARRAYS = ("means", "quats", "log_scales", "opacity_logits", "rgb", "feat")
+
+
+class HostStepper:
+    """Steps whose inputs (field parameters and targets) come from pinned host memory and
+    whose results (device tensors the step writes) go back to pinned host memory, with each
+    step's transfers overlapped with its neighbours' compute: step i's upload runs on a copy
+    stream into one of two device input sets while step i-1 computes, and step i's results
+    are copied on the device to one of two staging sets, then downloaded on a second copy
+    stream while step i+1 computes.  `step(field, targets)` issues one step on the current
+    stream; `outputs` are the tensors it writes."""
+
+    def __init__(self, like_field: Field, like_targets: dict, outputs: Sequence[torch.Tensor]):
+        dev = like_field.means.device
+        clone = lambda t: torch.empty_like(t)
+        self.fields = [Field(*(clone(getattr(like_field, k)) for k in _FIELD_ARRAYS)) for _ in range(2)]
+        self.targets = [{k: clone(v) for k, v in like_targets.items()} for _ in range(2)]
+        self.outputs = list(outputs)
+        self.staging = [[clone(o) for o in self.outputs] for _ in range(2)]
+        self.host_out = [[torch.empty(o.shape, dtype=o.dtype, pin_memory=True) for o in self.outputs]
+                         for _ in range(2)]
+        self.h2d, self.d2h = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+        ev = lambda: [torch.cuda.Event() for _ in range(2)]
+        self.uploaded, self.computed, self.downloaded = ev(), ev(), ev()
+        self.bytes_in = sum(getattr(like_field, k).numel() * getattr(like_field, k).element_size()
+                            for k in _FIELD_ARRAYS) + sum(v.numel() * v.element_size() for v in like_targets.values())
+        self.bytes_out = sum(o.numel() * o.element_size() for o in self.outputs)
+
+    def run(self, step, host_inputs, on_result=None):
+        """Runs one step per (host_field, host_targets) pair of `host_inputs` (dicts of pinned
+        host tensors keyed like Field's arrays and like the targets).  on_result(i, tensors)
+        receives step i's results in pinned host memory once they have arrived (valid until
+        the callback returns).  Returns the number of steps."""
+        compute = torch.cuda.current_stream()
+        pending = [None, None]          # step whose download occupies host_out[buf]
+        n = 0
+        for i, (hf, ht) in enumerate(host_inputs):
+            buf = i & 1
+            # upload into input set buf once step i-2 has finished computing on it
+            if i >= 2:
+                self.h2d.wait_event(self.computed[buf])
+            with torch.cuda.stream(self.h2d):
+                f, tg = self.fields[buf], self.targets[buf]
+                for k in _FIELD_ARRAYS:
+                    getattr(f, k).copy_(hf[k], non_blocking=True)
+                for k, v in ht.items():
+                    tg[k].copy_(v, non_blocking=True)
+                self.uploaded[buf].record(self.h2d)
+            compute.wait_event(self.uploaded[buf])
+            step(f, tg)
+            # results to staging set buf once step i-2's download from it is done
+            if i >= 2:
+                compute.wait_event(self.downloaded[buf])
+            for s, o in zip(self.staging[buf], self.outputs):
+                s.copy_(o, non_blocking=True)
+            self.computed[buf].record(compute)
+            # host buffer buf is free once step i-2's results were handed over
+            if pending[buf] is not None:
+                self.downloaded[buf].synchronize()
+                if on_result is not None:
+                    on_result(pending[buf], self.host_out[buf])
+            self.d2h.wait_event(self.computed[buf])
+            with torch.cuda.stream(self.d2h):
+                for h, s in zip(self.host_out[buf], self.staging[buf]):
+                    h.copy_(s, non_blocking=True)
+                self.downloaded[buf].record(self.d2h)
+            pending[buf] = i
+            n += 1
+        for buf in sorted((b for b in range(2) if pending[b] is not None), key=lambda b: pending[b]):
+            self.downloaded[buf].synchronize()
+            if on_result is not None:
+                on_result(pending[buf], self.host_out[buf])
+        return n

@@ -189,3 +189,44 @@ def test_captured_tracking_loop_follows_oracle():
     # sideways translation trade off on a scene 3 m ahead, so the centre may not improve)
     assert loss_end < 0.5 * loss_start and eo[0] < e0[0]
     assert d[0] < 1e-4 and d[1] < 1e-6, (e0, eo, eg, d)
+
+
+def test_host_stepper_overlapped_steps_match_sequential_ones():
+    """Four fwd+bwd steps with different field parameters and targets from pinned host memory:
+    the overlapped stepper (uploads and downloads on copy streams, two input and two result
+    sets) hands back each step's own results, equal to the same steps run one after another."""
+    gs, cams, frames = _two_view_room(8000)
+    prm_g, _ = C.params_pair()
+    field = raster.Field.from_numpy(gs, "cuda")
+    r = raster.fit_capacity(field, cams, 16, margin=1.5, params=prm_g, n_classes=8)
+    dec = synth.decoder(8, 16)
+    W, b = torch.as_tensor(dec.W).cuda(), torch.as_tensor(dec.b).cuda()
+    tg0 = _targets(frames)
+    g = synth.rng(57)
+    inputs = []
+    for i in range(4):
+        hf = {k: (getattr(field, k).cpu() + (0.01 * i if k == "means" else 0.0)).pin_memory()
+              for k in ("means", "quats", "log_scales", "opacity_logits", "rgb", "feat")}
+        ht = {k: v.cpu().pin_memory() for k, v in tg0.items()}
+        ht["rgb"] = (ht["rgb"] * float(g.uniform(0.5, 1.0))).pin_memory()
+        inputs.append((hf, ht))
+    outs = [r.d_means, r.d_log_scales, r.d_rgb, r.d_feat, r.loss_out]
+    mode = L.GS_GRAD_MAP
+
+    def step(f, tg):
+        r.iteration(f, tg, W, b, raster.MAPPING, mode)
+
+    want = []
+    for hf, ht in inputs:
+        f = raster.Field(*(hf[k].cuda() for k in ("means", "quats", "log_scales", "opacity_logits", "rgb", "feat")))
+        step(f, {k: v.cuda() for k, v in ht.items()})
+        want.append([o.clone().cpu() for o in outs])
+    got = {}
+    stepper = raster.HostStepper(field, tg0, outs)
+    n = stepper.run(step, inputs, on_result=lambda i, host: got.__setitem__(i, [h.clone() for h in host]))
+    assert n == 4 and sorted(got) == [0, 1, 2, 3]
+    for i in range(4):
+        for a, w_ in zip(got[i], want[i]):
+            if not torch.equal(a, w_):          # float atomics may add in another order
+                C.assert_grad_close(f"step {i}", a.numpy().astype(np.float64), w_.numpy().astype(np.float64), 1e-5)
+    assert not torch.equal(got[0][-1], got[1][-1])          # the steps differ
