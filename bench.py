@@ -648,6 +648,28 @@ def run_ours(args, rank, world, local_rank):
         roof = {"kernel": stages[dom], "bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"),
                 "unit": "GB/s", "frac": None, "traffic": None}
 
+    # every stage against its binding resource: algorithmic bytes (HBM-bound stages) or FP32
+    # flops (the blend kernels) per step, divided by the stage's event time
+    n_g, D_, hbm = field.n, WORKLOAD["d"], peaks.get("hbm_gbs")
+    stage_work = {
+        "project": ("hbm", (44 + 40) * n_g),                                 # read params, write records
+        "bin_sort": ("hbm", (12 + 24 + 8) * m_inst),                         # duplicate, one keyed permutation, ranges
+        "render_fwd": ("alu", fwd_fl),
+        "loss": ("hbm", ((6 + D_) * 4 + 17 + (5 + D_) * 4) * r.P),          # images + targets in, pixel grads out
+        "render_bwd": ("alu", bwd_fl),
+        "project_bwd": ("hbm", (40 + 56 + 44 + 44) * n_g),                   # records, splat grads, params, grads
+        "pose+dsr+step": ("hbm", (3 + 6) * 4 * n_g + 2 * 12 * n_g),          # twist parts; DSR two passes over 3N
+    }
+    stages_roof = {}
+    for name, t_ms in zip(stages, per_stage):
+        kind, work = stage_work[name]
+        peak = hbm if kind == "hbm" else fp32_peak
+        achieved = work / (t_ms * 1e-3) / (1e9 if kind == "hbm" else 1e12)
+        stages_roof[name] = {"bound": kind, "achieved": round(achieved, 2), "unit": "GB/s" if kind == "hbm" else
+                             "TFLOP/s", "frac": round(achieved / peak, 4) if peak else None}
+    weighted = sum(t * (stages_roof[n]["frac"] or 0.0) for n, t in zip(stages, per_stage)) / sum(per_stage)
+    stages_roof["time_weighted_frac"] = round(weighted, 4)
+
     forms = None if args.no_forms else run_forms(args, gs, dec, dev, flush)
     tracking = None if args.no_forms else run_tracking(args, dev, flush)
     slam_loop = None if args.no_forms else run_slam(args, dev)
@@ -713,7 +735,8 @@ def run_ours(args, rank, world, local_rank):
     line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded room scene; Replica-shaped)",
-            "config": dict(WORKLOAD, grad_mode=GRAD_MODE_NAME, l2="flushed between timed steps (512 MB write)",
+            "config": dict(WORKLOAD, grad_mode=GRAD_MODE_NAME, l2="flushed between timed steps (512 MB write); "
+                           "e2e steps move 254 MB of inputs and results each (above L2)",
                            instances=m_inst, parallelism=f"replicas x{world}",
                            px_per_thread={"fwd": tuned.fwd_px_per_thread, "bwd": tuned.bwd_px_per_thread},
                            bwd_blocks="one per pixel group" if tuned.bwd_blocks == 1 else "one per 16x16 tile",
@@ -724,7 +747,7 @@ def run_ours(args, rank, world, local_rank):
             "extras": extras,
             "tracking": tracking,
             "slam": slam_loop,
-            "roofline": roof, "cpu_baseline": cpu,
+            "roofline": roof, "stages_roofline": stages_roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "iters/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": kernels_per_step(r.n_tiles) * args.steps,

@@ -10,6 +10,13 @@ difference without FP32 summation noise.  A perturbation that moves a
 threshold decision (alpha_min, the transmittance stop, a tile edge) makes
 the loss jump; such parameters are found by comparing the steps h and h/2.
 
+Batching form: 24 keyframes of the room loop (12 at 1200x680, 12 at 640x480) against one
+1M-Gaussian, 16-dim field, forward and backward over all of them in one launch per stage,
+replayed from one CUDA graph.  A window of tiles of one keyframe of each size is checked
+against the oracle (every Gaussian whose rectangle meets the window, so the window is
+exact), and the gradients, summed over the views, against the sum of the two windows'
+oracle gradients.
+
 Precision form: 2M Gaussians, 32-dim BF16 features and FP16 colours, 8
 keyframes at 1200x680 in one batch, forward and backward.  Against the
 oracle fed the same rounded values the error is the blend's own; against the
@@ -145,6 +152,108 @@ def test_differentiation_form_gradients_match_central_differences():
     assert len(resolved) >= 56
     assert {x[0] for x in resolved} == {n for n, _ in _GROUPS}
     assert max(err.values()) < 2e-3, err
+
+
+def _batching_form_scene():
+    room = synth.make_room(synth.SEED_SCENE)
+    gs = synth.room_field(1_000_000, 16, seed=synth.SEED_SCENE, room=room)
+    loop = synth.keyframe_loop(room=room)
+    pick = synth.draw_keyframes(24)
+    cams = [synth.camera(1200, 680, 600.0, T_cw=loop[i]) for i in pick[:12]]
+    cams += [synth.camera(640, 480, 525.0, T_cw=loop[i]) for i in pick[12:]]
+    return gs, cams
+
+
+def _window(gs, cam, prm_o, half_w, half_h):
+    """Tiles [x0, x1) x [y0, y1) around the view's centre, the Gaussians whose rectangles
+    meet them and the window's pixel mask."""
+    TX, TY = (cam.width + 15) // 16, (cam.height + 15) // 16
+    win = (TX // 2 - half_w, TY // 2 - half_h, TX // 2 + half_w, TY // 2 + half_h)
+    rect = oracle.project(gs, cam, prm_o)["rect"]
+    meets = (rect[:, 0] < win[2]) & (rect[:, 2] > win[0]) & (rect[:, 1] < win[3]) & (rect[:, 3] > win[1])
+    in_win = np.zeros((cam.height, cam.width), bool)
+    in_win[16 * win[1]:16 * win[3], 16 * win[0]:16 * win[2]] = True
+    return np.nonzero(meets)[0], in_win
+
+
+def test_batching_form_matches_oracle_on_windows():
+    """24 keyframes in one batch (one graph): images on a window of keyframe 0 (1200x680) and of
+    keyframe 12 (640x480) against the oracle, the replay equal to the eager launch, and the
+    view-summed gradients of upstream gradients set on those two windows against the sum of
+    the oracle's two window backwards."""
+    gs, cams = _batching_form_scene()
+    D = 16
+    prm_g, prm_o = C.params_pair()
+    field, r = C.gpu_forward(gs, cams, prm_g, want_keys=False)
+    assert r.status() == 0 and r.n_views == 24
+    eager = [t.clone() for t in (r.img_rgb, r.img_depth, r.img_feat, r.img_T, r.img_nc)]
+
+    views = {0: _window(gs, cams[0], prm_o, 12, 6), 12: _window(gs, cams[12], prm_o, 8, 5)}
+    gp = C.gpu_projection(r)
+    keeps, subs = {}, {}
+    for v, (idx, in_win) in views.items():
+        sub = gs.subset(idx)
+        op, ob, oimg = oracle.forward(sub, cams[v], prm_o)
+        sl = slice(v * gs.n, (v + 1) * gs.n)
+        gsub = {k: a[sl][idx] for k, a in gp.items()}
+        excl, _ = C.excluded_pixels(cams[v], op, gsub, oimg)
+        keep = in_win & ~excl
+        assert keep.sum() > 0.95 * in_win.sum()
+        C.assert_forward_close(C.np_images(r, v), oimg, ~keep, D)
+        keeps[v], subs[v] = keep, (sub, op, ob)
+
+    # upstream gradients on the two windows only, the whole batch backward, replayed from a graph
+    for t in (r.g_rgb, r.g_depth, r.g_sil, r.g_feat):
+        t.zero_()
+    gimgs = {}
+    for v, keep in keeps.items():
+        H, W = cams[v].height, cams[v].width
+        g = C.random_image_grads(H * W, D, 31 + v)
+        m = keep.ravel()
+        a, b_ = r.pix_off[v], r.pix_off[v + 1]
+        for k in g:
+            g[k] = g[k] * m
+        r.g_rgb[:, a:b_] = torch.as_tensor(g["rgb"], dtype=torch.float32)
+        r.g_depth[a:b_] = torch.as_tensor(g["depth"], dtype=torch.float32)
+        r.g_sil[a:b_] = torch.as_tensor(g["sil"], dtype=torch.float32)
+        r.g_feat[:, a:b_] = torch.as_tensor(g["feat"], dtype=torch.float32)
+        gimgs[v] = {k: x.reshape((-1, H, W) if x.ndim == 2 else (H, W)) for k, x in g.items()}
+
+    def batch():
+        r.forward(field)
+        r.backward(field, L.GS_GRAD_MAP)
+
+    cur = torch.cuda.current_stream()
+    side = torch.cuda.Stream()
+    side.wait_stream(cur)
+    with torch.cuda.stream(side):
+        batch()
+    cur.wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        batch()
+    for t in (r.img_rgb, r.img_depth, r.img_feat, r.img_T, r.img_nc):
+        t.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert r.status() == 0
+    for a, b_ in zip(eager, (r.img_rgb, r.img_depth, r.img_feat, r.img_T, r.img_nc)):
+        assert torch.equal(a, b_)
+
+    groups = dict(means=r.d_means, quats=r.d_quats, log_scales=r.d_log_scales, opacity_logits=r.d_logits,
+                  rgb=r.d_rgb, feat=r.d_feat)
+    got = {k: t.cpu().numpy().astype(np.float64) for k, t in groups.items()}
+    want = {k: np.zeros_like(a) for k, a in got.items()}
+    for v, (sub, op, ob) in subs.items():
+        ow = oracle.backward_from_image_grads(sub, cams[v], prm_o, op, ob, gimgs[v])
+        idx = views[v][0]
+        for k in want:
+            want[k][idx] += ow[k]
+    touched = np.union1d(views[0][0], views[12][0])
+    for k in got:
+        C.assert_grad_close(k, got[k][touched], want[k][touched])
+        rest = np.setdiff1d(np.arange(gs.n), touched)
+        assert np.abs(got[k][rest]).max() == 0.0, k
 
 
 def _precision_form_scene():
