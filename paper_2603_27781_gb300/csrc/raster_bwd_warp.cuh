@@ -55,31 +55,6 @@ __device__ __forceinline__ void add_deferred(const float (&a)[HW], int64_t item,
 // Register cap: with one pixel per thread 24 blocks per SM (80 registers at D = 16; shared
 // memory would allow 26); with two, shared memory bounds the blocks at 16, which 127
 // registers still allow.
-// TF32 bits of x, rounded to nearest (ties away), in a 32-bit container.
-__device__ __forceinline__ uint32_t tf32_bits(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
-
-// x = hi + lo with hi and lo TF32: hi carries the top 11 significant bits, lo the next 11,
-// so hi_a hi_b + hi_a lo_b + lo_a hi_b is the FP32 product up to about 2^-22 relative.
-__device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo) {
-    hi = tf32_bits(x);
-    lo = tf32_bits(x - __uint_as_float(hi));
-}
-
-// d += a b for one 16x8x8 tile on the tensor cores (TF32 inputs, FP32 accumulation).
-// Fragments (g = lane / 4, q = lane % 4): a = A[g][q], A[g+8][q], A[g][q+4], A[g+8][q+4];
-// b = B[q][g], B[q+4][g]; d = D[g][2q], D[g][2q+1], D[g+8][2q], D[g+8][2q+1].
-__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-        "{%0, %1, %2, %3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
 template <int D, int NP> constexpr int warp_bwd_min_blocks() { return NP == 1 ? 24 : 16; }
 
 template <int D, int NP, bool MAP, typename RT, typename FT>
@@ -98,13 +73,7 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP>())
     __shared__ uint32_t s_item[STAGE];
     __shared__ int s_pos[STAGE];
     __shared__ uint32_t s_list[64];
-    // deferred contraction on the tensor cores: C[slot][term] = sum_px w[slot][px] g[px][term],
-    // terms padded to whole 8-column tiles; the result rows reuse the weight rows' memory
-    constexpr int NTILE = (LY::NW + 7) / 8;
-    constexpr int CS = NTILE * 8 + 4;  // result row stride
-    constexpr int WBUF = LY::SLOTS * LY::WROW > 16 * CS ? LY::SLOTS * LY::WROW : 16 * CS;
-    static_assert(LY::SLOTS == 16 && LY::PXW % 8 == 0, "one 16-row tile of slots, 8-pixel k-steps");
-    __shared__ __align__(16) float s_w[MAP ? WBUF : 4];
+    __shared__ __align__(16) float s_w[MAP ? LY::SLOTS * LY::WROW : 4];
     __shared__ __align__(16) float s_g[MAP ? LY::PXW * LY::GROW : 4];
     __shared__ uint32_t s_slot_item[MAP ? LY::SLOTS : 1];
     const RT *rgb = static_cast<const RT *>(A.rgb);
@@ -173,63 +142,45 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP>())
     int n_slot = 0;
     // lane (j, h) contracts slot j's weights with terms [h HW, (h + 1) HW) of the
     // group's gradients and adds the sums to splat j's accumulators
-    // The deferred terms of the recorded slots: C = W G on the tensor cores (W: 16 slots x the
-    // group's pixels, G: pixels x the 4 + D terms), each product as three TF32 products
-    // (FP32 accuracy), then lane (j, h) adds terms [h HW, (h + 1) HW) of slot j to its
-    // splat's accumulators.
     auto flush = [&]() {
-        if constexpr (MAP) {
-            __syncwarp();
-            const int gq = lane >> 2, tq = lane & 3;
-            float c[NTILE][4];
+        if constexpr (!MAP) return;
+        __syncwarp();
+        const int j = lane & (LY::SLOTS - 1), h = lane >> 4;
+        const float4 *wr = reinterpret_cast<const float4 *>(s_w + j * LY::WROW);
+        const float4 *gr = reinterpret_cast<const float4 *>(s_g + h * LY::HWP);
+        float acc[LY::HW];
+        float accp[LY::HWP];
 #pragma unroll
-            for (int nt = 0; nt < NTILE; ++nt) c[nt][0] = c[nt][1] = c[nt][2] = c[nt][3] = 0.f;
+        for (int c = 0; c < LY::HWP; ++c) accp[c] = 0.f;
+#pragma unroll 2
+        for (int q = 0; q < LY::PXW / 4; ++q) {
+            const float4 w4 = wr[q];
+            const float wq[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
-            for (int k0 = 0; k0 < LY::PXW; k0 += 8) {
-                uint32_t ah[4], al[4];
-                split_tf32(s_w[gq * LY::WROW + k0 + tq], ah[0], al[0]);
-                split_tf32(s_w[(gq + 8) * LY::WROW + k0 + tq], ah[1], al[1]);
-                split_tf32(s_w[gq * LY::WROW + k0 + tq + 4], ah[2], al[2]);
-                split_tf32(s_w[(gq + 8) * LY::WROW + k0 + tq + 4], ah[3], al[3]);
+            for (int i = 0; i < 4; ++i) {
+                const float4 *g4 = gr + (4 * q + i) * (LY::GROW / 4);
 #pragma unroll
-                for (int nt = 0; nt < NTILE; ++nt) {
-                    const int t = nt * 8 + gq;  // this lane's B column: term t
-                    float g0 = 0.f, g1 = 0.f;
-                    if (t < LY::NW) {
-                        const int col = (t / LY::HW) * LY::HWP + t % LY::HW;
-                        g0 = s_g[(k0 + tq) * LY::GROW + col];
-                        g1 = s_g[(k0 + tq + 4) * LY::GROW + col];
-                    }
-                    uint32_t bh0, bl0, bh1, bl1;
-                    split_tf32(g0, bh0, bl0);
-                    split_tf32(g1, bh1, bl1);
-                    mma_tf32(c[nt], al, bh0, bh1);  // the small products first
-                    mma_tf32(c[nt], ah, bl0, bl1);
-                    mma_tf32(c[nt], ah, bh0, bh1);
+                for (int c = 0; c < LY::HWP / 4; ++c) {
+                    const float4 gv = g4[c];
+                    accp[4 * c] = fmaf(wq[i], gv.x, accp[4 * c]);
+                    if (4 * c + 1 < LY::HW) accp[4 * c + 1] = fmaf(wq[i], gv.y, accp[4 * c + 1]);
+                    if (4 * c + 2 < LY::HW) accp[4 * c + 2] = fmaf(wq[i], gv.z, accp[4 * c + 2]);
+                    if (4 * c + 3 < LY::HW) accp[4 * c + 3] = fmaf(wq[i], gv.w, accp[4 * c + 3]);
                 }
             }
-            __syncwarp();  // every lane has read its weights: the rows take the results
-#pragma unroll
-            for (int nt = 0; nt < NTILE; ++nt) {
-                *reinterpret_cast<float2 *>(s_w + gq * CS + nt * 8 + 2 * tq) = make_float2(c[nt][0], c[nt][1]);
-                *reinterpret_cast<float2 *>(s_w + (gq + 8) * CS + nt * 8 + 2 * tq) = make_float2(c[nt][2], c[nt][3]);
-            }
-            __syncwarp();
-            const int j = lane & (LY::SLOTS - 1), h = lane >> 4;
-            if (j < n_slot) {
-                float acc[LY::HW];
-#pragma unroll
-                for (int q = 0; q < LY::HW; ++q) acc[q] = s_w[j * CS + h * LY::HW + q];
-                const int64_t item = s_slot_item[j];
-                const int64_t g = item - voff;
-                if (h == 0)
-                    add_deferred<D, LY::HW, 0>(acc, item, g, A.acc_uvod, A.acc_rgb, A.d_feat);
-                else
-                    add_deferred<D, LY::HW, LY::HW>(acc, item, g, A.acc_uvod, A.acc_rgb, A.d_feat);
-            }
-            __syncwarp();
-            n_slot = 0;
         }
+#pragma unroll
+        for (int c = 0; c < LY::HW; ++c) acc[c] = accp[c];
+        if (j < n_slot) {
+            const int64_t item = s_slot_item[j];
+            const int64_t g = item - voff;
+            if (h == 0)
+                add_deferred<D, LY::HW, 0>(acc, item, g, A.acc_uvod, A.acc_rgb, A.d_feat);
+            else
+                add_deferred<D, LY::HW, LY::HW>(acc, item, g, A.acc_uvod, A.acc_rgb, A.d_feat);
+        }
+        __syncwarp();
+        n_slot = 0;
     };
 
     const float inv_l2e = 1.f / kLog2e;
