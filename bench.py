@@ -495,6 +495,19 @@ def run_slam(args, dev, n_frames=8):
             "timing": "host wall clock around each frame (each phase ends with a read-back)"}
 
 
+def job_rate(ms_local, world, device=None):
+    """Whole-job rate of N replicas that each ran one step per ms_local: the slowest rank's
+    time per step (max over ranks) and N steps per that time, in steps/s."""
+    ms = float(ms_local)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * 1000.0 / ms
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -590,12 +603,7 @@ def run_ours(args, rank, world, local_rank):
             per_stage[s] += ev[s].elapsed_time(ev[s + 1])
         total += ev[0].elapsed_time(ev[7])
     per_stage /= args.steps
-    ms = total / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * 1000.0 / ms
+    ms, value = job_rate(total / args.steps, world, dev)
 
     # ---- end to end through the API: every step uploads its inputs (the field's parameters and
     # the targets) from pinned host memory and brings its results (every gradient, the loss, the
@@ -620,7 +628,7 @@ def run_ours(args, rank, world, local_rank):
         e1.record(stepper.d2h)
         e1.synchronize()
         e2e_ms = [e0.elapsed_time(e1) / n_e2e]
-    e2e_value = world * 1000.0 / float(np.mean(e2e_ms)) if e2e_ms else None
+    e2e_value = job_rate(float(np.mean(e2e_ms)), world, dev)[1] if e2e_ms else None
 
     # ---- roofline of the dominant kernel (from the per-stage events of the timed steps)
     peaks = {}
