@@ -207,8 +207,8 @@ def kernels_per_step(n_tiles):
     project = 1
     # compaction (3), depth histogram + 4 passes, emission (3), tile histogram + passes, ranges, tile order
     bin_sort = 3 + 1 + 4 + 3 + 1 + tile_passes + 1 + 1
-    # loss + its finish; DSR: stats, finish, mask, finish, gradient
-    fwd, loss, bwd, proj_bwd, pose, dsr, step = 1, 2, 1, 1, 1, 5, 1
+    # loss + its finish; DSR: stats and mask (each finished by its last block), gradient
+    fwd, loss, bwd, proj_bwd, pose, dsr, step = 1, 2, 1, 1, 1, 3, 1
     return project + bin_sort + fwd + loss + bwd + proj_bwd + pose + dsr + step
 
 

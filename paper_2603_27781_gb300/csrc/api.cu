@@ -97,7 +97,7 @@ WsLayout ws_layout(int64_t n, int n_views, int64_t capacity, const ViewTable *vt
     const int64_t P = vt ? vt->pix_off[vt->n_views] : 0;
     const int ssim_rows = vt ? ssim_blocks(*vt) : 0;
     L.loss_part_d = take(sizeof(double) * ((size_t)kLossBlocks + ssim_rows) * 3);
-    L.dsr_part = take(sizeof(double) * 512 * 6);
+    L.dsr_part = take(sizeof(double) * 512 * 6 + 2 * sizeof(uint32_t));  // partials + two arrival counters
     L.ssim_maps = take(sizeof(float) * 9 * (size_t)P);
     L.expand_counts = take(sizeof(uint32_t) * 2 * (vt ? (size_t)vt->n_views * expand_blocks_x(*vt) : 0));
     L.misc_end = off;

@@ -231,7 +231,7 @@ struct WsLayout {
     size_t loss_part_d;   // f64 [kLossBlocks + SSIM tiles][3] loss-term partials
     size_t ssim_maps;     // f32 [9 P] SSIM window partials (3 planes per channel)
     size_t expand_counts; // u32 [2][views x 256-pixel blocks] expansion counts and offsets
-    size_t dsr_part;      // f64 [512][6] DSR partials
+    size_t dsr_part;      // f64 [512][6] DSR partials, then two u32 arrival counters
     size_t misc_end;
     size_t total;
     int64_t vn, capacity;

@@ -454,14 +454,29 @@ __device__ __forceinline__ void for_my_elements(int64_t m, const float *x, F f) 
     for (int64_t e = b0 + 4 * n4 + threadIdx.x; e < b1; e += blockDim.x) f(e, x[e]);
 }
 
-// Sum of a strided f64 partial column over nb blocks, by the whole block (fixed order).
-__device__ double sum_partials(const double *part, int stride, int col, int nb, double *s_red) {
+
+// True in the block that finishes last (its partial and every other block's are written
+// and visible); that block then resets *ctr for the next call.
+__device__ bool last_block(uint32_t *ctr) {
+    __shared__ bool s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(ctr, 1u) == gridDim.x - 1;
+    __syncthreads();
+    return s_last;
+}
+
+// Sum of a strided f64 partial column written by other blocks of this grid (read past L1).
+__device__ double sum_partials_cg(const double *part, int stride, int col, int nb, double *s_red) {
     double x = 0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) x += part[(size_t)b * stride + col];
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) x += __ldcg(part + (size_t)b * stride + col);
     return block_sum_f64(x, s_red);
 }
 
-__global__ void __launch_bounds__(256) dsr_stats_kernel(int64_t m, const float *ls, double *part) {
+// Pass 1 of Eq. 12: per-block sums of s and s^2 over the 3N scales; the last block turns
+// them into the population mean and deviation, out[1], out[2] (detached constants).
+__global__ void __launch_bounds__(256) dsr_stats_kernel(int64_t m, const float *ls, double *part, double *out,
+                                                        uint32_t *ctr) {
     __shared__ double s_red[8];
     Kahan s1, s2;
     for_my_elements(m, ls, [&](int64_t, float l) {
@@ -475,19 +490,14 @@ __global__ void __launch_bounds__(256) dsr_stats_kernel(int64_t m, const float *
         part[2 * blockIdx.x] = t1;
         part[2 * blockIdx.x + 1] = t2;
     }
-}
-
-// One block: the population mean and deviation of the 3N scales from the stats partials,
-// written to out[1], out[2] (the constants of Eq. 12, detached).
-__global__ void __launch_bounds__(256) dsr_finish_stats_kernel(int nb, int64_t m, const double *stats_part,
-                                                               double *out) {
-    __shared__ double s_red[8];
-    const double t1 = sum_partials(stats_part, 2, 0, nb, s_red);
-    const double t2 = sum_partials(stats_part, 2, 1, nb, s_red);
+    if (!last_block(ctr)) return;
+    const double u1 = sum_partials_cg(part, 2, 0, gridDim.x, s_red);
+    const double u2 = sum_partials_cg(part, 2, 1, gridDim.x, s_red);
     if (threadIdx.x == 0) {
-        const double mu = t1 / (double)m, var = t2 / (double)m - mu * mu;
+        const double mu = u1 / (double)m, var = u2 / (double)m - mu * mu;
         out[1] = mu;
         out[2] = sqrt(var > 0 ? var : 0.0);
+        *ctr = 0u;
     }
 }
 
@@ -496,8 +506,11 @@ __device__ __forceinline__ float2 dsr_bounds(const double *out) {
     return make_float2((float)(out[1] + 2.0 * out[2]), (float)(out[1] - 2.0 * out[2]));
 }
 
-__global__ void __launch_bounds__(256) dsr_mask_kernel(int64_t m, const float *ls, const double *out,
-                                                       double *mask_part) {
+// Pass 2: per-block sizes and sums of the two sets; the last block forms their means and
+// the regulariser's value, out = (lam_big L_big + lam_small L_small, mu, sigma, n_big,
+// n_small, L_big, L_small, 0).
+__global__ void __launch_bounds__(256) dsr_mask_kernel(int64_t m, const float *ls, double *out, double *mask_part,
+                                                       float lam_big, float lam_small, uint32_t *ctr) {
     __shared__ double s_red[8];
     const float2 bd = dsr_bounds(out);
     Kahan sb, ss;
@@ -511,23 +524,18 @@ __global__ void __launch_bounds__(256) dsr_mask_kernel(int64_t m, const float *l
                          block_sum_f64((double)ss.s - ss.c, s_red), block_sum_f64((double)ns, s_red)};
     if (threadIdx.x == 0)
         for (int k = 0; k < 4; ++k) mask_part[4 * blockIdx.x + k] = t[k];
-}
-
-// One block: the sizes and means of the two sets and the regulariser's value,
-// out = (lam_big L_big + lam_small L_small, mu, sigma, n_big, n_small, L_big, L_small, 0).
-__global__ void __launch_bounds__(256) dsr_finish_mask_kernel(int nb, const double *mask_part, float lam_big,
-                                                              float lam_small, double *out) {
-    __shared__ double s_red[8];
-    double t[4];
-    for (int k = 0; k < 4; ++k) t[k] = sum_partials(mask_part, 4, k, nb, s_red);
+    if (!last_block(ctr)) return;
+    double u[4];
+    for (int k = 0; k < 4; ++k) u[k] = sum_partials_cg(mask_part, 4, k, gridDim.x, s_red);
     if (threadIdx.x == 0) {
-        const double Lb = t[1] > 0 ? t[0] / t[1] : 0.0, Ls = t[3] > 0 ? t[2] / t[3] : 0.0;
+        const double Lb = u[1] > 0 ? u[0] / u[1] : 0.0, Ls = u[3] > 0 ? u[2] / u[3] : 0.0;
         out[0] = (double)lam_big * Lb + (double)lam_small * Ls;
-        out[3] = t[1];
-        out[4] = t[3];
+        out[3] = u[1];
+        out[4] = u[3];
         out[5] = Lb;
         out[6] = Ls;
         out[7] = 0.0;
+        *ctr = 0u;
     }
 }
 
@@ -750,12 +758,12 @@ extern "C" gs_status gs_dsr(int64_t n, const float *log_scales, float lam_big, f
     if (!log_scales || !d_log_scales) return GS_ERR_ARG;
     const int64_t m = 3 * n;
     const int grid = std::min(ceil_div(m, 256), kRedBlocks);
-    dsr_stats_kernel<<<grid, 256, 0, st>>>(m, log_scales, part);
-    dsr_finish_stats_kernel<<<1, 256, 0, st>>>(grid, m, part, out);
-    dsr_mask_kernel<<<grid, 256, 0, st>>>(m, log_scales, out, part + 2 * kRedBlocks);
-    dsr_finish_mask_kernel<<<1, 256, 0, st>>>(grid, part + 2 * kRedBlocks, lam_big, lam_small, out);
+    // two arrival counters after the partials (zeroed here; each finishing block resets its own)
+    uint32_t *ctr = reinterpret_cast<uint32_t *>(part + 6 * kRedBlocks);
+    if ((s = cuda_status(cudaMemsetAsync(ctr, 0, 2 * sizeof(uint32_t), st)))) return s;
+    dsr_stats_kernel<<<grid, 256, 0, st>>>(m, log_scales, part, out, ctr);
+    dsr_mask_kernel<<<grid, 256, 0, st>>>(m, log_scales, out, part + 2 * kRedBlocks, lam_big, lam_small, ctr + 1);
     dsr_grad_kernel<<<grid, 256, 0, st>>>(m, log_scales, lam_big, lam_small, out, d_log_scales);
-    (void)s;
     return last_launch();
 }
 
