@@ -45,6 +45,21 @@ __device__ __forceinline__ float warp_transpose_reduce(float (&v)[N], int lane) 
 
 constexpr size_t align16(size_t b) { return (b + 15) / 16 * 16; }
 
+// Per splat, lanes 0-4 of a warp hold the reduced moments S = sum over its pixels of
+// (dx, dy, dx^2, dx dy, dy^2) x dpow, dpow = o G dL/dalpha.  The centre gradient is
+// -(1/log2 e) (2 qa S_x + qb S_y, qb S_x + 2 qc S_y) and the conic's is -(S_xx/2, S_xy,
+// S_yy/2) with (qa, qb, qc) the splat's log2-scaled conic; lane i returns gradient value i
+// (lanes >= 5 return r unchanged).  All lanes must call it (a shuffle pairs lanes 0 and 1).
+__device__ __forceinline__ float geo_grads(float r, int i, const SplatGeo &s) {
+    const float o = __shfl_xor_sync(0xffffffffu, r, 1);
+    const float c = -1.f / kLog2e;
+    if (i == 0) return c * fmaf(2.f * s.qa, r, s.qb * o);
+    if (i == 1) return c * fmaf(2.f * s.qc, r, s.qb * o);
+    if (i == 2 || i == 4) return -0.5f * r;
+    if (i == 3) return -r;
+    return r;
+}
+
 // Per splat the kernel accumulates: centre (2), conic (3), opacity, then the
 // alpha-T weighted terms depth, r, g, b and the D features.
 //
@@ -233,7 +248,6 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS) raster_bwd_kernel(ViewTabl
     if (my_max > 0) atomicMax(&s_max_last, my_max);
     __syncthreads();
     const int max_last = s_max_last;
-    const float inv_l2e = 1.f / kLog2e;
 
     for (int b_end = max_last; b_end > 0; b_end -= LY::BATCH) {
         const int b_start = max(0, b_end - LY::BATCH);
@@ -299,11 +313,14 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS) raster_bwd_kernel(ViewTabl
                     if (e[p].oG < prm.alpha_max) {
                         const float dpow = e[p].oG * da;
                         const float dx = e[p].dx, dy = e[p].dy;
-                        val[0] += (2.f * s.qa * dx + s.qb * dy) * (-dpow * inv_l2e);
-                        val[1] += (s.qb * dx + 2.f * s.qc * dy) * (-dpow * inv_l2e);
-                        val[2] += -0.5f * dx * dx * dpow;
-                        val[3] += -dx * dy * dpow;
-                        val[4] += -0.5f * dy * dy * dpow;
+                        // moments of dpow over the pixels; the splat's constants scale them
+                        // once, after the warp reduction (geo_grads)
+                        const float ax = dx * dpow, ay = dy * dpow;
+                        val[0] += ax;
+                        val[1] += ay;
+                        val[2] = fmaf(ax, dx, val[2]);
+                        val[3] = fmaf(ax, dy, val[3]);
+                        val[4] = fmaf(ay, dy, val[4]);
                         if (MAP) val[5] += e[p].G * da;
                     }
                     if constexpr (LY::DEFER) {
@@ -332,8 +349,8 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS) raster_bwd_kernel(ViewTabl
                 float v0[LY::C0];
 #pragma unroll
                 for (int i = 0; i < LY::C0; ++i) v0[i] = val[i];
-                const float r = warp_transpose_reduce<LY::C0>(v0, lane);
                 const int idx = lane & (LY::C0 - 1);
+                const float r = geo_grads(warp_transpose_reduce<LY::C0>(v0, lane), idx, s);
                 if (lane < LY::C0 && idx < LY::NR && r != 0.f) atomicAdd(&s_acc[k * LY::ROW + idx], r);
             }
             if constexpr (LY::C1 > 0) {

@@ -183,7 +183,6 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP>())
         n_slot = 0;
     };
 
-    const float inv_l2e = 1.f / kLog2e;
     // Every listed splat was blended by a pixel of the group, so no box culling is needed.
     auto process = [&](const int k) {
         const int pos = s_pos[k];
@@ -227,11 +226,14 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP>())
                 if (e[p].oG < prm.alpha_max) {
                     const float dpow = e[p].oG * da;
                     const float dx = e[p].dx, dy = e[p].dy;
-                    val[0] += (2.f * s.qa * dx + s.qb * dy) * (-dpow * inv_l2e);
-                    val[1] += (s.qb * dx + 2.f * s.qc * dy) * (-dpow * inv_l2e);
-                    val[2] += -0.5f * dx * dx * dpow;
-                    val[3] += -dx * dy * dpow;
-                    val[4] += -0.5f * dy * dy * dpow;
+                    // moments of dpow over the pixels; the splat's constants scale them
+                    // once, after the warp reduction (geo_grads)
+                    const float ax = dx * dpow, ay = dy * dpow;
+                    val[0] += ax;
+                    val[1] += ay;
+                    val[2] = fmaf(ax, dx, val[2]);
+                    val[3] = fmaf(ax, dy, val[3]);
+                    val[4] = fmaf(ay, dy, val[4]);
                     if (MAP) val[5] += e[p].G * da;
                 }
                 if (MAP) wv[p] = a * Tb;
@@ -246,11 +248,11 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP>())
             if (lane == 0) s_slot_item[n_slot] = item;
             ++n_slot;
         }
-        // lane i ends with the warp's sum of value (i mod 8): centre (0, 1), conic (2-4), and
+        // lane i ends with the warp's gradient value (i mod 8): centre (0, 1), conic (2-4), and
         // opacity (map mode) or depth (pose mode) (5); lanes 0-5 add them in one warp-wide
         // reduction instruction (two 16-byte targets: acc_uvod (u, v, opacity, depth) and
         // acc_conic (A, B, C))
-        const float r = warp_transpose_reduce<8>(val, lane);
+        const float r = geo_grads(warp_transpose_reduce<8>(val, lane), lane & 7, s);
         if (lane < 6 && r != 0.f) {
             float *dst = lane == 5 ? reinterpret_cast<float *>(A.acc_uvod + item) + (MAP ? 2 : 3)
                          : lane < 2 ? reinterpret_cast<float *>(A.acc_uvod + item) + lane
