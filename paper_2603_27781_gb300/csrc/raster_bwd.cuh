@@ -50,14 +50,13 @@ constexpr size_t align16(size_t b) { return (b + 15) / 16 * 16; }
 // -(1/log2 e) (2 qa S_x + qb S_y, qb S_x + 2 qc S_y) and the conic's is -(S_xx/2, S_xy,
 // S_yy/2) with (qa, qb, qc) the splat's log2-scaled conic; lane i returns gradient value i
 // (lanes >= 5 return r unchanged).  All lanes must call it (a shuffle pairs lanes 0 and 1).
+// Branch-free: a lane-dependent branch here would serialise five paths per splat.
 __device__ __forceinline__ float geo_grads(float r, int i, const SplatGeo &s) {
     const float o = __shfl_xor_sync(0xffffffffu, r, 1);
-    const float c = -1.f / kLog2e;
-    if (i == 0) return c * fmaf(2.f * s.qa, r, s.qb * o);
-    if (i == 1) return c * fmaf(2.f * s.qc, r, s.qb * o);
-    if (i == 2 || i == 4) return -0.5f * r;
-    if (i == 3) return -r;
-    return r;
+    const float a = i == 0 ? 2.f * s.qa : 2.f * s.qc;
+    const float centre = (-1.f / kLog2e) * fmaf(a, r, s.qb * o);
+    const float scale = (i == 2 || i == 4) ? -0.5f : (i == 3 ? -1.f : 1.f);
+    return i < 2 ? centre : scale * r;
 }
 
 // Per splat the kernel accumulates: centre (2), conic (3), opacity, then the
