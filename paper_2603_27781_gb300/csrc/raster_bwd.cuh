@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS) raster_bwd_kernel(ViewTabl
             for (int i = 0; i < LY::C0 + LY::C1; ++i) val[i] = 0.f;
 #pragma unroll
             for (int p = 0; p < NP; ++p) wv[p] = 0.f;
-            if (any) {
+            {
                 const float4 c = s_rgbd[k];
                 float x[NCH];
                 x[0] = c.x; x[1] = c.y; x[2] = c.z; x[3] = c.w; x[4] = 1.f;
@@ -295,10 +295,11 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS) raster_bwd_kernel(ViewTabl
                     const float4 f = s_feat[k * D4 + q];
                     x[5 + 4 * q] = f.x; x[6 + 4 * q] = f.y; x[7 + 4 * q] = f.z; x[8 + 4 * q] = f.w;
                 }
+                // Branch-free over the lanes: a pixel that did not blend the splat runs the same
+                // instructions with alpha 0 and keeps its state, and every sum it adds to is 0.
 #pragma unroll
                 for (int p = 0; p < NP; ++p) {
-                    if (!contrib[p]) continue;
-                    const float a = e[p].alpha;
+                    const float a = contrib[p] ? e[p].alpha : 0.f;
                     const float Tb = __fdividef(T[p], 1.f - a);
                     const float w = a * Tb;
                     // g.x as three interleaved partial sums (shorter dependent chain)
@@ -308,20 +309,19 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS) raster_bwd_kernel(ViewTabl
                     const float gx = gx3[0] + gx3[1] + gx3[2];
                     const float da = Tb * (gx - gS[p]);
                     gS[p] = fmaf(a, gx - gS[p], gS[p]);
-                    T[p] = Tb;
-                    if (e[p].oG < prm.alpha_max) {
-                        const float dpow = e[p].oG * da;
-                        const float dx = e[p].dx, dy = e[p].dy;
-                        // moments of dpow over the pixels; the splat's constants scale them
-                        // once, after the warp reduction (geo_grads)
-                        const float ax = dx * dpow, ay = dy * dpow;
-                        val[0] += ax;
-                        val[1] += ay;
-                        val[2] = fmaf(ax, dx, val[2]);
-                        val[3] = fmaf(ax, dy, val[3]);
-                        val[4] = fmaf(ay, dy, val[4]);
-                        if (MAP) val[5] += e[p].G * da;
-                    }
+                    T[p] = contrib[p] ? Tb : T[p];
+                    // moments of dpow over the pixels where alpha is not clamped; the splat's
+                    // constants scale them once, after the warp reduction (geo_grads)
+                    const bool free_alpha = contrib[p] && e[p].oG < prm.alpha_max;
+                    const float dpow = free_alpha ? e[p].oG * da : 0.f;
+                    const float dx = e[p].dx, dy = e[p].dy;
+                    const float ax = dx * dpow, ay = dy * dpow;
+                    val[0] += ax;
+                    val[1] += ay;
+                    val[2] = fmaf(ax, dx, val[2]);
+                    val[3] = fmaf(ax, dy, val[3]);
+                    val[4] = fmaf(ay, dy, val[4]);
+                    if (MAP) val[5] += e[p].G * (free_alpha ? da : 0.f);
                     if constexpr (LY::DEFER) {
                         wv[p] = w;
                     } else if (MAP) {
