@@ -136,9 +136,7 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS, fwd_min_blocks(D, NP)) ras
                     any = any || b;
                 }
                 lbits |= (any ? 1u : 0u) << (k & 31);
-                // skip only when no lane blended (a warp-uniform branch); a lane that blended
-                // nothing runs the accumulation with weights of exactly 0
-                if (!__any_sync(0xffffffffu, any)) continue;
+                if (!any) continue;
                 const float4 c = s_rgbd[k];
 #pragma unroll
                 for (int p = 0; p < NP; ++p) {
@@ -292,9 +290,7 @@ __global__ void __launch_bounds__(32, fwd_group_min_blocks(D, NP)) raster_fwd_gr
                 any = any || b;
             }
             lbits |= (any ? 1u : 0u) << k;
-            // skip only when no lane blended (a warp-uniform branch); a lane that blended
-            // nothing runs the accumulation with weights of exactly 0
-            if (!__any_sync(0xffffffffu, any)) continue;
+            if (!any) continue;
             const float4 c = s_rgbd[k];
 #pragma unroll
             for (int p = 0; p < NP; ++p) {
