@@ -298,6 +298,57 @@ def time_graph(jobs, steps, flush):
     return float(np.mean(ms))
 
 
+def run_configs(args, dev, flush):
+    """The other configurations of the workload family, each as one graph-captured fwd+bwd
+    step of the whole path (autotuned launch shapes, L2 flushed between replays): the
+    batching form (24 keyframes, 12 at 1200x680 and 12 at 640x480, drawn from the 200-pose
+    loop, on the 1M-Gaussian D=16 room field), the precision form (2M Gaussians, D=32 BF16
+    features, FP16 colours, 8 keyframes at 1200x680) and the differentiation form (1M
+    Gaussians, D=32 FP32, one 640x480 frame, fx=525)."""
+    import torch
+    from paper_2603_27781_gb300 import raster, synth
+    room = synth.make_room(synth.SEED_SCENE)
+    loop = synth.keyframe_loop(room=room)
+    timing = "one CUDA graph per configuration, replays timed with CUDA events, L2 flushed between replays"
+    out = {}
+
+    def measure(name, field, cams, dec, **info):
+        # the step's cost does not depend on the target values: seeded uniform targets stand
+        # in for ray casts of the room here (they take seconds per frame on the host)
+        frames = [synth.random_frame(c, WORKLOAD["k"], seed=synth.SEED_TARGET + i) for i, c in enumerate(cams)]
+        job = FormJob(field, cams, frames, dec, dev, WORKLOAD["k"])
+        t = job.tune()
+        ms = time_graph([job], args.form_steps, flush)
+        out[name] = dict(info, frames=len(cams), ms_per_step=ms, frames_per_s=len(cams) * 1000.0 / ms,
+                         instances=int(job.r.instances()),
+                         px_per_thread_fwd_bwd=[f"w{t.fwd_px_per_thread}" if t.fwd_blocks == 1 else
+                                                str(t.fwd_px_per_thread),
+                                                f"w{t.bwd_px_per_thread}" if t.bwd_blocks == 1 else
+                                                str(t.bwd_px_per_thread)], timing=timing)
+        del job
+        torch.cuda.empty_cache()
+
+    pick = synth.draw_keyframes(24)
+    cams = [synth.camera(1200, 680, 600.0, T_cw=loop[i]) for i in pick[:12]]
+    cams += [synth.camera(640, 480, 525.0, T_cw=loop[i]) for i in pick[12:]]
+    gs = synth.room_field(1_000_000, 16, seed=synth.SEED_SCENE, room=room)
+    measure("batching_24_keyframes", raster.Field.from_numpy(gs, dev), cams, synth.decoder(WORKLOAD["k"], 16),
+            workload="1M Gaussians, D=16 FP32; 12 keyframes at 1200x680 fx=600 + 12 at 640x480 fx=525")
+    del gs
+    gs = synth.room_field(2_000_000, 32, seed=synth.SEED_SCENE, room=room)
+    cams = [synth.camera(1200, 680, 600.0, T_cw=loop[i]) for i in synth.draw_keyframes(8)]
+    measure("precision_2M_d32_bf16_f16", raster.Field.from_numpy(gs, dev, rgb_dtype=torch.float16,
+                                                                 feat_dtype=torch.bfloat16),
+            cams, synth.decoder(WORKLOAD["k"], 32),
+            workload="2M Gaussians, D=32 BF16 features, FP16 colours (f32 blending); 8 keyframes at 1200x680")
+    del gs
+    gs = synth.room_field(1_000_000, 32, seed=synth.SEED_SCENE, room=room)
+    measure("differentiation_1M_d32_640x480", raster.Field.from_numpy(gs, dev),
+            [synth.room_camera(640, 480, 525.0, room=room)], synth.decoder(WORKLOAD["k"], 32),
+            workload="1M Gaussians, D=32 FP32; one frame at 640x480 fx=525")
+    return out
+
+
 def run_forms(args, gs, dec, dev, flush, batch=8):
     """The batched and reduced-precision forms against the plain one, on the same
     keyframes: `batch` poses drawn from the loop through the room, 1200x680, each
@@ -681,6 +732,7 @@ def run_ours(args, rank, world, local_rank):
     forms = None if args.no_forms else run_forms(args, gs, dec, dev, flush)
     tracking = None if args.no_forms else run_tracking(args, dev, flush)
     slam_loop = None if args.no_forms else run_slam(args, dev)
+    configs = None if args.no_forms else run_configs(args, dev, flush)
 
     # the SSIM term of the paper's mapping colour loss (Eq. 15, lambda = 0.2) on the same frame:
     # the loss step with and without it (events around 20 calls each)
@@ -755,6 +807,7 @@ def run_ours(args, rank, world, local_rank):
             "extras": extras,
             "tracking": tracking,
             "slam": slam_loop,
+            "other_configs": configs,
             "roofline": roof, "stages_roofline": stages_roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "iters/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
