@@ -87,7 +87,8 @@ typedef struct {
     int32_t fwd_px_per_thread, bwd_px_per_thread;
     /* Block shape of gs_render_bwd (results do not depend on it beyond the
      * order of float atomics): GS_BWD_BLOCKS_GROUP = one 32-thread block per
-     * 8x4 pixel group (bwd_px_per_thread 1, or 2 for 16x4 bands; 0 means 1),
+     * 8x4 pixel group (bwd_px_per_thread 1, or 2 for 16x4 bands; 0 means 2 at
+     * feature dim 16, else 1),
      * each adding its own sums with atomics, for feature dims 16 and 32 with
      * the forward's blend mask (else GS_ERR_UNSUPPORTED); GS_BWD_BLOCKS_TILE =
      * one block per 16x16 tile whose warps combine each splat's sums in shared
