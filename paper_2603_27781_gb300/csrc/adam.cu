@@ -1,8 +1,7 @@
 // Mapping update: one bias-corrected Adam step of every parameter group of the field
-// with the per-group learning rates of supplementary C.1.  One launch: blockIdx.y picks
-// the group, the x-blocks stride over its 4-element chunks (float4 loads and stores
-// where the group's four arrays allow, two chunks in flight per thread); 28 bytes per
-// parameter (read p, g, m, v; write p, m, v), an HBM-bound pass.
+// with the per-group learning rates of supplementary C.1.  One launch walks all six
+// groups as 4-element chunks (float4 loads and stores where the arrays allow);
+// 28 bytes per parameter (read p, g, m, v; write p, m, v), an HBM-bound pass.
 #include "common.cuh"
 
 namespace gs {
@@ -15,6 +14,7 @@ struct AdamGroups {
     const float *g[kGroups];
     float *m[kGroups], *v[kGroups];
     int64_t count[kGroups];
+    int64_t chunk_off[kGroups + 1];  // first 4-element chunk of each group
     float lr[kGroups];
 };
 
@@ -49,56 +49,33 @@ __global__ void __launch_bounds__(256) adam_kernel(AdamGroups G, AdamCoef K, con
     }
     __syncthreads();
     const float bc1 = s_bc[0], bc2 = s_bc[1];
-    // group blockIdx.y; the threads of the x-blocks stride over its 4-element chunks, two
-    // chunks per iteration with all eight loads issued before any update
-    const int k = blockIdx.y;
-    const int64_t count = G.count[k];
-    float *p = G.p[k], *m = G.m[k], *v = G.v[k];
-    const float *g = G.g[k];
-    const float lr = G.lr[k];
-    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const bool vec = ((reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(g) |
-                       reinterpret_cast<uintptr_t>(m) | reinterpret_cast<uintptr_t>(v)) & 15) == 0;
-    int64_t done = 0;  // elements handled by the float4 loop
-    if (vec) {
-        const int64_t full = count / 4;
-        float4 *P4 = reinterpret_cast<float4 *>(p), *M4 = reinterpret_cast<float4 *>(m);
-        float4 *V4 = reinterpret_cast<float4 *>(v);
-        const float4 *G4 = reinterpret_cast<const float4 *>(g);
-        for (int64_t c = t0; c < full; c += 2 * stride) {
-            const int64_t c2 = c + stride;
-            const bool two = c2 < full;
-            float4 P = P4[c], M = M4[c], V = V4[c];
-            const float4 Gr = G4[c];
-            float4 P2 = P, M2 = M, V2 = V, Gr2 = Gr;
-            if (two) {
-                P2 = P4[c2];
-                M2 = M4[c2];
-                V2 = V4[c2];
-                Gr2 = G4[c2];
-            }
+    const int64_t total = G.chunk_off[kGroups];
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < total;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int k = 0;
+        while (k + 1 < kGroups && c >= G.chunk_off[k + 1]) ++k;
+        const int64_t e0 = 4 * (c - G.chunk_off[k]);
+        const int n = (int)min((int64_t)4, G.count[k] - e0);
+        float *p = G.p[k] + e0, *m = G.m[k] + e0, *v = G.v[k] + e0;
+        const float *g = G.g[k] + e0;
+        const float lr = G.lr[k];
+        const bool vec = n == 4 && ((reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(g) |
+                                     reinterpret_cast<uintptr_t>(m) | reinterpret_cast<uintptr_t>(v)) & 15) == 0;
+        if (vec) {
+            float4 P = *reinterpret_cast<float4 *>(p), M = *reinterpret_cast<float4 *>(m);
+            float4 V = *reinterpret_cast<float4 *>(v);
+            const float4 Gr = *reinterpret_cast<const float4 *>(g);
             adam_one(P.x, Gr.x, M.x, V.x, lr, K, bc1, bc2);
             adam_one(P.y, Gr.y, M.y, V.y, lr, K, bc1, bc2);
             adam_one(P.z, Gr.z, M.z, V.z, lr, K, bc1, bc2);
             adam_one(P.w, Gr.w, M.w, V.w, lr, K, bc1, bc2);
-            P4[c] = P;
-            M4[c] = M;
-            V4[c] = V;
-            if (two) {
-                adam_one(P2.x, Gr2.x, M2.x, V2.x, lr, K, bc1, bc2);
-                adam_one(P2.y, Gr2.y, M2.y, V2.y, lr, K, bc1, bc2);
-                adam_one(P2.z, Gr2.z, M2.z, V2.z, lr, K, bc1, bc2);
-                adam_one(P2.w, Gr2.w, M2.w, V2.w, lr, K, bc1, bc2);
-                P4[c2] = P2;
-                M4[c2] = M2;
-                V4[c2] = V2;
-            }
+            *reinterpret_cast<float4 *>(p) = P;
+            *reinterpret_cast<float4 *>(m) = M;
+            *reinterpret_cast<float4 *>(v) = V;
+        } else {
+            for (int j = 0; j < n; ++j) adam_one(p[j], g[j], m[j], v[j], lr, K, bc1, bc2);
         }
-        done = 4 * full;
     }
-    // the rest (the last 1-3 elements, or every element of an unaligned group), scalar
-    for (int64_t e = done + t0; e < count; e += stride) adam_one(p[e], g[e], m[e], v[e], lr, K, bc1, bc2);
 }
 
 }  // namespace
@@ -124,6 +101,7 @@ extern "C" gs_status gs_adam_step(const gs_field_mut *f, const gs_gaussian_grads
     const int64_t M = n * (14 + f->feat_dim);
     AdamGroups G;
     int64_t off = 0;
+    G.chunk_off[0] = 0;
     for (int k = 0; k < kGroups; ++k) {
         G.p[k] = ps[k];
         G.g[k] = gr[k];
@@ -131,6 +109,7 @@ extern "C" gs_status gs_adam_step(const gs_field_mut *f, const gs_gaussian_grads
         G.v[k] = moments + M + off;
         G.count[k] = n * width[k];
         G.lr[k] = lr[k];
+        G.chunk_off[k + 1] = G.chunk_off[k] + (G.count[k] + 3) / 4;
         off += G.count[k];
     }
     AdamCoef K;
@@ -145,9 +124,8 @@ extern "C" gs_status gs_adam_step(const gs_field_mut *f, const gs_gaussian_grads
     K.bc2 = step ? 1.0 - pow(beta2, step) : 0.0;
     cudaStream_t st = (cudaStream_t)stream;
     if (step == 0) adam_count_kernel<<<1, 1, 0, st>>>(step_ctr);
-    int64_t most = 1;
-    for (int k = 0; k < kGroups; ++k) most = std::max(most, (G.count[k] + 7) / 8);
-    const dim3 grid((unsigned)std::min<int64_t>((most + 255) / 256, 152 * 4), kGroups);
+    const int64_t chunks = G.chunk_off[kGroups];
+    const int grid = (int)std::min<int64_t>((chunks + 255) / 256, 152 * 16);
     adam_kernel<<<grid, 256, 0, st>>>(G, K, step ? nullptr : step_ctr);
     return last_launch();
 }
