@@ -35,55 +35,6 @@ __device__ __forceinline__ void adam_one(float &p, float g, float &m, float &v, 
     p -= lr * (m / bc1) / (sqrtf(v / bc2) + k.eps);
 }
 
-// One 4-element chunk of a group: where it is, how many elements, and whether its four
-// arrays allow float4 access.
-struct Chunk {
-    float *p, *m, *v;
-    const float *g;
-    float lr;
-    int n;
-    bool vec;
-};
-
-__device__ __forceinline__ Chunk locate(const AdamGroups &G, int64_t c) {
-    int k = 0;
-    while (k + 1 < kGroups && c >= G.chunk_off[k + 1]) ++k;
-    const int64_t e0 = 4 * (c - G.chunk_off[k]);
-    Chunk r;
-    r.n = (int)min((int64_t)4, G.count[k] - e0);
-    r.p = G.p[k] + e0;
-    r.m = G.m[k] + e0;
-    r.v = G.v[k] + e0;
-    r.g = G.g[k] + e0;
-    r.lr = G.lr[k];
-    r.vec = r.n == 4 && ((reinterpret_cast<uintptr_t>(r.p) | reinterpret_cast<uintptr_t>(r.g) |
-                          reinterpret_cast<uintptr_t>(r.m) | reinterpret_cast<uintptr_t>(r.v)) & 15) == 0;
-    return r;
-}
-
-__device__ __forceinline__ void load4(const Chunk &a, float4 &P, float4 &M, float4 &V, float4 &Gr) {
-    P = *reinterpret_cast<const float4 *>(a.p);
-    M = *reinterpret_cast<const float4 *>(a.m);
-    V = *reinterpret_cast<const float4 *>(a.v);
-    Gr = *reinterpret_cast<const float4 *>(a.g);
-}
-
-// The update of a chunk: from the loaded float4s, or element by element when not vec.
-__device__ __forceinline__ void update(const Chunk &a, float4 &P, float4 &M, float4 &V, const float4 &Gr,
-                                       const AdamCoef &K, float bc1, float bc2) {
-    if (a.vec) {
-        adam_one(P.x, Gr.x, M.x, V.x, a.lr, K, bc1, bc2);
-        adam_one(P.y, Gr.y, M.y, V.y, a.lr, K, bc1, bc2);
-        adam_one(P.z, Gr.z, M.z, V.z, a.lr, K, bc1, bc2);
-        adam_one(P.w, Gr.w, M.w, V.w, a.lr, K, bc1, bc2);
-        *reinterpret_cast<float4 *>(a.p) = P;
-        *reinterpret_cast<float4 *>(a.m) = M;
-        *reinterpret_cast<float4 *>(a.v) = V;
-    } else {
-        for (int j = 0; j < a.n; ++j) adam_one(a.p[j], a.g[j], a.m[j], a.v[j], a.lr, K, bc1, bc2);
-    }
-}
-
 __global__ void __launch_bounds__(256) adam_kernel(AdamGroups G, AdamCoef K, const double *ctr) {
     __shared__ float s_bc[2];
     if (threadIdx.x == 0) {
@@ -99,16 +50,31 @@ __global__ void __launch_bounds__(256) adam_kernel(AdamGroups G, AdamCoef K, con
     __syncthreads();
     const float bc1 = s_bc[0], bc2 = s_bc[1];
     const int64_t total = G.chunk_off[kGroups];
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    // two chunks per iteration, c and c + stride, with their loads issued before either update
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += 2 * stride) {
-        Chunk a = locate(G, c), b = locate(G, c + stride < total ? c + stride : c);
-        const bool two = c + stride < total;
-        float4 Pa, Ma, Va, Ga, Pb, Mb, Vb, Gb;
-        if (a.vec) load4(a, Pa, Ma, Va, Ga);
-        if (two && b.vec) load4(b, Pb, Mb, Vb, Gb);
-        update(a, Pa, Ma, Va, Ga, K, bc1, bc2);
-        if (two) update(b, Pb, Mb, Vb, Gb, K, bc1, bc2);
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < total;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int k = 0;
+        while (k + 1 < kGroups && c >= G.chunk_off[k + 1]) ++k;
+        const int64_t e0 = 4 * (c - G.chunk_off[k]);
+        const int n = (int)min((int64_t)4, G.count[k] - e0);
+        float *p = G.p[k] + e0, *m = G.m[k] + e0, *v = G.v[k] + e0;
+        const float *g = G.g[k] + e0;
+        const float lr = G.lr[k];
+        const bool vec = n == 4 && ((reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(g) |
+                                     reinterpret_cast<uintptr_t>(m) | reinterpret_cast<uintptr_t>(v)) & 15) == 0;
+        if (vec) {
+            float4 P = *reinterpret_cast<float4 *>(p), M = *reinterpret_cast<float4 *>(m);
+            float4 V = *reinterpret_cast<float4 *>(v);
+            const float4 Gr = *reinterpret_cast<const float4 *>(g);
+            adam_one(P.x, Gr.x, M.x, V.x, lr, K, bc1, bc2);
+            adam_one(P.y, Gr.y, M.y, V.y, lr, K, bc1, bc2);
+            adam_one(P.z, Gr.z, M.z, V.z, lr, K, bc1, bc2);
+            adam_one(P.w, Gr.w, M.w, V.w, lr, K, bc1, bc2);
+            *reinterpret_cast<float4 *>(p) = P;
+            *reinterpret_cast<float4 *>(m) = M;
+            *reinterpret_cast<float4 *>(v) = V;
+        } else {
+            for (int j = 0; j < n; ++j) adam_one(p[j], g[j], m[j], v[j], lr, K, bc1, bc2);
+        }
     }
 }
 
