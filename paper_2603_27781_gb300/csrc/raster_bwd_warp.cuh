@@ -11,8 +11,10 @@
 // its pixels blended (back to front, from the mask words), stages 16 splat
 // records at a time in its own shared memory, runs the same per-pixel recurrence
 // and the same deferred contraction of the alpha-T weighted terms, and adds its
-// sums to the per-Gaussian accumulators with vector atomics.  Nothing waits on
-// another warp, and a finished group frees its resources at once.
+// sums to the per-Gaussian accumulators with L2 reductions (one warp-wide scalar
+// instruction for the six geometric sums, float4/float2 ones for the deferred
+// terms).  Nothing waits on another warp, and a finished group frees its
+// resources at once.
 #pragma once
 
 #include "raster_bwd.cuh"
