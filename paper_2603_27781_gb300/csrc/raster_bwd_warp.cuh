@@ -189,15 +189,15 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP>())
     auto process = [&](const int k) {
         const int pos = s_pos[k];
         const SplatGeo s = s_geo[k];
+        // the mask listed this splat because a pixel of the group blended it, so some lane
+        // contributes: no vote is needed before the work
         PairEval e[NP];
-        bool contrib[NP], any = false;
+        bool contrib[NP];
 #pragma unroll
         for (int p = 0; p < NP; ++p) {
             e[p] = eval_pair(s, pxc[p], pyc[p], prm.alpha_min, prm.alpha_max);
             contrib[p] = pos < last[p] && !e[p].skip;
-            any |= contrib[p];
         }
-        if (!__any_sync(0xffffffffu, any)) return;
         float val[8], wv[NP];
 #pragma unroll
         for (int i = 0; i < 8; ++i) val[i] = 0.f;

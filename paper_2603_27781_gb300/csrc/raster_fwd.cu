@@ -109,7 +109,9 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS, fwd_min_blocks(D, NP)) ras
             uint32_t lbits = 0u;
             const int k_end = min(c0 + 32, nb);
             for (int k = max(c0, k_lo); k < k_end; ++k) {
-                if (__all_sync(0xffffffffu, all_done())) { finished = true; break; }
+                // every 4th splat: are all of the warp's pixels done? (a later exit only runs
+                // splats whose pairs blend nothing)
+                if (((k - c0) & 3) == 0 && __all_sync(0xffffffffu, all_done())) { finished = true; break; }
                 const SplatGeo s = s_geo[k];
                 if (!reaches_box(s.u, s.v, s_ext[k], bcx, bcy, hx, hy)) continue;
                 float al[NP];
