@@ -11,7 +11,9 @@
 // A stable sort by tile of a depth-ordered, index-tie-broken stream is exactly
 // the (tile, depth, index) order.
 //
-// Each radix pass is one kernel: a block ranks its 2048 keys stably within the
+// The digit histograms of every pass are counted by the kernels that write the keys (the
+// compaction for the depth keys, the emission for the tile keys), one warp-aggregated
+// shared-memory atomic per distinct digit.  Each radix pass is one kernel: a block ranks its 2048 keys stably within the
 // block (warp match + per-warp digit counters), publishes its per-digit
 // counts, finds its global offsets by a chained look-back over earlier blocks,
 // and scatters through shared memory.  Blocks take tile numbers from an atomic
@@ -111,9 +113,36 @@ __global__ void __launch_bounds__(1024) blocksum_scan_kernel(uint32_t *block_sum
     }
 }
 
+// Adds the 8-bit digits of passes [0, n_passes) of `key` (lanes with `valid`) to the block's
+// shared histograms, one atomic per distinct digit per warp.  Every lane of the warp calls it.
+__device__ __forceinline__ void hist_add(uint32_t (*sh)[256], int n_passes, bool valid, uint32_t key) {
+    const uint32_t mask = __ballot_sync(0xffffffffu, valid);
+    if (!valid) return;
+    const int lane = threadIdx.x & 31;
+    for (int p = 0; p < n_passes; ++p) {
+        const uint32_t d = (key >> (8 * p)) & 255u;
+        const uint32_t peers = __match_any_sync(mask, d);
+        if (lane == __ffs(peers) - 1) atomicAdd(&sh[p][d], __popc(peers));
+    }
+}
+
+// Adds the block's shared histograms into the global ones (zero counts skipped).
+__device__ __forceinline__ void hist_flush(uint32_t (*sh)[256], int n_passes, uint32_t *hist) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < n_passes * 256; i += blockDim.x) {
+        const uint32_t c = (&sh[0][0])[i];
+        if (c) atomicAdd(&hist[i], c);
+    }
+}
+
+// Order-preserving compaction of the visible items with their depth keys; also the digit
+// histograms of the depth sort's four passes (no separate pass over the keys).
 __global__ void __launch_bounds__(256) vis_compact_kernel(const int32_t *touched, const float4 *uvdo, int64_t count,
-                                                          const uint32_t *block_sums, uint32_t *keys, uint32_t *vals) {
+                                                          const uint32_t *block_sums, uint32_t *keys, uint32_t *vals,
+                                                          uint32_t *hist) {
     __shared__ uint32_t s_warp[9];
+    __shared__ uint32_t sh[4][256];
+    for (int i = threadIdx.x; i < 4 * 256; i += 256) (&sh[0][0])[i] = 0u;
     int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanIPT;
     bool f[kScanIPT];
     uint32_t c = 0;
@@ -125,12 +154,16 @@ __global__ void __launch_bounds__(256) vis_compact_kernel(const int32_t *touched
     uint32_t tot;
     uint32_t off = block_sums[blockIdx.x] + block_exclusive_scan(c, &tot, s_warp);
 #pragma unroll
-    for (int k = 0; k < kScanIPT; ++k)
+    for (int k = 0; k < kScanIPT; ++k) {
+        const uint32_t key = f[k] ? __float_as_uint(uvdo[base + k].z) : 0u;
         if (f[k]) {
-            keys[off] = __float_as_uint(uvdo[base + k].z);
+            keys[off] = key;
             vals[off] = (uint32_t)(base + k);
             ++off;
         }
+        hist_add(sh, 4, f[k], key);
+    }
+    hist_flush(sh, 4, hist);
 }
 
 // ------------------------------------------------------------ instance emission
@@ -154,14 +187,18 @@ __global__ void __launch_bounds__(kEmitBlock) emit_reduce_kernel(const uint32_t 
 // per round (the owner of instance q is found by a 5-step binary search over
 // the lanes' offsets), so every store is coalesced and long items are spread
 // over the warp.
+// Also the digit histograms of the tile sort's n_passes passes over the written keys.
 __global__ void __launch_bounds__(kEmitBlock) emit_kernel(ViewTable vt, const uint32_t *sorted_items,
                                                           const int32_t *touched, const float4 *uvdo,
                                                           const float4 *conic, const uint32_t *counters,
                                                           const uint32_t *block_sums, int64_t capacity,
-                                                          uint32_t *tile_keys, uint32_t *inst_vals) {
+                                                          uint32_t *tile_keys, uint32_t *inst_vals, int n_passes,
+                                                          uint32_t *hist) {
     __shared__ uint32_t s_warp[9];
+    __shared__ uint32_t sh[4][256];
     const int64_t count = counters[CTR_NVIS];
-    if ((int64_t)blockIdx.x * kEmitBlock >= count) return;
+    if ((int64_t)blockIdx.x * kEmitBlock >= count) return;  // whole block: no barrier is skipped by part of it
+    for (int i = threadIdx.x; i < 4 * 256; i += kEmitBlock) (&sh[0][0])[i] = 0u;
     const int lane = threadIdx.x & 31;
     const int64_t i = (int64_t)blockIdx.x * kEmitBlock + threadIdx.x;
     uint32_t item = 0, c = 0;
@@ -198,46 +235,21 @@ __global__ void __launch_bounds__(kEmitBlock) emit_kernel(ViewTable vt, const ui
         const int o_w = __shfl_sync(0xffffffffu, w, owner), o_tx = __shfl_sync(0xffffffffu, tx, owner);
         const uint32_t o_tb = __shfl_sync(0xffffffffu, tb, owner);
         const int64_t off = (int64_t)wbase + q;
-        if (q < wtotal && off < capacity) {
+        const bool write = q < wtotal && off < capacity;
+        uint32_t key = 0u;
+        if (write) {
             const int k = (int)(q - o_rel);
             const int ky = k / o_w, kx = k - ky * o_w;
-            tile_keys[off] = o_tb + (uint32_t)((o_y0 + ky) * o_tx + o_x0 + kx);
+            key = o_tb + (uint32_t)((o_y0 + ky) * o_tx + o_x0 + kx);
+            tile_keys[off] = key;
             inst_vals[off] = o_item;
         }
+        hist_add(sh, n_passes, write, key);
     }
+    hist_flush(sh, n_passes, hist);
 }
 
 // ------------------------------------------------------------------ radix sort
-// Digit histograms of every pass in one read of the keys.
-__global__ void __launch_bounds__(256) radix_hist_kernel(const uint32_t *keys, const uint32_t *count_ptr,
-                                                         int n_passes, uint32_t *hist) {
-    __shared__ uint32_t sh[4][256];
-    for (int i = threadIdx.x; i < 4 * 256; i += 256) (&sh[0][0])[i] = 0;
-    __syncthreads();
-    int64_t n = *count_ptr;
-    int lane = threadIdx.x & 31;
-    int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t wb = warp * 32; wb < n; wb += nwarps * 32) {
-        int64_t i = wb + lane;
-        bool valid = i < n;
-        uint32_t mask = __ballot_sync(0xffffffffu, valid);
-        if (valid) {
-            uint32_t k = keys[i];
-            for (int p = 0; p < n_passes; ++p) {
-                uint32_t d = (k >> (8 * p)) & 255u;
-                uint32_t peers = __match_any_sync(mask, d);
-                if (lane == __ffs(peers) - 1) atomicAdd(&sh[p][d], __popc(peers));
-            }
-        }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < n_passes * 256; i += 256) {
-        uint32_t c = (&sh[0][0])[i];
-        if (c) atomicAdd(&hist[i], c);
-    }
-}
-
 __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint32_t *keys_in, const uint32_t *vals_in,
                                                                 uint32_t *keys_out, uint32_t *vals_out,
                                                                 const uint32_t *count_ptr, int shift,
@@ -378,14 +390,13 @@ struct SortBufs {
     uint32_t *k0, *v0, *k1, *v1;
 };
 
-// Stable LSD sort of (key, val) pairs by `n_passes` 8-bit digits from bit 0.
-// Input in (k0, v0); output lands in (k0, v0) if n_passes is even, else (k1, v1).
-gs_status radix_sort(SortBufs b, const uint32_t *count_ptr, int64_t max_count, int n_passes, uint32_t *hist,
+// Stable LSD sort of (key, val) pairs by `n_passes` 8-bit digits from bit 0, given the
+// digit histograms of every pass (hist [n_passes][256], written by the kernel that
+// produced the keys).  Input in (k0, v0); output lands in (k0, v0) if n_passes is even,
+// else (k1, v1).
+gs_status radix_sort(SortBufs b, const uint32_t *count_ptr, int64_t max_count, int n_passes, const uint32_t *hist,
                      uint32_t *lookback, int lb_tiles, uint32_t *tile_ctrs, int32_t *status, cudaStream_t st) {
     if (max_count <= 0 || n_passes <= 0) return GS_OK;
-    int grid_h = ceil_div(max_count, 256 * 8);
-    if (grid_h > 152 * 8) grid_h = 152 * 8;
-    radix_hist_kernel<<<grid_h, 256, 0, st>>>(b.k0, count_ptr, n_passes, hist);
     int grid = ceil_div(max_count, kSortTile);
     uint32_t *ki = b.k0, *vi = b.v0, *ko = b.k1, *vo = b.v1;
     for (int p = 0; p < n_passes; ++p) {
@@ -502,7 +513,7 @@ extern "C" gs_status gs_bin_sort(int64_t n, const gs_projected *proj, const gs_c
     vis_reduce_kernel<<<nb, 256, 0, st>>>(proj->tiles_touched, vn, block_sums);
     blocksum_scan_kernel<<<1, 1024, 0, st>>>(block_sums, nullptr, nb, kScanBlock, counters, CTR_NVIS, -1, 0, nullptr,
                                              nullptr);
-    vis_compact_kernel<<<nb, 256, 0, st>>>(proj->tiles_touched, uvdo, vn, block_sums, dk_a, dv_a);
+    vis_compact_kernel<<<nb, 256, 0, st>>>(proj->tiles_touched, uvdo, vn, block_sums, dk_a, dv_a, hist);
     if ((s = last_launch())) return s;
 
     // 2. stable sort of the visible items by depth (4 passes: result in dk_a/dv_a)
@@ -525,7 +536,7 @@ extern "C" gs_status gs_bin_sort(int64_t n, const gs_projected *proj, const gs_c
     blocksum_scan_kernel<<<1, 1024, 0, st>>>(block_sums, counters + CTR_NVIS, 0, kEmitBlock, counters, CTR_MRAW, CTR_M,
                                              out->capacity, out->n_inst, out->status);
     emit_kernel<<<nbe, kEmitBlock, 0, st>>>(vt, sorted_items, proj->tiles_touched, uvdo, conic, counters, block_sums,
-                                    out->capacity, tk_a, emit_vals);
+                                    out->capacity, tk_a, emit_vals, tile_passes, hist + 4 * 256);
     if ((s = last_launch())) return s;
     if (out->capacity == 0) return write_tile_order(out, total_tiles, st);
 
