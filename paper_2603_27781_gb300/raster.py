@@ -352,12 +352,12 @@ class Renderer:
 
 def fit_capacity(field: Field, cams, feat_dim: int, margin: float = 1.25, params: RasterParams = RasterParams(),
                  n_classes: int = 0, device="cuda") -> Renderer:
-    """Builds a Renderer whose instance capacity fits this field and these views."""
-    probe = Renderer(field.n, cams, feat_dim, 0, device, params, n_classes)
-    probe.project(field)
-    need = int(probe.touched.sum(dtype=torch.int64).item())
-    cap = max(1024, int(need * margin))
-    return Renderer(field.n, cams, feat_dim, cap, device, params, n_classes)
+    """Builds a Renderer whose instance capacity fits this field and these views (the
+    instances of one projection, times the margin)."""
+    r = Renderer(field.n, cams, feat_dim, 0, device, params, n_classes)
+    need = int(r.instances_needed(field).item())
+    r.ensure_capacity(max(1024, int(need * margin)))
+    return r
 
 
 # supplementary C.1 mapping learning rates, in the update's group order:
