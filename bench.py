@@ -260,9 +260,8 @@ class FormJob:
         r.loss(self.targets, self.W, self.b, w)
         r.render_bwd(f, self.mode)
         r.project_bwd(f, self.mode)
-        r.pose_grad()
-        r.dsr(f, w.big, w.small)
-        r.pose_step(self.T_state, self.adam, 0, pose_f32=self.pose_f32)
+        r.side_by_side(lambda s: r.dsr(f, w.big, w.small, s),
+                       lambda: (r.pose_grad(), r.pose_step(self.T_state, self.adam, 0, pose_f32=self.pose_f32)))
 
 
 def time_graph(jobs, steps, flush):
@@ -602,9 +601,9 @@ def run_ours(args, rank, world, local_rank):
         rec(5)
         r.project_bwd(f, mode)
         rec(6)
-        r.pose_grad()
-        r.dsr(f, w.big, w.small)
-        r.pose_step(T_state, adam, 0, pose_f32=pose_f32)
+        # the DSR on the renderer's side stream beside the twist reduction and the pose step
+        r.side_by_side(lambda s: r.dsr(f, w.big, w.small, s),
+                       lambda: (r.pose_grad(), r.pose_step(T_state, adam, 0, pose_f32=pose_f32)))
         rec(7)
 
     stages = ["project", "bin_sort", "render_fwd", "loss", "render_bwd", "project_bwd", "pose+dsr+step"]

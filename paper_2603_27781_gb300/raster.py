@@ -327,12 +327,33 @@ class Renderer:
     def iteration(self, field: Field, targets, decoder_W, decoder_b, w: LossWeights, grad_mode=L.GS_GRAD_MAP,
                   pose_dev=None, stream=None):
         """One fwd+bwd pass of the whole path: project, bin/sort, blend, loss, blend and
-        projection backward, pose-twist reduction, DSR.  Asynchronous."""
+        projection backward, pose-twist reduction, DSR.  Asynchronous.  With both the twist and
+        the DSR to do, the DSR (which needs only the log-scale gradient the projection backward
+        has written) runs on a side stream beside the twist reduction and rejoins the stream
+        before the call returns (also inside a CUDA-graph capture)."""
         self.forward(field, pose_dev, stream)
         self.loss(targets, decoder_W, decoder_b, w, stream)
-        self.backward(field, grad_mode, pose_dev, stream)
-        if (grad_mode & L.GS_GRAD_MAP) and (w.big or w.small):
-            self.dsr(field, w.big, w.small, stream)
+        dsr = (grad_mode & L.GS_GRAD_MAP) and (w.big or w.small)
+        if not (dsr and grad_mode & L.GS_GRAD_POSE):
+            self.backward(field, grad_mode, pose_dev, stream)
+            if dsr:
+                self.dsr(field, w.big, w.small, stream)
+            return
+        self.render_bwd(field, grad_mode, stream)
+        self.project_bwd(field, grad_mode, pose_dev, stream)
+        self.side_by_side(lambda s: self.dsr(field, w.big, w.small, s), lambda: self.pose_grad(stream), stream)
+
+    def side_by_side(self, side_work, main_work, stream=None):
+        """Runs side_work(side_stream) on the renderer's side stream after everything issued
+        so far on `stream`, main_work() on `stream`, and makes `stream` wait for both."""
+        main = stream if stream is not None else torch.cuda.current_stream(self.device)
+        if getattr(self, "_side", None) is None:
+            self._side = torch.cuda.Stream(self.device)
+        self._side.wait_stream(main)
+        with torch.cuda.stream(self._side):
+            side_work(self._side)
+        main_work()
+        main.wait_stream(self._side)
 
     def status(self) -> int:
         """Device status word of the last binning (0 = ok); synchronises."""
