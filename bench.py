@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--form-steps", type=int, default=10)
@@ -659,13 +659,21 @@ def run_ours(args, rank, world, local_rank):
     # ---- end to end through the API: every step uploads its inputs (the field's parameters and
     # the targets) from pinned host memory and brings its results (every gradient, the loss, the
     # DSR terms, the twist) back to pinned host memory; HostStepper overlaps each step's
-    # transfers with the neighbouring steps' compute (two input and two result sets)
+    # transfers with the neighbouring steps' compute (two input and two result sets, the
+    # renderer's result tensors rebound to the set of each step)
     host = {k: getattr(field, k).cpu().pin_memory() for k in
             ("means", "quats", "log_scales", "opacity_logits", "rgb", "feat")}
     host_t = {k: v.cpu().pin_memory() for k, v in targets.items()}
     outs = [r.d_means, r.d_quats, r.d_log_scales, r.d_logits, r.d_rgb, r.d_feat, r.loss_out, r.dsr_out,
             r.d_twist]
-    stepper = raster.HostStepper(field, targets, outs)
+    # two result sets the steps alternate between, downloaded straight from the one just written
+    names = ("d_means", "d_quats", "d_log_scales", "d_logits", "d_rgb", "d_feat", "loss_out", "dsr_out", "d_twist")
+    sets = [{k: getattr(r, k) for k in r.OUTPUTS}, r.output_set()]
+
+    def bind(k):
+        r.bind_outputs(sets[k])
+        return [sets[k][n] for n in names]
+    stepper = raster.HostStepper(field, targets, outs, bind=bind)
     h2d, d2h = stepper.bytes_in, stepper.bytes_out
     e2e_ms = []
     if args.e2e_steps > 0:
@@ -679,6 +687,7 @@ def run_ours(args, rank, world, local_rank):
         e1.record(stepper.d2h)
         e1.synchronize()
         e2e_ms = [e0.elapsed_time(e1) / n_e2e]
+    r.bind_outputs(sets[0])
     e2e_value = job_rate(float(np.mean(e2e_ms)), world, dev)[1] if e2e_ms else None
 
     # ---- roofline of the dominant kernel (from the per-stage events of the timed steps)

@@ -180,6 +180,18 @@ class Renderer:
         self.d_dec_b = torch.zeros(K, dtype=f32, device=dev)
         self.prm_c = params.c()
 
+    OUTPUTS = ("d_means", "d_quats", "d_log_scales", "d_logits", "d_rgb", "d_feat", "d_dec_W", "d_dec_b",
+               "d_twist", "loss_out", "dsr_out")
+
+    def output_set(self) -> dict:
+        """A new set of the step's result tensors (gradients, losses) shaped like the bound one."""
+        return {k: torch.zeros_like(getattr(self, k)) for k in self.OUTPUTS}
+
+    def bind_outputs(self, outs: dict):
+        """Makes the following calls write their results into `outs` (an output_set())."""
+        for k, t in outs.items():
+            setattr(self, k, t)
+
     def set_n(self, n: int):
         """Serves a field of n <= n_cap Gaussians with the buffers already allocated (every
         per-Gaussian buffer keeps its n_cap rows; the calls use the first n)."""
@@ -576,17 +588,20 @@ class HostStepper:
     whose results (device tensors the step writes) go back to pinned host memory, with each
     step's transfers overlapped with its neighbours' compute: step i's upload runs on a copy
     stream into one of two device input sets while step i-1 computes, and step i's results
-    are copied on the device to one of two staging sets, then downloaded on a second copy
-    stream while step i+1 computes.  `step(field, targets)` issues one step on the current
-    stream; `outputs` are the tensors it writes."""
+    are downloaded on a second copy stream while step i+1 computes.  `step(field, targets)`
+    issues one step on the current stream; `outputs` are the tensors it writes.  With
+    `bind`, bind(k) makes the next step write output set k (k = 0, 1) and returns that set's
+    tensors, and the results are downloaded from there; without it they are first copied on
+    the device into one of two staging sets."""
 
-    def __init__(self, like_field: Field, like_targets: dict, outputs: Sequence[torch.Tensor]):
+    def __init__(self, like_field: Field, like_targets: dict, outputs: Sequence[torch.Tensor], bind=None):
         dev = like_field.means.device
         clone = lambda t: torch.empty_like(t)
         self.fields = [Field(*(clone(getattr(like_field, k)) for k in _FIELD_ARRAYS)) for _ in range(2)]
         self.targets = [{k: clone(v) for k, v in like_targets.items()} for _ in range(2)]
         self.outputs = list(outputs)
-        self.staging = [[clone(o) for o in self.outputs] for _ in range(2)]
+        self.bind = bind
+        self.staging = None if bind is not None else [[clone(o) for o in self.outputs] for _ in range(2)]
         self.host_out = [[torch.empty(o.shape, dtype=o.dtype, pin_memory=True) for o in self.outputs]
                          for _ in range(2)]
         self.h2d, self.d2h = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
@@ -617,12 +632,20 @@ class HostStepper:
                     tg[k].copy_(v, non_blocking=True)
                 self.uploaded[buf].record(self.h2d)
             compute.wait_event(self.uploaded[buf])
-            step(f, tg)
-            # results to staging set buf once step i-2's download from it is done
-            if i >= 2:
-                compute.wait_event(self.downloaded[buf])
-            for s, o in zip(self.staging[buf], self.outputs):
-                s.copy_(o, non_blocking=True)
+            if self.bind is not None:
+                # the step writes output set buf once step i-2's download from it is done
+                if i >= 2:
+                    compute.wait_event(self.downloaded[buf])
+                results = self.bind(buf)
+                step(f, tg)
+            else:
+                step(f, tg)
+                # results to staging set buf once step i-2's download from it is done
+                if i >= 2:
+                    compute.wait_event(self.downloaded[buf])
+                for s, o in zip(self.staging[buf], self.outputs):
+                    s.copy_(o, non_blocking=True)
+                results = self.staging[buf]
             self.computed[buf].record(compute)
             # host buffer buf is free once step i-2's results were handed over
             if pending[buf] is not None:
@@ -631,7 +654,7 @@ class HostStepper:
                     on_result(pending[buf], self.host_out[buf])
             self.d2h.wait_event(self.computed[buf])
             with torch.cuda.stream(self.d2h):
-                for h, s in zip(self.host_out[buf], self.staging[buf]):
+                for h, s in zip(self.host_out[buf], results):
                     h.copy_(s, non_blocking=True)
                 self.downloaded[buf].record(self.d2h)
             pending[buf] = i

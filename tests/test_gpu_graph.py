@@ -221,12 +221,22 @@ def test_host_stepper_overlapped_steps_match_sequential_ones():
         f = raster.Field(*(hf[k].cuda() for k in ("means", "quats", "log_scales", "opacity_logits", "rgb", "feat")))
         step(f, {k: v.cuda() for k, v in ht.items()})
         want.append([o.clone().cpu() for o in outs])
-    got = {}
-    stepper = raster.HostStepper(field, tg0, outs)
-    n = stepper.run(step, inputs, on_result=lambda i, host: got.__setitem__(i, [h.clone() for h in host]))
-    assert n == 4 and sorted(got) == [0, 1, 2, 3]
-    for i in range(4):
-        for a, w_ in zip(got[i], want[i]):
-            if not torch.equal(a, w_):          # float atomics may add in another order
-                C.assert_grad_close(f"step {i}", a.numpy().astype(np.float64), w_.numpy().astype(np.float64), 1e-5)
-    assert not torch.equal(got[0][-1], got[1][-1])          # the steps differ
+    names = ("d_means", "d_log_scales", "d_rgb", "d_feat", "loss_out")
+    sets = [{k: getattr(r, k) for k in r.OUTPUTS}, r.output_set()]
+
+    def bind(k):
+        r.bind_outputs(sets[k])
+        return [sets[k][nm] for nm in names]
+
+    for use_bind in (False, True):       # staged results, then two alternating result sets
+        got = {}
+        stepper = raster.HostStepper(field, tg0, outs, bind=bind if use_bind else None)
+        n = stepper.run(step, inputs, on_result=lambda i, host: got.__setitem__(i, [h.clone() for h in host]))
+        r.bind_outputs(sets[0])
+        assert n == 4 and sorted(got) == [0, 1, 2, 3]
+        for i in range(4):
+            for a, w_ in zip(got[i], want[i]):
+                if not torch.equal(a, w_):          # float atomics may add in another order
+                    C.assert_grad_close(f"step {i}", a.numpy().astype(np.float64), w_.numpy().astype(np.float64),
+                                        1e-5)
+        assert not torch.equal(got[0][-1], got[1][-1])          # the steps differ
