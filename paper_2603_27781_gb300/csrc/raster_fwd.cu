@@ -1,7 +1,8 @@
 // Forward blend (GS3LAM Eq. 4-7 and 10): one CTA per 16x16 tile, NP pixels per
 // thread.  Splats of the tile are staged 128 at a time in shared memory (one
-// record per thread load) and read back as broadcasts; a warp skips a splat
-// whose alpha >= alpha_min region misses its pixel box; every pixel walks the
+// record per thread load) and read back as broadcasts; a warp tests 32 splats at
+// a time (one per lane, one ballot) for whether their alpha >= alpha_min region
+// reaches its pixel box, and walks only those that do; every pixel walks the
 // rest front to back and stops at the T_min threshold; the CTA leaves as soon
 // as all of its pixels are done.  With a blend mask, each warp also records, per
 // 8x4 pixel group and 32-instance word, which splats any pixel of it blended.
@@ -107,13 +108,21 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS, fwd_min_blocks(D, NP)) ras
         const int nb = min((uint32_t)kBatch, end - b0);
         for (int c0 = k_lo & ~31; c0 < nb && !finished; c0 += 32) {
             uint32_t lbits = 0u;
-            const int k_end = min(c0 + 32, nb);
-            for (int k = max(c0, k_lo); k < k_end; ++k) {
-                // every 4th splat: are all of the warp's pixels done? (a later exit only runs
-                // splats whose pairs blend nothing)
-                if (((k - c0) & 3) == 0 && __all_sync(0xffffffffu, all_done())) { finished = true; break; }
+            // the chunk's splats in [k_lo, nb) that can reach the warp's box, lane k - c0
+            // testing splat k
+            const int kl = c0 + lane;
+            bool reach = false;
+            if (kl >= k_lo && kl < nb) {
+                reach = reaches_box(s_geo[kl].u, s_geo[kl].v, s_ext[kl], bcx, bcy, hx, hy);
+            }
+            uint32_t todo = __ballot_sync(0xffffffffu, reach);
+            for (int n_run = 0; todo; ++n_run) {
+                const int k = c0 + __ffs(todo) - 1;
+                todo &= todo - 1;
+                // every 4th splat walked: are all of the warp's pixels done? (a later exit only
+                // runs splats whose pairs blend nothing)
+                if ((n_run & 3) == 0 && __all_sync(0xffffffffu, all_done())) { finished = true; break; }
                 const SplatGeo s = s_geo[k];
-                if (!reaches_box(s.u, s.v, s_ext[k], bcx, bcy, hx, hy)) continue;
                 float al[NP];
                 bool ok[NP];
 #pragma unroll
@@ -201,7 +210,6 @@ __global__ void __launch_bounds__(32, fwd_group_min_blocks(D, NP)) raster_fwd_gr
     constexpr int D4 = D / 4, DD = D > 0 ? D : 1;
     constexpr int GW = SH::WARPS;  // pixel-group blocks per tile
     __shared__ SplatGeo s_geo[32];
-    __shared__ float2 s_ext[32];
     __shared__ float4 s_rgbd[32];
     __shared__ float4 s_feat[32 * (D4 > 0 ? D4 : 1)];
 
@@ -246,6 +254,8 @@ __global__ void __launch_bounds__(32, fwd_group_min_blocks(D, NP)) raster_fwd_gr
     };
     for (uint32_t b0 = start & ~31u; b0 < end; b0 += 32) {
         if (__all_sync(0xffffffffu, all_done())) break;
+        // lane k stages splat b0 + k and tests whether it can reach the group's box
+        bool reach = false;
         {
             const uint32_t j = b0 + lane;
             if (j >= start && j < end) {
@@ -254,20 +264,20 @@ __global__ void __launch_bounds__(32, fwd_group_min_blocks(D, NP)) raster_fwd_gr
                 const float4 a = uvdo[item];
                 const float4 c = conic[item];
                 s_geo[lane] = make_geo(a, uv_lo[item], c);
-                s_ext[lane] = splat_extent(c, a.w, prm.alpha_min);
+                reach = reaches_box(a.x, a.y, splat_extent(c, a.w, prm.alpha_min), bcx, bcy, hx, hy);
                 s_rgbd[lane] = load_rgbd(rgb, g, a.z);
 #pragma unroll
                 for (int q = 0; q < D4; ++q) s_feat[lane * D4 + q] = load_feat4(feat, g * D + 4 * q);
             }
         }
+        uint32_t todo = __ballot_sync(0xffffffffu, reach);
         __syncwarp();
-        const int k_lo = b0 < start ? (int)(start - b0) : 0;
-        const int nb = (int)min(32u, end - b0);
         uint32_t lbits = 0u;
-        for (int k = k_lo; k < nb; ++k) {
-            if (__all_sync(0xffffffffu, all_done())) break;
+        for (int n_run = 0; todo; ++n_run) {
+            const int k = __ffs(todo) - 1;
+            todo &= todo - 1;
+            if ((n_run & 3) == 0 && __all_sync(0xffffffffu, all_done())) break;
             const SplatGeo sg = s_geo[k];
-            if (!reaches_box(sg.u, sg.v, s_ext[k], bcx, bcy, hx, hy)) continue;
             float al[NP];
             bool ok[NP];
 #pragma unroll
