@@ -69,7 +69,7 @@ extern "C" gs_status gs_render_bwd(const gs_gaussians *g, const gs_projected *pr
     const bool group_ok = (D == 16 || D == 32) && A.bmask && prm.bwd_np <= 2;
     Params pr = prm;
     pr.bwd_warp = prm.bwd_blocks == GS_BWD_BLOCKS_GROUP || (prm.bwd_blocks == GS_BWD_BLOCKS_DEFAULT && group_ok);
-    // default pixels per thread: 2 for the per-group form at D = 16 (16x4 bands), else 1
+    // default pixels per thread: 2 for the per-group form at D = 16 (8x8 blocks), else 1
     const int np = prm.bwd_np ? prm.bwd_np : (pr.bwd_warp ? (D == 16 ? 2 : 1) : default_bwd_np(D));
     const bool half = g->rgb_dtype == GS_F16;
     return map ? dispatch_bwd_map(D, np, half, vt, pr, A, st) : dispatch_bwd_pose(D, np, half, vt, pr, A, st);

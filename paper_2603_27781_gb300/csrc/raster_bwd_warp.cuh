@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP>())
     for (int64_t wi = (hi_i - 1) >> 5; wi >= (lo_i >> 5); --wi) {
         uint32_t m = 0u;
 #pragma unroll
-        for (int j = 0; j < NP; ++j) m |= A.bmask[(int64_t)(grp * NP + j) * A.bm_stride + wi];
+        for (int j = 0; j < NP; ++j) m |= A.bmask[(int64_t)SH::group(grp, j) * A.bm_stride + wi];
         const int64_t base = wi << 5;
         if (base < lo_i) m &= ~0u << (int)(lo_i - base);
         if (hi_i - base < 32) m &= (1u << (int)(hi_i - base)) - 1u;

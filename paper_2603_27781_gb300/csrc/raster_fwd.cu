@@ -25,8 +25,9 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS, fwd_min_blocks(D, NP)) ras
     const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges, int64_t P, float *o_rgb, float *o_depth,
     float *o_sil, float *o_feat, float *o_T, int32_t *o_nc, int32_t *o_nb, uint32_t *bmask, int64_t bm_stride,
     const uint32_t *__restrict__ order) {
-    using SH = Shape<NP>;
+    using SH = Shape<NP, true>;  // 16x4 bands at NP = 2 (measured faster here than 8x8 blocks)
     constexpr int NT = SH::THREADS;
+    constexpr int NL = SH::PIX_GROUPS ? NP : 1;  // mask bit registers per thread
     constexpr int D4 = D / 4, DD = D > 0 ? D : 1;
     __shared__ SplatGeo s_geo[kBatch];
     __shared__ float2 s_ext[kBatch];
@@ -71,16 +72,17 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS, fwd_min_blocks(D, NP)) ras
         return a;
     };
     // blend-mask bits: batches start on 32-instance boundaries, so each 32-splat
-    // chunk of a batch is one word of the mask; a lane ORs "one of my pixels
-    // blended splat k" into a register and the warp combines the lanes of each
-    // of its NP groups at the end of the chunk
+    // chunk of a batch is one word of the mask; a lane ORs "my pixel(s) of group j
+    // blended splat k" into a register (one per group its pixels lie in) and the
+    // warp combines the lanes of each of its NP groups at the end of the chunk
     const int warp = tid >> 5, lane = tid & 31;
-    auto flush = [&](uint32_t lbits, uint32_t word_idx) {
+    auto flush = [&](const uint32_t (&lbits)[NL], uint32_t word_idx) {
 #pragma unroll
         for (int j = 0; j < NP; ++j) {
-            const uint32_t mine = (lanes_of_group<NP>(j) >> lane) & 1u ? lbits : 0u;
+            const uint32_t mine =
+                SH::PIX_GROUPS ? lbits[j % NL] : ((SH::lanes_of_group(j) >> lane) & 1u ? lbits[0] : 0u);
             const uint32_t word = __reduce_or_sync(0xffffffffu, mine);
-            if (lane == 0 && word) atomicOr(&bmask[(int64_t)(warp * NP + j) * bm_stride + word_idx], word);
+            if (lane == 0 && word) atomicOr(&bmask[(int64_t)SH::group(warp, j) * bm_stride + word_idx], word);
         }
     };
 
@@ -107,7 +109,9 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS, fwd_min_blocks(D, NP)) ras
         const int k_lo = b0 < start ? (int)(start - b0) : 0;
         const int nb = min((uint32_t)kBatch, end - b0);
         for (int c0 = k_lo & ~31; c0 < nb && !finished; c0 += 32) {
-            uint32_t lbits = 0u;
+            uint32_t lbits[NL];
+#pragma unroll
+            for (int j = 0; j < NL; ++j) lbits[j] = 0u;
             // the chunk's splats in [k_lo, nb) that can reach the warp's box, lane k - c0
             // testing splat k
             const int kl = c0 + lane;
@@ -145,8 +149,9 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS, fwd_min_blocks(D, NP)) ras
                     last[p] = b ? pos : last[p];
                     blended[p] += b ? 1 : 0;
                     any = any || b;
+                    if (SH::PIX_GROUPS) lbits[p % NL] |= (b ? 1u : 0u) << (k & 31);
                 }
-                lbits |= (any ? 1u : 0u) << (k & 31);
+                if (!SH::PIX_GROUPS) lbits[0] |= (any ? 1u : 0u) << (k & 31);
                 if (!any) continue;
                 const float4 c = s_rgbd[k];
 #pragma unroll
@@ -191,7 +196,7 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS, fwd_min_blocks(D, NP)) ras
 }
 
 // The same blend with one 32-thread block per pixel group (an 8x4 group with one pixel
-// per thread, a 16x4 band with two): the group stages the tile's splats 32 at a time in
+// per thread, an 8x8 block with two): the group stages the tile's splats 32 at a time in
 // its own shared memory, so it never waits at a barrier for the tile's other groups, and
 // it leaves as soon as its own pixels are done, freeing its registers and shared memory.
 // Arithmetic, order and outputs are those of raster_fwd_kernel.
@@ -208,6 +213,7 @@ __global__ void __launch_bounds__(32, fwd_group_min_blocks(D, NP)) raster_fwd_gr
     const uint32_t *__restrict__ order) {
     using SH = Shape<NP>;
     constexpr int D4 = D / 4, DD = D > 0 ? D : 1;
+    constexpr int NL = SH::PIX_GROUPS ? NP : 1;  // mask bit registers per thread
     constexpr int GW = SH::WARPS;  // pixel-group blocks per tile
     __shared__ SplatGeo s_geo[32];
     __shared__ float4 s_rgbd[32];
@@ -272,7 +278,9 @@ __global__ void __launch_bounds__(32, fwd_group_min_blocks(D, NP)) raster_fwd_gr
         }
         uint32_t todo = __ballot_sync(0xffffffffu, reach);
         __syncwarp();
-        uint32_t lbits = 0u;
+        uint32_t lbits[NL];
+#pragma unroll
+        for (int j = 0; j < NL; ++j) lbits[j] = 0u;
         for (int n_run = 0; todo; ++n_run) {
             const int k = __ffs(todo) - 1;
             todo &= todo - 1;
@@ -300,8 +308,9 @@ __global__ void __launch_bounds__(32, fwd_group_min_blocks(D, NP)) raster_fwd_gr
                 last[p] = b ? pos : last[p];
                 blended[p] += b ? 1 : 0;
                 any = any || b;
+                if (SH::PIX_GROUPS) lbits[p % NL] |= (b ? 1u : 0u) << k;
             }
-            lbits |= (any ? 1u : 0u) << k;
+            if (!SH::PIX_GROUPS) lbits[0] |= (any ? 1u : 0u) << k;
             if (!any) continue;
             const float4 c = s_rgbd[k];
 #pragma unroll
@@ -330,9 +339,10 @@ __global__ void __launch_bounds__(32, fwd_group_min_blocks(D, NP)) raster_fwd_gr
             // neighbouring tile's blocks, hence the atomic OR
 #pragma unroll
             for (int j = 0; j < NP; ++j) {
-                const uint32_t mine = (lanes_of_group<NP>(j) >> lane) & 1u ? lbits : 0u;
+                const uint32_t mine =
+                    SH::PIX_GROUPS ? lbits[j % NL] : ((SH::lanes_of_group(j) >> lane) & 1u ? lbits[0] : 0u);
                 const uint32_t word = __reduce_or_sync(0xffffffffu, mine);
-                if (lane == 0 && word) atomicOr(&bmask[(int64_t)(grp * NP + j) * bm_stride + (b0 >> 5)], word);
+                if (lane == 0 && word) atomicOr(&bmask[(int64_t)SH::group(grp, j) * bm_stride + (b0 >> 5)], word);
             }
         }
         __syncwarp();  // every lane is done with the staged chunk before the next one
