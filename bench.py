@@ -506,12 +506,22 @@ def run_slam(args, dev, n_frames=8):
     cams = [synth.camera(Wd, Hd, fx, T_cw=T) for T in path]
     frames = [synth.raycast_room(room, c) for c in cams]
     dec = synth.decoder(WORKLOAD["k"], WORKLOAD["d"])
+    W_dec, b_dec = torch.as_tensor(dec.W).to(dev), torch.as_tensor(dec.b).to(dev)
+    # untimed warm-up: three frames of the same loop with a few iterations each, so that every
+    # kernel and library path the loop uses is loaded before the timed run (their first use on
+    # a fresh machine cost about 3 s once, in the first two frames' mapping)
+    wcfg = slam.SlamConfig(n_track=4, n_map=4, n_init=4, t_opt=2, kf_every=2)
+    warm = slam.Slam(cams[0], W_dec, b_dec, 3, synth.rskm_draws(3 * 4), torch.as_tensor(
+        synth.feature_bank(Wd * Hd * 3, WORKLOAD["d"])), wcfg, gaussian_capacity=Wd * Hd * 3, device=dev)
+    for t in range(3):
+        warm.process(frames[t], T0=path[0] if t == 0 else None)
+    torch.cuda.synchronize()
+    del warm
     cfg = slam.SlamConfig(n_track=40, n_map=60, n_init=60, t_opt=2, kf_every=5)
     n_draws = cfg.n_init + (n_frames - 1) * cfg.n_map
     cap = Wd * Hd * n_frames
-    s = slam.Slam(cams[0], torch.as_tensor(dec.W).to(dev), torch.as_tensor(dec.b).to(dev), n_frames,
-                  synth.rskm_draws(n_draws), torch.as_tensor(synth.feature_bank(cap, WORKLOAD["d"])), cfg,
-                  gaussian_capacity=cap, device=dev)
+    s = slam.Slam(cams[0], W_dec, b_dec, n_frames, synth.rskm_draws(n_draws),
+                  torch.as_tensor(synth.feature_bank(cap, WORKLOAD["d"])), cfg, gaussian_capacity=cap, device=dev)
     t0 = time.perf_counter()
     for t, fr in enumerate(frames):
         s.process(fr, T0=path[0] if t == 0 else None)
@@ -543,7 +553,8 @@ def run_slam(args, dev, n_frames=8):
             "gaussians_per_frame": s.sizes, "keyframes": s.kf_frames,
             "ate_cm": 100 * ate, "ate_cm_constant_velocity_start": 100 * one_step,
             "map_psnr_db_at_sequence_poses": [round(x, 2) for x in psnr],
-            "timing": "host wall clock around each frame (each phase ends with a read-back)"}
+            "timing": "host wall clock around each frame (each phase ends with a read-back), after an "
+                      "untimed three-frame warm-up run of the loop"}
 
 
 def job_rate(ms_local, world, device=None):

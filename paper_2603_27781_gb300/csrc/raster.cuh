@@ -11,44 +11,44 @@ constexpr int kBatch = 128;  // splats staged in shared memory per round
 // Launch shape with NP pixels per thread (1, 2 or 4) for one 16x16 tile.
 //   NP = 1: 8 warps, each an 8x4 block of pixels;
 //   NP = 2: 4 warps, each an 8x8 block, a thread owning 2 pixels 4 rows apart
-//           (pixel p in the block's p-th 8x4 half), or with BAND each a 16x4 band,
-//           a thread owning 2 horizontal neighbours;
+//           (pixel p in the block's p-th 8x4 half), or with HPAIR 2 horizontal
+//           neighbours;
 //   NP = 4: 2 warps, each a 16x8 band, a thread owning a 2x2 block.
 // A thread's pixels share every shared-memory read of a splat and are
 // evaluated together, so their arithmetic chains interleave.  Square 8x8 blocks
 // have a shorter edge than 16x4 bands, so fewer splats reach a block without
-// reaching most of its pixels (the per-group backward walks 6 % fewer); the
-// per-tile forward measured faster with bands.
-template <int NP, bool BAND = false> struct Shape {
-    static constexpr bool SQ2 = NP == 2 && !BAND;      // the 8x8 two-pixel layout
+// reaching most of its pixels (6 % fewer walked by the per-group backward).  On the
+// 1M-Gaussian 1200x680 frame the forward ran fastest with horizontal pairs and the
+// backward with vertical ones.
+template <int NP, bool HPAIR = false> struct Shape {
     static constexpr int THREADS = kTilePix / NP;
     static constexpr int WARPS = THREADS / 32;
-    static constexpr int BW = NP == 1 || SQ2 ? 8 : 16;  // warp box width
-    static constexpr int BH = NP == 1 || (NP == 2 && BAND) ? 4 : 8;
-    // pixel p of every thread lies in the warp's p-th blend-mask group (8x8 layout); otherwise
-    // all pixels of a thread lie in one group
-    static constexpr bool PIX_GROUPS = SQ2;
+    static constexpr int BW = NP == 4 ? 16 : 8;  // warp box width
+    static constexpr int BH = NP == 1 ? 4 : 8;
+    // pixel p of every thread lies in the warp's p-th blend-mask group (vertical pairs);
+    // otherwise all pixels of a thread lie in one group
+    static constexpr bool PIX_GROUPS = NP == 2 && !HPAIR;
     __device__ static void warp_origin(int w, int &x0, int &y0) {
-        x0 = NP == 1 || SQ2 ? (w & 1) * 8 : 0;
-        y0 = NP == 1 ? (w >> 1) * 4 : (SQ2 ? (w >> 1) * 8 : w * BH);
+        x0 = NP == 4 ? 0 : (w & 1) * 8;
+        y0 = NP == 1 ? (w >> 1) * 4 : (NP == 2 ? (w >> 1) * 8 : w * BH);
     }
     __device__ static void pixel(int tid, int p, int &lx, int &ly) {
         const int lane = tid & 31, w = tid >> 5;
         int x0, y0;
         warp_origin(w, x0, y0);
         if (NP == 1) { lx = x0 + (lane & 7); ly = y0 + (lane >> 3); }
-        else if (SQ2) { lx = x0 + (lane & 7); ly = y0 + (lane >> 3) + 4 * p; }
-        else if (NP == 2) { lx = (lane & 7) * 2 + p; ly = y0 + (lane >> 3); }
+        else if (NP == 2 && HPAIR) { lx = x0 + (lane & 3) * 2 + p; ly = y0 + (lane >> 2); }
+        else if (NP == 2) { lx = x0 + (lane & 7); ly = y0 + (lane >> 3) + 4 * p; }
         else { lx = (lane & 7) * 2 + (p & 1); ly = y0 + (lane >> 3) * 2 + (p >> 1); }
     }
     // blend-mask group of the j-th (j < NP) of warp w's groups
     __host__ __device__ static constexpr int group(int w, int j) {
-        return NP == 1 ? w : (SQ2 ? ((w >> 1) * 2 + j) * 2 + (w & 1) : w * NP + j);
+        return NP == 1 ? w : (NP == 2 ? ((w >> 1) * 2 + j) * 2 + (w & 1) : w * 4 + j);
     }
     // where a thread's pixels share one group: which lanes own pixels of warp group j
     __device__ static uint32_t lanes_of_group(int j) {
-        if (NP == 1 || SQ2) return 0xffffffffu;
-        if (NP == 2) return j == 0 ? 0x0f0f0f0fu : 0xf0f0f0f0u;
+        if (NP == 1 || PIX_GROUPS) return 0xffffffffu;
+        if (NP == 2) return j == 0 ? 0x0000ffffu : 0xffff0000u;
         const uint32_t m[4] = {0x00000f0fu, 0x0000f0f0u, 0x0f0f0000u, 0xf0f00000u};
         return m[j];
     }

@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS, fwd_min_blocks(D, NP)) ras
     const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges, int64_t P, float *o_rgb, float *o_depth,
     float *o_sil, float *o_feat, float *o_T, int32_t *o_nc, int32_t *o_nb, uint32_t *bmask, int64_t bm_stride,
     const uint32_t *__restrict__ order) {
-    using SH = Shape<NP, true>;  // 16x4 bands at NP = 2 (measured faster here than 8x8 blocks)
+    using SH = Shape<NP, true>;  // horizontal pixel pairs
     constexpr int NT = SH::THREADS;
     constexpr int NL = SH::PIX_GROUPS ? NP : 1;  // mask bit registers per thread
     constexpr int D4 = D / 4, DD = D > 0 ? D : 1;
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(32, fwd_group_min_blocks(D, NP)) raster_fwd_gr
     const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges, int64_t P, float *o_rgb, float *o_depth,
     float *o_sil, float *o_feat, float *o_T, int32_t *o_nc, int32_t *o_nb, uint32_t *bmask, int64_t bm_stride,
     const uint32_t *__restrict__ order) {
-    using SH = Shape<NP>;
+    using SH = Shape<NP, true>;  // horizontal pixel pairs
     constexpr int D4 = D / 4, DD = D > 0 ? D : 1;
     constexpr int NL = SH::PIX_GROUPS ? NP : 1;  // mask bit registers per thread
     constexpr int GW = SH::WARPS;  // pixel-group blocks per tile
