@@ -114,15 +114,21 @@ __global__ void __launch_bounds__(1024) blocksum_scan_kernel(uint32_t *block_sum
 }
 
 // Adds the 8-bit digits of passes [0, n_passes) of `key` (lanes with `valid`) to the block's
-// shared histograms, one atomic per distinct digit per warp.  Every lane of the warp calls it.
+// shared histograms.  Every lane of the warp calls it.  Per pass: one atomic for the warp
+// when all of its valid lanes have the same digit (the high digits of nearby keys), else one
+// per lane (the low digits, mostly distinct, so the atomics rarely collide).
 __device__ __forceinline__ void hist_add(uint32_t (*sh)[256], int n_passes, bool valid, uint32_t key) {
     const uint32_t mask = __ballot_sync(0xffffffffu, valid);
     if (!valid) return;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, first = __ffs(mask) - 1;
     for (int p = 0; p < n_passes; ++p) {
         const uint32_t d = (key >> (8 * p)) & 255u;
-        const uint32_t peers = __match_any_sync(mask, d);
-        if (lane == __ffs(peers) - 1) atomicAdd(&sh[p][d], __popc(peers));
+        const uint32_t d0 = __shfl_sync(mask, d, first);
+        if (__all_sync(mask, d == d0)) {
+            if (lane == first) atomicAdd(&sh[p][d], (uint32_t)__popc(mask));
+        } else {
+            atomicAdd(&sh[p][d], 1u);
+        }
     }
 }
 
