@@ -12,9 +12,9 @@
 // the (tile, depth, index) order.
 //
 // The digit histograms of every pass are counted by the kernels that write the keys (the
-// compaction for the depth keys, the emission for the tile keys), one warp-aggregated
-// shared-memory atomic per distinct digit.  Each radix pass is one kernel: a block ranks its 2048 keys stably within the
-// block (warp match + per-warp digit counters), publishes its per-digit
+// compaction for the depth keys, the emission for the tile keys) with shared-memory atomics.
+// Each radix pass is one kernel: a block ranks its 2048 keys stably within the block (peer
+// lanes of a digit from eight bit ballots + per-warp digit counters), publishes its per-digit
 // counts, finds its global offsets by a chained look-back over earlier blocks,
 // and scatters through shared memory.  Blocks take tile numbers from an atomic
 // counter so a block only waits on blocks that are already running; every wait
@@ -287,8 +287,16 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint32_t *
         bool valid = i < n;
         key[r] = valid ? keys_in[i] : 0u;
         val[r] = valid ? vals_in[i] : 0u;
-        uint32_t d = valid ? (key[r] >> shift) & 255u : 256u + lane;  // invalid lanes never match
-        uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t d = (key[r] >> shift) & 255u;
+        // lanes with the same digit: one ballot per digit bit (cheaper than match.any);
+        // invalid lanes match nothing and are matched by nothing
+        const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+        uint32_t peers = valid ? vmask : (1u << lane);
+#pragma unroll
+        for (int bit = 0; bit < 8; ++bit) {
+            const uint32_t set = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
+            if (valid) peers &= (d >> bit) & 1u ? set : ~set;
+        }
         int leader = __ffs(peers) - 1;
         uint32_t b = 0;
         if (valid && lane == leader) {
