@@ -591,8 +591,9 @@ class HostStepper:
     are downloaded on a second copy stream while step i+1 computes.  `step(field, targets)`
     issues one step on the current stream; `outputs` are the tensors it writes.  With
     `bind`, bind(k) makes the next step write output set k (k = 0, 1) and returns that set's
-    tensors, and the results are downloaded from there; without it they are first copied on
-    the device into one of two staging sets."""
+    tensors, and the results are downloaded from there (the set of the last step stays bound
+    when run returns); without it they are first copied on the device into one of two
+    staging sets."""
 
     def __init__(self, like_field: Field, like_targets: dict, outputs: Sequence[torch.Tensor], bind=None):
         dev = like_field.means.device
