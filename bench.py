@@ -680,8 +680,8 @@ def run_ours(args, rank, world, local_rank):
     # the targets) from pinned host memory and brings its results (every gradient, the loss, the
     # DSR terms, the twist) back to pinned host memory; HostStepper overlaps each step's
     # transfers with the neighbouring steps' compute (two input and two result sets, the
-    # renderer's result tensors rebound to the set of each step); each step is the replay of
-    # the captured step of its buffer set, as in the headline timing
+    # renderer's result tensors rebound to the set of each step); each step after the first
+    # on a set is the replay of the graph captured from it, as in the headline timing
     host = {k: getattr(field, k).cpu().pin_memory() for k in
             ("means", "quats", "log_scales", "opacity_logits", "rgb", "feat")}
     host_t = {k: v.cpu().pin_memory() for k, v in targets.items()}
@@ -694,43 +694,22 @@ def run_ours(args, rank, world, local_rank):
     def bind(k):
         r.bind_outputs(sets[k])
         return [sets[k][n] for n in names]
-    stepper = raster.HostStepper(field, targets, outs, bind=bind)
+    stepper = raster.HostStepper(field, targets, outs, bind=bind, graphs=True)
     h2d, d2h = stepper.bytes_in, stepper.bytes_out
     e2e_ms = []
     if args.e2e_steps > 0:
-        # one captured step per buffer set k (the stepper's inputs k in, results k out); the
-        # stepper replays the graph of the set it hands over
-        graphs = []
-        side = torch.cuda.Stream(dev)
-        for k in range(2):
-            for name, t in host.items():
-                getattr(stepper.fields[k], name).copy_(t)
-            for name, t in host_t.items():
-                stepper.targets[k][name].copy_(t)
-            bind(k)
-            side.wait_stream(stream)
-            with torch.cuda.stream(side):
-                step(None, stepper.fields[k], stepper.targets[k])
-            stream.wait_stream(side)
-            g = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(g):
-                step(None, stepper.fields[k], stepper.targets[k])
-            graphs.append(g)
-        torch.cuda.synchronize()
-
-        def replay(f, tg):
-            graphs[0 if f is stepper.fields[0] else 1].replay()
-        stepper.run(replay, [(host, host_t)] * 2)      # untimed warm-up
+        run_step = lambda f, tg: step(None, f, tg)
+        stepper.run(run_step, [(host, host_t)] * 2)      # untimed warm-up (captures the graphs)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         flush.fill_(0.0)
         e0.record(stream)
         stepper.h2d.wait_stream(stream)
-        n_e2e = stepper.run(replay, [(host, host_t)] * args.e2e_steps)
+        n_e2e = stepper.run(run_step, [(host, host_t)] * args.e2e_steps)
         e1.record(stepper.d2h)
         e1.synchronize()
         e2e_ms = [e0.elapsed_time(e1) / n_e2e]
-        del graphs
+        stepper.graphs = None            # frees the captured graphs
     r.bind_outputs(sets[0])
     e2e_value = job_rate(float(np.mean(e2e_ms)), world, dev)[1] if e2e_ms else None
 

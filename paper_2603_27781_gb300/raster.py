@@ -593,15 +593,20 @@ class HostStepper:
     `bind`, bind(k) makes the next step write output set k (k = 0, 1) and returns that set's
     tensors, and the results are downloaded from there (the set of the last step stays bound
     when run returns); without it they are first copied on the device into one of two
-    staging sets."""
+    staging sets.  With `graphs`, the first step on each input set runs as called and is
+    captured in a CUDA graph, and every later step on that set replays it: the step must then
+    launch the same work on the same buffers each time, with any state that changes from step
+    to step kept on the device (the capture synchronises the device once per set)."""
 
-    def __init__(self, like_field: Field, like_targets: dict, outputs: Sequence[torch.Tensor], bind=None):
+    def __init__(self, like_field: Field, like_targets: dict, outputs: Sequence[torch.Tensor], bind=None,
+                 graphs: bool = False):
         dev = like_field.means.device
         clone = lambda t: torch.empty_like(t)
         self.fields = [Field(*(clone(getattr(like_field, k)) for k in _FIELD_ARRAYS)) for _ in range(2)]
         self.targets = [{k: clone(v) for k, v in like_targets.items()} for _ in range(2)]
         self.outputs = list(outputs)
         self.bind = bind
+        self.graphs = [None, None] if graphs else None
         self.staging = None if bind is not None else [[clone(o) for o in self.outputs] for _ in range(2)]
         self.host_out = [[torch.empty(o.shape, dtype=o.dtype, pin_memory=True) for o in self.outputs]
                          for _ in range(2)]
@@ -611,6 +616,20 @@ class HostStepper:
         self.bytes_in = sum(getattr(like_field, k).numel() * getattr(like_field, k).element_size()
                             for k in _FIELD_ARRAYS) + sum(v.numel() * v.element_size() for v in like_targets.values())
         self.bytes_out = sum(o.numel() * o.element_size() for o in self.outputs)
+
+    def _step(self, step, buf, f, tg):
+        if self.graphs is None:
+            step(f, tg)
+        elif self.graphs[buf] is None:
+            # first step on set buf: run it (these are its results), then capture it for the
+            # later steps on the set
+            step(f, tg)
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                step(f, tg)
+            self.graphs[buf] = g
+        else:
+            self.graphs[buf].replay()
 
     def run(self, step, host_inputs, on_result=None):
         """Runs one step per (host_field, host_targets) pair of `host_inputs` (dicts of pinned
@@ -638,9 +657,9 @@ class HostStepper:
                 if i >= 2:
                     compute.wait_event(self.downloaded[buf])
                 results = self.bind(buf)
-                step(f, tg)
+                self._step(step, buf, f, tg)
             else:
-                step(f, tg)
+                self._step(step, buf, f, tg)
                 # results to staging set buf once step i-2's download from it is done
                 if i >= 2:
                     compute.wait_event(self.downloaded[buf])

@@ -194,7 +194,8 @@ def test_captured_tracking_loop_follows_oracle():
 def test_host_stepper_overlapped_steps_match_sequential_ones():
     """Four fwd+bwd steps with different field parameters and targets from pinned host memory:
     the overlapped stepper (uploads and downloads on copy streams, two input and two result
-    sets) hands back each step's own results, equal to the same steps run one after another."""
+    sets; the steps called or replayed from per-set CUDA graphs) hands back each step's own
+    results, equal to the same steps run one after another."""
     gs, cams, frames = _two_view_room(8000)
     prm_g, _ = C.params_pair()
     field = raster.Field.from_numpy(gs, "cuda")
@@ -228,9 +229,11 @@ def test_host_stepper_overlapped_steps_match_sequential_ones():
         r.bind_outputs(sets[k])
         return [sets[k][nm] for nm in names]
 
-    for use_bind in (False, True):       # staged results, then two alternating result sets
+    # staged results or two alternating result sets; steps called, or replayed from the graph
+    # captured from the first step on each input set
+    for use_bind, graphs in ((False, False), (True, False), (False, True), (True, True)):
         got = {}
-        stepper = raster.HostStepper(field, tg0, outs, bind=bind if use_bind else None)
+        stepper = raster.HostStepper(field, tg0, outs, bind=bind if use_bind else None, graphs=graphs)
         n = stepper.run(step, inputs, on_result=lambda i, host: got.__setitem__(i, [h.clone() for h in host]))
         r.bind_outputs(sets[0])
         assert n == 4 and sorted(got) == [0, 1, 2, 3]
