@@ -43,7 +43,7 @@ _lib = None
 
 # Raster parameter order of the C source.
 PARAM_NAMES = ("tile", "alpha_min", "alpha_max", "T_min", "z_near", "lowpass", "radius_sigma",
-               "bg_r", "bg_g", "bg_b")
+               "bg_r", "bg_g", "bg_b", "exact_jacobian")
 
 
 def build(force: bool = False) -> str:
@@ -91,10 +91,14 @@ class Params:
     lowpass: float = 0.3
     radius_sigma: float = 3.0
     bg: tuple = (0.0, 0.0, 0.0)
+    # False: the EWA Jacobian is evaluated at (x/z, y/z) clamped to the view widened by 15 %
+    # per side (the 3DGS rasterizer convention); True: unclamped, the literal Eq. 3
+    exact_jacobian: bool = False
 
     def array(self):
         return np.array([self.tile, self.alpha_min, self.alpha_max, self.T_min, self.z_near,
-                         self.lowpass, self.radius_sigma, *self.bg], dtype=np.float64)
+                         self.lowpass, self.radius_sigma, *self.bg, float(self.exact_jacobian)],
+                        dtype=np.float64)
 
 
 def _cam(cam):
@@ -159,13 +163,14 @@ def render_fwd(cam, proj, rgb, feat, vals, ranges, prm: Params, view_offset=0, t
     P = W * H
     out = dict(rgb=np.zeros((3, H, W)), depth=np.zeros((H, W)), sil=np.zeros((H, W)),
                feat=np.zeros((D, H, W)), T=np.zeros((H, W)), n_contrib=np.zeros((H, W), np.int32),
-               margin=np.zeros((H, W)), sens=np.zeros((H, W)))
+               margin=np.zeros((H, W)), sens=np.zeros((H, W)), sens_depth=np.zeros((H, W)))
     args = [_d(proj["uv"]), _d(proj["conic"]), _d(proj["opacity"]), _d(proj["depth"]), _d(rgb), _d(feat)]
     _L().or_render_fwd(ctypes.c_int(W), ctypes.c_int(H), ctypes.c_int(prm.tile), ctypes.c_int(D),
                        I64(view_offset), I64(tile_offset), *map(_p, args),
                        _p(np.ascontiguousarray(vals, np.uint32)), _p(np.ascontiguousarray(ranges, np.uint32)),
                        _p(prm.array()), *(_p(out[k]) for k in ("rgb", "depth", "sil", "feat", "T",
-                                                               "n_contrib", "margin", "sens")))
+                                                               "n_contrib", "margin", "sens",
+                                                               "sens_depth")))
     return out
 
 

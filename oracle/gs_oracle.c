@@ -42,7 +42,7 @@
 /* Raster parameters, passed as a double array in this order. */
 enum {
     P_TILE = 0, P_ALPHA_MIN, P_ALPHA_MAX, P_T_MIN, P_Z_NEAR, P_LOWPASS,
-    P_RADIUS_SIGMA, P_BG_R, P_BG_G, P_BG_B, P_COUNT
+    P_RADIUS_SIGMA, P_BG_R, P_BG_G, P_BG_B, P_EXACT_J, P_COUNT
 };
 
 /* Camera intrinsics, passed as a double array: width, height, fx, fy, cx, cy. */
@@ -105,16 +105,26 @@ static float depth_key(const double T[16], const double mu[3]) {
 }
 
 /* Point at which the EWA Jacobian J of Eq. 3 is evaluated: (x/z, y/z) of the
- * camera-frame centre, clamped to the view's extent widened by 15% of the image
- * size on each side (for a centred principal point: 1.3 x the half field of
- * view, the convention of the 3DGS rasterizer that GS3LAM renders with).  The
- * projected centre itself is never clamped.  in_x / in_y report whether the
- * coordinate is inside the clamp interval (its derivative is 0 outside). */
-static void jacobian_point(const double p[3], const double *cam, double *tx, double *ty, int *in_x, int *in_y) {
+ * camera-frame centre.  With prm[P_EXACT_J] = 0 (the default) it is clamped to
+ * the view's extent widened by 15% of the image size on each side (for a
+ * centred principal point: 1.3 x the half field of view, the convention of the
+ * 3DGS rasterizer that GS3LAM renders with); with prm[P_EXACT_J] != 0 it is not
+ * clamped, which is the literal perspective Jacobian of Eq. 3.  The projected
+ * centre itself is never clamped.  in_x / in_y report whether the coordinate is
+ * inside the clamp interval (its derivative is 0 outside). */
+static void jacobian_point(const double p[3], const double *cam, const double *prm, double *tx, double *ty,
+                           int *in_x, int *in_y) {
     double W = cam[C_W], H = cam[C_H], fx = cam[C_FX], fy = cam[C_FY], cx = cam[C_CX], cy = cam[C_CY];
+    double x = p[0] / p[2], y = p[1] / p[2];
+    if (prm[P_EXACT_J] != 0) {
+        *tx = x;
+        *ty = y;
+        if (in_x) *in_x = 1;
+        if (in_y) *in_y = 1;
+        return;
+    }
     double lox = (-cx - 0.15 * W) / fx, hix = (W - cx + 0.15 * W) / fx;
     double loy = (-cy - 0.15 * H) / fy, hiy = (H - cy + 0.15 * H) / fy;
-    double x = p[0] / p[2], y = p[1] / p[2];
     *tx = x < lox ? lox : (x > hix ? hix : x);
     *ty = y < loy ? loy : (y > hiy ? hiy : y);
     if (in_x) *in_x = (x >= lox && x <= hix);
@@ -186,7 +196,7 @@ void or_project(int64_t n, const double *means, const double *quats, const doubl
         mm3(tmp, RcwT, Sc);
         double z = p[2];
         double tx_, ty_;
-        jacobian_point(p, cam, &tx_, &ty_, NULL, NULL);
+        jacobian_point(p, cam, prm, &tx_, &ty_, NULL, NULL);
         double J[6] = {fx / z, 0, -fx * tx_ / z, 0, fy / z, -fy * ty_ / z};
         double JS[6];
         for (int r = 0; r < 2; r++)
@@ -307,14 +317,31 @@ int64_t or_bin_sort(int n_views, int64_t n_per_view, const int32_t *rect, const 
  *   w = alpha T; accumulate w c, w d, w f, w; T <- T (1 - alpha)
  * Outputs: rgb = sum w c + T bg, depth = sum w d, sil = sum w (Eq. 10),
  * feat = sum w f, T_final, n_contrib = 1-based list position of the last
- * blended splat.  margin = smallest relative distance of any threshold
- * decision taken for that pixel (for excluding pixels where a different
- * rounding could flip a decision).  sens = sum over blended splats of
- * w (|A| dx^2 + 2 |B dx dy| + |C| dy^2) / 2: the absolute change of the
- * exponents, weighted by the blend, per unit relative change of the conics,
- * i.e. how strongly the pixel amplifies rounding in the 2D covariances (an
- * elongated splat evaluated far along its long axis makes the quadratic form
- * a difference of large terms).
+ * blended splat.
+ *
+ * Two further per-pixel figures say how well single-precision inputs determine
+ * the pixel (they are not part of the method; the parity tests use them to
+ * tell rounding from error).  The unit is a relative rounding eps of 1e-7.
+ * Model: each splat's 2D covariance Sigma2D is known to within eps * lambda_max
+ * per entry (it is formed in single precision from a 3D covariance), and its
+ * alpha carries a further relative rounding of 4 eps (opacity, exponential,
+ * product).  To first order a perturbation dSigma changes the exponent by
+ * 1/2 y^T dSigma y with y = Sigma2D^-1 (dx, dy), so splat j's alpha moves by
+ * at most r_j eps relative, r_j = 1/2 lambda_max (|y1| + |y2|)^2 + 4 (0 where
+ * alpha is clamped at alpha_max).
+ *   margin = the smallest gap of any threshold decision taken at the pixel
+ *     over that decision's rounding bound (alpha against alpha_min and
+ *     alpha_max: |ln(alpha / threshold)| over eps r_j; the transmittance stop:
+ *     |ln(T (1 - alpha) / T_min)| over eps times the accumulated sensitivity of
+ *     T (1 - alpha), sum of alpha_k r_k / (1 - alpha_k) + 1 per blended splat):
+ *     a decision can flip only where margin < 1.
+ *   sens = the first-order bound, in units of eps, of the absolute change of
+ *     any of the pixel's colour, silhouette and feature values: for an output
+ *     x, d out / d alpha_j = T_j (x_j - S_j) with S_j the blended value behind
+ *     splat j, so |d out| <= eps sum_j w_j r_j |x_j - S_j|; the maximum over
+ *     the channels.
+ *   sens_depth = the same bound for the depth divided by |depth| (relative;
+ *     0 where nothing is blended).
  *
  * Gaussian attributes are indexed by vals[j] (a view-local index after
  * subtracting view_offset); images are planar [C, H, W].
@@ -325,21 +352,75 @@ typedef struct {
     const uint32_t *vals, *ranges;
     const double *prm;
     int64_t view_offset, tile_offset;
+    int conditioning; /* compute r_j and the decision margins (forward images only) */
 } raster_ctx;
 
-static double rel_gap(double a, double b) { return fabs(a - b) / fabs(b); }
+/* Blended splats of one pixel, front to back (scratch sized by the longest tile list). */
+typedef struct {
+    int64_t *pos;   /* view-local Gaussian index */
+    double *alpha;  /* alpha_j */
+    double *T;      /* transmittance in front of j */
+    double *G;      /* e^power */
+    int *clamped;   /* alpha clamped at alpha_max */
+    double *r;      /* rounding sensitivity r_j of alpha_j (0 where clamped) */
+} blend_list;
+
+static int blend_list_alloc(blend_list *l, int64_t n) {
+    size_t m = (size_t)(n > 0 ? n : 1);
+    l->pos = (int64_t *)malloc(sizeof(int64_t) * m);
+    l->alpha = (double *)malloc(sizeof(double) * m);
+    l->T = (double *)malloc(sizeof(double) * m);
+    l->G = (double *)malloc(sizeof(double) * m);
+    l->clamped = (int *)malloc(sizeof(int) * m);
+    l->r = (double *)malloc(sizeof(double) * m);
+    return l->pos && l->alpha && l->T && l->G && l->clamped && l->r;
+}
+
+static void blend_list_free(blend_list *l) {
+    free(l->pos); free(l->alpha); free(l->T); free(l->G); free(l->clamped); free(l->r);
+}
+
+/* Longest tile list of a view (scratch size of the per-pixel lists). */
+static int64_t longest_tile(const uint32_t *ranges, int64_t tile_offset, int64_t n_tiles) {
+    int64_t maxlen = 1;
+    for (int64_t t = 0; t < n_tiles; t++) {
+        int64_t len = (int64_t)ranges[2 * (tile_offset + t) + 1] - ranges[2 * (tile_offset + t)];
+        if (len > maxlen) maxlen = len;
+    }
+    return maxlen;
+}
+
+/* Gap between a positive value and a threshold as |ln(a / b)|: a relative change
+ * of a by e flips a < b only if |e| reaches it (to first order; the relative gap
+ * |a - b| / b for a near b).  0 < a: underflow to 0 counts as an infinite gap. */
+static double log_gap(double a, double b) { return a > 0 ? fabs(log(a / b)) : INFINITY; }
+
+/* The unit eps of the rounding figures: a relative rounding of 1e-7 (about two
+ * units in the last place of a single-precision value). */
+#define COND_EPS 1e-7
+
+/* Relative rounding sensitivity of alpha for a splat with conic cn evaluated at
+ * offset (dx, dy), in units of eps (see the comment above): lambda_max of
+ * Sigma2D = cn^-1 is 1 / lambda_min(cn) = (m + sqrt(m^2 - det)) / det. */
+static double alpha_sensitivity(const double cn[3], double dx, double dy) {
+    double det = cn[0] * cn[2] - cn[1] * cn[1];
+    double m = 0.5 * (cn[0] + cn[2]);
+    double disc = m * m - det;
+    double lam = (m + sqrt(disc > 0 ? disc : 0)) / det;
+    double y1 = cn[0] * dx + cn[1] * dy, y2 = cn[1] * dx + cn[2] * dy;
+    double q = fabs(y1) + fabs(y2);
+    return 0.5 * lam * q * q + 4.0;
+}
 
 /* Visit the splats of pixel (px, py) front to back; writes the blended list
- * (positions, alphas, transmittance before each, clamp flags) into the scratch
- * arrays when given; returns the number of blended splats. */
+ * into l and returns the number of blended splats. */
 static int64_t blend_pixel(const raster_ctx *c, int px, int py, double *acc_rgb, double *acc_depth,
                            double *acc_sil, double *acc_feat, double *T_out, int64_t *last_out,
-                           double *margin_out, double *sens_out, int64_t *list_pos, double *list_alpha,
-                           double *list_T, double *list_G, int *list_clamped) {
+                           double *margin_out, blend_list *l) {
     const double *prm = c->prm;
     int64_t t = c->tile_offset + (int64_t)(py / c->tile) * c->tx + px / c->tile;
     uint32_t start = c->ranges[2 * t], end = c->ranges[2 * t + 1];
-    double T = 1.0, margin = INFINITY, sens = 0.0;
+    double T = 1.0, margin = INFINITY, cT = 0.0;
     double pxc = px + 0.5, pyc = py + 0.5;
     int64_t nb = 0, last = 0;
     for (int d = 0; d < 3; d++) acc_rgb[d] = 0;
@@ -355,42 +436,76 @@ static int64_t blend_pixel(const raster_ctx *c, int px, int py, double *acc_rgb,
         double G = exp(power);
         double oG = c->opacity[g] * G;
         double alpha = oG < prm[P_ALPHA_MAX] ? oG : prm[P_ALPHA_MAX];
-        double m1 = rel_gap(oG, prm[P_ALPHA_MAX]);
-        if (m1 < margin) margin = m1;
-        if (prm[P_ALPHA_MIN] > 0) {
-            double m2 = rel_gap(alpha, prm[P_ALPHA_MIN]);
-            if (m2 < margin) margin = m2;
+        int clamped = !(oG < prm[P_ALPHA_MAX]);
+        double r = c->conditioning ? alpha_sensitivity(cn, dx, dy) : 1.0;
+        if (c->conditioning) {
+            double m1 = log_gap(oG, prm[P_ALPHA_MAX]) / (COND_EPS * r);
+            if (m1 < margin) margin = m1;
+            if (prm[P_ALPHA_MIN] > 0) {
+                double m2 = log_gap(alpha, prm[P_ALPHA_MIN]) / (COND_EPS * r);
+                if (m2 < margin) margin = m2;
+            }
         }
         if (alpha < prm[P_ALPHA_MIN]) continue;
         double Tn = T * (1.0 - alpha);
-        if (prm[P_T_MIN] > 0) {
-            double m3 = rel_gap(Tn, prm[P_T_MIN]);
+        double r_alpha = clamped ? 0.0 : r;
+        /* relative sensitivity of T (1 - alpha): the splats in front, this one, one rounding */
+        double cTn = cT + alpha * r_alpha / (1.0 - alpha) + 1.0;
+        if (c->conditioning && prm[P_T_MIN] > 0) {
+            double m3 = log_gap(Tn, prm[P_T_MIN]) / (COND_EPS * cTn);
             if (m3 < margin) margin = m3;
         }
         if (Tn < prm[P_T_MIN]) break;
         double w = alpha * T;
-        /* conditioning: the exponent's absolute error per unit relative error of (A, B, C) */
-        sens += w * 0.5 * (fabs(cn[0]) * dx * dx + 2.0 * fabs(cn[1] * dx * dy) + fabs(cn[2]) * dy * dy);
         for (int d = 0; d < 3; d++) acc_rgb[d] += w * c->rgb[3 * g + d];
         *acc_depth += w * c->depth[g];
         *acc_sil += w;
         for (int d = 0; d < c->D; d++) acc_feat[d] += w * c->feat[(int64_t)c->D * g + d];
-        if (list_pos) {
-            list_pos[nb] = g;
-            list_alpha[nb] = alpha;
-            list_T[nb] = T;
-            list_G[nb] = G;
-            list_clamped[nb] = !(oG < prm[P_ALPHA_MAX]);
-        }
+        l->pos[nb] = g;
+        l->alpha[nb] = alpha;
+        l->T[nb] = T;
+        l->G[nb] = G;
+        l->clamped[nb] = clamped;
+        l->r[nb] = r_alpha;
         nb++;
         T = Tn;
+        cT = cTn;
         last = (int64_t)(j - start) + 1;
     }
     *T_out = T;
     *last_out = last;
     *margin_out = margin;
-    *sens_out = sens;
     return nb;
+}
+
+/* First-order rounding bounds of a blended pixel (sens, sens_depth above):
+ * walks the blended list back to front with the value S behind each splat of
+ * every channel (background bg for colour, 0 for depth, silhouette and
+ * features). */
+static void pixel_sensitivity(const raster_ctx *c, const blend_list *l, int64_t nb, double depth,
+                              double *S, double *kap, double *sens_out, double *sens_depth_out) {
+    const double *prm = c->prm;
+    int nch = 5 + c->D; /* r, g, b, depth, sil, features */
+    for (int d = 0; d < 3; d++) S[d] = prm[P_BG_R + d];
+    for (int ch = 3; ch < nch; ch++) S[ch] = 0;
+    for (int ch = 0; ch < nch; ch++) kap[ch] = 0;
+    for (int64_t k = nb - 1; k >= 0; k--) {
+        int64_t g = l->pos[k];
+        double alpha = l->alpha[k], wr = alpha * l->T[k] * l->r[k];
+        for (int ch = 0; ch < nch; ch++) {
+            double x = ch < 3 ? c->rgb[3 * g + ch]
+                     : ch == 3 ? c->depth[g]
+                     : ch == 4 ? 1.0
+                     : c->feat[(int64_t)c->D * g + (ch - 5)];
+            kap[ch] += wr * fabs(x - S[ch]);
+            S[ch] = alpha * x + (1.0 - alpha) * S[ch];
+        }
+    }
+    double m = 0;
+    for (int ch = 0; ch < nch; ch++)
+        if (ch != 3 && kap[ch] > m) m = kap[ch];
+    *sens_out = m;
+    *sens_depth_out = depth != 0 ? kap[3] / fabs(depth) : 0.0;
 }
 
 /* Renders one view.  Arrays out_* are planar [C, H, W] for that view. */
@@ -399,28 +514,36 @@ void or_render_fwd(int W, int H, int tile, int D, int64_t view_offset, int64_t t
                    const double *rgb, const double *feat, const uint32_t *vals, const uint32_t *ranges,
                    const double *prm, double *out_rgb, double *out_depth, double *out_sil,
                    double *out_feat, double *out_T, int32_t *out_ncontrib, double *out_margin,
-                   double *out_sens) {
+                   double *out_sens, double *out_sens_depth) {
     raster_ctx c = {W, H, tile, (W + tile - 1) / tile, D, uv, conic, opacity, depth, rgb, feat,
-                    vals, ranges, prm, view_offset, tile_offset};
+                    vals, ranges, prm, view_offset, tile_offset, 1};
     int64_t P = (int64_t)W * H;
+    blend_list l;
+    int ok = blend_list_alloc(&l, longest_tile(ranges, tile_offset, (int64_t)c.tx * ((H + tile - 1) / tile)));
     double *acc_feat = (double *)malloc(sizeof(double) * (size_t)(D > 0 ? D : 1));
-    for (int py = 0; py < H; py++)
-        for (int px = 0; px < W; px++) {
-            int64_t pix = (int64_t)py * W + px;
-            double acc_rgb[3], acc_depth, acc_sil, T, margin, sens;
-            int64_t last;
-            blend_pixel(&c, px, py, acc_rgb, &acc_depth, &acc_sil, acc_feat, &T, &last, &margin, &sens,
-                        NULL, NULL, NULL, NULL, NULL);
-            for (int d = 0; d < 3; d++) out_rgb[d * P + pix] = acc_rgb[d] + T * prm[P_BG_R + d];
-            out_depth[pix] = acc_depth;
-            out_sil[pix] = acc_sil;
-            for (int d = 0; d < D; d++) out_feat[d * P + pix] = acc_feat[d];
-            out_T[pix] = T;
-            out_ncontrib[pix] = (int32_t)last;
-            out_margin[pix] = margin;
-            out_sens[pix] = sens;
-        }
-    free(acc_feat);
+    double *S = (double *)malloc(sizeof(double) * (size_t)(5 + D));
+    double *kap = (double *)malloc(sizeof(double) * (size_t)(5 + D));
+    if (ok && acc_feat && S && kap)
+        for (int py = 0; py < H; py++)
+            for (int px = 0; px < W; px++) {
+                int64_t pix = (int64_t)py * W + px;
+                double acc_rgb[3], acc_depth, acc_sil, T, margin, sens, sens_depth;
+                int64_t last;
+                int64_t nb = blend_pixel(&c, px, py, acc_rgb, &acc_depth, &acc_sil, acc_feat, &T, &last, &margin,
+                                         &l);
+                pixel_sensitivity(&c, &l, nb, acc_depth, S, kap, &sens, &sens_depth);
+                for (int d = 0; d < 3; d++) out_rgb[d * P + pix] = acc_rgb[d] + T * prm[P_BG_R + d];
+                out_depth[pix] = acc_depth;
+                out_sil[pix] = acc_sil;
+                for (int d = 0; d < D; d++) out_feat[d * P + pix] = acc_feat[d];
+                out_T[pix] = T;
+                out_ncontrib[pix] = (int32_t)last;
+                out_margin[pix] = margin;
+                out_sens[pix] = sens;
+                out_sens_depth[pix] = sens_depth;
+            }
+    blend_list_free(&l);
+    free(acc_feat); free(S); free(kap);
 }
 
 /* ------------------------------------------------------- A8: blend backward */
@@ -445,31 +568,22 @@ void or_render_bwd(int W, int H, int tile, int D, int64_t view_offset, int64_t t
                    const double *g_feat, double *d_uv, double *d_conic, double *d_opacity,
                    double *d_depth, double *d_rgb, double *d_feat) {
     raster_ctx c = {W, H, tile, (W + tile - 1) / tile, D, uv, conic, opacity, depth, rgb, feat,
-                    vals, ranges, prm, view_offset, tile_offset};
+                    vals, ranges, prm, view_offset, tile_offset, 0};
     int64_t P = (int64_t)W * H;
-    int64_t maxlen = 1;
-    for (int64_t t = 0; t < (int64_t)c.tx * ((H + tile - 1) / tile); t++) {
-        int64_t len = (int64_t)ranges[2 * (tile_offset + t) + 1] - ranges[2 * (tile_offset + t)];
-        if (len > maxlen) maxlen = len;
-    }
-    int64_t *lp = (int64_t *)malloc(sizeof(int64_t) * (size_t)maxlen);
-    double *la = (double *)malloc(sizeof(double) * (size_t)maxlen);
-    double *lT = (double *)malloc(sizeof(double) * (size_t)maxlen);
-    double *lG = (double *)malloc(sizeof(double) * (size_t)maxlen);
-    int *lc = (int *)malloc(sizeof(int) * (size_t)maxlen);
+    blend_list l;
+    int ok = blend_list_alloc(&l, longest_tile(ranges, tile_offset, (int64_t)c.tx * ((H + tile - 1) / tile)));
     int nch = 5 + D;
     double *S = (double *)malloc(sizeof(double) * (size_t)nch);
     double *gx = (double *)malloc(sizeof(double) * (size_t)nch);
     double *x = (double *)malloc(sizeof(double) * (size_t)nch);
     double *acc_feat = (double *)malloc(sizeof(double) * (size_t)(D > 0 ? D : 1));
 
-    for (int py = 0; py < H; py++)
+    for (int py = 0; ok && S && gx && x && acc_feat && py < H; py++)
         for (int px = 0; px < W; px++) {
             int64_t pix = (int64_t)py * W + px;
-            double acc_rgb[3], acc_depth, acc_sil, T, margin, sens;
+            double acc_rgb[3], acc_depth, acc_sil, T, margin;
             int64_t last;
-            int64_t nb = blend_pixel(&c, px, py, acc_rgb, &acc_depth, &acc_sil, acc_feat, &T, &last,
-                                     &margin, &sens, lp, la, lT, lG, lc);
+            int64_t nb = blend_pixel(&c, px, py, acc_rgb, &acc_depth, &acc_sil, acc_feat, &T, &last, &margin, &l);
             /* channel order: r, g, b, depth, sil, feat[0..D) */
             for (int d = 0; d < 3; d++) { gx[d] = g_rgb[d * P + pix]; S[d] = prm[P_BG_R + d]; }
             gx[3] = g_depth[pix]; S[3] = 0;
@@ -477,8 +591,8 @@ void or_render_bwd(int W, int H, int tile, int D, int64_t view_offset, int64_t t
             for (int d = 0; d < D; d++) { gx[5 + d] = g_feat[d * P + pix]; S[5 + d] = 0; }
             double pxc = px + 0.5, pyc = py + 0.5;
             for (int64_t k = nb - 1; k >= 0; k--) {
-                int64_t g = lp[k];
-                double alpha = la[k], Tk = lT[k], w = alpha * Tk;
+                int64_t g = l.pos[k];
+                double alpha = l.alpha[k], Tk = l.T[k], w = alpha * Tk;
                 for (int d = 0; d < 3; d++) x[d] = rgb[3 * g + d];
                 x[3] = depth[g];
                 x[4] = 1.0;
@@ -491,8 +605,8 @@ void or_render_bwd(int W, int H, int tile, int D, int64_t view_offset, int64_t t
                 for (int d = 0; d < 3; d++) d_rgb[3 * g + d] += w * gx[d];
                 d_depth[g] += w * gx[3];
                 for (int d = 0; d < D; d++) d_feat[(int64_t)D * g + d] += w * gx[5 + d];
-                if (lc[k]) continue; /* alpha clamped at alpha_max: flat in o and G */
-                double G = lG[k], o = opacity[g];
+                if (l.clamped[k]) continue; /* alpha clamped at alpha_max: flat in o and G */
+                double G = l.G[k], o = opacity[g];
                 d_opacity[g] += G * dalpha;
                 double dpow = o * G * dalpha;
                 const double *cn = conic + 3 * g;
@@ -504,7 +618,8 @@ void or_render_bwd(int W, int H, int tile, int D, int64_t view_offset, int64_t t
                 d_uv[2 * g + 1] += (cn[1] * dx + cn[2] * dy) * dpow;
             }
         }
-    free(lp); free(la); free(lT); free(lG); free(lc); free(S); free(gx); free(x); free(acc_feat);
+    blend_list_free(&l);
+    free(S); free(gx); free(x); free(acc_feat);
 }
 
 /* ------------------------------------ A9-A10: projection backward and pose (B.1) */
@@ -566,7 +681,7 @@ void or_project_bwd(int64_t n, const double *means, const double *quats, const d
         double x = p[0], y = p[1], z = p[2], z2 = z * z;
         double tx_, ty_;
         int in_x, in_y;
-        jacobian_point(p, cam, &tx_, &ty_, &in_x, &in_y);
+        jacobian_point(p, cam, prm, &tx_, &ty_, &in_x, &in_y);
         double J[6] = {fx / z, 0, -fx * tx_ / z, 0, fy / z, -fy * ty_ / z};
         double JS[6];
         for (int r = 0; r < 2; r++)

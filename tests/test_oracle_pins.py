@@ -416,7 +416,8 @@ def test_backward_matches_finite_differences_with_thresholds():
     gs, cam, gimg = _fd_setup(32, prm)
     gs.opacity_logits[:2] = 6.0                   # alpha_max clamp is active at their centres
     img = oracle.forward(gs, cam, prm)[2]
-    assert img["margin"].min() > 1e-4
+    # every decision's relative gap is over 1e-4 (margin is in units of 1e-7 r_j, r_j >= 4)
+    assert img["margin"].min() > 250
     _check_fd(gs, cam, prm, gimg, 1e-7, 1e-5)
 
 
@@ -444,6 +445,139 @@ def test_jacobian_clamp_bounds_off_view_footprints():
     ce = oracle.project(at_edge, cam, Params(lowpass=0.0))["cov2d"][0]
     cf = oracle.project(far, cam, Params(lowpass=0.0))["cov2d"][0]
     np.testing.assert_allclose(cf, ce, rtol=1e-12)
+
+
+def _pinhole(cam, p):
+    return np.array([cam.fx * p[0] / p[2] + cam.cx, cam.fy * p[1] / p[2] + cam.cy])
+
+
+def test_exact_jacobian_is_the_linearised_pinhole_map():
+    """exact_jacobian: Sigma2D = J Sc J^T with J the derivative of the pinhole map at the
+    camera-frame centre (central differences of the map itself), also far outside the view,
+    where the clamped mode keeps the boundary's footprint instead."""
+    cam = camera(64, 48, 40.0, cx=32, cy=24)
+    q = np.array([0.9, 0.2, -0.3, 0.25])
+    q /= np.linalg.norm(q)
+    s = np.array([0.05, 0.02, 0.08])
+    for p in ([0.1, -0.05, 1.5], [8.0, 0.3, 1.0], [-3.0, 5.0, 2.0]):
+        p = np.array(p)
+        gs = field([p], [q], [np.log(s)], [0.0], [[0, 0, 0]], [[0.0]])
+        got = oracle.project(gs, cam, Params(lowpass=0.0, exact_jacobian=True))["cov2d"][0]
+        h = 1e-6
+        J = np.stack([(_pinhole(cam, p + h * e) - _pinhole(cam, p - h * e)) / (2 * h) for e in np.eye(3)], 1)
+        R = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()
+        S2 = J @ (R @ np.diag(s ** 2) @ R.T) @ J.T
+        np.testing.assert_allclose(got, [S2[0, 0], S2[0, 1], S2[1, 1]], rtol=1e-7, atol=1e-9 * S2.max())
+        clamped = oracle.project(gs, cam, Params(lowpass=0.0))["cov2d"][0]
+        inside = abs(p[0] / p[2]) <= 0.65 * 64 / 40 and abs(p[1] / p[2]) <= 0.65 * 48 / 40
+        assert np.array_equal(clamped, got) == inside
+
+
+def test_backward_matches_finite_differences_with_exact_jacobian():
+    """The clamped-Jacobian scene of the test above with the literal Eq. 3 Jacobian."""
+    prm = Params(alpha_min=0.0, alpha_max=1.0, T_min=0.0, lowpass=0.3, radius_sigma=40.0, exact_jacobian=True)
+    gs, cam, gimg = _fd_setup(34, prm)
+    gs.means[:4, 0] = gs.means[:4, 2] * np.array([1.1, -1.2, 1.05, -1.3])
+    gs.log_scales[:4] += 1.0
+    assert (oracle.project(gs, cam, prm)["radius"][:4] > 0).all()
+    _check_fd(gs, cam, prm, gimg, 1e-6, 1e-6)
+
+
+# -------------------------------------------------------------- rounding figures
+def _perturbed_images(gs, cam, prm, proj, bins, corner, eps):
+    """Renders with every splat's Sigma2D entries (a, b, c) moved by eps * lambda_max * corner
+    (corner: [n, 3] in [-1, 1]), the same bins (the perturbation is far too small to move a
+    rectangle)."""
+    a, b, c = proj["cov2d"].T
+    m = 0.5 * (a + c)
+    lam = m + np.sqrt(np.maximum(m * m - (a * c - b * b), 0))
+    cov = proj["cov2d"] + eps * lam[:, None] * corner
+    det = cov[:, 0] * cov[:, 2] - cov[:, 1] ** 2
+    live = proj["radius"] > 0
+    conic = proj["conic"].copy()
+    conic[live] = np.stack([cov[:, 2], -cov[:, 1], cov[:, 0]], 1)[live] / det[live, None]
+    p2 = dict(proj, conic=conic)
+    return oracle.render_fwd(cam, p2, gs.rgb, gs.feat, bins[1], bins[2], prm)
+
+
+def test_rounding_figures_bound_first_order_perturbations():
+    """sens and sens_depth, times eps, bound the change of every output under any perturbation
+    of the 2D covariances by eps * lambda_max per entry, at every pixel whose decisions cannot
+    flip."""
+    gs = synth.box_field(300, 4, seed=41)
+    gs = synth.Gaussians(*(x.astype(np.float64) for x in gs.arrays()))
+    cam = camera(40, 30, 36.0, cx=20, cy=15)
+    prm = Params()
+    proj, bins, img = oracle.forward(gs, cam, prm)
+    eps = 1e-10
+    ok = img["margin"] > 1
+    assert ok.mean() > 0.99
+    g = synth.rng(42)
+    for trial in range(4):
+        corner = g.uniform(-1, 1, (gs.n, 3)) if trial < 2 else np.sign(g.standard_normal((gs.n, 3)))
+        img2 = _perturbed_images(gs, cam, prm, proj, bins, corner, eps)
+        assert np.array_equal(img2["n_contrib"][ok], img["n_contrib"][ok])
+        bound = eps * img["sens"] * (1 + 1e-6) + 1e-18
+        for k in ("rgb", "feat"):
+            assert (np.abs(img2[k] - img[k])[:, ok] <= bound[ok]).all(), k
+        assert (np.abs(img2["sil"] - img["sil"])[ok] <= bound[ok]).all()
+        dbound = eps * img["sens_depth"] * np.abs(img["depth"]) * (1 + 1e-6) + 1e-18
+        assert (np.abs(img2["depth"] - img["depth"])[ok] <= dbound[ok]).all()
+
+
+def _needle(alpha_min=1.0 / 255.0, stacked=False):
+    """One splat, 4 px along the image diagonal and 0.1 px (plus the low-pass) across it; with
+    stacked, a second one 10 % farther and 10 % larger behind it (the same footprint)."""
+    cam = camera(32, 24, 60.0, cx=16, cy=12)
+    q = [math.cos(math.pi / 8), 0, 0, math.sin(math.pi / 8)]       # 45 deg about the optical axis
+    ls = np.log([0.2, 0.005, 0.005])
+    if not stacked:
+        gs = field([[0, 0, 3.0]], [q], [ls], [2.2], [[0.3, 0.6, 0.9]], [[1.0, -1.0]])
+    else:
+        gs = field([[0, 0, 3.0], [0, 0, 3.3]], [q, q], [ls, ls + np.log(1.1)], [0.0, 0.5],
+                   [[0.3, 0.6, 0.9], [0.8, 0.1, 0.5]], [[0.5, -0.3], [0.2, -0.1]])
+    return gs, cam, Params(alpha_min=alpha_min)
+
+
+@pytest.mark.parametrize("stacked", [False, True])
+def test_rounding_figures_are_attained_across_a_needle(stacked):
+    """At a pixel across the needle's short axis the worst corner of the perturbation reaches
+    the bound to within the alpha rounding term that a covariance perturbation does not
+    exercise (more than 90 % of it); with two needles the front one's term counts what is
+    blended behind it (the silhouette, whose bound is the largest here)."""
+    gs, cam, prm = _needle(stacked=stacked)
+    proj, bins, img = oracle.forward(gs, cam, prm)
+    assert img["n_contrib"][12, 15] == (2 if stacked else 1)
+    y, x = 12, 15                                   # centre offset (-0.5, +0.5): across the needle
+    assert 0.1 < img["sil"][y, x] < 0.9
+    eps = 1e-10
+    best_s, best_d = 0.0, 0.0
+    for corner in np.array(np.meshgrid([-1, 1], [-1, 1], [-1, 1])).reshape(3, -1).T:
+        img2 = _perturbed_images(gs, cam, prm, proj, bins, corner[None, :].astype(float), eps)
+        best_s = max(best_s, abs(img2["sil"][y, x] - img["sil"][y, x]))
+        best_d = max(best_d, abs(img2["depth"][y, x] - img["depth"][y, x]) / img["depth"][y, x])
+    assert 0.9 <= best_s / (eps * img["sens"][y, x]) <= 1.0 + 1e-6
+    assert 0.9 <= best_d / (eps * img["sens_depth"][y, x]) <= 1.0 + 1e-6
+
+
+@pytest.mark.parametrize("which", ["alpha_min", "T_min"])
+def test_margin_is_the_distance_to_a_flipped_decision(which):
+    """With alpha_min just under the needle's alpha at one pixel (or T_min just over the
+    transmittance it leaves), a worst-corner perturbation of 0.9 margin units keeps the
+    decision and one of 1.2 units flips it."""
+    gs, cam, _ = _needle()
+    y, x = 12, 15
+    a0 = oracle.forward(gs, cam, Params())[2]["sil"][y, x]
+    prm = Params(alpha_min=a0 * (1 - 1e-6)) if which == "alpha_min" else Params(T_min=(1 - a0) * (1 + 1e-6))
+    proj, bins, img = oracle.forward(gs, cam, prm)
+    m = img["margin"][y, x]
+    assert 0.01 < m < 1
+    blended = img["n_contrib"][y, x]
+    corners = np.array(np.meshgrid([-1, 1], [-1, 1], [-1, 1])).reshape(3, -1).T.astype(float)
+    for scale, flips in ((0.9, False), (1.2, True)):
+        got = [_perturbed_images(gs, cam, prm, proj, bins, c[None, :], scale * m * 1e-7)["n_contrib"][y, x] != blended
+               for c in corners]
+        assert any(got) == flips, scale
 
 
 def test_pose_translation_gradient_is_rotated_mean_gradient_sum():
