@@ -51,8 +51,12 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-o", tmp, _SRC,
+               "-lm"]
+        try:      # per-row / per-Gaussian loops in parallel where gcc has OpenMP
+            subprocess.check_call(cmd[:1] + ["-fopenmp"] + cmd[1:], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(cmd)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -67,7 +71,14 @@ def _L():
         _lib.or_dsr.restype = ctypes.c_double
         _lib.or_ssim.restype = ctypes.c_double
         _lib.or_lower_median.restype = ctypes.c_double
+        _lib.or_get_threads.restype = ctypes.c_int
     return _lib
+
+
+def set_threads(n: int = 0) -> int:
+    """Threads of the oracle's parallel loops (0: every core); returns the count in use."""
+    _L().or_set_threads(ctypes.c_int(n))
+    return int(_L().or_get_threads())
 
 
 def _d(a):
@@ -157,20 +168,24 @@ def bin_sort(rect, depth_key, cams, tile=16, n_per_view=None):
 
 
 # ---------------------------------------------------------------------- render
-def render_fwd(cam, proj, rgb, feat, vals, ranges, prm: Params, view_offset=0, tile_offset=0):
+def render_fwd(cam, proj, rgb, feat, vals, ranges, prm: Params, view_offset=0, tile_offset=0,
+               conditioning=True):
+    """Front-to-back blend of one view; with conditioning, also the per-pixel rounding figures
+    margin, sens and sens_depth (see gs_oracle.c)."""
     W, H = cam.width, cam.height
     D = feat.shape[1]
     P = W * H
     out = dict(rgb=np.zeros((3, H, W)), depth=np.zeros((H, W)), sil=np.zeros((H, W)),
-               feat=np.zeros((D, H, W)), T=np.zeros((H, W)), n_contrib=np.zeros((H, W), np.int32),
-               margin=np.zeros((H, W)), sens=np.zeros((H, W)), sens_depth=np.zeros((H, W)))
+               feat=np.zeros((D, H, W)), T=np.zeros((H, W)), n_contrib=np.zeros((H, W), np.int32))
+    if conditioning:
+        out.update(margin=np.zeros((H, W)), sens=np.zeros((H, W)), sens_depth=np.zeros((H, W)))
     args = [_d(proj["uv"]), _d(proj["conic"]), _d(proj["opacity"]), _d(proj["depth"]), _d(rgb), _d(feat)]
+    cond = [_p(out[k]) if conditioning else None for k in ("margin", "sens", "sens_depth")]
     _L().or_render_fwd(ctypes.c_int(W), ctypes.c_int(H), ctypes.c_int(prm.tile), ctypes.c_int(D),
                        I64(view_offset), I64(tile_offset), *map(_p, args),
                        _p(np.ascontiguousarray(vals, np.uint32)), _p(np.ascontiguousarray(ranges, np.uint32)),
-                       _p(prm.array()), *(_p(out[k]) for k in ("rgb", "depth", "sil", "feat", "T",
-                                                               "n_contrib", "margin", "sens",
-                                                               "sens_depth")))
+                       _p(prm.array()), *(_p(out[k]) for k in ("rgb", "depth", "sil", "feat", "T", "n_contrib")),
+                       *cond)
     return out
 
 
@@ -289,11 +304,11 @@ def pose_step(T, grad, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-15):
 
 
 # ------------------------------------------------------------- full pipelines
-def forward(gs, cam, prm: Params):
+def forward(gs, cam, prm: Params, conditioning=True):
     """Projection, binning, sort and blend of one view; returns (proj, bins, images)."""
     proj = project(gs, cam, prm)
     keys, vals, ranges = bin_sort(proj["rect"], proj["depth_key"], [cam], prm.tile)
-    img = render_fwd(cam, proj, gs.rgb, gs.feat, vals, ranges, prm)
+    img = render_fwd(cam, proj, gs.rgb, gs.feat, vals, ranges, prm, conditioning=conditioning)
     return proj, (keys, vals, ranges), img
 
 
@@ -307,9 +322,10 @@ def backward_from_image_grads(gs, cam, prm: Params, proj, bins, g):
                 d2=r)
 
 
-def step(gs, cam, prm: Params, target, dec, w: LossWeights, with_dsr=True):
-    """One fwd+bwd iteration: render, loss (+ DSR), all gradients, pose twist."""
-    proj, bins, img = forward(gs, cam, prm)
+def step(gs, cam, prm: Params, target, dec, w: LossWeights, with_dsr=True, conditioning=True):
+    """One fwd+bwd iteration: render, loss (+ DSR), all gradients, pose twist (with
+    conditioning, the images carry the rounding figures of render_fwd)."""
+    proj, bins, img = forward(gs, cam, prm, conditioning)
     L = loss(img, target, dec, w)
     grads = backward_from_image_grads(gs, cam, prm, proj, bins, L)
     total = L["total"]

@@ -38,6 +38,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* Raster parameters, passed as a double array in this order. */
 enum {
@@ -49,6 +52,26 @@ enum {
 enum { C_W = 0, C_H, C_FX, C_FY, C_CX, C_CY };
 
 int or_param_count(void) { return P_COUNT; }
+
+/* Threads of the per-Gaussian and per-pixel loops (projection, blend, their
+ * backwards), which are parallel over Gaussians or image rows when built with
+ * OpenMP; 1 thread otherwise.  The per-Gaussian gradient sums of the blend
+ * backward are then added atomically, so their order (and last bits) varies. */
+void or_set_threads(int n) {
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : omp_get_num_procs());
+#else
+    (void)n;
+#endif
+}
+
+int or_get_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------ helpers */
 static int64_t floordiv(int64_t a, int64_t b) {
@@ -160,6 +183,7 @@ void or_project(int64_t n, const double *means, const double *quats, const doubl
     double RcwT[9];
     transpose3(Rcw, RcwT);
 
+    #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; i++) {
         const double *mu = means + 3 * i;
         uv[2 * i] = uv[2 * i + 1] = 0;
@@ -508,42 +532,51 @@ static void pixel_sensitivity(const raster_ctx *c, const blend_list *l, int64_t 
     *sens_depth_out = depth != 0 ? kap[3] / fabs(depth) : 0.0;
 }
 
-/* Renders one view.  Arrays out_* are planar [C, H, W] for that view. */
+/* Renders one view.  Arrays out_* are planar [C, H, W] for that view; out_margin,
+ * out_sens and out_sens_depth may be NULL (the rounding figures are then not computed). */
 void or_render_fwd(int W, int H, int tile, int D, int64_t view_offset, int64_t tile_offset,
                    const double *uv, const double *conic, const double *opacity, const double *depth,
                    const double *rgb, const double *feat, const uint32_t *vals, const uint32_t *ranges,
                    const double *prm, double *out_rgb, double *out_depth, double *out_sil,
                    double *out_feat, double *out_T, int32_t *out_ncontrib, double *out_margin,
                    double *out_sens, double *out_sens_depth) {
+    /* the rounding figures only when asked for (out_margin, out_sens, out_sens_depth not NULL) */
+    int cond = out_margin && out_sens && out_sens_depth;
     raster_ctx c = {W, H, tile, (W + tile - 1) / tile, D, uv, conic, opacity, depth, rgb, feat,
-                    vals, ranges, prm, view_offset, tile_offset, 1};
+                    vals, ranges, prm, view_offset, tile_offset, cond};
     int64_t P = (int64_t)W * H;
+    int64_t maxlen = longest_tile(ranges, tile_offset, (int64_t)c.tx * ((H + tile - 1) / tile));
+    #pragma omp parallel
+    {
     blend_list l;
-    int ok = blend_list_alloc(&l, longest_tile(ranges, tile_offset, (int64_t)c.tx * ((H + tile - 1) / tile)));
+    int ok = blend_list_alloc(&l, maxlen);
     double *acc_feat = (double *)malloc(sizeof(double) * (size_t)(D > 0 ? D : 1));
     double *S = (double *)malloc(sizeof(double) * (size_t)(5 + D));
     double *kap = (double *)malloc(sizeof(double) * (size_t)(5 + D));
-    if (ok && acc_feat && S && kap)
+    #pragma omp for schedule(dynamic, 4)
         for (int py = 0; py < H; py++)
-            for (int px = 0; px < W; px++) {
+            for (int px = 0; ok && acc_feat && S && kap && px < W; px++) {
                 int64_t pix = (int64_t)py * W + px;
                 double acc_rgb[3], acc_depth, acc_sil, T, margin, sens, sens_depth;
                 int64_t last;
                 int64_t nb = blend_pixel(&c, px, py, acc_rgb, &acc_depth, &acc_sil, acc_feat, &T, &last, &margin,
                                          &l);
-                pixel_sensitivity(&c, &l, nb, acc_depth, S, kap, &sens, &sens_depth);
+                if (cond) pixel_sensitivity(&c, &l, nb, acc_depth, S, kap, &sens, &sens_depth);
                 for (int d = 0; d < 3; d++) out_rgb[d * P + pix] = acc_rgb[d] + T * prm[P_BG_R + d];
                 out_depth[pix] = acc_depth;
                 out_sil[pix] = acc_sil;
                 for (int d = 0; d < D; d++) out_feat[d * P + pix] = acc_feat[d];
                 out_T[pix] = T;
                 out_ncontrib[pix] = (int32_t)last;
-                out_margin[pix] = margin;
-                out_sens[pix] = sens;
-                out_sens_depth[pix] = sens_depth;
+                if (cond) {
+                    out_margin[pix] = margin;
+                    out_sens[pix] = sens;
+                    out_sens_depth[pix] = sens_depth;
+                }
             }
     blend_list_free(&l);
     free(acc_feat); free(S); free(kap);
+    }
 }
 
 /* ------------------------------------------------------- A8: blend backward */
@@ -570,16 +603,20 @@ void or_render_bwd(int W, int H, int tile, int D, int64_t view_offset, int64_t t
     raster_ctx c = {W, H, tile, (W + tile - 1) / tile, D, uv, conic, opacity, depth, rgb, feat,
                     vals, ranges, prm, view_offset, tile_offset, 0};
     int64_t P = (int64_t)W * H;
-    blend_list l;
-    int ok = blend_list_alloc(&l, longest_tile(ranges, tile_offset, (int64_t)c.tx * ((H + tile - 1) / tile)));
+    int64_t maxlen = longest_tile(ranges, tile_offset, (int64_t)c.tx * ((H + tile - 1) / tile));
     int nch = 5 + D;
+    #pragma omp parallel
+    {
+    blend_list l;
+    int ok = blend_list_alloc(&l, maxlen);
     double *S = (double *)malloc(sizeof(double) * (size_t)nch);
     double *gx = (double *)malloc(sizeof(double) * (size_t)nch);
     double *x = (double *)malloc(sizeof(double) * (size_t)nch);
     double *acc_feat = (double *)malloc(sizeof(double) * (size_t)(D > 0 ? D : 1));
 
-    for (int py = 0; ok && S && gx && x && acc_feat && py < H; py++)
-        for (int px = 0; px < W; px++) {
+    #pragma omp for schedule(dynamic, 4)
+    for (int py = 0; py < H; py++)
+        for (int px = 0; ok && S && gx && x && acc_feat && px < W; px++) {
             int64_t pix = (int64_t)py * W + px;
             double acc_rgb[3], acc_depth, acc_sil, T, margin;
             int64_t last;
@@ -602,24 +639,38 @@ void or_render_bwd(int W, int H, int tile, int D, int64_t view_offset, int64_t t
                     dalpha += gx[ch] * Tk * (x[ch] - S[ch]);
                     S[ch] = alpha * x[ch] + (1.0 - alpha) * S[ch];
                 }
-                for (int d = 0; d < 3; d++) d_rgb[3 * g + d] += w * gx[d];
+                for (int d = 0; d < 3; d++) {
+                    #pragma omp atomic
+                    d_rgb[3 * g + d] += w * gx[d];
+                }
+                #pragma omp atomic
                 d_depth[g] += w * gx[3];
-                for (int d = 0; d < D; d++) d_feat[(int64_t)D * g + d] += w * gx[5 + d];
+                for (int d = 0; d < D; d++) {
+                    #pragma omp atomic
+                    d_feat[(int64_t)D * g + d] += w * gx[5 + d];
+                }
                 if (l.clamped[k]) continue; /* alpha clamped at alpha_max: flat in o and G */
                 double G = l.G[k], o = opacity[g];
+                #pragma omp atomic
                 d_opacity[g] += G * dalpha;
                 double dpow = o * G * dalpha;
                 const double *cn = conic + 3 * g;
                 double dx = pxc - uv[2 * g], dy = pyc - uv[2 * g + 1];
+                #pragma omp atomic
                 d_conic[3 * g] += -0.5 * dx * dx * dpow;
+                #pragma omp atomic
                 d_conic[3 * g + 1] += -dx * dy * dpow;
+                #pragma omp atomic
                 d_conic[3 * g + 2] += -0.5 * dy * dy * dpow;
+                #pragma omp atomic
                 d_uv[2 * g] += (cn[0] * dx + cn[1] * dy) * dpow;
+                #pragma omp atomic
                 d_uv[2 * g + 1] += (cn[1] * dx + cn[2] * dy) * dpow;
             }
         }
     blend_list_free(&l);
     free(S); free(gx); free(x); free(acc_feat);
+    }
 }
 
 /* ------------------------------------ A9-A10: projection backward and pose (B.1) */
@@ -652,7 +703,9 @@ void or_project_bwd(int64_t n, const double *means, const double *quats, const d
     double RcwT[9];
     transpose3(Rcw, RcwT);
     for (int k = 0; k < 6; k++) twist[k] = 0;
+    double tw[6] = {0, 0, 0, 0, 0, 0};
 
+    #pragma omp parallel for schedule(static) reduction(+ : tw[:6])
     for (int64_t i = 0; i < n; i++) {
         double *gm = d_means + 3 * i, *gq = d_quats + 4 * i, *gs = d_log_scales + 3 * i;
         for (int k = 0; k < 3; k++) gm[k] = gs[k] = 0;
@@ -770,13 +823,14 @@ void or_project_bwd(int64_t n, const double *means, const double *quats, const d
         mm3(Sc, Gc, SG);
         mm3(Gc, Sc, GSc);
         for (int k = 0; k < 9; k++) Am[k] = SG[k] - GSc[k];
-        twist[0] += gp[0];
-        twist[1] += gp[1];
-        twist[2] += gp[2];
-        twist[3] += y * gp[2] - z * gp[1] + 2.0 * Am[5];
-        twist[4] += z * gp[0] - x * gp[2] + 2.0 * Am[6];
-        twist[5] += x * gp[1] - y * gp[0] + 2.0 * Am[1];
+        tw[0] += gp[0];
+        tw[1] += gp[1];
+        tw[2] += gp[2];
+        tw[3] += y * gp[2] - z * gp[1] + 2.0 * Am[5];
+        tw[4] += z * gp[0] - x * gp[2] + 2.0 * Am[6];
+        tw[5] += x * gp[1] - y * gp[0] + 2.0 * Am[1];
     }
+    for (int k = 0; k < 6; k++) twist[k] = tw[k];
 }
 
 /* -------------------------------------------------- A7: decoder and losses */

@@ -37,7 +37,7 @@ def _rank_main(rank, world, port, times, out):
 def test_job_rate_takes_the_slowest_rank():
     world, port = 2, _free_port()
     times = [2.0, 5.0]
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:    # not forked: the oracle's OpenMP threads may be running
         out = m.dict()
         mp.spawn(_rank_main, args=(world, port, times, out), nprocs=world, join=True)
         got = dict(out)
