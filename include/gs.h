@@ -50,7 +50,8 @@ typedef enum {
     GS_ERR_CAPACITY = -2,    /* more tile instances than gs_binning.capacity */
     GS_ERR_CUDA = -3,        /* a CUDA runtime call or launch failed */
     GS_ERR_TIMEOUT = -4,     /* a bounded device-side wait gave up */
-    GS_ERR_UNSUPPORTED = -5  /* valid but not built (feature dim, tile size, dtype) */
+    GS_ERR_UNSUPPORTED = -5, /* valid but not built (feature dim, tile size, dtype) */
+    GS_ERR_CHECK = -6        /* a library built with GS_CHECKS=1 found an index out of range */
 } gs_status;
 
 typedef enum { GS_F32 = 0, GS_BF16 = 1, GS_F16 = 2 } gs_dtype;
@@ -101,9 +102,26 @@ typedef struct {
      * GS_BWD_BLOCKS_TILE = one block per tile; GS_BWD_BLOCKS_DEFAULT (0) = the
      * library's choice for the launch shape. */
     int32_t fwd_blocks;
+    /* Where the EWA Jacobian J of Eq. 3 is evaluated (gs_project, gs_project_bwd):
+     * GS_JACOBIAN_CLAMPED (0, the default) at (x/z, y/z) clamped to the view
+     * widened by 15% of its size per side (the 3DGS rasterizer convention: a
+     * Gaussian far outside the view keeps the footprint it would have at that
+     * boundary; the clamped coordinate has zero derivative), GS_JACOBIAN_EXACT
+     * (1) at (x/z, y/z) itself, the literal perspective Jacobian.  Other values
+     * return GS_ERR_ARG. */
+    int32_t jacobian;
+    /* Bounded device-side waits (the look-back of gs_bin_sort's radix passes): a
+     * wait gives up after this many polls of a flag another block has not yet
+     * published, sets GS_ERR_TIMEOUT in the status word and lets the call finish
+     * without reading what it waited for.  0 = the library default (2^22 polls,
+     * about 0.3 s); negative = a block gives up at the first earlier block it
+     * looks at (a test hook: gs_bin_sort then reports GS_ERR_TIMEOUT whenever a
+     * radix pass has more than one block of 2048 keys). */
+    int32_t spin_limit;
 } gs_raster_params;
 
 enum { GS_BWD_BLOCKS_DEFAULT = 0, GS_BWD_BLOCKS_GROUP = 1, GS_BWD_BLOCKS_TILE = 2 };
+enum { GS_JACOBIAN_CLAMPED = 0, GS_JACOBIAN_EXACT = 1 };
 
 /* The Semantic Gaussian Field of Eq. 1, structure of arrays.
  *   means [n,3], quats [n,4] (w,x,y,z; normalised inside), log_scales [n,3]
@@ -274,7 +292,12 @@ gs_status gs_project(const gs_gaussians *g, const gs_camera *cams, int n_views,
  * 64-bit key (tile << 32 | depth bits) of items listed in index order.  Writes
  * ranges for every tile (empty tiles get [0,0)), n_inst, and keys if non-NULL.
  * If the count exceeds out->capacity, *out->status = GS_ERR_CAPACITY and the
- * binning is incomplete (its required size is still written to n_inst).
+ * binning is incomplete (its required size is still written to n_inst).  If a
+ * bounded wait gives up, *out->status = GS_ERR_TIMEOUT.  Once the status word is
+ * set, the remaining binning kernels skip their work (ranges stay empty), and
+ * gs_render_fwd / gs_render_bwd given that binning render nothing: images,
+ * blend mask contents beyond their clearing, and gradients beyond their zeroing
+ * are left as they were.
  * ws: workspace of ws_bytes >= gs_workspace_size(...). */
 gs_status gs_bin_sort(int64_t n, const gs_projected *proj, const gs_camera *cams, int n_views,
                       const gs_raster_params *p, void *ws, size_t ws_bytes, gs_binning *out,
@@ -354,16 +377,20 @@ gs_status gs_loss_fwd_bwd(const gs_camera *cams, int n_views, int feat_dim, cons
  * or inside a per-frame real-time budget, plugins whose host application owns
  * every device allocation, and bindings from environments without a device
  * allocator.  The paper has no counterpart; it is a deployment convenience.
- * Arguments and results are exactly those of gs_loss_fwd_bwd without the
- * workspace.  Its scratch is one static device array of 4,415,488 bytes
- * (4.2 MiB) that every GPU which loads the library holds until the process
- * exits; it serves at most 16 views (more returns GS_ERR_UNSUPPORTED before
- * any launch).  The first call on a device looks up that array's device
- * address with the device current (cudaGetSymbolAddress), so make the first
- * call on each device before any stream capture.  All calls share the one
- * array: calls that overlap on the GPU (concurrent streams, or host threads
- * using the same device) race and must be serialised by the caller.  The call
- * allocates nothing and frees nothing. */
+ * Arguments and results are those of gs_loss_fwd_bwd without the workspace,
+ * with two limits: at most 16 views, and no SSIM term (lp->ssim must be 0; a
+ * nonzero value in [0, 1] returns GS_ERR_UNSUPPORTED, a value outside it or a
+ * nonzero one in tracking mode GS_ERR_ARG).  Every argument is checked before
+ * anything is launched.  Its scratch is one static device array of 4,415,488
+ * bytes (4.2 MiB) that every GPU which loads the library holds until the
+ * process exits.  The array's device address is looked up (cudaGetSymbolAddress,
+ * with the device current) on each call made outside a stream capture; a call
+ * inside a capture reuses the address of the device's last call outside one, so
+ * make a first call on each device before any stream capture, and again after
+ * the device's context has been reset (cudaDeviceReset) before capturing.  All
+ * calls share the one array: calls that overlap on the GPU (concurrent streams,
+ * or host threads using the same device) race and must be serialised by the
+ * caller.  The call allocates nothing and frees nothing. */
 gs_status gs_loss_fwd_bwd_noalloc(const gs_camera *cams, int n_views, int feat_dim, const gs_images *img,
                                   const gs_targets *tgt, const float *dec_W, const float *dec_b,
                                   const gs_loss_params *lp, gs_image_grads_out *grad, float *d_dec_W,

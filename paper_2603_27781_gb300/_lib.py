@@ -13,8 +13,10 @@ from . import build as _build
 
 LIB_PATH = _build.LIB_PATH
 
-GS_OK, GS_ERR_ARG, GS_ERR_CAPACITY, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
+GS_OK, GS_ERR_ARG, GS_ERR_CAPACITY, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_ERR_UNSUPPORTED, GS_ERR_CHECK = \
+    0, -1, -2, -3, -4, -5, -6
 GS_BWD_BLOCKS_DEFAULT, GS_BWD_BLOCKS_GROUP, GS_BWD_BLOCKS_TILE = 0, 1, 2
+GS_JACOBIAN_CLAMPED, GS_JACOBIAN_EXACT = 0, 1
 GS_F32, GS_BF16, GS_F16 = 0, 1, 2
 GS_GRAD_MAP, GS_GRAD_POSE = 1, 2
 
@@ -28,7 +30,8 @@ class gs_raster_params(Structure):
     _fields_ = [("tile", c_int32), ("alpha_min", c_float), ("alpha_max", c_float), ("T_min", c_float),
                 ("z_near", c_float), ("lowpass", c_float), ("radius_sigma", c_float), ("bg_rgb", c_float * 3),
                 ("fwd_px_per_thread", c_int32), ("bwd_px_per_thread", c_int32),
-                ("bwd_blocks", c_int32), ("fwd_blocks", c_int32)]
+                ("bwd_blocks", c_int32), ("fwd_blocks", c_int32), ("jacobian", c_int32),
+                ("spin_limit", c_int32)]
 
 
 class gs_gaussians(Structure):

@@ -62,7 +62,18 @@ bool make_params(const gs_raster_params *p, Params *out) {
     if (p->fwd_blocks < GS_BWD_BLOCKS_DEFAULT || p->fwd_blocks > GS_BWD_BLOCKS_TILE) return false;
     out->fwd_blocks = p->fwd_blocks;
     out->fwd_group = false;
+    if (p->jacobian != GS_JACOBIAN_CLAMPED && p->jacobian != GS_JACOBIAN_EXACT) return false;
+    out->exact_jacobian = p->jacobian == GS_JACOBIAN_EXACT;
+    out->spin_limit = p->spin_limit == 0 ? kDefaultSpinLimit : (p->spin_limit < 0 ? -1 : p->spin_limit);
     return true;
+}
+
+void apply_jacobian_mode(const Params &prm, ViewTable *vt) {
+    if (!prm.exact_jacobian) return;
+    for (int v = 0; v < vt->n_views; ++v) {
+        vt->jx_lo[v] = vt->jy_lo[v] = -INFINITY;
+        vt->jx_hi[v] = vt->jy_hi[v] = INFINITY;
+    }
 }
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -120,6 +131,7 @@ const char *gs_strerror(int status) {
         case GS_ERR_CUDA: return "CUDA runtime error";
         case GS_ERR_TIMEOUT: return "a bounded device-side wait gave up";
         case GS_ERR_UNSUPPORTED: return "unsupported configuration";
+        case GS_ERR_CHECK: return "a checked build found an index out of range";
         default: return "unknown status";
     }
 }

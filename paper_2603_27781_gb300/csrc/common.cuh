@@ -38,7 +38,19 @@ struct Params {
     bool bwd_warp;       // resolved: map-mode backward as one 32-thread block per pixel group
     int fwd_blocks;      // forward block shape (GS_BWD_BLOCKS_*)
     bool fwd_group;      // resolved: forward as one 32-thread block per pixel group
+    bool exact_jacobian; // GS_JACOBIAN_EXACT: J of Eq. 3 at the unclamped (x/z, y/z)
+    int spin_limit;      // polls of a bounded wait before it gives up (< 0: at once)
 };
+
+constexpr int kDefaultSpinLimit = 1 << 22;
+
+// Whether a binning's status word is set (capacity overflow or a wait that gave up): every
+// kernel after the failure skips its work.  The word was written by an earlier kernel of the
+// stream or by a block of the running one; either way a set word is never cleared before the
+// next binning.
+__device__ __forceinline__ bool binning_failed(const int32_t *status) {
+    return status && __ldcg(status) != 0;
+}
 
 // Default pixels per thread of the blend kernels for a feature dimension.
 inline int default_fwd_np(int D) { return D >= 16 ? 2 : 1; }
@@ -47,6 +59,8 @@ inline int default_bwd_np(int D) { return D >= 32 ? 2 : (D >= 16 ? 4 : 1); }
 // Builds the table from host cameras; returns false on invalid input.
 bool make_view_table(const gs_camera *cams, int n_views, int64_t n, ViewTable *vt);
 bool make_params(const gs_raster_params *p, Params *out);
+// With GS_JACOBIAN_EXACT, opens the Jacobian's clamp interval of every view to the whole line.
+void apply_jacobian_mode(const Params &prm, ViewTable *vt);
 
 __device__ __forceinline__ int view_of_tile(const ViewTable &vt, int gt) {
     int v = 0;

@@ -69,9 +69,10 @@ struct Geo {
 };
 
 // EWA projection of one Gaussian into view v.  J is evaluated at (x/z, y/z)
-// clamped to the view widened by 15% of its size per side (1.3 x the half field
-// of view for a centred principal point), which keeps splats whose centres fall
-// far outside the view from stretching with (x/z)^2; the centre is not clamped.
+// clamped to the view table's interval: by default the view widened by 15% of its
+// size per side (1.3 x the half field of view for a centred principal point), which
+// keeps splats whose centres fall far outside the view from stretching with
+// (x/z)^2; the whole line for the exact Jacobian.  The centre is not clamped.
 __device__ __forceinline__ void project_geo(const float mu[3], const Shape &sh, const float R[9], const float t[3],
                                             const ViewTable &vt, int v, const Params &prm, Geo &o,
                                             bool precise_centre = false) {
@@ -324,6 +325,7 @@ extern "C" gs_status gs_project(const gs_gaussians *g, const gs_camera *cams, in
     ViewTable vt;
     Params prm;
     if (!make_view_table(cams, n_views, g->n, &vt) || !make_params(p, &prm)) return GS_ERR_ARG;
+    apply_jacobian_mode(prm, &vt);
     if (g->n * n_views >= ((int64_t)1 << 30)) return GS_ERR_ARG;
     if (g->n == 0) return GS_OK;
     if (!g->means || !g->quats || !g->log_scales || !g->opacity_logits || !out->uvdo || !out->uv_lo ||
@@ -349,6 +351,7 @@ extern "C" gs_status gs_project_bwd(const gs_gaussians *g, const gs_camera *cams
     ViewTable vt;
     Params prm;
     if (!make_view_table(cams, n_views, g->n, &vt) || !make_params(p, &prm)) return GS_ERR_ARG;
+    apply_jacobian_mode(prm, &vt);
     const bool map = grad_mode & GS_GRAD_MAP, pose = grad_mode & GS_GRAD_POSE;
     if (map && (!out || !out->means || !out->quats || !out->log_scales || !out->opacity_logits || !out->rgb))
         return GS_ERR_ARG;

@@ -104,6 +104,45 @@ __device__ __forceinline__ float2 splat_extent(float4 c, float o, float alpha_mi
     return make_float2(sqrtf(qmax * sxx) * 1.001f + 0.01f, sqrtf(qmax * syy) * 1.001f + 0.01f);
 }
 
+// Checked build (compiled with GS_CHECKS=1): the indices a blend kernel takes from the
+// binning and the forward images are verified before use.  A tile's instance range must lie
+// within the binning's capacity and a staged item must be one of its view's Gaussians; a
+// violation sets GS_ERR_CHECK in the binning's status word and the access is replaced by an
+// in-bounds one (an empty range, the view's first Gaussian).  Without GS_CHECKS these are
+// no-ops.
+#ifndef GS_CHECKS
+#define GS_CHECKS 0
+#endif
+
+__device__ __forceinline__ void checked_range(uint32_t &start, uint32_t &end, int64_t capacity, int32_t *status) {
+    if (GS_CHECKS && !(start <= end && (int64_t)end <= capacity)) {
+        set_status(status, GS_ERR_CHECK);
+        end = start = 0;
+    }
+}
+
+__device__ __forceinline__ uint32_t checked_item(uint32_t item, int64_t voff, int64_t n, int32_t *status) {
+    if (GS_CHECKS && !((int64_t)item >= voff && (int64_t)item < voff + n)) {
+        set_status(status, GS_ERR_CHECK);
+        return (uint32_t)voff;
+    }
+    return item;
+}
+
+// The number of a tile's instances the backward walks (the largest last-contributor position
+// of its pixels): within the tile's range, which lies within the capacity; else 0.
+__device__ __forceinline__ int checked_last(uint32_t start, const uint32_t *ranges, int gt, int last,
+                                            int64_t capacity, int32_t *status) {
+    if (GS_CHECKS) {
+        const uint32_t end = ranges[2 * gt + 1];
+        if (!(start <= end && (int64_t)end <= capacity && last >= 0 && (uint32_t)last <= end - start)) {
+            set_status(status, GS_ERR_CHECK);
+            return 0;
+        }
+    }
+    return last;
+}
+
 // Whether a splat centred at (u, v) with extent e can reach the warp's pixel box
 // (pixel centres from (bx0 + 0.5, by0 + 0.5), bw x bh of them).
 __device__ __forceinline__ bool reaches_box(float u, float v, float2 e, float bcx, float bcy, float hx, float hy) {

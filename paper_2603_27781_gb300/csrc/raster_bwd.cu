@@ -63,6 +63,8 @@ extern "C" gs_status gs_render_bwd(const gs_gaussians *g, const gs_projected *pr
     A.bmask = fwd->blend_mask;
     A.bm_stride = bins->capacity / 32 + 1;
     A.order = bins->tile_order;
+    A.status = bins->status;
+    A.capacity = bins->capacity;
     // block shape: per pixel group where that form applies (D 16 or 32, the blend mask,
     // 1 or 2 pixels per thread), unless the caller asks for one
     const int D = g->feat_dim;

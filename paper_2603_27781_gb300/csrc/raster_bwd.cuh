@@ -115,6 +115,8 @@ struct BwdArgs {
     const uint32_t *bmask;  // blend-mask planes from the forward (NULL: scan every splat)
     int64_t bm_stride;
     const uint32_t *order;  // tile launch order (NULL: tile = block index)
+    int32_t *status;        // the binning's status word: set means render nothing
+    int64_t capacity;       // the binning's instance capacity
 };
 
 template <int D, int NP, bool MAP, typename RT, typename FT>
@@ -137,6 +139,7 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS) raster_bwd_kernel(ViewTabl
     const RT *rgb = static_cast<const RT *>(A.rgb);
     const FT *feat = static_cast<const FT *>(A.feat);
 
+    if (binning_failed(A.status)) return;  // the binning overflowed or gave up
     const int gt = A.order ? (int)A.order[blockIdx.x] : (int)blockIdx.x;
     if (gt < 0 || gt >= vt.tile_off[vt.n_views]) return;  // not a permutation of the tiles: leave the tile
     const int v = view_of_tile(vt, gt);
@@ -246,14 +249,14 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS) raster_bwd_kernel(ViewTabl
     __syncthreads();
     if (my_max > 0) atomicMax(&s_max_last, my_max);
     __syncthreads();
-    const int max_last = s_max_last;
+    const int max_last = checked_last(start, A.ranges, gt, s_max_last, A.capacity, A.status);
 
     for (int b_end = max_last; b_end > 0; b_end -= LY::BATCH) {
         const int b_start = max(0, b_end - LY::BATCH);
         const int cnt = b_end - b_start;
         __syncthreads();
         for (int i = tid; i < cnt; i += NT) {
-            const uint32_t item = A.vals[start + b_start + i];
+            const uint32_t item = checked_item(A.vals[start + b_start + i], voff, vt.n, A.status);
             const int64_t g = (int64_t)item - voff;
             const float4 a = A.uvdo[item];
             const float4 c = A.conic[item];
@@ -394,7 +397,7 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS) raster_bwd_kernel(ViewTabl
 #pragma unroll
             for (int j = 0; j < LY::NV; ++j) nz |= a[j] != 0.f;
             if (!nz) continue;
-            const uint32_t item = A.vals[start + b_start + i];
+            const uint32_t item = checked_item(A.vals[start + b_start + i], voff, vt.n, A.status);
             const int64_t g = (int64_t)item - voff;
             if (MAP) {
                 atomicAdd(&A.acc_uvod[item], make_float4(a[0], a[1], a[5], a[6]));

@@ -81,6 +81,7 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP>())
     const RT *rgb = static_cast<const RT *>(A.rgb);
     const FT *feat = static_cast<const FT *>(A.feat);
 
+    if (binning_failed(A.status)) return;  // the binning overflowed or gave up
     const int rank = blockIdx.x / GW, grp = blockIdx.x % GW;
     const int gt = A.order ? (int)A.order[rank] : rank;
     if (gt < 0 || gt >= vt.tile_off[vt.n_views]) return;  // not a permutation of the tiles: leave the tile
@@ -122,7 +123,7 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP>())
         gS[p] = gch[p][0] * prm.bg[0] + gch[p][1] * prm.bg[1] + gch[p][2] * prm.bg[2];
         my_max = max(my_max, last[p]);
     }
-    const int wmax = __reduce_max_sync(0xffffffffu, my_max);
+    const int wmax = checked_last(start, A.ranges, gt, __reduce_max_sync(0xffffffffu, my_max), A.capacity, A.status);
     if (wmax == 0) return;  // no pixel of the group blended anything (warp-uniform)
     // the group's pixel p * 32 + lane: gradients of depth, r, g, b, features
 #pragma unroll
@@ -271,7 +272,7 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP>())
     auto stage_and_process = [&](const int off, const int cnt) {
         if (lane < cnt) {
             const uint32_t ii = s_list[off + lane];
-            const uint32_t item = A.vals[ii];
+            const uint32_t item = checked_item(A.vals[ii], voff, vt.n, A.status);
             const int64_t g = (int64_t)item - voff;
             const float4 a = A.uvdo[item];
             const float4 c = A.conic[item];

@@ -24,7 +24,7 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS, fwd_min_blocks(D, NP)) ras
     const float4 *__restrict__ conic, const RT *__restrict__ rgb, const FT *__restrict__ feat,
     const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges, int64_t P, float *o_rgb, float *o_depth,
     float *o_sil, float *o_feat, float *o_T, int32_t *o_nc, int32_t *o_nb, uint32_t *bmask, int64_t bm_stride,
-    const uint32_t *__restrict__ order) {
+    const uint32_t *__restrict__ order, int32_t *status, int64_t capacity) {
     using SH = Shape<NP, true>;  // horizontal pixel pairs
     constexpr int NT = SH::THREADS;
     constexpr int NL = SH::PIX_GROUPS ? NP : 1;  // mask bit registers per thread
@@ -34,13 +34,15 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS, fwd_min_blocks(D, NP)) ras
     __shared__ float4 s_rgbd[kBatch];
     __shared__ float4 s_feat[kBatch * (D4 > 0 ? D4 : 1)];
 
+    if (binning_failed(status)) return;  // the binning overflowed or gave up: render nothing
     const int gt = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
     if (gt < 0 || gt >= vt.tile_off[vt.n_views]) return;  // not a permutation of the tiles: leave the tile
     const int v = view_of_tile(vt, gt);
     const int t = gt - vt.tile_off[v];
     const int tx = t % vt.TX[v], ty = t / vt.TX[v];
     const int tid = threadIdx.x;
-    const uint32_t start = ranges[2 * gt], end = ranges[2 * gt + 1];
+    uint32_t start = ranges[2 * gt], end = ranges[2 * gt + 1];
+    checked_range(start, end, capacity, status);
     const int64_t voff = (int64_t)v * vt.n;
     int bx0, by0;
     SH::warp_origin(tid >> 5, bx0, by0);
@@ -94,7 +96,7 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS, fwd_min_blocks(D, NP)) ras
         for (int i = tid; i < kBatch; i += NT) {
             const uint32_t j = b0 + i;
             if (j >= start && j < end) {
-                const uint32_t item = vals[j];
+                const uint32_t item = checked_item(vals[j], voff, vt.n, status);
                 const int64_t g = (int64_t)item - voff;
                 const float4 a = uvdo[item];
                 const float4 c = conic[item];
@@ -210,7 +212,7 @@ __global__ void __launch_bounds__(32, fwd_group_min_blocks(D, NP)) raster_fwd_gr
     const float4 *__restrict__ conic, const RT *__restrict__ rgb, const FT *__restrict__ feat,
     const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges, int64_t P, float *o_rgb, float *o_depth,
     float *o_sil, float *o_feat, float *o_T, int32_t *o_nc, int32_t *o_nb, uint32_t *bmask, int64_t bm_stride,
-    const uint32_t *__restrict__ order) {
+    const uint32_t *__restrict__ order, int32_t *status, int64_t capacity) {
     using SH = Shape<NP, true>;  // horizontal pixel pairs
     constexpr int D4 = D / 4, DD = D > 0 ? D : 1;
     constexpr int NL = SH::PIX_GROUPS ? NP : 1;  // mask bit registers per thread
@@ -219,6 +221,7 @@ __global__ void __launch_bounds__(32, fwd_group_min_blocks(D, NP)) raster_fwd_gr
     __shared__ float4 s_rgbd[32];
     __shared__ float4 s_feat[32 * (D4 > 0 ? D4 : 1)];
 
+    if (binning_failed(status)) return;  // the binning overflowed or gave up: render nothing
     const int rank = blockIdx.x / GW, grp = blockIdx.x % GW;
     const int gt = order ? (int)order[rank] : rank;
     if (gt < 0 || gt >= vt.tile_off[vt.n_views]) return;  // not a permutation of the tiles: leave the tile
@@ -227,7 +230,8 @@ __global__ void __launch_bounds__(32, fwd_group_min_blocks(D, NP)) raster_fwd_gr
     const int tx = t % vt.TX[v], ty = t / vt.TX[v];
     const int lane = threadIdx.x;
     const int tid = grp * 32 + lane;  // the thread's index in the tile kernel's numbering
-    const uint32_t start = ranges[2 * gt], end = ranges[2 * gt + 1];
+    uint32_t start = ranges[2 * gt], end = ranges[2 * gt + 1];
+    checked_range(start, end, capacity, status);
     const int64_t voff = (int64_t)v * vt.n;
     int bx0, by0;
     SH::warp_origin(grp, bx0, by0);
@@ -265,7 +269,7 @@ __global__ void __launch_bounds__(32, fwd_group_min_blocks(D, NP)) raster_fwd_gr
         {
             const uint32_t j = b0 + lane;
             if (j >= start && j < end) {
-                const uint32_t item = vals[j];
+                const uint32_t item = checked_item(vals[j], voff, vt.n, status);
                 const int64_t g = (int64_t)item - voff;
                 const float4 a = uvdo[item];
                 const float4 c = conic[item];
@@ -375,7 +379,7 @@ gs_status launch(const ViewTable &vt, const Params &prm, const gs_gaussians *g, 
             reinterpret_cast<const float4 *>(proj->conic), static_cast<const RT *>(g->rgb),
             static_cast<const FT *>(g->feat), bins->vals, bins->ranges, P, out->rgb, out->depth, out->sil,
             out->feat, out->T_final, out->n_contrib, out->n_blended, out->blend_mask, bins->capacity / 32 + 1,
-            bins->tile_order);
+            bins->tile_order, bins->status, bins->capacity);
     };
     if constexpr (NP <= 2) {
         if (prm.fwd_group) {

@@ -31,7 +31,6 @@ namespace {
 constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagPre = 2u << 30;
 constexpr uint32_t kValMask = (1u << 30) - 1;
-constexpr int kSpinLimit = 1 << 22;
 
 // ----------------------------------------------------------- block scan helper
 // Exclusive scan of one value per thread over a 256-thread block; returns the
@@ -83,7 +82,9 @@ __global__ void __launch_bounds__(1024) blocksum_scan_kernel(uint32_t *block_sum
                                                              uint32_t *counters, int slot, int cap_slot,
                                                              int64_t capacity, int64_t *n_inst, int32_t *status) {
     __shared__ uint32_t s_part[1024];
+    const bool failed = binning_failed(status);
     int64_t nb = nb_from ? ((int64_t)*nb_from + items_per_block - 1) / items_per_block : nb_fixed;
+    if (failed) return;  // whole block (the word is only written by earlier kernels)
     int64_t per = (nb + 1023) / 1024;
     int64_t b0 = (int64_t)threadIdx.x * per;
     uint32_t s = 0;
@@ -177,12 +178,15 @@ constexpr int kEmitBlock = 256;  // sorted items per block of the emission kerne
 
 __global__ void __launch_bounds__(kEmitBlock) emit_reduce_kernel(const uint32_t *sorted_items,
                                                                  const int32_t *touched, const uint32_t *counters,
-                                                                 uint32_t *block_sums) {
+                                                                 uint32_t *block_sums, int64_t vn,
+                                                                 const int32_t *status) {
     __shared__ uint32_t s_warp[9];
+    const bool failed = binning_failed(status);  // the depth sort gave up: its items are not valid
     const int64_t count = counters[CTR_NVIS];
     const int64_t i = (int64_t)blockIdx.x * kEmitBlock + threadIdx.x;
-    if ((int64_t)blockIdx.x * kEmitBlock >= count) return;
-    const uint32_t c = i < count ? (uint32_t)touched[sorted_items[i]] : 0u;
+    if (failed || (int64_t)blockIdx.x * kEmitBlock >= count) return;
+    const uint32_t it = i < count ? sorted_items[i] : 0u;
+    const uint32_t c = i < count && it < vn ? (uint32_t)touched[it] : 0u;
     uint32_t tot;
     block_exclusive_scan(c, &tot, s_warp);
     if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
@@ -199,18 +203,21 @@ __global__ void __launch_bounds__(kEmitBlock) emit_kernel(ViewTable vt, const ui
                                                           const float4 *conic, const uint32_t *counters,
                                                           const uint32_t *block_sums, int64_t capacity,
                                                           uint32_t *tile_keys, uint32_t *inst_vals, int n_passes,
-                                                          uint32_t *hist) {
+                                                          uint32_t *hist, int64_t vn, const int32_t *status) {
     __shared__ uint32_t s_warp[9];
     __shared__ uint32_t sh[4][256];
+    // whole block (the word is only written by earlier kernels): after a failed depth sort or an
+    // overflow nothing is emitted
+    const bool failed = binning_failed(status);
     const int64_t count = counters[CTR_NVIS];
-    if ((int64_t)blockIdx.x * kEmitBlock >= count) return;  // whole block: no barrier is skipped by part of it
+    if (failed || (int64_t)blockIdx.x * kEmitBlock >= count) return;  // whole block: no barrier is skipped
     for (int i = threadIdx.x; i < 4 * 256; i += kEmitBlock) (&sh[0][0])[i] = 0u;
     const int lane = threadIdx.x & 31;
     const int64_t i = (int64_t)blockIdx.x * kEmitBlock + threadIdx.x;
     uint32_t item = 0, c = 0;
     int x0 = 0, y0 = 0, w = 1, tx = 1;
     uint32_t tb = 0;
-    if (i < count) {
+    if (i < count && sorted_items[i] < vn) {
         item = sorted_items[i];
         c = (uint32_t)touched[item];
         const int v = (int)(item / (uint32_t)vt.n);
@@ -260,7 +267,7 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint32_t *
                                                                 uint32_t *keys_out, uint32_t *vals_out,
                                                                 const uint32_t *count_ptr, int shift,
                                                                 const uint32_t *pass_hist, uint32_t *tile_ctr,
-                                                                uint32_t *lookback, int32_t *status) {
+                                                                uint32_t *lookback, int32_t *status, int spin_limit) {
     constexpr int W = kSortThreads / 32;
     __shared__ uint32_t s_keys[kSortTile];
     __shared__ uint32_t s_vals[kSortTile];
@@ -270,12 +277,23 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint32_t *
     __shared__ uint32_t s_dbase[256];  // global exclusive digit base of the pass
     __shared__ uint32_t s_warp[9];
     __shared__ uint32_t s_tile;
+    __shared__ int s_failed;
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
+    if (tid == 0) {
+        s_tile = atomicAdd(tile_ctr, 1u);
+        s_failed = binning_failed(status);
+    }
     for (int i = tid; i < W * 256; i += kSortThreads) (&s_whist[0][0])[i] = 0;
     __syncthreads();
     const uint32_t tile = s_tile;
+    if (s_failed) {
+        // an earlier wait gave up (or the count overflowed): this pass's output is not used.  The
+        // block still publishes an inclusive prefix (0: never more than the true one, so a block
+        // that adds it scatters in bounds) so that no running block waits for it.
+        st_relaxed(lookback + (size_t)tile * 256 + tid, kFlagPre);
+        return;
+    }
     const int64_t n = *count_ptr;
     const int64_t base = (int64_t)tile * kSortTile;
     if (base >= n) return;
@@ -346,10 +364,11 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint32_t *
                 if (done) break;
                 if (t - i < 0) { done = true; break; }
                 uint32_t vv = w[i];
+                if (spin_limit < 0) { timeout = true; done = true; break; }  // test hook: give up at once
                 if ((vv & ~kValMask) == 0u) {
                     const uint32_t *pp = lookback + (size_t)(t - i) * 256 + d;
                     int spin = 0;
-                    while ((vv & ~kValMask) == 0u && spin < kSpinLimit) {
+                    while ((vv & ~kValMask) == 0u && spin < spin_limit) {
                         if (++spin > 64) __nanosleep(64);
                         vv = ld_relaxed(pp);
                     }
@@ -388,16 +407,23 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint32_t *
     }
 }
 
+// Per-tile [start, end) of the sorted instances.  Tile ids and items are checked against the
+// tile count and the item count: only a sort that gave up (status set, so nothing runs here)
+// could leave other values, but a range write out of bounds must not be possible at all.
 __global__ void __launch_bounds__(256) ranges_kernel(const uint32_t *tile_keys, const uint32_t *vals,
                                                      const uint32_t *counters, const float4 *uvdo, uint32_t *ranges,
-                                                     uint64_t *keys64) {
+                                                     uint64_t *keys64, int64_t n_tiles, int64_t vn,
+                                                     const int32_t *status) {
+    const bool failed = binning_failed(status);
     int64_t m = counters[CTR_M];
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= m) return;
+    if (failed || j >= m) return;
     uint32_t t = tile_keys[j];
+    if (t >= n_tiles) return;
     if (j == 0 || tile_keys[j - 1] != t) ranges[2 * (size_t)t] = (uint32_t)j;
     if (j == m - 1 || tile_keys[j + 1] != t) ranges[2 * (size_t)t + 1] = (uint32_t)(j + 1);
-    if (keys64) keys64[j] = ((uint64_t)t << 32) | __float_as_uint(uvdo[vals[j]].z);
+    const uint32_t it = vals[j];
+    if (keys64) keys64[j] = ((uint64_t)t << 32) | (it < vn ? __float_as_uint(uvdo[it].z) : 0u);
 }
 
 struct SortBufs {
@@ -409,14 +435,15 @@ struct SortBufs {
 // produced the keys).  Input in (k0, v0); output lands in (k0, v0) if n_passes is even,
 // else (k1, v1).
 gs_status radix_sort(SortBufs b, const uint32_t *count_ptr, int64_t max_count, int n_passes, const uint32_t *hist,
-                     uint32_t *lookback, int lb_tiles, uint32_t *tile_ctrs, int32_t *status, cudaStream_t st) {
+                     uint32_t *lookback, int lb_tiles, uint32_t *tile_ctrs, int32_t *status, int spin_limit,
+                     cudaStream_t st) {
     if (max_count <= 0 || n_passes <= 0) return GS_OK;
     int grid = ceil_div(max_count, kSortTile);
     uint32_t *ki = b.k0, *vi = b.v0, *ko = b.k1, *vo = b.v1;
     for (int p = 0; p < n_passes; ++p) {
         onesweep_kernel<<<grid, kSortThreads, 0, st>>>(ki, vi, ko, vo, count_ptr, 8 * p, hist + 256 * p,
                                                          tile_ctrs + p, lookback + (size_t)p * lb_tiles * 256,
-                                                         status);
+                                                         status, spin_limit);
         uint32_t *tk = ki, *tv = vi;
         ki = ko; vi = vo; ko = tk; vo = tv;
     }
@@ -532,7 +559,7 @@ extern "C" gs_status gs_bin_sort(int64_t n, const gs_projected *proj, const gs_c
 
     // 2. stable sort of the visible items by depth (4 passes: result in dk_a/dv_a)
     if ((s = radix_sort({dk_a, dv_a, dk_b, dv_b}, counters + CTR_NVIS, vn, 4, hist, lookback, L.lb_tiles_depth,
-                        counters + CTR_TILE, out->status, st)))
+                        counters + CTR_TILE, out->status, prm.spin_limit, st)))
         return s;
     const uint32_t *sorted_items = dv_a;
 
@@ -546,24 +573,25 @@ extern "C" gs_status gs_bin_sort(int64_t n, const gs_projected *proj, const gs_c
     uint32_t *emit_vals = (tile_passes % 2 == 0) ? out->vals : tv_b;
     uint32_t *other_vals = (tile_passes % 2 == 0) ? tv_b : out->vals;
     const int nbe = ceil_div(vn, kEmitBlock);
-    emit_reduce_kernel<<<nbe, kEmitBlock, 0, st>>>(sorted_items, proj->tiles_touched, counters, block_sums);
+    emit_reduce_kernel<<<nbe, kEmitBlock, 0, st>>>(sorted_items, proj->tiles_touched, counters, block_sums, vn,
+                                                   out->status);
     blocksum_scan_kernel<<<1, 1024, 0, st>>>(block_sums, counters + CTR_NVIS, 0, kEmitBlock, counters, CTR_MRAW, CTR_M,
                                              out->capacity, out->n_inst, out->status);
     emit_kernel<<<nbe, kEmitBlock, 0, st>>>(vt, sorted_items, proj->tiles_touched, uvdo, conic, counters, block_sums,
-                                    out->capacity, tk_a, emit_vals, tile_passes, hist + 4 * 256);
+                                    out->capacity, tk_a, emit_vals, tile_passes, hist + 4 * 256, vn, out->status);
     if ((s = last_launch())) return s;
     if (out->capacity == 0) return write_tile_order(out, total_tiles, st);
 
     // 4. stable sort of the instances by tile id
     if ((s = radix_sort({tk_a, emit_vals, tk_b, other_vals}, counters + CTR_M, out->capacity, tile_passes,
                         hist + 4 * 256, lookback + (size_t)4 * L.lb_tiles_depth * 256, L.lb_tiles_inst,
-                        counters + CTR_TILE + 4, out->status, st)))
+                        counters + CTR_TILE + 4, out->status, prm.spin_limit, st)))
         return s;
     const uint32_t *sorted_tiles = (tile_passes % 2 == 0) ? tk_a : tk_b;
 
     // 5. per-tile ranges (and the 64-bit keys if requested)
     ranges_kernel<<<ceil_div(out->capacity, 256), 256, 0, st>>>(sorted_tiles, out->vals, counters, uvdo, out->ranges,
-                                                                out->keys);
+                                                                out->keys, total_tiles, vn, out->status);
     if ((s = last_launch())) return s;
     return write_tile_order(out, total_tiles, st);
 }
