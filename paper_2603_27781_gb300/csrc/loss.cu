@@ -351,15 +351,19 @@ __global__ void __launch_bounds__(LossShape<D, KC>::NT) loss_kernel(
             __syncwarp();
         }
     }
-    if (K > 0) {
-        if constexpr (D > 0) {
-            if (kr < K) {
+    // the warps' sums enter the block's in warp order (one warp at a time), so the decoder
+    // gradient is the same bits on every run and through every entry point
+    for (int w = 0; w < SH::WARPS; ++w) {
+        if (K > 0 && wid == w) {
+            if constexpr (D > 0) {
+                if (kr < K) {
 #pragma unroll
-                for (int e = 0; e < EPL; ++e)
-                    if (accW[e] != 0.f) atomicAdd(&s_dW[kr * D + d0 + e], accW[e]);
+                    for (int e = 0; e < EPL; ++e) s_dW[kr * D + d0 + e] += accW[e];
+                }
             }
+            if (lane < K) s_dW[K * D + lane] += accb;
         }
-        if (lane < K && accb != 0.f) atomicAdd(&s_dW[K * D + lane], accb);
+        __syncthreads();
     }
     // per-block partials, weighted and normalised by the view's pixel count
     const double wc = block_sum_f64((double)lc * lp.color / (double)Pv, s_red);
@@ -812,16 +816,25 @@ static __device__ __align__(256) unsigned char g_noalloc_loss_scratch[kNoAllocBy
 constexpr int kNoAllocMaxDevices = 256;
 std::atomic<void *> g_noalloc_scratch_addr[kNoAllocMaxDevices];
 
-// Device address of the scratch array on the current device, looked up once per
-// device (host code only sees a host-side stand-in for the symbol).
-gs_status noalloc_scratch(char **out) {
+// Device address of the scratch array on the current device (host code only sees a
+// host-side stand-in for the symbol).  Outside a stream capture it is looked up on every
+// call (cheap once the module is loaded), so a context torn down and created again gets
+// its own address; during a capture, where the lookup is not attempted, the address of the
+// last call outside a capture on this device is used.
+gs_status noalloc_scratch(cudaStream_t st, char **out) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return GS_ERR_CUDA;
     if (dev < 0 || dev >= kNoAllocMaxDevices) return GS_ERR_UNSUPPORTED;
-    void *p = g_noalloc_scratch_addr[dev].load(std::memory_order_acquire);
-    if (!p) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    const bool capturing = cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone;
+    (void)cudaGetLastError();  // a refused query must not linger as the sticky last error
+    void *p = nullptr;
+    if (!capturing) {
         if (cudaGetSymbolAddress(&p, g_noalloc_loss_scratch) != cudaSuccess || !p) return GS_ERR_CUDA;
         g_noalloc_scratch_addr[dev].store(p, std::memory_order_release);
+    } else {
+        p = g_noalloc_scratch_addr[dev].load(std::memory_order_acquire);
+        if (!p) return GS_ERR_UNSUPPORTED;  // first call on this device inside a capture
     }
     *out = static_cast<char *>(p);
     return GS_OK;
@@ -846,9 +859,12 @@ extern "C" gs_status gs_loss_fwd_bwd_noalloc(const gs_camera *cams, int n_views,
         !tgt->label || !grad->rgb || !grad->depth || !grad->sil || (feat_dim && !grad->feat))
         return GS_ERR_ARG;
     if (lp->n_classes > 0 && (!dec_W || !dec_b || !d_dec_W || !d_dec_b)) return GS_ERR_ARG;
+    if (!(lp->ssim >= 0.f && lp->ssim <= 1.f) || (lp->ssim > 0.f && lp->mask_mode != 0)) return GS_ERR_ARG;
+    if (lp->ssim != 0.f) return GS_ERR_UNSUPPORTED;  // the SSIM maps need per-pixel scratch
+    // every argument is checked: only now is the shared array touched
     char *w = nullptr;
     gs_status s;
-    if ((s = noalloc_scratch(&w))) return s;
+    if ((s = noalloc_scratch(st, &w))) return s;
     uint32_t *mh = reinterpret_cast<uint32_t *>(w);
     float *part_f = reinterpret_cast<float *>(w + kNoAllocHistBytes);
     double *part_d = reinterpret_cast<double *>(w + kNoAllocHistBytes + kNoAllocPartFBytes);
@@ -861,7 +877,6 @@ extern "C" gs_status gs_loss_fwd_bwd_noalloc(const gs_camera *cams, int n_views,
             median_hist_kernel<<<grid, 256, 0, st>>>(vt, pass, img->depth, tgt->depth, mh);
         if ((s = last_launch())) return s;
     }
-    if (lp->ssim != 0.f) return GS_ERR_UNSUPPORTED;  // the SSIM maps need per-pixel scratch
     LossP q{lp->color, lp->depth, lp->sem, lp->tau_obs, lp->mask_mode, lp->n_classes};
 #define GS_LOSS(DD)                                                                                              \
     case DD:                                                                                                     \

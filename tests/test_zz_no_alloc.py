@@ -69,8 +69,9 @@ def _run_both(seed, sizes, weights):
     pairs = [(out["g_rgb"], r.g_rgb), (out["g_depth"], r.g_depth), (out["g_sil"], r.g_sil),
              (out["g_feat"], r.g_feat), (out["dW"], r.d_dec_W), (out["db"], r.d_dec_b), (out["loss"], r.loss_out),
              (out["mask"], r.mask), (out["median"], r.median)]
+    # the same kernels on the same inputs, every reduction in a fixed order: identical bits
     for got, want in pairs:
-        np.testing.assert_allclose(got.cpu().numpy(), want.cpu().numpy(), rtol=1e-5, atol=1e-9)
+        assert torch.equal(got, want)
     return out
 
 
@@ -96,17 +97,24 @@ def test_noalloc_loss_rejects_more_views_than_its_scratch_holds():
     assert status == L.GS_ERR_UNSUPPORTED
 
 
-def test_noalloc_loss_rejects_the_ssim_term():
-    """The SSIM maps of Eq. 15 need per-pixel scratch the static array does not hold."""
+@pytest.mark.parametrize("ssim,mask_mode,want", [(0.2, 0, L.GS_ERR_UNSUPPORTED), (0.2, 1, L.GS_ERR_ARG),
+                                                  (float("nan"), 0, L.GS_ERR_ARG), (1.5, 0, L.GS_ERR_ARG)])
+def test_noalloc_loss_refuses_the_ssim_term_before_any_launch(ssim, mask_mode, want):
+    """The SSIM maps of Eq. 15 need per-pixel scratch the static array does not hold: a nonzero
+    SSIM weight is refused (out-of-range or tracking-mode weights as argument errors, as by the
+    workspace entry point) before anything is launched: the loss output keeps its contents."""
     cams = [synth.camera(8, 8, 4.0)]
     r = raster.Renderer(0, cams, 0, 0, n_classes=1)
     p = lambda t: ctypes.c_void_p(t.data_ptr())
-    lp = L.gs_loss_params(0.5, 1.0, 0.0, 0, 0.99, 0, 0.2)
+    lp = L.gs_loss_params(0.5, 1.0, 0.0, mask_mode, 0.99, 0, ssim)
     tg = dict(rgb=torch.zeros(3, r.P, device="cuda"), depth=torch.ones(r.P, device="cuda"),
               label=torch.zeros(r.P, dtype=torch.uint8, device="cuda"))
     tgt = L.gs_targets(p(tg["rgb"]), p(tg["depth"]), p(tg["label"]))
     g = r.image_grads_c()
+    r.loss_out.fill_(7.0)
     status = L.gs_loss_fwd_bwd_noalloc(r.cams_c, 1, 0, ctypes.byref(r.images_c()), ctypes.byref(tgt), None, None,
                                        ctypes.byref(lp), ctypes.byref(g), None, None, p(r.loss_out), None, None,
                                        None)
-    assert status == L.GS_ERR_UNSUPPORTED
+    assert status == want
+    torch.cuda.synchronize()
+    assert (r.loss_out == 7.0).all()     # nothing ran
