@@ -1,6 +1,8 @@
 """Shared helpers of the GPU parity tests: seeded cases, the CUDA path, the oracle, comparison rules."""
 from __future__ import annotations
 
+import dataclasses
+
 import numpy as np
 import torch
 
@@ -8,18 +10,25 @@ import oracle
 from paper_2603_27781_gb300 import raster, synth
 from paper_2603_27781_gb300 import _lib as L
 
-# Forward tolerances (FP32 vs FP64): rgb/sil/feat max abs, depth max relative.
+# Forward tolerances (FP32 vs FP64): rgb/sil/feat max abs, depth max relative (per pixel).
 TOL_ABS = 1e-5
 TOL_DEPTH_REL = 1e-5
 # Gradient tolerance: per group, max |g - r| <= 1e-3 max |r| and ||g - r|| <= 1e-3 ||r||.
 TOL_GRAD = 1e-3
-# A pixel whose nearest threshold decision (alpha_min, alpha_max, T_min) is within this
-# relative distance in the oracle is excluded (FP32 rounding may decide it differently).
-MARGIN = 1e-4
-# A pixel whose blend amplifies relative rounding of the 2D covariances by more than this
-# (oracle "sens": blend-weighted |A|dx^2 + 2|B dx dy| + |C|dy^2, halved) is excluded: at
-# f32's ~1e-7 relative rounding of Sigma2D its value is not determined to 1e-5.
+# The oracle states, per pixel, how well single-precision inputs determine it (render_fwd's
+# margin, sens, sens_depth: first-order bounds in units of a 1e-7 relative rounding of each
+# splat's 2D covariance and alpha).  A pixel is excluded from the element-wise comparison (and
+# counted) when a threshold decision is within MARGIN_MIN of its rounding bound, or when its
+# rounding bound exceeds the gradient tolerance (SENS_CUT x 1e-7 = 1e-3).  Where the bound
+# exceeds the forward tolerance (SENS_MAX x 1e-7 = 1e-5), that pixel's forward tolerance is
+# widened to WIDEN times its bound (absolute for colour, silhouette and features, relative
+# for the depth) and the pixel is still compared.
+MARGIN_MIN = 10.0
 SENS_MAX = 100.0
+SENS_CUT = 1e4
+WIDEN = 2.0
+# Largest excluded share of the compared pixels.
+EXCL_MAX = 5e-3
 
 
 def params_pair(**kw):
@@ -29,6 +38,22 @@ def params_pair(**kw):
 def box_case(n=2000, d=16, w=64, h=48, fx=60.0, seed=0, T=None):
     gs = synth.box_field(n, d, seed=seed)
     cam = synth.camera(w, h, fx, cx=w / 2, cy=h / 2, T_cw=T)
+    return gs, cam
+
+
+def offview_case(seed=7):
+    """Box scene with 300 of its 2,000 Gaussians moved beside the view, their centres at
+    |x/z| in [0.72, 1.0] (the Jacobian clamp starts at 0.69 for this camera), scales e times
+    larger, so their tails reach into the image: the clamped and the exact Jacobian of Eq. 3
+    give them different footprints."""
+    gs = synth.box_field(2000, 8, seed=seed)
+    cam = synth.camera(64, 48, 60.0, cx=32, cy=24)
+    g = synth.rng(seed + 1)
+    k = 300
+    z = gs.means[:k, 2]
+    side = np.where(g.random(k) < 0.5, -1.0, 1.0)
+    gs.means[:k, 0] = (side * g.uniform(0.72, 1.0, k) * z).astype(np.float32)
+    gs.log_scales[:k] += np.float32(1.0)
     return gs, cam
 
 
@@ -68,45 +93,123 @@ def gpu_binning(r):
             r.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2))
 
 
-def excluded_pixels(cam, orc_proj, gpu_proj, orc_img, tile=16):
-    """Pixels where FP32 and FP64 may legitimately differ: tiles covered by a splat whose
-    rectangle differs between the two projections, pixels whose nearest threshold decision
-    lies within MARGIN (relative) in the oracle, and ill-conditioned pixels (SENS_MAX)."""
+@dataclasses.dataclass
+class Exclusion:
+    """Pixels where FP32 and FP64 may legitimately differ, by reason: rect (a splat whose tile
+    rectangle differs between the two projections can be blended there), margin (a threshold
+    decision within MARGIN_MIN of its rounding bound) and cond (rounding bound above the
+    gradient tolerance).  shifted: the tiles where such a splat is in one list only, whose
+    later list positions (n_contrib) differ by one while the images agree.  widened: pixels
+    compared with a forward tolerance widened to their rounding bound."""
+    rect: np.ndarray
+    margin: np.ndarray
+    cond: np.ndarray
+    shifted: np.ndarray
+    widened: np.ndarray
+    n_rect_splats: int
+
+    @property
+    def mask(self):
+        return self.rect | self.margin | self.cond
+
+    def report(self, region=None):
+        r = np.ones_like(self.mask) if region is None else region
+        n = int(r.sum())
+        parts = {k: int((getattr(self, k) & r).sum()) for k in ("rect", "margin", "cond", "widened", "shifted")}
+        tot = int((self.mask & r).sum())
+        return (f"excluded {tot} of {n} pixels ({tot / max(n, 1):.3%}): rect {parts['rect']} "
+                f"({self.n_rect_splats} splats), margin {parts['margin']}, cond {parts['cond']}; "
+                f"tolerance widened at {parts['widened']}, list positions shifted at {parts['shifted']}")
+
+    def check(self, where, region=None, limit=EXCL_MAX):
+        r = np.ones_like(self.mask) if region is None else region
+        frac = (self.mask & r).sum() / max(int(r.sum()), 1)
+        print(f"{where}: {self.report(region)}")
+        assert frac <= limit, (where, self.report(region))
+        return self
+
+
+def exclusion(cam, orc_proj, gpu_proj, orc_img, alpha_min=1.0 / 255.0, tile=16):
+    """The Exclusion of one view: orc_proj / orc_img from the oracle, gpu_proj the GPU's
+    projection of the same Gaussians (same order).  A splat whose rectangle differs changes a
+    pixel's list only in the tiles one rectangle has and the other lacks, and only where it
+    can be blended (its oracle alpha reaches half of alpha_min; every pixel of those tiles
+    when alpha_min is 0)."""
     W, H = cam.width, cam.height
     g_rect, _ = oracle.rects(gpu_proj["uv"], gpu_proj["radius"], W, H, tile)
-    diff = np.nonzero(np.any(g_rect != orc_proj["rect"], axis=1))[0]
-    tx = (W + tile - 1) // tile
-    ty = (H + tile - 1) // tile
-    bad_tiles = np.zeros((ty, tx), bool)
+    o_rect = orc_proj["rect"]
+    diff = np.nonzero(np.any(g_rect != o_rect, axis=1))[0]
+    rect = np.zeros((H, W), bool)
+    shifted = np.zeros((H, W), bool)
     for i in diff:
-        for rc in (g_rect[i], orc_proj["rect"][i]):
-            bad_tiles[rc[1]:rc[3], rc[0]:rc[2]] = True
-    mask = np.repeat(np.repeat(bad_tiles, tile, 0), tile, 1)[:H, :W]
-    mask |= orc_img["margin"] < MARGIN
-    mask |= orc_img["sens"] > SENS_MAX
-    return mask, len(diff)
+        cover = np.zeros(((H + tile - 1) // tile, (W + tile - 1) // tile), np.int8)
+        for rc in (g_rect[i], o_rect[i]):
+            cover[rc[1]:rc[3], rc[0]:rc[2]] += 1
+        sym = np.repeat(np.repeat(cover == 1, tile, 0), tile, 1)[:H, :W]
+        if not sym.any():
+            continue
+        shifted |= sym
+        ys, xs = np.nonzero(sym)
+        if alpha_min > 0 and orc_proj["radius"][i] > 0:
+            A, B, C = orc_proj["conic"][i]
+            dx, dy = xs + 0.5 - orc_proj["uv"][i, 0], ys + 0.5 - orc_proj["uv"][i, 1]
+            a = orc_proj["opacity"][i] * np.exp(-0.5 * (A * dx * dx + C * dy * dy) - B * dx * dy)
+            keep = a >= 0.5 * alpha_min
+            ys, xs = ys[keep], xs[keep]
+        rect[ys, xs] = True
+    margin = orc_img["margin"] < MARGIN_MIN
+    cond = (orc_img["sens"] > SENS_CUT) | (orc_img["sens_depth"] > SENS_CUT)
+    widened = ~cond & ((orc_img["sens"] > SENS_MAX) | (orc_img["sens_depth"] > SENS_MAX))
+    return Exclusion(rect, margin, cond, shifted, widened, len(diff))
 
 
-def assert_forward_close(gimg, oimg, excl, D):
+def excluded_pixels(cam, orc_proj, gpu_proj, orc_img, tile=16, alpha_min=1.0 / 255.0):
+    ex = exclusion(cam, orc_proj, gpu_proj, orc_img, alpha_min, tile)
+    return ex.mask, ex.n_rect_splats
+
+
+def assert_forward_close(gimg, oimg, excl, D, shifted=None):
+    """Element-wise forward parity on the pixels not in excl: colour, silhouette and features
+    within TOL_ABS, depth within TOL_DEPTH_REL of the oracle's depth (0 where nothing is
+    blended), each widened to WIDEN times the pixel's first-order rounding bound where that is
+    larger; the last contributor equal outside the shifted tiles."""
     keep = ~excl
+    tol = np.maximum(TOL_ABS, WIDEN * 1e-7 * oimg["sens"])[keep]
     for k in ("rgb", "feat"):
         a, b = gimg[k], oimg[k]
         err = np.abs(a - b)[:, keep] if a.ndim == 3 else np.abs(a - b)[keep]
         if err.size:
-            assert err.max() <= TOL_ABS, (k, float(err.max()))
+            assert (err <= tol).all(), (k, float(err.max()), float((err / tol).max()))
     err = np.abs(gimg["sil"] - oimg["sil"])[keep]
-    assert err.size == 0 or err.max() <= TOL_ABS, ("sil", float(err.max()))
-    # depth: relative 1e-5 image-wise (max error over max depth, as for the gradient groups) and
-    # per pixel wherever the pixel is covered (sil >= 0.5); a faint pixel's depth is a small sum
-    # of weights whose f32 rounding is bounded by the silhouette tolerance instead
+    assert err.size == 0 or (err <= tol).all(), ("sil", float(err.max()), float((err / tol).max()))
     d_o, d_g = oimg["depth"][keep], gimg["depth"][keep]
     if d_o.size:
-        assert np.abs(d_g - d_o).max() <= TOL_DEPTH_REL * np.abs(oimg["depth"]).max(), ("depth", "image")
-        cov = oimg["sil"][keep] >= 0.5
-        if cov.any():
-            err = np.abs(d_g[cov] - d_o[cov]) / np.abs(d_o[cov])
-            assert err.max() <= TOL_DEPTH_REL, ("depth", float(err.max()))
-    np.testing.assert_array_equal(gimg["n_contrib"][keep], oimg["n_contrib"][keep])
+        rel = np.maximum(TOL_DEPTH_REL, WIDEN * 1e-7 * oimg["sens_depth"][keep])
+        err = np.abs(d_g - d_o)
+        bad = err > rel * np.abs(d_o)
+        assert not bad.any(), ("depth", int(bad.sum()), float((err / np.maximum(rel * np.abs(d_o), 1e-300)).max()))
+    same = keep if shifted is None else keep & ~shifted
+    np.testing.assert_array_equal(gimg["n_contrib"][same], oimg["n_contrib"][same])
+
+
+def rounding_report(gimg, oimg, excl):
+    """Observed FP32 error over the oracle's first-order rounding bound plus an allowance of
+    1e-6 (a tenth of the tolerance) for the rounding of the sums themselves, which the figure
+    does not model: |err| / (1e-7 sens + 1e-6) for colour, silhouette and features,
+    |err| / ((1e-7 sens_depth + 1e-6) |depth|) for the depth, on the kept pixels (max, 99.9 %
+    quantile per output)."""
+    keep = ~excl
+    out = {}
+    for k in ("rgb", "sil", "feat", "depth"):
+        e = np.abs(gimg[k] - oimg[k])
+        if k == "depth":
+            b = (1e-7 * oimg["sens_depth"] + 1e-6) * np.abs(oimg["depth"])
+        else:
+            b = 1e-7 * oimg["sens"] + 1e-6
+        ratio = np.where(e > 0, e / np.maximum(b, 1e-300), 0.0)
+        ratio = ratio[:, keep] if ratio.ndim == 3 else ratio[keep]
+        out[k] = (float(ratio.max()), float(np.quantile(ratio, 0.999))) if ratio.size else (0.0, 0.0)
+    return out
 
 
 def assert_grad_close(name, g, r, tol=TOL_GRAD):
@@ -175,12 +278,14 @@ def bwd_compare(gs, cams, prm_g, prm_o, seed=7, rgb_dtype=torch.float32, feat_dt
     gso = gs if gs_oracle is None else gs_oracle
     projs, bins, oimgs = oracle_multiview(gso, cams, prm_o)
     gp = gpu_projection(r)
-    grads_v, P_off = [], 0
+    grads_v, P_off, excls = [], 0, []
     for v, cam in enumerate(cams):
         sl = slice(v * gs.n, (v + 1) * gs.n)
         gpv = {k: a[sl] for k, a in gp.items()}
-        excl, _ = excluded_pixels(cam, projs[v], gpv, oimgs[v])
-        assert_forward_close(np_images(r, v), oimgs[v], excl, gs.feat_dim)
+        ex = exclusion(cam, projs[v], gpv, oimgs[v], prm_o.alpha_min).check(f"view {v} ({cam.width}x{cam.height})")
+        excls.append(ex)
+        excl = ex.mask
+        assert_forward_close(np_images(r, v), oimgs[v], excl, gs.feat_dim, ex.shifted)
         P = cam.width * cam.height
         g = random_image_grads(P, gs.feat_dim, seed + v)
         keep = ~excl.ravel()
@@ -198,6 +303,7 @@ def bwd_compare(gs, cams, prm_g, prm_o, seed=7, rgb_dtype=torch.float32, feat_dt
     r.backward(field, L.GS_GRAD_MAP | L.GS_GRAD_POSE)
     torch.cuda.synchronize()
     ob = oracle_multiview_backward(gso, cams, prm_o, projs, bins, grads_v)
+    ob["images"], ob["exclusions"] = oimgs, excls
     D = gs.feat_dim
     got = dict(means=r.d_means, quats=r.d_quats, log_scales=r.d_log_scales, opacity_logits=r.d_logits, rgb=r.d_rgb,
                feat=r.d_feat[:, :D], twist=r.d_twist)

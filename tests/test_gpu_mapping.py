@@ -99,6 +99,9 @@ def test_mapping_iteration_with_update_matches_oracle():
     z = {k: np.zeros_like(getattr(gs, k), dtype=np.float64) for k in GROUPS}
     p_ref, _, _ = oracle.adam_step({k: getattr(gs, k) for k in GROUPS}, ref["grads"], z, z, 1, oracle.MAPPING_LR)
     field, r = C.gpu_forward(gs, cam, prm_g, n_classes=8)
+    # every pixel of this scene is determined to the tolerances by its f32 inputs
+    ex = C.exclusion(cam, ref["proj"], C.gpu_projection(r), ref["img"], prm_o.alpha_min)
+    assert ex.check("mapping iteration").mask.sum() == 0
     opt = raster.MappingAdam(field)
     r.iteration(field, _targets(tgt), torch.as_tensor(dec.W).cuda(), torch.as_tensor(dec.b).cuda(),
                 raster.MAPPING_SSIM, L.GS_GRAD_MAP)

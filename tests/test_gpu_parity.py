@@ -64,6 +64,24 @@ def test_projection_matches_oracle(name):
     np.testing.assert_array_equal(gp["touched"], touched)
 
 
+@pytest.mark.parametrize("exact", [False, True])
+def test_jacobian_modes_match_oracle(exact):
+    """Gaussians beside the view: projection, forward and every gradient against the oracle
+    with the clamped Jacobian and with the exact one of Eq. 3, whose footprints differ."""
+    gs, cam = C.offview_case()
+    prm_g, prm_o = C.params_pair(exact_jacobian=exact)
+    _, r = C.gpu_forward(gs, cam, prm_g)
+    gp = C.gpu_projection(r)
+    op = oracle.project(gs, cam, prm_o)
+    vis = (gp["radius"] > 0) & (op["radius"] > 0)
+    scale = np.maximum(np.abs(op["conic"][vis, 0]), np.abs(op["conic"][vis, 2]))[:, None]
+    assert (np.abs(gp["conic"][vis] - op["conic"][vis]) <= 2e-4 * scale).all()
+    other = oracle.project(gs, cam, C.params_pair(exact_jacobian=not exact)[1])
+    moved = np.abs(other["conic"][:300] - op["conic"][:300]).max(1) > 1e-2 * np.abs(op["conic"][:300]).max(1)
+    assert moved.sum() > 100          # the two modes differ for the Gaussians beside the view
+    C.bwd_compare(gs, [cam], prm_g, prm_o, seed=21)
+
+
 def _check_sort(gs, cams, prm_g):
     _, r = C.gpu_forward(gs, cams, prm_g)
     assert r.status() == 0
@@ -104,9 +122,8 @@ def test_render_fwd_matches_oracle(name):
     _, r = C.gpu_forward(gs, cam, prm_g)
     gimg = C.np_images(r)
     op, _, oimg = oracle.forward(gs, cam, prm_o)
-    excl, ndiff = C.excluded_pixels(cam, op, C.gpu_projection(r), oimg)
-    assert excl.mean() < 5e-3, (excl.sum(), ndiff)
-    C.assert_forward_close(gimg, oimg, excl, gs.feat_dim)
+    ex = C.exclusion(cam, op, C.gpu_projection(r), oimg).check(name)
+    C.assert_forward_close(gimg, oimg, ex.mask, gs.feat_dim, ex.shifted)
     np.testing.assert_allclose(gimg["sil"] + gimg["T"], 1.0, atol=1e-5)
 
 
@@ -449,8 +466,8 @@ def test_full_iteration_tiny_scene(exact, ssim):
     wo, wg = (oracle.MAPPING_SSIM, raster.MAPPING_SSIM) if ssim else (oracle.MAPPING, raster.MAPPING)
     ref = oracle.step(gs, cam, prm_o, tgt, dec, wo)
     field, r = C.gpu_forward(gs, cam, prm_g, n_classes=8)
-    excl, _ = C.excluded_pixels(cam, ref["proj"], C.gpu_projection(r), ref["img"])
-    assert excl.sum() == 0
+    ex = C.exclusion(cam, ref["proj"], C.gpu_projection(r), ref["img"], prm_o.alpha_min)
+    assert ex.check("whole iteration").mask.sum() == 0
     tg = dict(rgb=torch.as_tensor(tgt.rgb.reshape(3, -1)).cuda(), depth=torch.as_tensor(tgt.depth.ravel()).cuda(),
               label=torch.as_tensor(tgt.label.ravel()).cuda())
     r.iteration(field, tg, torch.as_tensor(dec.W).cuda(), torch.as_tensor(dec.b).cuda(), wg,
@@ -479,6 +496,73 @@ def test_autograd_function_matches_direct_backward():
     for name, p, d in zip(("means", "quats", "log_scales", "logits", "rgb", "feat"), params,
                           (r.d_means, r.d_quats, r.d_log_scales, r.d_logits, r.d_rgb, r.d_feat)):
         C.assert_grad_close(name, p.grad.cpu().numpy(), d.cpu().numpy(), 1e-5)
+
+
+def _autograd_grads(r, gs, gl):
+    """Parameter gradients of sum_k <image_k, gl_k> through RasterizeSG."""
+    params = [torch.as_tensor(a).cuda().requires_grad_(True) for a in gs.arrays()]
+    rgb, depth, sil, feat = raster.rasterize(r, *params)
+    loss = (rgb * gl[0]).sum() + (depth * gl[1]).sum() + (sil * gl[2]).sum() + (feat * gl[3]).sum()
+    loss.backward()
+    return dict(zip(("means", "quats", "log_scales", "opacity_logits", "rgb", "feat"),
+                    (p.grad.double().cpu().numpy() for p in params)))
+
+
+@pytest.mark.parametrize("name", ["box_64x48", "room_20k_330x190"])
+def test_autograd_function_matches_oracle(name):
+    """Gradients of a linear functional of the rendered images through the torch.autograd
+    wrapper against the oracle's analytic backward of the same functional (upstream gradients
+    zero at the excluded pixels)."""
+    gs, cam = CASES[name]()
+    prm_g, prm_o = C.params_pair()
+    field, r = C.gpu_forward(gs, cam, prm_g)
+    proj, bins, oimg = oracle.forward(gs, cam, prm_o)
+    ex = C.exclusion(cam, proj, C.gpu_projection(r), oimg).check(f"autograd {name}")
+    g = C.random_image_grads(r.P, gs.feat_dim, 12)
+    keep = ~ex.mask.ravel()
+    gl = [torch.as_tensor(g[k] * keep, dtype=torch.float32).cuda() for k in ("rgb", "depth", "sil", "feat")]
+    got = _autograd_grads(r, gs, gl)
+    H, W = cam.height, cam.width
+    gimg = {k: (g[k] * keep).reshape((-1, H, W) if g[k].ndim == 2 else (H, W)) for k in g}
+    want = oracle.backward_from_image_grads(gs, cam, prm_o, proj, bins, gimg)
+    for k, v in got.items():
+        C.assert_grad_close(k, v, want[k])
+
+
+def test_autograd_function_matches_central_differences():
+    """The wrapper's gradients against FP64 central differences (step 1e-6) of the oracle's
+    render of the same functional, in exact mode (Eq. 4-7 without thresholds), on 24
+    parameters drawn over every group."""
+    gs, cam = C.box_case(300, 4, 48, 40, 45.0, seed=5)
+    kw = dict(alpha_min=0.0, alpha_max=1.0, T_min=0.0, radius_sigma=8.0)
+    prm_g, prm_o = C.params_pair(**kw)
+    field, r = C.gpu_forward(gs, cam, prm_g)
+    g = C.random_image_grads(r.P, 4, 13)
+    gl = [torch.as_tensor(g[k], dtype=torch.float32).cuda() for k in ("rgb", "depth", "sil", "feat")]
+    got = _autograd_grads(r, gs, gl)
+    H, W = cam.height, cam.width
+    gimg = {k: v.reshape((-1, H, W) if v.ndim == 2 else (H, W)) for k, v in g.items()}
+    base = synth.Gaussians(*(a.astype(np.float64) for a in gs.arrays()))
+
+    def functional(x):
+        img = oracle.forward(x, cam, prm_o)[2]
+        return sum(float((img[k] * gimg[k]).sum()) for k in gimg)
+
+    rng_ = synth.rng(14)
+    h = 1e-6
+    for k in range(24):
+        name = ("means", "quats", "log_scales", "opacity_logits", "rgb", "feat")[k % 6]
+        arr = getattr(base, name)
+        idx = np.unravel_index(int(rng_.integers(arr.size)), arr.shape)
+        keep = arr[idx]
+        arr[idx] = keep + h
+        fp = functional(base)
+        arr[idx] = keep - h
+        fm = functional(base)
+        arr[idx] = keep
+        fd = (fp - fm) / (2 * h)
+        scale = np.abs(got[name]).max()
+        assert abs(got[name][idx] - fd) <= 1e-3 * max(abs(fd), 1e-2 * scale), (name, idx, got[name][idx], fd)
 
 
 # ----------------------------------------------------------------- edge cases
@@ -511,6 +595,38 @@ def test_capacity_overflow_is_reported():
     assert r.status() == L.GS_ERR_CAPACITY
     op = oracle.project(gs, cam, oracle.Params())
     assert r.instances() == int(op["touched"].sum())
+
+
+def test_bounded_wait_that_gives_up_reports_timeout_and_renders_nothing():
+    """With the spin limit's test hook every radix-sort block after the first gives up its
+    look-back at once: the binning reports GS_ERR_TIMEOUT, the ranges stay empty, and the blend
+    kernels leave the images and the gradients as they were (the images keep a sentinel, the
+    zeroed gradients stay zero).  The same renderer then renders normally again."""
+    gs, cam = C.box_case(2000, 16, 64, 48, 60.0)
+    field, r = C.gpu_forward(gs, cam, C.params_pair()[0])
+    assert r.instances() > 2 * 2048                   # the tile sort has several blocks
+    good = {k: v.clone() for k, v in r.images().items()}
+    for t in (r.img_rgb, r.img_depth, r.img_sil, r.img_feat, r.img_T):
+        t.fill_(-7.0)
+    r.params = raster.RasterParams(spin_limit=-1)
+    r.prm_c = r.params.c()
+    r.forward(field)
+    r.g_rgb.fill_(1.0); r.g_depth.fill_(1.0); r.g_feat.fill_(1.0)
+    r.backward(field, L.GS_GRAD_MAP | L.GS_GRAD_POSE)
+    torch.cuda.synchronize()
+    assert r.status() == L.GS_ERR_TIMEOUT
+    assert int(r.ranges.view(torch.int32).abs().max()) == 0
+    for t in (r.img_rgb, r.img_depth, r.img_sil, r.img_feat, r.img_T):
+        assert bool((t == -7.0).all())
+    for t in (r.d_means, r.d_quats, r.d_log_scales, r.d_logits, r.d_rgb, r.d_feat, r.d_twist):
+        assert not bool(t.abs().max() > 0)
+    r.params = raster.RasterParams()
+    r.prm_c = r.params.c()
+    r.forward(field)
+    torch.cuda.synchronize()
+    assert r.status() == 0
+    for k, v in r.images().items():
+        assert torch.equal(v, good[k]), k
 
 
 def test_argument_errors_return_status():
