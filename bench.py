@@ -246,12 +246,26 @@ def kernels_per_step(n_tiles):
     return project + bin_sort + fwd + loss + bwd + proj_bwd + pose + dsr + step
 
 
-def fwd_bwd_flops(evaluated, blended, D):
-    """Algorithmic FP32 work of the two blend kernels (an FMA counts as 2, ex2 and min as 1)."""
+def listed_pairs(r, px_per_thread):
+    """(block, splat) pairs the per-group backward walks: set bits of the blend mask, per 8x4
+    group, or of the union of the two stacked groups of an 8x8 block with two pixels per thread."""
+    m = r.blend_mask.view(8, -1).cpu().numpy().view(np.uint32)
+    if px_per_thread == 2:
+        m = np.stack([m[0] | m[2], m[1] | m[3], m[4] | m[6], m[5] | m[7]])
+    return int(np.unpackbits(m.view(np.uint8)).sum())
+
+
+def fwd_bwd_flops(evaluated, blended, D, F=None, listed=0):
+    """Algorithmic FP32 work of the two blend kernels (an FMA counts as 2, ex2 and min as 1).
+    F: feature-like channels of the backward (D, or K with the factored feature gradient,
+    which adds W^T (K x D FMAs) and W f (as many) per listed (block, splat) pair)."""
+    F = D if F is None else F
     eval_pair = 12                       # 2 sub, fmul+ffma, 2 fmul + ffma, ex2, fmul, min
     fwd_blend = 12 + 2 * D               # T update, weight, 3 rgb + depth FMAs, silhouette add, D feature FMAs
-    bwd_blend = 54 + 6 * D               # T recovery, 5+D channels x (sub + 2 FMA), opacity/conic/centre terms
-    return evaluated * eval_pair + blended * fwd_blend, evaluated * eval_pair + blended * bwd_blend
+    bwd_blend = 54 + 6 * F               # T recovery, 5+F channels x (sub + 2 FMA), opacity/conic/centre terms
+    bwd_listed = 4 * F * D if F != D else 0
+    return (evaluated * eval_pair + blended * fwd_blend,
+            evaluated * eval_pair + blended * bwd_blend + listed * bwd_listed)
 
 
 class FormJob:
@@ -281,17 +295,19 @@ class FormJob:
         from paper_2603_27781_gb300 import autotune
         r = self.r
         r.forward(self.field)
-        r.loss(self.targets, self.W, self.b, self.w)
-        tuned, _ = autotune.tune_blend(r, self.field, self.mode)
+        fac = r.use_factored(self.W)
+        r.loss(self.targets, self.W, self.b, self.w, factored=fac)
+        tuned, _ = autotune.tune_blend(r, self.field, self.mode, factored=fac)
         return tuned
 
     def step(self):
         r, f, w = self.r, self.field, self.w
+        fac = r.use_factored(self.W)
         r.project(f)
         r.bin_sort()
         r.render_fwd(f)
-        r.loss(self.targets, self.W, self.b, w)
-        r.render_bwd(f, self.mode)
+        r.loss(self.targets, self.W, self.b, w, factored=fac)
+        r.render_bwd(f, self.mode, factored=fac)
         r.project_bwd(f, self.mode)
         r.side_by_side(lambda s: r.dsr(f, w.big, w.small, s),
                        lambda: (r.pose_grad(), r.pose_step(self.T_state, self.adam, 0, pose_f32=self.pose_f32)))
@@ -639,9 +655,10 @@ def run_ours(args, rank, world, local_rank):
         rec(2)
         r.render_fwd(f)
         rec(3)
-        r.loss(tg, W, b, w)
+        fac = r.use_factored(W)
+        r.loss(tg, W, b, w, factored=fac)
         rec(4)
-        r.render_bwd(f, mode)
+        r.render_bwd(f, mode, factored=fac)
         rec(5)
         r.project_bwd(f, mode)
         rec(6)
@@ -654,7 +671,7 @@ def run_ours(args, rank, world, local_rank):
     # launch shape of the blend kernels, tuned on this frame (untimed)
     from paper_2603_27781_gb300 import autotune
     r.forward(field)
-    r.loss(targets, W, b, w)
+    r.loss(targets, W, b, w, factored=r.use_factored(W))
     if args.shapes:
         f_s, b_s = args.shapes.split(",")
         tuned = dataclasses.replace(r.params, fwd_px_per_thread=int(f_s.lstrip("w")),
@@ -662,7 +679,7 @@ def run_ours(args, rank, world, local_rank):
                                     bwd_px_per_thread=int(b_s.lstrip("w")), bwd_blocks=1 if b_s.startswith("w") else 2)
         r.params, r.prm_c, tune_ms = tuned, tuned.c(), {}
     else:
-        tuned, tune_ms = autotune.tune_blend(r, field, mode)
+        tuned, tune_ms = autotune.tune_blend(r, field, mode, factored=r.use_factored(W))
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -676,6 +693,8 @@ def run_ours(args, rank, world, local_rank):
     blended = int(r.img_nb.sum(dtype=torch.int64).item())
     r.count_blended = False
     m_inst = r.instances()
+    factored = r.use_factored(W)
+    listed = listed_pairs(r, tuned.bwd_px_per_thread or 2) if factored else 0
 
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     events = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(args.steps)]
@@ -755,7 +774,7 @@ def run_ours(args, rank, world, local_rank):
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     props = torch.cuda.get_device_properties(dev)
     fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s, FMA = 2
-    fwd_fl, bwd_fl = fwd_bwd_flops(evaluated, blended, WORKLOAD["d"])
+    fwd_fl, bwd_fl = fwd_bwd_flops(evaluated, blended, WORKLOAD["d"], WORKLOAD["k"] if factored else None, listed)
     dom = int(np.argmax(per_stage))
     if stages[dom] in ("render_bwd", "render_fwd"):
         fl = bwd_fl if stages[dom] == "render_bwd" else fwd_fl
@@ -767,7 +786,9 @@ def run_ours(args, rank, world, local_rank):
         roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak, "traffic": captured_traffic(kname, shape, WORKLOAD["d"]),
                 "peak_source": f"FP32 FMA issue: {props.multi_processor_count} SMs x 128 lanes x 2 x {sm_max:.0f} MHz",
-                "work": f"{evaluated} evaluated pairs, {blended} blended pairs per launch"}
+                "work": f"{evaluated} evaluated pairs, {blended} blended pairs per launch"
+                        + (f", {listed} listed (block, splat) pairs (factored feature gradient, K = {WORKLOAD['k']})"
+                           if factored else "")}
     else:
         roof = {"kernel": stages[dom], "bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"),
                 "unit": "GB/s", "frac": None, "traffic": None}

@@ -197,20 +197,36 @@ typedef struct {
 } gs_images;
 
 /* Gradients of the loss w.r.t. the rendered images, same layout as gs_images.
- * sil may be NULL (treated as zero). */
+ * sil may be NULL (treated as zero).
+ * Factored feature gradient (optional): with feat_basis not NULL, the gradient of
+ * the features is feat_basis^T feat_coef, feat_basis being device f32
+ * [feat_rank, D] (the weights of a linear decoder, Eq. 8) and feat_coef device f32
+ * [feat_rank, P] planes (the gradient w.r.t. the decoder's logits, as
+ * gs_loss_fwd_bwd writes it), and feat is ignored.  gs_render_bwd then evaluates
+ * the K-term products and multiplies by feat_basis^T once per splat: the same
+ * gradient in fewer operations when feat_rank < D.  Supported by the per-group
+ * backward (feature dims 16 and 32 with the blend mask) for feat_rank <= 8, else
+ * GS_ERR_UNSUPPORTED.  feat_basis NULL: the fields after feat are not read. */
 typedef struct {
     const float *rgb;
     const float *depth;
     const float *sil;
     const float *feat;
+    const float *feat_coef;
+    const float *feat_basis;
+    int32_t feat_rank;
 } gs_image_grads;
 
-/* Writable image gradients produced by gs_loss_fwd_bwd. */
+/* Writable image gradients produced by gs_loss_fwd_bwd.  feat_coef (optional,
+ * device f32 [K, P]): if not NULL, the loss writes the gradient w.r.t. the
+ * decoder's logits there (the factored form of gs_image_grads, with the decoder
+ * weights as the basis) and does not write feat, which may then be NULL. */
 typedef struct {
     float *rgb;
     float *depth;
     float *sil;
     float *feat;
+    float *feat_coef;
 } gs_image_grads_out;
 
 /* Gradients w.r.t. the gs_gaussians parameters, all f32, same shapes. */

@@ -60,10 +60,13 @@ class gs_splat_grads(Structure):
 
 
 class gs_image_grads(Structure):
-    _fields_ = [("rgb", c_void_p), ("depth", c_void_p), ("sil", c_void_p), ("feat", c_void_p)]
+    _fields_ = [("rgb", c_void_p), ("depth", c_void_p), ("sil", c_void_p), ("feat", c_void_p),
+                ("feat_coef", c_void_p), ("feat_basis", c_void_p), ("feat_rank", c_int32)]
 
 
-gs_image_grads_out = gs_image_grads
+class gs_image_grads_out(Structure):
+    _fields_ = [("rgb", c_void_p), ("depth", c_void_p), ("sil", c_void_p), ("feat", c_void_p),
+                ("feat_coef", c_void_p)]
 
 
 class gs_field_mut(Structure):

@@ -32,13 +32,16 @@ def _time(fn, reps: int, stream) -> float:
     return ev[0].elapsed_time(ev[1]) / reps
 
 
-def tune_blend(r: Renderer, field, grad_mode: int = L.GS_GRAD_MAP, reps: int = 5, verbose: bool = False):
+def tune_blend(r: Renderer, field, grad_mode: int = L.GS_GRAD_MAP, reps: int = 5, verbose: bool = False,
+               factored: bool = False):
     """Returns (RasterParams with the fastest fwd/bwd launch shapes, timings in ms).  Shapes
     are keyed by pixels per thread (one block per tile) and "w1", "w2" (one 32-thread block
     per pixel group).
 
     The renderer's image gradients (r.g_*) must hold the gradients to time the
-    backward with (e.g. after a loss call); the projection and binning are run here.
+    backward with (e.g. after a loss call; with factored, a factored loss call, and only the
+    per-group shapes, which alone take that form, are timed); the projection and binning
+    are run here.
     """
     stream = torch.cuda.current_stream()
     base = r.params
@@ -63,9 +66,11 @@ def tune_blend(r: Renderer, field, grad_mode: int = L.GS_GRAD_MAP, reps: int = 5
     shapes.update({f"w{np_}": dict(bwd_px_per_thread=np_, bwd_blocks=L.GS_BWD_BLOCKS_GROUP)
                    for np_ in WARP_CANDIDATES})
     for key, shape in shapes.items():
+        if factored and shape["bwd_blocks"] == L.GS_BWD_BLOCKS_TILE:
+            continue
         r.prm_c = dataclasses.replace(base, **fwd, **shape).c()
         try:
-            timings["bwd"][key] = _time(lambda: r.render_bwd(field, grad_mode), reps, stream)
+            timings["bwd"][key] = _time(lambda: r.render_bwd(field, grad_mode, factored=factored), reps, stream)
         except L.GsError as e:
             if e.status != L.GS_ERR_UNSUPPORTED:
                 raise

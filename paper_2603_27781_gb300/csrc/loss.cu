@@ -182,7 +182,7 @@ template <int D, int KC>
 __global__ void __launch_bounds__(LossShape<D, KC>::NT) loss_kernel(
     ViewTable vt, LossP lp, const float *rgb, const float *depth, const float *sil, const float *feat,
     const float *trgb, const float *tdepth, const uint8_t *label, const float *Wd, const float *bd, int64_t P,
-    const uint32_t *med_hist, float *g_rgb, float *g_depth, float *g_sil, float *g_feat, float *part_f,
+    const uint32_t *med_hist, float *g_rgb, float *g_depth, float *g_sil, float *g_feat, float *g_coef, float *part_f,
     double *part_d, float *mask_out, float *median_out) {
     using SH = LossShape<D, KC>;
     constexpr int NT = SH::NT, DD = SH::DD, EPL = SH::EPL;
@@ -247,9 +247,6 @@ __global__ void __launch_bounds__(LossShape<D, KC>::NT) loss_kernel(
 #pragma unroll
             for (int d = 0; d < D; ++d) f[d] = feat[d * P + pix];
             const int lab = label[pix];
-            float gf[DD];
-#pragma unroll
-            for (int d = 0; d < DD; ++d) gf[d] = 0.f;
             if (lab != 255 && lab < K) {
                 // z = W f + b, each row read as float4 and summed in four partial sums
                 float z[KC];
@@ -294,9 +291,21 @@ __global__ void __launch_bounds__(LossShape<D, KC>::NT) loss_kernel(
                 const float scale = m * lp.sem * invP;
                 const float inv_se = 1.f / se;
 #pragma unroll
+                for (int k = 0; k < KC; ++k)
+                    if (k < K) dz[k] = scale * (e[k] * inv_se - (k == lab ? 1.f : 0.f));
+            }
+            if (g_coef) {
+                // the factored feature gradient: dL/dz itself (g_feat = W^T dz is left to the backward)
+#pragma unroll
+                for (int k = 0; k < KC; ++k)
+                    if (k < K) g_coef[k * P + pix] = dz[k];
+            } else {
+                float gf[DD];
+#pragma unroll
+                for (int d = 0; d < DD; ++d) gf[d] = 0.f;
+#pragma unroll
                 for (int k = 0; k < KC; ++k) {
                     if (k < K) {
-                        dz[k] = scale * (e[k] * inv_se - (k == lab ? 1.f : 0.f));
                         if constexpr (D % 4 == 0) {
                             const float4 *wr = reinterpret_cast<const float4 *>(s_W + k * D);
 #pragma unroll
@@ -313,9 +322,9 @@ __global__ void __launch_bounds__(LossShape<D, KC>::NT) loss_kernel(
                         }
                     }
                 }
-            }
 #pragma unroll
-            for (int d = 0; d < D; ++d) g_feat[d * P + pix] = gf[d];
+                for (int d = 0; d < D; ++d) g_feat[d * P + pix] = gf[d];
+            }
         }
         if (K > 0) {
             // stage the warp's dz and f, then accumulate this lane's dW / db entries over its 32 pixels
@@ -683,11 +692,11 @@ gs_status launch_loss(const ViewTable &vt, const LossP &lp, const gs_images *img
     if (lp.K <= 8)
         loss_kernel<D, 8><<<grid, LossShape<D, 8>::NT, 0, st>>>(
             vt, lp, img->rgb, img->depth, img->sil, img->feat, tgt->rgb, tgt->depth, tgt->label, W, b, P, mh, g->rgb,
-            g->depth, g->sil, g->feat, part_f, part_d, mask_out, median_out);
+            g->depth, g->sil, g->feat, g->feat_coef, part_f, part_d, mask_out, median_out);
     else
         loss_kernel<D, kMaxK><<<grid, LossShape<D, kMaxK>::NT, 0, st>>>(
             vt, lp, img->rgb, img->depth, img->sil, img->feat, tgt->rgb, tgt->depth, tgt->label, W, b, P, mh, g->rgb,
-            g->depth, g->sil, g->feat, part_f, part_d, mask_out, median_out);
+            g->depth, g->sil, g->feat, g->feat_coef, part_f, part_d, mask_out, median_out);
     int rows = bx * vt.n_views;
     if (lp.ssim_coef != 0.f) {
         // the SSIM tiles add their colour-term shares as further partial rows
@@ -716,7 +725,7 @@ extern "C" gs_status gs_loss_fwd_bwd(const gs_camera *cams, int n_views, int fea
     if (!feat_dim_ok(feat_dim)) return GS_ERR_UNSUPPORTED;
     if (lp->n_classes < 0 || lp->n_classes > kMaxK || (lp->mask_mode != 0 && lp->mask_mode != 1)) return GS_ERR_ARG;
     if (!img->rgb || !img->depth || !img->sil || (feat_dim && !img->feat) || !tgt->rgb || !tgt->depth ||
-        !tgt->label || !grad->rgb || !grad->depth || !grad->sil || (feat_dim && !grad->feat))
+        !tgt->label || !grad->rgb || !grad->depth || !grad->sil || (feat_dim && !grad->feat && !grad->feat_coef))
         return GS_ERR_ARG;
     if (lp->n_classes > 0 && (!dec_W || !dec_b || !d_dec_W || !d_dec_b)) return GS_ERR_ARG;
     if (!(lp->ssim >= 0.f && lp->ssim <= 1.f) || (lp->ssim > 0.f && lp->mask_mode != 0)) return GS_ERR_ARG;
@@ -856,7 +865,7 @@ extern "C" gs_status gs_loss_fwd_bwd_noalloc(const gs_camera *cams, int n_views,
     if (!feat_dim_ok(feat_dim)) return GS_ERR_UNSUPPORTED;
     if (lp->n_classes < 0 || lp->n_classes > kMaxK || (lp->mask_mode != 0 && lp->mask_mode != 1)) return GS_ERR_ARG;
     if (!img->rgb || !img->depth || !img->sil || (feat_dim && !img->feat) || !tgt->rgb || !tgt->depth ||
-        !tgt->label || !grad->rgb || !grad->depth || !grad->sil || (feat_dim && !grad->feat))
+        !tgt->label || !grad->rgb || !grad->depth || !grad->sil || (feat_dim && !grad->feat && !grad->feat_coef))
         return GS_ERR_ARG;
     if (lp->n_classes > 0 && (!dec_W || !dec_b || !d_dec_W || !d_dec_b)) return GS_ERR_ARG;
     if (!(lp->ssim >= 0.f && lp->ssim <= 1.f) || (lp->ssim > 0.f && lp->mask_mode != 0)) return GS_ERR_ARG;

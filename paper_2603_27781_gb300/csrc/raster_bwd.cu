@@ -1,6 +1,6 @@
 // Entry point of the blend backward (kernels in raster_bwd.cuh, instantiated by
 // raster_bwd_map.cu and raster_bwd_pose.cu).
-#include "raster_bwd.cuh"
+#include "raster_bwd_warp.cuh"
 
 namespace gs {
 bool storage_ok(const gs_gaussians *g);
@@ -22,9 +22,11 @@ extern "C" gs_status gs_render_bwd(const gs_gaussians *g, const gs_projected *pr
     if (g->n == 0) return GS_OK;
     if (!storage_ok(g)) return GS_ERR_UNSUPPORTED;
     if (!sg->uvod || !sg->conic || (map && (!sg->rgb || (g->feat_dim && !d_feat)))) return GS_ERR_ARG;
+    const bool factored = dL->feat_basis != nullptr;
     if (!proj->uvdo || !proj->uv_lo || !proj->conic || !bins->vals || !bins->ranges || !fwd->T_final || !fwd->n_contrib ||
-        !dL->rgb || !dL->depth || (g->feat_dim && !dL->feat))
+        !dL->rgb || !dL->depth || (g->feat_dim && !factored && !dL->feat) || (factored && !dL->feat_coef))
         return GS_ERR_ARG;
+    if (factored && (dL->feat_rank < 1 || dL->feat_rank > kFactorK)) return GS_ERR_UNSUPPORTED;
     if ((reinterpret_cast<uintptr_t>(sg->uvod) | reinterpret_cast<uintptr_t>(sg->conic) |
          reinterpret_cast<uintptr_t>(sg->rgb) | reinterpret_cast<uintptr_t>(d_feat)) & 15)
         return GS_ERR_ARG;
@@ -56,6 +58,9 @@ extern "C" gs_status gs_render_bwd(const gs_gaussians *g, const gs_projected *pr
     A.g_depth = dL->depth;
     A.g_sil = dL->sil;
     A.g_feat = dL->feat;
+    A.feat_coef = factored ? dL->feat_coef : nullptr;
+    A.feat_basis = factored ? dL->feat_basis : nullptr;
+    A.feat_rank = factored ? dL->feat_rank : 0;
     A.acc_uvod = acc_uvod;
     A.acc_conic = acc_conic;
     A.acc_rgb = acc_rgb;
@@ -71,6 +76,7 @@ extern "C" gs_status gs_render_bwd(const gs_gaussians *g, const gs_projected *pr
     const bool group_ok = (D == 16 || D == 32) && A.bmask && prm.bwd_np <= 2;
     Params pr = prm;
     pr.bwd_warp = prm.bwd_blocks == GS_BWD_BLOCKS_GROUP || (prm.bwd_blocks == GS_BWD_BLOCKS_DEFAULT && group_ok);
+    if (factored && !pr.bwd_warp) return GS_ERR_UNSUPPORTED;  // the tile kernel takes the features' gradient
     // default pixels per thread: 2 for the per-group form at D = 16 (8x8 blocks), else 1
     const int np = prm.bwd_np ? prm.bwd_np : (pr.bwd_warp ? (D == 16 ? 2 : 1) : default_bwd_np(D));
     const bool half = g->rgb_dtype == GS_F16;

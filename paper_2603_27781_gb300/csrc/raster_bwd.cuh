@@ -110,6 +110,10 @@ struct BwdArgs {
     const float *T_final;
     const int32_t *n_contrib;
     const float *g_rgb, *g_depth, *g_sil, *g_feat;
+    // factored feature gradient g_feat = feat_basis^T feat_coef (NULL basis: g_feat as given)
+    const float *feat_coef;   // [feat_rank, P]
+    const float *feat_basis;  // [feat_rank, D]
+    int feat_rank;
     float4 *acc_uvod, *acc_conic, *acc_rgb;
     float *d_feat;
     const uint32_t *bmask;  // blend-mask planes from the forward (NULL: scan every splat)
@@ -461,6 +465,11 @@ gs_status dispatch_bwd(int D, int np, bool half, const ViewTable &vt, const Para
     return GS_ERR_UNSUPPORTED;
 }
 
+// The per-group form with half storage (f16 colour, bf16 features), one translation unit per mode.
+gs_status dispatch_bwd_warp_map_half(int D, int np, const ViewTable &vt, const Params &prm, const BwdArgs &A,
+                                     cudaStream_t st);
+gs_status dispatch_bwd_warp_pose_half(int D, int np, const ViewTable &vt, const Params &prm, const BwdArgs &A,
+                                      cudaStream_t st);
 gs_status dispatch_bwd_map(int D, int np, bool half, const ViewTable &vt, const Params &prm, const BwdArgs &A,
                            cudaStream_t st);
 gs_status dispatch_bwd_pose(int D, int np, bool half, const ViewTable &vt, const Params &prm, const BwdArgs &A,

@@ -1,83 +1,102 @@
 // Blend backward (Eq. 4-7 differentiated) with one single-warp block per pixel
 // group, D 16 or 32, with the forward's blend mask: map mode (every parameter's
-// sums, the weighted terms deferred) and pose-only mode (the six sums the
-// projection backward needs for the twist).
+// sums) and pose-only mode (the six sums the projection backward needs for the
+// twist).
 //
 // The tile kernel's eight warps share one staged splat batch and meet at a CTA
 // barrier per batch, so a tile's warps all wait for whichever of them has the
 // longest masked list, and the CTA holds its registers and shared memory until
-// its slowest warp ends.  Here each pixel group (the same 8x4 groups, NP of them
-// per warp) is its own 32-thread block: it builds its own list of the instances
-// its pixels blended (back to front, from the mask words), stages 16 splat
-// records at a time in its own shared memory, runs the same per-pixel recurrence
-// and the same deferred contraction of the alpha-T weighted terms, and adds its
-// sums to the per-Gaussian accumulators with L2 reductions (one warp-wide scalar
-// instruction for the six geometric sums, float4/float2 ones for the deferred
-// terms).  Nothing waits on another warp, and a finished group frees its
-// resources at once.
+// its slowest warp ends.  Here each pixel group (an 8x4 group, or an 8x8 block of
+// two with two pixels per thread) is its own 32-thread block: it builds its own
+// list of the instances its pixels blended (back to front, from the mask words),
+// stages a few splat records at a time in its own shared memory and runs the
+// per-pixel recurrence on them.  Nothing waits on another warp, and a finished
+// group frees its resources at once.
+//
+// Map mode defers every per-splat sum.  While it walks a stage of splats, each
+// pixel only records, per splat, its weight w = alpha T (the factor of the depth,
+// colour and feature gradients) and dpow = o G dL/dalpha (zero where alpha is
+// clamped), the factor of every geometric gradient: with (lx, ly) the pixel centre
+// relative to the block centre and (cx, cy) the splat centre, dx = lx - cx, so the
+// centre and conic gradients need only the moments of dpow
+//   S1, Sx, Sy, Sxx, Sxy, Syy = sum over pixels of dpow (1, lx, ly, lx^2, lx ly, ly^2),
+// expanded about the splat centre afterwards (sum dpow dx = Sx - cx S1, and so on),
+// and the opacity gradient is S1 / o.  After the stage, lanes (slot, part) contract
+// the slots with the block's per-pixel terms (weights against the gradients of
+// depth, colour and features; dpow against the fixed coordinates) in one pass of
+// FP32 FMAs, and each slot's sums go out as 16-byte L2 reductions.  No warp
+// reduction runs per splat.
+//
+// Factored feature gradients.  When the image gradient of the features comes from
+// a linear decoder (Eq. 8 read as a 1x1 convolution), g_feat = W^T e with e the
+// gradient of the K logits.  Then g_feat . f = e . (W f) and sum_p w_p g_feat,p =
+// W^T sum_p w_p e_p, so the kernel stages z = W f (K values) per splat, evaluates
+// the K-term dot product per pixel and contracts K terms, and multiplies by W^T once
+// per splat: the same sums, in fewer operations when K < D.
 #pragma once
 
 #include "raster_bwd.cuh"
 
 namespace gs {
 
-// Adds terms [T0, T0 + HW) of a deferred row (depth, r, g, b, then the D
-// features) to the accumulators: depth to acc_uvod[item].w, colour as one float4,
-// features as float4 / float2 runs on their natural alignment.
-template <int D, int HW, int T0>
-__device__ __forceinline__ void add_deferred(const float (&a)[HW], int64_t item, int64_t g, float4 *acc_uvod,
-                                             float4 *acc_rgb, float *d_feat) {
-    if constexpr (T0 == 0) {
-        if (a[0] != 0.f) atomicAdd(reinterpret_cast<float *>(acc_uvod + item) + 3, a[0]);
-        if (a[1] != 0.f || a[2] != 0.f || a[3] != 0.f) atomicAdd(acc_rgb + g, make_float4(a[1], a[2], a[3], 0.f));
-    }
-    constexpr int fa = (T0 > 4 ? T0 : 4) - 4;  // first feature of these terms
-    constexpr int fb = T0 + HW - 4;            // one past the last
-    float *f = d_feat + g * D;
-#pragma unroll
-    for (int q = 0; q < D / 4; ++q) {
-        const int lo = 4 * q > fa ? 4 * q : fa, hi = 4 * q + 4 < fb ? 4 * q + 4 : fb;
-        if (lo >= hi) continue;
-        const int c0 = lo + 4 - T0;  // index of feature lo in a[]
-        if (hi - lo == 4) {
-            const float4 v = make_float4(a[c0], a[c0 + 1], a[c0 + 2], a[c0 + 3]);
-            if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f)
-                atomicAdd(reinterpret_cast<float4 *>(f + lo), v);
-        } else if (hi - lo == 2 && (lo & 1) == 0) {
-            const float2 v = make_float2(a[c0], a[c0 + 1]);
-            if (v.x != 0.f || v.y != 0.f) atomicAdd(reinterpret_cast<float2 *>(f + lo), v);
-        } else {
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                if (k < hi - lo && a[c0 + k] != 0.f) atomicAdd(f + lo + k, a[c0 + k]);
-        }
-    }
+// Feature-like gradient channels per pixel in the factored form: the K <= kFactorK logit
+// gradients (zero beyond K).
+constexpr int kFactorK = 8;
+
+// Map-mode layout: SL slots (splats staged and contracted together), LPS = 32 / SL
+// lanes per slot in the contraction, each owning HW of the NWT weighted terms and
+// RPL of the block's pixel rows in the moments.
+template <int D, int NP, int KF, int SL>
+struct WarpMapLayout {
+    static constexpr int F = KF ? KF : D;
+    static constexpr int PXW = 32 * NP;         // pixels of the block, 8 wide
+    static constexpr int ROWS = PXW / 8;
+    static constexpr int LPS = 32 / SL;
+    static constexpr int NWT = 4 + F;           // weighted terms: depth, r, g, b, F
+    static constexpr int HW = NWT / LPS;
+    static constexpr int HWP = (HW + 3) / 4 * 4;
+    static constexpr int GROW = LPS * HWP;      // a pixel's row of weighted terms
+    static constexpr int WROW = PXW + 4;        // a slot's row of per-pixel values (padded against bank conflicts)
+    static constexpr int RPL = ROWS / LPS;
+    static_assert(NWT % LPS == 0 && ROWS % LPS == 0 && D % (4 * LPS) == 0, "lanes per slot divide the work");
+};
+
+// Slots per stage in map mode: 8 (four lanes per slot) keeps the per-slot arrays small
+// enough for more resident blocks; pose mode stages 16.
+constexpr int kMapSlots = 8;
+constexpr int kPoseStage = 16;
+
+// Resident blocks per SM the register allocation must allow: 24 with one pixel per thread
+// (80 registers), 16 with two (128), except where 16 would spill at D = 32: the map mode with
+// the features themselves (whose 19.5 KB of shared memory allows 11 blocks anyway) and the
+// pose mode with the factored form.
+template <int D, int NP, bool MAP, int KF> constexpr int warp_bwd_min_blocks() {
+    return NP == 1 ? 24 : (D == 32 && (MAP ? KF == 0 : KF > 0)) ? (MAP ? 11 : 12) : 16;
 }
 
-// Register cap: with one pixel per thread 24 blocks per SM (80 registers at D = 16; shared
-// memory would allow 26); with two, shared memory bounds the blocks at 16, which 127
-// registers still allow.
-template <int D, int NP> constexpr int warp_bwd_min_blocks() { return NP == 1 ? 24 : 16; }
-
-template <int D, int NP, bool MAP, typename RT, typename FT>
-__global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP>())
+template <int D, int NP, bool MAP, int KF, typename RT, typename FT>
+__global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP, MAP, KF>())
     raster_bwd_warp_kernel(ViewTable vt, Params prm, BwdArgs A) {
-    using LY = BwdLayout<D, NP, MAP>;
     using SH = Shape<NP>;
-    static_assert(!MAP || LY::DEFER, "the map-mode warp-block backward is the deferred form");
-    constexpr int D4 = D / 4;
-    constexpr int NCH = 5 + D;
-    constexpr int GW = SH::WARPS;  // pixel-group blocks per tile
-    constexpr int STAGE = 16;      // splat records staged at a time
+    using WL = WarpMapLayout<D, NP, KF, kMapSlots>;
+    constexpr int F = WL::F;
+    constexpr int F4 = F / 4;
+    constexpr int NCH = 5 + F;            // r, g, b, depth, sil, then F
+    constexpr int GW = SH::WARPS;         // pixel-group blocks per tile
+    constexpr int STAGE = MAP ? kMapSlots : kPoseStage;
+    constexpr int PARTS = 32 / STAGE;     // lanes per staged splat
+    static_assert(F % 4 == 0 && (KF == 0 || KF % PARTS == 0), "staged values in float4 / lane parts");
     __shared__ SplatGeo s_geo[STAGE];
     __shared__ float4 s_rgbd[STAGE];
-    __shared__ float4 s_feat[STAGE * D4];
+    __shared__ __align__(16) float s_feat[STAGE * F];  // features, or z = W f in the factored form
     __shared__ uint32_t s_item[STAGE];
     __shared__ int s_pos[STAGE];
     __shared__ uint32_t s_list[64];
-    __shared__ __align__(16) float s_w[MAP ? LY::SLOTS * LY::WROW : 4];
-    __shared__ __align__(16) float s_g[MAP ? LY::PXW * LY::GROW : 4];
-    __shared__ uint32_t s_slot_item[MAP ? LY::SLOTS : 1];
+    __shared__ __align__(16) float s_w[MAP ? STAGE * WL::WROW : 4];   // [slot][pixel] alpha T
+    __shared__ __align__(16) float s_p[MAP ? STAGE * WL::WROW : 4];   // [slot][pixel] dpow
+    __shared__ __align__(16) float s_g[MAP ? WL::PXW * WL::GROW : 4]; // [pixel][part][term] gradients
+    __shared__ float s_t[MAP ? STAGE * WL::NWT : 4];                  // [slot][term] summed terms
+    __shared__ float s_basis[KF ? KF * D : 1];                        // W, K x D (rows >= K zero)
     const RT *rgb = static_cast<const RT *>(A.rgb);
     const FT *feat = static_cast<const FT *>(A.feat);
 
@@ -93,6 +112,14 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP>())
     const uint32_t start = A.ranges[2 * gt];
     const int64_t voff = (int64_t)v * vt.n;
     const int64_t P = A.P;
+    int bx0, by0;
+    SH::warp_origin(grp, bx0, by0);
+    // block centre: pixel (lx, ly) of the block sits at (lx - 3.5, ly + 0.5 - ROWS / 2) from it
+    const float bcx = (float)(tx * kTile + bx0) + 4.f, bcy = (float)(ty * kTile + by0) + 0.5f * WL::ROWS;
+
+    if constexpr (KF > 0) {
+        for (int i = lane; i < KF * D; i += 32) s_basis[i] = i < A.feat_rank * D ? A.feat_basis[i] : 0.f;
+    }
 
     float gch[NP][NCH], T[NP], gS[NP], pxc[NP], pyc[NP];
     int last[NP];
@@ -117,73 +144,157 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP>())
             gch[p][2] = A.g_rgb[2 * P + pix];
             gch[p][3] = A.g_depth[pix];
             gch[p][4] = A.g_sil ? A.g_sil[pix] : 0.f;
+            if constexpr (KF > 0) {
 #pragma unroll
-            for (int d = 0; d < D; ++d) gch[p][5 + d] = A.g_feat[d * P + pix];
+                for (int k = 0; k < KF; ++k) gch[p][5 + k] = k < A.feat_rank ? A.feat_coef[k * P + pix] : 0.f;
+            } else {
+#pragma unroll
+                for (int d = 0; d < D; ++d) gch[p][5 + d] = A.g_feat[d * P + pix];
+            }
         }
         gS[p] = gch[p][0] * prm.bg[0] + gch[p][1] * prm.bg[1] + gch[p][2] * prm.bg[2];
         my_max = max(my_max, last[p]);
     }
     const int wmax = checked_last(start, A.ranges, gt, __reduce_max_sync(0xffffffffu, my_max), A.capacity, A.status);
     if (wmax == 0) return;  // no pixel of the group blended anything (warp-uniform)
-    // the group's pixel p * 32 + lane: gradients of depth, r, g, b, features
+    if constexpr (MAP) {
+        // pixel q = p * 32 + lane of the block: its weighted terms (depth, r, g, b, F), part by part
 #pragma unroll
-    for (int p = 0; p < (MAP ? NP : 0); ++p) {
-        float term[LY::NW];
-        term[0] = gch[p][3];
-        term[1] = gch[p][0];
-        term[2] = gch[p][1];
-        term[3] = gch[p][2];
+        for (int p = 0; p < NP; ++p) {
+            float term[WL::NWT];
+            term[0] = gch[p][3];
+            term[1] = gch[p][0];
+            term[2] = gch[p][1];
+            term[3] = gch[p][2];
 #pragma unroll
-        for (int d = 0; d < D; ++d) term[4 + d] = gch[p][5 + d];
-        float *row = s_g + (p * 32 + lane) * LY::GROW;
+            for (int f = 0; f < F; ++f) term[4 + f] = gch[p][5 + f];
+            float *row = s_g + (p * 32 + lane) * WL::GROW;
 #pragma unroll
-        for (int c = 0; c < LY::GROW; ++c) {
-            const int h = c / LY::HWP, i = c % LY::HWP;
-            row[c] = i < LY::HW ? term[h * LY::HW + i] : 0.f;
+            for (int c = 0; c < WL::GROW; ++c) {
+                const int h = c / WL::HWP, i = c % WL::HWP;
+                row[c] = i < WL::HW ? term[h * WL::HW + i] : 0.f;
+            }
         }
     }
-    int n_slot = 0;
-    // lane (j, h) contracts slot j's weights with terms [h HW, (h + 1) HW) of the
-    // group's gradients and adds the sums to splat j's accumulators
-    auto flush = [&]() {
-        if constexpr (!MAP) return;
+
+    // Map mode, after a stage of cnt splats: lane (j, part) sums slot j's weighted terms
+    // [part HW, (part + 1) HW) over the block's pixels and the dpow moments over its RPL rows,
+    // then the slot's sums go to the splat's accumulators.
+    auto contract = [&](const int cnt) {
         __syncwarp();
-        const int j = lane & (LY::SLOTS - 1), h = lane >> 4;
-        const float4 *wr = reinterpret_cast<const float4 *>(s_w + j * LY::WROW);
-        const float4 *gr = reinterpret_cast<const float4 *>(s_g + h * LY::HWP);
-        float acc[LY::HW];
-        float accp[LY::HWP];
+        const int j = lane % STAGE, part = lane / STAGE;
+        const float4 *wr = reinterpret_cast<const float4 *>(s_w + j * WL::WROW);
+        const float4 *gr = reinterpret_cast<const float4 *>(s_g + part * WL::HWP);
+        float acc[WL::HWP];
 #pragma unroll
-        for (int c = 0; c < LY::HWP; ++c) accp[c] = 0.f;
+        for (int c = 0; c < WL::HWP; ++c) acc[c] = 0.f;
 #pragma unroll 2
-        for (int q = 0; q < LY::PXW / 4; ++q) {
+        for (int q = 0; q < WL::PXW / 4; ++q) {
             const float4 w4 = wr[q];
             const float wq[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                const float4 *g4 = gr + (4 * q + i) * (LY::GROW / 4);
+                const float4 *g4 = gr + (4 * q + i) * (WL::GROW / 4);
 #pragma unroll
-                for (int c = 0; c < LY::HWP / 4; ++c) {
+                for (int c = 0; c < WL::HWP / 4; ++c) {
                     const float4 gv = g4[c];
-                    accp[4 * c] = fmaf(wq[i], gv.x, accp[4 * c]);
-                    if (4 * c + 1 < LY::HW) accp[4 * c + 1] = fmaf(wq[i], gv.y, accp[4 * c + 1]);
-                    if (4 * c + 2 < LY::HW) accp[4 * c + 2] = fmaf(wq[i], gv.z, accp[4 * c + 2]);
-                    if (4 * c + 3 < LY::HW) accp[4 * c + 3] = fmaf(wq[i], gv.w, accp[4 * c + 3]);
+                    acc[4 * c] = fmaf(wq[i], gv.x, acc[4 * c]);
+                    if (4 * c + 1 < WL::HW) acc[4 * c + 1] = fmaf(wq[i], gv.y, acc[4 * c + 1]);
+                    if (4 * c + 2 < WL::HW) acc[4 * c + 2] = fmaf(wq[i], gv.z, acc[4 * c + 2]);
+                    if (4 * c + 3 < WL::HW) acc[4 * c + 3] = fmaf(wq[i], gv.w, acc[4 * c + 3]);
                 }
             }
         }
+        // moments of dpow over rows [part RPL, (part + 1) RPL) of the block
+        const float4 *pr = reinterpret_cast<const float4 *>(s_p + j * WL::WROW);
+        float m1 = 0.f, mx = 0.f, my = 0.f, mxx = 0.f, mxy = 0.f, myy = 0.f;
 #pragma unroll
-        for (int c = 0; c < LY::HW; ++c) acc[c] = accp[c];
-        if (j < n_slot) {
-            const int64_t item = s_slot_item[j];
-            const int64_t g = item - voff;
-            if (h == 0)
-                add_deferred<D, LY::HW, 0>(acc, item, g, A.acc_uvod, A.acc_rgb, A.d_feat);
-            else
-                add_deferred<D, LY::HW, LY::HW>(acc, item, g, A.acc_uvod, A.acc_rgb, A.d_feat);
+        for (int r = 0; r < WL::RPL; ++r) {
+            const int ly = part * WL::RPL + r;
+            const float lyc = (float)ly + 0.5f - 0.5f * WL::ROWS;
+            const float4 d0 = pr[2 * ly], d1 = pr[2 * ly + 1];
+            const float d[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
+            float r0 = 0.f, rx = 0.f, rxx = 0.f;
+#pragma unroll
+            for (int lx = 0; lx < 8; ++lx) {
+                const float lxc = (float)lx - 3.5f;
+                r0 += d[lx];
+                rx = fmaf(d[lx], lxc, rx);
+                rxx = fmaf(d[lx], lxc * lxc, rxx);
+            }
+            m1 += r0;
+            mx += rx;
+            mxx += rxx;
+            my = fmaf(lyc, r0, my);
+            mxy = fmaf(lyc, rx, mxy);
+            myy = fmaf(lyc * lyc, r0, myy);
+        }
+#pragma unroll
+        for (int s = STAGE; s < 32; s <<= 1) {
+            m1 += __shfl_xor_sync(0xffffffffu, m1, s);
+            mx += __shfl_xor_sync(0xffffffffu, mx, s);
+            my += __shfl_xor_sync(0xffffffffu, my, s);
+            mxx += __shfl_xor_sync(0xffffffffu, mxx, s);
+            mxy += __shfl_xor_sync(0xffffffffu, mxy, s);
+            myy += __shfl_xor_sync(0xffffffffu, myy, s);
+        }
+        if (j < cnt) {
+#pragma unroll
+            for (int c = 0; c < WL::HW; ++c) s_t[j * WL::NWT + part * WL::HW + c] = acc[c];
         }
         __syncwarp();
-        n_slot = 0;
+        if (j < cnt) {
+            const int64_t item = s_item[j];
+            const int64_t g = item - voff;
+            const float *tj = s_t + j * WL::NWT;
+            if (part == 0) {
+                // centre and opacity from the moments expanded about the splat centre; depth
+                const SplatGeo sg = s_geo[j];
+                const float cx = __fadd_rn(__fsub_rn(sg.u, bcx), sg.ulo), cy = __fadd_rn(__fsub_rn(sg.v, bcy), sg.vlo);
+                const float Mx = fmaf(-cx, m1, mx), My = fmaf(-cy, m1, my);
+                const float du = (-1.f / kLog2e) * fmaf(2.f * sg.qa, Mx, sg.qb * My);
+                const float dv = (-1.f / kLog2e) * fmaf(2.f * sg.qc, My, sg.qb * Mx);
+                const float4 val = make_float4(du, dv, m1 / sg.o, tj[0]);
+                if (val.x != 0.f || val.y != 0.f || val.z != 0.f || val.w != 0.f) atomicAdd(A.acc_uvod + item, val);
+            } else if (part == 1) {
+                const SplatGeo sg = s_geo[j];
+                const float cx = __fadd_rn(__fsub_rn(sg.u, bcx), sg.ulo), cy = __fadd_rn(__fsub_rn(sg.v, bcy), sg.vlo);
+                // sum dpow dx^2 = Sxx - 2 cx Sx + cx^2 S1, and likewise
+                const float Mxx = fmaf(-cx, fmaf(-cx, m1, 2.f * mx), mxx);
+                const float Mxy = fmaf(cx * cy, m1, fmaf(-cx, my, fmaf(-cy, mx, mxy)));
+                const float Myy = fmaf(-cy, fmaf(-cy, m1, 2.f * my), myy);
+                const float4 val = make_float4(-0.5f * Mxx, -Mxy, -0.5f * Myy, 0.f);
+                if (val.x != 0.f || val.y != 0.f || val.z != 0.f) atomicAdd(A.acc_conic + item, val);
+            }
+            if (part == (WL::LPS > 2 ? 2 : 0)) {
+                const float4 val = make_float4(tj[1], tj[2], tj[3], 0.f);
+                if (val.x != 0.f || val.y != 0.f || val.z != 0.f) atomicAdd(A.acc_rgb + g, val);
+            }
+            // features [part D / LPS, (part + 1) D / LPS): the summed feature terms, or W^T times the
+            // summed logit terms
+            constexpr int DP = D / WL::LPS;
+            float *fo = A.d_feat + g * D + part * DP;
+#pragma unroll
+            for (int c4 = 0; c4 < DP / 4; ++c4) {
+                float o4[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int c = part * DP + 4 * c4 + i;
+                    if constexpr (KF > 0) {
+                        float s = 0.f;
+#pragma unroll
+                        for (int k = 0; k < KF; ++k) s = fmaf(s_basis[k * D + c], tj[4 + k], s);
+                        o4[i] = s;
+                    } else {
+                        o4[i] = tj[4 + c];
+                    }
+                }
+                const float4 val = make_float4(o4[0], o4[1], o4[2], o4[3]);
+                if (val.x != 0.f || val.y != 0.f || val.z != 0.f || val.w != 0.f)
+                    atomicAdd(reinterpret_cast<float4 *>(fo) + c4, val);
+            }
+        }
+        __syncwarp();
     };
 
     // Every listed splat was blended by a pixel of the group, so no box culling is needed.
@@ -199,38 +310,42 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP>())
             e[p] = eval_pair(s, pxc[p], pyc[p], prm.alpha_min, prm.alpha_max);
             contrib[p] = pos < last[p] && !e[p].skip;
         }
-        float val[8], wv[NP];
+        float val[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) val[i] = 0.f;
-#pragma unroll
-        for (int p = 0; p < NP; ++p) wv[p] = 0.f;
+        float x[NCH];
         {
             const float4 c = s_rgbd[k];
-            float x[NCH];
             x[0] = c.x; x[1] = c.y; x[2] = c.z; x[3] = c.w; x[4] = 1.f;
+            const float4 *sf = reinterpret_cast<const float4 *>(s_feat + k * F);
 #pragma unroll
-            for (int q = 0; q < D4; ++q) {
-                const float4 f = s_feat[k * D4 + q];
+            for (int q = 0; q < F4; ++q) {
+                const float4 f = sf[q];
                 x[5 + 4 * q] = f.x; x[6 + 4 * q] = f.y; x[7 + 4 * q] = f.z; x[8 + 4 * q] = f.w;
             }
-            // Branch-free over the lanes: a pixel that did not blend the splat runs the same
-            // instructions with alpha 0 and keeps its state, and every sum it adds to is 0.
+        }
+        // Branch-free over the lanes: a pixel that did not blend the splat runs the same
+        // instructions with alpha 0 and keeps its state, and every value it records is 0.
 #pragma unroll
-            for (int p = 0; p < NP; ++p) {
-                const float a = contrib[p] ? e[p].alpha : 0.f;
-                const float Tb = __fdividef(T[p], 1.f - a);
-                // g.x as three interleaved partial sums (shorter dependent chain)
-                float gx3[3] = {0.f, 0.f, 0.f};
+        for (int p = 0; p < NP; ++p) {
+            const float a = contrib[p] ? e[p].alpha : 0.f;
+            const float Tb = __fdividef(T[p], 1.f - a);
+            // g.x as three interleaved partial sums (shorter dependent chain)
+            float gx3[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-                for (int ch = 0; ch < NCH; ++ch) gx3[ch % 3] = fmaf(gch[p][ch], x[ch], gx3[ch % 3]);
-                const float gx = gx3[0] + gx3[1] + gx3[2];
-                const float da = Tb * (gx - gS[p]);
-                gS[p] = fmaf(a, gx - gS[p], gS[p]);
-                T[p] = contrib[p] ? Tb : T[p];
-                // moments of dpow over the pixels where alpha is not clamped; the splat's
-                // constants scale them once, after the warp reduction (geo_grads)
-                const bool free_alpha = contrib[p] && e[p].oG < prm.alpha_max;
-                const float dpow = free_alpha ? e[p].oG * da : 0.f;
+            for (int ch = 0; ch < NCH; ++ch) gx3[ch % 3] = fmaf(gch[p][ch], x[ch], gx3[ch % 3]);
+            const float gx = gx3[0] + gx3[1] + gx3[2];
+            const float da = Tb * (gx - gS[p]);
+            gS[p] = fmaf(a, gx - gS[p], gS[p]);
+            T[p] = contrib[p] ? Tb : T[p];
+            const bool free_alpha = contrib[p] && e[p].oG < prm.alpha_max;
+            const float dpow = free_alpha ? e[p].oG * da : 0.f;
+            if constexpr (MAP) {
+                s_w[k * WL::WROW + p * 32 + lane] = a * Tb;
+                s_p[k * WL::WROW + p * 32 + lane] = dpow;
+            } else {
+                // moments of dpow over the pixels; the splat's constants scale them once, after
+                // the warp reduction (geo_grads); the depth term as the sixth value
                 const float dx = e[p].dx, dy = e[p].dy;
                 const float ax = dx * dpow, ay = dy * dpow;
                 val[0] += ax;
@@ -238,53 +353,64 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP>())
                 val[2] = fmaf(ax, dx, val[2]);
                 val[3] = fmaf(ax, dy, val[3]);
                 val[4] = fmaf(ay, dy, val[4]);
-                if (MAP) val[5] += e[p].G * (free_alpha ? da : 0.f);
-                if (MAP) wv[p] = a * Tb;
-                else val[5] = fmaf(a * Tb, gch[p][3], val[5]);  // pose mode: the depth term
+                val[5] = fmaf(a * Tb, gch[p][3], val[5]);
             }
         }
-        const uint32_t item = s_item[k];
-        if constexpr (MAP) {
-            float *wr = s_w + n_slot * LY::WROW;
-#pragma unroll
-            for (int p = 0; p < NP; ++p) wr[p * 32 + lane] = wv[p];
-            if (lane == 0) s_slot_item[n_slot] = item;
-            ++n_slot;
-        }
-        // lane i ends with the warp's gradient value (i mod 8): centre (0, 1), conic (2-4), and
-        // opacity (map mode) or depth (pose mode) (5); lanes 0-5 add them in one warp-wide
-        // reduction instruction (two 16-byte targets: acc_uvod (u, v, opacity, depth) and
-        // acc_conic (A, B, C))
-        const float r = geo_grads(warp_transpose_reduce<8>(val, lane), lane & 7, s);
-        if (lane < 6 && r != 0.f) {
-            float *dst = lane == 5 ? reinterpret_cast<float *>(A.acc_uvod + item) + (MAP ? 2 : 3)
-                         : lane < 2 ? reinterpret_cast<float *>(A.acc_uvod + item) + lane
-                                    : reinterpret_cast<float *>(A.acc_conic + item) + (lane - 2);
-            atomicAdd(dst, r);
-        }
-        if constexpr (MAP) {
-            if (n_slot == LY::SLOTS) flush();
+        if constexpr (!MAP) {
+            // lane i ends with the warp's value (i mod 8): centre (0, 1), conic (2-4), depth (5); lanes
+            // 0-5 add them in one warp-wide reduction instruction
+            const uint32_t item = s_item[k];
+            const float r = geo_grads(warp_transpose_reduce<8>(val, lane), lane & 7, s);
+            if (lane < 6 && r != 0.f) {
+                float *dst = lane == 5 ? reinterpret_cast<float *>(A.acc_uvod + item) + 3
+                             : lane < 2 ? reinterpret_cast<float *>(A.acc_uvod + item) + lane
+                                        : reinterpret_cast<float *>(A.acc_conic + item) + (lane - 2);
+                atomicAdd(dst, r);
+            }
         }
     };
 
-    // stages list entries [off, off + cnt) (instance indices, back to front; cnt <= STAGE)
-    // and walks them
+    // stages list entries [off, off + cnt) (instance indices, back to front; cnt <= STAGE),
+    // walks them and, in map mode, contracts the stage's slots
     auto stage_and_process = [&](const int off, const int cnt) {
-        if (lane < cnt) {
-            const uint32_t ii = s_list[off + lane];
+        const int si = lane % STAGE, part = lane / STAGE;
+        if (si < cnt) {
+            const uint32_t ii = s_list[off + si];
             const uint32_t item = checked_item(A.vals[ii], voff, vt.n, A.status);
             const int64_t g = (int64_t)item - voff;
-            const float4 a = A.uvdo[item];
-            const float4 c = A.conic[item];
-            s_geo[lane] = make_geo(a, A.uv_lo[item], c);
-            s_rgbd[lane] = load_rgbd(rgb, g, a.z);
+            if (part == 0) {
+                const float4 a = A.uvdo[item];
+                const float4 c = A.conic[item];
+                s_geo[si] = make_geo(a, A.uv_lo[item], c);
+                s_rgbd[si] = load_rgbd(rgb, g, a.z);
+                s_item[si] = item;
+                s_pos[si] = (int)(ii - start);
+            }
+            if constexpr (KF > 0) {
+                // z = W f for this part's K / PARTS logits
+                float f[D];
 #pragma unroll
-            for (int q = 0; q < D4; ++q) s_feat[lane * D4 + q] = load_feat4(feat, g * D + 4 * q);
-            s_item[lane] = item;
-            s_pos[lane] = (int)(ii - start);
+                for (int q = 0; q < D / 4; ++q) {
+                    const float4 f4 = load_feat4(feat, g * D + 4 * q);
+                    f[4 * q] = f4.x; f[4 * q + 1] = f4.y; f[4 * q + 2] = f4.z; f[4 * q + 3] = f4.w;
+                }
+#pragma unroll
+                for (int kk = 0; kk < KF / PARTS; ++kk) {
+                    const int k = part * (KF / PARTS) + kk;
+                    float z = 0.f;
+#pragma unroll
+                    for (int d = 0; d < D; ++d) z = fmaf(s_basis[k * D + d], f[d], z);
+                    s_feat[si * F + k] = z;
+                }
+            } else if (part == 0) {
+                float4 *sf = reinterpret_cast<float4 *>(s_feat + si * F);
+#pragma unroll
+                for (int q = 0; q < F4; ++q) sf[q] = load_feat4(feat, g * D + 4 * q);
+            }
         }
         __syncwarp();
         for (int k = 0; k < cnt; ++k) process(k);
+        if constexpr (MAP) contract(cnt);
         __syncwarp();
     };
 
@@ -314,34 +440,29 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP>())
         }
     }
     for (int off = 0; off < n; off += STAGE) stage_and_process(off, min(STAGE, n - off));
-    if constexpr (MAP) {
-        if (n_slot > 0) flush();
-    }
 }
 
-template <int D, int NP, bool MAP, typename RT, typename FT>
+template <int D, int NP, bool MAP, int KF, typename RT, typename FT>
 gs_status launch_bwd_warp(const ViewTable &vt, const Params &prm, const BwdArgs &A, cudaStream_t st) {
     const int n_tiles = vt.tile_off[vt.n_views];
-    raster_bwd_warp_kernel<D, NP, MAP, RT, FT><<<n_tiles * Shape<NP>::WARPS, 32, 0, st>>>(vt, prm, A);
+    raster_bwd_warp_kernel<D, NP, MAP, KF, RT, FT><<<n_tiles * Shape<NP>::WARPS, 32, 0, st>>>(vt, prm, A);
     return last_launch();
 }
 
-// The warp-block form: D 16 or 32, 1 or 2 pixels per thread, blend mask present.
-template <bool MAP>
-gs_status dispatch_bwd_warp(int D, int np, bool half, const ViewTable &vt, const Params &prm, const BwdArgs &A,
-                            cudaStream_t st) {
+// The warp-block form: D 16 or 32, 1 or 2 pixels per thread, blend mask present; factored
+// feature gradients (A.feat_basis) with at most kFactorK logits.
+template <bool MAP, typename RT, typename FT>
+gs_status dispatch_bwd_warp_typed(int D, int np, const ViewTable &vt, const Params &prm, const BwdArgs &A,
+                                  cudaStream_t st) {
     if (!A.bmask) return GS_ERR_UNSUPPORTED;
-    if (half) {
-        if (D == 16 && np == 1) return launch_bwd_warp<16, 1, MAP, __half, __nv_bfloat16>(vt, prm, A, st);
-        if (D == 16 && np == 2) return launch_bwd_warp<16, 2, MAP, __half, __nv_bfloat16>(vt, prm, A, st);
-        if (D == 32 && np == 1) return launch_bwd_warp<32, 1, MAP, __half, __nv_bfloat16>(vt, prm, A, st);
-        if (D == 32 && np == 2) return launch_bwd_warp<32, 2, MAP, __half, __nv_bfloat16>(vt, prm, A, st);
-        return GS_ERR_UNSUPPORTED;
-    }
-    if (D == 16 && np == 1) return launch_bwd_warp<16, 1, MAP, float, float>(vt, prm, A, st);
-    if (D == 16 && np == 2) return launch_bwd_warp<16, 2, MAP, float, float>(vt, prm, A, st);
-    if (D == 32 && np == 1) return launch_bwd_warp<32, 1, MAP, float, float>(vt, prm, A, st);
-    if (D == 32 && np == 2) return launch_bwd_warp<32, 2, MAP, float, float>(vt, prm, A, st);
+    const bool fact = A.feat_basis != nullptr;
+    if (fact && (A.feat_rank < 1 || A.feat_rank > kFactorK || !A.feat_coef)) return GS_ERR_UNSUPPORTED;
+#define GS_BWD_WARP(DD, NN)                                                                              \
+    if (D == DD && np == NN)                                                                             \
+        return fact ? launch_bwd_warp<DD, NN, MAP, kFactorK, RT, FT>(vt, prm, A, st)                     \
+                    : launch_bwd_warp<DD, NN, MAP, 0, RT, FT>(vt, prm, A, st);
+    GS_BWD_WARP(16, 1) GS_BWD_WARP(16, 2) GS_BWD_WARP(32, 1) GS_BWD_WARP(32, 2)
+#undef GS_BWD_WARP
     return GS_ERR_UNSUPPORTED;
 }
 

@@ -86,6 +86,9 @@ def _stream(stream=None):
 
 _DTYPE = {torch.float32: L.GS_F32, torch.float16: L.GS_F16, torch.bfloat16: L.GS_BF16}
 
+# largest decoder class count of the factored feature gradient (gs_image_grads.feat_rank)
+FACTOR_K = 8
+
 
 @dataclasses.dataclass
 class Field:
@@ -182,6 +185,11 @@ class Renderer:
         K = max(int(n_classes), 1)
         self.d_dec_W = torch.zeros(K, max(D, 1), dtype=f32, device=dev)
         self.d_dec_b = torch.zeros(K, dtype=f32, device=dev)
+        # factored feature gradient (gs_image_grads.feat_basis): the loss writes dL/dz of the decoder's
+        # K <= 8 logits and the per-group backward contracts those, for feature widths 16 and 32
+        self.factored = D in (16, 32) and 1 <= int(n_classes) <= FACTOR_K
+        self.g_coef = torch.zeros(FACTOR_K, P, dtype=f32, device=dev) if self.factored else None
+        self._basis = None             # decoder weights of the last factored loss
         self.prm_c = params.c()
 
     OUTPUTS = ("d_means", "d_quats", "d_log_scales", "d_logits", "d_rgb", "d_feat", "d_dec_W", "d_dec_b",
@@ -255,9 +263,23 @@ class Renderer:
     def splat_grads_c(self):
         return L.gs_splat_grads(_p(self.sg_uvod), _p(self.sg_conic), _p(self.sg_rgb))
 
-    def image_grads_c(self):
+    def image_grads_c(self, factored=False):
+        """The image gradients for gs_render_bwd; factored: the decoder-logit form the last
+        factored loss() wrote (g_feat = W^T g_coef)."""
+        if factored:
+            W = self._basis
+            if W is None:
+                raise ValueError("no factored loss has been computed with this renderer")
+            return L.gs_image_grads(_p(self.g_rgb), _p(self.g_depth), _p(self.g_sil), None, _p(self.g_coef), _p(W),
+                                    int(W.shape[0]))
         return L.gs_image_grads(_p(self.g_rgb), _p(self.g_depth), _p(self.g_sil),
-                                _p(self.g_feat) if self.feat_dim else None)
+                                _p(self.g_feat) if self.feat_dim else None, None, None, 0)
+
+    def image_grads_out_c(self, factored=False):
+        """The image-gradient outputs of gs_loss_fwd_bwd (factored: the logit gradient)."""
+        return L.gs_image_grads_out(_p(self.g_rgb), _p(self.g_depth), _p(self.g_sil),
+                                    _p(self.g_feat) if self.feat_dim and not factored else None,
+                                    _p(self.g_coef) if factored else None)
 
     def gaussian_grads_c(self):
         return L.gs_gaussian_grads(_p(self.d_means), _p(self.d_quats), _p(self.d_log_scales), _p(self.d_logits),
@@ -280,11 +302,19 @@ class Renderer:
                                                  self.cams_c, self.n_views, ctypes.byref(self.prm_c),
                                                  ctypes.byref(ic), _stream(stream)))
 
-    def loss(self, targets, decoder_W: torch.Tensor, decoder_b: torch.Tensor, w: LossWeights, stream=None):
+    def loss(self, targets, decoder_W: torch.Tensor, decoder_b: torch.Tensor, w: LossWeights, stream=None,
+             factored=False):
+        """Decoder and losses (gs_loss_fwd_bwd).  factored: write the gradient of the decoder's
+        logits (g_coef) instead of the features' (needs self.factored), for a following
+        render_bwd(factored=True)."""
         K = int(decoder_W.shape[0]) if decoder_W is not None else 0
+        if factored:
+            if not self.factored or not 1 <= K <= FACTOR_K:
+                raise ValueError("the factored feature gradient needs feature width 16 or 32 and 1-8 classes")
+            self._basis = decoder_W
         lp = L.gs_loss_params(w.color, w.depth, w.sem, w.mask_mode, w.tau_obs, K, w.ssim)
         tc = L.gs_targets(_p(targets["rgb"]), _p(targets["depth"]), _p(targets["label"]))
-        ic, gc = self.images_c(), self.image_grads_c()
+        ic, gc = self.images_c(), self.image_grads_out_c(factored)
         L.check("gs_loss_fwd_bwd", L.gs_loss_fwd_bwd(self.cams_c, self.n_views, self.feat_dim, ctypes.byref(ic),
                                                      ctypes.byref(tc), _p(decoder_W), _p(decoder_b),
                                                      ctypes.byref(lp), _p(self.ws), self.ws.numel(),
@@ -292,8 +322,8 @@ class Renderer:
                                                      _p(self.loss_out), _p(self.mask), _p(self.median),
                                                      _stream(stream)))
 
-    def render_bwd(self, field: Field, grad_mode: int = L.GS_GRAD_MAP, stream=None):
-        pc, bc, ic, gc, sg = (self.projected_c(), self.binning_c(), self.images_c(), self.image_grads_c(),
+    def render_bwd(self, field: Field, grad_mode: int = L.GS_GRAD_MAP, stream=None, factored=False):
+        pc, bc, ic, gc, sg = (self.projected_c(), self.binning_c(), self.images_c(), self.image_grads_c(factored),
                               self.splat_grads_c())
         L.check("gs_render_bwd", L.gs_render_bwd(ctypes.byref(field.c()), ctypes.byref(pc), ctypes.byref(bc),
                                                  self.cams_c, self.n_views, ctypes.byref(self.prm_c), grad_mode,
@@ -307,9 +337,9 @@ class Renderer:
                                                    ctypes.byref(sg), ctypes.byref(oc), _p(self.pose_part),
                                                    _stream(stream)))
 
-    def backward(self, field: Field, grad_mode: int = L.GS_GRAD_MAP, pose_dev=None, stream=None):
+    def backward(self, field: Field, grad_mode: int = L.GS_GRAD_MAP, pose_dev=None, stream=None, factored=False):
         """Blend backward then projection backward (and the twist reduction in pose mode)."""
-        self.render_bwd(field, grad_mode, stream)
+        self.render_bwd(field, grad_mode, stream, factored)
         self.project_bwd(field, grad_mode, pose_dev, stream)
         if grad_mode & L.GS_GRAD_POSE:
             self.pose_grad(stream)
@@ -348,16 +378,25 @@ class Renderer:
         has written) runs on a side stream beside the twist reduction and rejoins the stream
         before the call returns (also inside a CUDA-graph capture)."""
         self.forward(field, pose_dev, stream)
-        self.loss(targets, decoder_W, decoder_b, w, stream)
+        fac = self.use_factored(decoder_W)
+        self.loss(targets, decoder_W, decoder_b, w, stream, factored=fac)
         dsr = (grad_mode & L.GS_GRAD_MAP) and (w.big or w.small)
         if not (dsr and grad_mode & L.GS_GRAD_POSE):
-            self.backward(field, grad_mode, pose_dev, stream)
+            self.backward(field, grad_mode, pose_dev, stream, factored=fac)
             if dsr:
                 self.dsr(field, w.big, w.small, stream)
             return
-        self.render_bwd(field, grad_mode, stream)
+        self.render_bwd(field, grad_mode, stream, factored=fac)
         self.project_bwd(field, grad_mode, pose_dev, stream)
         self.side_by_side(lambda s: self.dsr(field, w.big, w.small, s), lambda: self.pose_grad(stream), stream)
+
+    def use_factored(self, decoder_W) -> bool:
+        """Whether a step with this decoder takes the factored feature gradient: the renderer
+        supports it, the decoder has 1-8 classes and the per-group backward will run (the
+        blend mask is on and the backward block shape is not forced to whole tiles)."""
+        K = int(decoder_W.shape[0]) if decoder_W is not None else 0
+        return (self.factored and 1 <= K <= FACTOR_K and self.use_blend_mask
+                and self.params.bwd_blocks != L.GS_BWD_BLOCKS_TILE and self.params.bwd_px_per_thread <= 2)
 
     def side_by_side(self, side_work, main_work, stream=None):
         """Runs side_work(side_stream) on the renderer's side stream after everything issued

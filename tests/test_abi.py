@@ -74,7 +74,7 @@ def test_argument_errors_before_any_launch(lib):
     fake = ctypes.c_void_p(1 << 20)
     img = L.gs_images(fake, fake, fake, fake, fake, fake, None, None)
     tgt = L.gs_targets(fake, fake, fake)
-    grads = L.gs_image_grads(fake, fake, fake, fake)
+    grads = L.gs_image_grads_out(fake, fake, fake, fake, None)
     for weights in ((0.5, 1.0, 0.01, 1, 0.99, 8, 0.2), (0.5, 1.0, 0.01, 0, 0.99, 8, 1.5),
                     (0.5, 1.0, 0.01, 0, 0.99, 8, -0.1)):
         lp = L.gs_loss_params(*weights)

@@ -214,6 +214,40 @@ def test_warp_block_backward_agrees_with_the_tile_kernel(np_):
         r.backward(field, L.GS_GRAD_MAP)
 
 
+@pytest.mark.parametrize("D,np_", [(16, 1), (16, 2), (32, 1), (32, 2)])
+def test_factored_feature_gradient_matches_the_feature_form(D, np_):
+    """The loss's decoder-logit gradient e satisfies W^T e = its feature gradient, and the
+    per-group backward given (e, W) returns the gradients it returns given W^T e, in map mode
+    (every group) and pose mode (the twist), over a frame and a ragged second view."""
+    gs, cam, room = C.room_case(20000, D, 200, 120, 100.0)
+    cams = [cam, synth.camera(90, 61, 45.0, T_cw=synth.keyframe_loop(8, room=room)[3])]
+    prm = raster.RasterParams(bwd_blocks=L.GS_BWD_BLOCKS_GROUP, bwd_px_per_thread=np_)
+    field, r = C.gpu_forward(gs, cams, prm, n_classes=8)
+    assert r.factored
+    dec = synth.decoder(8, D, seed=3)
+    Wd, bd = torch.as_tensor(dec.W).cuda(), torch.as_tensor(dec.b).cuda()
+    rast = [synth.raycast_room(room, c) for c in cams]
+    tg = dict(rgb=torch.as_tensor(np.concatenate([t.rgb.reshape(3, -1) for t in rast], 1)).cuda(),
+              depth=torch.as_tensor(np.concatenate([t.depth.ravel() for t in rast])).cuda(),
+              label=torch.as_tensor(np.concatenate([t.label.ravel() for t in rast])).cuda())
+    r.loss(tg, Wd, bd, raster.MAPPING)
+    g_feat = r.g_feat[:D].clone()
+    r.loss(tg, Wd, bd, raster.MAPPING, factored=True)
+    C.assert_grad_close("W^T e", (Wd.t() @ r.g_coef).cpu().numpy(), g_feat.cpu().numpy(), 1e-6)
+    outs = []
+    for fac in (False, True):
+        r.backward(field, L.GS_GRAD_MAP | L.GS_GRAD_POSE, factored=fac)
+        outs.append([t.clone() for t in (r.d_means, r.d_quats, r.d_log_scales, r.d_logits, r.d_rgb, r.d_feat[:, :D],
+                                         r.d_twist)])
+    for name, a, b in zip(("means", "quats", "log_scales", "logits", "rgb", "feat", "twist"), *outs):
+        C.assert_grad_close(name, b.cpu().numpy(), a.cpu().numpy(), 1e-5)
+    twists = []
+    for fac in (False, True):
+        r.backward(field, L.GS_GRAD_POSE, factored=fac)
+        twists.append(r.d_twist.clone())
+    C.assert_grad_close("pose twist", twists[1].cpu().numpy(), twists[0].cpu().numpy(), 1e-5)
+
+
 def test_blend_mask_skips_only_non_contributing_splats():
     """The backward with the forward's blend mask equals the full scan."""
     gs, cam, _ = C.room_case(20000, 16, 330, 190, 165.0)

@@ -59,7 +59,7 @@ def _run_both(seed, sizes, weights):
     p = lambda t: ctypes.c_void_p(t.data_ptr())
     lp = L.gs_loss_params(weights.color, weights.depth, weights.sem, weights.mask_mode, weights.tau_obs, K)
     tc = L.gs_targets(p(tg["rgb"]), p(tg["depth"]), p(tg["label"]))
-    gc = L.gs_image_grads(p(out["g_rgb"]), p(out["g_depth"]), p(out["g_sil"]), p(out["g_feat"]))
+    gc = L.gs_image_grads_out(p(out["g_rgb"]), p(out["g_depth"]), p(out["g_sil"]), p(out["g_feat"]), None)
     status = L.gs_loss_fwd_bwd_noalloc(r.cams_c, len(cams), D, ctypes.byref(r.images_c()), ctypes.byref(tc),
                                        p(W), p(b), ctypes.byref(lp), ctypes.byref(gc), p(out["dW"]), p(out["db"]),
                                        p(out["loss"]), p(out["mask"]), p(out["median"]),
@@ -90,7 +90,7 @@ def test_noalloc_loss_rejects_more_views_than_its_scratch_holds():
     tg = dict(rgb=torch.zeros(3, r.P, device="cuda"), depth=torch.ones(r.P, device="cuda"),
               label=torch.zeros(r.P, dtype=torch.uint8, device="cuda"))
     tgt = L.gs_targets(p(tg["rgb"]), p(tg["depth"]), p(tg["label"]))
-    g = r.image_grads_c()
+    g = r.image_grads_out_c()
     status = L.gs_loss_fwd_bwd_noalloc(r.cams_c, 17, 0, ctypes.byref(r.images_c()), ctypes.byref(tgt), None, None,
                                        ctypes.byref(lp), ctypes.byref(g), None, None, p(r.loss_out), None, None,
                                        None)
@@ -110,7 +110,7 @@ def test_noalloc_loss_refuses_the_ssim_term_before_any_launch(ssim, mask_mode, w
     tg = dict(rgb=torch.zeros(3, r.P, device="cuda"), depth=torch.ones(r.P, device="cuda"),
               label=torch.zeros(r.P, dtype=torch.uint8, device="cuda"))
     tgt = L.gs_targets(p(tg["rgb"]), p(tg["depth"]), p(tg["label"]))
-    g = r.image_grads_c()
+    g = r.image_grads_out_c()
     r.loss_out.fill_(7.0)
     status = L.gs_loss_fwd_bwd_noalloc(r.cams_c, 1, 0, ctypes.byref(r.images_c()), ctypes.byref(tgt), None, None,
                                        ctypes.byref(lp), ctypes.byref(g), None, None, p(r.loss_out), None, None,
