@@ -390,6 +390,11 @@ def run_configs(args, dev, flush):
                                                                  feat_dtype=torch.bfloat16),
             cams, synth.decoder(WORKLOAD["k"], 32),
             workload="2M Gaussians, D=32 BF16 features, FP16 colours (f32 blending); 8 keyframes at 1200x680")
+    # the same step with FP32 storage: the precision form's plain counterpart
+    measure("precision_2M_d32_fp32", raster.Field.from_numpy(gs, dev), cams, synth.decoder(WORKLOAD["k"], 32),
+            workload="2M Gaussians, D=32 FP32 features and colours; 8 keyframes at 1200x680")
+    out["precision_2M_d32_bf16_f16"]["speedup_vs_fp32"] = (out["precision_2M_d32_fp32"]["ms_per_step"]
+                                                           / out["precision_2M_d32_bf16_f16"]["ms_per_step"])
     del gs
     gs = synth.room_field(1_000_000, 32, seed=synth.SEED_SCENE, room=room)
     measure("differentiation_1M_d32_640x480", raster.Field.from_numpy(gs, dev),

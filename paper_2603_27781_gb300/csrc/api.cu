@@ -101,6 +101,7 @@ WsLayout ws_layout(int64_t n, int n_views, int64_t capacity, const ViewTable *vt
     L.tvals_b = take(sizeof(uint32_t) * (size_t)capacity);
     L.hist = take(sizeof(uint32_t) * 8 * 256);
     L.lookback = take(sizeof(uint32_t) * 256 * ((size_t)4 * L.lb_tiles_depth + (size_t)3 * L.lb_tiles_inst));
+    L.tile_counts = take(sizeof(uint32_t) * (vt ? (size_t)vt->tile_off[vt->n_views] : 0));
     L.bin_end = off;
     off = 0;
     L.med_hist = take(sizeof(uint32_t) * 4 * 256 * (size_t)n_views);

@@ -220,8 +220,33 @@ __device__ __forceinline__ void tile_rect(float u, float v, int r, int TX, int T
     y1 = cl(fdiv(iv + r) + 1, TY);
 }
 
+// Programmatic dependent launch: a kernel launched with launch_pdl may start (be scheduled,
+// run its prologue) while the kernel before it on the stream finishes; pdl_wait() blocks until
+// that kernel has completed and its writes are visible, so every read of its results comes
+// after it.  pdl_trigger() lets the next kernel be launched once every block of this one has
+// called it (or exited).  Both are no-ops for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Host helpers.
 inline gs_status cuda_status(cudaError_t e) { return e == cudaSuccess ? GS_OK : GS_ERR_CUDA; }
+
+// Launches kernel<<<grid, block, smem, st>>>(args...) with programmatic stream serialization
+// (the kernel must call pdl_wait() before it reads what earlier work on the stream wrote).
+template <typename... KArgs, typename... Args>
+gs_status launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cuda_status(cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...));
+}
 inline gs_status last_launch() {
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? GS_OK : GS_ERR_CUDA;
@@ -238,6 +263,7 @@ struct WsLayout {
     size_t tkeys_a, tkeys_b, tvals_b;           // u32 [capacity]
     size_t hist;          // u32 [8 passes][256]
     size_t lookback;      // u32 [8 passes][max tiles][256]
+    size_t tile_counts;   // u32 [total image tiles]: instances per image tile
     size_t bin_end;
     // loss / dsr
     size_t med_hist;      // u32 [4][V][256]

@@ -62,8 +62,33 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t *t
     return r;
 }
 
+// ------------------------------------------------------------ state of a call
+// Zeroes what a binning accumulates into: the ranges, the counters, the instance count and
+// status word, the tile counts, the digit histograms and the look-back flags (the last and
+// largest in 16-byte stores over the whole grid).
+__global__ void __launch_bounds__(256) bin_init_kernel(uint32_t *ranges, int64_t n_ranges, uint32_t *counters,
+                                                       int64_t *n_inst, int32_t *status, uint32_t *tile_counts,
+                                                       int64_t n_tiles, uint32_t *hist, uint4 *lookback,
+                                                       int64_t n_lookback4) {
+    pdl_wait();
+    pdl_trigger();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t i = i0; i < n_lookback4; i += stride) lookback[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (int64_t i = i0; i < n_ranges; i += stride) ranges[i] = 0u;
+    for (int64_t i = i0; i < n_tiles; i += stride) tile_counts[i] = 0u;
+    for (int64_t i = i0; i < 8 * 256; i += stride) hist[i] = 0u;
+    for (int64_t i = i0; i < 64; i += stride) counters[i] = 0u;
+    if (i0 == 0) {
+        *n_inst = 0;
+        *status = 0;
+    }
+}
+
 // ------------------------------------------------ compaction of visible items
 __global__ void __launch_bounds__(256) vis_reduce_kernel(const int32_t *touched, int64_t count, uint32_t *block_sums) {
+    pdl_wait();     // the previous kernel's results
+    pdl_trigger();  // the next kernel may be scheduled now
     __shared__ uint32_t s_warp[9];
     int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanIPT;
     uint32_t c = 0;
@@ -81,6 +106,8 @@ __global__ void __launch_bounds__(1024) blocksum_scan_kernel(uint32_t *block_sum
                                                              int64_t nb_fixed, int items_per_block,
                                                              uint32_t *counters, int slot, int cap_slot,
                                                              int64_t capacity, int64_t *n_inst, int32_t *status) {
+    pdl_wait();     // the previous kernel's results
+    pdl_trigger();  // the next kernel may be scheduled now
     __shared__ uint32_t s_part[1024];
     const bool failed = binning_failed(status);
     int64_t nb = nb_from ? ((int64_t)*nb_from + items_per_block - 1) / items_per_block : nb_fixed;
@@ -147,6 +174,8 @@ __device__ __forceinline__ void hist_flush(uint32_t (*sh)[256], int n_passes, ui
 __global__ void __launch_bounds__(256) vis_compact_kernel(const int32_t *touched, const float4 *uvdo, int64_t count,
                                                           const uint32_t *block_sums, uint32_t *keys, uint32_t *vals,
                                                           uint32_t *hist) {
+    pdl_wait();     // the previous kernel's results
+    pdl_trigger();  // the next kernel may be scheduled now
     __shared__ uint32_t s_warp[9];
     __shared__ uint32_t sh[4][256];
     for (int i = threadIdx.x; i < 4 * 256; i += 256) (&sh[0][0])[i] = 0u;
@@ -180,6 +209,8 @@ __global__ void __launch_bounds__(kEmitBlock) emit_reduce_kernel(const uint32_t 
                                                                  const int32_t *touched, const uint32_t *counters,
                                                                  uint32_t *block_sums, int64_t vn,
                                                                  const int32_t *status) {
+    pdl_wait();     // the previous kernel's results
+    pdl_trigger();  // the next kernel may be scheduled now
     __shared__ uint32_t s_warp[9];
     const bool failed = binning_failed(status);  // the depth sort gave up: its items are not valid
     const int64_t count = counters[CTR_NVIS];
@@ -192,11 +223,11 @@ __global__ void __launch_bounds__(kEmitBlock) emit_reduce_kernel(const uint32_t 
     if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
 }
 
-// One thread per sorted item computes its instance offset; each warp then
-// writes the instances of its 32 items cooperatively, 32 consecutive instances
-// per round (the owner of instance q is found by a 5-step binary search over
-// the lanes' offsets), so every store is coalesced and long items are spread
-// over the warp.
+// One thread per sorted item computes its instance offset; the block's instances are then
+// split evenly over its warps, 32 consecutive instances per warp round, each lane finding
+// the item that owns its instance by a binary search over the block's item offsets in
+// shared memory.  Every store is coalesced, and a few long items (large splats) no longer
+// keep one warp of the block busy while the others idle.
 // Also the digit histograms of the tile sort's n_passes passes over the written keys.
 __global__ void __launch_bounds__(kEmitBlock) emit_kernel(ViewTable vt, const uint32_t *sorted_items,
                                                           const int32_t *touched, const float4 *uvdo,
@@ -204,15 +235,20 @@ __global__ void __launch_bounds__(kEmitBlock) emit_kernel(ViewTable vt, const ui
                                                           const uint32_t *block_sums, int64_t capacity,
                                                           uint32_t *tile_keys, uint32_t *inst_vals, int n_passes,
                                                           uint32_t *hist, int64_t vn, const int32_t *status) {
+    pdl_wait();     // the previous kernel's results
+    pdl_trigger();  // the next kernel may be scheduled now
     __shared__ uint32_t s_warp[9];
     __shared__ uint32_t sh[4][256];
+    __shared__ uint32_t s_off[kEmitBlock];   // exclusive instance offset of each item in the block
+    __shared__ uint32_t s_item[kEmitBlock];
+    __shared__ uint4 s_rect[kEmitBlock];     // (x0, y0, width, tiles per row | first tile of the view << 16)
     // whole block (the word is only written by earlier kernels): after a failed depth sort or an
     // overflow nothing is emitted
     const bool failed = binning_failed(status);
     const int64_t count = counters[CTR_NVIS];
     if (failed || (int64_t)blockIdx.x * kEmitBlock >= count) return;  // whole block: no barrier is skipped
     for (int i = threadIdx.x; i < 4 * 256; i += kEmitBlock) (&sh[0][0])[i] = 0u;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t i = (int64_t)blockIdx.x * kEmitBlock + threadIdx.x;
     uint32_t item = 0, c = 0;
     int x0 = 0, y0 = 0, w = 1, tx = 1;
@@ -229,33 +265,36 @@ __global__ void __launch_bounds__(kEmitBlock) emit_kernel(ViewTable vt, const ui
         tb = (uint32_t)vt.tile_off[v];
     }
     uint32_t tot;
-    const uint32_t excl = block_sums[blockIdx.x] + block_exclusive_scan(c, &tot, s_warp);
-    const uint32_t wbase = __shfl_sync(0xffffffffu, excl, 0);
-    const uint32_t wtotal = __shfl_sync(0xffffffffu, excl + c, 31) - wbase;
-    const uint32_t rel = excl - wbase;
-    for (uint32_t q0 = 0; q0 < wtotal; q0 += 32) {
+    const uint32_t excl = block_exclusive_scan(c, &tot, s_warp);
+    s_off[threadIdx.x] = excl;
+    s_item[threadIdx.x] = item;
+    s_rect[threadIdx.x] = make_uint4((uint32_t)x0, (uint32_t)y0, (uint32_t)w, (uint32_t)tx);
+    if (threadIdx.x == 0) s_warp[8] = tot;
+    __shared__ uint32_t s_tb[kEmitBlock];
+    s_tb[threadIdx.x] = tb;
+    __syncthreads();
+    const uint32_t bbase = block_sums[blockIdx.x];
+    // warp wid takes instances [q_lo, q_hi) of the block, in whole rounds of 32
+    const uint32_t per = ((tot + 32u * (kEmitBlock / 32) - 1) / (32u * (kEmitBlock / 32))) * 32u;
+    const uint32_t q_lo = min(tot, (uint32_t)wid * per), q_hi = min(tot, q_lo + per);
+    for (uint32_t q0 = q_lo; q0 < q_hi; q0 += 32) {
         const uint32_t q = q0 + lane;
+        const bool valid = q < q_hi;
+        // the owner: the last item whose offset is <= q (items with no instances share offsets)
         int owner = 0;
 #pragma unroll
-        for (int step = 16; step >= 1; step >>= 1) {
-            const int cand = owner + step;
-            const uint32_t rc = __shfl_sync(0xffffffffu, rel, cand & 31);
-            if (cand < 32 && rc <= q) owner = cand;
-        }
-        const uint32_t o_rel = __shfl_sync(0xffffffffu, rel, owner);
-        const uint32_t o_item = __shfl_sync(0xffffffffu, item, owner);
-        const int o_x0 = __shfl_sync(0xffffffffu, x0, owner), o_y0 = __shfl_sync(0xffffffffu, y0, owner);
-        const int o_w = __shfl_sync(0xffffffffu, w, owner), o_tx = __shfl_sync(0xffffffffu, tx, owner);
-        const uint32_t o_tb = __shfl_sync(0xffffffffu, tb, owner);
-        const int64_t off = (int64_t)wbase + q;
-        const bool write = q < wtotal && off < capacity;
+        for (int step = kEmitBlock / 2; step >= 1; step >>= 1)
+            if (s_off[owner + step] <= q) owner += step;
+        const int64_t off = (int64_t)bbase + q;
+        const bool write = valid && off < capacity;
         uint32_t key = 0u;
         if (write) {
-            const int k = (int)(q - o_rel);
-            const int ky = k / o_w, kx = k - ky * o_w;
-            key = o_tb + (uint32_t)((o_y0 + ky) * o_tx + o_x0 + kx);
+            const uint4 rc = s_rect[owner];
+            const int k = (int)(q - s_off[owner]);
+            const int ky = k / (int)rc.z, kx = k - ky * (int)rc.z;
+            key = s_tb[owner] + (uint32_t)(((int)rc.y + ky) * (int)rc.w + (int)rc.x + kx);
             tile_keys[off] = key;
-            inst_vals[off] = o_item;
+            inst_vals[off] = s_item[owner];
         }
         hist_add(sh, n_passes, write, key);
     }
@@ -267,7 +306,10 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint32_t *
                                                                 uint32_t *keys_out, uint32_t *vals_out,
                                                                 const uint32_t *count_ptr, int shift,
                                                                 const uint32_t *pass_hist, uint32_t *tile_ctr,
-                                                                uint32_t *lookback, int32_t *status, int spin_limit) {
+                                                                uint32_t *lookback, int32_t *status, int spin_limit,
+                                                                uint32_t *tile_counts, uint32_t n_tiles) {
+    pdl_wait();     // the previous kernel's results
+    pdl_trigger();  // the next kernel may be scheduled now
     constexpr int W = kSortThreads / 32;
     __shared__ uint32_t s_keys[kSortTile];
     __shared__ uint32_t s_vals[kSortTile];
@@ -404,26 +446,29 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint32_t *
         uint32_t dst = s_glob[dd] + (uint32_t)i - s_excl[dd];
         keys_out[dst] = k;
         vals_out[dst] = s_vals[i];
+        // last pass of the tile sort: the block's keys are sorted by tile here, so each run of one
+        // tile adds its length to the tile's count (end + 1 from its last key, -start from its first)
+        if (tile_counts && k < n_tiles) {
+            if (i == 0 || s_keys[i - 1] != k) atomicAdd(&tile_counts[k], 0u - (uint32_t)i);
+            if (i == tile_n - 1 || s_keys[i + 1] != k) atomicAdd(&tile_counts[k], (uint32_t)i + 1u);
+        }
     }
 }
 
-// Per-tile [start, end) of the sorted instances.  Tile ids and items are checked against the
-// tile count and the item count: only a sort that gave up (status set, so nothing runs here)
-// could leave other values, but a range write out of bounds must not be possible at all.
-__global__ void __launch_bounds__(256) ranges_kernel(const uint32_t *tile_keys, const uint32_t *vals,
-                                                     const uint32_t *counters, const float4 *uvdo, uint32_t *ranges,
-                                                     uint64_t *keys64, int64_t n_tiles, int64_t vn,
-                                                     const int32_t *status) {
+// The optional 64-bit keys (tile << 32 | depth bits) of the sorted instances.  Tile ids and
+// items are checked against their counts: only a sort that gave up (status set, so nothing
+// runs here) could leave other values, but an access out of bounds must not be possible.
+__global__ void __launch_bounds__(256) keys64_kernel(const uint32_t *tile_keys, const uint32_t *vals,
+                                                     const uint32_t *counters, const float4 *uvdo, uint64_t *keys64,
+                                                     int64_t n_tiles, int64_t vn, const int32_t *status) {
+    pdl_wait();     // the previous kernel's results
+    pdl_trigger();  // the next kernel may be scheduled now
     const bool failed = binning_failed(status);
     int64_t m = counters[CTR_M];
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (failed || j >= m) return;
-    uint32_t t = tile_keys[j];
-    if (t >= n_tiles) return;
-    if (j == 0 || tile_keys[j - 1] != t) ranges[2 * (size_t)t] = (uint32_t)j;
-    if (j == m - 1 || tile_keys[j + 1] != t) ranges[2 * (size_t)t + 1] = (uint32_t)(j + 1);
-    const uint32_t it = vals[j];
-    if (keys64) keys64[j] = ((uint64_t)t << 32) | (it < vn ? __float_as_uint(uvdo[it].z) : 0u);
+    const uint32_t t = tile_keys[j], it = vals[j];
+    keys64[j] = t < n_tiles && it < vn ? ((uint64_t)t << 32) | __float_as_uint(uvdo[it].z) : ~0ull;
 }
 
 struct SortBufs {
@@ -436,14 +481,15 @@ struct SortBufs {
 // else (k1, v1).
 gs_status radix_sort(SortBufs b, const uint32_t *count_ptr, int64_t max_count, int n_passes, const uint32_t *hist,
                      uint32_t *lookback, int lb_tiles, uint32_t *tile_ctrs, int32_t *status, int spin_limit,
-                     cudaStream_t st) {
+                     cudaStream_t st, uint32_t *tile_counts = nullptr, uint32_t n_tiles = 0) {
     if (max_count <= 0 || n_passes <= 0) return GS_OK;
     int grid = ceil_div(max_count, kSortTile);
     uint32_t *ki = b.k0, *vi = b.v0, *ko = b.k1, *vo = b.v1;
     for (int p = 0; p < n_passes; ++p) {
-        onesweep_kernel<<<grid, kSortThreads, 0, st>>>(ki, vi, ko, vo, count_ptr, 8 * p, hist + 256 * p,
-                                                         tile_ctrs + p, lookback + (size_t)p * lb_tiles * 256,
-                                                         status, spin_limit);
+        const gs_status s = launch_pdl(onesweep_kernel, grid, kSortThreads, 0, st, ki, vi, ko, vo, count_ptr, 8 * p,
+                                       hist + 256 * p, tile_ctrs + p, lookback + (size_t)p * lb_tiles * 256, status,
+                                       spin_limit, p == n_passes - 1 ? tile_counts : nullptr, n_tiles);
+        if (s) return s;
         uint32_t *tk = ki, *tv = vi;
         ki = ko; vi = vo; ko = tk; vo = tv;
     }
@@ -456,57 +502,84 @@ gs_status radix_sort(SortBufs b, const uint32_t *count_ptr, int64_t max_count, i
 namespace gs {
 namespace {
 
-// Launch order of the blend kernels' tiles: decreasing instance count, so the
-// longest tiles start first and the short ones fill in behind them (longest-
-// processing-time-first; the order within a count bucket is arbitrary).  One
-// CTA: counting sort on a bucket of the count (exact below 1024 instances,
-// 64-instance steps above, saturating at 50,112), buckets taken high to low.
+// Per-tile ranges and the launch order of the blend kernels' tiles, from the instance count of
+// every tile (counted by the last tile-sort pass).  One CTA of 1024 threads.
+//   ranges: an exclusive scan of the counts (each thread scans a contiguous chunk of tiles),
+//   [0, 0) for an empty tile;
+//   order: decreasing instance count, so the longest tiles start first and the short ones fill
+//   in behind them (longest-processing-time-first; the order within a count bucket is
+//   arbitrary): a counting sort on a bucket of the count (exact below 1024 instances,
+//   64-instance steps above, saturating at 50,112), buckets taken high to low.
+// After a failed binning the ranges stay empty and every count is taken as 0.
 __device__ __forceinline__ int order_bucket(uint32_t c) {
     return c < 1024u ? (int)(c >> 2) : (int)min(256u + ((c - 1024u) >> 6), 1023u);
 }
 
-__global__ void __launch_bounds__(1024) tile_order_kernel(const uint32_t *ranges, int n_tiles, uint32_t *order) {
+// Exclusive scan of one value per thread over the 1024-thread block; returns the prefix.
+__device__ __forceinline__ uint32_t scan1024(uint32_t x, uint32_t *warp_tot) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t inc = x;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += y;
+    }
+    if (lane == 31) warp_tot[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        const uint32_t t = warp_tot[lane];
+        uint32_t ti = t;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, ti, d);
+            if (lane >= d) ti += y;
+        }
+        warp_tot[lane] = ti - t;  // exclusive over warps
+    }
+    __syncthreads();
+    const uint32_t r = warp_tot[wid] + inc - x;
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(1024) ranges_order_kernel(const uint32_t *counts, int n_tiles, uint32_t *ranges,
+                                                            uint32_t *order, const int32_t *status) {
+    pdl_wait();     // the previous kernel's results
+    pdl_trigger();  // the next kernel may be scheduled now
     __shared__ uint32_t hist[1024];
     __shared__ uint32_t warp_tot[32];
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int tid = threadIdx.x;
+    const bool failed = binning_failed(status);
+    const int per = (n_tiles + 1023) / 1024, t0 = tid * per, t1 = min(n_tiles, t0 + per);
+    uint32_t sum = 0;
+    for (int t = t0; t < t1; ++t) sum += failed ? 0u : counts[t];
+    uint32_t run = scan1024(sum, warp_tot);
+    if (!failed)
+        for (int t = t0; t < t1; ++t) {
+            const uint32_t c = counts[t];
+            ranges[2 * t] = c ? run : 0u;  // empty tiles: [0, 0)
+            ranges[2 * t + 1] = c ? run + c : 0u;
+            run += c;
+        }
+    if (!order) return;  // whole block
     hist[tid] = 0u;
     __syncthreads();
-    for (int t = tid; t < n_tiles; t += 1024) atomicAdd(&hist[order_bucket(ranges[2 * t + 1] - ranges[2 * t])], 1u);
+    for (int t = tid; t < n_tiles; t += 1024) atomicAdd(&hist[order_bucket(failed ? 0u : counts[t])], 1u);
     __syncthreads();
     // exclusive scan over buckets from the highest down: thread i takes bucket 1023 - i
     const uint32_t h = hist[1023 - tid];
-    uint32_t x = h;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
-        if (lane >= d) x += y;
-    }
-    if (lane == 31) warp_tot[wid] = x;
-    __syncthreads();
-    if (wid == 0) {
-        uint32_t wsum = warp_tot[lane];
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, wsum, d);
-            if (lane >= d) wsum += y;
-        }
-        warp_tot[lane] = wsum;  // inclusive over warps
-    }
-    __syncthreads();
-    const uint32_t before = (wid > 0 ? warp_tot[wid - 1] : 0u) + x - h;
-    __syncthreads();
+    const uint32_t before = scan1024(h, warp_tot);
     hist[1023 - tid] = before;  // first slot of bucket 1023 - tid
     __syncthreads();
     for (int t = tid; t < n_tiles; t += 1024) {
-        const uint32_t pos = atomicAdd(&hist[order_bucket(ranges[2 * t + 1] - ranges[2 * t])], 1u);
+        const uint32_t pos = atomicAdd(&hist[order_bucket(failed ? 0u : counts[t])], 1u);
         order[pos] = (uint32_t)t;
     }
 }
 
-gs_status write_tile_order(const gs_binning *out, int64_t total_tiles, cudaStream_t st) {
-    if (!out->tile_order) return GS_OK;
-    tile_order_kernel<<<1, 1024, 0, st>>>(out->ranges, (int)total_tiles, out->tile_order);
-    return last_launch();
+gs_status write_ranges_order(const uint32_t *counts, const gs_binning *out, int64_t total_tiles, cudaStream_t st) {
+    return launch_pdl(ranges_order_kernel, 1, 1024, 0, st, counts, (int)total_tiles, out->ranges, out->tile_order,
+                      out->status);
 }
 
 }  // namespace
@@ -523,26 +596,28 @@ extern "C" gs_status gs_bin_sort(int64_t n, const gs_projected *proj, const gs_c
     if (!make_view_table(cams, n_views, n, &vt) || !make_params(p, &prm)) return GS_ERR_ARG;
     if (out->capacity < 0 || out->capacity >= ((int64_t)1 << 30) || n * n_views >= ((int64_t)1 << 30)) return GS_ERR_ARG;
     if (!out->vals || !out->ranges || !out->n_inst || !out->status || !ws) return GS_ERR_ARG;
-    WsLayout L = ws_layout(n, n_views, out->capacity);
+    WsLayout L = ws_layout(n, n_views, out->capacity, &vt);
     if (ws_bytes < L.bin_end || (reinterpret_cast<uintptr_t>(ws) & 255)) return GS_ERR_ARG;
     char *w = static_cast<char *>(ws);
     uint32_t *counters = reinterpret_cast<uint32_t *>(w + L.counters);
     uint32_t *block_sums = reinterpret_cast<uint32_t *>(w + L.scan_blocks);
     uint32_t *hist = reinterpret_cast<uint32_t *>(w + L.hist);
     uint32_t *lookback = reinterpret_cast<uint32_t *>(w + L.lookback);
+    uint32_t *tile_counts = reinterpret_cast<uint32_t *>(w + L.tile_counts);
     int64_t total_tiles = vt.tile_off[n_views];
     int64_t vn = n * n_views;
 
+    if (vn > 0 && (!proj->uvdo || !proj->conic || !proj->tiles_touched)) return GS_ERR_ARG;
+
+    // Every kernel of the binning is launched with programmatic stream serialization: it is
+    // scheduled while its predecessor drains and waits for it (pdl_wait) before reading.
     gs_status s;
-    if ((s = cuda_status(cudaMemsetAsync(out->ranges, 0, sizeof(uint32_t) * 2 * total_tiles, st)))) return s;
-    if ((s = cuda_status(cudaMemsetAsync(counters, 0, sizeof(uint32_t) * 64, st)))) return s;
-    if ((s = cuda_status(cudaMemsetAsync(out->n_inst, 0, sizeof(int64_t), st)))) return s;
-    if ((s = cuda_status(cudaMemsetAsync(out->status, 0, sizeof(int32_t), st)))) return s;
-    if (vn == 0) return write_tile_order(out, total_tiles, st);
-    if (!proj->uvdo || !proj->conic || !proj->tiles_touched) return GS_ERR_ARG;
-    if ((s = cuda_status(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * 8 * 256, st)))) return s;
-    size_t lb_bytes = sizeof(uint32_t) * 256 * ((size_t)4 * L.lb_tiles_depth + (size_t)3 * L.lb_tiles_inst);
-    if ((s = cuda_status(cudaMemsetAsync(lookback, 0, lb_bytes, st)))) return s;
+    const int64_t n_lb4 = vn > 0 ? 64 * ((int64_t)4 * L.lb_tiles_depth + (int64_t)3 * L.lb_tiles_inst) : 0;
+    const int init_grid = (int)std::max<int64_t>(1, std::min<int64_t>((n_lb4 + 255) / 256, 1216));
+    if ((s = launch_pdl(bin_init_kernel, init_grid, 256, 0, st, out->ranges, 2 * total_tiles, counters, out->n_inst,
+                        out->status, tile_counts, total_tiles, hist, reinterpret_cast<uint4 *>(lookback), n_lb4)))
+        return s;
+    if (vn == 0) return write_ranges_order(tile_counts, out, total_tiles, st);
 
     const float4 *uvdo = reinterpret_cast<const float4 *>(proj->uvdo);
     const float4 *conic = reinterpret_cast<const float4 *>(proj->conic);
@@ -551,11 +626,13 @@ extern "C" gs_status gs_bin_sort(int64_t n, const gs_projected *proj, const gs_c
 
     // 1. compact visible items in index order, keyed by depth bits
     int nb = ceil_div(vn, kScanBlock);
-    vis_reduce_kernel<<<nb, 256, 0, st>>>(proj->tiles_touched, vn, block_sums);
-    blocksum_scan_kernel<<<1, 1024, 0, st>>>(block_sums, nullptr, nb, kScanBlock, counters, CTR_NVIS, -1, 0, nullptr,
-                                             nullptr);
-    vis_compact_kernel<<<nb, 256, 0, st>>>(proj->tiles_touched, uvdo, vn, block_sums, dk_a, dv_a, hist);
-    if ((s = last_launch())) return s;
+    if ((s = launch_pdl(vis_reduce_kernel, nb, 256, 0, st, proj->tiles_touched, vn, block_sums))) return s;
+    if ((s = launch_pdl(blocksum_scan_kernel, 1, 1024, 0, st, block_sums, nullptr, (int64_t)nb, kScanBlock, counters,
+                        (int)CTR_NVIS, -1, (int64_t)0, nullptr, nullptr)))
+        return s;
+    if ((s = launch_pdl(vis_compact_kernel, nb, 256, 0, st, proj->tiles_touched, uvdo, vn, block_sums, dk_a, dv_a,
+                        hist)))
+        return s;
 
     // 2. stable sort of the visible items by depth (4 passes: result in dk_a/dv_a)
     if ((s = radix_sort({dk_a, dv_a, dk_b, dv_b}, counters + CTR_NVIS, vn, 4, hist, lookback, L.lb_tiles_depth,
@@ -573,25 +650,31 @@ extern "C" gs_status gs_bin_sort(int64_t n, const gs_projected *proj, const gs_c
     uint32_t *emit_vals = (tile_passes % 2 == 0) ? out->vals : tv_b;
     uint32_t *other_vals = (tile_passes % 2 == 0) ? tv_b : out->vals;
     const int nbe = ceil_div(vn, kEmitBlock);
-    emit_reduce_kernel<<<nbe, kEmitBlock, 0, st>>>(sorted_items, proj->tiles_touched, counters, block_sums, vn,
-                                                   out->status);
-    blocksum_scan_kernel<<<1, 1024, 0, st>>>(block_sums, counters + CTR_NVIS, 0, kEmitBlock, counters, CTR_MRAW, CTR_M,
-                                             out->capacity, out->n_inst, out->status);
-    emit_kernel<<<nbe, kEmitBlock, 0, st>>>(vt, sorted_items, proj->tiles_touched, uvdo, conic, counters, block_sums,
-                                    out->capacity, tk_a, emit_vals, tile_passes, hist + 4 * 256, vn, out->status);
-    if ((s = last_launch())) return s;
-    if (out->capacity == 0) return write_tile_order(out, total_tiles, st);
+    if ((s = launch_pdl(emit_reduce_kernel, nbe, kEmitBlock, 0, st, sorted_items, proj->tiles_touched, counters,
+                        block_sums, vn, out->status)))
+        return s;
+    if ((s = launch_pdl(blocksum_scan_kernel, 1, 1024, 0, st, block_sums, counters + CTR_NVIS, (int64_t)0, kEmitBlock,
+                        counters, (int)CTR_MRAW, (int)CTR_M, out->capacity, out->n_inst, out->status)))
+        return s;
+    if ((s = launch_pdl(emit_kernel, nbe, kEmitBlock, 0, st, vt, sorted_items, proj->tiles_touched, uvdo, conic,
+                        counters, block_sums, out->capacity, tk_a, emit_vals, tile_passes, hist + 4 * 256, vn,
+                        out->status)))
+        return s;
+    if (out->capacity == 0) return write_ranges_order(tile_counts, out, total_tiles, st);
 
     // 4. stable sort of the instances by tile id
     if ((s = radix_sort({tk_a, emit_vals, tk_b, other_vals}, counters + CTR_M, out->capacity, tile_passes,
                         hist + 4 * 256, lookback + (size_t)4 * L.lb_tiles_depth * 256, L.lb_tiles_inst,
-                        counters + CTR_TILE + 4, out->status, prm.spin_limit, st)))
+                        counters + CTR_TILE + 4, out->status, prm.spin_limit, st, tile_counts, (uint32_t)total_tiles)))
         return s;
     const uint32_t *sorted_tiles = (tile_passes % 2 == 0) ? tk_a : tk_b;
 
-    // 5. per-tile ranges (and the 64-bit keys if requested)
-    ranges_kernel<<<ceil_div(out->capacity, 256), 256, 0, st>>>(sorted_tiles, out->vals, counters, uvdo, out->ranges,
-                                                                out->keys, total_tiles, vn, out->status);
-    if ((s = last_launch())) return s;
-    return write_tile_order(out, total_tiles, st);
+    // 5. per-tile ranges from the tile counts, the launch order, and the 64-bit keys if requested
+    if ((s = write_ranges_order(tile_counts, out, total_tiles, st))) return s;
+    if (out->keys) {
+        if ((s = launch_pdl(keys64_kernel, ceil_div(out->capacity, 256), 256, 0, st, sorted_tiles, out->vals, counters,
+                            uvdo, out->keys, total_tiles, vn, out->status)))
+            return s;
+    }
+    return GS_OK;
 }
