@@ -97,6 +97,17 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP, MAP, KF>())
     __shared__ __align__(16) float s_g[MAP ? WL::PXW * WL::GROW : 4]; // [pixel][part][term] gradients
     __shared__ float s_t[MAP ? STAGE * WL::NWT : 4];                  // [slot][term] summed terms
     __shared__ float s_basis[KF ? KF * D : 1];                        // W, K x D (rows >= K zero)
+    // raw records of two stages (the next one is copied while the current one is processed):
+    // centre / depth / opacity, conic / radius, centre low parts, colour (f32 storage), features
+    constexpr bool RGB32 = sizeof(RT) == 4;
+    constexpr int FB = D * (int)sizeof(FT);   // feature bytes per Gaussian
+    constexpr int FCH = FB / 16;              // their 16-byte chunks
+    constexpr int NCOPY = 3 + (RGB32 ? 3 : 0) + FCH;
+    static_assert(FB % 16 == 0, "features in 16-byte chunks");
+    __shared__ float4 r_a[2][STAGE], r_c[2][STAGE];
+    __shared__ float2 r_lo[2][STAGE];
+    __shared__ float r_rgb[2][STAGE][4];
+    __shared__ __align__(16) unsigned char r_f[2][STAGE * FB];
     const RT *rgb = static_cast<const RT *>(A.rgb);
     const FT *feat = static_cast<const FT *>(A.feat);
 
@@ -298,7 +309,7 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP, MAP, KF>())
     };
 
     // Every listed splat was blended by a pixel of the group, so no box culling is needed.
-    auto process = [&](const int k) {
+    auto process = [&](const int k, const float *sfeat) {
         const int pos = s_pos[k];
         const SplatGeo s = s_geo[k];
         // the mask listed this splat because a pixel of the group blended it, so some lane
@@ -317,7 +328,7 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP, MAP, KF>())
         {
             const float4 c = s_rgbd[k];
             x[0] = c.x; x[1] = c.y; x[2] = c.z; x[3] = c.w; x[4] = 1.f;
-            const float4 *sf = reinterpret_cast<const float4 *>(s_feat + k * F);
+            const float4 *sf = reinterpret_cast<const float4 *>(sfeat + k * F);
 #pragma unroll
             for (int q = 0; q < F4; ++q) {
                 const float4 f = sf[q];
@@ -370,76 +381,125 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP, MAP, KF>())
         }
     };
 
-    // stages list entries [off, off + cnt) (instance indices, back to front; cnt <= STAGE),
-    // walks them and, in map mode, contracts the stage's slots
-    auto stage_and_process = [&](const int off, const int cnt) {
+    // Stages and walks list entries [0, cnt) (instance indices, back to front; cnt <= 32), STAGE at
+    // a time: the batch's items are loaded once (one per lane), each stage's records are copied
+    // into shared memory asynchronously, the next stage's while the current one is processed,
+    // and in map mode each stage's slots are contracted after it.
+    auto run_batch = [&](const int cnt) {
         const int si = lane % STAGE, part = lane / STAGE;
-        if (si < cnt) {
-            const uint32_t ii = s_list[off + si];
-            const uint32_t item = checked_item(A.vals[ii], voff, vt.n, A.status);
-            const int64_t g = (int64_t)item - voff;
-            if (part == 0) {
-                const float4 a = A.uvdo[item];
-                const float4 c = A.conic[item];
-                s_geo[si] = make_geo(a, A.uv_lo[item], c);
-                s_rgbd[si] = load_rgbd(rgb, g, a.z);
-                s_item[si] = item;
-                s_pos[si] = (int)(ii - start);
-            }
-            if constexpr (KF > 0) {
-                // z = W f for this part's K / PARTS logits
-                float f[D];
+        const uint32_t my_ii = lane < cnt ? s_list[lane] : 0u;
+        const uint32_t my_item = lane < cnt ? checked_item(A.vals[my_ii], voff, vt.n, A.status) : (uint32_t)voff;
+        const int n_st = (cnt + STAGE - 1) / STAGE;
+        auto issue = [&](const int st) {
+            const int e = st * STAGE + si, b = st & 1;
+            const uint32_t item = __shfl_sync(0xffffffffu, my_item, e & 31);
+            if (e < cnt) {
+                const int64_t g = (int64_t)item - voff;
 #pragma unroll
-                for (int q = 0; q < D / 4; ++q) {
-                    const float4 f4 = load_feat4(feat, g * D + 4 * q);
-                    f[4 * q] = f4.x; f[4 * q + 1] = f4.y; f[4 * q + 2] = f4.z; f[4 * q + 3] = f4.w;
+                for (int c = part; c < NCOPY; c += PARTS) {
+                    if (c == 0) cp_async16(&r_a[b][si], A.uvdo + item);
+                    else if (c == 1) cp_async16(&r_c[b][si], A.conic + item);
+                    else if (c == 2) cp_async8(&r_lo[b][si], A.uv_lo + item);
+                    else if (RGB32 && c < 6) cp_async4(&r_rgb[b][si][c - 3], rgb + 3 * g + (c - 3));
+                    else {
+                        const int q = c - (RGB32 ? 6 : 3);
+                        cp_async16(&r_f[b][si * FB + 16 * q], reinterpret_cast<const unsigned char *>(feat + g * D) + 16 * q);
+                    }
                 }
-#pragma unroll
-                for (int kk = 0; kk < KF / PARTS; ++kk) {
-                    const int k = part * (KF / PARTS) + kk;
-                    float z = 0.f;
-#pragma unroll
-                    for (int d = 0; d < D; ++d) z = fmaf(s_basis[k * D + d], f[d], z);
-                    s_feat[si * F + k] = z;
-                }
-            } else if (part == 0) {
-                float4 *sf = reinterpret_cast<float4 *>(s_feat + si * F);
-#pragma unroll
-                for (int q = 0; q < F4; ++q) sf[q] = load_feat4(feat, g * D + 4 * q);
             }
+            cp_async_commit();
+        };
+        issue(0);
+        for (int st = 0; st < n_st; ++st) {
+            const int b = st & 1, c_cnt = min(STAGE, cnt - st * STAGE);
+            if (st + 1 < n_st) {
+                issue(st + 1);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            __syncwarp();
+            // the stage's working records from the raw ones
+            const int e = st * STAGE + si;
+            const uint32_t ii = __shfl_sync(0xffffffffu, my_ii, e & 31);
+            const uint32_t item = __shfl_sync(0xffffffffu, my_item, e & 31);
+            if (si < c_cnt) {
+                const int64_t g = (int64_t)item - voff;
+                if (part == 0) {
+                    const float4 a = r_a[b][si];
+                    s_geo[si] = make_geo(a, r_lo[b][si], r_c[b][si]);
+                    s_rgbd[si] = RGB32 ? make_float4(r_rgb[b][si][0], r_rgb[b][si][1], r_rgb[b][si][2], a.z)
+                                       : load_rgbd(rgb, g, a.z);
+                    s_item[si] = item;
+                    s_pos[si] = (int)(ii - start);
+                }
+                const FT *fr = reinterpret_cast<const FT *>(&r_f[b][si * FB]);
+                if constexpr (KF > 0) {
+                    // z = W f for this part's K / PARTS logits
+#pragma unroll
+                    for (int kk = 0; kk < KF / PARTS; ++kk) {
+                        const int k = part * (KF / PARTS) + kk;
+                        float z = 0.f;
+#pragma unroll
+                        for (int q = 0; q < D / 4; ++q) {
+                            const float4 f4 = load_feat4(fr, 4 * q);
+                            z = fmaf(s_basis[k * D + 4 * q], f4.x, z);
+                            z = fmaf(s_basis[k * D + 4 * q + 1], f4.y, z);
+                            z = fmaf(s_basis[k * D + 4 * q + 2], f4.z, z);
+                            z = fmaf(s_basis[k * D + 4 * q + 3], f4.w, z);
+                        }
+                        s_feat[si * F + k] = z;
+                    }
+                } else if (!RGB32 || sizeof(FT) != 4) {
+                    // half storage: the features widened to f32
+                    for (int q = part; q < D / 4; q += PARTS)
+                        reinterpret_cast<float4 *>(s_feat + si * F)[q] = load_feat4(fr, 4 * q);
+                }
+            }
+            __syncwarp();
+            // f32 features are read where they landed; the others from the widened copy
+            const float *sfeat = (KF == 0 && sizeof(FT) == 4) ? reinterpret_cast<const float *>(r_f[b]) : s_feat;
+            for (int k = 0; k < c_cnt; ++k) process(k, sfeat);
+            if constexpr (MAP) contract(c_cnt);
+            __syncwarp();
         }
-        __syncwarp();
-        for (int k = 0; k < cnt; ++k) process(k);
-        if constexpr (MAP) contract(cnt);
-        __syncwarp();
     };
 
-    // the group's blended instances, back to front: each mask word appends its set bits
-    // (highest first) to the list; every 32 entries are staged and processed
+    // the group's blended instances, back to front: the mask words are read 32 at a time (lane
+    // l holds word wc - l), each word appends its set bits (highest first) to the list, and every
+    // 32 entries are staged and processed
     const int64_t lo_i = start, hi_i = (int64_t)start + wmax;
+    const int64_t w_lo = lo_i >> 5;
     int n = 0;  // entries in the list (warp-uniform, < 32 between words)
-    for (int64_t wi = (hi_i - 1) >> 5; wi >= (lo_i >> 5); --wi) {
-        uint32_t m = 0u;
+    for (int64_t wc = (hi_i - 1) >> 5; wc >= w_lo; wc -= 32) {
+        const int64_t wl = wc - lane;
+        uint32_t mw = 0u;
+        if (wl >= w_lo) {
 #pragma unroll
-        for (int j = 0; j < NP; ++j) m |= A.bmask[(int64_t)SH::group(grp, j) * A.bm_stride + wi];
-        const int64_t base = wi << 5;
-        if (base < lo_i) m &= ~0u << (int)(lo_i - base);
-        if (hi_i - base < 32) m &= (1u << (int)(hi_i - base)) - 1u;
-        if (m == 0u) continue;
-        const int b = 31 - lane;
-        const int above = lane == 0 ? 0 : __popc(m >> (32 - lane));  // set bits above bit b
-        if ((m >> b) & 1u) s_list[n + above] = (uint32_t)(base + b);
-        n += __popc(m);
-        __syncwarp();
-        if (n >= 32) {
-#pragma unroll
-            for (int off = 0; off < 32; off += STAGE) stage_and_process(off, STAGE);
-            if (lane < n - 32) s_list[lane] = s_list[32 + lane];
+            for (int j = 0; j < NP; ++j) mw |= A.bmask[(int64_t)SH::group(grp, j) * A.bm_stride + wl];
+            const int64_t base = wl << 5;
+            if (base < lo_i) mw &= ~0u << (int)(lo_i - base);
+            if (hi_i - base < 32) mw &= (1u << (int)(hi_i - base)) - 1u;
+        }
+        const int nw = wc - w_lo + 1 < 32 ? (int)(wc - w_lo + 1) : 32;
+        for (int t = 0; t < nw; ++t) {
+            const uint32_t m = __shfl_sync(0xffffffffu, mw, t);
+            if (m == 0u) continue;
+            const int64_t base = (wc - t) << 5;
+            const int b = 31 - lane;
+            const int above = lane == 0 ? 0 : __popc(m >> (32 - lane));  // set bits above bit b
+            if ((m >> b) & 1u) s_list[n + above] = (uint32_t)(base + b);
+            n += __popc(m);
             __syncwarp();
-            n -= 32;
+            if (n >= 32) {
+                run_batch(32);
+                if (lane < n - 32) s_list[lane] = s_list[32 + lane];
+                __syncwarp();
+                n -= 32;
+            }
         }
     }
-    for (int off = 0; off < n; off += STAGE) stage_and_process(off, min(STAGE, n - off));
+    if (n > 0) run_batch(n);
 }
 
 template <int D, int NP, bool MAP, int KF, typename RT, typename FT>
