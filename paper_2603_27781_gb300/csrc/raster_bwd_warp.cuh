@@ -43,23 +43,34 @@ namespace gs {
 // gradients (zero beyond K).
 constexpr int kFactorK = 8;
 
-// Map-mode layout: SL slots (splats staged and contracted together), LPS = 32 / SL
-// lanes per slot in the contraction, each owning HW of the NWT weighted terms and
-// RPL of the block's pixel rows in the moments.
+// Map-mode layout: SL slots (splats staged and contracted together); in the contraction lane
+// (column c, slot group j) sums the NWT weighted terms and the dpow column sums of SPL slots over
+// the ROWS pixels of column c, and the eight columns are then added by shuffles.  In the epilogue
+// LPS = 32 / SL lanes serve each slot.
 template <int D, int NP, int KF, int SL>
 struct WarpMapLayout {
     static constexpr int F = KF ? KF : D;
     static constexpr int PXW = 32 * NP;         // pixels of the block, 8 wide
     static constexpr int ROWS = PXW / 8;
     static constexpr int LPS = 32 / SL;
+    static constexpr int SPL = SL / 4;          // slots per lane in the contraction
     static constexpr int NWT = 4 + F;           // weighted terms: depth, r, g, b, F
-    static constexpr int HW = NWT / LPS;
-    static constexpr int HWP = (HW + 3) / 4 * 4;
-    static constexpr int GROW = LPS * HWP;      // a pixel's row of weighted terms
+    static constexpr int GROW = NWT;            // a pixel's row of weighted terms
+    static constexpr int NSV = NWT + 6;         // a slot's sums: the terms and six moments
+    // The contraction runs in up to four chunks of terms so that a lane's running sums fit in
+    // its registers (at most 2 CAPS values): the first chunk [0, T1) carries the moments,
+    // then [T1, T2), [T2, T3) and [T3, NWT).
+    static constexpr int CAPS = NP == 1 ? 12 : 28;
+    static constexpr int TC = CAPS / 4 * 4;
+    static constexpr int T1 = NWT < (CAPS - 6) / 4 * 4 ? NWT : (CAPS - 6) / 4 * 4;
+    static constexpr int T2 = NWT < T1 + TC ? NWT : T1 + TC;
+    static constexpr int T3 = NWT < T2 + TC ? NWT : T2 + TC;
+    static_assert(NWT <= T3 + TC, "four chunks cover the terms");
     static constexpr int WROW = PXW + 4;        // a slot's row of per-pixel values (padded against bank conflicts)
-    static constexpr int RPL = ROWS / LPS;
-    static_assert(NWT % LPS == 0 && ROWS % LPS == 0 && D % (4 * LPS) == 0, "lanes per slot divide the work");
+    static_assert(NWT % 4 == 0 && SL == 8 && D % (4 * LPS) == 0, "16-byte rows; lanes divide the work");
 };
+
+template <int V> struct IntC { static constexpr int value = V; };
 
 // Slots per stage in map mode: 8 (four lanes per slot) keeps the per-slot arrays small
 // enough for more resident blocks; pose mode stages 16.
@@ -94,8 +105,8 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP, MAP, KF>())
     __shared__ uint32_t s_list[64];
     __shared__ __align__(16) float s_w[MAP ? STAGE * WL::WROW : 4];   // [slot][pixel] alpha T
     __shared__ __align__(16) float s_p[MAP ? STAGE * WL::WROW : 4];   // [slot][pixel] dpow
-    __shared__ __align__(16) float s_g[MAP ? WL::PXW * WL::GROW : 4]; // [pixel][part][term] gradients
-    __shared__ float s_t[MAP ? STAGE * WL::NWT : 4];                  // [slot][term] summed terms
+    __shared__ __align__(16) float s_g[MAP ? WL::PXW * WL::GROW : 4]; // [pixel][term] gradients
+    __shared__ float s_t[MAP ? STAGE * WL::NSV : 4];                  // [slot][sum] sums
     __shared__ float s_basis[KF ? KF * D : 1];                        // W, K x D (rows >= K zero)
     // raw records of two stages (the next one is copied while the current one is processed):
     // centre / depth / opacity, conic / radius, centre low parts, colour (f32 storage), features
@@ -179,85 +190,105 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP, MAP, KF>())
             term[3] = gch[p][2];
 #pragma unroll
             for (int f = 0; f < F; ++f) term[4 + f] = gch[p][5 + f];
-            float *row = s_g + (p * 32 + lane) * WL::GROW;
+            float4 *row = reinterpret_cast<float4 *>(s_g + (p * 32 + lane) * WL::GROW);
 #pragma unroll
-            for (int c = 0; c < WL::GROW; ++c) {
-                const int h = c / WL::HWP, i = c % WL::HWP;
-                row[c] = i < WL::HW ? term[h * WL::HW + i] : 0.f;
-            }
+            for (int c = 0; c < WL::NWT / 4; ++c)
+                row[c] = make_float4(term[4 * c], term[4 * c + 1], term[4 * c + 2], term[4 * c + 3]);
         }
     }
 
-    // Map mode, after a stage of cnt splats: lane (j, part) sums slot j's weighted terms
-    // [part HW, (part + 1) HW) over the block's pixels and the dpow moments over its RPL rows,
-    // then the slot's sums go to the splat's accumulators.
-    auto contract = [&](const int cnt) {
-        __syncwarp();
-        const int j = lane % STAGE, part = lane / STAGE;
-        const float4 *wr = reinterpret_cast<const float4 *>(s_w + j * WL::WROW);
-        const float4 *gr = reinterpret_cast<const float4 *>(s_g + part * WL::HWP);
-        float acc[WL::HWP];
+    // Map mode, after a stage of cnt splats: lane (column col, slot group jg) sums, for slots
+    // jg SPL + sj, w times the weighted terms [T0, T1) and (with MOM) dpow times (1, ly, ly^2) over
+    // the pixels of its column (eight distinct 16-byte rows per quarter-warp read), scales the
+    // column sums by the column's coordinate into the six moments, and the eight columns are
+    // added by a transpose reduction, lane col keeping block col of the chunk's sums.
+    auto contract_chunk = [&](auto t0c, auto t1c, auto momc) {
+        constexpr int T0 = decltype(t0c)::value, T1 = decltype(t1c)::value;
+        constexpr bool MOM = decltype(momc)::value != 0;
+        constexpr int NT = T1 - T0, CV = NT + (MOM ? 6 : 0);
+        constexpr int CVP = (WL::SPL * CV + 7) / 8 * 8;
+        const int col = lane & 7, jg = lane >> 3;
+        float acc[CVP];
 #pragma unroll
-        for (int c = 0; c < WL::HWP; ++c) acc[c] = 0.f;
-#pragma unroll 2
-        for (int q = 0; q < WL::PXW / 4; ++q) {
-            const float4 w4 = wr[q];
-            const float wq[4] = {w4.x, w4.y, w4.z, w4.w};
+        for (int c = 0; c < CVP; ++c) acc[c] = 0.f;
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const float4 *g4 = gr + (4 * q + i) * (WL::GROW / 4);
+        for (int ly = 0; ly < WL::ROWS; ++ly) {
+            const int q = ly * 8 + col;
+            const float lyc = (float)ly + 0.5f - 0.5f * WL::ROWS;
+            float w[WL::SPL];
 #pragma unroll
-                for (int c = 0; c < WL::HWP / 4; ++c) {
-                    const float4 gv = g4[c];
-                    acc[4 * c] = fmaf(wq[i], gv.x, acc[4 * c]);
-                    if (4 * c + 1 < WL::HW) acc[4 * c + 1] = fmaf(wq[i], gv.y, acc[4 * c + 1]);
-                    if (4 * c + 2 < WL::HW) acc[4 * c + 2] = fmaf(wq[i], gv.z, acc[4 * c + 2]);
-                    if (4 * c + 3 < WL::HW) acc[4 * c + 3] = fmaf(wq[i], gv.w, acc[4 * c + 3]);
+            for (int sj = 0; sj < WL::SPL; ++sj) {
+                const int j = jg * WL::SPL + sj;
+                w[sj] = s_w[j * WL::WROW + q];
+                if constexpr (MOM) {
+                    const float dp = s_p[j * WL::WROW + q];
+                    float *a = acc + sj * CV + NT;
+                    a[0] += dp;
+                    a[1] = fmaf(lyc, dp, a[1]);
+                    a[2] = fmaf(lyc * lyc, dp, a[2]);
+                }
+            }
+            const float4 *g4 = reinterpret_cast<const float4 *>(s_g + q * WL::GROW + T0);
+#pragma unroll
+            for (int c = 0; c < NT / 4; ++c) {
+                const float4 gv = g4[c];
+#pragma unroll
+                for (int sj = 0; sj < WL::SPL; ++sj) {
+                    float *a = acc + sj * CV + 4 * c;
+                    a[0] = fmaf(w[sj], gv.x, a[0]);
+                    a[1] = fmaf(w[sj], gv.y, a[1]);
+                    a[2] = fmaf(w[sj], gv.z, a[2]);
+                    a[3] = fmaf(w[sj], gv.w, a[3]);
                 }
             }
         }
-        // moments of dpow over rows [part RPL, (part + 1) RPL) of the block
-        const float4 *pr = reinterpret_cast<const float4 *>(s_p + j * WL::WROW);
-        float m1 = 0.f, mx = 0.f, my = 0.f, mxx = 0.f, mxy = 0.f, myy = 0.f;
+        if constexpr (MOM) {
+            // column sums of dpow (1, ly, ly^2) -> moments (1, lx, ly, lx^2, lx ly, ly^2)
+            const float lxc = (float)col - 3.5f;
 #pragma unroll
-        for (int r = 0; r < WL::RPL; ++r) {
-            const int ly = part * WL::RPL + r;
-            const float lyc = (float)ly + 0.5f - 0.5f * WL::ROWS;
-            const float4 d0 = pr[2 * ly], d1 = pr[2 * ly + 1];
-            const float d[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
-            float r0 = 0.f, rx = 0.f, rxx = 0.f;
-#pragma unroll
-            for (int lx = 0; lx < 8; ++lx) {
-                const float lxc = (float)lx - 3.5f;
-                r0 += d[lx];
-                rx = fmaf(d[lx], lxc, rx);
-                rxx = fmaf(d[lx], lxc * lxc, rxx);
+            for (int sj = 0; sj < WL::SPL; ++sj) {
+                float *a = acc + sj * CV + NT;
+                const float c0 = a[0], c1 = a[1], c2 = a[2];
+                a[1] = lxc * c0;
+                a[2] = c1;
+                a[3] = lxc * lxc * c0;
+                a[4] = lxc * c1;
+                a[5] = c2;
             }
-            m1 += r0;
-            mx += rx;
-            mxx += rxx;
-            my = fmaf(lyc, r0, my);
-            mxy = fmaf(lyc, rx, mxy);
-            myy = fmaf(lyc * lyc, r0, myy);
+        }
+        // transpose reduction over the eight columns (lanes xor 4, 2, 1)
+#pragma unroll
+        for (int sft = 4, len = CVP; sft >= 1; sft >>= 1, len >>= 1) {
+            const bool up = col & sft;
+#pragma unroll
+            for (int i = 0; i < len / 2; ++i) {
+                const float send = up ? acc[i] : acc[i + len / 2];
+                const float keep = up ? acc[i + len / 2] : acc[i];
+                acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, sft);
+            }
         }
 #pragma unroll
-        for (int s = STAGE; s < 32; s <<= 1) {
-            m1 += __shfl_xor_sync(0xffffffffu, m1, s);
-            mx += __shfl_xor_sync(0xffffffffu, mx, s);
-            my += __shfl_xor_sync(0xffffffffu, my, s);
-            mxx += __shfl_xor_sync(0xffffffffu, mxx, s);
-            mxy += __shfl_xor_sync(0xffffffffu, mxy, s);
-            myy += __shfl_xor_sync(0xffffffffu, myy, s);
+        for (int i = 0; i < CVP / 8; ++i) {
+            const int v = col * (CVP / 8) + i, sj = v / CV, t = v % CV;
+            if (v < WL::SPL * CV) s_t[(jg * WL::SPL + sj) * WL::NSV + (t < NT ? T0 + t : WL::NWT + t - NT)] = acc[i];
         }
-        if (j < cnt) {
-#pragma unroll
-            for (int c = 0; c < WL::HW; ++c) s_t[j * WL::NWT + part * WL::HW + c] = acc[c];
-        }
+    };
+    // Then lanes (slot j, part) send slot j's sums to the splat's accumulators.
+    auto contract = [&](const int cnt) {
         __syncwarp();
+        contract_chunk(IntC<0>(), IntC<WL::T1>(), IntC<1>());
+        if constexpr (WL::T2 > WL::T1) contract_chunk(IntC<WL::T1>(), IntC<WL::T2>(), IntC<0>());
+        if constexpr (WL::T3 > WL::T2) contract_chunk(IntC<WL::T2>(), IntC<WL::T3>(), IntC<0>());
+        if constexpr (WL::NWT > WL::T3) contract_chunk(IntC<WL::T3>(), IntC<WL::NWT>(), IntC<0>());
+        __syncwarp();
+        const int j = lane % STAGE, part = lane / STAGE;
         if (j < cnt) {
             const int64_t item = s_item[j];
             const int64_t g = item - voff;
-            const float *tj = s_t + j * WL::NWT;
+            // slot j's sums: the terms (depth, r, g, b, F) then the moments (S1, Sx, Sy, Sxx, Sxy, Syy)
+            const float *tj = s_t + j * WL::NSV;
+            const float m1 = tj[WL::NWT], mx = tj[WL::NWT + 1], my = tj[WL::NWT + 2];
+            const float mxx = tj[WL::NWT + 3], mxy = tj[WL::NWT + 4], myy = tj[WL::NWT + 5];
             if (part == 0) {
                 // centre and opacity from the moments expanded about the splat centre; depth
                 const SplatGeo sg = s_geo[j];
@@ -292,10 +323,10 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP, MAP, KF>())
                 for (int i = 0; i < 4; ++i) {
                     const int c = part * DP + 4 * c4 + i;
                     if constexpr (KF > 0) {
-                        float s = 0.f;
+                        float sacc = 0.f;
 #pragma unroll
-                        for (int k = 0; k < KF; ++k) s = fmaf(s_basis[k * D + c], tj[4 + k], s);
-                        o4[i] = s;
+                        for (int k = 0; k < KF; ++k) sacc = fmaf(s_basis[k * D + c], tj[4 + k], sacc);
+                        o4[i] = sacc;
                     } else {
                         o4[i] = tj[4 + c];
                     }
