@@ -343,20 +343,16 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint32_t *
     uint32_t key[kSortIPT], val[kSortIPT], rank[kSortIPT];
 #pragma unroll
     for (int r = 0; r < kSortIPT; ++r) {
-        int64_t i = base + (int64_t)w * (kSortIPT * 32) + r * 32 + lane;
-        bool valid = i < n;
-        key[r] = valid ? keys_in[i] : 0u;
-        val[r] = valid ? vals_in[i] : 0u;
-        const uint32_t d = (key[r] >> shift) & 255u;
-        // lanes with the same digit: one ballot per digit bit (cheaper than match.any);
-        // invalid lanes match nothing and are matched by nothing
-        const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
-        uint32_t peers = valid ? vmask : (1u << lane);
+        const int64_t i = base + (int64_t)w * (kSortIPT * 32) + r * 32 + lane;
+        key[r] = i < n ? keys_in[i] : 0u;
+        val[r] = i < n ? vals_in[i] : 0u;
+    }
 #pragma unroll
-        for (int bit = 0; bit < 8; ++bit) {
-            const uint32_t set = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
-            if (valid) peers &= (d >> bit) & 1u ? set : ~set;
-        }
+    for (int r = 0; r < kSortIPT; ++r) {
+        const bool valid = base + (int64_t)w * (kSortIPT * 32) + r * 32 + lane < n;
+        const uint32_t d = (key[r] >> shift) & 255u;
+        // lanes with the same digit; an invalid lane matches only itself
+        const uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : 256u + lane);
         int leader = __ffs(peers) - 1;
         uint32_t b = 0;
         if (valid && lane == leader) {
@@ -369,7 +365,7 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint32_t *
     }
     __syncthreads();
 
-    // per-digit: warp-exclusive offsets, block count, block-exclusive offsets
+    // per-digit: warp-exclusive offsets and the block's count, published at once for later tiles
     const int d = tid;  // kSortThreads == 256 == radix
     uint32_t cnt = 0;
 #pragma unroll
@@ -378,22 +374,32 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint32_t *
         s_whist[ww][d] = cnt;
         cnt += c;
     }
+    uint32_t *my = lookback + (size_t)tile * 256 + d;
+    st_relaxed(my, (tile == 0 ? kFlagPre : kFlagAgg) | cnt);
+    // block-exclusive digit offsets and the pass's digit bases
     uint32_t lb_tot;
     uint32_t hist_d = pass_hist[d];
-    uint32_t excl_local = block_exclusive_scan(cnt, &lb_tot, s_warp);
-    s_excl[d] = excl_local;
+    s_excl[d] = block_exclusive_scan(cnt, &lb_tot, s_warp);
     uint32_t hist_tot;
-    s_dbase[d] = block_exclusive_scan(hist_d, &hist_tot, s_warp);
+    s_dbase[d] = block_exclusive_scan(hist_d, &hist_tot, s_warp);  // its barriers publish s_excl
 
-    // chained look-back over earlier tiles for digit d
-    uint32_t *my = lookback + (size_t)tile * 256 + d;
+    // local scatter by digit into shared memory (the keys leave the registers before the wait)
+#pragma unroll
+    for (int r = 0; r < kSortIPT; ++r) {
+        int64_t i = base + (int64_t)w * (kSortIPT * 32) + r * 32 + lane;
+        if (i < n) {
+            uint32_t dd = (key[r] >> shift) & 255u;
+            uint32_t pos = s_excl[dd] + s_whist[w][dd] + rank[r];
+            s_keys[pos] = key[r];
+            s_vals[pos] = val[r];
+        }
+    }
+
+    // chained look-back over earlier tiles for digit d: kWin of their flags are read at a time
+    // (all tiles start together, so the chain is as long as the tile number over kWin); spin
+    // (bounded) only on a tile that has not published its count yet
     uint32_t prefix = 0;
-    if (tile == 0) {
-        st_relaxed(my, kFlagPre | cnt);
-    } else {
-        st_relaxed(my, kFlagAgg | cnt);
-        // walk back over earlier tiles, reading 8 of their flags at a time; spin
-        // (bounded) only on a tile that has not published its count yet
+    if (tile != 0) {
         constexpr int kWin = 8;
         int64_t t = (int64_t)tile - 1;
         bool done = false, timeout = false;
@@ -403,10 +409,13 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint32_t *
             for (int i = 0; i < kWin; ++i) w[i] = t - i >= 0 ? ld_relaxed(lookback + (size_t)(t - i) * 256 + d) : 0u;
 #pragma unroll
             for (int i = 0; i < kWin; ++i) {
-                if (done) break;
-                if (t - i < 0) { done = true; break; }
+                if (done) continue;
+                if (t - i < 0 || spin_limit < 0) {  // the first tile passed; or the test hook: give up at once
+                    timeout = spin_limit < 0;
+                    done = true;
+                    continue;
+                }
                 uint32_t vv = w[i];
-                if (spin_limit < 0) { timeout = true; done = true; break; }  // test hook: give up at once
                 if ((vv & ~kValMask) == 0u) {
                     const uint32_t *pp = lookback + (size_t)(t - i) * 256 + d;
                     int spin = 0;
@@ -414,7 +423,11 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint32_t *
                         if (++spin > 64) __nanosleep(64);
                         vv = ld_relaxed(pp);
                     }
-                    if ((vv & ~kValMask) == 0u) { timeout = true; done = true; break; }
+                    if ((vv & ~kValMask) == 0u) {
+                        timeout = true;
+                        done = true;
+                        continue;
+                    }
                 }
                 prefix += vv & kValMask;
                 if ((vv & ~kValMask) == kFlagPre) done = true;
@@ -427,18 +440,7 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint32_t *
     s_glob[d] = s_dbase[d] + prefix;
     __syncthreads();
 
-    // local scatter by digit, then coalesced-by-run global writes
-#pragma unroll
-    for (int r = 0; r < kSortIPT; ++r) {
-        int64_t i = base + (int64_t)w * (kSortIPT * 32) + r * 32 + lane;
-        if (i < n) {
-            uint32_t dd = (key[r] >> shift) & 255u;
-            uint32_t pos = s_excl[dd] + s_whist[w][dd] + rank[r];
-            s_keys[pos] = key[r];
-            s_vals[pos] = val[r];
-        }
-    }
-    __syncthreads();
+    // coalesced-by-run global writes
     int tile_n = (int)min((int64_t)kSortTile, n - base);
     for (int i = tid; i < tile_n; i += kSortThreads) {
         uint32_t k = s_keys[i];
