@@ -297,7 +297,7 @@ class FormJob:
         r.forward(self.field)
         fac = r.use_factored(self.W)
         r.loss(self.targets, self.W, self.b, self.w, factored=fac)
-        tuned, _ = autotune.tune_blend(r, self.field, self.mode, factored=fac)
+        tuned, self.tune_ms = autotune.tune_blend(r, self.field, self.mode, factored=fac)
         return tuned
 
     def step(self):
@@ -355,7 +355,8 @@ def run_configs(args, dev, flush):
     features, FP16 colours, 8 keyframes at 1200x680) and the differentiation form (1M
     Gaussians, D=32 FP32, one 640x480 frame, fx=525)."""
     import torch
-    from paper_2603_27781_gb300 import raster, synth
+    from paper_2603_27781_gb300 import _lib as L
+    from paper_2603_27781_gb300 import autotune, raster, synth
     room = synth.make_room(synth.SEED_SCENE)
     loop = synth.keyframe_loop(room=room)
     timing = "one CUDA graph per configuration, replays timed with CUDA events, L2 flushed between replays"
@@ -368,12 +369,24 @@ def run_configs(args, dev, flush):
         job = FormJob(field, cams, frames, dec, dev, WORKLOAD["k"])
         t = job.tune()
         ms = time_graph([job], args.form_steps, flush)
+        # the whole step again with the tuned forward shape scheduled the other way: one block
+        # per tile (the hardware's block scheduler) against resident blocks on a work counter
+        by_schedule = {}
+        for blocks, label in ((L.GS_BWD_BLOCKS_TILE, "one block per tile"),
+                              (L.GS_BLOCKS_QUEUE, "resident blocks, tile queue")):
+            if t.fwd_blocks == blocks:
+                by_schedule[label] = ms
+            elif t.fwd_blocks in (L.GS_BWD_BLOCKS_TILE, L.GS_BLOCKS_QUEUE):
+                job.r.params = dataclasses.replace(t, fwd_blocks=blocks)
+                job.r.prm_c = job.r.params.c()
+                by_schedule[label] = time_graph([job], args.form_steps, flush)
+        job.r.params, job.r.prm_c = t, t.c()
         out[name] = dict(info, frames=len(cams), ms_per_step=ms, frames_per_s=len(cams) * 1000.0 / ms,
                          instances=int(job.r.instances()),
-                         px_per_thread_fwd_bwd=[f"w{t.fwd_px_per_thread}" if t.fwd_blocks == 1 else
-                                                str(t.fwd_px_per_thread),
-                                                f"w{t.bwd_px_per_thread}" if t.bwd_blocks == 1 else
-                                                str(t.bwd_px_per_thread)], timing=timing)
+                         px_per_thread_fwd_bwd=[str(k) for k in autotune.shape_keys(t)],
+                         step_ms_by_forward_schedule=by_schedule,
+                         autotune_fwd_ms={str(k): round(v, 4) for k, v in job.tune_ms["fwd"].items()},
+                         timing=timing)
         del job
         torch.cuda.empty_cache()
 
@@ -409,7 +422,7 @@ def run_forms(args, gs, dec, dev, flush, batch=8):
     form's step graph-captured and its blend launch shape autotuned.  Frames/s =
     frames per step / time per step."""
     import torch
-    from paper_2603_27781_gb300 import raster, synth
+    from paper_2603_27781_gb300 import autotune, raster, synth
     room = synth.make_room(synth.SEED_SCENE)
     loop = synth.keyframe_loop(room=room)
     cams = [synth.camera(WORKLOAD["width"], WORKLOAD["height"], WORKLOAD["fx"], T_cw=loop[i])
@@ -426,9 +439,7 @@ def run_forms(args, gs, dec, dev, flush, batch=8):
              ("batched_f16rgb_bf16feat", lambda: [FormJob(half, cams, frames, dec, dev, k)])]
     for name, make in specs:
         jobs = make()
-        shapes = sorted({(f"w{t.fwd_px_per_thread}" if t.fwd_blocks == 1 else str(t.fwd_px_per_thread),
-                          f"w{t.bwd_px_per_thread}" if t.bwd_blocks == 1 else str(t.bwd_px_per_thread))
-                         for t in (j.tune() for j in jobs)})
+        shapes = sorted({tuple(str(k) for k in autotune.shape_keys(j.tune())) for j in jobs})
         ms = time_graph(jobs, args.form_steps, flush)
         out[name] = {"frames_per_step": batch, "steps_per_graph": len(jobs), "ms_per_step": ms,
                      "frames_per_s": batch * 1000.0 / ms, "ms_per_frame": ms / batch,
@@ -678,10 +689,7 @@ def run_ours(args, rank, world, local_rank):
     r.forward(field)
     r.loss(targets, W, b, w, factored=r.use_factored(W))
     if args.shapes:
-        f_s, b_s = args.shapes.split(",")
-        tuned = dataclasses.replace(r.params, fwd_px_per_thread=int(f_s.lstrip("w")),
-                                    fwd_blocks=1 if f_s.startswith("w") else 2,
-                                    bwd_px_per_thread=int(b_s.lstrip("w")), bwd_blocks=1 if b_s.startswith("w") else 2)
+        tuned = dataclasses.replace(r.params, **autotune.parse_shapes(args.shapes))
         r.params, r.prm_c, tune_ms = tuned, tuned.c(), {}
     else:
         tuned, tune_ms = autotune.tune_blend(r, field, mode, factored=r.use_factored(W))
@@ -786,7 +794,7 @@ def run_ours(args, rank, world, local_rank):
         achieved = fl / (per_stage[dom] * 1e-3) / 1e12
         is_bwd = stages[dom] == "render_bwd"
         kname = ("raster_bwd_warp_kernel" if tuned.bwd_blocks == 1 else "raster_bwd_kernel") if is_bwd \
-            else ("raster_fwd_group_kernel" if tuned.fwd_blocks == 1 else "raster_fwd_kernel")
+            else ("raster_fwd_group_kernel" if tuned.fwd_blocks == L.GS_BWD_BLOCKS_GROUP else "raster_fwd_kernel")
         shape = tuned.bwd_px_per_thread if is_bwd else tuned.fwd_px_per_thread
         roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak, "traffic": captured_traffic(kname, shape, WORKLOAD["d"]),
@@ -893,7 +901,9 @@ def run_ours(args, rank, world, local_rank):
                                   "same step launched eagerly with events between its stages",
                            px_per_thread={"fwd": tuned.fwd_px_per_thread, "bwd": tuned.bwd_px_per_thread},
                            bwd_blocks="one per pixel group" if tuned.bwd_blocks == 1 else "one per 16x16 tile",
-                           fwd_blocks="one per pixel group" if tuned.fwd_blocks == 1 else "one per 16x16 tile",
+                           fwd_blocks={L.GS_BWD_BLOCKS_GROUP: "one per pixel group",
+                                       L.GS_BLOCKS_QUEUE: "resident blocks taking 16x16 tiles from a work counter"
+                                       }.get(tuned.fwd_blocks, "one per 16x16 tile"),
                            autotune_ms={k: {str(n): round(t, 4) for n, t in v.items()} for k, v in tune_ms.items()}),
             "stages_ms": {s: float(t) for s, t in zip(stages, per_stage)},
             "eager_ms_per_step": eager_ms,

@@ -99,8 +99,12 @@ typedef struct {
     /* Block shape of gs_render_fwd (images identical either way; the blend mask
      * too): GS_BWD_BLOCKS_GROUP = one 32-thread block per pixel group
      * (fwd_px_per_thread 1 or 2), which leaves as soon as its pixels are done;
-     * GS_BWD_BLOCKS_TILE = one block per tile; GS_BWD_BLOCKS_DEFAULT (0) = the
-     * library's choice for the launch shape. */
+     * GS_BWD_BLOCKS_TILE = one block per tile; GS_BLOCKS_QUEUE = one block per
+     * tile's worth of threads, but only as many blocks as are resident on the
+     * GPU at once, each taking tiles (in the tile order) from the work counters
+     * gs_binning.queue, which must then not be NULL (else GS_ERR_ARG), until
+     * none is left; GS_BWD_BLOCKS_DEFAULT (0) = the library's choice for the
+     * launch shape. */
     int32_t fwd_blocks;
     /* Where the EWA Jacobian J of Eq. 3 is evaluated (gs_project, gs_project_bwd):
      * GS_JACOBIAN_CLAMPED (0, the default) at (x/z, y/z) clamped to the view
@@ -120,7 +124,7 @@ typedef struct {
     int32_t spin_limit;
 } gs_raster_params;
 
-enum { GS_BWD_BLOCKS_DEFAULT = 0, GS_BWD_BLOCKS_GROUP = 1, GS_BWD_BLOCKS_TILE = 2 };
+enum { GS_BWD_BLOCKS_DEFAULT = 0, GS_BWD_BLOCKS_GROUP = 1, GS_BWD_BLOCKS_TILE = 2, GS_BLOCKS_QUEUE = 3 };
 enum { GS_JACOBIAN_CLAMPED = 0, GS_JACOBIAN_EXACT = 1 };
 
 /* The Semantic Gaussian Field of Eq. 1, structure of arrays.
@@ -165,7 +169,11 @@ typedef struct {
  * keys/vals.  tile_order (optional, device u32 [total tiles]): a permutation
  * of the tiles by decreasing instance count (order within equal counts
  * unspecified), in which gs_render_fwd / gs_render_bwd launch their tiles
- * when it is not NULL; gs_bin_sort writes it whenever it is not NULL. */
+ * when it is not NULL; gs_bin_sort writes it whenever it is not NULL.
+ * queue (optional, device u32 [2]): the work counters of the GS_BLOCKS_QUEUE
+ * forward; gs_bin_sort sets them to 0 whenever queue is not NULL, and every
+ * such launch leaves them 0 when it completes, so launches may repeat.  Two
+ * launches that share a queue must not overlap on the GPU. */
 typedef struct {
     int64_t capacity;
     uint64_t *keys;
@@ -174,6 +182,7 @@ typedef struct {
     int64_t *n_inst;
     int32_t *status;
     uint32_t *tile_order;
+    uint32_t *queue;
 } gs_binning;
 
 /* Rendered images, planar f32 over all views' pixels (P = sum W H):

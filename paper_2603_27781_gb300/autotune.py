@@ -32,11 +32,30 @@ def _time(fn, reps: int, stream) -> float:
     return ev[0].elapsed_time(ev[1]) / reps
 
 
+_PREFIX = {L.GS_BWD_BLOCKS_GROUP: "w", L.GS_BLOCKS_QUEUE: "q"}
+_BLOCKS = {"w": L.GS_BWD_BLOCKS_GROUP, "q": L.GS_BLOCKS_QUEUE}
+
+
+def shape_keys(p: RasterParams):
+    """The (forward, backward) timing keys of the launch shapes of RasterParams p."""
+    key = lambda blocks, np_: _PREFIX[blocks] + str(np_) if blocks in _PREFIX else np_
+    return key(p.fwd_blocks, p.fwd_px_per_thread), key(p.bwd_blocks, p.bwd_px_per_thread)
+
+
+def parse_shapes(text: str) -> dict:
+    """RasterParams fields for "fwd,bwd" shape keys such as "2,w2" or "q2,w2"."""
+    f_s, b_s = text.split(",")
+    blocks = lambda k: _BLOCKS.get(k[0], L.GS_BWD_BLOCKS_TILE)
+    return dict(fwd_px_per_thread=int(f_s.lstrip("wq")), fwd_blocks=blocks(f_s),
+                bwd_px_per_thread=int(b_s.lstrip("wq")), bwd_blocks=blocks(b_s))
+
+
 def tune_blend(r: Renderer, field, grad_mode: int = L.GS_GRAD_MAP, reps: int = 5, verbose: bool = False,
                factored: bool = False):
     """Returns (RasterParams with the fastest fwd/bwd launch shapes, timings in ms).  Shapes
-    are keyed by pixels per thread (one block per tile) and "w1", "w2" (one 32-thread block
-    per pixel group).
+    are keyed by pixels per thread (one block per tile), "w1", "w2" (one 32-thread block
+    per pixel group) and, for the forward, "q1", "q2", "q4" (resident blocks taking tiles
+    from a work counter).
 
     The renderer's image gradients (r.g_*) must hold the gradients to time the
     backward with (e.g. after a loss call; with factored, a factored loss call, and only the
@@ -51,6 +70,7 @@ def tune_blend(r: Renderer, field, grad_mode: int = L.GS_GRAD_MAP, reps: int = 5
     fshapes = {np_: dict(fwd_px_per_thread=np_, fwd_blocks=L.GS_BWD_BLOCKS_TILE) for np_ in CANDIDATES}
     fshapes.update({f"w{np_}": dict(fwd_px_per_thread=np_, fwd_blocks=L.GS_BWD_BLOCKS_GROUP)
                     for np_ in WARP_CANDIDATES})
+    fshapes.update({f"q{np_}": dict(fwd_px_per_thread=np_, fwd_blocks=L.GS_BLOCKS_QUEUE) for np_ in CANDIDATES})
     for key, shape in fshapes.items():
         r.prm_c = dataclasses.replace(base, **shape).c()
         try:

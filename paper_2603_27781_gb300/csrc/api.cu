@@ -59,7 +59,7 @@ bool make_params(const gs_raster_params *p, Params *out) {
     if (p->bwd_blocks < GS_BWD_BLOCKS_DEFAULT || p->bwd_blocks > GS_BWD_BLOCKS_TILE) return false;
     out->bwd_blocks = p->bwd_blocks;
     out->bwd_warp = false;
-    if (p->fwd_blocks < GS_BWD_BLOCKS_DEFAULT || p->fwd_blocks > GS_BWD_BLOCKS_TILE) return false;
+    if (p->fwd_blocks < GS_BWD_BLOCKS_DEFAULT || p->fwd_blocks > GS_BLOCKS_QUEUE) return false;
     out->fwd_blocks = p->fwd_blocks;
     out->fwd_group = false;
     if (p->jacobian != GS_JACOBIAN_CLAMPED && p->jacobian != GS_JACOBIAN_EXACT) return false;

@@ -38,6 +38,7 @@ struct Params {
     bool bwd_warp;       // resolved: map-mode backward as one 32-thread block per pixel group
     int fwd_blocks;      // forward block shape (GS_BWD_BLOCKS_*)
     bool fwd_group;      // resolved: forward as one 32-thread block per pixel group
+    bool fwd_queue;      // resolved: forward as resident CTAs taking tiles from a work counter
     bool exact_jacobian; // GS_JACOBIAN_EXACT: J of Eq. 3 at the unclamped (x/z, y/z)
     int spin_limit;      // polls of a bounded wait before it gives up (< 0: at once)
 };

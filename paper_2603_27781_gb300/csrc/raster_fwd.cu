@@ -18,13 +18,14 @@ constexpr int fwd_min_blocks(int D, int NP) {
     return NP == 1 ? (D == 0 ? 8 : D <= 4 ? 6 : D <= 16 ? 5 : 3) : NP == 2 ? (D <= 16 ? 6 : 4) : 6;
 }
 
+// One 16x16 tile gt of the blend, by the whole CTA (every exit is uniform over the CTA).
 template <int D, int NP, typename RT, typename FT>
-__global__ void __launch_bounds__(Shape<NP>::THREADS, fwd_min_blocks(D, NP)) raster_fwd_kernel(
-    ViewTable vt, Params prm, const float4 *__restrict__ uvdo, const float2 *__restrict__ uv_lo,
+__device__ __forceinline__ void fwd_tile(
+    const ViewTable &vt, const Params &prm, const float4 *__restrict__ uvdo, const float2 *__restrict__ uv_lo,
     const float4 *__restrict__ conic, const RT *__restrict__ rgb, const FT *__restrict__ feat,
     const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges, int64_t P, float *o_rgb, float *o_depth,
     float *o_sil, float *o_feat, float *o_T, int32_t *o_nc, int32_t *o_nb, uint32_t *bmask, int64_t bm_stride,
-    const uint32_t *__restrict__ order, int32_t *status, int64_t capacity) {
+    const int gt, int32_t *status, int64_t capacity) {
     using SH = Shape<NP, true>;  // horizontal pixel pairs
     constexpr int NT = SH::THREADS;
     constexpr int NL = SH::PIX_GROUPS ? NP : 1;  // mask bit registers per thread
@@ -34,8 +35,6 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS, fwd_min_blocks(D, NP)) ras
     __shared__ float4 s_rgbd[kBatch];
     __shared__ float4 s_feat[kBatch * (D4 > 0 ? D4 : 1)];
 
-    if (binning_failed(status)) return;  // the binning overflowed or gave up: render nothing
-    const int gt = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
     if (gt < 0 || gt >= vt.tile_off[vt.n_views]) return;  // not a permutation of the tiles: leave the tile
     const int v = view_of_tile(vt, gt);
     const int t = gt - vt.tile_off[v];
@@ -197,6 +196,45 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS, fwd_min_blocks(D, NP)) ras
     }
 }
 
+// With QUEUE, the grid is as many CTAs as fit on the GPU at once and each takes tiles, in the
+// tile order, from the work counter queue[0] until none is left; the last CTA to finish
+// (counted in queue[1]) sets both counters back to 0 for the next launch.  Nothing waits.
+template <int D, int NP, typename RT, typename FT, bool QUEUE>
+__global__ void __launch_bounds__(Shape<NP>::THREADS, fwd_min_blocks(D, NP)) raster_fwd_kernel(
+    ViewTable vt, Params prm, const float4 *__restrict__ uvdo, const float2 *__restrict__ uv_lo,
+    const float4 *__restrict__ conic, const RT *__restrict__ rgb, const FT *__restrict__ feat,
+    const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges, int64_t P, float *o_rgb, float *o_depth,
+    float *o_sil, float *o_feat, float *o_T, int32_t *o_nc, int32_t *o_nb, uint32_t *bmask, int64_t bm_stride,
+    const uint32_t *__restrict__ order, int32_t *status, int64_t capacity, uint32_t *queue) {
+    const int n_tiles = vt.tile_off[vt.n_views];
+    const bool failed = binning_failed(status);  // the binning overflowed or gave up: render nothing
+    if constexpr (QUEUE) {
+        __shared__ int s_idx;
+        for (;;) {
+            __syncthreads();  // the previous tile's reads of shared memory and s_idx are done
+            if (threadIdx.x == 0) s_idx = failed ? n_tiles : (int)atomicAdd(queue, 1u);
+            __syncthreads();
+            const int idx = s_idx;
+            if (idx >= n_tiles) break;
+            fwd_tile<D, NP, RT, FT>(vt, prm, uvdo, uv_lo, conic, rgb, feat, vals, ranges, P, o_rgb, o_depth, o_sil,
+                                    o_feat, o_T, o_nc, o_nb, bmask, bm_stride, order ? (int)order[idx] : idx,
+                                    status, capacity);
+        }
+        if (threadIdx.x == 0) {
+            __threadfence();
+            if (atomicAdd(queue + 1, 1u) == gridDim.x - 1) {  // every CTA has taken its last item
+                queue[0] = 0u;
+                queue[1] = 0u;
+            }
+        }
+    } else {
+        if (failed) return;
+        fwd_tile<D, NP, RT, FT>(vt, prm, uvdo, uv_lo, conic, rgb, feat, vals, ranges, P, o_rgb, o_depth, o_sil,
+                                o_feat, o_T, o_nc, o_nb, bmask, bm_stride,
+                                order ? (int)order[blockIdx.x] : (int)blockIdx.x, status, capacity);
+    }
+}
+
 // The same blend with one 32-thread block per pixel group (an 8x4 group with one pixel
 // per thread, an 8x8 block with two): the group stages the tile's splats 32 at a time in
 // its own shared memory, so it never waits at a barrier for the tile's other groups, and
@@ -212,7 +250,7 @@ __global__ void __launch_bounds__(32, fwd_group_min_blocks(D, NP)) raster_fwd_gr
     const float4 *__restrict__ conic, const RT *__restrict__ rgb, const FT *__restrict__ feat,
     const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges, int64_t P, float *o_rgb, float *o_depth,
     float *o_sil, float *o_feat, float *o_T, int32_t *o_nc, int32_t *o_nb, uint32_t *bmask, int64_t bm_stride,
-    const uint32_t *__restrict__ order, int32_t *status, int64_t capacity) {
+    const uint32_t *__restrict__ order, int32_t *status, int64_t capacity, uint32_t * /*queue*/) {
     using SH = Shape<NP, true>;  // horizontal pixel pairs
     constexpr int D4 = D / 4, DD = D > 0 ? D : 1;
     constexpr int NL = SH::PIX_GROUPS ? NP : 1;  // mask bit registers per thread
@@ -379,7 +417,7 @@ gs_status launch(const ViewTable &vt, const Params &prm, const gs_gaussians *g, 
             reinterpret_cast<const float4 *>(proj->conic), static_cast<const RT *>(g->rgb),
             static_cast<const FT *>(g->feat), bins->vals, bins->ranges, P, out->rgb, out->depth, out->sil,
             out->feat, out->T_final, out->n_contrib, out->n_blended, out->blend_mask, bins->capacity / 32 + 1,
-            bins->tile_order, bins->status, bins->capacity);
+            bins->tile_order, bins->status, bins->capacity, bins->queue);
     };
     if constexpr (NP <= 2) {
         if (prm.fwd_group) {
@@ -387,7 +425,22 @@ gs_status launch(const ViewTable &vt, const Params &prm, const gs_gaussians *g, 
             return last_launch();
         }
     }
-    args(raster_fwd_kernel<D, NP, RT, FT>, tiles, Shape<NP>::THREADS);
+    if (prm.fwd_queue) {
+        // one wave: as many CTAs as are resident at once
+        static int res = 0;  // this kernel instance: SMs x resident CTAs per SM
+        if (res == 0) {
+            int dev = 0, sms = 0, per_sm = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess ||
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raster_fwd_kernel<D, NP, RT, FT, true>,
+                                                              Shape<NP>::THREADS, 0) != cudaSuccess)
+                return GS_ERR_CUDA;
+            res = sms * (per_sm > 0 ? per_sm : 1);
+        }
+        args(raster_fwd_kernel<D, NP, RT, FT, true>, tiles < res ? tiles : res, Shape<NP>::THREADS);
+        return last_launch();
+    }
+    args(raster_fwd_kernel<D, NP, RT, FT, false>, tiles, Shape<NP>::THREADS);
     return last_launch();
 }
 
@@ -437,7 +490,9 @@ extern "C" gs_status gs_render_fwd(const gs_gaussians *g, const gs_projected *pr
     }
     const int np = prm.fwd_np ? prm.fwd_np : default_fwd_np(g->feat_dim);
     prm.fwd_group = prm.fwd_blocks == GS_BWD_BLOCKS_GROUP;
+    prm.fwd_queue = prm.fwd_blocks == GS_BLOCKS_QUEUE;
     if (prm.fwd_group && np > 2) return GS_ERR_UNSUPPORTED;
+    if (prm.fwd_queue && !bins->queue) return GS_ERR_ARG;
     if (g->rgb_dtype == GS_F16) {
         if (g->feat_dim == 16) return by_np<16, __half, __nv_bfloat16>(np, vt, prm, g, proj, bins, out, st);
         return by_np<32, __half, __nv_bfloat16>(np, vt, prm, g, proj, bins, out, st);

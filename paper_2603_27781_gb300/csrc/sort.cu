@@ -64,12 +64,12 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t *t
 
 // ------------------------------------------------------------ state of a call
 // Zeroes what a binning accumulates into: the ranges, the counters, the instance count and
-// status word, the tile counts, the digit histograms and the look-back flags (the last and
-// largest in 16-byte stores over the whole grid).
+// status word, the queued forward's work counters, the tile counts, the digit histograms and
+// the look-back flags (the last and largest in 16-byte stores over the whole grid).
 __global__ void __launch_bounds__(256) bin_init_kernel(uint32_t *ranges, int64_t n_ranges, uint32_t *counters,
                                                        int64_t *n_inst, int32_t *status, uint32_t *tile_counts,
                                                        int64_t n_tiles, uint32_t *hist, uint4 *lookback,
-                                                       int64_t n_lookback4) {
+                                                       int64_t n_lookback4, uint32_t *queue) {
     pdl_wait();
     pdl_trigger();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -82,6 +82,7 @@ __global__ void __launch_bounds__(256) bin_init_kernel(uint32_t *ranges, int64_t
     if (i0 == 0) {
         *n_inst = 0;
         *status = 0;
+        if (queue) queue[0] = queue[1] = 0u;
     }
 }
 
@@ -617,7 +618,8 @@ extern "C" gs_status gs_bin_sort(int64_t n, const gs_projected *proj, const gs_c
     const int64_t n_lb4 = vn > 0 ? 64 * ((int64_t)4 * L.lb_tiles_depth + (int64_t)3 * L.lb_tiles_inst) : 0;
     const int init_grid = (int)std::max<int64_t>(1, std::min<int64_t>((n_lb4 + 255) / 256, 1216));
     if ((s = launch_pdl(bin_init_kernel, init_grid, 256, 0, st, out->ranges, 2 * total_tiles, counters, out->n_inst,
-                        out->status, tile_counts, total_tiles, hist, reinterpret_cast<uint4 *>(lookback), n_lb4)))
+                        out->status, tile_counts, total_tiles, hist, reinterpret_cast<uint4 *>(lookback), n_lb4,
+                        out->queue)))
         return s;
     if (vn == 0) return write_ranges_order(tile_counts, out, total_tiles, st);
 

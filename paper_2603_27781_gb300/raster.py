@@ -146,6 +146,7 @@ class Renderer:
         self.ranges = torch.zeros(2 * self.n_tiles, dtype=i32, device=dev)
         self.tile_order = torch.zeros(max(self.n_tiles, 1), dtype=i32, device=dev)
         self.use_tile_order = True      # blend tiles launched longest first
+        self.queue = torch.zeros(2, dtype=i32, device=dev)  # work counters of the queued forward
         self.n_inst = torch.zeros(1, dtype=torch.int64, device=dev)
         self.status_word = torch.zeros(1, dtype=i32, device=dev)
         ws_bytes = L.library().gs_workspace_size(n, V, self.cams_c, capacity, feat_dim)
@@ -252,7 +253,7 @@ class Renderer:
     def binning_c(self, want_keys=False):
         return L.gs_binning(self.capacity, _p(self.keys) if want_keys else None, _p(self.vals), _p(self.ranges),
                             _p(self.n_inst), _p(self.status_word),
-                            _p(self.tile_order) if self.use_tile_order else None)
+                            _p(self.tile_order) if self.use_tile_order else None, _p(self.queue))
 
     def images_c(self):
         return L.gs_images(_p(self.img_rgb), _p(self.img_depth), _p(self.img_sil),

@@ -6,6 +6,9 @@ Binning and sort are compared bit for bit; floating-point outputs within the
 stated tolerances, excluding (and counting) pixels where a threshold decision is
 within rounding distance in the oracle.
 """
+import ctypes
+import dataclasses
+
 import numpy as np
 import pytest
 import torch
@@ -296,6 +299,42 @@ def test_tile_order_is_a_longest_first_permutation_and_changes_nothing():
         C.assert_grad_close("ordered", a.cpu().numpy(), b.cpu().numpy(), 1e-5)
 
 
+def test_queued_forward_matches_one_block_per_tile_and_resets_its_counters():
+    """Two views: resident blocks taking tiles from the work counter render the same images
+    and blend mask as one block per tile, for every pixels-per-thread shape, in the tile
+    order and in index order; the counters are back at 0 after each launch, so repeated
+    launches after one binning agree; a NULL counter pointer is refused."""
+    gs, cam, room = C.room_case(20000, 16, 330, 190, 165.0)
+    cams = [cam, synth.camera(100, 70, 60.0, T_cw=synth.keyframe_loop(8, room=room)[3])]
+    base = C.params_pair()[0]
+    field, r = C.gpu_forward(gs, cams, base)
+    names = ("img_rgb", "img_depth", "img_sil", "img_feat", "img_T", "img_nc", "blend_mask")
+    for use_order in (True, False):
+        r.use_tile_order = use_order
+        for np_ in (1, 2, 4):
+            outs = []
+            for blocks in (L.GS_BWD_BLOCKS_TILE, L.GS_BLOCKS_QUEUE, L.GS_BLOCKS_QUEUE):
+                r.params = dataclasses.replace(base, fwd_px_per_thread=np_, fwd_blocks=blocks)
+                r.prm_c = r.params.c()
+                r.project(field)
+                r.bin_sort()
+                for _ in range(2 if blocks == L.GS_BLOCKS_QUEUE else 1):
+                    r.render_fwd(field)
+                    torch.cuda.synchronize()
+                    assert r.queue.cpu().tolist() == [0, 0]
+                outs.append([getattr(r, n).clone() for n in names])
+            for other in outs[1:]:
+                for n, a, b in zip(names, outs[0], other):
+                    assert torch.equal(a, b), (use_order, np_, n)
+    r.params = dataclasses.replace(base, fwd_blocks=L.GS_BLOCKS_QUEUE)
+    r.prm_c = r.params.c()
+    b = r.binning_c()
+    b.queue = None
+    status = L.gs_render_fwd(ctypes.byref(field.c()), ctypes.byref(r.projected_c()), ctypes.byref(b), r.cams_c,
+                             r.n_views, ctypes.byref(r.prm_c), ctypes.byref(r.images_c()), None)
+    assert status == L.GS_ERR_ARG
+
+
 def test_autotuner_picks_a_supported_shape():
     from paper_2603_27781_gb300 import autotune
     gs, cam, _ = C.room_case(20000, 16, 330, 190, 165.0)
@@ -303,11 +342,11 @@ def test_autotuner_picks_a_supported_shape():
     g = C.random_image_grads(r.P, 16, 6)
     r.g_rgb.copy_(torch.as_tensor(g["rgb"])); r.g_feat.copy_(torch.as_tensor(g["feat"]))
     tuned, t = autotune.tune_blend(r, field, L.GS_GRAD_MAP)
-    assert set(t["fwd"]) == {1, 2, 4, "w1", "w2"} and set(t["bwd"]) == {1, 2, 4, "w1", "w2"}
-    assert (f"w{tuned.fwd_px_per_thread}" if tuned.fwd_blocks == L.GS_BWD_BLOCKS_GROUP
-            else tuned.fwd_px_per_thread) in t["fwd"]
-    assert (f"w{tuned.bwd_px_per_thread}" if tuned.bwd_blocks == L.GS_BWD_BLOCKS_GROUP
-            else tuned.bwd_px_per_thread) in t["bwd"]
+    assert set(t["fwd"]) == {1, 2, 4, "w1", "w2", "q1", "q2", "q4"} and set(t["bwd"]) == {1, 2, 4, "w1", "w2"}
+    kf, kb = autotune.shape_keys(tuned)
+    assert kf in t["fwd"] and kb in t["bwd"]
+    assert autotune.parse_shapes(f"{kf},{kb}") == {k: getattr(tuned, k) for k in (
+        "fwd_px_per_thread", "fwd_blocks", "bwd_px_per_thread", "bwd_blocks")}
 
 
 def test_render_bwd_multiview_sums_views():
