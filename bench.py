@@ -384,8 +384,10 @@ def run_configs(args, dev, flush):
         out[name] = dict(info, frames=len(cams), ms_per_step=ms, frames_per_s=len(cams) * 1000.0 / ms,
                          instances=int(job.r.instances()),
                          px_per_thread_fwd_bwd=[str(k) for k in autotune.shape_keys(t)],
-                         step_ms_by_forward_schedule=by_schedule,
+                         fwd_batch=t.fwd_batch or 128, step_ms_by_forward_schedule=by_schedule,
                          autotune_fwd_ms={str(k): round(v, 4) for k, v in job.tune_ms["fwd"].items()},
+                         autotune_fwd_batch_ms={str(k): round(v, 4)
+                                                for k, v in job.tune_ms.get("fwd_batch", {}).items()},
                          timing=timing)
         del job
         torch.cuda.empty_cache()
@@ -900,6 +902,7 @@ def run_ours(args, rank, world, local_rank):
                            launch="each timed step one replay of a captured CUDA graph; stages_ms from the "
                                   "same step launched eagerly with events between its stages",
                            px_per_thread={"fwd": tuned.fwd_px_per_thread, "bwd": tuned.bwd_px_per_thread},
+                           fwd_batch=tuned.fwd_batch or 128,
                            bwd_blocks="one per pixel group" if tuned.bwd_blocks == 1 else "one per 16x16 tile",
                            fwd_blocks={L.GS_BWD_BLOCKS_GROUP: "one per pixel group",
                                        L.GS_BLOCKS_QUEUE: "resident blocks taking 16x16 tiles from a work counter"

@@ -122,6 +122,12 @@ typedef struct {
      * looks at (a test hook: gs_bin_sort then reports GS_ERR_TIMEOUT whenever a
      * radix pass has more than one block of 2048 keys). */
     int32_t spin_limit;
+    /* Splats the per-tile forward (fwd_blocks GS_BWD_BLOCKS_TILE or
+     * GS_BLOCKS_QUEUE) stages in shared memory per round: 64, 128 or 256
+     * (0 = 128); other values return GS_ERR_ARG.  64 and 256 are built for two
+     * pixels per thread at feature dims 16 and 32 (else GS_ERR_UNSUPPORTED).
+     * Results do not depend on it. */
+    int32_t fwd_batch;
 } gs_raster_params;
 
 enum { GS_BWD_BLOCKS_DEFAULT = 0, GS_BWD_BLOCKS_GROUP = 1, GS_BWD_BLOCKS_TILE = 2, GS_BLOCKS_QUEUE = 3 };

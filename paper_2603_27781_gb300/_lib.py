@@ -31,7 +31,7 @@ class gs_raster_params(Structure):
                 ("z_near", c_float), ("lowpass", c_float), ("radius_sigma", c_float), ("bg_rgb", c_float * 3),
                 ("fwd_px_per_thread", c_int32), ("bwd_px_per_thread", c_int32),
                 ("bwd_blocks", c_int32), ("fwd_blocks", c_int32), ("jacobian", c_int32),
-                ("spin_limit", c_int32)]
+                ("spin_limit", c_int32), ("fwd_batch", c_int32)]
 
 
 class gs_gaussians(Structure):

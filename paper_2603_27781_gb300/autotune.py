@@ -19,6 +19,7 @@ from .raster import RasterParams, Renderer
 
 CANDIDATES = (1, 2, 4)
 WARP_CANDIDATES = (1, 2)   # one 32-thread block per pixel group (fwd_blocks / bwd_blocks = 1)
+BATCH_CANDIDATES = (64, 128, 256)  # splats staged per round by the per-tile forward
 
 
 def _time(fn, reps: int, stream) -> float:
@@ -43,11 +44,16 @@ def shape_keys(p: RasterParams):
 
 
 def parse_shapes(text: str) -> dict:
-    """RasterParams fields for "fwd,bwd" shape keys such as "2,w2" or "q2,w2"."""
+    """RasterParams fields for "fwd,bwd" shape keys such as "2,w2", "q2,w2" or, with the
+    forward's staged batch, "2@64,w2"."""
     f_s, b_s = text.split(",")
+    f_s, _, batch = f_s.partition("@")
     blocks = lambda k: _BLOCKS.get(k[0], L.GS_BWD_BLOCKS_TILE)
-    return dict(fwd_px_per_thread=int(f_s.lstrip("wq")), fwd_blocks=blocks(f_s),
-                bwd_px_per_thread=int(b_s.lstrip("wq")), bwd_blocks=blocks(b_s))
+    out = dict(fwd_px_per_thread=int(f_s.lstrip("wq")), fwd_blocks=blocks(f_s),
+               bwd_px_per_thread=int(b_s.lstrip("wq")), bwd_blocks=blocks(b_s))
+    if batch:
+        out["fwd_batch"] = int(batch)
+    return out
 
 
 def tune_blend(r: Renderer, field, grad_mode: int = L.GS_GRAD_MAP, reps: int = 5, verbose: bool = False,
@@ -55,7 +61,8 @@ def tune_blend(r: Renderer, field, grad_mode: int = L.GS_GRAD_MAP, reps: int = 5
     """Returns (RasterParams with the fastest fwd/bwd launch shapes, timings in ms).  Shapes
     are keyed by pixels per thread (one block per tile), "w1", "w2" (one 32-thread block
     per pixel group) and, for the forward, "q1", "q2", "q4" (resident blocks taking tiles
-    from a work counter).
+    from a work counter); for a per-tile forward the splats it stages per round are then
+    timed at 64, 128 and 256 (timings["fwd_batch"]).
 
     The renderer's image gradients (r.g_*) must hold the gradients to time the
     backward with (e.g. after a loss call; with factored, a factored loss call, and only the
@@ -79,7 +86,19 @@ def tune_blend(r: Renderer, field, grad_mode: int = L.GS_GRAD_MAP, reps: int = 5
             if e.status != L.GS_ERR_UNSUPPORTED:
                 raise
     best_f = min(timings["fwd"], key=timings["fwd"].get)
-    fwd = fshapes[best_f]
+    fwd = dict(fshapes[best_f])
+    if fwd["fwd_blocks"] != L.GS_BWD_BLOCKS_GROUP:
+        # the splats staged per round by the per-tile forward, for the chosen shape ("2@64": shape 2, 64)
+        timings["fwd_batch"] = {128: timings["fwd"][best_f]}
+        for batch in BATCH_CANDIDATES:
+            if batch != 128:
+                r.prm_c = dataclasses.replace(base, **fwd, fwd_batch=batch).c()
+                try:
+                    timings["fwd_batch"][batch] = _time(lambda: r.render_fwd(field), reps, stream)
+                except L.GsError as e:  # not built for this shape
+                    if e.status != L.GS_ERR_UNSUPPORTED:
+                        raise
+        fwd["fwd_batch"] = min(timings["fwd_batch"], key=timings["fwd_batch"].get)
     r.prm_c = dataclasses.replace(base, **fwd).c()
     r.render_fwd(field)
     shapes = {np_: dict(bwd_px_per_thread=np_, bwd_blocks=L.GS_BWD_BLOCKS_TILE) for np_ in CANDIDATES}

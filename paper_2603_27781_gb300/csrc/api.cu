@@ -65,6 +65,8 @@ bool make_params(const gs_raster_params *p, Params *out) {
     if (p->jacobian != GS_JACOBIAN_CLAMPED && p->jacobian != GS_JACOBIAN_EXACT) return false;
     out->exact_jacobian = p->jacobian == GS_JACOBIAN_EXACT;
     out->spin_limit = p->spin_limit == 0 ? kDefaultSpinLimit : (p->spin_limit < 0 ? -1 : p->spin_limit);
+    if (p->fwd_batch != 0 && p->fwd_batch != 64 && p->fwd_batch != 128 && p->fwd_batch != 256) return false;
+    out->fwd_batch = p->fwd_batch ? p->fwd_batch : 128;
     return true;
 }
 

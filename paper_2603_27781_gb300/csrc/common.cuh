@@ -41,6 +41,7 @@ struct Params {
     bool fwd_queue;      // resolved: forward as resident CTAs taking tiles from a work counter
     bool exact_jacobian; // GS_JACOBIAN_EXACT: J of Eq. 3 at the unclamped (x/z, y/z)
     int spin_limit;      // polls of a bounded wait before it gives up (< 0: at once)
+    int fwd_batch;       // splats staged per round by the per-tile forward (64, 128 or 256)
 };
 
 constexpr int kDefaultSpinLimit = 1 << 22;

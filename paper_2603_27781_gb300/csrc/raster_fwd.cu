@@ -6,6 +6,8 @@
 // rest front to back and stops at the T_min threshold; the CTA leaves as soon
 // as all of its pixels are done.  With a blend mask, each warp also records, per
 // 8x4 pixel group and 32-instance word, which splats any pixel of it blended.
+#include <type_traits>
+
 #include "raster.cuh"
 
 namespace gs {
@@ -18,8 +20,9 @@ constexpr int fwd_min_blocks(int D, int NP) {
     return NP == 1 ? (D == 0 ? 8 : D <= 4 ? 6 : D <= 16 ? 5 : 3) : NP == 2 ? (D <= 16 ? 6 : 4) : 6;
 }
 
-// One 16x16 tile gt of the blend, by the whole CTA (every exit is uniform over the CTA).
-template <int D, int NP, typename RT, typename FT>
+// One 16x16 tile gt of the blend, by the whole CTA (every exit is uniform over the CTA), staging
+// BATCH splats per round.
+template <int D, int NP, typename RT, typename FT, int BATCH>
 __device__ __forceinline__ void fwd_tile(
     const ViewTable &vt, const Params &prm, const float4 *__restrict__ uvdo, const float2 *__restrict__ uv_lo,
     const float4 *__restrict__ conic, const RT *__restrict__ rgb, const FT *__restrict__ feat,
@@ -30,10 +33,12 @@ __device__ __forceinline__ void fwd_tile(
     constexpr int NT = SH::THREADS;
     constexpr int NL = SH::PIX_GROUPS ? NP : 1;  // mask bit registers per thread
     constexpr int D4 = D / 4, DD = D > 0 ? D : 1;
-    __shared__ SplatGeo s_geo[kBatch];
-    __shared__ float2 s_ext[kBatch];
-    __shared__ float4 s_rgbd[kBatch];
-    __shared__ float4 s_feat[kBatch * (D4 > 0 ? D4 : 1)];
+    // the batch's records: geometry, culling extents, colour and depth, features
+    constexpr int batch = BATCH;
+    __shared__ SplatGeo s_geo[BATCH];
+    __shared__ float2 s_ext[BATCH];
+    __shared__ float4 s_rgbd[BATCH];
+    __shared__ float4 s_feat[BATCH * (D4 > 0 ? D4 : 1)];
 
     if (gt < 0 || gt >= vt.tile_off[vt.n_views]) return;  // not a permutation of the tiles: leave the tile
     const int v = view_of_tile(vt, gt);
@@ -90,9 +95,9 @@ __device__ __forceinline__ void fwd_tile(
     bool finished = false;
     // every warp stays in the batch loop (it stages splats and meets the CTA
     // barriers); a warp whose pixels are all done only skips the splat loop
-    for (uint32_t b0 = start & ~31u; b0 < end; b0 += kBatch) {
+    for (uint32_t b0 = start & ~31u; b0 < end; b0 += batch) {
         if (__syncthreads_count(!all_done()) == 0) break;
-        for (int i = tid; i < kBatch; i += NT) {
+        for (int i = tid; i < batch; i += NT) {
             const uint32_t j = b0 + i;
             if (j >= start && j < end) {
                 const uint32_t item = checked_item(vals[j], voff, vt.n, status);
@@ -108,7 +113,7 @@ __device__ __forceinline__ void fwd_tile(
         }
         __syncthreads();
         const int k_lo = b0 < start ? (int)(start - b0) : 0;
-        const int nb = min((uint32_t)kBatch, end - b0);
+        const int nb = min((uint32_t)batch, end - b0);
         for (int c0 = k_lo & ~31; c0 < nb && !finished; c0 += 32) {
             uint32_t lbits[NL];
 #pragma unroll
@@ -199,7 +204,7 @@ __device__ __forceinline__ void fwd_tile(
 // With QUEUE, the grid is as many CTAs as fit on the GPU at once and each takes tiles, in the
 // tile order, from the work counter queue[0] until none is left; the last CTA to finish
 // (counted in queue[1]) sets both counters back to 0 for the next launch.  Nothing waits.
-template <int D, int NP, typename RT, typename FT, bool QUEUE>
+template <int D, int NP, typename RT, typename FT, bool QUEUE, int BATCH>
 __global__ void __launch_bounds__(Shape<NP>::THREADS, fwd_min_blocks(D, NP)) raster_fwd_kernel(
     ViewTable vt, Params prm, const float4 *__restrict__ uvdo, const float2 *__restrict__ uv_lo,
     const float4 *__restrict__ conic, const RT *__restrict__ rgb, const FT *__restrict__ feat,
@@ -216,7 +221,7 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS, fwd_min_blocks(D, NP)) ras
             __syncthreads();
             const int idx = s_idx;
             if (idx >= n_tiles) break;
-            fwd_tile<D, NP, RT, FT>(vt, prm, uvdo, uv_lo, conic, rgb, feat, vals, ranges, P, o_rgb, o_depth, o_sil,
+            fwd_tile<D, NP, RT, FT, BATCH>(vt, prm, uvdo, uv_lo, conic, rgb, feat, vals, ranges, P, o_rgb, o_depth, o_sil,
                                     o_feat, o_T, o_nc, o_nb, bmask, bm_stride, order ? (int)order[idx] : idx,
                                     status, capacity);
         }
@@ -229,7 +234,7 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS, fwd_min_blocks(D, NP)) ras
         }
     } else {
         if (failed) return;
-        fwd_tile<D, NP, RT, FT>(vt, prm, uvdo, uv_lo, conic, rgb, feat, vals, ranges, P, o_rgb, o_depth, o_sil,
+        fwd_tile<D, NP, RT, FT, BATCH>(vt, prm, uvdo, uv_lo, conic, rgb, feat, vals, ranges, P, o_rgb, o_depth, o_sil,
                                 o_feat, o_T, o_nc, o_nb, bmask, bm_stride,
                                 order ? (int)order[blockIdx.x] : (int)blockIdx.x, status, capacity);
     }
@@ -411,8 +416,8 @@ gs_status launch(const ViewTable &vt, const Params &prm, const gs_gaussians *g, 
                  const gs_binning *bins, gs_images *out, cudaStream_t st) {
     const int tiles = vt.tile_off[vt.n_views];
     const int64_t P = vt.pix_off[vt.n_views];
-    auto args = [&](auto kern, int blocks, int threads) {
-        kern<<<blocks, threads, 0, st>>>(
+    auto args = [&](auto kern, int blocks, int threads, size_t smem) {
+        kern<<<blocks, threads, smem, st>>>(
             vt, prm, reinterpret_cast<const float4 *>(proj->uvdo), reinterpret_cast<const float2 *>(proj->uv_lo),
             reinterpret_cast<const float4 *>(proj->conic), static_cast<const RT *>(g->rgb),
             static_cast<const FT *>(g->feat), bins->vals, bins->ranges, P, out->rgb, out->depth, out->sil,
@@ -421,27 +426,38 @@ gs_status launch(const ViewTable &vt, const Params &prm, const gs_gaussians *g, 
     };
     if constexpr (NP <= 2) {
         if (prm.fwd_group) {
-            args(raster_fwd_group_kernel<D, NP, RT, FT>, tiles * Shape<NP>::WARPS, 32);
+            args(raster_fwd_group_kernel<D, NP, RT, FT>, tiles * Shape<NP>::WARPS, 32, 0);
             return last_launch();
         }
     }
-    if (prm.fwd_queue) {
-        // one wave: as many CTAs as are resident at once
-        static int res = 0;  // this kernel instance: SMs x resident CTAs per SM
-        if (res == 0) {
-            int dev = 0, sms = 0, per_sm = 0;
-            if (cudaGetDevice(&dev) != cudaSuccess ||
-                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raster_fwd_kernel<D, NP, RT, FT, true>,
-                                                              Shape<NP>::THREADS, 0) != cudaSuccess)
-                return GS_ERR_CUDA;
-            res = sms * (per_sm > 0 ? per_sm : 1);
+    // the per-tile forward with BATCH splats staged per round; batches other than 128 are built
+    // for the two-pixel shape at feature widths 16 and 32
+    auto per_tile = [&](auto batch_c) -> gs_status {
+        constexpr int B = decltype(batch_c)::value;
+        if (prm.fwd_queue) {
+            // one wave: as many CTAs as are resident at once
+            static int res = 0;  // this kernel instance: SMs x resident CTAs per SM
+            if (res == 0) {
+                int dev = 0, sms = 0, per_sm = 0;
+                if (cudaGetDevice(&dev) != cudaSuccess ||
+                    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raster_fwd_kernel<D, NP, RT, FT, true, B>,
+                                                                  Shape<NP>::THREADS, 0) != cudaSuccess)
+                    return GS_ERR_CUDA;
+                res = sms * (per_sm > 0 ? per_sm : 1);
+            }
+            args(raster_fwd_kernel<D, NP, RT, FT, true, B>, tiles < res ? tiles : res, Shape<NP>::THREADS, 0);
+        } else {
+            args(raster_fwd_kernel<D, NP, RT, FT, false, B>, tiles, Shape<NP>::THREADS, 0);
         }
-        args(raster_fwd_kernel<D, NP, RT, FT, true>, tiles < res ? tiles : res, Shape<NP>::THREADS);
         return last_launch();
+    };
+    if (prm.fwd_batch == 128) return per_tile(std::integral_constant<int, 128>());
+    if constexpr (NP == 2 && D >= 16) {
+        if (prm.fwd_batch == 64) return per_tile(std::integral_constant<int, 64>());
+        if (prm.fwd_batch == 256) return per_tile(std::integral_constant<int, 256>());
     }
-    args(raster_fwd_kernel<D, NP, RT, FT, false>, tiles, Shape<NP>::THREADS);
-    return last_launch();
+    return GS_ERR_UNSUPPORTED;
 }
 
 template <int D, typename RT, typename FT>

@@ -30,16 +30,17 @@ class RasterParams:
     fwd_px_per_thread: int = 0     # launch shape only (0 = library default)
     bwd_px_per_thread: int = 0
     bwd_blocks: int = 0            # backward block shape (0 default, 1 per pixel group, 2 per tile)
-    fwd_blocks: int = 0            # forward block shape (same values)
+    fwd_blocks: int = 0            # forward block shape (same values, and 3 resident blocks on a tile queue)
     exact_jacobian: bool = False   # J of Eq. 3 at the unclamped (x/z, y/z) (GS_JACOBIAN_EXACT)
     spin_limit: int = 0            # polls of a bounded wait (0 library default; < 0 give up at once)
+    fwd_batch: int = 0             # splats staged per round by the per-tile forward (64, 128, 256; 0 = 128)
 
     def c(self) -> L.gs_raster_params:
         return L.gs_raster_params(self.tile, self.alpha_min, self.alpha_max, self.T_min, self.z_near, self.lowpass,
                                   self.radius_sigma, (ctypes.c_float * 3)(*self.bg), self.fwd_px_per_thread,
                                   self.bwd_px_per_thread, self.bwd_blocks, self.fwd_blocks,
                                   L.GS_JACOBIAN_EXACT if self.exact_jacobian else L.GS_JACOBIAN_CLAMPED,
-                                  self.spin_limit)
+                                  self.spin_limit, self.fwd_batch)
 
 
 @dataclasses.dataclass

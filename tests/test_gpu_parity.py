@@ -301,9 +301,10 @@ def test_tile_order_is_a_longest_first_permutation_and_changes_nothing():
 
 def test_queued_forward_matches_one_block_per_tile_and_resets_its_counters():
     """Two views: resident blocks taking tiles from the work counter render the same images
-    and blend mask as one block per tile, for every pixels-per-thread shape, in the tile
-    order and in index order; the counters are back at 0 after each launch, so repeated
-    launches after one binning agree; a NULL counter pointer is refused."""
+    and blend mask as one block per tile, for every pixels-per-thread shape and staged batch
+    of 64, 128 or 256 splats, in the tile order and in index order; the counters are back at
+    0 after each launch, so repeated launches after one binning agree; a NULL counter pointer
+    and a batch of another size are refused."""
     gs, cam, room = C.room_case(20000, 16, 330, 190, 165.0)
     cams = [cam, synth.camera(100, 70, 60.0, T_cw=synth.keyframe_loop(8, room=room)[3])]
     base = C.params_pair()[0]
@@ -313,11 +314,18 @@ def test_queued_forward_matches_one_block_per_tile_and_resets_its_counters():
         r.use_tile_order = use_order
         for np_ in (1, 2, 4):
             outs = []
-            for blocks in (L.GS_BWD_BLOCKS_TILE, L.GS_BLOCKS_QUEUE, L.GS_BLOCKS_QUEUE):
-                r.params = dataclasses.replace(base, fwd_px_per_thread=np_, fwd_blocks=blocks)
+            for blocks, batch in ((L.GS_BWD_BLOCKS_TILE, 0), (L.GS_BLOCKS_QUEUE, 0), (L.GS_BLOCKS_QUEUE, 128),
+                                  (L.GS_BWD_BLOCKS_TILE, 64), (L.GS_BWD_BLOCKS_TILE, 256),
+                                  (L.GS_BLOCKS_QUEUE, 64), (L.GS_BLOCKS_QUEUE, 256)):
+                r.params = dataclasses.replace(base, fwd_px_per_thread=np_, fwd_blocks=blocks, fwd_batch=batch)
                 r.prm_c = r.params.c()
                 r.project(field)
                 r.bin_sort()
+                if batch in (64, 256) and np_ != 2:  # built for two pixels per thread only
+                    with pytest.raises(L.GsError) as e:
+                        r.render_fwd(field)
+                    assert e.value.status == L.GS_ERR_UNSUPPORTED
+                    continue
                 for _ in range(2 if blocks == L.GS_BLOCKS_QUEUE else 1):
                     r.render_fwd(field)
                     torch.cuda.synchronize()
@@ -333,6 +341,11 @@ def test_queued_forward_matches_one_block_per_tile_and_resets_its_counters():
     status = L.gs_render_fwd(ctypes.byref(field.c()), ctypes.byref(r.projected_c()), ctypes.byref(b), r.cams_c,
                              r.n_views, ctypes.byref(r.prm_c), ctypes.byref(r.images_c()), None)
     assert status == L.GS_ERR_ARG
+    r.params = dataclasses.replace(base, fwd_batch=100)
+    with pytest.raises(L.GsError) as e:
+        r.prm_c = r.params.c()
+        r.render_fwd(field)
+    assert e.value.status == L.GS_ERR_ARG
 
 
 def test_autotuner_picks_a_supported_shape():
