@@ -113,12 +113,16 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP, MAP, KF>())
     constexpr bool RGB32 = sizeof(RT) == 4;
     constexpr int FB = D * (int)sizeof(FT);   // feature bytes per Gaussian
     constexpr int FCH = FB / 16;              // their 16-byte chunks
+    // a staged slot's feature row, padded to an odd number of 16-byte chunks so that the eight
+    // slots' rows start in different banks (the copies and the reads of one chunk index are
+    // then conflict-free)
+    constexpr int FBP = FCH % 2 == 0 ? FB + 16 : FB;
     constexpr int NCOPY = 3 + (RGB32 ? 3 : 0) + FCH;
     static_assert(FB % 16 == 0, "features in 16-byte chunks");
     __shared__ float4 r_a[2][STAGE], r_c[2][STAGE];
     __shared__ float2 r_lo[2][STAGE];
     __shared__ float r_rgb[2][STAGE][4];
-    __shared__ __align__(16) unsigned char r_f[2][STAGE * FB];
+    __shared__ __align__(16) unsigned char r_f[2][STAGE * FBP];
     const RT *rgb = static_cast<const RT *>(A.rgb);
     const FT *feat = static_cast<const FT *>(A.feat);
 
@@ -340,7 +344,7 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP, MAP, KF>())
     };
 
     // Every listed splat was blended by a pixel of the group, so no box culling is needed.
-    auto process = [&](const int k, const float *sfeat) {
+    auto process = [&](const int k, const float *sfeat, const int fstride) {
         const int pos = s_pos[k];
         const SplatGeo s = s_geo[k];
         // the mask listed this splat because a pixel of the group blended it, so some lane
@@ -359,7 +363,7 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP, MAP, KF>())
         {
             const float4 c = s_rgbd[k];
             x[0] = c.x; x[1] = c.y; x[2] = c.z; x[3] = c.w; x[4] = 1.f;
-            const float4 *sf = reinterpret_cast<const float4 *>(sfeat + k * F);
+            const float4 *sf = reinterpret_cast<const float4 *>(sfeat + k * fstride);
 #pragma unroll
             for (int q = 0; q < F4; ++q) {
                 const float4 f = sf[q];
@@ -434,7 +438,7 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP, MAP, KF>())
                     else if (RGB32 && c < 6) cp_async4(&r_rgb[b][si][c - 3], rgb + 3 * g + (c - 3));
                     else {
                         const int q = c - (RGB32 ? 6 : 3);
-                        cp_async16(&r_f[b][si * FB + 16 * q], reinterpret_cast<const unsigned char *>(feat + g * D) + 16 * q);
+                        cp_async16(&r_f[b][si * FBP + 16 * q], reinterpret_cast<const unsigned char *>(feat + g * D) + 16 * q);
                     }
                 }
             }
@@ -464,7 +468,7 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP, MAP, KF>())
                     s_item[si] = item;
                     s_pos[si] = (int)(ii - start);
                 }
-                const FT *fr = reinterpret_cast<const FT *>(&r_f[b][si * FB]);
+                const FT *fr = reinterpret_cast<const FT *>(&r_f[b][si * FBP]);
                 if constexpr (KF > 0) {
                     // z = W f for this part's K / PARTS logits
 #pragma unroll
@@ -489,8 +493,9 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP, MAP, KF>())
             }
             __syncwarp();
             // f32 features are read where they landed; the others from the widened copy
-            const float *sfeat = (KF == 0 && sizeof(FT) == 4) ? reinterpret_cast<const float *>(r_f[b]) : s_feat;
-            for (int k = 0; k < c_cnt; ++k) process(k, sfeat);
+            constexpr bool IN_PLACE = KF == 0 && sizeof(FT) == 4;
+            const float *sfeat = IN_PLACE ? reinterpret_cast<const float *>(r_f[b]) : s_feat;
+            for (int k = 0; k < c_cnt; ++k) process(k, sfeat, IN_PLACE ? FBP / 4 : F);
             if constexpr (MAP) contract(c_cnt);
             __syncwarp();
         }
