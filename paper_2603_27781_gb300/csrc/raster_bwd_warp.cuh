@@ -21,11 +21,12 @@
 // centre and conic gradients need only the moments of dpow
 //   S1, Sx, Sy, Sxx, Sxy, Syy = sum over pixels of dpow (1, lx, ly, lx^2, lx ly, ly^2),
 // expanded about the splat centre afterwards (sum dpow dx = Sx - cx S1, and so on),
-// and the opacity gradient is S1 / o.  After the stage, lanes (slot, part) contract
-// the slots with the block's per-pixel terms (weights against the gradients of
-// depth, colour and features; dpow against the fixed coordinates) in one pass of
-// FP32 FMAs, and each slot's sums go out as 16-byte L2 reductions.  No warp
-// reduction runs per splat.
+// and the opacity gradient is S1 / o.  After the stage, lanes (pixel column, slot
+// pair) contract the slots with the block's per-pixel terms (weights against the
+// gradients of depth, colour and features; dpow against the row coordinates) down
+// their column in FP32 FMAs, the eight columns are combined by one transpose
+// reduction per stage, and each slot's sums go out as 16-byte L2 reductions.  No
+// warp reduction runs per splat.
 //
 // Factored feature gradients.  When the image gradient of the features comes from
 // a linear decoder (Eq. 8 read as a 1x1 convolution), g_feat = W^T e with e the
@@ -107,7 +108,10 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP, MAP, KF>())
     __shared__ __align__(16) float s_p[MAP ? STAGE * WL::WROW : 4];   // [slot][pixel] dpow
     __shared__ __align__(16) float s_g[MAP ? WL::PXW * WL::GROW : 4]; // [pixel][term] gradients
     __shared__ float s_t[MAP ? STAGE * WL::NSV : 4];                  // [slot][sum] sums
-    __shared__ float s_basis[KF ? KF * D : 1];                        // W, K x D (rows >= K zero)
+    // W, K x D (rows >= K zero), rows padded by 4 so that the four lane parts, which read rows
+    // k = part (K / 4) + kk, fall in different banks
+    constexpr int BROW = D + 4;
+    __shared__ __align__(16) float s_basis[KF ? KF * BROW : 4];
     // raw records of two stages (the next one is copied while the current one is processed):
     // centre / depth / opacity, conic / radius, centre low parts, colour (f32 storage), features
     constexpr bool RGB32 = sizeof(RT) == 4;
@@ -144,7 +148,8 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP, MAP, KF>())
     const float bcx = (float)(tx * kTile + bx0) + 4.f, bcy = (float)(ty * kTile + by0) + 0.5f * WL::ROWS;
 
     if constexpr (KF > 0) {
-        for (int i = lane; i < KF * D; i += 32) s_basis[i] = i < A.feat_rank * D ? A.feat_basis[i] : 0.f;
+        for (int i = lane; i < KF * D; i += 32)
+            s_basis[(i / D) * BROW + i % D] = i < A.feat_rank * D ? A.feat_basis[i] : 0.f;
     }
 
     float gch[NP][NCH], T[NP], gS[NP], pxc[NP], pyc[NP];
@@ -329,7 +334,7 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP, MAP, KF>())
                     if constexpr (KF > 0) {
                         float sacc = 0.f;
 #pragma unroll
-                        for (int k = 0; k < KF; ++k) sacc = fmaf(s_basis[k * D + c], tj[4 + k], sacc);
+                        for (int k = 0; k < KF; ++k) sacc = fmaf(s_basis[k * BROW + c], tj[4 + k], sacc);
                         o4[i] = sacc;
                     } else {
                         o4[i] = tj[4 + c];
@@ -478,10 +483,11 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP, MAP, KF>())
 #pragma unroll
                         for (int q = 0; q < D / 4; ++q) {
                             const float4 f4 = load_feat4(fr, 4 * q);
-                            z = fmaf(s_basis[k * D + 4 * q], f4.x, z);
-                            z = fmaf(s_basis[k * D + 4 * q + 1], f4.y, z);
-                            z = fmaf(s_basis[k * D + 4 * q + 2], f4.z, z);
-                            z = fmaf(s_basis[k * D + 4 * q + 3], f4.w, z);
+                            const float4 w4 = reinterpret_cast<const float4 *>(s_basis + k * BROW)[q];
+                            z = fmaf(w4.x, f4.x, z);
+                            z = fmaf(w4.y, f4.y, z);
+                            z = fmaf(w4.z, f4.z, z);
+                            z = fmaf(w4.w, f4.w, z);
                         }
                         s_feat[si * F + k] = z;
                     }
