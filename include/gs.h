@@ -124,8 +124,9 @@ typedef struct {
     int32_t spin_limit;
     /* Splats the per-tile forward (fwd_blocks GS_BWD_BLOCKS_TILE or
      * GS_BLOCKS_QUEUE) stages in shared memory per round: 64, 128 or 256
-     * (0 = 128); other values return GS_ERR_ARG.  64 and 256 are built for two
-     * pixels per thread at feature dims 16 and 32 (else GS_ERR_UNSUPPORTED).
+     * (0 = 128); other values return GS_ERR_ARG.  64 is built for two pixels
+     * per thread at feature dims 16 and 32, 256 for two pixels per thread at
+     * feature dim 16 (else GS_ERR_UNSUPPORTED).
      * Results do not depend on it. */
     int32_t fwd_batch;
 } gs_raster_params;

@@ -149,4 +149,34 @@ __device__ __forceinline__ bool reaches_box(float u, float v, float2 e, float bc
     return fabsf(u - bcx) <= e.x + hx && fabsf(v - bcy) <= e.y + hy;
 }
 
+// The splat's constants for reaches_box_exact: the edge optima rx = -qb / (2 qc), ry = -qb /
+// (2 qa) and the exponent threshold log2(alpha_min / o) (-inf when alpha_min is 0).
+__device__ __forceinline__ float4 ellipse_cull(const SplatGeo &s, float alpha_min) {
+    return make_float4(-s.qb / (2.f * s.qc), -s.qb / (2.f * s.qa), __log2f(alpha_min) - __log2f(s.o), 0.f);
+}
+
+// Whether any point of the box of pixel centres [bcx - hx, bcx + hx] x [bcy - hy, bcy + hy]
+// can have alpha >= alpha_min, i.e. exponent p(x, y) = qa x^2 + qb x y + qc y^2 >= log2(alpha_min
+// / o) with (x, y) relative to the centre: the exact ellipse against the box, where the
+// extent test bounds the ellipse by its rectangle.  p is concave with its maximum 0 at the
+// centre; with the centre outside the box its maximum over the box lies on an edge, on the
+// vertical edge x = xe at y = clamp(rx xe) and on the horizontal edge y = ye at
+// x = clamp(ry ye).  Conservative: the box is widened by 0.01 px (the centre's low part and the
+// rounding of pixel - centre) and the threshold lowered by 1e-5 of the largest term magnitude
+// over the box plus 1e-4 (rounding of p and of the exponential), so no pair that the evaluation
+// would blend is culled.
+__device__ __forceinline__ bool reaches_box_exact(const SplatGeo &s, float4 k, float bcx, float bcy, float hx,
+                                                  float hy) {
+    const float x0 = (bcx - hx - 0.01f) - s.u, x1 = (bcx + hx + 0.01f) - s.u;
+    const float y0 = (bcy - hy - 0.01f) - s.v, y1 = (bcy + hy + 0.01f) - s.v;
+    if (x0 <= 0.f && x1 >= 0.f && y0 <= 0.f && y1 >= 0.f) return true;
+    auto p = [&](float x, float y) { return fmaf(fmaf(s.qa, x, s.qb * y), x, s.qc * y * y); };
+    const float ya = fminf(fmaxf(k.x * x0, y0), y1), yb = fminf(fmaxf(k.x * x1, y0), y1);
+    const float xa = fminf(fmaxf(k.y * y0, x0), x1), xb = fminf(fmaxf(k.y * y1, x0), x1);
+    const float best = fmaxf(fmaxf(p(x0, ya), p(x1, yb)), fmaxf(p(xa, y0), p(xb, y1)));
+    const float X = fmaxf(fabsf(x0), fabsf(x1)), Y = fmaxf(fabsf(y0), fabsf(y1));
+    const float mag = fmaf(-s.qa, X * X, fmaf(fabsf(s.qb), X * Y, -s.qc * Y * Y));
+    return best >= k.z - fmaf(1e-5f, mag, 1e-4f);
+}
+
 }  // namespace gs

@@ -37,6 +37,7 @@ __device__ __forceinline__ void fwd_tile(
     constexpr int batch = BATCH;
     __shared__ SplatGeo s_geo[BATCH];
     __shared__ float2 s_ext[BATCH];
+    __shared__ float4 s_cull[BATCH];
     __shared__ float4 s_rgbd[BATCH];
     __shared__ float4 s_feat[BATCH * (D4 > 0 ? D4 : 1)];
 
@@ -106,6 +107,7 @@ __device__ __forceinline__ void fwd_tile(
                 const float4 c = conic[item];
                 s_geo[i] = make_geo(a, uv_lo[item], c);
                 s_ext[i] = splat_extent(c, a.w, prm.alpha_min);
+                s_cull[i] = ellipse_cull(s_geo[i], prm.alpha_min);
                 s_rgbd[i] = load_rgbd(rgb, g, a.z);
 #pragma unroll
                 for (int q = 0; q < D4; ++q) s_feat[i * D4 + q] = load_feat4(feat, g * D + 4 * q);
@@ -123,7 +125,9 @@ __device__ __forceinline__ void fwd_tile(
             const int kl = c0 + lane;
             bool reach = false;
             if (kl >= k_lo && kl < nb) {
-                reach = reaches_box(s_geo[kl].u, s_geo[kl].v, s_ext[kl], bcx, bcy, hx, hy);
+                const SplatGeo sg = s_geo[kl];
+                reach = reaches_box(sg.u, sg.v, s_ext[kl], bcx, bcy, hx, hy) &&
+                        reaches_box_exact(sg, s_cull[kl], bcx, bcy, hx, hy);
             }
             uint32_t todo = __ballot_sync(0xffffffffu, reach);
             for (int n_run = 0; todo; ++n_run) {
@@ -316,8 +320,10 @@ __global__ void __launch_bounds__(32, fwd_group_min_blocks(D, NP)) raster_fwd_gr
                 const int64_t g = (int64_t)item - voff;
                 const float4 a = uvdo[item];
                 const float4 c = conic[item];
-                s_geo[lane] = make_geo(a, uv_lo[item], c);
-                reach = reaches_box(a.x, a.y, splat_extent(c, a.w, prm.alpha_min), bcx, bcy, hx, hy);
+                const SplatGeo sg = make_geo(a, uv_lo[item], c);
+                s_geo[lane] = sg;
+                reach = reaches_box(a.x, a.y, splat_extent(c, a.w, prm.alpha_min), bcx, bcy, hx, hy) &&
+                        reaches_box_exact(sg, ellipse_cull(sg, prm.alpha_min), bcx, bcy, hx, hy);
                 s_rgbd[lane] = load_rgbd(rgb, g, a.z);
 #pragma unroll
                 for (int q = 0; q < D4; ++q) s_feat[lane * D4 + q] = load_feat4(feat, g * D + 4 * q);
@@ -431,7 +437,7 @@ gs_status launch(const ViewTable &vt, const Params &prm, const gs_gaussians *g, 
         }
     }
     // the per-tile forward with BATCH splats staged per round; batches other than 128 are built
-    // for the two-pixel shape at feature widths 16 and 32
+    // for the two-pixel shape: 64 at feature widths 16 and 32, 256 at 16
     auto per_tile = [&](auto batch_c) -> gs_status {
         constexpr int B = decltype(batch_c)::value;
         if (prm.fwd_queue) {
@@ -453,10 +459,10 @@ gs_status launch(const ViewTable &vt, const Params &prm, const gs_gaussians *g, 
         return last_launch();
     };
     if (prm.fwd_batch == 128) return per_tile(std::integral_constant<int, 128>());
-    if constexpr (NP == 2 && D >= 16) {
+    if constexpr (NP == 2 && D >= 16)
         if (prm.fwd_batch == 64) return per_tile(std::integral_constant<int, 64>());
+    if constexpr (NP == 2 && D == 16)  // 256 records of D = 32 would not fit the 48 KB of static shared memory
         if (prm.fwd_batch == 256) return per_tile(std::integral_constant<int, 256>());
-    }
     return GS_ERR_UNSUPPORTED;
 }
 

@@ -321,7 +321,7 @@ def test_queued_forward_matches_one_block_per_tile_and_resets_its_counters():
                 r.prm_c = r.params.c()
                 r.project(field)
                 r.bin_sort()
-                if batch in (64, 256) and np_ != 2:  # built for two pixels per thread only
+                if batch in (64, 256) and np_ != 2:  # built for two pixels per thread (and D = 16, 32) only
                     with pytest.raises(L.GsError) as e:
                         r.render_fwd(field)
                     assert e.value.status == L.GS_ERR_UNSUPPORTED
