@@ -118,6 +118,19 @@ def test_bin_sort_bit_exact_multiview_and_ties():
     _check_sort(gs, cams, C.params_pair()[0])
 
 
+@pytest.mark.parametrize("width", [16, 48])
+def test_bin_sort_bit_exact_long_tiles(width):
+    """Tiles of more than 4096 instances: 9,000 Gaussians in front of a 16x16 (one tile) or
+    48x16 image, half of them on the centres of the others (equal depth keys, ordered by
+    item)."""
+    gs, cam = C.box_case(9000, 8, width, 16, 12.0)
+    gs.means[1::2] = gs.means[0::2][: gs.means[1::2].shape[0]]
+    _check_sort(gs, [cam], C.params_pair()[0])
+    _, r = C.gpu_forward(gs, [cam], C.params_pair()[0])
+    rg = r.ranges.cpu().numpy().astype(np.int64).reshape(-1, 2)
+    assert (rg[:, 1] - rg[:, 0]).max() > 4096
+
+
 @pytest.mark.parametrize("name", list(CASES))
 def test_render_fwd_matches_oracle(name):
     gs, cam = CASES[name]()
