@@ -438,6 +438,22 @@ gs_status gs_loss_fwd_bwd_noalloc(const gs_camera *cams, int n_views, int feat_d
 gs_status gs_dsr(int64_t n, const float *log_scales, float lam_big, float lam_small, void *ws,
                  size_t ws_bytes, float *d_log_scales, double *out, gs_stream stream);
 
+/* The two halves of gs_dsr, so that the value (two reductions over the scales,
+ * which need only log_scales) can run on another stream beside the rest of a
+ * step and only the gradient waits for the projection backward.
+ * gs_dsr_value writes out exactly as gs_dsr does, with its partial sums in
+ * scratch: device memory of GS_DSR_SCRATCH_BYTES bytes, 256-byte aligned, used
+ * by one call at a time (it need not be the workspace, so the call may overlap
+ * gs_bin_sort and gs_loss_fwd_bwd).  gs_dsr_grad then adds lam_big * dL_big +
+ * lam_small * dL_small to d_log_scales (+=) from that out, after gs_dsr_value
+ * has completed (stream order or an event).  n = 0: gs_dsr_value writes zeros,
+ * gs_dsr_grad does nothing.  GS_ERR_ARG for a missing buffer or n < 0. */
+#define GS_DSR_SCRATCH_BYTES 24832
+gs_status gs_dsr_value(int64_t n, const float *log_scales, float lam_big, float lam_small, void *scratch,
+                       double *out, gs_stream stream);
+gs_status gs_dsr_grad(int64_t n, const float *log_scales, float lam_big, float lam_small, const double *out,
+                      float *d_log_scales, gs_stream stream);
+
 /* Pose step for tracking (Sec. 3.4; learning rates of supp. C.1): Adam on
  * the left twist of each view, then T <- Exp(delta) T.  T_state: device f64
  * [n_views,16] (updated); adam: device f64 [n_views,12] (m, v; zero before

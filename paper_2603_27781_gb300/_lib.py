@@ -18,6 +18,7 @@ GS_OK, GS_ERR_ARG, GS_ERR_CAPACITY, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_ERR_UNSUPPOR
 GS_BWD_BLOCKS_DEFAULT, GS_BWD_BLOCKS_GROUP, GS_BWD_BLOCKS_TILE, GS_BLOCKS_QUEUE = 0, 1, 2, 3
 GS_JACOBIAN_CLAMPED, GS_JACOBIAN_EXACT = 0, 1
 GS_F32, GS_BF16, GS_F16 = 0, 1, 2
+GS_DSR_SCRATCH_BYTES = 24832
 GS_GRAD_MAP, GS_GRAD_POSE = 1, 2
 
 
@@ -118,6 +119,8 @@ _SIGNATURES = {
                                         c_void_p, _P(gs_loss_params), _P(gs_image_grads_out), c_void_p, c_void_p,
                                         c_void_p, c_void_p, c_void_p, c_void_p]),
     "gs_dsr": (c_int, [c_int64, c_void_p, c_float, c_float, c_void_p, c_size_t, c_void_p, c_void_p, c_void_p]),
+    "gs_dsr_value": (c_int, [c_int64, c_void_p, c_float, c_float, c_void_p, c_void_p, c_void_p]),
+    "gs_dsr_grad": (c_int, [c_int64, c_void_p, c_float, c_float, c_void_p, c_void_p, c_void_p]),
     "gs_pose_step": (c_int, [c_int, c_void_p, c_void_p, c_void_p, c_int, _P(c_double), c_double, c_double,
                              c_double, c_void_p, c_void_p]),
     "gs_adam_step": (c_int, [_P(gs_field_mut), _P(gs_gaussian_grads), c_void_p, c_int, c_void_p, _P(c_float),
@@ -182,6 +185,8 @@ gs_pose_grad = _wrap("gs_pose_grad")
 gs_loss_fwd_bwd = _wrap("gs_loss_fwd_bwd")
 gs_loss_fwd_bwd_noalloc = _wrap("gs_loss_fwd_bwd_noalloc")
 gs_dsr = _wrap("gs_dsr")
+gs_dsr_value = _wrap("gs_dsr_value")
+gs_dsr_grad = _wrap("gs_dsr_grad")
 gs_pose_step = _wrap("gs_pose_step")
 gs_adam_step = _wrap("gs_adam_step")
 gs_expand = _wrap("gs_expand")

@@ -758,6 +758,37 @@ extern "C" gs_status gs_loss_fwd_bwd(const gs_camera *cams, int n_views, int fea
 #undef GS_LOSS
 }
 
+namespace gs {
+namespace {
+static_assert(6 * kRedBlocks * sizeof(double) + 2 * sizeof(uint32_t) <= GS_DSR_SCRATCH_BYTES,
+              "the DSR partials and their arrival counters fit the scratch");
+
+// The value of Eq. 12 into out, with its partials (and two arrival counters after them) in part.
+gs_status dsr_value(int64_t n, const float *log_scales, float lam_big, float lam_small, double *part, double *out,
+                    cudaStream_t st) {
+    if (n == 0) return cuda_status(cudaMemsetAsync(out, 0, 8 * sizeof(double), st));
+    const int64_t m = 3 * n;
+    const int grid = std::min(ceil_div(m, 256), kRedBlocks);
+    // the arrival counters are zeroed here; each finishing block resets its own
+    uint32_t *ctr = reinterpret_cast<uint32_t *>(part + 6 * kRedBlocks);
+    gs_status s;
+    if ((s = cuda_status(cudaMemsetAsync(ctr, 0, 2 * sizeof(uint32_t), st)))) return s;
+    dsr_stats_kernel<<<grid, 256, 0, st>>>(m, log_scales, part, out, ctr);
+    dsr_mask_kernel<<<grid, 256, 0, st>>>(m, log_scales, out, part + 2 * kRedBlocks, lam_big, lam_small, ctr + 1);
+    return last_launch();
+}
+
+gs_status dsr_grad(int64_t n, const float *log_scales, float lam_big, float lam_small, const double *out,
+                   float *d_log_scales, cudaStream_t st) {
+    if (n == 0) return GS_OK;
+    const int64_t m = 3 * n;
+    dsr_grad_kernel<<<std::min(ceil_div(m, 256), kRedBlocks), 256, 0, st>>>(m, log_scales, lam_big, lam_small, out,
+                                                                             d_log_scales);
+    return last_launch();
+}
+}  // namespace
+}  // namespace gs
+
 extern "C" gs_status gs_dsr(int64_t n, const float *log_scales, float lam_big, float lam_small, void *ws,
                             size_t ws_bytes, float *d_log_scales, double *out, gs_stream stream) {
     using namespace gs;
@@ -765,19 +796,26 @@ extern "C" gs_status gs_dsr(int64_t n, const float *log_scales, float lam_big, f
     if (n < 0 || !out || !ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return GS_ERR_ARG;
     WsLayout L = ws_layout(0, 1, 0);
     if (ws_bytes < L.misc_end) return GS_ERR_ARG;
+    if (n > 0 && (!log_scales || !d_log_scales)) return GS_ERR_ARG;
     double *part = reinterpret_cast<double *>(static_cast<char *>(ws) + L.dsr_part);
     gs_status s;
-    if (n == 0) return cuda_status(cudaMemsetAsync(out, 0, 8 * sizeof(double), st));
-    if (!log_scales || !d_log_scales) return GS_ERR_ARG;
-    const int64_t m = 3 * n;
-    const int grid = std::min(ceil_div(m, 256), kRedBlocks);
-    // two arrival counters after the partials (zeroed here; each finishing block resets its own)
-    uint32_t *ctr = reinterpret_cast<uint32_t *>(part + 6 * kRedBlocks);
-    if ((s = cuda_status(cudaMemsetAsync(ctr, 0, 2 * sizeof(uint32_t), st)))) return s;
-    dsr_stats_kernel<<<grid, 256, 0, st>>>(m, log_scales, part, out, ctr);
-    dsr_mask_kernel<<<grid, 256, 0, st>>>(m, log_scales, out, part + 2 * kRedBlocks, lam_big, lam_small, ctr + 1);
-    dsr_grad_kernel<<<grid, 256, 0, st>>>(m, log_scales, lam_big, lam_small, out, d_log_scales);
-    return last_launch();
+    if ((s = dsr_value(n, log_scales, lam_big, lam_small, part, out, st))) return s;
+    return dsr_grad(n, log_scales, lam_big, lam_small, out, d_log_scales, st);
+}
+
+extern "C" gs_status gs_dsr_value(int64_t n, const float *log_scales, float lam_big, float lam_small, void *scratch,
+                                  double *out, gs_stream stream) {
+    using namespace gs;
+    if (n < 0 || !out || !scratch || (reinterpret_cast<uintptr_t>(scratch) & 255) || (n > 0 && !log_scales))
+        return GS_ERR_ARG;
+    return dsr_value(n, log_scales, lam_big, lam_small, static_cast<double *>(scratch), out, (cudaStream_t)stream);
+}
+
+extern "C" gs_status gs_dsr_grad(int64_t n, const float *log_scales, float lam_big, float lam_small, const double *out,
+                                 float *d_log_scales, gs_stream stream) {
+    using namespace gs;
+    if (n < 0 || !out || (n > 0 && (!log_scales || !d_log_scales))) return GS_ERR_ARG;
+    return dsr_grad(n, log_scales, lam_big, lam_small, out, d_log_scales, (cudaStream_t)stream);
 }
 
 extern "C" gs_status gs_pose_grad(int64_t n, int n_views, const float *pose_part, double *d_twist, gs_stream stream) {

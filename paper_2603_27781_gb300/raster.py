@@ -182,6 +182,7 @@ class Renderer:
         self.d_twist = torch.zeros(V, 6, dtype=torch.float64, device=dev)
         self.loss_out = torch.zeros(4, dtype=torch.float64, device=dev)
         self.dsr_out = torch.zeros(8, dtype=torch.float64, device=dev)
+        self.dsr_scratch = torch.empty(L.GS_DSR_SCRATCH_BYTES, dtype=torch.uint8, device=dev)
         self.mask = torch.zeros(P, dtype=f32, device=dev)
         self.median = torch.zeros(V, dtype=f32, device=dev)
         K = max(int(n_classes), 1)
@@ -354,6 +355,17 @@ class Renderer:
         L.check("gs_dsr", L.gs_dsr(self.n, _p(field.log_scales), lam_big, lam_small, _p(self.ws), self.ws.numel(),
                                    _p(self.d_log_scales), _p(self.dsr_out), _stream(stream)))
 
+    def dsr_value(self, field: Field, lam_big: float, lam_small: float, stream=None):
+        """The value of Eq. 12 into dsr_out (gs_dsr_value; its own scratch, so it may run beside
+        the binning and the loss on another stream)."""
+        L.check("gs_dsr_value", L.gs_dsr_value(self.n, _p(field.log_scales), lam_big, lam_small,
+                                               _p(self.dsr_scratch), _p(self.dsr_out), _stream(stream)))
+
+    def dsr_grad(self, field: Field, lam_big: float, lam_small: float, stream=None):
+        """Adds the gradient of Eq. 12 from dsr_out to d_log_scales (gs_dsr_grad)."""
+        L.check("gs_dsr_grad", L.gs_dsr_grad(self.n, _p(field.log_scales), lam_big, lam_small, _p(self.dsr_out),
+                                             _p(self.d_log_scales), _stream(stream)))
+
     def pose_step(self, T_state, adam, step, lr=TRACKING_LR, b1=0.9, b2=0.999, eps=1e-15, pose_f32=None,
                   stream=None):
         """Adam step on the view twists.  step >= 1 is the 1-based step number; step 0
@@ -375,22 +387,24 @@ class Renderer:
     def iteration(self, field: Field, targets, decoder_W, decoder_b, w: LossWeights, grad_mode=L.GS_GRAD_MAP,
                   pose_dev=None, stream=None):
         """One fwd+bwd pass of the whole path: project, bin/sort, blend, loss, blend and
-        projection backward, pose-twist reduction, DSR.  Asynchronous.  With both the twist and
-        the DSR to do, the DSR (which needs only the log-scale gradient the projection backward
-        has written) runs on a side stream beside the twist reduction and rejoins the stream
-        before the call returns (also inside a CUDA-graph capture)."""
+        projection backward, pose-twist reduction, DSR.  Asynchronous.  The DSR's value (which
+        needs only the log-scales) runs on a side stream beside the whole step, its gradient
+        there beside the twist reduction once the projection backward has written the
+        log-scale gradient, and the side stream rejoins `stream` before the call returns (also
+        inside a CUDA-graph capture)."""
+        dsr = (grad_mode & L.GS_GRAD_MAP) and (w.big or w.small)
+        if dsr:  # its value needs only the log-scales: beside the whole step on the side stream
+            self.side_start(lambda s: self.dsr_value(field, w.big, w.small, s), stream)
         self.forward(field, pose_dev, stream)
         fac = self.use_factored(decoder_W)
         self.loss(targets, decoder_W, decoder_b, w, stream, factored=fac)
-        dsr = (grad_mode & L.GS_GRAD_MAP) and (w.big or w.small)
-        if not (dsr and grad_mode & L.GS_GRAD_POSE):
+        if not dsr:
             self.backward(field, grad_mode, pose_dev, stream, factored=fac)
-            if dsr:
-                self.dsr(field, w.big, w.small, stream)
             return
         self.render_bwd(field, grad_mode, stream, factored=fac)
         self.project_bwd(field, grad_mode, pose_dev, stream)
-        self.side_by_side(lambda s: self.dsr(field, w.big, w.small, s), lambda: self.pose_grad(stream), stream)
+        main = (lambda: self.pose_grad(stream)) if grad_mode & L.GS_GRAD_POSE else (lambda: None)
+        self.side_by_side(lambda s: self.dsr_grad(field, w.big, w.small, s), main, stream)
 
     def use_factored(self, decoder_W) -> bool:
         """Whether a step with this decoder takes the factored feature gradient: the renderer
@@ -399,6 +413,16 @@ class Renderer:
         K = int(decoder_W.shape[0]) if decoder_W is not None else 0
         return (self.factored and 1 <= K <= FACTOR_K and self.use_blend_mask
                 and self.params.bwd_blocks != L.GS_BWD_BLOCKS_TILE and self.params.bwd_px_per_thread <= 2)
+
+    def side_start(self, side_work, stream=None):
+        """Runs side_work(side_stream) on the renderer's side stream after everything issued so
+        far on `stream`, without waiting for it; a later side_by_side joins it."""
+        main = stream if stream is not None else torch.cuda.current_stream(self.device)
+        if getattr(self, "_side", None) is None:
+            self._side = torch.cuda.Stream(self.device)
+        self._side.wait_stream(main)
+        with torch.cuda.stream(self._side):
+            side_work(self._side)
 
     def side_by_side(self, side_work, main_work, stream=None):
         """Runs side_work(side_stream) on the renderer's side stream after everything issued

@@ -90,6 +90,12 @@ def test_argument_errors_before_any_launch(lib):
     for bad_args in (args(2, 3, 2, fake, 8), args(5, 4, 2, fake, 8), args(2, 2, 0, fake, 8), args(2, 2, 2, None, 8),
                      args(2, 2, 2, fake, 0), args(4, 4, 2, fake, 8), args(-1, 0, 2, fake, 8)):
         assert lib.gs_rskm_draw(*bad_args) == L.GS_ERR_ARG
+    # the halves of the DSR: missing buffers, a negative count, an unaligned scratch
+    assert lib.gs_dsr_value(10, None, 1.0, 1.0, None, None, None) == L.GS_ERR_ARG
+    assert lib.gs_dsr_value(-1, None, 1.0, 1.0, None, None, None) == L.GS_ERR_ARG
+    assert lib.gs_dsr_value(10, 4096, 1.0, 1.0, 257, 4096, None) == L.GS_ERR_ARG
+    assert lib.gs_dsr_grad(10, None, 1.0, 1.0, None, None, None) == L.GS_ERR_ARG
+    assert lib.gs_dsr_grad(-1, 4096, 1.0, 1.0, 4096, 4096, None) == L.GS_ERR_ARG
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):

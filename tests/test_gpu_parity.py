@@ -503,6 +503,28 @@ def test_median_is_bit_exact_on_large_views():
         assert r.median[v].item() == np.float32(oracle.lower_median(e.astype(np.float64)))
 
 
+def test_dsr_in_two_halves_equals_one_call():
+    """gs_dsr_value on a side stream (its own scratch) followed by gs_dsr_grad gives the
+    value and the gradient of gs_dsr bit for bit."""
+    gs, _, _ = C.room_case(200000, 0, 64, 48, 60.0)
+    ls = torch.as_tensor(gs.log_scales).cuda()
+    r = raster.Renderer(gs.n, [synth.camera(64, 48, 60.0)], 0, 0)
+    field = raster.Field(torch.zeros(gs.n, 3).cuda(), torch.zeros(gs.n, 4).cuda(), ls, torch.zeros(gs.n).cuda(),
+                         torch.zeros(gs.n, 3).cuda(), torch.zeros(gs.n, 0).cuda())
+    base = torch.randn(gs.n, 3, generator=torch.Generator().manual_seed(3)).cuda()
+    r.d_log_scales.copy_(base)
+    r.dsr(field, 0.01, 0.001)
+    torch.cuda.synchronize()
+    one = (r.dsr_out.clone(), r.d_log_scales.clone())
+    r.d_log_scales.copy_(base)
+    r.dsr_out.zero_()
+    r.side_start(lambda s: r.dsr_value(field, 0.01, 0.001, s))
+    r.side_by_side(lambda s: r.dsr_grad(field, 0.01, 0.001, s), lambda: None)
+    torch.cuda.synchronize()
+    assert torch.equal(r.dsr_out, one[0]) and torch.equal(r.d_log_scales, one[1])
+    assert float(one[0][3]) > 0                                  # the large-scale set is not empty
+
+
 def test_dsr_matches_oracle():
     gs, _, _ = C.room_case(200000, 0, 64, 48, 60.0)
     ls = torch.as_tensor(gs.log_scales).cuda()
