@@ -184,6 +184,8 @@ __global__ void __launch_bounds__(LossShape<D, KC>::NT) loss_kernel(
     const float *trgb, const float *tdepth, const uint8_t *label, const float *Wd, const float *bd, int64_t P,
     const uint32_t *med_hist, float *g_rgb, float *g_depth, float *g_sil, float *g_feat, float *g_coef, float *part_f,
     double *part_d, float *mask_out, float *median_out) {
+    pdl_wait();     // the previous kernel's results
+    pdl_trigger();  // the next kernel may be scheduled now
     using SH = LossShape<D, KC>;
     constexpr int NT = SH::NT, DD = SH::DD, EPL = SH::EPL;
     __shared__ __align__(16) float s_W[KC * DD];
@@ -394,6 +396,8 @@ __global__ void __launch_bounds__(LossShape<D, KC>::NT) loss_kernel(
 __global__ void __launch_bounds__(256) loss_finish_kernel(int nblk, int nrows_d, int K, int D, const float *part_f,
                                                           const double *part_d, float *dW, float *db,
                                                           double *loss_out) {
+    pdl_wait();     // the previous kernel's results
+    pdl_trigger();  // the next kernel may be scheduled now
     __shared__ double s_red[8];
     const int nval = K * D + K, j = blockIdx.x;
     if (j < nval) {
@@ -490,6 +494,8 @@ __device__ double sum_partials_cg(const double *part, int stride, int col, int n
 // them into the population mean and deviation, out[1], out[2] (detached constants).
 __global__ void __launch_bounds__(256) dsr_stats_kernel(int64_t m, const float *ls, double *part, double *out,
                                                         uint32_t *ctr) {
+    pdl_wait();     // the previous kernel's results
+    pdl_trigger();  // the next kernel may be scheduled now
     __shared__ double s_red[8];
     Kahan s1, s2;
     for_my_elements(m, ls, [&](int64_t, float l) {
@@ -524,6 +530,8 @@ __device__ __forceinline__ float2 dsr_bounds(const double *out) {
 // n_small, L_big, L_small, 0).
 __global__ void __launch_bounds__(256) dsr_mask_kernel(int64_t m, const float *ls, double *out, double *mask_part,
                                                        float lam_big, float lam_small, uint32_t *ctr) {
+    pdl_wait();     // the previous kernel's results
+    pdl_trigger();  // the next kernel may be scheduled now
     __shared__ double s_red[8];
     const float2 bd = dsr_bounds(out);
     Kahan sb, ss;
@@ -554,6 +562,8 @@ __global__ void __launch_bounds__(256) dsr_mask_kernel(int64_t m, const float *l
 
 __global__ void __launch_bounds__(256) dsr_grad_kernel(int64_t m, const float *ls, float lam_big, float lam_small,
                                                        const double *out, float *d_ls) {
+    pdl_wait();     // the previous kernel's results
+    pdl_trigger();  // the next kernel may be scheduled now
     const float2 bd = dsr_bounds(out);
     const double nb = out[3], ns = out[4];
     const float gb = nb > 0 ? (float)(lam_big / nb) : 0.f;
@@ -573,6 +583,8 @@ __global__ void __launch_bounds__(256) dsr_grad_kernel(int64_t m, const float *l
 constexpr int kPoseBlocks = 128;
 
 __global__ void __launch_bounds__(256) pose_reduce_kernel(int64_t n, const float *pose_part, double *d_twist) {
+    pdl_wait();     // the previous kernel's results
+    pdl_trigger();  // the next kernel may be scheduled now
     __shared__ double s_red[8];
     const int vk = blockIdx.y;  // view * 6 + component
     const float *p = pose_part + (int64_t)vk * n;
@@ -593,6 +605,8 @@ constexpr int kPoseLanes = 16;
 __global__ void pose_step_kernel(int n_views, const double *grad, double *Tst, double *adam, double bc1, double bc2,
                                  double lr0, double lr1, double lr2, double lr3, double lr4, double lr5, double b1,
                                  double b2, double eps, float *pose_f32) {
+    pdl_wait();     // the previous kernel's results
+    pdl_trigger();  // the next kernel may be scheduled now
     __shared__ double s_bc[2];
     __shared__ double s_dl[kMaxViews][6], s_abc[kMaxViews][3], s_R[kMaxViews][9], s_V[kMaxViews][9];
     __shared__ double s_t[kMaxViews][3];
@@ -689,14 +703,15 @@ gs_status launch_loss(const ViewTable &vt, const LossP &lp, const gs_images *img
     const int bx = loss_blocks_x(vt, lp.K <= 8 ? resident_blocks(loss_kernel<D, 8>, LossShape<D, 8>::NT)
                                               : resident_blocks(loss_kernel<D, kMaxK>, LossShape<D, kMaxK>::NT));
     dim3 grid(bx, vt.n_views);
-    if (lp.K <= 8)
-        loss_kernel<D, 8><<<grid, LossShape<D, 8>::NT, 0, st>>>(
-            vt, lp, img->rgb, img->depth, img->sil, img->feat, tgt->rgb, tgt->depth, tgt->label, W, b, P, mh, g->rgb,
-            g->depth, g->sil, g->feat, g->feat_coef, part_f, part_d, mask_out, median_out);
-    else
-        loss_kernel<D, kMaxK><<<grid, LossShape<D, kMaxK>::NT, 0, st>>>(
-            vt, lp, img->rgb, img->depth, img->sil, img->feat, tgt->rgb, tgt->depth, tgt->label, W, b, P, mh, g->rgb,
-            g->depth, g->sil, g->feat, g->feat_coef, part_f, part_d, mask_out, median_out);
+    const gs_status ls =
+        lp.K <= 8 ? launch_pdl(loss_kernel<D, 8>, grid, LossShape<D, 8>::NT, 0, st, vt, lp, img->rgb, img->depth,
+                               img->sil, img->feat, tgt->rgb, tgt->depth, tgt->label, W, b, P, mh, g->rgb, g->depth,
+                               g->sil, g->feat, g->feat_coef, part_f, part_d, mask_out, median_out)
+                  : launch_pdl(loss_kernel<D, kMaxK>, grid, LossShape<D, kMaxK>::NT, 0, st, vt, lp, img->rgb,
+                               img->depth, img->sil, img->feat, tgt->rgb, tgt->depth, tgt->label, W, b, P, mh,
+                               g->rgb, g->depth, g->sil, g->feat, g->feat_coef, part_f, part_d, mask_out,
+                               median_out);
+    if (ls) return ls;
     int rows = bx * vt.n_views;
     if (lp.ssim_coef != 0.f) {
         // the SSIM tiles add their colour-term shares as further partial rows
@@ -705,9 +720,8 @@ gs_status launch_loss(const ViewTable &vt, const LossP &lp, const gs_images *img
         if (s) return s;
         rows += ssim_blocks(vt);
     }
-    loss_finish_kernel<<<lp.K * D + lp.K + 4, 256, 0, st>>>(bx * vt.n_views, rows, lp.K, D, part_f, part_d, dW, db,
-                                                             loss_out);
-    return last_launch();
+    return launch_pdl(loss_finish_kernel, lp.K * D + lp.K + 4, 256, 0, st, bx * vt.n_views, rows, lp.K, D, part_f,
+                      part_d, dW, db, loss_out);
 }
 
 }  // namespace
@@ -773,18 +787,17 @@ gs_status dsr_value(int64_t n, const float *log_scales, float lam_big, float lam
     uint32_t *ctr = reinterpret_cast<uint32_t *>(part + 6 * kRedBlocks);
     gs_status s;
     if ((s = cuda_status(cudaMemsetAsync(ctr, 0, 2 * sizeof(uint32_t), st)))) return s;
-    dsr_stats_kernel<<<grid, 256, 0, st>>>(m, log_scales, part, out, ctr);
-    dsr_mask_kernel<<<grid, 256, 0, st>>>(m, log_scales, out, part + 2 * kRedBlocks, lam_big, lam_small, ctr + 1);
-    return last_launch();
+    if ((s = launch_pdl(dsr_stats_kernel, grid, 256, 0, st, m, log_scales, part, out, ctr))) return s;
+    return launch_pdl(dsr_mask_kernel, grid, 256, 0, st, m, log_scales, out, part + 2 * kRedBlocks, lam_big, lam_small,
+                      ctr + 1);
 }
 
 gs_status dsr_grad(int64_t n, const float *log_scales, float lam_big, float lam_small, const double *out,
                    float *d_log_scales, cudaStream_t st) {
     if (n == 0) return GS_OK;
     const int64_t m = 3 * n;
-    dsr_grad_kernel<<<std::min(ceil_div(m, 256), kRedBlocks), 256, 0, st>>>(m, log_scales, lam_big, lam_small, out,
-                                                                             d_log_scales);
-    return last_launch();
+    return launch_pdl(dsr_grad_kernel, std::min(ceil_div(m, 256), kRedBlocks), 256, 0, st, m, log_scales, lam_big,
+                      lam_small, out, d_log_scales);
 }
 }  // namespace
 }  // namespace gs
@@ -827,8 +840,7 @@ extern "C" gs_status gs_pose_grad(int64_t n, int n_views, const float *pose_part
     if (n == 0) return GS_OK;
     if (!pose_part) return GS_ERR_ARG;
     dim3 grid(std::min(ceil_div(n, 256 * 8), kPoseBlocks), 6 * n_views);
-    pose_reduce_kernel<<<grid, 256, 0, st>>>(n, pose_part, d_twist);
-    return last_launch();
+    return launch_pdl(pose_reduce_kernel, grid, 256, 0, st, n, pose_part, d_twist);
 }
 
 extern "C" gs_status gs_pose_step(int n_views, const double *d_twist, double *T_state, double *adam, int step,
@@ -839,9 +851,8 @@ extern "C" gs_status gs_pose_step(int n_views, const double *d_twist, double *T_
     // Adam bias corrections 1 - beta^step: on the host for a given step, on the
     // device (from the counter after the moments) for step 0
     const double bc1 = step ? 1.0 - pow(beta1, step) : -1.0, bc2 = step ? 1.0 - pow(beta2, step) : -1.0;
-    pose_step_kernel<<<1, kPoseLanes * n_views, 0, (cudaStream_t)stream>>>(n_views, d_twist, T_state, adam, bc1, bc2, lr[0], lr[1],
-                                                         lr[2], lr[3], lr[4], lr[5], beta1, beta2, eps, pose_f32);
-    return last_launch();
+    return launch_pdl(pose_step_kernel, 1, kPoseLanes * n_views, 0, (cudaStream_t)stream, n_views, d_twist, T_state,
+                      adam, bc1, bc2, lr[0], lr[1], lr[2], lr[3], lr[4], lr[5], beta1, beta2, eps, pose_f32);
 }
 
 // ------------------------------------------------- allocation-free loss entry

@@ -141,6 +141,8 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(ViewTable vt, Params p
                                                           const float *quats, const float *log_scales,
                                                           const float *logits, const float *pose_dev, float4 *uvdo,
                                                           float2 *uv_lo, float4 *conic, int32_t *touched) {
+    pdl_wait();     // the previous kernel's results
+    pdl_trigger();  // the next kernel may be scheduled now
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int v = blockIdx.y;
     if (g >= n) return;
@@ -188,6 +190,8 @@ __global__ void __launch_bounds__(128, 5) project_bwd_kernel(ViewTable vt, Param
                                                           const float4 *acc_rgb, int grad_mode,
                                                           float *d_means, float *d_quats, float *d_log_scales,
                                                           float *d_logits, float *d_rgb, float *pose_part) {
+    pdl_wait();     // the previous kernel's results
+    pdl_trigger();  // the next kernel may be scheduled now
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n) return;
     Shape sh;
@@ -335,11 +339,10 @@ extern "C" gs_status gs_project(const gs_gaussians *g, const gs_camera *cams, in
          reinterpret_cast<uintptr_t>(out->conic)) & 15 || (reinterpret_cast<uintptr_t>(out->uv_lo) & 7))
         return GS_ERR_ARG;
     dim3 grid(ceil_div(g->n, 256), n_views);
-    project_fwd_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(
-        vt, prm, g->n, g->means, g->quats, g->log_scales, g->opacity_logits, pose_dev,
-        reinterpret_cast<float4 *>(out->uvdo), reinterpret_cast<float2 *>(out->uv_lo),
-        reinterpret_cast<float4 *>(out->conic), out->tiles_touched);
-    return last_launch();
+    return launch_pdl(project_fwd_kernel, grid, 256, 0, (cudaStream_t)stream, vt, prm, g->n, g->means, g->quats,
+                      g->log_scales, g->opacity_logits, pose_dev, reinterpret_cast<float4 *>(out->uvdo),
+                      reinterpret_cast<float2 *>(out->uv_lo), reinterpret_cast<float4 *>(out->conic),
+                      out->tiles_touched);
 }
 
 extern "C" gs_status gs_project_bwd(const gs_gaussians *g, const gs_camera *cams, int n_views, const float *pose_dev,
@@ -365,11 +368,10 @@ extern "C" gs_status gs_project_bwd(const gs_gaussians *g, const gs_camera *cams
          reinterpret_cast<uintptr_t>(map ? out->quats : nullptr)) & 15)
         return GS_ERR_ARG;
     dim3 grid(ceil_div(g->n, 128));
-    project_bwd_kernel<<<grid, 128, 0, (cudaStream_t)stream>>>(
-        vt, prm, g->n, g->means, g->quats, g->log_scales, g->opacity_logits, pose_dev,
-        reinterpret_cast<const float4 *>(sg->uvod), reinterpret_cast<const float4 *>(sg->conic),
-        reinterpret_cast<const float4 *>(sg->rgb), grad_mode, map ? out->means : nullptr,
-        map ? out->quats : nullptr, map ? out->log_scales : nullptr, map ? out->opacity_logits : nullptr,
-        map ? out->rgb : nullptr, pose ? pose_part : nullptr);
-    return last_launch();
+    return launch_pdl(project_bwd_kernel, grid, 128, 0, (cudaStream_t)stream, vt, prm, g->n, g->means, g->quats,
+                      g->log_scales, g->opacity_logits, pose_dev, reinterpret_cast<const float4 *>(sg->uvod),
+                      reinterpret_cast<const float4 *>(sg->conic), reinterpret_cast<const float4 *>(sg->rgb),
+                      grad_mode, map ? out->means : nullptr, map ? out->quats : nullptr,
+                      map ? out->log_scales : nullptr, map ? out->opacity_logits : nullptr,
+                      map ? out->rgb : nullptr, pose ? pose_part : nullptr);
 }

@@ -125,6 +125,8 @@ struct BwdArgs {
 
 template <int D, int NP, bool MAP, typename RT, typename FT>
 __global__ void __launch_bounds__(Shape<NP>::THREADS) raster_bwd_kernel(ViewTable vt, Params prm, BwdArgs A) {
+    pdl_wait();     // the previous kernel's results
+    pdl_trigger();  // the next kernel may be scheduled now
     using LY = BwdLayout<D, NP, MAP>;
     using SH = Shape<NP>;
     constexpr int NT = SH::THREADS;
@@ -428,8 +430,7 @@ gs_status launch_bwd(const ViewTable &vt, const Params &prm, const BwdArgs &A, c
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
         if (s) return s;
     }
-    kern<<<vt.tile_off[vt.n_views], Shape<NP>::THREADS, bytes, st>>>(vt, prm, A);
-    return last_launch();
+    return launch_pdl(kern, vt.tile_off[vt.n_views], Shape<NP>::THREADS, bytes, st, vt, prm, A);
 }
 
 // Dispatch over feature dim, pixels per thread and storage for one mode.

@@ -89,6 +89,8 @@ template <int D, int NP, bool MAP, int KF> constexpr int warp_bwd_min_blocks() {
 template <int D, int NP, bool MAP, int KF, typename RT, typename FT>
 __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP, MAP, KF>())
     raster_bwd_warp_kernel(ViewTable vt, Params prm, BwdArgs A) {
+    pdl_wait();     // the previous kernel's results
+    pdl_trigger();  // the next kernel may be scheduled now
     using SH = Shape<NP>;
     using WL = WarpMapLayout<D, NP, KF, kMapSlots>;
     constexpr int F = WL::F;
@@ -547,8 +549,8 @@ __global__ void __launch_bounds__(32, warp_bwd_min_blocks<D, NP, MAP, KF>())
 template <int D, int NP, bool MAP, int KF, typename RT, typename FT>
 gs_status launch_bwd_warp(const ViewTable &vt, const Params &prm, const BwdArgs &A, cudaStream_t st) {
     const int n_tiles = vt.tile_off[vt.n_views];
-    raster_bwd_warp_kernel<D, NP, MAP, KF, RT, FT><<<n_tiles * Shape<NP>::WARPS, 32, 0, st>>>(vt, prm, A);
-    return last_launch();
+    return launch_pdl(raster_bwd_warp_kernel<D, NP, MAP, KF, RT, FT>, n_tiles * Shape<NP>::WARPS, 32, 0, st, vt, prm,
+                      A);
 }
 
 // The warp-block form: D 16 or 32, 1 or 2 pixels per thread, blend mask present; factored

@@ -215,6 +215,8 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS, fwd_min_blocks(D, NP)) ras
     const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges, int64_t P, float *o_rgb, float *o_depth,
     float *o_sil, float *o_feat, float *o_T, int32_t *o_nc, int32_t *o_nb, uint32_t *bmask, int64_t bm_stride,
     const uint32_t *__restrict__ order, int32_t *status, int64_t capacity, uint32_t *queue) {
+    pdl_wait();     // the previous kernel's results
+    pdl_trigger();  // the next kernel may be scheduled now
     const int n_tiles = vt.tile_off[vt.n_views];
     const bool failed = binning_failed(status);  // the binning overflowed or gave up: render nothing
     if constexpr (QUEUE) {
@@ -260,6 +262,8 @@ __global__ void __launch_bounds__(32, fwd_group_min_blocks(D, NP)) raster_fwd_gr
     const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges, int64_t P, float *o_rgb, float *o_depth,
     float *o_sil, float *o_feat, float *o_T, int32_t *o_nc, int32_t *o_nb, uint32_t *bmask, int64_t bm_stride,
     const uint32_t *__restrict__ order, int32_t *status, int64_t capacity, uint32_t * /*queue*/) {
+    pdl_wait();     // the previous kernel's results
+    pdl_trigger();  // the next kernel may be scheduled now
     using SH = Shape<NP, true>;  // horizontal pixel pairs
     constexpr int D4 = D / 4, DD = D > 0 ? D : 1;
     constexpr int NL = SH::PIX_GROUPS ? NP : 1;  // mask bit registers per thread
@@ -422,18 +426,17 @@ gs_status launch(const ViewTable &vt, const Params &prm, const gs_gaussians *g, 
                  const gs_binning *bins, gs_images *out, cudaStream_t st) {
     const int tiles = vt.tile_off[vt.n_views];
     const int64_t P = vt.pix_off[vt.n_views];
-    auto args = [&](auto kern, int blocks, int threads, size_t smem) {
-        kern<<<blocks, threads, smem, st>>>(
-            vt, prm, reinterpret_cast<const float4 *>(proj->uvdo), reinterpret_cast<const float2 *>(proj->uv_lo),
-            reinterpret_cast<const float4 *>(proj->conic), static_cast<const RT *>(g->rgb),
-            static_cast<const FT *>(g->feat), bins->vals, bins->ranges, P, out->rgb, out->depth, out->sil,
-            out->feat, out->T_final, out->n_contrib, out->n_blended, out->blend_mask, bins->capacity / 32 + 1,
-            bins->tile_order, bins->status, bins->capacity, bins->queue);
+    auto args = [&](auto kern, int blocks, int threads, size_t smem) -> gs_status {
+        return launch_pdl(
+            kern, blocks, threads, smem, st, vt, prm, reinterpret_cast<const float4 *>(proj->uvdo),
+            reinterpret_cast<const float2 *>(proj->uv_lo), reinterpret_cast<const float4 *>(proj->conic),
+            static_cast<const RT *>(g->rgb), static_cast<const FT *>(g->feat), bins->vals, bins->ranges, P, out->rgb,
+            out->depth, out->sil, out->feat, out->T_final, out->n_contrib, out->n_blended, out->blend_mask,
+            bins->capacity / 32 + 1, bins->tile_order, bins->status, bins->capacity, bins->queue);
     };
     if constexpr (NP <= 2) {
         if (prm.fwd_group) {
-            args(raster_fwd_group_kernel<D, NP, RT, FT>, tiles * Shape<NP>::WARPS, 32, 0);
-            return last_launch();
+            return args(raster_fwd_group_kernel<D, NP, RT, FT>, tiles * Shape<NP>::WARPS, 32, 0);
         }
     }
     // the per-tile forward with BATCH splats staged per round; batches other than 128 are built
@@ -452,11 +455,10 @@ gs_status launch(const ViewTable &vt, const Params &prm, const gs_gaussians *g, 
                     return GS_ERR_CUDA;
                 res = sms * (per_sm > 0 ? per_sm : 1);
             }
-            args(raster_fwd_kernel<D, NP, RT, FT, true, B>, tiles < res ? tiles : res, Shape<NP>::THREADS, 0);
-        } else {
-            args(raster_fwd_kernel<D, NP, RT, FT, false, B>, tiles, Shape<NP>::THREADS, 0);
+            return args(raster_fwd_kernel<D, NP, RT, FT, true, B>, tiles < res ? tiles : res, Shape<NP>::THREADS,
+                        0);
         }
-        return last_launch();
+        return args(raster_fwd_kernel<D, NP, RT, FT, false, B>, tiles, Shape<NP>::THREADS, 0);
     };
     if (prm.fwd_batch == 128) return per_tile(std::integral_constant<int, 128>());
     if constexpr (NP == 2 && D >= 16)
