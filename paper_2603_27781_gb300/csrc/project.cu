@@ -123,17 +123,15 @@ __device__ __forceinline__ void project_geo(const float mu[3], const Shape &sh, 
         o.v = fy * o.p[1] * iz + cy;
         o.ulo = o.vlo = 0.f;
     }
-    float det = o.a * o.c - o.b * o.b;
-    if (det > 1e-2f * o.a * o.c && isfinite(det)) {
-        float id = 1.f / det;
-        o.A = o.c * id; o.B = -o.b * id; o.C = o.a * id;
-    } else {
-        // near-singular Sigma2D: determinant and inverse in double precision
-        double dd = (double)o.a * (double)o.c - (double)o.b * (double)o.b;
-        if (!(dd > 0.0) || !isfinite(dd)) { o.ok = false; return; }
-        double id = 1.0 / dd;
-        o.A = (float)(o.c * id); o.B = (float)(-o.b * id); o.C = (float)(o.a * id);
-    }
+    // det = a c - b^2 by Kahan's FMA algorithm for 2x2 determinants (the rounding error of b^2,
+    // recovered exactly by a second FMA, is added back): accurate to a few units in the last
+    // place of det itself even when a c and b^2 nearly cancel (an elongated splat), so the
+    // inverse needs no wider arithmetic
+    const float bb = __fmul_rn(o.b, o.b);
+    const float det = __fadd_rn(__fmaf_rn(o.a, o.c, -bb), __fmaf_rn(-o.b, o.b, bb));
+    if (!(det > 0.f) || !isfinite(det)) { o.ok = false; return; }
+    const float id = 1.f / det;
+    o.A = o.c * id; o.B = -o.b * id; o.C = o.a * id;
     o.ok = isfinite(o.u) && isfinite(o.v) && isfinite(o.A) && isfinite(o.B) && isfinite(o.C);
 }
 
