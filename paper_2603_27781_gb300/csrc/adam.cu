@@ -84,6 +84,7 @@ __global__ void __launch_bounds__(256) adam_kernel(AdamGroups G, AdamCoef K, con
 extern "C" gs_status gs_adam_step(const gs_field_mut *f, const gs_gaussian_grads *grads, float *moments, int step,
                                   double *step_ctr, const float *lr, double beta1, double beta2, double eps,
                                   gs_stream stream) {
+    GS_NVTX_RANGE("gs_adam_step");
     using namespace gs;
     if (!f || !grads || !lr || f->n < 0 || step < 0 || (step == 0 && !step_ctr)) return GS_ERR_ARG;
     if (!(beta1 >= 0.0 && beta1 < 1.0 && beta2 >= 0.0 && beta2 < 1.0 && eps >= 0.0)) return GS_ERR_ARG;

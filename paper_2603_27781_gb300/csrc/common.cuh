@@ -4,6 +4,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <algorithm>
@@ -252,6 +253,17 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // Host helpers.
+// A named NVTX range for the duration of an entry point: a profiler's timeline shows each
+// call around its launches (nvtx3 is header-only; without a tool attached the calls cost a
+// few nanoseconds).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+#define GS_NVTX_RANGE(name) ::gs::NvtxRange gs_nvtx_range_(name)
+
 inline gs_status cuda_status(cudaError_t e) { return e == cudaSuccess ? GS_OK : GS_ERR_CUDA; }
 
 // Launches kernel<<<grid, block, smem, st>>>(args...) with programmatic stream serialization

@@ -732,6 +732,7 @@ extern "C" gs_status gs_loss_fwd_bwd(const gs_camera *cams, int n_views, int fea
                                      const gs_loss_params *lp, void *ws, size_t ws_bytes, gs_image_grads_out *grad,
                                      float *d_dec_W, float *d_dec_b, double *loss_out, float *mask_out,
                                      float *median_out, gs_stream stream) {
+    GS_NVTX_RANGE("gs_loss_fwd_bwd");
     using namespace gs;
     cudaStream_t st = (cudaStream_t)stream;
     ViewTable vt;
@@ -804,6 +805,7 @@ gs_status dsr_grad(int64_t n, const float *log_scales, float lam_big, float lam_
 
 extern "C" gs_status gs_dsr(int64_t n, const float *log_scales, float lam_big, float lam_small, void *ws,
                             size_t ws_bytes, float *d_log_scales, double *out, gs_stream stream) {
+    GS_NVTX_RANGE("gs_dsr");
     using namespace gs;
     cudaStream_t st = (cudaStream_t)stream;
     if (n < 0 || !out || !ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return GS_ERR_ARG;
@@ -818,6 +820,7 @@ extern "C" gs_status gs_dsr(int64_t n, const float *log_scales, float lam_big, f
 
 extern "C" gs_status gs_dsr_value(int64_t n, const float *log_scales, float lam_big, float lam_small, void *scratch,
                                   double *out, gs_stream stream) {
+    GS_NVTX_RANGE("gs_dsr_value");
     using namespace gs;
     if (n < 0 || !out || !scratch || (reinterpret_cast<uintptr_t>(scratch) & 255) || (n > 0 && !log_scales))
         return GS_ERR_ARG;
@@ -826,12 +829,14 @@ extern "C" gs_status gs_dsr_value(int64_t n, const float *log_scales, float lam_
 
 extern "C" gs_status gs_dsr_grad(int64_t n, const float *log_scales, float lam_big, float lam_small, const double *out,
                                  float *d_log_scales, gs_stream stream) {
+    GS_NVTX_RANGE("gs_dsr_grad");
     using namespace gs;
     if (n < 0 || !out || (n > 0 && (!log_scales || !d_log_scales))) return GS_ERR_ARG;
     return dsr_grad(n, log_scales, lam_big, lam_small, out, d_log_scales, (cudaStream_t)stream);
 }
 
 extern "C" gs_status gs_pose_grad(int64_t n, int n_views, const float *pose_part, double *d_twist, gs_stream stream) {
+    GS_NVTX_RANGE("gs_pose_grad");
     using namespace gs;
     cudaStream_t st = (cudaStream_t)stream;
     if (n < 0 || n_views < 1 || n_views > kMaxViews || !d_twist) return GS_ERR_ARG;
@@ -846,6 +851,7 @@ extern "C" gs_status gs_pose_grad(int64_t n, int n_views, const float *pose_part
 extern "C" gs_status gs_pose_step(int n_views, const double *d_twist, double *T_state, double *adam, int step,
                                   const double *lr, double beta1, double beta2, double eps, float *pose_f32,
                                   gs_stream stream) {
+    GS_NVTX_RANGE("gs_pose_step");
     using namespace gs;
     if (n_views < 1 || n_views > kMaxViews || !d_twist || !T_state || !adam || !lr || step < 0) return GS_ERR_ARG;
     // Adam bias corrections 1 - beta^step: on the host for a given step, on the
@@ -906,6 +912,7 @@ extern "C" gs_status gs_loss_fwd_bwd_noalloc(const gs_camera *cams, int n_views,
                                              const gs_loss_params *lp, gs_image_grads_out *grad, float *d_dec_W,
                                              float *d_dec_b, double *loss_out, float *mask_out, float *median_out,
                                              gs_stream stream) {
+    GS_NVTX_RANGE("gs_loss_fwd_bwd_noalloc");
     using namespace gs;
     cudaStream_t st = (cudaStream_t)stream;
     ViewTable vt;
@@ -1082,6 +1089,7 @@ extern "C" gs_status gs_expand(const gs_camera *cams, int n_views, const gs_imag
                                float tau_unobs, const float *feat_init, int64_t n_existing, gs_field_mut *field,
                                int64_t *n_new, int64_t *src_pix, int32_t *status, void *ws, size_t ws_bytes,
                                gs_stream stream) {
+    GS_NVTX_RANGE("gs_expand");
     using namespace gs;
     ViewTable vt;
     if (!img || !tgt || !field || !n_new || !status || !make_view_table(cams, n_views, 0, &vt)) return GS_ERR_ARG;

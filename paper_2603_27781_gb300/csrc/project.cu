@@ -322,6 +322,7 @@ __global__ void __launch_bounds__(128, 5) project_bwd_kernel(ViewTable vt, Param
 
 extern "C" gs_status gs_project(const gs_gaussians *g, const gs_camera *cams, int n_views, const float *pose_dev,
                                 const gs_raster_params *p, gs_projected *out, gs_stream stream) {
+    GS_NVTX_RANGE("gs_project");
     using namespace gs;
     if (!g || !out || g->n < 0) return GS_ERR_ARG;
     ViewTable vt;
@@ -346,6 +347,7 @@ extern "C" gs_status gs_project(const gs_gaussians *g, const gs_camera *cams, in
 extern "C" gs_status gs_project_bwd(const gs_gaussians *g, const gs_camera *cams, int n_views, const float *pose_dev,
                                     const gs_raster_params *p, int grad_mode, const gs_splat_grads *sg,
                                     gs_gaussian_grads *out, float *pose_part, gs_stream stream) {
+    GS_NVTX_RANGE("gs_project_bwd");
     using namespace gs;
     if (!g || !sg || g->n < 0) return GS_ERR_ARG;
     if (grad_mode <= 0 || grad_mode > (GS_GRAD_MAP | GS_GRAD_POSE)) return GS_ERR_ARG;

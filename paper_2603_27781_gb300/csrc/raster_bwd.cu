@@ -10,6 +10,7 @@ extern "C" gs_status gs_render_bwd(const gs_gaussians *g, const gs_projected *pr
                                    const gs_camera *cams, int n_views, const gs_raster_params *p, int grad_mode,
                                    const gs_images *fwd, const gs_image_grads *dL, gs_splat_grads *sg, float *d_feat,
                                    gs_stream stream) {
+    GS_NVTX_RANGE("gs_render_bwd");
     using namespace gs;
     cudaStream_t st = (cudaStream_t)stream;
     if (!g || !proj || !bins || !fwd || !dL || !sg || g->n < 0) return GS_ERR_ARG;

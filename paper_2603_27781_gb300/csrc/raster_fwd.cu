@@ -493,6 +493,7 @@ bool storage_ok(const gs_gaussians *g) {
 extern "C" gs_status gs_render_fwd(const gs_gaussians *g, const gs_projected *proj, const gs_binning *bins,
                                    const gs_camera *cams, int n_views, const gs_raster_params *p, gs_images *out,
                                    gs_stream stream) {
+    GS_NVTX_RANGE("gs_render_fwd");
     using namespace gs;
     if (!g || !proj || !bins || !out || g->n < 0) return GS_ERR_ARG;
     ViewTable vt;

@@ -88,6 +88,7 @@ extern "C" gs_status gs_rskm_draw(const gs_keyframes *kf, int32_t n_kf, int32_t 
                                   const uint32_t *draws, int64_t n_draws, int32_t *state, int32_t *picked,
                                   float *out_rgb, float *out_depth, uint8_t *out_label, float *pose_f32,
                                   gs_stream stream) {
+    GS_NVTX_RANGE("gs_rskm_draw");
     if (!kf || !kf->rgb || !kf->depth || !kf->label || !kf->T_cw || kf->P <= 0 || kf->capacity <= 0)
         return GS_ERR_ARG;
     if (n_kf < 0 || n_kf > kf->capacity || cur_slot < 0 || cur_slot > n_kf || cur_slot >= kf->capacity)

@@ -591,6 +591,7 @@ gs_status write_ranges_order(const uint32_t *counts, const gs_binning *out, int6
 extern "C" gs_status gs_bin_sort(int64_t n, const gs_projected *proj, const gs_camera *cams, int n_views,
                                  const gs_raster_params *p, void *ws, size_t ws_bytes, gs_binning *out,
                                  gs_stream stream) {
+    GS_NVTX_RANGE("gs_bin_sort");
     using namespace gs;
     cudaStream_t st = (cudaStream_t)stream;
     ViewTable vt;
