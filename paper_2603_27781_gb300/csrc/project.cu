@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(ViewTable vt, Params p
 
 // Register cap: five 128-thread blocks per SM (96 registers, no spills) instead of four
 // at 124 registers: the kernel is latency-bound and the extra warps hide it (-13 %).
-__global__ void __launch_bounds__(128, 5) project_bwd_kernel(ViewTable vt, Params prm, int64_t n, const float *means,
+__global__ void __launch_bounds__(128, 6) project_bwd_kernel(ViewTable vt, Params prm, int64_t n, const float *means,
                                                           const float *quats, const float *log_scales,
                                                           const float *logits, const float *pose_dev,
                                                           const float4 *acc_uvod, const float4 *acc_conic,
