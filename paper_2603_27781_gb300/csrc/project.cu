@@ -179,8 +179,9 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(ViewTable vt, Params p
     touched[item] = tt;
 }
 
-// Register cap: five 128-thread blocks per SM (96 registers, no spills) instead of four
-// at 124 registers: the kernel is latency-bound and the extra warps hide it (-13 %).
+// Register cap: six 128-thread blocks per SM (80 registers, 16 bytes spilled) instead of
+// four at 124 registers: the kernel is latency-bound and the extra warps hide it (five
+// blocks at 96 registers: -13 %; six: a further -8 %; seven spill 80 bytes).
 __global__ void __launch_bounds__(128, 6) project_bwd_kernel(ViewTable vt, Params prm, int64_t n, const float *means,
                                                           const float *quats, const float *log_scales,
                                                           const float *logits, const float *pose_dev,
