@@ -314,9 +314,11 @@ struct WsLayout {
 };
 
 constexpr int kLossBlocks = 1024;
-constexpr int kSortThreads = 256;
+constexpr int kSortThreads = 256;       // threads of a depth-sort pass block
+constexpr int kSortThreadsInst = 1024;  // threads of a tile-sort pass block
 constexpr int kSortIPT = 8;
 constexpr int kSortTile = kSortThreads * kSortIPT;
+constexpr int kSortTileInst = kSortThreadsInst * kSortIPT;
 constexpr int kScanIPT = 8;
 constexpr int kScanBlock = 256 * kScanIPT;
 

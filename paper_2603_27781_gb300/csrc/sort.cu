@@ -13,8 +13,9 @@
 //
 // The digit histograms of every pass are counted by the kernels that write the keys (the
 // compaction for the depth keys, the emission for the tile keys) with shared-memory atomics.
-// Each radix pass is one kernel: a block ranks its 2048 keys stably within the block (peer
-// lanes of a digit from eight bit ballots + per-warp digit counters), publishes its per-digit
+// Each radix pass is one kernel: a block ranks its keys (2048 in a depth pass, 8192 in a tile
+// pass) stably within the block (peer lanes of a digit from match_any + per-warp digit
+// counters), publishes its per-digit
 // counts, finds its global offsets by a chained look-back over earlier blocks,
 // and scatters through shared memory.  Blocks take tile numbers from an atomic
 // counter so a block only waits on blocks that are already running; every wait
@@ -33,9 +34,12 @@ constexpr uint32_t kFlagPre = 2u << 30;
 constexpr uint32_t kValMask = (1u << 30) - 1;
 
 // ----------------------------------------------------------- block scan helper
-// Exclusive scan of one value per thread over a 256-thread block; returns the
-// prefix and writes the block total to *total.
+// Exclusive scan of one value per thread over a block of NT threads (256 unless given);
+// returns the prefix and writes the block total to *total.  s_warp holds NT / 32 + 1 values.
+template <int NT = 256>
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t *total, uint32_t *s_warp) {
+    constexpr int W = NT / 32;
+    static_assert(NT % 32 == 0 && W <= 32, "block of at most 32 warps");
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint32_t inc = x;
 #pragma unroll
@@ -46,18 +50,18 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t *t
     if (lane == 31) s_warp[w] = inc;
     __syncthreads();
     if (w == 0) {
-        uint32_t t = lane < 8 ? s_warp[lane] : 0, ti = t;
+        uint32_t t = lane < W ? s_warp[lane] : 0, ti = t;
 #pragma unroll
-        for (int o = 1; o < 8; o <<= 1) {
+        for (int o = 1; o < W; o <<= 1) {
             uint32_t y = __shfl_up_sync(0xffffffffu, ti, o);
             if (lane >= o) ti += y;
         }
-        if (lane < 8) s_warp[lane] = ti - t;
-        if (lane == 7) s_warp[8] = ti;
+        if (lane < W) s_warp[lane] = ti - t;
+        if (lane == W - 1) s_warp[W] = ti;
     }
     __syncthreads();
     uint32_t r = s_warp[w] + inc - x;
-    *total = s_warp[8];
+    *total = s_warp[W];
     __syncthreads();
     return r;
 }
@@ -303,42 +307,57 @@ __global__ void __launch_bounds__(kEmitBlock) emit_kernel(ViewTable vt, const ui
 }
 
 // ------------------------------------------------------------------ radix sort
-__global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint32_t *keys_in, const uint32_t *vals_in,
-                                                                uint32_t *keys_out, uint32_t *vals_out,
-                                                                const uint32_t *count_ptr, int shift,
-                                                                const uint32_t *pass_hist, uint32_t *tile_ctr,
-                                                                uint32_t *lookback, int32_t *status, int spin_limit,
-                                                                uint32_t *tile_counts, uint32_t n_tiles) {
+// Shared memory of a radix-pass block of NT threads (dynamic: 99 KB at NT = 1024).
+template <int NT>
+struct SortSmem {
+    uint32_t keys[NT * kSortIPT];
+    uint32_t vals[NT * kSortIPT];
+    uint32_t whist[NT / 32][256];
+    uint32_t excl[256];   // block-local exclusive digit offsets
+    uint32_t glob[256];   // global destination of the digit's first key in this block
+    uint32_t dbase[256];  // global exclusive digit base of the pass
+    uint32_t warp[NT / 32 + 1];
+    uint32_t tile;
+    int failed;
+};
+
+// One radix pass, NT threads per block and kSortIPT keys per thread: 256 threads for the depth
+// passes over the visible items, 1024 for the tile passes over the instances, where a quarter
+// as many blocks means a sixteenth of the look-back's reads (every block starts at once and
+// reads back through about half of the blocks before it).
+template <int NT>
+__global__ void __launch_bounds__(NT) onesweep_kernel(const uint32_t *keys_in, const uint32_t *vals_in,
+                                                      uint32_t *keys_out, uint32_t *vals_out,
+                                                      const uint32_t *count_ptr, int shift,
+                                                      const uint32_t *pass_hist, uint32_t *tile_ctr,
+                                                      uint32_t *lookback, int32_t *status, int spin_limit,
+                                                      uint32_t *tile_counts, uint32_t n_tiles) {
     pdl_wait();     // the previous kernel's results
     pdl_trigger();  // the next kernel may be scheduled now
-    constexpr int W = kSortThreads / 32;
-    __shared__ uint32_t s_keys[kSortTile];
-    __shared__ uint32_t s_vals[kSortTile];
-    __shared__ uint32_t s_whist[W][256];
-    __shared__ uint32_t s_excl[256];   // block-local exclusive digit offsets
-    __shared__ uint32_t s_glob[256];   // global destination of the digit's first key in this block
-    __shared__ uint32_t s_dbase[256];  // global exclusive digit base of the pass
-    __shared__ uint32_t s_warp[9];
-    __shared__ uint32_t s_tile;
-    __shared__ int s_failed;
+    constexpr int W = NT / 32, TILE = NT * kSortIPT;
+    static_assert(NT >= 256, "one thread per digit");
+    extern __shared__ __align__(16) unsigned char sort_smem[];
+    SortSmem<NT> &S = *reinterpret_cast<SortSmem<NT> *>(sort_smem);
+    uint32_t *s_keys = S.keys, *s_vals = S.vals, *s_excl = S.excl, *s_glob = S.glob, *s_dbase = S.dbase;
+    uint32_t(*s_whist)[256] = S.whist;
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     if (tid == 0) {
-        s_tile = atomicAdd(tile_ctr, 1u);
-        s_failed = binning_failed(status);
+        S.tile = atomicAdd(tile_ctr, 1u);
+        S.failed = binning_failed(status);
     }
-    for (int i = tid; i < W * 256; i += kSortThreads) (&s_whist[0][0])[i] = 0;
+    for (int i = tid; i < W * 256; i += NT) (&s_whist[0][0])[i] = 0;
     __syncthreads();
-    const uint32_t tile = s_tile;
-    if (s_failed) {
+    const uint32_t tile = S.tile;
+    if (S.failed) {
         // an earlier wait gave up (or the count overflowed): this pass's output is not used.  The
         // block still publishes an inclusive prefix (0: never more than the true one, so a block
         // that adds it scatters in bounds) so that no running block waits for it.
-        st_relaxed(lookback + (size_t)tile * 256 + tid, kFlagPre);
+        if (tid < 256) st_relaxed(lookback + (size_t)tile * 256 + tid, kFlagPre);
         return;
     }
     const int64_t n = *count_ptr;
-    const int64_t base = (int64_t)tile * kSortTile;
+    const int64_t base = (int64_t)tile * TILE;
     if (base >= n) return;
 
     uint32_t key[kSortIPT], val[kSortIPT], rank[kSortIPT];
@@ -366,23 +385,28 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint32_t *
     }
     __syncthreads();
 
-    // per-digit: warp-exclusive offsets and the block's count, published at once for later tiles
-    const int d = tid;  // kSortThreads == 256 == radix
-    uint32_t cnt = 0;
+    // per-digit (thread d < 256): warp-exclusive offsets and the block's count, published at once
+    // for later tiles
+    const int d = tid;
+    uint32_t cnt = 0, hist_d = 0;
+    uint32_t *my = lookback + (size_t)tile * 256 + (d & 255);
+    if (d < 256) {
 #pragma unroll
-    for (int ww = 0; ww < W; ++ww) {
-        uint32_t c = s_whist[ww][d];
-        s_whist[ww][d] = cnt;
-        cnt += c;
+        for (int ww = 0; ww < W; ++ww) {
+            uint32_t c = s_whist[ww][d];
+            s_whist[ww][d] = cnt;
+            cnt += c;
+        }
+        st_relaxed(my, (tile == 0 ? kFlagPre : kFlagAgg) | cnt);
+        hist_d = pass_hist[d];
     }
-    uint32_t *my = lookback + (size_t)tile * 256 + d;
-    st_relaxed(my, (tile == 0 ? kFlagPre : kFlagAgg) | cnt);
     // block-exclusive digit offsets and the pass's digit bases
     uint32_t lb_tot;
-    uint32_t hist_d = pass_hist[d];
-    s_excl[d] = block_exclusive_scan(cnt, &lb_tot, s_warp);
+    const uint32_t ex = block_exclusive_scan<NT>(cnt, &lb_tot, S.warp);
+    if (d < 256) s_excl[d] = ex;
     uint32_t hist_tot;
-    s_dbase[d] = block_exclusive_scan(hist_d, &hist_tot, s_warp);  // its barriers publish s_excl
+    const uint32_t db = block_exclusive_scan<NT>(hist_d, &hist_tot, S.warp);  // its barriers publish s_excl
+    if (d < 256) s_dbase[d] = db;
 
     // local scatter by digit into shared memory (the keys leave the registers before the wait)
 #pragma unroll
@@ -400,7 +424,7 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint32_t *
     // (all tiles start together, so the chain is as long as the tile number over kWin); spin
     // (bounded) only on a tile that has not published its count yet
     uint32_t prefix = 0;
-    if (tile != 0) {
+    if (tile != 0 && d < 256) {
         constexpr int kWin = 8;
         int64_t t = (int64_t)tile - 1;
         bool done = false, timeout = false;
@@ -438,12 +462,12 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint32_t *
         if (timeout) set_status(status, GS_ERR_TIMEOUT);
         st_relaxed(my, kFlagPre | (prefix + cnt));
     }
-    s_glob[d] = s_dbase[d] + prefix;
+    if (d < 256) s_glob[d] = s_dbase[d] + prefix;
     __syncthreads();
 
     // coalesced-by-run global writes
-    int tile_n = (int)min((int64_t)kSortTile, n - base);
-    for (int i = tid; i < tile_n; i += kSortThreads) {
+    int tile_n = (int)min((int64_t)TILE, n - base);
+    for (int i = tid; i < tile_n; i += NT) {
         uint32_t k = s_keys[i];
         uint32_t dd = (k >> shift) & 255u;
         uint32_t dst = s_glob[dd] + (uint32_t)i - s_excl[dd];
@@ -482,14 +506,28 @@ struct SortBufs {
 // digit histograms of every pass (hist [n_passes][256], written by the kernel that
 // produced the keys).  Input in (k0, v0); output lands in (k0, v0) if n_passes is even,
 // else (k1, v1).
+template <int NT>
 gs_status radix_sort(SortBufs b, const uint32_t *count_ptr, int64_t max_count, int n_passes, const uint32_t *hist,
                      uint32_t *lookback, int lb_tiles, uint32_t *tile_ctrs, int32_t *status, int spin_limit,
                      cudaStream_t st, uint32_t *tile_counts = nullptr, uint32_t n_tiles = 0) {
     if (max_count <= 0 || n_passes <= 0) return GS_OK;
-    int grid = ceil_div(max_count, kSortTile);
+    constexpr size_t smem = sizeof(SortSmem<NT>);
+    if (smem > 48 * 1024) {
+        // above the static limit: opted in once per device
+        static bool opted[64] = {false};
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return GS_ERR_CUDA;
+        if (dev < 0 || dev >= 64 || !opted[dev]) {
+            if (cudaFuncSetAttribute(onesweep_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                cudaSuccess)
+                return GS_ERR_CUDA;
+            if (dev >= 0 && dev < 64) opted[dev] = true;
+        }
+    }
+    int grid = ceil_div(max_count, (int64_t)NT * kSortIPT);
     uint32_t *ki = b.k0, *vi = b.v0, *ko = b.k1, *vo = b.v1;
     for (int p = 0; p < n_passes; ++p) {
-        const gs_status s = launch_pdl(onesweep_kernel, grid, kSortThreads, 0, st, ki, vi, ko, vo, count_ptr, 8 * p,
+        const gs_status s = launch_pdl(onesweep_kernel<NT>, grid, NT, smem, st, ki, vi, ko, vo, count_ptr, 8 * p,
                                        hist + 256 * p, tile_ctrs + p, lookback + (size_t)p * lb_tiles * 256, status,
                                        spin_limit, p == n_passes - 1 ? tile_counts : nullptr, n_tiles);
         if (s) return s;
@@ -640,7 +678,7 @@ extern "C" gs_status gs_bin_sort(int64_t n, const gs_projected *proj, const gs_c
         return s;
 
     // 2. stable sort of the visible items by depth (4 passes: result in dk_a/dv_a)
-    if ((s = radix_sort({dk_a, dv_a, dk_b, dv_b}, counters + CTR_NVIS, vn, 4, hist, lookback, L.lb_tiles_depth,
+    if ((s = radix_sort<kSortThreads>({dk_a, dv_a, dk_b, dv_b}, counters + CTR_NVIS, vn, 4, hist, lookback, L.lb_tiles_depth,
                         counters + CTR_TILE, out->status, prm.spin_limit, st)))
         return s;
     const uint32_t *sorted_items = dv_a;
@@ -668,7 +706,7 @@ extern "C" gs_status gs_bin_sort(int64_t n, const gs_projected *proj, const gs_c
     if (out->capacity == 0) return write_ranges_order(tile_counts, out, total_tiles, st);
 
     // 4. stable sort of the instances by tile id
-    if ((s = radix_sort({tk_a, emit_vals, tk_b, other_vals}, counters + CTR_M, out->capacity, tile_passes,
+    if ((s = radix_sort<kSortThreadsInst>({tk_a, emit_vals, tk_b, other_vals}, counters + CTR_M, out->capacity, tile_passes,
                         hist + 4 * 256, lookback + (size_t)4 * L.lb_tiles_depth * 256, L.lb_tiles_inst,
                         counters + CTR_TILE + 4, out->status, prm.spin_limit, st, tile_counts, (uint32_t)total_tiles)))
         return s;

@@ -720,12 +720,13 @@ def test_capacity_overflow_is_reported():
 
 def test_bounded_wait_that_gives_up_reports_timeout_and_renders_nothing():
     """With the spin limit's test hook every radix-sort block after the first gives up its
-    look-back at once: the binning reports GS_ERR_TIMEOUT, the ranges stay empty, and the blend
+    look-back at once (8,000 visible Gaussians and about 31,600 instances: several blocks in
+    every pass): the binning reports GS_ERR_TIMEOUT, the ranges stay empty, and the blend
     kernels leave the images and the gradients as they were (the images keep a sentinel, the
     zeroed gradients stay zero).  The same renderer then renders normally again."""
-    gs, cam = C.box_case(2000, 16, 64, 48, 60.0)
+    gs, cam = C.box_case(8000, 16, 160, 120, 150.0)
     field, r = C.gpu_forward(gs, cam, C.params_pair()[0])
-    assert r.instances() > 2 * 2048                   # the tile sort has several blocks
+    assert r.instances() > 2 * 8192                   # the tile sort has several 8192-key blocks
     good = {k: v.clone() for k, v in r.images().items()}
     for t in (r.img_rgb, r.img_depth, r.img_sil, r.img_feat, r.img_T):
         t.fill_(-7.0)
