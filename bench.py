@@ -303,13 +303,15 @@ class FormJob:
     def step(self):
         r, f, w = self.r, self.field, self.w
         fac = r.use_factored(self.W)
-        # the DSR's value (log-scales only) on the side stream beside the rest of the step
-        r.side_start(lambda s: r.dsr_value(f, w.big, w.small, s))
+        # on the side stream beside the forward half: the clearing of the blend backward's sums
+        # and the DSR's value (log-scales only)
+        r.side_start(lambda s: (r.clear_grads(f, self.mode, s), r.dsr_value(f, w.big, w.small, s)))
         r.project(f)
         r.bin_sort()
         r.render_fwd(f)
         r.loss(self.targets, self.W, self.b, w, factored=fac)
-        r.render_bwd(f, self.mode, factored=fac)
+        r.side_join()
+        r.render_bwd(f, self.mode, factored=fac, accumulate=True)
         r.project_bwd(f, self.mode)
         r.side_by_side(lambda s: r.dsr_grad(f, w.big, w.small, s),
                        lambda: (r.pose_grad(), r.pose_step(self.T_state, self.adam, 0, pose_f32=self.pose_f32)))
@@ -669,8 +671,9 @@ def run_ours(args, rank, world, local_rank):
         tg = targets if tg is None else tg
         rec = (lambda i: ev[i].record(stream)) if ev is not None else (lambda i: None)
         rec(0)
-        # the DSR's value (log-scales only) on the renderer's side stream beside the whole step
-        r.side_start(lambda s: r.dsr_value(f, w.big, w.small, s))
+        # on the renderer's side stream beside the forward half: the clearing of the blend
+        # backward's sums and the DSR's value (log-scales only)
+        r.side_start(lambda s: (r.clear_grads(f, mode, s), r.dsr_value(f, w.big, w.small, s)))
         r.project(f)
         rec(1)
         r.bin_sort()
@@ -680,7 +683,8 @@ def run_ours(args, rank, world, local_rank):
         fac = r.use_factored(W)
         r.loss(tg, W, b, w, factored=fac)
         rec(4)
-        r.render_bwd(f, mode, factored=fac)
+        r.side_join()
+        r.render_bwd(f, mode, factored=fac, accumulate=True)
         rec(5)
         r.project_bwd(f, mode)
         rec(6)

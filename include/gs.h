@@ -58,8 +58,11 @@ typedef enum { GS_F32 = 0, GS_BF16 = 1, GS_F16 = 2 } gs_dtype;
 
 /* gs_render_bwd modes (bit set).  GS3LAM optimises poses and the field
  * separately (Sec. 3.2.3): tracking needs only the pose twist, mapping only
- * the Gaussian parameters. */
-enum { GS_GRAD_MAP = 1, GS_GRAD_POSE = 2 };
+ * the Gaussian parameters.  GS_GRAD_ACCUMULATE (with either): gs_render_bwd
+ * adds to sg and d_feat as they are instead of first setting them to zero, for
+ * a caller that cleared them beforehand with gs_splat_grads_clear (on another
+ * stream, say, beside the forward blend). */
+enum { GS_GRAD_MAP = 1, GS_GRAD_POSE = 2, GS_GRAD_ACCUMULATE = 4 };
 
 /* Pinhole camera.  T_cw is the row-major 4x4 world-to-camera transform
  * (Sec. 3.2.1), OpenCV axes: x right, y down, z forward.  Pixel (x, y) samples
@@ -360,12 +363,22 @@ typedef struct {
  * blended value behind a splat, d out / d alpha = T (x - S).  Per-splat
  * gradients are reduced across the warp and the CTA before one atomic add per
  * (tile, splat).  Overwrites sg (rgb only with GS_GRAD_MAP) and, with
- * GS_GRAD_MAP, d_feat (f32 [n, feat_dim], summed over views).  fwd must be the
+ * GS_GRAD_MAP, d_feat (f32 [n, feat_dim], summed over views); adds to them
+ * with GS_GRAD_ACCUMULATE.  fwd must be the
  * gs_render_fwd output of the same inputs (T_final, n_contrib are read). */
 gs_status gs_render_bwd(const gs_gaussians *g, const gs_projected *proj, const gs_binning *bins,
                         const gs_camera *cams, int n_views, const gs_raster_params *p, int grad_mode,
                         const gs_images *fwd, const gs_image_grads *dL, gs_splat_grads *sg, float *d_feat,
                         gs_stream stream);
+
+/* Sets to zero what gs_render_bwd with the same g, n_views and grad_mode
+ * (GS_GRAD_MAP and/or GS_GRAD_POSE) accumulates into: sg->uvod and sg->conic
+ * (n_views * g->n float4 each) and, with GS_GRAD_MAP, sg->rgb (g->n float4)
+ * and d_feat (g->n * feat_dim f32; may be NULL when feat_dim is 0).  Device
+ * buffers, 16-byte aligned, owned by the caller; asynchronous on stream.
+ * Returns GS_ERR_ARG for a bad mode, a NULL or misaligned buffer. */
+gs_status gs_splat_grads_clear(const gs_gaussians *g, int n_views, int grad_mode, gs_splat_grads *sg,
+                               float *d_feat, gs_stream stream);
 
 /* Backward of the projection (chain rule of supp. B.1, per factor): from the
  * per-splat gradients to the 3D parameters, summed over views.  GS_GRAD_MAP

@@ -19,7 +19,7 @@ GS_BWD_BLOCKS_DEFAULT, GS_BWD_BLOCKS_GROUP, GS_BWD_BLOCKS_TILE, GS_BLOCKS_QUEUE 
 GS_JACOBIAN_CLAMPED, GS_JACOBIAN_EXACT = 0, 1
 GS_F32, GS_BF16, GS_F16 = 0, 1, 2
 GS_DSR_SCRATCH_BYTES = 24832
-GS_GRAD_MAP, GS_GRAD_POSE = 1, 2
+GS_GRAD_MAP, GS_GRAD_POSE, GS_GRAD_ACCUMULATE = 1, 2, 4
 
 
 class gs_camera(Structure):
@@ -109,6 +109,7 @@ _SIGNATURES = {
     "gs_render_bwd": (c_int, [_P(gs_gaussians), _P(gs_projected), _P(gs_binning), _P(gs_camera), c_int,
                               _P(gs_raster_params), c_int, _P(gs_images), _P(gs_image_grads), _P(gs_splat_grads),
                               c_void_p, c_void_p]),
+    "gs_splat_grads_clear": (c_int, [_P(gs_gaussians), c_int, c_int, _P(gs_splat_grads), c_void_p, c_void_p]),
     "gs_project_bwd": (c_int, [_P(gs_gaussians), _P(gs_camera), c_int, c_void_p, _P(gs_raster_params), c_int,
                                _P(gs_splat_grads), _P(gs_gaussian_grads), c_void_p, c_void_p]),
     "gs_pose_grad": (c_int, [c_int64, c_int, c_void_p, c_void_p, c_void_p]),
@@ -180,6 +181,7 @@ gs_project = _wrap("gs_project")
 gs_bin_sort = _wrap("gs_bin_sort")
 gs_render_fwd = _wrap("gs_render_fwd")
 gs_render_bwd = _wrap("gs_render_bwd")
+gs_splat_grads_clear = _wrap("gs_splat_grads_clear")
 gs_project_bwd = _wrap("gs_project_bwd")
 gs_pose_grad = _wrap("gs_pose_grad")
 gs_loss_fwd_bwd = _wrap("gs_loss_fwd_bwd")

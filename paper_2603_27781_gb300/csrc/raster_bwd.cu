@@ -6,6 +6,39 @@ namespace gs {
 bool storage_ok(const gs_gaussians *g);
 }  // namespace gs
 
+namespace gs {
+// Zeroes the sums gs_render_bwd accumulates into (vn = n_views * g->n items).
+static gs_status clear_splat_grads(const gs_gaussians *g, int64_t vn, bool map, gs_splat_grads *sg, float *d_feat,
+                                   cudaStream_t st) {
+    gs_status s;
+    if ((s = cuda_status(cudaMemsetAsync(sg->uvod, 0, sizeof(float4) * vn, st)))) return s;
+    if ((s = cuda_status(cudaMemsetAsync(sg->conic, 0, sizeof(float4) * vn, st)))) return s;
+    if (map) {
+        if ((s = cuda_status(cudaMemsetAsync(sg->rgb, 0, sizeof(float4) * g->n, st)))) return s;
+        if (g->feat_dim && (s = cuda_status(cudaMemsetAsync(d_feat, 0, sizeof(float) * g->feat_dim * g->n, st))))
+            return s;
+    }
+    return GS_OK;
+}
+}  // namespace gs
+
+extern "C" gs_status gs_splat_grads_clear(const gs_gaussians *g, int n_views, int grad_mode, gs_splat_grads *sg,
+                                          float *d_feat, gs_stream stream) {
+    GS_NVTX_RANGE("gs_splat_grads_clear");
+    using namespace gs;
+    if (!g || !sg || g->n < 0 || n_views < 1 || n_views > kMaxViews) return GS_ERR_ARG;
+    if ((grad_mode & ~(GS_GRAD_MAP | GS_GRAD_POSE | GS_GRAD_ACCUMULATE)) || !(grad_mode & (GS_GRAD_MAP | GS_GRAD_POSE)))
+        return GS_ERR_ARG;
+    if (!feat_dim_ok(g->feat_dim)) return GS_ERR_UNSUPPORTED;
+    const bool map = grad_mode & GS_GRAD_MAP;
+    if (g->n == 0) return GS_OK;
+    if (!sg->uvod || !sg->conic || (map && (!sg->rgb || (g->feat_dim && !d_feat)))) return GS_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(sg->uvod) | reinterpret_cast<uintptr_t>(sg->conic) |
+         reinterpret_cast<uintptr_t>(sg->rgb) | reinterpret_cast<uintptr_t>(d_feat)) & 15)
+        return GS_ERR_ARG;
+    return clear_splat_grads(g, (int64_t)n_views * g->n, map, sg, d_feat, (cudaStream_t)stream);
+}
+
 extern "C" gs_status gs_render_bwd(const gs_gaussians *g, const gs_projected *proj, const gs_binning *bins,
                                    const gs_camera *cams, int n_views, const gs_raster_params *p, int grad_mode,
                                    const gs_images *fwd, const gs_image_grads *dL, gs_splat_grads *sg, float *d_feat,
@@ -14,7 +47,9 @@ extern "C" gs_status gs_render_bwd(const gs_gaussians *g, const gs_projected *pr
     using namespace gs;
     cudaStream_t st = (cudaStream_t)stream;
     if (!g || !proj || !bins || !fwd || !dL || !sg || g->n < 0) return GS_ERR_ARG;
-    if (grad_mode <= 0 || grad_mode > (GS_GRAD_MAP | GS_GRAD_POSE)) return GS_ERR_ARG;
+    if ((grad_mode & ~(GS_GRAD_MAP | GS_GRAD_POSE | GS_GRAD_ACCUMULATE)) || !(grad_mode & (GS_GRAD_MAP | GS_GRAD_POSE)))
+        return GS_ERR_ARG;
+    const bool accumulate = grad_mode & GS_GRAD_ACCUMULATE;
     ViewTable vt;
     Params prm;
     if (!make_view_table(cams, n_views, g->n, &vt) || !make_params(p, &prm)) return GS_ERR_ARG;
@@ -37,13 +72,7 @@ extern "C" gs_status gs_render_bwd(const gs_gaussians *g, const gs_projected *pr
     float4 *acc_conic = reinterpret_cast<float4 *>(sg->conic);
     float4 *acc_rgb = reinterpret_cast<float4 *>(sg->rgb);
     gs_status s;
-    if ((s = cuda_status(cudaMemsetAsync(acc_uvod, 0, sizeof(float4) * vn, st)))) return s;
-    if ((s = cuda_status(cudaMemsetAsync(acc_conic, 0, sizeof(float4) * vn, st)))) return s;
-    if (map) {
-        if ((s = cuda_status(cudaMemsetAsync(acc_rgb, 0, sizeof(float4) * g->n, st)))) return s;
-        if (g->feat_dim && (s = cuda_status(cudaMemsetAsync(d_feat, 0, sizeof(float) * g->feat_dim * g->n, st))))
-            return s;
-    }
+    if (!accumulate && (s = clear_splat_grads(g, vn, map, sg, d_feat, st))) return s;
     BwdArgs A;
     A.uvdo = reinterpret_cast<const float4 *>(proj->uvdo);
     A.uv_lo = reinterpret_cast<const float2 *>(proj->uv_lo);

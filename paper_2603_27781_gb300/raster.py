@@ -325,13 +325,25 @@ class Renderer:
                                                      _p(self.loss_out), _p(self.mask), _p(self.median),
                                                      _stream(stream)))
 
-    def render_bwd(self, field: Field, grad_mode: int = L.GS_GRAD_MAP, stream=None, factored=False):
+    def render_bwd(self, field: Field, grad_mode: int = L.GS_GRAD_MAP, stream=None, factored=False,
+                   accumulate=False):
+        """gs_render_bwd; with accumulate, into the splat sums as they are (cleared before by
+        clear_grads, possibly on another stream that this one has waited for)."""
         pc, bc, ic, gc, sg = (self.projected_c(), self.binning_c(), self.images_c(), self.image_grads_c(factored),
                               self.splat_grads_c())
+        mode = grad_mode | (L.GS_GRAD_ACCUMULATE if accumulate else 0)
         L.check("gs_render_bwd", L.gs_render_bwd(ctypes.byref(field.c()), ctypes.byref(pc), ctypes.byref(bc),
-                                                 self.cams_c, self.n_views, ctypes.byref(self.prm_c), grad_mode,
+                                                 self.cams_c, self.n_views, ctypes.byref(self.prm_c), mode,
                                                  ctypes.byref(ic), ctypes.byref(gc), ctypes.byref(sg),
                                                  _p(self.d_feat) if self.feat_dim else None, _stream(stream)))
+
+    def clear_grads(self, field: Field, grad_mode: int = L.GS_GRAD_MAP, stream=None):
+        """gs_splat_grads_clear: zeroes the splat sums a render_bwd with this mode adds to."""
+        sg = self.splat_grads_c()
+        L.check("gs_splat_grads_clear", L.gs_splat_grads_clear(ctypes.byref(field.c()), self.n_views, grad_mode,
+                                                               ctypes.byref(sg),
+                                                               _p(self.d_feat) if self.feat_dim else None,
+                                                               _stream(stream)))
 
     def project_bwd(self, field: Field, grad_mode: int = L.GS_GRAD_MAP, pose_dev=None, stream=None):
         sg, oc = self.splat_grads_c(), self.gaussian_grads_c()
@@ -387,22 +399,29 @@ class Renderer:
     def iteration(self, field: Field, targets, decoder_W, decoder_b, w: LossWeights, grad_mode=L.GS_GRAD_MAP,
                   pose_dev=None, stream=None):
         """One fwd+bwd pass of the whole path: project, bin/sort, blend, loss, blend and
-        projection backward, pose-twist reduction, DSR.  Asynchronous.  The DSR's value (which
-        needs only the log-scales) runs on a side stream beside the whole step, its gradient
+        projection backward, pose-twist reduction, DSR.  Asynchronous.  On a side stream beside
+        the forward half: the clearing of the blend backward's sums and the DSR's value (which
+        needs only the log-scales); the blend backward waits for them.  The DSR's gradient runs
         there beside the twist reduction once the projection backward has written the
         log-scale gradient, and the side stream rejoins `stream` before the call returns (also
         inside a CUDA-graph capture)."""
         dsr = (grad_mode & L.GS_GRAD_MAP) and (w.big or w.small)
-        if dsr:  # its value needs only the log-scales: beside the whole step on the side stream
-            self.side_start(lambda s: self.dsr_value(field, w.big, w.small, s), stream)
+
+        def side(s):
+            self.clear_grads(field, grad_mode, s)
+            if dsr:
+                self.dsr_value(field, w.big, w.small, s)
+        self.side_start(side, stream)
         self.forward(field, pose_dev, stream)
         fac = self.use_factored(decoder_W)
         self.loss(targets, decoder_W, decoder_b, w, stream, factored=fac)
-        if not dsr:
-            self.backward(field, grad_mode, pose_dev, stream, factored=fac)
-            return
-        self.render_bwd(field, grad_mode, stream, factored=fac)
+        self.side_join(stream)
+        self.render_bwd(field, grad_mode, stream, factored=fac, accumulate=True)
         self.project_bwd(field, grad_mode, pose_dev, stream)
+        if not dsr:
+            if grad_mode & L.GS_GRAD_POSE:
+                self.pose_grad(stream)
+            return
         main = (lambda: self.pose_grad(stream)) if grad_mode & L.GS_GRAD_POSE else (lambda: None)
         self.side_by_side(lambda s: self.dsr_grad(field, w.big, w.small, s), main, stream)
 
@@ -423,6 +442,12 @@ class Renderer:
         self._side.wait_stream(main)
         with torch.cuda.stream(self._side):
             side_work(self._side)
+
+    def side_join(self, stream=None):
+        """Makes `stream` wait for everything issued so far on the side stream."""
+        main = stream if stream is not None else torch.cuda.current_stream(self.device)
+        if getattr(self, "_side", None) is not None:
+            main.wait_stream(self._side)
 
     def side_by_side(self, side_work, main_work, stream=None):
         """Runs side_work(side_stream) on the renderer's side stream after everything issued

@@ -96,6 +96,16 @@ def test_argument_errors_before_any_launch(lib):
     assert lib.gs_dsr_value(10, 4096, 1.0, 1.0, 257, 4096, None) == L.GS_ERR_ARG
     assert lib.gs_dsr_grad(10, None, 1.0, 1.0, None, None, None) == L.GS_ERR_ARG
     assert lib.gs_dsr_grad(-1, 4096, 1.0, 1.0, 4096, 4096, None) == L.GS_ERR_ARG
+    # clearing the splat sums: a mode without MAP or POSE, an unknown bit, missing or unaligned
+    # buffers, no views
+    sg = L.gs_splat_grads(fake, fake, fake)
+    for mode in (0, L.GS_GRAD_ACCUMULATE, 8 | L.GS_GRAD_MAP):
+        assert lib.gs_splat_grads_clear(ctypes.byref(g), 1, mode, ctypes.byref(sg), fake, None) == L.GS_ERR_ARG
+    assert lib.gs_splat_grads_clear(ctypes.byref(g), 0, L.GS_GRAD_MAP, ctypes.byref(sg), fake, None) == L.GS_ERR_ARG
+    assert lib.gs_splat_grads_clear(ctypes.byref(g), 1, L.GS_GRAD_MAP, ctypes.byref(sg), None, None) == L.GS_ERR_ARG
+    odd = L.gs_splat_grads(ctypes.c_void_p((1 << 20) + 4), fake, fake)
+    assert lib.gs_splat_grads_clear(ctypes.byref(g), 1, L.GS_GRAD_POSE, ctypes.byref(odd), None, None) == L.GS_ERR_ARG
+    assert lib.gs_splat_grads_clear(None, 1, L.GS_GRAD_MAP, ctypes.byref(sg), fake, None) == L.GS_ERR_ARG
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):

@@ -503,6 +503,40 @@ def test_median_is_bit_exact_on_large_views():
         assert r.median[v].item() == np.float32(oracle.lower_median(e.astype(np.float64)))
 
 
+def test_cleared_sums_accumulate_like_the_clearing_backward():
+    """gs_splat_grads_clear on the side stream beside the forward, then gs_render_bwd with
+    GS_GRAD_ACCUMULATE, gives the sums of gs_render_bwd's own clearing (the atomic sums agree
+    to their rounding), whatever the buffers held before; a second accumulating call adds the
+    same sums again."""
+    gs, cam = C.box_case(2000, 16, 64, 48, 60.0)
+    prm = C.params_pair()[0]
+    mode = L.GS_GRAD_MAP | L.GS_GRAD_POSE
+    field, r = C.gpu_forward(gs, cam, prm)
+    g = torch.Generator(device="cuda").manual_seed(5)
+    for t in (r.g_rgb, r.g_depth, r.g_feat):
+        t.copy_(torch.randn(t.shape, generator=g, device="cuda"))
+    sums = lambda: [t.clone() for t in (r.sg_uvod, r.sg_conic, r.sg_rgb, r.d_feat)]
+    r.render_bwd(field, mode)
+    torch.cuda.synchronize()
+    ref = sums()
+    for t in (r.sg_uvod, r.sg_conic, r.sg_rgb, r.d_feat):
+        t.fill_(3.0)
+    r.side_start(lambda s: r.clear_grads(field, mode, s))
+    r.render_fwd(field)
+    r.side_join()
+    r.render_bwd(field, mode, accumulate=True)
+    torch.cuda.synchronize()
+    once = sums()
+    r.render_bwd(field, mode, accumulate=True)
+    torch.cuda.synchronize()
+    twice = sums()
+    for a, b, c in zip(ref, once, twice):
+        tol = 1e-5 * float(a.abs().max()) + 1e-30
+        assert float((a - b).abs().max()) <= tol
+        assert float((2 * a - c).abs().max()) <= 2 * tol
+    assert float(ref[0].abs().max()) > 0 and float(ref[3].abs().max()) > 0
+
+
 def test_dsr_in_two_halves_equals_one_call():
     """gs_dsr_value on a side stream (its own scratch) followed by gs_dsr_grad gives the
     value and the gradient of gs_dsr bit for bit."""
