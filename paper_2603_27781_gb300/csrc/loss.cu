@@ -180,10 +180,13 @@ struct LossShape {
 
 template <int D, int KC>
 __global__ void __launch_bounds__(LossShape<D, KC>::NT) loss_kernel(
-    ViewTable vt, LossP lp, const float *rgb, const float *depth, const float *sil, const float *feat,
-    const float *trgb, const float *tdepth, const uint8_t *label, const float *Wd, const float *bd, int64_t P,
-    const uint32_t *med_hist, float *g_rgb, float *g_depth, float *g_sil, float *g_feat, float *g_coef, float *part_f,
-    double *part_d, float *mask_out, float *median_out) {
+    ViewTable vt, LossP lp, const float *__restrict__ rgb, const float *__restrict__ depth,
+    const float *__restrict__ sil, const float *__restrict__ feat, const float *__restrict__ trgb,
+    const float *__restrict__ tdepth, const uint8_t *__restrict__ label, const float *__restrict__ Wd,
+    const float *__restrict__ bd, int64_t P, const uint32_t *__restrict__ med_hist, float *__restrict__ g_rgb,
+    float *__restrict__ g_depth, float *__restrict__ g_sil, float *__restrict__ g_feat, float *__restrict__ g_coef,
+    float *__restrict__ part_f, double *__restrict__ part_d, float *__restrict__ mask_out,
+    float *__restrict__ median_out) {
     pdl_wait();     // the previous kernel's results
     pdl_trigger();  // the next kernel may be scheduled now
     using SH = LossShape<D, KC>;

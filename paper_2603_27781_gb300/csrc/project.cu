@@ -135,10 +135,14 @@ __device__ __forceinline__ void project_geo(const float mu[3], const Shape &sh, 
     o.ok = isfinite(o.u) && isfinite(o.v) && isfinite(o.A) && isfinite(o.B) && isfinite(o.C);
 }
 
-__global__ void __launch_bounds__(256) project_fwd_kernel(ViewTable vt, Params prm, int64_t n, const float *means,
-                                                          const float *quats, const float *log_scales,
-                                                          const float *logits, const float *pose_dev, float4 *uvdo,
-                                                          float2 *uv_lo, float4 *conic, int32_t *touched) {
+__global__ void __launch_bounds__(256) project_fwd_kernel(ViewTable vt, Params prm, int64_t n,
+                                                          const float *__restrict__ means,
+                                                          const float *__restrict__ quats,
+                                                          const float *__restrict__ log_scales,
+                                                          const float *__restrict__ logits,
+                                                          const float *__restrict__ pose_dev, float4 *__restrict__ uvdo,
+                                                          float2 *__restrict__ uv_lo, float4 *__restrict__ conic,
+                                                          int32_t *__restrict__ touched) {
     pdl_wait();     // the previous kernel's results
     pdl_trigger();  // the next kernel may be scheduled now
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -182,13 +186,19 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(ViewTable vt, Params p
 // Register cap: six 128-thread blocks per SM (80 registers, 16 bytes spilled) instead of
 // four at 124 registers: the kernel is latency-bound and the extra warps hide it (five
 // blocks at 96 registers: -13 %; six: a further -8 %; seven spill 80 bytes).
-__global__ void __launch_bounds__(128, 6) project_bwd_kernel(ViewTable vt, Params prm, int64_t n, const float *means,
-                                                          const float *quats, const float *log_scales,
-                                                          const float *logits, const float *pose_dev,
-                                                          const float4 *acc_uvod, const float4 *acc_conic,
-                                                          const float4 *acc_rgb, int grad_mode,
-                                                          float *d_means, float *d_quats, float *d_log_scales,
-                                                          float *d_logits, float *d_rgb, float *pose_part) {
+__global__ void __launch_bounds__(128, 6) project_bwd_kernel(ViewTable vt, Params prm, int64_t n,
+                                                          const float *__restrict__ means,
+                                                          const float *__restrict__ quats,
+                                                          const float *__restrict__ log_scales,
+                                                          const float *__restrict__ logits,
+                                                          const float *__restrict__ pose_dev,
+                                                          const float4 *__restrict__ acc_uvod,
+                                                          const float4 *__restrict__ acc_conic,
+                                                          const float4 *__restrict__ acc_rgb, int grad_mode,
+                                                          float *__restrict__ d_means, float *__restrict__ d_quats,
+                                                          float *__restrict__ d_log_scales,
+                                                          float *__restrict__ d_logits, float *__restrict__ d_rgb,
+                                                          float *__restrict__ pose_part) {
     pdl_wait();     // the previous kernel's results
     pdl_trigger();  // the next kernel may be scheduled now
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
