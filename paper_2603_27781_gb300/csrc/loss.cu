@@ -607,7 +607,7 @@ constexpr int kPoseLanes = 16;
 
 __global__ void pose_step_kernel(int n_views, const double *grad, double *Tst, double *adam, double bc1, double bc2,
                                  double lr0, double lr1, double lr2, double lr3, double lr4, double lr5, double b1,
-                                 double b2, double eps, float *pose_f32) {
+                                 double b2, double lb1, double lb2, double eps, float *pose_f32) {
     pdl_wait();     // the previous kernel's results
     pdl_trigger();  // the next kernel may be scheduled now
     __shared__ double s_bc[2];
@@ -619,8 +619,9 @@ __global__ void pose_step_kernel(int n_views, const double *grad, double *Tst, d
         double c1 = bc1, c2 = bc2;
         if (bc1 < 0.0) {  // device step count: this step is the stored count + 1
             const double step = adam[12 * n_views] + 1.0;
-            c1 = 1.0 - pow(b1, step);
-            c2 = 1.0 - pow(b2, step);
+            // beta^step as exp(step ln beta), ln beta from the host (one exp instead of a pow)
+            c1 = 1.0 - exp(step * lb1);
+            c2 = 1.0 - exp(step * lb2);
             adam[12 * n_views] = step;
         }
         s_bc[0] = c1;
@@ -642,8 +643,20 @@ __global__ void pose_step_kernel(int n_views, const double *grad, double *Tst, d
         const double *ph = s_dl[v] + 3;
         const double th = sqrt(ph[0] * ph[0] + ph[1] * ph[1] + ph[2] * ph[2]);
         double a, b, c;
-        if (th < 1e-8) { a = 1 - th * th / 6; b = 0.5 - th * th / 24; c = 1.0 / 6 - th * th / 120; }
-        else { a = sin(th) / th; b = (1 - cos(th)) / (th * th); c = (th - sin(th)) / (th * th * th); }
+        if (th < 0.05) {
+            // a = sin(th)/th, b = (1 - cos th)/th^2, c = (th - sin th)/th^3 by their Taylor series in
+            // t = th^2 up to t^4: the next terms are below 1e-20 here, and the series avoids the
+            // cancellation of 1 - cos th (the rotation increments of a tracking step are ~1e-3)
+            const double t = th * th;
+            a = 1.0 + t * (-1.0 / 6 + t * (1.0 / 120 + t * (-1.0 / 5040 + t * (1.0 / 362880))));
+            b = 0.5 + t * (-1.0 / 24 + t * (1.0 / 720 + t * (-1.0 / 40320 + t * (1.0 / 3628800))));
+            c = 1.0 / 6 + t * (-1.0 / 120 + t * (1.0 / 5040 + t * (-1.0 / 362880 + t * (1.0 / 39916800))));
+        } else {
+            const double sn = sin(th), cs = cos(th);
+            a = sn / th;
+            b = (1 - cs) / (th * th);
+            c = (th - sn) / (th * th * th);
+        }
         s_abc[v][0] = a;
         s_abc[v][1] = b;
         s_abc[v][2] = c;
@@ -861,7 +874,8 @@ extern "C" gs_status gs_pose_step(int n_views, const double *d_twist, double *T_
     // device (from the counter after the moments) for step 0
     const double bc1 = step ? 1.0 - pow(beta1, step) : -1.0, bc2 = step ? 1.0 - pow(beta2, step) : -1.0;
     return launch_pdl(pose_step_kernel, 1, kPoseLanes * n_views, 0, (cudaStream_t)stream, n_views, d_twist, T_state,
-                      adam, bc1, bc2, lr[0], lr[1], lr[2], lr[3], lr[4], lr[5], beta1, beta2, eps, pose_f32);
+                      adam, bc1, bc2, lr[0], lr[1], lr[2], lr[3], lr[4], lr[5], beta1, beta2, log(beta1),
+                      log(beta2), eps, pose_f32);
 }
 
 // ------------------------------------------------- allocation-free loss entry
