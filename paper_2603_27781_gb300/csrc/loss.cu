@@ -221,6 +221,8 @@ __global__ void __launch_bounds__(LossShape<D, KC>::NT) loss_kernel(
 #pragma unroll
     for (int e = 0; e < EPL; ++e) accW[e] = 0.f;
 
+    // two pixels of the grid-stride loop in flight: the next one's loads issue beside this one's work
+#pragma unroll 2
     for (int64_t base = (int64_t)blockIdx.x * NT; base < Pv; base += (int64_t)gridDim.x * NT) {
         const int64_t i = base + tid;
         float f[DD], dz[KC];
