@@ -106,8 +106,12 @@ typedef struct {
      * tile's worth of threads, but only as many blocks as are resident on the
      * GPU at once, each taking tiles (in the tile order) from the work counters
      * gs_binning.queue, which must then not be NULL (else GS_ERR_ARG), until
-     * none is left; GS_BWD_BLOCKS_DEFAULT (0) = the library's choice for the
-     * launch shape. */
+     * none is left; GS_BLOCKS_RING = one block per tile whose warps stage the
+     * tile's splats into a ring of batch slots and walk them each at its own
+     * pace (two pixels per thread, feature dims 16 and 32, else
+     * GS_ERR_UNSUPPORTED; fwd_batch 128 gives two slots of 128 splats, 64 four
+     * slots of 64 at dim 16 and three at dim 32); GS_BWD_BLOCKS_DEFAULT (0) = the
+     * library's choice for the launch shape. */
     int32_t fwd_blocks;
     /* Where the EWA Jacobian J of Eq. 3 is evaluated (gs_project, gs_project_bwd):
      * GS_JACOBIAN_CLAMPED (0, the default) at (x/z, y/z) clamped to the view
@@ -123,7 +127,8 @@ typedef struct {
      * without reading what it waited for.  0 = the library default (2^22 polls,
      * about 0.3 s); negative = a block gives up at the first earlier block it
      * looks at (a test hook: gs_bin_sort then reports GS_ERR_TIMEOUT whenever a
-     * radix pass has more than one block of 2048 keys). */
+     * radix pass has more than one block of 2048 keys, and a GS_BLOCKS_RING
+     * forward whenever one of its warps has to wait for another). */
     int32_t spin_limit;
     /* Splats the per-tile forward (fwd_blocks GS_BWD_BLOCKS_TILE or
      * GS_BLOCKS_QUEUE) stages in shared memory per round: 64, 128 or 256
@@ -134,7 +139,7 @@ typedef struct {
     int32_t fwd_batch;
 } gs_raster_params;
 
-enum { GS_BWD_BLOCKS_DEFAULT = 0, GS_BWD_BLOCKS_GROUP = 1, GS_BWD_BLOCKS_TILE = 2, GS_BLOCKS_QUEUE = 3 };
+enum { GS_BWD_BLOCKS_DEFAULT = 0, GS_BWD_BLOCKS_GROUP = 1, GS_BWD_BLOCKS_TILE = 2, GS_BLOCKS_QUEUE = 3, GS_BLOCKS_RING = 4 };
 enum { GS_JACOBIAN_CLAMPED = 0, GS_JACOBIAN_EXACT = 1 };
 
 /* The Semantic Gaussian Field of Eq. 1, structure of arrays.

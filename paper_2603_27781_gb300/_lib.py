@@ -15,7 +15,7 @@ LIB_PATH = _build.LIB_PATH
 
 GS_OK, GS_ERR_ARG, GS_ERR_CAPACITY, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_ERR_UNSUPPORTED, GS_ERR_CHECK = \
     0, -1, -2, -3, -4, -5, -6
-GS_BWD_BLOCKS_DEFAULT, GS_BWD_BLOCKS_GROUP, GS_BWD_BLOCKS_TILE, GS_BLOCKS_QUEUE = 0, 1, 2, 3
+GS_BWD_BLOCKS_DEFAULT, GS_BWD_BLOCKS_GROUP, GS_BWD_BLOCKS_TILE, GS_BLOCKS_QUEUE, GS_BLOCKS_RING = 0, 1, 2, 3, 4
 GS_JACOBIAN_CLAMPED, GS_JACOBIAN_EXACT = 0, 1
 GS_F32, GS_BF16, GS_F16 = 0, 1, 2
 GS_DSR_SCRATCH_BYTES = 24832

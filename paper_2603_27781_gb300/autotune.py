@@ -33,8 +33,8 @@ def _time(fn, reps: int, stream) -> float:
     return ev[0].elapsed_time(ev[1]) / reps
 
 
-_PREFIX = {L.GS_BWD_BLOCKS_GROUP: "w", L.GS_BLOCKS_QUEUE: "q"}
-_BLOCKS = {"w": L.GS_BWD_BLOCKS_GROUP, "q": L.GS_BLOCKS_QUEUE}
+_PREFIX = {L.GS_BWD_BLOCKS_GROUP: "w", L.GS_BLOCKS_QUEUE: "q", L.GS_BLOCKS_RING: "r"}
+_BLOCKS = {"w": L.GS_BWD_BLOCKS_GROUP, "q": L.GS_BLOCKS_QUEUE, "r": L.GS_BLOCKS_RING}
 
 
 def shape_keys(p: RasterParams):
@@ -44,13 +44,13 @@ def shape_keys(p: RasterParams):
 
 
 def parse_shapes(text: str) -> dict:
-    """RasterParams fields for "fwd,bwd" shape keys such as "2,w2", "q2,w2" or, with the
-    forward's staged batch, "2@64,w2"."""
+    """RasterParams fields for "fwd,bwd" shape keys such as "2,w2", "q2,w2", "r2,w2" or, with
+    the forward's staged batch, "2@64,w2"."""
     f_s, b_s = text.split(",")
     f_s, _, batch = f_s.partition("@")
     blocks = lambda k: _BLOCKS.get(k[0], L.GS_BWD_BLOCKS_TILE)
-    out = dict(fwd_px_per_thread=int(f_s.lstrip("wq")), fwd_blocks=blocks(f_s),
-               bwd_px_per_thread=int(b_s.lstrip("wq")), bwd_blocks=blocks(b_s))
+    out = dict(fwd_px_per_thread=int(f_s.lstrip("wqr")), fwd_blocks=blocks(f_s),
+               bwd_px_per_thread=int(b_s.lstrip("wqr")), bwd_blocks=blocks(b_s))
     if batch:
         out["fwd_batch"] = int(batch)
     return out
@@ -61,8 +61,9 @@ def tune_blend(r: Renderer, field, grad_mode: int = L.GS_GRAD_MAP, reps: int = 5
     """Returns (RasterParams with the fastest fwd/bwd launch shapes, timings in ms).  Shapes
     are keyed by pixels per thread (one block per tile), "w1", "w2" (one 32-thread block
     per pixel group) and, for the forward, "q1", "q2", "q4" (resident blocks taking tiles
-    from a work counter); for a per-tile forward the splats it stages per round are then
-    timed at 64, 128 and 256 (timings["fwd_batch"]).
+    from a work counter) and "r2", "r2@64" (the tile's splats staged into a ring of batch
+    slots that each warp walks at its own pace); for a per-tile forward the splats it stages
+    per round are then timed at 64, 128 and 256 (timings["fwd_batch"]).
 
     The renderer's image gradients (r.g_*) must hold the gradients to time the
     backward with (e.g. after a loss call; with factored, a factored loss call, and only the
@@ -78,6 +79,8 @@ def tune_blend(r: Renderer, field, grad_mode: int = L.GS_GRAD_MAP, reps: int = 5
     fshapes.update({f"w{np_}": dict(fwd_px_per_thread=np_, fwd_blocks=L.GS_BWD_BLOCKS_GROUP)
                     for np_ in WARP_CANDIDATES})
     fshapes.update({f"q{np_}": dict(fwd_px_per_thread=np_, fwd_blocks=L.GS_BLOCKS_QUEUE) for np_ in CANDIDATES})
+    fshapes["r2"] = dict(fwd_px_per_thread=2, fwd_blocks=L.GS_BLOCKS_RING)
+    fshapes["r2@64"] = dict(fwd_px_per_thread=2, fwd_blocks=L.GS_BLOCKS_RING, fwd_batch=64)
     for key, shape in fshapes.items():
         r.prm_c = dataclasses.replace(base, **shape).c()
         try:
@@ -89,10 +92,11 @@ def tune_blend(r: Renderer, field, grad_mode: int = L.GS_GRAD_MAP, reps: int = 5
     fwd = dict(fshapes[best_f])
     if fwd["fwd_blocks"] != L.GS_BWD_BLOCKS_GROUP:
         # the splats staged per round by the per-tile forward, for the chosen shape ("2@64": shape 2, 64)
-        timings["fwd_batch"] = {128: timings["fwd"][best_f]}
+        best_batch = fwd.get("fwd_batch", 128)
+        timings["fwd_batch"] = {best_batch: timings["fwd"][best_f]}
         for batch in BATCH_CANDIDATES:
-            if batch != 128:
-                r.prm_c = dataclasses.replace(base, **fwd, fwd_batch=batch).c()
+            if batch != best_batch:
+                r.prm_c = dataclasses.replace(base, **dict(fwd, fwd_batch=batch)).c()
                 try:
                     timings["fwd_batch"][batch] = _time(lambda: r.render_fwd(field), reps, stream)
                 except L.GsError as e:  # not built for this shape

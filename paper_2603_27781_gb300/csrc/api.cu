@@ -59,9 +59,10 @@ bool make_params(const gs_raster_params *p, Params *out) {
     if (p->bwd_blocks < GS_BWD_BLOCKS_DEFAULT || p->bwd_blocks > GS_BWD_BLOCKS_TILE) return false;
     out->bwd_blocks = p->bwd_blocks;
     out->bwd_warp = false;
-    if (p->fwd_blocks < GS_BWD_BLOCKS_DEFAULT || p->fwd_blocks > GS_BLOCKS_QUEUE) return false;
+    if (p->fwd_blocks < GS_BWD_BLOCKS_DEFAULT || p->fwd_blocks > GS_BLOCKS_RING) return false;
     out->fwd_blocks = p->fwd_blocks;
     out->fwd_group = false;
+    out->fwd_ring = false;
     if (p->jacobian != GS_JACOBIAN_CLAMPED && p->jacobian != GS_JACOBIAN_EXACT) return false;
     out->exact_jacobian = p->jacobian == GS_JACOBIAN_EXACT;
     out->spin_limit = p->spin_limit == 0 ? kDefaultSpinLimit : (p->spin_limit < 0 ? -1 : p->spin_limit);

@@ -40,6 +40,7 @@ struct Params {
     int fwd_blocks;      // forward block shape (GS_BWD_BLOCKS_*)
     bool fwd_group;      // resolved: forward as one 32-thread block per pixel group
     bool fwd_queue;      // resolved: forward as resident CTAs taking tiles from a work counter
+    bool fwd_ring;       // resolved: forward with the tile's splats staged into a ring of batch slots
     bool exact_jacobian; // GS_JACOBIAN_EXACT: J of Eq. 3 at the unclamped (x/z, y/z)
     int spin_limit;      // polls of a bounded wait before it gives up (< 0: at once)
     int fwd_batch;       // splats staged per round by the per-tile forward (64, 128 or 256)
@@ -251,6 +252,24 @@ __device__ __forceinline__ void tile_rect(float u, float v, int r, int TX, int T
 // called it (or exited).  Both are no-ops for a kernel launched without the attribute.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Shared-memory mbarriers (CTA scope): init with the number of arrivals a phase takes, arrive
+// (release), and a test whether the phase of the given parity has completed (acquire); the
+// caller bounds its polls.
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(bar)),
+                 "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"((uint32_t)__cvta_generic_to_shared(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
 
 // Host helpers.
 // A named NVTX range for the duration of an entry point: a profiler's timeline shows each

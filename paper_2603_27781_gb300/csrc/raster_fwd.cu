@@ -421,6 +421,260 @@ __global__ void __launch_bounds__(32, fwd_group_min_blocks(D, NP)) raster_fwd_gr
     }
 }
 
+// One batch slot of the ring forward: B staged splat records.
+template <int D, int B>
+struct RingSlot {
+    SplatGeo geo[B];
+    float2 ext[B];
+    float4 cull[B];
+    float4 rgbd[B];
+    float4 feat[B * (D / 4 > 0 ? D / 4 : 1)];
+};
+
+// The per-tile forward with its splats staged into a ring of NBUF batch slots of B records:
+// the four warps stage each batch together (a quarter each) and walk the staged batches at
+// their own pace, synchronised per slot by mbarriers instead of CTA barriers: slot full (every
+// warp has staged its quarter) and slot empty (every warp has walked it), so a warp can run up
+// to NBUF - 1 batches ahead of the slowest.  A warp whose pixels are all done still stages
+// its quarters; once every warp's pixels are done, the next batch staged carries a stop flag
+// and every warp leaves at that same batch.  Arithmetic, order and outputs are those of
+// raster_fwd_kernel.  Every wait is bounded (prm.spin_limit polls); one that gives up sets
+// GS_ERR_TIMEOUT in the status word and its warp leaves without writing its pixels.
+template <int D, typename RT, typename FT, int B, int NBUF>
+__global__ void __launch_bounds__(Shape<2, true>::THREADS, fwd_min_blocks(D, 2)) raster_fwd_ring_kernel(
+    ViewTable vt, Params prm, const float4 *__restrict__ uvdo, const float2 *__restrict__ uv_lo,
+    const float4 *__restrict__ conic, const RT *__restrict__ rgb, const FT *__restrict__ feat,
+    const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges, int64_t P, float *o_rgb, float *o_depth,
+    float *o_sil, float *o_feat, float *o_T, int32_t *o_nc, int32_t *o_nb, uint32_t *bmask, int64_t bm_stride,
+    const uint32_t *__restrict__ order, int32_t *status, int64_t capacity, uint32_t * /*queue*/) {
+    pdl_wait();     // the previous kernel's results
+    pdl_trigger();  // the next kernel may be scheduled now
+    constexpr int NP = 2;
+    using SH = Shape<NP, true>;  // horizontal pixel pairs
+    constexpr int NT = SH::THREADS, NW = SH::WARPS;
+    constexpr int NL = SH::PIX_GROUPS ? NP : 1;
+    constexpr int D4 = D / 4, DD = D > 0 ? D : 1;
+    constexpr int QB = B / NW;  // records a warp stages per batch
+    static_assert(B % 32 == 0 && QB <= 32 && NBUF >= 2, "ring shape");
+    __shared__ RingSlot<D, B> s_slot[NBUF];
+    __shared__ __align__(8) uint64_t s_full[NBUF], s_empty[NBUF];
+    __shared__ int s_stop[NBUF][NW];
+    __shared__ int s_done;
+
+    if (binning_failed(status)) return;  // the binning overflowed or gave up: render nothing
+    const int gt = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
+    if (gt < 0 || gt >= vt.tile_off[vt.n_views]) return;  // not a permutation of the tiles: leave the tile
+    const int v = view_of_tile(vt, gt);
+    const int t = gt - vt.tile_off[v];
+    const int tx = t % vt.TX[v], ty = t / vt.TX[v];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    uint32_t start = ranges[2 * gt], end = ranges[2 * gt + 1];
+    checked_range(start, end, capacity, status);
+    const int64_t voff = (int64_t)v * vt.n;
+    if (tid < NBUF) {
+        mbar_init(&s_full[tid], NT);
+        mbar_init(&s_empty[tid], NT);
+    }
+    if (tid == 0) s_done = 0;
+    __syncthreads();  // the barriers are initialised before any thread uses them
+
+    const uint32_t first = start & ~31u;
+    const int n_batch = end > first ? (int)((end - first + B - 1) / B) : 0;
+    // warp `warp` stages records [warp QB, (warp + 1) QB) of batch j into its slot, with its
+    // stop flag (every warp's pixels done when it staged), then arrives on the slot's full barrier
+    auto stage = [&](int j) {
+        RingSlot<D, B> &S = s_slot[j % NBUF];
+        const uint32_t b0 = first + (uint32_t)j * B;
+        if (lane < QB) {
+            const int k = warp * QB + lane;
+            const uint32_t jj = b0 + k;
+            if (jj >= start && jj < end) {
+                const uint32_t item = checked_item(vals[jj], voff, vt.n, status);
+                const int64_t g = (int64_t)item - voff;
+                const float4 a = uvdo[item];
+                const float4 c = conic[item];
+                const SplatGeo sg = make_geo(a, uv_lo[item], c);
+                S.geo[k] = sg;
+                S.ext[k] = splat_extent(c, a.w, prm.alpha_min);
+                S.cull[k] = ellipse_cull(sg, prm.alpha_min);
+                S.rgbd[k] = load_rgbd(rgb, g, a.z);
+#pragma unroll
+                for (int q = 0; q < D4; ++q) S.feat[k * D4 + q] = load_feat4(feat, g * D + 4 * q);
+            }
+        }
+        if (lane == 0) s_stop[j % NBUF][warp] = *(volatile int *)&s_done == NW;
+        mbar_arrive(&s_full[j % NBUF]);
+    };
+
+    int bx0, by0;
+    SH::warp_origin(warp, bx0, by0);
+    const float bcx = (float)(tx * kTile + bx0) + 0.5f * SH::BW, bcy = (float)(ty * kTile + by0) + 0.5f * SH::BH;
+    const float hx = 0.5f * (SH::BW - 1), hy = 0.5f * (SH::BH - 1);
+    float pxc[NP], pyc[NP], T[NP], ar[NP], ag[NP], ab[NP], ad[NP], as[NP], af[NP][DD];
+    int last[NP], blended[NP];
+    bool inside[NP], done[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        int lx, ly;
+        SH::pixel(tid, p, lx, ly);
+        const int px = tx * kTile + lx, py = ty * kTile + ly;
+        inside[p] = px < vt.W[v] && py < vt.H[v];
+        done[p] = !inside[p];
+        pxc[p] = (float)px + 0.5f;
+        pyc[p] = (float)py + 0.5f;
+        T[p] = 1.f;
+        ar[p] = ag[p] = ab[p] = ad[p] = as[p] = 0.f;
+#pragma unroll
+        for (int d = 0; d < DD; ++d) af[p][d] = 0.f;
+        last[p] = blended[p] = 0;
+    }
+    auto all_done = [&]() {
+        bool a = true;
+#pragma unroll
+        for (int p = 0; p < NP; ++p) a = a && done[p];
+        return a;
+    };
+    auto flush = [&](const uint32_t (&lbits)[NL], uint32_t word_idx) {
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            const uint32_t mine =
+                SH::PIX_GROUPS ? lbits[j % NL] : ((SH::lanes_of_group(j) >> lane) & 1u ? lbits[0] : 0u);
+            const uint32_t word = __reduce_or_sync(0xffffffffu, mine);
+            if (lane == 0 && word) atomicOr(&bmask[(int64_t)SH::group(warp, j) * bm_stride + word_idx], word);
+        }
+    };
+
+    // a wait the whole warp takes together (every lane sees the phase complete), bounded
+    auto wait_warp = [&](uint64_t *bar, uint32_t parity) {
+        for (int it = 0;; ++it) {
+            if (__all_sync(0xffffffffu, mbar_test(bar, parity))) return true;
+            if (prm.spin_limit < 0 || it >= prm.spin_limit) return false;
+        }
+    };
+    for (int j = 0; j < NBUF - 1 && j < n_batch; ++j) stage(j);
+    bool counted = false;  // this warp's pixels are all done and s_done counts it
+    bool ok = true;
+    for (int i = 0; i < n_batch; ++i) {
+        const int slot = i % NBUF;
+        if (!wait_warp(&s_full[slot], (uint32_t)(i / NBUF) & 1u)) {
+            ok = false;
+            break;
+        }
+        bool stop = false;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) stop = stop || s_stop[slot][w];
+        if (stop) break;  // the same batch for every warp: every pixel of the tile is done
+        const RingSlot<D, B> &S = s_slot[slot];
+        const uint32_t b0 = first + (uint32_t)i * B;
+        if (!__all_sync(0xffffffffu, all_done())) {
+            const int k_lo = b0 < start ? (int)(start - b0) : 0;
+            const int nb = min((uint32_t)B, end - b0);
+            bool finished = false;
+            for (int c0 = k_lo & ~31; c0 < nb && !finished; c0 += 32) {
+                uint32_t lbits[NL];
+#pragma unroll
+                for (int jj = 0; jj < NL; ++jj) lbits[jj] = 0u;
+                const int kl = c0 + lane;
+                bool reach = false;
+                if (kl >= k_lo && kl < nb) {
+                    const SplatGeo sg = S.geo[kl];
+                    reach = reaches_box(sg.u, sg.v, S.ext[kl], bcx, bcy, hx, hy) &&
+                            reaches_box_exact(sg, S.cull[kl], bcx, bcy, hx, hy);
+                }
+                uint32_t todo = __ballot_sync(0xffffffffu, reach);
+                for (int n_run = 0; todo; ++n_run) {
+                    const int k = c0 + __ffs(todo) - 1;
+                    todo &= todo - 1;
+                    if ((n_run & 3) == 0 && __all_sync(0xffffffffu, all_done())) { finished = true; break; }
+                    const SplatGeo s = S.geo[k];
+                    float al[NP];
+                    bool okp[NP];
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) {
+                        const PairEval e = eval_pair(s, pxc[p], pyc[p], prm.alpha_min, prm.alpha_max);
+                        al[p] = e.alpha;
+                        okp[p] = !done[p] && !e.skip;
+                    }
+                    float wgt[NP];
+                    bool any = false;
+                    const int pos = (int)(b0 - start) + k + 1;
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) {
+                        const float Tn = T[p] * (1.f - al[p]);
+                        const bool stp = okp[p] && Tn < prm.T_min;
+                        const bool b = okp[p] && !stp;
+                        done[p] = done[p] || stp;
+                        wgt[p] = b ? al[p] * T[p] : 0.f;
+                        T[p] = b ? Tn : T[p];
+                        last[p] = b ? pos : last[p];
+                        blended[p] += b ? 1 : 0;
+                        any = any || b;
+                        if (SH::PIX_GROUPS) lbits[p % NL] |= (b ? 1u : 0u) << (k & 31);
+                    }
+                    if (!SH::PIX_GROUPS) lbits[0] |= (any ? 1u : 0u) << (k & 31);
+                    if (!any) continue;
+                    const float4 c = S.rgbd[k];
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) {
+                        const float w = wgt[p];
+                        ar[p] = fmaf(w, c.x, ar[p]);
+                        ag[p] = fmaf(w, c.y, ag[p]);
+                        ab[p] = fmaf(w, c.z, ab[p]);
+                        ad[p] = fmaf(w, c.w, ad[p]);
+                        as[p] += w;
+                    }
+#pragma unroll
+                    for (int q = 0; q < D4; ++q) {
+                        const float4 f = S.feat[k * D4 + q];
+#pragma unroll
+                        for (int p = 0; p < NP; ++p) {
+                            af[p][4 * q] = fmaf(wgt[p], f.x, af[p][4 * q]);
+                            af[p][4 * q + 1] = fmaf(wgt[p], f.y, af[p][4 * q + 1]);
+                            af[p][4 * q + 2] = fmaf(wgt[p], f.z, af[p][4 * q + 2]);
+                            af[p][4 * q + 3] = fmaf(wgt[p], f.w, af[p][4 * q + 3]);
+                        }
+                    }
+                }
+                if (bmask) flush(lbits, (b0 + c0) >> 5);
+            }
+        }
+        if (!counted && __all_sync(0xffffffffu, all_done())) {
+            counted = true;
+            if (lane == 0) atomicAdd(&s_done, 1);
+        }
+        __syncwarp();
+        mbar_arrive(&s_empty[slot]);
+        // batch i + NBUF - 1 goes into the slot batch i - 1 used, once every warp has walked it
+        const int jn = i + NBUF - 1;
+        if (jn < n_batch) {
+            if (i >= 1 && !wait_warp(&s_empty[jn % NBUF], (uint32_t)((i - 1) / NBUF) & 1u)) {
+                ok = false;
+                break;
+            }
+            stage(jn);
+        }
+    }
+    if (!ok) {
+        set_status(status, GS_ERR_TIMEOUT);
+        return;  // this warp's pixels stay unwritten; the status word says so
+    }
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        if (!inside[p]) continue;
+        const int64_t pix = vt.pix_off[v] + (int64_t)((int)pyc[p]) * vt.W[v] + (int)pxc[p];
+        o_rgb[pix] = ar[p] + T[p] * prm.bg[0];
+        o_rgb[P + pix] = ag[p] + T[p] * prm.bg[1];
+        o_rgb[2 * P + pix] = ab[p] + T[p] * prm.bg[2];
+        o_depth[pix] = ad[p];
+        o_sil[pix] = as[p];
+#pragma unroll
+        for (int d = 0; d < D; ++d) o_feat[d * P + pix] = af[p][d];
+        o_T[pix] = T[p];
+        o_nc[pix] = last[p];
+        if (o_nb) o_nb[pix] = blended[p];
+    }
+}
+
 template <int D, int NP, typename RT, typename FT>
 gs_status launch(const ViewTable &vt, const Params &prm, const gs_gaussians *g, const gs_projected *proj,
                  const gs_binning *bins, gs_images *out, cudaStream_t st) {
@@ -438,6 +692,20 @@ gs_status launch(const ViewTable &vt, const Params &prm, const gs_gaussians *g, 
         if (prm.fwd_group) {
             return args(raster_fwd_group_kernel<D, NP, RT, FT>, tiles * Shape<NP>::WARPS, 32, 0);
         }
+    }
+    if (prm.fwd_ring) {
+        // batch slots within the 48 KB of static shared memory: two of 128 or four of 64 records
+        // at D = 16, three of 64 at D = 32
+        if constexpr (NP == 2 && D == 16) {
+            if (prm.fwd_batch == 128)
+                return args(raster_fwd_ring_kernel<D, RT, FT, 128, 2>, tiles, Shape<2, true>::THREADS, 0);
+            if (prm.fwd_batch == 64)
+                return args(raster_fwd_ring_kernel<D, RT, FT, 64, 4>, tiles, Shape<2, true>::THREADS, 0);
+        }
+        if constexpr (NP == 2 && D == 32)
+            if (prm.fwd_batch == 64)
+                return args(raster_fwd_ring_kernel<D, RT, FT, 64, 3>, tiles, Shape<2, true>::THREADS, 0);
+        return GS_ERR_UNSUPPORTED;
     }
     // the per-tile forward with BATCH splats staged per round; batches other than 128 are built
     // for the two-pixel shape: 64 at feature widths 16 and 32, 256 at 16
@@ -516,6 +784,8 @@ extern "C" gs_status gs_render_fwd(const gs_gaussians *g, const gs_projected *pr
     const int np = prm.fwd_np ? prm.fwd_np : default_fwd_np(g->feat_dim);
     prm.fwd_group = prm.fwd_blocks == GS_BWD_BLOCKS_GROUP;
     prm.fwd_queue = prm.fwd_blocks == GS_BLOCKS_QUEUE;
+    prm.fwd_ring = prm.fwd_blocks == GS_BLOCKS_RING;
+    if (prm.fwd_ring && np != 2) return GS_ERR_UNSUPPORTED;
     if (prm.fwd_group && np > 2) return GS_ERR_UNSUPPORTED;
     if (prm.fwd_queue && !bins->queue) return GS_ERR_ARG;
     if (g->rgb_dtype == GS_F16) {

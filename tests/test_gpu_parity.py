@@ -312,6 +312,51 @@ def test_tile_order_is_a_longest_first_permutation_and_changes_nothing():
         C.assert_grad_close("ordered", a.cpu().numpy(), b.cpu().numpy(), 1e-5)
 
 
+def test_ring_forward_matches_one_block_per_tile():
+    """The forward whose warps walk a ring of staged batch slots at their own pace renders the
+    same images and blend mask, bit for bit, as one block per tile with CTA barriers: two views
+    in the tile order and in index order, two slots of 128 or four of 64 splats; one 16x16 tile
+    of 9,000 Gaussians (more than 4,096 instances, the tile's pixels saturate, so every warp
+    leaves at the same batch before the end); D = 32 with three slots of 64.  Other pixels per
+    thread and batch sizes are refused."""
+    names = ("img_rgb", "img_depth", "img_sil", "img_feat", "img_T", "img_nc", "blend_mask")
+
+    def render(r, field, base, blocks, batch):
+        r.params = dataclasses.replace(base, fwd_px_per_thread=2, fwd_blocks=blocks, fwd_batch=batch)
+        r.prm_c = r.params.c()
+        r.project(field)
+        r.bin_sort()
+        r.render_fwd(field)
+        torch.cuda.synchronize()
+        assert r.status() == 0
+        return [getattr(r, n).clone() for n in names]
+
+    base = C.params_pair()[0]
+    gs, cam, room = C.room_case(20000, 16, 330, 190, 165.0)
+    cams = [cam, synth.camera(100, 70, 60.0, T_cw=synth.keyframe_loop(8, room=room)[3])]
+    long_gs, long_cam = C.box_case(9000, 16, 16, 16, 12.0)
+    d32_gs, d32_cam, _ = C.room_case(20000, 32, 200, 120, 100.0)
+    for g, c, batches in ((gs, cams, (128, 64)), (long_gs, [long_cam], (128, 64)), (d32_gs, [d32_cam], (64,))):
+        field, r = C.gpu_forward(g, c, base)
+        for use_order in (True, False):
+            r.use_tile_order = use_order
+            ref = render(r, field, base, L.GS_BWD_BLOCKS_TILE, 0)
+            for batch in batches:
+                out = render(r, field, base, L.GS_BLOCKS_RING, batch)
+                for n, a, b in zip(names, ref, out):
+                    assert torch.equal(a, b), (g.n, use_order, batch, n)
+        if g is long_gs:
+            nc = r.img_nc.cpu().numpy()
+            rg = r.ranges.cpu().numpy().astype(np.int64).reshape(-1, 2)
+            assert (rg[:, 1] - rg[:, 0]).max() > 4096 and nc.max() < (rg[:, 1] - rg[:, 0]).max() - 256
+    for np_, batch in ((1, 128), (4, 128), (2, 256)):
+        r.params = dataclasses.replace(base, fwd_px_per_thread=np_, fwd_blocks=L.GS_BLOCKS_RING, fwd_batch=batch)
+        r.prm_c = r.params.c()
+        with pytest.raises(L.GsError) as e:
+            r.render_fwd(field)
+        assert e.value.status == L.GS_ERR_UNSUPPORTED
+
+
 def test_queued_forward_matches_one_block_per_tile_and_resets_its_counters():
     """Two views: resident blocks taking tiles from the work counter render the same images
     and blend mask as one block per tile, for every pixels-per-thread shape and staged batch
