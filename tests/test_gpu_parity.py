@@ -413,7 +413,8 @@ def test_autotuner_picks_a_supported_shape():
     g = C.random_image_grads(r.P, 16, 6)
     r.g_rgb.copy_(torch.as_tensor(g["rgb"])); r.g_feat.copy_(torch.as_tensor(g["feat"]))
     tuned, t = autotune.tune_blend(r, field, L.GS_GRAD_MAP)
-    assert set(t["fwd"]) == {1, 2, 4, "w1", "w2", "q1", "q2", "q4"} and set(t["bwd"]) == {1, 2, 4, "w1", "w2"}
+    assert set(t["fwd"]) == {1, 2, 4, "w1", "w2", "q1", "q2", "q4", "r2", "r2@64"}
+    assert set(t["bwd"]) == {1, 2, 4, "w1", "w2"}
     kf, kb = autotune.shape_keys(tuned)
     assert kf in t["fwd"] and kb in t["bwd"]
     assert autotune.parse_shapes(f"{kf},{kb}") == {k: getattr(tuned, k) for k in (
