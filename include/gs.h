@@ -305,6 +305,11 @@ int gs_version(void);
 /* Human-readable text of a status code (static storage). */
 const char *gs_strerror(int status);
 
+/* Text of the CUDA runtime error behind the calling host thread's last
+ * GS_ERR_CUDA from a failed CUDA call ("no error" if there was none; static
+ * storage). */
+const char *gs_cuda_error(void);
+
 /* Bytes of workspace needed by gs_bin_sort, gs_loss_fwd_bwd and gs_dsr for n
  * Gaussians, n_views host cameras, an instance capacity and a
  * feature dimension.  One buffer of this size serves all of them in stream

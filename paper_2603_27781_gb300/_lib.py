@@ -99,6 +99,7 @@ _P = POINTER
 _SIGNATURES = {
     "gs_version": (c_int, []),
     "gs_strerror": (c_char_p, [c_int]),
+    "gs_cuda_error": (c_char_p, []),
     "gs_workspace_size": (c_size_t, [c_int64, c_int, _P(gs_camera), c_int64, c_int]),
     "gs_project": (c_int, [_P(gs_gaussians), _P(gs_camera), c_int, c_void_p, _P(gs_raster_params),
                            _P(gs_projected), c_void_p]),
@@ -157,6 +158,8 @@ def exported_symbols():
 class GsError(RuntimeError):
     def __init__(self, name, status):
         msg = library().gs_strerror(status).decode()
+        if status == GS_ERR_CUDA:
+            msg += ": " + library().gs_cuda_error().decode()
         super().__init__(f"{name} failed: {msg} ({status})")
         self.status = status
 
@@ -176,6 +179,7 @@ def _wrap(name):
 
 gs_version = _wrap("gs_version")
 gs_strerror = _wrap("gs_strerror")
+gs_cuda_error = _wrap("gs_cuda_error")
 gs_workspace_size = _wrap("gs_workspace_size")
 gs_project = _wrap("gs_project")
 gs_bin_sort = _wrap("gs_bin_sort")

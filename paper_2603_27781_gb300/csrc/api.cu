@@ -123,9 +123,15 @@ WsLayout ws_layout(int64_t n, int n_views, int64_t capacity, const ViewTable *vt
 
 }  // namespace gs
 
+namespace gs {
+thread_local cudaError_t g_last_cuda_error = cudaSuccess;
+}  // namespace gs
+
 extern "C" {
 
 int gs_version(void) { return 10000; }
+
+const char *gs_cuda_error(void) { return cudaGetErrorString(gs::g_last_cuda_error); }
 
 const char *gs_strerror(int status) {
     switch (status) {

@@ -283,7 +283,13 @@ struct NvtxRange {
 };
 #define GS_NVTX_RANGE(name) ::gs::NvtxRange gs_nvtx_range_(name)
 
-inline gs_status cuda_status(cudaError_t e) { return e == cudaSuccess ? GS_OK : GS_ERR_CUDA; }
+// The CUDA error behind this host thread's last GS_ERR_CUDA from cuda_status (gs_cuda_error).
+extern thread_local cudaError_t g_last_cuda_error;
+inline gs_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return GS_OK;
+    g_last_cuda_error = e;
+    return GS_ERR_CUDA;
+}
 
 // Launches kernel<<<grid, block, smem, st>>>(args...) with programmatic stream serialization
 // (the kernel must call pdl_wait() before it reads what earlier work on the stream wrote).
