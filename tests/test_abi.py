@@ -37,6 +37,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_version_and_status_text(lib):
     assert lib.gs_version() >= 10000
     assert lib.gs_strerror(L.GS_ERR_CAPACITY).decode().startswith("tile instance")
+    assert isinstance(lib.gs_cuda_error().decode(), str) and lib.gs_cuda_error()  # a text, never NULL
     assert lib.gs_strerror(12345).decode() == "unknown status"
 
 
