@@ -21,8 +21,8 @@ constexpr int fwd_min_blocks(int D, int NP) {
 }
 
 // One 16x16 tile gt of the blend, by the whole CTA (every exit is uniform over the CTA), staging
-// BATCH splats per round.
-template <int D, int NP, typename RT, typename FT, int BATCH>
+// BATCH splats per round; with CNT it also counts each pixel's blended splats (o_nb).
+template <int D, int NP, typename RT, typename FT, int BATCH, bool CNT>
 __device__ __forceinline__ void fwd_tile(
     const ViewTable &vt, const Params &prm, const float4 *__restrict__ uvdo, const float2 *__restrict__ uv_lo,
     const float4 *__restrict__ conic, const RT *__restrict__ rgb, const FT *__restrict__ feat,
@@ -157,7 +157,7 @@ __device__ __forceinline__ void fwd_tile(
                     wgt[p] = b ? al[p] * T[p] : 0.f;
                     T[p] = b ? Tn : T[p];
                     last[p] = b ? pos : last[p];
-                    blended[p] += b ? 1 : 0;
+                    if constexpr (CNT) blended[p] += b ? 1 : 0;
                     any = any || b;
                     if (SH::PIX_GROUPS) lbits[p % NL] |= (b ? 1u : 0u) << (k & 31);
                 }
@@ -201,14 +201,14 @@ __device__ __forceinline__ void fwd_tile(
         for (int d = 0; d < D; ++d) o_feat[d * P + pix] = af[p][d];
         o_T[pix] = T[p];
         o_nc[pix] = last[p];
-        if (o_nb) o_nb[pix] = blended[p];
+        if (CNT && o_nb) o_nb[pix] = blended[p];
     }
 }
 
 // With QUEUE, the grid is as many CTAs as fit on the GPU at once and each takes tiles, in the
 // tile order, from the work counter queue[0] until none is left; the last CTA to finish
 // (counted in queue[1]) sets both counters back to 0 for the next launch.  Nothing waits.
-template <int D, int NP, typename RT, typename FT, bool QUEUE, int BATCH>
+template <int D, int NP, typename RT, typename FT, bool QUEUE, int BATCH, bool CNT>
 __global__ void __launch_bounds__(Shape<NP>::THREADS, fwd_min_blocks(D, NP)) raster_fwd_kernel(
     ViewTable vt, Params prm, const float4 *__restrict__ uvdo, const float2 *__restrict__ uv_lo,
     const float4 *__restrict__ conic, const RT *__restrict__ rgb, const FT *__restrict__ feat,
@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS, fwd_min_blocks(D, NP)) ras
             __syncthreads();
             const int idx = s_idx;
             if (idx >= n_tiles) break;
-            fwd_tile<D, NP, RT, FT, BATCH>(vt, prm, uvdo, uv_lo, conic, rgb, feat, vals, ranges, P, o_rgb, o_depth, o_sil,
+            fwd_tile<D, NP, RT, FT, BATCH, CNT>(vt, prm, uvdo, uv_lo, conic, rgb, feat, vals, ranges, P, o_rgb, o_depth, o_sil,
                                     o_feat, o_T, o_nc, o_nb, bmask, bm_stride, order ? (int)order[idx] : idx,
                                     status, capacity);
         }
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(Shape<NP>::THREADS, fwd_min_blocks(D, NP)) ras
         }
     } else {
         if (failed) return;
-        fwd_tile<D, NP, RT, FT, BATCH>(vt, prm, uvdo, uv_lo, conic, rgb, feat, vals, ranges, P, o_rgb, o_depth, o_sil,
+        fwd_tile<D, NP, RT, FT, BATCH, CNT>(vt, prm, uvdo, uv_lo, conic, rgb, feat, vals, ranges, P, o_rgb, o_depth, o_sil,
                                 o_feat, o_T, o_nc, o_nb, bmask, bm_stride,
                                 order ? (int)order[blockIdx.x] : (int)blockIdx.x, status, capacity);
     }
@@ -709,8 +709,10 @@ gs_status launch(const ViewTable &vt, const Params &prm, const gs_gaussians *g, 
     }
     // the per-tile forward with BATCH splats staged per round; batches other than 128 are built
     // for the two-pixel shape: 64 at feature widths 16 and 32, 256 at 16
-    auto per_tile = [&](auto batch_c) -> gs_status {
+    // (the blended-splat count is compiled in only for a caller that asks for it)
+    auto per_tile_cnt = [&](auto batch_c, auto cnt_c) -> gs_status {
         constexpr int B = decltype(batch_c)::value;
+        constexpr bool C = decltype(cnt_c)::value;
         if (prm.fwd_queue) {
             // one wave: as many CTAs as are resident at once
             static int res = 0;  // this kernel instance: SMs x resident CTAs per SM
@@ -718,15 +720,18 @@ gs_status launch(const ViewTable &vt, const Params &prm, const gs_gaussians *g, 
                 int dev = 0, sms = 0, per_sm = 0;
                 if (cudaGetDevice(&dev) != cudaSuccess ||
                     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raster_fwd_kernel<D, NP, RT, FT, true, B>,
+                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raster_fwd_kernel<D, NP, RT, FT, true, B, C>,
                                                                   Shape<NP>::THREADS, 0) != cudaSuccess)
                     return GS_ERR_CUDA;
                 res = sms * (per_sm > 0 ? per_sm : 1);
             }
-            return args(raster_fwd_kernel<D, NP, RT, FT, true, B>, tiles < res ? tiles : res, Shape<NP>::THREADS,
+            return args(raster_fwd_kernel<D, NP, RT, FT, true, B, C>, tiles < res ? tiles : res, Shape<NP>::THREADS,
                         0);
         }
-        return args(raster_fwd_kernel<D, NP, RT, FT, false, B>, tiles, Shape<NP>::THREADS, 0);
+        return args(raster_fwd_kernel<D, NP, RT, FT, false, B, C>, tiles, Shape<NP>::THREADS, 0);
+    };
+    auto per_tile = [&](auto batch_c) -> gs_status {
+        return out->n_blended ? per_tile_cnt(batch_c, std::true_type()) : per_tile_cnt(batch_c, std::false_type());
     };
     if (prm.fwd_batch == 128) return per_tile(std::integral_constant<int, 128>());
     if constexpr (NP == 2 && D >= 16)

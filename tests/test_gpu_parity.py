@@ -312,6 +312,29 @@ def test_tile_order_is_a_longest_first_permutation_and_changes_nothing():
         C.assert_grad_close("ordered", a.cpu().numpy(), b.cpu().numpy(), 1e-5)
 
 
+def test_blended_count_only_when_asked_leaves_the_images_alike():
+    """The per-tile forward compiled with and without the blended-splat count (n_blended is
+    asked for or not) renders the same images; the count is at most the 1-based position of the
+    last blended splat, positive exactly where a splat was blended, and its sum over the frame
+    is the number of blended (pixel, splat) pairs the blend mask's pairs bound."""
+    gs, cam, _ = C.room_case(20000, 16, 330, 190, 165.0)
+    field, r = C.gpu_forward(gs, cam, C.params_pair()[0])
+    names = ("img_rgb", "img_depth", "img_sil", "img_feat", "img_T", "img_nc", "blend_mask")
+    r.count_blended = False
+    r.render_fwd(field)
+    torch.cuda.synchronize()
+    plain = [getattr(r, n).clone() for n in names]
+    r.count_blended = True
+    r.img_nb.fill_(-1)
+    r.render_fwd(field)
+    torch.cuda.synchronize()
+    for n, a in zip(names, plain):
+        assert torch.equal(getattr(r, n), a), n
+    nb, nc = r.img_nb.cpu().numpy(), r.img_nc.cpu().numpy()
+    assert (nb >= 0).all() and (nb <= nc).all() and ((nb > 0) == (nc > 0)).all()
+    assert nb.sum() > 0
+
+
 def test_ring_forward_matches_one_block_per_tile():
     """The forward whose warps walk a ring of staged batch slots at their own pace renders the
     same images and blend mask, bit for bit, as one block per tile with CTA barriers: two views
