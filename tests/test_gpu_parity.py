@@ -672,6 +672,27 @@ def test_pose_step_matches_oracle():
     np.testing.assert_allclose(Tf.cpu().numpy().reshape(4, 4), Tref, atol=1e-6)
 
 
+def test_pose_step_large_and_small_rotations_match_oracle():
+    """Adam steps whose rotation increments lie above 0.05 rad (the exponential's coefficients
+    from sin and cos) and below it (their Taylor series), on both sides of the switch, against
+    the oracle's closed form."""
+    T = synth.look_pose((1.0, 2.0, 1.5), (0.3, 1.0, -0.1))
+    g = synth.rng(43)
+    r = raster.Renderer(0, [synth.camera(64, 48, 60.0)], 0, 0)
+    for rot_lr in (0.06, 0.02):  # first-step |phi| = rot_lr * sqrt(3): 0.104 and 0.035 rad
+        lr = np.array([0.01, 0.01, 0.01, rot_lr, rot_lr, rot_lr])
+        Ts = torch.as_tensor(T.reshape(1, 16)).cuda()
+        adam = torch.zeros(1, 12, dtype=torch.float64, device="cuda")
+        Tref, m, v = T.copy(), np.zeros(6), np.zeros(6)
+        for step in range(1, 4):
+            grad = g.standard_normal(6)
+            r.d_twist.copy_(torch.as_tensor(grad.reshape(1, 6)))
+            r.pose_step(Ts, adam, step, lr=tuple(lr))
+            Tref, m, v = oracle.pose_step(Tref, grad, m, v, step, lr)
+        np.testing.assert_allclose(Ts.cpu().numpy().reshape(4, 4), Tref, atol=1e-12)
+        assert abs(np.arccos(np.clip((np.trace(Tref[:3, :3] @ T[:3, :3].T) - 1) / 2, -1, 1))) > 0.02
+
+
 # ---------------------------------------------------------------- whole step
 @pytest.mark.parametrize("exact,ssim", [(True, False), (False, False), (False, True)])
 def test_full_iteration_tiny_scene(exact, ssim):
