@@ -238,9 +238,10 @@ def captured_traffic(kernel, px_per_thread, feat_dim):
 def kernels_per_step(n_tiles):
     tile_passes = max(1, math.ceil(math.ceil(math.log2(max(n_tiles, 2))) / 8))
     project = 1
-    # the binning's state reset, compaction (3, with the depth digit histograms), 4 depth passes,
-    # emission (3, with the tile digit histograms), tile passes, ranges with the tile order
-    bin_sort = 1 + 3 + 4 + 3 + tile_passes + 1
+    # the binning's state reset, compaction (3, with the depth digit histograms), 4 depth passes
+    # (the last with the emission's block counts), emission (2, with the tile digit histograms),
+    # tile passes, ranges with the tile order
+    bin_sort = 1 + 3 + 4 + 2 + tile_passes + 1
     # loss + its finish; DSR: stats and mask (each finished by its last block), gradient
     fwd, loss, bwd, proj_bwd, pose, dsr, step = 1, 2, 1, 1, 1, 3, 1
     return project + bin_sort + fwd + loss + bwd + proj_bwd + pose + dsr + step

@@ -94,6 +94,7 @@ WsLayout ws_layout(int64_t n, int n_views, int64_t capacity, const ViewTable *vt
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
     L.scan_blocks = take(sizeof(uint32_t) * (size_t)nb1);
+    L.emit_sums = take(sizeof(uint32_t) * (size_t)((vn + 255) / 256 + 1));
     L.counters = take(sizeof(uint32_t) * 64);
     L.dkeys_a = take(sizeof(uint32_t) * (size_t)vn);
     L.dvals_a = take(sizeof(uint32_t) * (size_t)vn);

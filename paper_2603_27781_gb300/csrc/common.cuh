@@ -318,6 +318,7 @@ inline bool feat_dim_ok(int d) { return d == 0 || d == 4 || d == 8 || d == 16 ||
 struct WsLayout {
     // bin_sort
     size_t scan_blocks;   // u32 [scan block sums], two levels
+    size_t emit_sums;     // u32 [emission blocks + 1]: instances per 256 depth-sorted items, then their offsets
     size_t counters;      // u32 [16]: n_vis, M (clamped), tile counters ...
     size_t dkeys_a, dvals_a, dkeys_b, dvals_b;  // u32 [VN]
     size_t tkeys_a, tkeys_b, tvals_b;           // u32 [capacity]

@@ -68,12 +68,14 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t *t
 
 // ------------------------------------------------------------ state of a call
 // Zeroes what a binning accumulates into: the ranges, the counters, the instance count and
-// status word, the queued forward's work counters, the tile counts, the digit histograms and
-// the look-back flags (the last and largest in 16-byte stores over the whole grid).
+// status word, the queued forward's work counters, the tile counts, the emission's per-block
+// instance counts, the digit histograms and the look-back flags (the last and largest in 16-byte
+// stores over the whole grid).
 __global__ void __launch_bounds__(256) bin_init_kernel(uint32_t *ranges, int64_t n_ranges, uint32_t *counters,
                                                        int64_t *n_inst, int32_t *status, uint32_t *tile_counts,
-                                                       int64_t n_tiles, uint32_t *hist, uint4 *lookback,
-                                                       int64_t n_lookback4, uint32_t *queue) {
+                                                       int64_t n_tiles, uint32_t *emit_sums, int64_t n_emit,
+                                                       uint32_t *hist, uint4 *lookback, int64_t n_lookback4,
+                                                       uint32_t *queue) {
     pdl_wait();
     pdl_trigger();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -81,6 +83,7 @@ __global__ void __launch_bounds__(256) bin_init_kernel(uint32_t *ranges, int64_t
     for (int64_t i = i0; i < n_lookback4; i += stride) lookback[i] = make_uint4(0u, 0u, 0u, 0u);
     for (int64_t i = i0; i < n_ranges; i += stride) ranges[i] = 0u;
     for (int64_t i = i0; i < n_tiles; i += stride) tile_counts[i] = 0u;
+    for (int64_t i = i0; i < n_emit; i += stride) emit_sums[i] = 0u;
     for (int64_t i = i0; i < 8 * 256; i += stride) hist[i] = 0u;
     for (int64_t i = i0; i < 64; i += stride) counters[i] = 0u;
     if (i0 == 0) {
@@ -210,24 +213,6 @@ __global__ void __launch_bounds__(256) vis_compact_kernel(const int32_t *touched
 // ------------------------------------------------------------ instance emission
 constexpr int kEmitBlock = 256;  // sorted items per block of the emission kernels
 
-__global__ void __launch_bounds__(kEmitBlock) emit_reduce_kernel(const uint32_t *sorted_items,
-                                                                 const int32_t *touched, const uint32_t *counters,
-                                                                 uint32_t *block_sums, int64_t vn,
-                                                                 const int32_t *status) {
-    pdl_wait();     // the previous kernel's results
-    pdl_trigger();  // the next kernel may be scheduled now
-    __shared__ uint32_t s_warp[9];
-    const bool failed = binning_failed(status);  // the depth sort gave up: its items are not valid
-    const int64_t count = counters[CTR_NVIS];
-    const int64_t i = (int64_t)blockIdx.x * kEmitBlock + threadIdx.x;
-    if (failed || (int64_t)blockIdx.x * kEmitBlock >= count) return;
-    const uint32_t it = i < count ? sorted_items[i] : 0u;
-    const uint32_t c = i < count && it < vn ? (uint32_t)touched[it] : 0u;
-    uint32_t tot;
-    block_exclusive_scan(c, &tot, s_warp);
-    if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
-}
-
 // One thread per sorted item computes its instance offset; the block's instances are then
 // split evenly over its warps, 32 consecutive instances per warp round, each lane finding
 // the item that owns its instance by a binary search over the block's item offsets in
@@ -336,7 +321,9 @@ __global__ void __launch_bounds__(NT, sort_min_blocks<NT>()) onesweep_kernel(con
                                                       const uint32_t *count_ptr, int shift,
                                                       const uint32_t *pass_hist, uint32_t *tile_ctr,
                                                       uint32_t *lookback, int32_t *status, int spin_limit,
-                                                      uint32_t *tile_counts, uint32_t n_tiles) {
+                                                      uint32_t *tile_counts, uint32_t n_tiles,
+                                                      const int32_t *emit_touched, uint32_t *emit_sums,
+                                                      uint32_t emit_vn) {
     pdl_wait();     // the previous kernel's results
     pdl_trigger();  // the next kernel may be scheduled now
     constexpr int W = NT / 32, TILE = NT * kSortIPT;
@@ -470,19 +457,41 @@ __global__ void __launch_bounds__(NT, sort_min_blocks<NT>()) onesweep_kernel(con
     if (d < 256) s_glob[d] = s_dbase[d] + prefix;
     __syncthreads();
 
-    // coalesced-by-run global writes
-    int tile_n = (int)min((int64_t)TILE, n - base);
-    for (int i = tid; i < tile_n; i += NT) {
-        uint32_t k = s_keys[i];
-        uint32_t dd = (k >> shift) & 255u;
-        uint32_t dst = s_glob[dd] + (uint32_t)i - s_excl[dd];
-        keys_out[dst] = k;
-        vals_out[dst] = s_vals[i];
-        // last pass of the tile sort: the block's keys are sorted by tile here, so each run of one
-        // tile adds its length to the tile's count (end + 1 from its last key, -start from its first)
-        if (tile_counts && k < n_tiles) {
-            if (i == 0 || s_keys[i - 1] != k) atomicAdd(&tile_counts[k], 0u - (uint32_t)i);
-            if (i == tile_n - 1 || s_keys[i + 1] != k) atomicAdd(&tile_counts[k], (uint32_t)i + 1u);
+    // coalesced-by-run global writes, in warp-uniform rounds of 32 consecutive keys
+    const int tile_n = (int)min((int64_t)TILE, n - base);
+    for (int i0 = tid - lane; i0 < tile_n; i0 += NT) {
+        const int i = i0 + lane;
+        const bool ok = i < tile_n;
+        uint32_t dst = 0u, v = 0u;
+        if (ok) {
+            const uint32_t k = s_keys[i];
+            const uint32_t dd = (k >> shift) & 255u;
+            dst = s_glob[dd] + (uint32_t)i - s_excl[dd];
+            v = s_vals[i];
+            keys_out[dst] = k;
+            vals_out[dst] = v;
+            // last pass of the tile sort: the block's keys are sorted by tile here, so each run of one
+            // tile adds its length to the tile's count (end + 1 from its last key, -start from its first)
+            if (tile_counts && k < n_tiles) {
+                if (i == 0 || s_keys[i - 1] != k) atomicAdd(&tile_counts[k], 0u - (uint32_t)i);
+                if (i == tile_n - 1 || s_keys[i + 1] != k) atomicAdd(&tile_counts[k], (uint32_t)i + 1u);
+            }
+        }
+        if (emit_sums) {
+            // last pass of the depth sort: the instances of each block of kEmitBlock sorted items,
+            // which the emission scans.  dst increases with i in a block (digits in order, each
+            // digit's keys at consecutive places), so the lanes of one emission block are
+            // consecutive: a segmented sum over the warp and one atomic per segment.
+            const uint32_t seg = ok ? dst / (uint32_t)kEmitBlock : 0xffffffffu;
+            uint32_t c = ok && v < emit_vn ? (uint32_t)emit_touched[v] : 0u;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, c, o);
+                const uint32_t sy = __shfl_up_sync(0xffffffffu, seg, o);
+                if (lane >= o && sy == seg) c += y;
+            }
+            const uint32_t s_next = __shfl_down_sync(0xffffffffu, seg, 1);
+            if (ok && (lane == 31 || s_next != seg) && c) atomicAdd(&emit_sums[seg], c);
         }
     }
 }
@@ -510,11 +519,13 @@ struct SortBufs {
 // Stable LSD sort of (key, val) pairs by `n_passes` 8-bit digits from bit 0, given the
 // digit histograms of every pass (hist [n_passes][256], written by the kernel that
 // produced the keys).  Input in (k0, v0); output lands in (k0, v0) if n_passes is even,
-// else (k1, v1).
+// else (k1, v1).  The last pass also adds the tile runs to tile_counts and, with emit_sums,
+// emit_touched[val] to the count of its kEmitBlock-item block of the output (either optional).
 template <int NT>
 gs_status radix_sort(SortBufs b, const uint32_t *count_ptr, int64_t max_count, int n_passes, const uint32_t *hist,
                      uint32_t *lookback, int lb_tiles, uint32_t *tile_ctrs, int32_t *status, int spin_limit,
-                     cudaStream_t st, uint32_t *tile_counts = nullptr, uint32_t n_tiles = 0) {
+                     cudaStream_t st, uint32_t *tile_counts = nullptr, uint32_t n_tiles = 0,
+                     const int32_t *emit_touched = nullptr, uint32_t *emit_sums = nullptr, uint32_t emit_vn = 0) {
     if (max_count <= 0 || n_passes <= 0) return GS_OK;
     constexpr size_t smem = sizeof(SortSmem<NT>);
     if (smem > 48 * 1024) {
@@ -534,7 +545,8 @@ gs_status radix_sort(SortBufs b, const uint32_t *count_ptr, int64_t max_count, i
     for (int p = 0; p < n_passes; ++p) {
         const gs_status s = launch_pdl(onesweep_kernel<NT>, grid, NT, smem, st, ki, vi, ko, vo, count_ptr, 8 * p,
                                        hist + 256 * p, tile_ctrs + p, lookback + (size_t)p * lb_tiles * 256, status,
-                                       spin_limit, p == n_passes - 1 ? tile_counts : nullptr, n_tiles);
+                                       spin_limit, p == n_passes - 1 ? tile_counts : nullptr, n_tiles, emit_touched,
+                                       p == n_passes - 1 ? emit_sums : nullptr, emit_vn);
         if (s) return s;
         uint32_t *tk = ki, *tv = vi;
         ki = ko; vi = vo; ko = tk; vo = tv;
@@ -648,6 +660,7 @@ extern "C" gs_status gs_bin_sort(int64_t n, const gs_projected *proj, const gs_c
     char *w = static_cast<char *>(ws);
     uint32_t *counters = reinterpret_cast<uint32_t *>(w + L.counters);
     uint32_t *block_sums = reinterpret_cast<uint32_t *>(w + L.scan_blocks);
+    uint32_t *emit_sums = reinterpret_cast<uint32_t *>(w + L.emit_sums);
     uint32_t *hist = reinterpret_cast<uint32_t *>(w + L.hist);
     uint32_t *lookback = reinterpret_cast<uint32_t *>(w + L.lookback);
     uint32_t *tile_counts = reinterpret_cast<uint32_t *>(w + L.tile_counts);
@@ -661,9 +674,10 @@ extern "C" gs_status gs_bin_sort(int64_t n, const gs_projected *proj, const gs_c
     gs_status s;
     const int64_t n_lb4 = vn > 0 ? 64 * ((int64_t)4 * L.lb_tiles_depth + (int64_t)3 * L.lb_tiles_inst) : 0;
     const int init_grid = (int)std::max<int64_t>(1, std::min<int64_t>((n_lb4 + 255) / 256, 1216));
+    const int64_t nbe = ceil_div(vn, kEmitBlock);  // emission blocks
     if ((s = launch_pdl(bin_init_kernel, init_grid, 256, 0, st, out->ranges, 2 * total_tiles, counters, out->n_inst,
-                        out->status, tile_counts, total_tiles, hist, reinterpret_cast<uint4 *>(lookback), n_lb4,
-                        out->queue)))
+                        out->status, tile_counts, total_tiles, emit_sums, nbe + 1, hist,
+                        reinterpret_cast<uint4 *>(lookback), n_lb4, out->queue)))
         return s;
     if (vn == 0) return write_ranges_order(tile_counts, out, total_tiles, st);
 
@@ -682,9 +696,11 @@ extern "C" gs_status gs_bin_sort(int64_t n, const gs_projected *proj, const gs_c
                         hist)))
         return s;
 
-    // 2. stable sort of the visible items by depth (4 passes: result in dk_a/dv_a)
+    // 2. stable sort of the visible items by depth (4 passes: result in dk_a/dv_a); the last pass
+    //    also counts the instances of every emission block of the sorted items
     if ((s = radix_sort<kSortThreads>({dk_a, dv_a, dk_b, dv_b}, counters + CTR_NVIS, vn, 4, hist, lookback, L.lb_tiles_depth,
-                        counters + CTR_TILE, out->status, prm.spin_limit, st)))
+                        counters + CTR_TILE, out->status, prm.spin_limit, st, nullptr, 0, proj->tiles_touched,
+                        emit_sums, (uint32_t)vn)))
         return s;
     const uint32_t *sorted_items = dv_a;
 
@@ -697,15 +713,11 @@ extern "C" gs_status gs_bin_sort(int64_t n, const gs_projected *proj, const gs_c
     // the emitted values go where the final pass must not land: out->vals ends the sort
     uint32_t *emit_vals = (tile_passes % 2 == 0) ? out->vals : tv_b;
     uint32_t *other_vals = (tile_passes % 2 == 0) ? tv_b : out->vals;
-    const int nbe = ceil_div(vn, kEmitBlock);
-    if ((s = launch_pdl(emit_reduce_kernel, nbe, kEmitBlock, 0, st, sorted_items, proj->tiles_touched, counters,
-                        block_sums, vn, out->status)))
-        return s;
-    if ((s = launch_pdl(blocksum_scan_kernel, 1, 1024, 0, st, block_sums, counters + CTR_NVIS, (int64_t)0, kEmitBlock,
+    if ((s = launch_pdl(blocksum_scan_kernel, 1, 1024, 0, st, emit_sums, counters + CTR_NVIS, (int64_t)0, kEmitBlock,
                         counters, (int)CTR_MRAW, (int)CTR_M, out->capacity, out->n_inst, out->status)))
         return s;
-    if ((s = launch_pdl(emit_kernel, nbe, kEmitBlock, 0, st, vt, sorted_items, proj->tiles_touched, uvdo, conic,
-                        counters, block_sums, out->capacity, tk_a, emit_vals, tile_passes, hist + 4 * 256, vn,
+    if ((s = launch_pdl(emit_kernel, (int)nbe, kEmitBlock, 0, st, vt, sorted_items, proj->tiles_touched, uvdo, conic,
+                        counters, emit_sums, out->capacity, tk_a, emit_vals, tile_passes, hist + 4 * 256, vn,
                         out->status)))
         return s;
     if (out->capacity == 0) return write_ranges_order(tile_counts, out, total_tiles, st);
