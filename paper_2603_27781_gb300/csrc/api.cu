@@ -89,7 +89,7 @@ WsLayout ws_layout(int64_t n, int n_views, int64_t capacity, const ViewTable *vt
     L.capacity = capacity;
     int64_t scan_n = vn > capacity ? vn : capacity;
     int64_t nb1 = (scan_n + 255) / 256 + 1;  // block sums of the 256-item emission blocks (the largest use)
-    L.lb_tiles_depth = (int)((vn + kSortTile - 1) / kSortTile);
+    L.lb_tiles_depth = (int)((vn + depth_sort_tile(vn) - 1) / depth_sort_tile(vn));
     L.lb_tiles_inst = (int)((capacity + kSortTileInst - 1) / kSortTileInst);
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };

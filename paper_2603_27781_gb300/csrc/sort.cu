@@ -20,6 +20,8 @@
 // and scatters through shared memory.  Blocks take tile numbers from an atomic
 // counter so a block only waits on blocks that are already running; every wait
 // is bounded and reports GS_ERR_TIMEOUT in the status word if it gives up.
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace gs {
@@ -178,7 +180,9 @@ __device__ __forceinline__ void hist_flush(uint32_t (*sh)[256], int n_passes, ui
 }
 
 // Order-preserving compaction of the visible items with their depth keys; also the digit
-// histograms of the depth sort's four passes (no separate pass over the keys).
+// histograms of the depth sort's four passes (no separate pass over the keys), counted over the
+// block's visible keys gathered in shared memory, so that the warps count only visible keys
+// (about a fifth of the items of a frame) in whole rounds of 32.
 __global__ void __launch_bounds__(256) vis_compact_kernel(const int32_t *touched, const float4 *uvdo, int64_t count,
                                                           const uint32_t *block_sums, uint32_t *keys, uint32_t *vals,
                                                           uint32_t *hist) {
@@ -186,6 +190,7 @@ __global__ void __launch_bounds__(256) vis_compact_kernel(const int32_t *touched
     pdl_trigger();  // the next kernel may be scheduled now
     __shared__ uint32_t s_warp[9];
     __shared__ uint32_t sh[4][256];
+    __shared__ uint32_t s_key[kScanBlock];  // the block's visible keys, in item order
     for (int i = threadIdx.x; i < 4 * 256; i += 256) (&sh[0][0])[i] = 0u;
     int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanIPT;
     bool f[kScanIPT];
@@ -196,16 +201,24 @@ __global__ void __launch_bounds__(256) vis_compact_kernel(const int32_t *touched
         c += f[k];
     }
     uint32_t tot;
-    uint32_t off = block_sums[blockIdx.x] + block_exclusive_scan(c, &tot, s_warp);
+    uint32_t loc = block_exclusive_scan(c, &tot, s_warp);
+    uint32_t off = block_sums[blockIdx.x] + loc;
 #pragma unroll
     for (int k = 0; k < kScanIPT; ++k) {
-        const uint32_t key = f[k] ? __float_as_uint(uvdo[base + k].z) : 0u;
         if (f[k]) {
+            const uint32_t key = __float_as_uint(uvdo[base + k].z);
             keys[off] = key;
             vals[off] = (uint32_t)(base + k);
+            s_key[loc] = key;
             ++off;
+            ++loc;
         }
-        hist_add(sh, 4, f[k], key);
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (uint32_t i0 = threadIdx.x - lane; i0 < tot; i0 += 256) {  // warp-uniform rounds
+        const uint32_t i = i0 + lane;
+        hist_add(sh, 4, i < tot, i < tot ? s_key[i] : 0u);
     }
     hist_flush(sh, 4, hist);
 }
@@ -292,11 +305,11 @@ __global__ void __launch_bounds__(kEmitBlock) emit_kernel(ViewTable vt, const ui
 }
 
 // ------------------------------------------------------------------ radix sort
-// Shared memory of a radix-pass block of NT threads (dynamic: 99 KB at NT = 1024).
-template <int NT>
+// Shared memory of a radix-pass block of NT threads with IPT keys each (dynamic: 99 KB for 1024 x 8).
+template <int NT, int IPT>
 struct SortSmem {
-    uint32_t keys[NT * kSortIPT];
-    uint32_t vals[NT * kSortIPT];
+    uint32_t keys[NT * IPT];
+    uint32_t vals[NT * IPT];
     uint32_t whist[NT / 32][256];
     uint32_t excl[256];   // block-local exclusive digit offsets
     uint32_t glob[256];   // global destination of the digit's first key in this block
@@ -306,17 +319,20 @@ struct SortSmem {
     int failed;
 };
 
-// One radix pass, NT threads per block and kSortIPT keys per thread: 256 threads for the depth
+// One radix pass, NT threads per block and IPT keys per thread: 256 threads for the depth
 // passes over the visible items, 1024 for the tile passes over the instances, where a quarter
 // as many blocks means a sixteenth of the look-back's reads (every block starts at once and
 // reads back through about half of the blocks before it).
-// Resident blocks per SM the register allocation must allow: four depth-pass blocks (64
-// registers); two tile-pass blocks (32 registers, about 100 bytes spilled, which costs less than
-// a second wave of blocks: tile sort 0.179 -> 0.172 ms on 2.2 M instances).
-template <int NT> constexpr int sort_min_blocks() { return NT == 256 ? 4 : (NT == 512 ? 3 : 2); }
+// Resident blocks per SM the register allocation must allow: four depth-pass blocks of 8 keys a
+// thread (64 registers), six of 4 (40); two tile-pass blocks (32 registers, about 100 bytes
+// spilled, which costs less than a second wave of blocks: tile sort 0.179 -> 0.172 ms on 2.2 M
+// instances).
+template <int NT, int IPT> constexpr int sort_min_blocks() {
+    return NT == 256 ? (IPT >= 8 ? 4 : 6) : (NT == 512 ? 3 : 2);
+}
 
-template <int NT>
-__global__ void __launch_bounds__(NT, sort_min_blocks<NT>()) onesweep_kernel(const uint32_t *keys_in, const uint32_t *vals_in,
+template <int NT, int IPT>
+__global__ void __launch_bounds__(NT, sort_min_blocks<NT, IPT>()) onesweep_kernel(const uint32_t *keys_in, const uint32_t *vals_in,
                                                       uint32_t *keys_out, uint32_t *vals_out,
                                                       const uint32_t *count_ptr, int shift,
                                                       const uint32_t *pass_hist, uint32_t *tile_ctr,
@@ -326,10 +342,10 @@ __global__ void __launch_bounds__(NT, sort_min_blocks<NT>()) onesweep_kernel(con
                                                       uint32_t emit_vn) {
     pdl_wait();     // the previous kernel's results
     pdl_trigger();  // the next kernel may be scheduled now
-    constexpr int W = NT / 32, TILE = NT * kSortIPT;
+    constexpr int W = NT / 32, TILE = NT * IPT;
     static_assert(NT >= 256, "one thread per digit");
     extern __shared__ __align__(16) unsigned char sort_smem[];
-    SortSmem<NT> &S = *reinterpret_cast<SortSmem<NT> *>(sort_smem);
+    SortSmem<NT, IPT> &S = *reinterpret_cast<SortSmem<NT, IPT> *>(sort_smem);
     uint32_t *s_keys = S.keys, *s_vals = S.vals, *s_excl = S.excl, *s_glob = S.glob, *s_dbase = S.dbase;
     uint32_t(*s_whist)[256] = S.whist;
 
@@ -352,16 +368,16 @@ __global__ void __launch_bounds__(NT, sort_min_blocks<NT>()) onesweep_kernel(con
     const int64_t base = (int64_t)tile * TILE;
     if (base >= n) return;
 
-    uint32_t key[kSortIPT], val[kSortIPT], rank[kSortIPT];
+    uint32_t key[IPT], val[IPT], rank[IPT];
 #pragma unroll
-    for (int r = 0; r < kSortIPT; ++r) {
-        const int64_t i = base + (int64_t)w * (kSortIPT * 32) + r * 32 + lane;
+    for (int r = 0; r < IPT; ++r) {
+        const int64_t i = base + (int64_t)w * (IPT * 32) + r * 32 + lane;
         key[r] = i < n ? keys_in[i] : 0u;
         val[r] = i < n ? vals_in[i] : 0u;
     }
 #pragma unroll
-    for (int r = 0; r < kSortIPT; ++r) {
-        const bool valid = base + (int64_t)w * (kSortIPT * 32) + r * 32 + lane < n;
+    for (int r = 0; r < IPT; ++r) {
+        const bool valid = base + (int64_t)w * (IPT * 32) + r * 32 + lane < n;
         const uint32_t d = (key[r] >> shift) & 255u;
         // lanes with the same digit; an invalid lane matches only itself
         const uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : 256u + lane);
@@ -402,8 +418,8 @@ __global__ void __launch_bounds__(NT, sort_min_blocks<NT>()) onesweep_kernel(con
 
     // local scatter by digit into shared memory (the keys leave the registers before the wait)
 #pragma unroll
-    for (int r = 0; r < kSortIPT; ++r) {
-        int64_t i = base + (int64_t)w * (kSortIPT * 32) + r * 32 + lane;
+    for (int r = 0; r < IPT; ++r) {
+        int64_t i = base + (int64_t)w * (IPT * 32) + r * 32 + lane;
         if (i < n) {
             uint32_t dd = (key[r] >> shift) & 255u;
             uint32_t pos = s_excl[dd] + s_whist[w][dd] + rank[r];
@@ -521,29 +537,29 @@ struct SortBufs {
 // produced the keys).  Input in (k0, v0); output lands in (k0, v0) if n_passes is even,
 // else (k1, v1).  The last pass also adds the tile runs to tile_counts and, with emit_sums,
 // emit_touched[val] to the count of its kEmitBlock-item block of the output (either optional).
-template <int NT>
+template <int NT, int IPT>
 gs_status radix_sort(SortBufs b, const uint32_t *count_ptr, int64_t max_count, int n_passes, const uint32_t *hist,
                      uint32_t *lookback, int lb_tiles, uint32_t *tile_ctrs, int32_t *status, int spin_limit,
                      cudaStream_t st, uint32_t *tile_counts = nullptr, uint32_t n_tiles = 0,
                      const int32_t *emit_touched = nullptr, uint32_t *emit_sums = nullptr, uint32_t emit_vn = 0) {
     if (max_count <= 0 || n_passes <= 0) return GS_OK;
-    constexpr size_t smem = sizeof(SortSmem<NT>);
+    constexpr size_t smem = sizeof(SortSmem<NT, IPT>);
     if (smem > 48 * 1024) {
         // above the static limit: opted in once per device
         static bool opted[64] = {false};
         int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess) return GS_ERR_CUDA;
         if (dev < 0 || dev >= 64 || !opted[dev]) {
-            if (cudaFuncSetAttribute(onesweep_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            if (cudaFuncSetAttribute(onesweep_kernel<NT, IPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
                 cudaSuccess)
                 return GS_ERR_CUDA;
             if (dev >= 0 && dev < 64) opted[dev] = true;
         }
     }
-    int grid = ceil_div(max_count, (int64_t)NT * kSortIPT);
+    int grid = ceil_div(max_count, (int64_t)NT * IPT);
     uint32_t *ki = b.k0, *vi = b.v0, *ko = b.k1, *vo = b.v1;
     for (int p = 0; p < n_passes; ++p) {
-        const gs_status s = launch_pdl(onesweep_kernel<NT>, grid, NT, smem, st, ki, vi, ko, vo, count_ptr, 8 * p,
+        const gs_status s = launch_pdl(onesweep_kernel<NT, IPT>, grid, NT, smem, st, ki, vi, ko, vo, count_ptr, 8 * p,
                                        hist + 256 * p, tile_ctrs + p, lookback + (size_t)p * lb_tiles * 256, status,
                                        spin_limit, p == n_passes - 1 ? tile_counts : nullptr, n_tiles, emit_touched,
                                        p == n_passes - 1 ? emit_sums : nullptr, emit_vn);
@@ -698,10 +714,14 @@ extern "C" gs_status gs_bin_sort(int64_t n, const gs_projected *proj, const gs_c
 
     // 2. stable sort of the visible items by depth (4 passes: result in dk_a/dv_a); the last pass
     //    also counts the instances of every emission block of the sorted items
-    if ((s = radix_sort<kSortThreads>({dk_a, dv_a, dk_b, dv_b}, counters + CTR_NVIS, vn, 4, hist, lookback, L.lb_tiles_depth,
-                        counters + CTR_TILE, out->status, prm.spin_limit, st, nullptr, 0, proj->tiles_touched,
-                        emit_sums, (uint32_t)vn)))
-        return s;
+    auto depth_sort = [&](auto ipt) {
+        return radix_sort<kSortThreads, decltype(ipt)::value>(
+            {dk_a, dv_a, dk_b, dv_b}, counters + CTR_NVIS, vn, 4, hist, lookback, L.lb_tiles_depth, counters + CTR_TILE,
+            out->status, prm.spin_limit, st, nullptr, 0, proj->tiles_touched, emit_sums, (uint32_t)vn);
+    };
+    s = vn <= kSortSmallItems ? depth_sort(std::integral_constant<int, kSortIPTSmall>())
+                              : depth_sort(std::integral_constant<int, kSortIPTLarge>());
+    if (s) return s;
     const uint32_t *sorted_items = dv_a;
 
     // 3. emit instances in depth order; instance count -> n_inst (clamped copy for the sort)
@@ -723,7 +743,7 @@ extern "C" gs_status gs_bin_sort(int64_t n, const gs_projected *proj, const gs_c
     if (out->capacity == 0) return write_ranges_order(tile_counts, out, total_tiles, st);
 
     // 4. stable sort of the instances by tile id
-    if ((s = radix_sort<kSortThreadsInst>({tk_a, emit_vals, tk_b, other_vals}, counters + CTR_M, out->capacity, tile_passes,
+    if ((s = radix_sort<kSortThreadsInst, kSortIPTInst>({tk_a, emit_vals, tk_b, other_vals}, counters + CTR_M, out->capacity, tile_passes,
                         hist + 4 * 256, lookback + (size_t)4 * L.lb_tiles_depth * 256, L.lb_tiles_inst,
                         counters + CTR_TILE + 4, out->status, prm.spin_limit, st, tile_counts, (uint32_t)total_tiles)))
         return s;

@@ -118,6 +118,17 @@ def test_bin_sort_bit_exact_multiview_and_ties():
     _check_sort(gs, cams, C.params_pair()[0])
 
 
+def test_bin_sort_bit_exact_with_the_larger_depth_blocks():
+    """The depth passes take 1,024-key blocks up to 2^21 (view, Gaussian) items and 2,048-key
+    blocks above; the other sort cases are below the switch, this one (300,000 Gaussians in 8
+    views, 2.4M items) is above it."""
+    gs, _, room = C.room_case(300_000, 8, 160, 96, 80.0)
+    poses = synth.keyframe_loop(16, room=room)
+    cams = [synth.camera(160, 96, 80.0, T_cw=poses[2 * i]) for i in range(8)]
+    assert gs.n * len(cams) > 1 << 21
+    _check_sort(gs, cams, C.params_pair()[0])
+
+
 @pytest.mark.parametrize("width", [16, 48])
 def test_bin_sort_bit_exact_long_tiles(width):
     """Tiles of more than 4096 instances: 9,000 Gaussians in front of a 16x16 (one tile) or
