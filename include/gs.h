@@ -127,7 +127,9 @@ typedef struct {
      * without reading what it waited for.  0 = the library default (2^22 polls,
      * about 0.3 s); negative = a block gives up at the first earlier block it
      * looks at (a test hook: gs_bin_sort then reports GS_ERR_TIMEOUT whenever a
-     * radix pass has more than one block of 2048 keys, and a GS_BLOCKS_RING
+     * radix pass has more than one block of keys: 1,024 visible items per depth
+     * pass block up to 2^21 (view, Gaussian) items and 2,048 above, 8,192
+     * instances per tile pass block; and a GS_BLOCKS_RING
      * forward whenever one of its warps has to wait for another). */
     int32_t spin_limit;
     /* Splats the per-tile forward (fwd_blocks GS_BWD_BLOCKS_TILE or
