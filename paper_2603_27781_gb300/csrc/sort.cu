@@ -13,7 +13,7 @@
 //
 // The digit histograms of every pass are counted by the kernels that write the keys (the
 // compaction for the depth keys, the emission for the tile keys) with shared-memory atomics.
-// Each radix pass is one kernel: a block ranks its keys (2048 in a depth pass, 8192 in a tile
+// Each radix pass is one kernel: a block ranks its keys (1024 or 2048 in a depth pass, 8192 in a tile
 // pass) stably within the block (peer lanes of a digit from match_any + per-warp digit
 // counters), publishes its per-digit
 // counts, finds its global offsets by a chained look-back over earlier blocks,
