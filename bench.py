@@ -629,6 +629,28 @@ def run_slam(args, dev, n_frames=8):
                       "untimed three-frame warm-up run of the loop"}
 
 
+def summary(stages_ms, stages_roof, forms, configs, tracking):
+    """The line's main ratios in a few hundred characters, as its last key (so that a reader who
+    keeps only the end of the line still has them); None where that part was not run."""
+    r3 = lambda x: None if x is None else round(float(x), 3)
+    out = {"stages_ms": {k: r3(v) for k, v in stages_ms.items()},
+           "stages_frac": {k: r3(v.get("frac")) for k, v in stages_roof.items() if isinstance(v, dict)}}
+    if forms:
+        fps = {k: r3((forms.get(k) or {}).get("frames_per_s"))
+               for k in ("single_fp32", "batched_fp32", "batched_f16rgb_bf16feat") if isinstance(forms.get(k), dict)}
+        out["forms_frames_per_s"] = fps
+        if fps.get("batched_fp32") and fps.get("batched_f16rgb_bf16feat"):
+            out["half_vs_batched_fp32"] = r3(fps["batched_f16rgb_bf16feat"] / fps["batched_fp32"])
+    if configs:
+        out["configs_ms_per_step"] = {k: r3(v.get("ms_per_step")) for k, v in configs.items() if isinstance(v, dict)}
+        prec = configs.get("precision_2M_d32_bf16_f16") or {}
+        if "speedup_vs_fp32" in prec:
+            out["precision_2M_d32_half_vs_fp32"] = r3(prec["speedup_vs_fp32"])
+    if tracking:
+        out["tracking_ms_per_frame"] = r3(tracking.get("ms_per_frame"))
+    return out
+
+
 def job_rate(ms_local, world, device=None):
     """Whole-job rate of N replicas that each ran one step per ms_local: the slowest rank's
     time per step (max over ranks) and N steps per that time, in steps/s."""
@@ -929,7 +951,8 @@ def run_ours(args, rank, world, local_rank):
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": kernels_per_step(r.n_tiles) * args.steps,
             "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
-            "wall_s": t_wall}
+            "wall_s": t_wall,
+            "summary": summary(dict(zip(stages, per_stage)), stages_roof, forms, configs, tracking)}
     if rank == 0:
         print(json.dumps(line), flush=True)
 

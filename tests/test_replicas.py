@@ -66,3 +66,28 @@ def test_reference_arm_runs_on_rank_zero_only():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_line_summary_is_short_and_tolerates_skipped_parts():
+    """The bench line ends with a compact summary of its ratios (a reader keeping only the
+    line's end still has them); with the forms and configurations skipped it still forms."""
+    sys.path.insert(0, ROOT)
+    import bench
+    stages = {"project": 0.0355, "bin_sort": 0.1667, "render_fwd": 0.322, "loss": 0.0593, "render_bwd": 0.5049,
+              "project_bwd": 0.0512, "pose+dsr+step": 0.0284}
+    roof = {k: {"bound": "hbm", "frac": 0.3} for k in stages}
+    roof["time_weighted_frac"] = 0.25
+    forms = {"single_fp32": {"frames_per_s": 916.9}, "batched_fp32": {"frames_per_s": 1127.1},
+             "batched_f16rgb_bf16feat": {"frames_per_s": 1117.5}}
+    configs = {"batching_24_keyframes": {"ms_per_step": 16.15},
+               "precision_2M_d32_bf16_f16": {"ms_per_step": 12.80, "speedup_vs_fp32": 1.027},
+               "precision_2M_d32_fp32": {"ms_per_step": 13.14},
+               "differentiation_1M_d32_640x480": {"ms_per_step": 0.763}}
+    s = bench.summary(stages, roof, forms, configs, {"ms_per_frame": 25.3})
+    assert s["half_vs_batched_fp32"] == round(1117.5 / 1127.1, 3)
+    assert s["precision_2M_d32_half_vs_fp32"] == 1.027
+    assert s["forms_frames_per_s"]["batched_fp32"] == 1127.1
+    assert "time_weighted_frac" not in s["stages_frac"]
+    assert len(json.dumps(s)) < 1000
+    bare = bench.summary(stages, roof, None, None, None)
+    assert set(bare) == {"stages_ms", "stages_frac"}
